@@ -1,0 +1,190 @@
+/*
+ * lfmm.h -- C ABI of the layered-medium fast multipole boundary-integral solver.
+ *
+ * The library solves 2-D sound-soft acoustic scattering by many bodies in a
+ * medium of horizontal layers with the single-layer, first-kind boundary
+ * integral equation of Sec. 3 of the paper (eqs. integralrep and
+ * BoundaryIntergateEquation), discretised by the lowest-order Nystrom method
+ * (eqs. linearSystem, matrixelmemts).  The operator K is applied by a fast
+ * multipole method with a free-space part per layer and reaction parts per
+ * non-zero reaction component (Sec. 4.1), the system K Phi = b is solved by
+ * GMRES with the overlapping domain-decomposition preconditioner of Sec. 4.2.
+ *
+ * Conventions shared by every call
+ *  - All functions are extern "C", never throw, and return an lfmm_status.
+ *    On error, lfmm_last_error() returns a thread-local message valid until
+ *    the next call on the same thread.  Argument errors are reported before
+ *    any device work.
+ *  - Complex vectors are interleaved (re, im) double precision, column-major
+ *    [n x nrhs] (column j starts at element j*n).
+ *  - The unknown is the paper's Phi = eta * phi and the right-hand side is
+ *    b = eta_{l'} g (Sec. 3.3, eq. matrixandvec); element order is the order
+ *    of the points passed to lfmm_geometry_build.
+ *  - Vector pointers are HOST pointers unless flags contain LFMM_DEVICE_PTRS,
+ *    in which case they are device pointers valid on `stream`.  `stream` is a
+ *    cudaStream_t (NULL = the legacy default stream).  Calls with host
+ *    pointers synchronise the stream before returning.
+ *  - Ownership: input arrays are borrowed for the duration of the call and
+ *    copied; outputs are caller allocated.  Handles are owned by the library
+ *    until the matching _destroy.  A geometry keeps a reference to its medium:
+ *    destroying a medium that still has geometries is refused.
+ *  - Thread safety: calls on different geometries may run concurrently;
+ *    calls on one geometry must be serialised by the caller.
+ */
+#ifndef LFMM_H
+#define LFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LFMM_OK = 0,
+    LFMM_NOT_CONVERGED = 1,           /* warning: outputs are valid (best iterate) */
+    LFMM_ERR_INVALID_ARG = -1,
+    LFMM_ERR_OUT_OF_MEMORY = -2,
+    LFMM_ERR_CUDA = -3,
+    LFMM_ERR_NODE_ON_INTERFACE = -4,  /* a point lies on (or within 1e-12*scale of) an interface */
+    LFMM_ERR_QUADRATURE = -5,
+    LFMM_ERR_TIMEOUT = -6,
+    LFMM_ERR_HBM_BUDGET = -7
+} lfmm_status;
+
+enum {
+    LFMM_DEVICE_PTRS = 1    /* vector arguments are device pointers */
+};
+
+typedef struct lfmm_medium_s *lfmm_medium;
+typedef struct lfmm_geometry_s *lfmm_geometry;
+
+/* FMM parameters (NULL = defaults). */
+typedef struct {
+    int32_t p;          /* expansion order at the fine levels (default 20); coarse levels
+                           raise it with k*w (wide-band rule), up to 80 */
+    int32_t leaf_size;  /* max points per leaf box (default 64) */
+    int32_t flags;      /* reserved, 0 */
+    int32_t reserved;
+} lfmm_params;
+
+/* GMRES parameters (NULL = defaults). */
+typedef struct {
+    double tol;         /* relative residual ||b - K x|| / ||b|| (default 1e-8, Sec. 5) */
+    int32_t max_iter;   /* default 1000 */
+    int32_t restart;    /* 0 = full GMRES (default) */
+    int32_t precond;    /* 1 = overlapping DD preconditioner (Sec. 4.2, default), 0 = none */
+    int32_t reserved;
+} lfmm_gmres_params;
+
+typedef struct {
+    int32_t iterations;        /* Krylov iterations of the last right-hand side */
+    int32_t converged;         /* 1 if every column reached tol */
+    double rel_residual;       /* final GMRES residual estimate (max over columns) */
+    double true_rel_residual;  /* ||b - K x|| / ||b|| recomputed with lfmm_matvec (max over columns) */
+    double solve_seconds;      /* wall time of the solve */
+} lfmm_gmres_info;
+
+/*
+ * Layered medium (Sec. 2.1).  n_layers = L+1 >= 1 layers, top layer first.
+ *   interface_y : L interface heights y = -d_l, strictly decreasing
+ *   wavenumber  : 2*(L+1) doubles, complex k_l (re, im); Re k > 0.  This build
+ *                 supports real wavenumbers only (Im k must be 0).
+ *   density     : L+1 values eta_l > 0 (the paper's "reflection index")
+ * Errors: LFMM_ERR_INVALID_ARG for any violated condition.
+ */
+lfmm_status lfmm_medium_create(int32_t n_layers, const double *interface_y,
+                               const double *wavenumber, const double *density,
+                               lfmm_medium *out);
+lfmm_status lfmm_medium_destroy(lfmm_medium m);
+
+/*
+ * Discretised scatterer boundaries (Sec. 3.3) and everything the fast
+ * operator needs: layer of each point, quadtree and interaction lists,
+ * Sommerfeld tables and near-field blocks, the preconditioner.
+ *   n       : number of elements/collocation points (>= 1)
+ *   points  : 2n doubles, collocation points (x, y) (element centres)
+ *   weights : n doubles, element lengths |Gamma_e| > 0
+ *   normals : 2n doubles or NULL (unused by the single-layer formulation)
+ *   prm     : NULL for defaults
+ * Errors: LFMM_ERR_INVALID_ARG, LFMM_ERR_NODE_ON_INTERFACE, LFMM_ERR_OUT_OF_MEMORY,
+ *         LFMM_ERR_CUDA, LFMM_ERR_QUADRATURE.
+ */
+lfmm_status lfmm_geometry_build(lfmm_medium m, int64_t n, const double *points,
+                                const double *weights, const double *normals,
+                                const lfmm_params *prm, lfmm_geometry *out);
+lfmm_status lfmm_geometry_destroy(lfmm_geometry g);
+
+/*
+ * Right-hand side of a plane incident wave (Sec. 2.2): b = eta_{l'} g with
+ * g = -(u_inc + u^b) on boundaries in the top layer and -u^b below
+ * (eq. homogeneousscattering); u_inc = exp(i k0 (x cos a - y sin a)) in the top
+ * layer, a in (0, pi) measured from the +x axis; u^b the background field.
+ *   nrhs      : number of incidence angles (columns of b)
+ *   angle_rad : nrhs angles (host array)
+ *   b         : [n x nrhs] complex output
+ */
+lfmm_status lfmm_rhs_plane_wave(lfmm_geometry g, int32_t nrhs, const double *angle_rad,
+                                void *b, int32_t flags, void *stream);
+
+/*
+ * y = K x, the Nystrom matrix-vector product of eq. Llayerscomponent (Sec. 3.3),
+ * applied by the layered-medium FMM (Sec. 4.1).  x and y: [n x nrhs] complex.
+ * x and y must not overlap.
+ */
+lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
+                        int32_t flags, void *stream);
+
+/*
+ * Solve K x = b by GMRES (x0 = 0), right-preconditioned by the overlapping
+ * domain-decomposition preconditioner when prm->precond is set (Sec. 4.2).
+ * Returns LFMM_NOT_CONVERGED (with the best iterate in x and info filled) if
+ * max_iter is reached.
+ */
+lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void *b, void *x,
+                             const lfmm_gmres_params *prm, lfmm_gmres_info *info,
+                             void *stream);
+
+/*
+ * Scattered field u^s at m off-boundary targets from the density Phi
+ * (eq. integralrep):  u^s(r) = (1/eta_{l(r)}) sum_e Phi_e |Gamma_e| G_{l_e l(r)}(c_e, r).
+ *   density : [n x nrhs] complex Phi
+ *   targets : 2m doubles (host)
+ *   u       : [m x nrhs] complex output
+ * A target on an interface returns LFMM_ERR_NODE_ON_INTERFACE.
+ */
+lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void *density, int64_t m,
+                            const double *targets, void *u, int32_t flags, void *stream);
+
+/*
+ * Elements of closed counter-clockwise polygons (Sec. 3.3: straight elements,
+ * collocation at the element centre).  Host-only helper.
+ *   n_poly, counts : number of polygons and vertices per polygon
+ *   vertices       : concatenated (x, y) vertices
+ *   points, weights, normals : outputs (2N, N, 2N doubles), N = sum(counts);
+ *                    chord midpoints, chord lengths, outward unit normals
+ */
+lfmm_status lfmm_polygon_elements(int32_t n_poly, const int32_t *counts, const double *vertices,
+                                  double *points, double *weights, double *normals);
+
+/*
+ * Introspection of a built geometry (used by the tests).  Copies the named
+ * array to host memory: `needed` receives its size in bytes; if host_out is
+ * NULL or nbytes is too small nothing is copied.  Names: "perm" (int32[n],
+ * sorted position -> input index), "box_level", "box_layer", "box_ix",
+ * "box_iy", "box_begin", "box_end", "box_parent" (int32[nbox]),
+ * "tree_params" (double[8]: x0, y0, W, D, l0, nbox, ncomp, n_near_blocks),
+ * "p_level" (int32[D+1]), "vfree_ptr"/"vfree_idx", "ufree_ptr"/"ufree_idx",
+ * "vreact_ptr"/"vreact_idx"/"vreact_comp", "ureact_ptr"/"ureact_idx"/"ureact_comp"
+ * (CSR over boxes), "components" (int32[4*ncomp]: ls, a, lt, b).
+ */
+lfmm_status lfmm_geometry_query(lfmm_geometry g, const char *name, void *host_out,
+                                int64_t nbytes, int64_t *needed);
+
+const char *lfmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFMM_H */

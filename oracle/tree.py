@@ -16,9 +16,11 @@ framework without giving its parameters; this is the reading used here):
     no cell of any layer holds more than ``leaf_size`` points (at most 18);
   * points are ordered by (layer, Morton key at level D, original index);
     boxes by (level, layer, Morton key);
-  * expansion order per level p_l = max(p, ceil(1.5 k_max w_l) + 12) with
-    w_l = W / 2^l, and expansions are used from the first level l0 >= 2 with
-    p_l <= 80 (coarser levels only pass their lists down);
+  * expansion order per level p_l = max(p, ceil(kR + 9 (kR)^(1/3))) with
+    kR = k_max w_l / sqrt(2) (box radius times the largest wavenumber; the
+    excess-bandwidth rule of wide-band multipole methods), w_l = W / 2^l, and
+    expansions are used from the first level l0 >= 2 with p_l <= 80 (coarser
+    levels only pass their lists down);
   * free-space lists (same layer): the candidates of box T are the children
     of its parent's near list (the root of T's layer at level 0); below l0
     all candidates stay near; from l0 on a candidate is near if its cell
@@ -142,7 +144,10 @@ class Tree:
                 break
         self.D = D
         kmax = float(np.max(k))
-        self.p_level = [max(p, int(math.ceil(1.5 * kmax * (W / float(1 << l)))) + 12) for l in range(D + 1)]
+        self.p_level = []
+        for l in range(D + 1):
+            kr = kmax * (W / float(1 << l)) * 0.70710678118654752
+            self.p_level.append(max(p, int(math.ceil(kr + 9.0 * math.pow(kr, 1.0 / 3.0)))))
         self.l0 = D + 1
         for l in range(L0_MIN, D + 1):
             if self.p_level[l] <= P_CAP:

@@ -1,0 +1,472 @@
+// api.cu -- the C ABI (include/lfmm.h): validation, handles, host/device marshalling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "geometry.h"
+
+namespace lfmm {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw CudaError{std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+struct ArgError {
+    std::string msg;
+};
+struct InterfaceError {
+    std::string msg;
+};
+
+// 8-point Gauss-Legendre rule by Newton iteration on P_8 (no stored tables)
+static void gauss_legendre8(double* x, double* w) {
+    const int n = 8;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+QuadRule make_quad_rule(const MediumDev& m) {
+    QuadRule q;
+    q.T = 1.2 * m.kmax + 1.0;
+    q.es_v0 = -3.6;
+    q.es_hv = 0.07;
+    q.nes = 84;          // v in [-3.6, 2.21]
+    q.min_panels = 16;
+    gauss_legendre8(q.gl_x, q.gl_w);
+    return q;
+}
+
+template <class F>
+static lfmm_status guarded(F&& f) {
+    try {
+        t_last_error.clear();
+        return f();
+    } catch (const ArgError& e) {
+        set_error(e.msg);
+        return LFMM_ERR_INVALID_ARG;
+    } catch (const InterfaceError& e) {
+        set_error(e.msg);
+        return LFMM_ERR_NODE_ON_INTERFACE;
+    } catch (const CudaError& e) {
+        set_error(e.msg);
+        if (e.msg.find("out of memory") != std::string::npos) return LFMM_ERR_OUT_OF_MEMORY;
+        return LFMM_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LFMM_ERR_OUT_OF_MEMORY;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return LFMM_ERR_INVALID_ARG;
+    } catch (...) {
+        set_error("unknown error");
+        return LFMM_ERR_CUDA;
+    }
+}
+
+static void require(bool c, const char* msg) {
+    if (!c) throw ArgError{msg};
+}
+
+static void free_geometry(lfmm_geometry_s* g) {
+    for (void* p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+    if (g->d_xs) cudaFree(g->d_xs);
+    if (g->d_ys) cudaFree(g->d_ys);
+    if (g->d_hostbuf_x) cudaFree(g->d_hostbuf_x);
+    if (g->d_hostbuf_y) cudaFree(g->d_hostbuf_y);
+}
+
+// sorted-order scratch and host staging for nrhs columns
+static void ensure_scratch(lfmm_geometry_s* g, int nrhs) {
+    if (g->nrhs_cap < nrhs) {
+        if (g->d_xs) cudaFree(g->d_xs);
+        if (g->d_ys) cudaFree(g->d_ys);
+        g->d_xs = g->d_ys = nullptr;
+        cuda_check(cudaMalloc(&g->d_xs, sizeof(cd) * g->n * nrhs), "cudaMalloc scratch");
+        cuda_check(cudaMalloc(&g->d_ys, sizeof(cd) * g->n * nrhs), "cudaMalloc scratch");
+        g->nrhs_cap = nrhs;
+    }
+}
+static void ensure_hostbuf(lfmm_geometry_s* g, size_t elems) {
+    if (g->hostbuf_cap < elems) {
+        if (g->d_hostbuf_x) cudaFree(g->d_hostbuf_x);
+        if (g->d_hostbuf_y) cudaFree(g->d_hostbuf_y);
+        g->d_hostbuf_x = g->d_hostbuf_y = nullptr;
+        cuda_check(cudaMalloc(&g->d_hostbuf_x, sizeof(cd) * elems), "cudaMalloc staging");
+        cuda_check(cudaMalloc(&g->d_hostbuf_y, sizeof(cd) * elems), "cudaMalloc staging");
+        g->hostbuf_cap = elems;
+    }
+}
+
+}  // namespace lfmm
+
+using namespace lfmm;
+
+extern "C" {
+
+const char* lfmm_last_error(void) { return t_last_error.c_str(); }
+
+lfmm_status lfmm_medium_create(int32_t n_layers, const double* interface_y, const double* wavenumber,
+                               const double* density, lfmm_medium* out) {
+    return guarded([&]() -> lfmm_status {
+        require(out != nullptr, "out is NULL");
+        require(n_layers >= 1 && n_layers <= LFMM_MAXLAY, "n_layers must be in [1, 16]");
+        require(wavenumber != nullptr && density != nullptr, "wavenumber/density is NULL");
+        require(n_layers == 1 || interface_y != nullptr, "interface_y is NULL");
+        lfmm_medium_s* m = new lfmm_medium_s();
+        std::memset(&m->m, 0, sizeof(m->m));
+        m->m.nl = n_layers;
+        m->m.kmax = 0.0;
+        for (int j = 0; j + 1 < n_layers; ++j) {
+            double y = interface_y[j];
+            if (!std::isfinite(y) || (j > 0 && !(y < interface_y[j - 1]))) {
+                delete m;
+                throw ArgError{"interface heights must be finite and strictly decreasing"};
+            }
+            m->m.yint[j] = y;
+        }
+        for (int l = 0; l < n_layers; ++l) {
+            double kr = wavenumber[2 * l], ki = wavenumber[2 * l + 1];
+            double eta = density[l];
+            if (!(std::isfinite(kr) && kr > 0.0) || ki != 0.0 || !(std::isfinite(eta) && eta > 0.0)) {
+                delete m;
+                throw ArgError{"wavenumbers must be real and positive (Im k = 0) and densities positive"};
+            }
+            m->m.k[l] = kr;
+            m->m.eta[l] = eta;
+            m->m.kmax = std::max(m->m.kmax, kr);
+        }
+        *out = m;
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_medium_destroy(lfmm_medium m) {
+    return guarded([&]() -> lfmm_status {
+        if (!m) return LFMM_OK;
+        require(m->geometries == 0, "medium still referenced by a geometry");
+        delete m;
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points, const double* weights,
+                                const double* normals, const lfmm_params* prm, lfmm_geometry* out) {
+    (void)normals;
+    lfmm_geometry_s* g = nullptr;
+    lfmm_status st = guarded([&]() -> lfmm_status {
+        auto t0 = std::chrono::steady_clock::now();
+        require(med != nullptr && out != nullptr, "medium/out is NULL");
+        require(n >= 1 && n < (int64_t)1 << 31, "n must be in [1, 2^31)");
+        require(points != nullptr && weights != nullptr, "points/weights is NULL");
+        int p = prm ? prm->p : 20;
+        int leaf = prm ? prm->leaf_size : 64;
+        require(p >= 1 && p <= 80, "p must be in [1, 80]");
+        require(leaf >= 1 && leaf <= 1024, "leaf_size must be in [1, 1024]");
+        const MediumDev& m = med->m;
+        std::vector<double> px(n), py(n), pw(n);
+        std::vector<int> layer(n);
+        for (int64_t i = 0; i < n; ++i) {
+            px[i] = points[2 * i];
+            py[i] = points[2 * i + 1];
+            pw[i] = weights[i];
+            require(std::isfinite(px[i]) && std::isfinite(py[i]), "points must be finite");
+            require(std::isfinite(pw[i]) && pw[i] > 0.0, "weights must be positive");
+            int l = 0;
+            while (l < m.nl - 1 && py[i] < m.yint[l]) ++l;
+            layer[i] = l;
+            for (int j = 0; j + 1 < m.nl; ++j) {
+                double sc = std::max(1.0, std::fabs(m.yint[j]));
+                if (std::fabs(py[i] - m.yint[j]) <= 1e-12 * sc)
+                    throw InterfaceError{"a collocation point lies on an interface"};
+            }
+        }
+        g = new lfmm_geometry_s();
+        g->med = med;
+        g->m = m;
+        g->n = n;
+        g->p = p;
+        g->leaf_size = leaf;
+        g->quad = make_quad_rule(m);
+        build_tree(g->tree, px, py, layer, m, p, leaf);
+        TreeHost& t = g->tree;
+        // sorted-order copies
+        g->hx.resize(n); g->hy.resize(n); g->hw.resize(n);
+        for (int64_t s = 0; s < n; ++s) {
+            int i = t.perm[s];
+            g->hx[s] = px[i]; g->hy[s] = py[i]; g->hw[s] = pw[i];
+        }
+        g->d_x = dupload(g, g->hx);
+        g->d_y = dupload(g, g->hy);
+        g->d_w = dupload(g, g->hw);
+        g->d_layer = dupload(g, t.layer_sorted);
+        g->d_perm = dupload(g, t.perm);
+        g->d_box_begin = dupload(g, t.box_begin);
+        g->d_box_end = dupload(g, t.box_end);
+        g->d_box_layer = dupload(g, t.box_layer);
+        g->d_box_level = dupload(g, t.box_level);
+        g->d_box_ix = dupload(g, t.box_ix);
+        g->d_box_iy = dupload(g, t.box_iy);
+        g->d_box_parent = dupload(g, t.box_parent);
+        g->d_child_begin = dupload(g, t.child_begin);
+        g->d_child_end = dupload(g, t.child_end);
+        std::vector<double> bcx(t.nbox), bcy(t.nbox);
+        for (int b = 0; b < t.nbox; ++b) { bcx[b] = t.cx(b); bcy[b] = t.cy(b); }
+        g->d_box_cx = dupload(g, bcx);
+        g->d_box_cy = dupload(g, bcy);
+        std::vector<int> comp(4 * std::max<size_t>(t.comps.size(), 1), 0);
+        for (size_t c = 0; c < t.comps.size(); ++c) {
+            comp[4 * c] = t.comps[c].ls; comp[4 * c + 1] = t.comps[c].a;
+            comp[4 * c + 2] = t.comps[c].lt; comp[4 * c + 3] = t.comps[c].b;
+        }
+        g->d_comp = dupload(g, comp);
+        near_build(g);
+        fmm_build(g);
+        g->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        med->geometries += 1;
+        *out = g;
+        return LFMM_OK;
+    });
+    if (st != LFMM_OK && g) {
+        free_geometry(g);
+        delete g;
+    }
+    return st;
+}
+
+lfmm_status lfmm_geometry_destroy(lfmm_geometry g) {
+    return guarded([&]() -> lfmm_status {
+        if (!g) return LFMM_OK;
+        cudaDeviceSynchronize();
+        free_geometry(g);
+        if (g->med) g->med->geometries -= 1;
+        delete g;
+        return LFMM_OK;
+    });
+}
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, int32_t flags, void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && x != nullptr && y != nullptr, "NULL argument");
+        require(nrhs >= 1, "nrhs must be >= 1");
+        require(x != y, "x and y must not overlap");
+        cudaStream_t s = as_stream(stream);
+        ensure_scratch(g, nrhs);
+        const size_t elems = (size_t)g->n * nrhs;
+        const cd* xin = (const cd*)x;
+        cd* yout = (cd*)y;
+        const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
+        if (!dev) {
+            ensure_hostbuf(g, elems);
+            cuda_check(cudaMemcpyAsync(g->d_hostbuf_x, x, sizeof(cd) * elems, cudaMemcpyHostToDevice, s), "x h2d");
+            xin = g->d_hostbuf_x;
+            yout = g->d_hostbuf_y;
+        }
+        gather_sorted(g, xin, g->d_xs, nrhs, s);
+        apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s);
+        scatter_sorted(g, g->d_ys, yout, nrhs, s);
+        if (!dev) {
+            cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "y d2h");
+            cuda_check(cudaStreamSynchronize(s), "matvec sync");
+        }
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void* x, const lfmm_gmres_params* prm,
+                             lfmm_gmres_info* info, void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && b != nullptr && x != nullptr, "NULL argument");
+        require(nrhs >= 1, "nrhs must be >= 1");
+        double tol = prm ? prm->tol : 1e-8;
+        int maxit = prm ? prm->max_iter : 1000;
+        int pre = prm ? prm->precond : 1;
+        require(tol > 0.0 && maxit >= 1, "invalid GMRES parameters");
+        require(!prm || prm->restart == 0, "restarted GMRES is not available in this build (restart must be 0)");
+        cudaStream_t s = as_stream(stream);
+        if (pre && !g->pc_ready) precond_build(g);
+        ensure_scratch(g, nrhs);
+        const size_t elems = (size_t)g->n * nrhs;
+        cd* bb = nullptr;
+        cd* xx = nullptr;
+        cuda_check(cudaMalloc(&bb, sizeof(cd) * elems), "malloc b");
+        cuda_check(cudaMalloc(&xx, sizeof(cd) * elems), "malloc x");
+        struct F { cd *a, *b; ~F() { cudaFree(a); cudaFree(b); } } fr{bb, xx};
+        cuda_check(cudaMemcpyAsync(g->d_ys, b, sizeof(cd) * elems, cudaMemcpyDefault, s), "b copy");
+        gather_sorted(g, g->d_ys, bb, nrhs, s);
+        lfmm_gmres_info local;
+        int ok = gmres_sorted(g, bb, xx, nrhs, tol, maxit, pre != 0, s, info ? info : &local);
+        scatter_sorted(g, xx, g->d_ys, nrhs, s);
+        cuda_check(cudaMemcpyAsync(x, g->d_ys, sizeof(cd) * elems, cudaMemcpyDefault, s), "x copy");
+        cuda_check(cudaStreamSynchronize(s), "gmres sync");
+        return ok ? LFMM_OK : LFMM_NOT_CONVERGED;
+    });
+}
+
+lfmm_status lfmm_rhs_plane_wave(lfmm_geometry g, int32_t nrhs, const double* angle_rad, void* b, int32_t flags,
+                                void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && angle_rad != nullptr && b != nullptr, "NULL argument");
+        require(nrhs >= 1, "nrhs must be >= 1");
+        for (int c = 0; c < nrhs; ++c)
+            require(std::isfinite(angle_rad[c]) && angle_rad[c] > 0.0 && angle_rad[c] < M_PI,
+                    "incidence angles must lie in (0, pi)");
+        cudaStream_t s = as_stream(stream);
+        ensure_scratch(g, nrhs);
+        rhs_plane_wave_sorted(g, nrhs, angle_rad, g->d_xs, s);
+        const size_t elems = (size_t)g->n * nrhs;
+        if (flags & LFMM_DEVICE_PTRS) {
+            scatter_sorted(g, g->d_xs, (cd*)b, nrhs, s);
+        } else {
+            scatter_sorted(g, g->d_xs, g->d_ys, nrhs, s);
+            cuda_check(cudaMemcpyAsync(b, g->d_ys, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "b d2h");
+            cuda_check(cudaStreamSynchronize(s), "rhs sync");
+        }
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void* density, int64_t m, const double* targets,
+                            void* u, int32_t flags, void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && density != nullptr && targets != nullptr && u != nullptr, "NULL argument");
+        require(nrhs >= 1 && m >= 1, "nrhs and m must be >= 1");
+        const MediumDev& md = g->m;
+        for (int64_t i = 0; i < m; ++i) {
+            require(std::isfinite(targets[2 * i]) && std::isfinite(targets[2 * i + 1]), "targets must be finite");
+            for (int j = 0; j + 1 < md.nl; ++j) {
+                double sc = std::max(1.0, std::fabs(md.yint[j]));
+                if (std::fabs(targets[2 * i + 1] - md.yint[j]) <= 1e-12 * sc)
+                    throw InterfaceError{"a target lies on an interface"};
+            }
+        }
+        cudaStream_t s = as_stream(stream);
+        ensure_scratch(g, nrhs);
+        const size_t elems = (size_t)g->n * nrhs;
+        cuda_check(cudaMemcpyAsync(g->d_ys, density, sizeof(cd) * elems, cudaMemcpyDefault, s), "density copy");
+        gather_sorted(g, g->d_ys, g->d_xs, nrhs, s);
+        double* d_t = nullptr;
+        cd* d_u = nullptr;
+        cuda_check(cudaMalloc(&d_t, sizeof(double) * 2 * m), "malloc targets");
+        cuda_check(cudaMalloc(&d_u, sizeof(cd) * m * nrhs), "malloc u");
+        struct F { double* a; cd* b; ~F() { cudaFree(a); cudaFree(b); } } fr{d_t, d_u};
+        cuda_check(cudaMemcpyAsync(d_t, targets, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s), "targets");
+        eval_field_direct(g, nrhs, g->d_xs, m, d_t, d_u, s);
+        cuda_check(cudaMemcpyAsync(u, d_u, sizeof(cd) * m * nrhs, cudaMemcpyDefault, s), "u copy");
+        cuda_check(cudaStreamSynchronize(s), "field sync");
+        (void)flags;
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_polygon_elements(int32_t n_poly, const int32_t* counts, const double* vertices, double* points,
+                                  double* weights, double* normals) {
+    return guarded([&]() -> lfmm_status {
+        require(n_poly >= 1 && counts && vertices && points && weights, "NULL or empty argument");
+        int64_t base = 0;
+        for (int pI = 0; pI < n_poly; ++pI) {
+            int nv = counts[pI];
+            require(nv >= 3, "a polygon needs at least 3 vertices");
+            for (int e = 0; e < nv; ++e) {
+                const double* a = vertices + 2 * (base + e);
+                const double* b = vertices + 2 * (base + (e + 1) % nv);
+                double tx = b[0] - a[0], ty = b[1] - a[1];
+                double len = std::hypot(tx, ty);
+                require(len > 0.0, "degenerate (zero-length) edge");
+                points[2 * (base + e)] = 0.5 * (a[0] + b[0]);
+                points[2 * (base + e) + 1] = 0.5 * (a[1] + b[1]);
+                weights[base + e] = len;
+                if (normals) {
+                    normals[2 * (base + e)] = ty / len;
+                    normals[2 * (base + e) + 1] = -tx / len;
+                }
+            }
+            base += nv;
+        }
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_out, int64_t nbytes,
+                                int64_t* needed) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && name != nullptr, "NULL argument");
+        TreeHost& t = g->tree;
+        std::vector<int> tmp;
+        std::vector<double> dtmp;
+        const void* src = nullptr;
+        int64_t bytes = 0;
+        std::string nm(name);
+        auto iv = [&](const std::vector<int>& v) { src = v.data(); bytes = (int64_t)(v.size() * sizeof(int)); };
+        if (nm == "perm") iv(t.perm);
+        else if (nm == "box_level") iv(t.box_level);
+        else if (nm == "box_layer") iv(t.box_layer);
+        else if (nm == "box_ix") iv(t.box_ix);
+        else if (nm == "box_iy") iv(t.box_iy);
+        else if (nm == "box_begin") iv(t.box_begin);
+        else if (nm == "box_end") iv(t.box_end);
+        else if (nm == "box_parent") iv(t.box_parent);
+        else if (nm == "p_level") iv(t.p_level);
+        else if (nm == "vfree_ptr") iv(t.vfree_ptr);
+        else if (nm == "vfree_idx") iv(t.vfree_idx);
+        else if (nm == "ufree_ptr") iv(t.ufree_ptr);
+        else if (nm == "ufree_idx") iv(t.ufree_idx);
+        else if (nm == "vreact_ptr") iv(t.vreact_ptr);
+        else if (nm == "vreact_idx") iv(t.vreact_idx);
+        else if (nm == "vreact_comp") iv(t.vreact_comp);
+        else if (nm == "ureact_ptr") iv(t.ureact_ptr);
+        else if (nm == "ureact_idx") iv(t.ureact_idx);
+        else if (nm == "ureact_comp") iv(t.ureact_comp);
+        else if (nm == "components") {
+            for (auto& c : t.comps) { tmp.push_back(c.ls); tmp.push_back(c.a); tmp.push_back(c.lt); tmp.push_back(c.b); }
+            iv(tmp);
+        } else if (nm == "tree_params") {
+            dtmp = {t.x0, t.y0, t.W, (double)t.D, (double)t.l0, (double)t.nbox, (double)t.comps.size(),
+                    (double)g->n_blocks, (double)g->nb_nnz, (double)g->n_rkeys, g->setup_seconds};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else {
+            throw ArgError{"unknown query name"};
+        }
+        if (needed) *needed = bytes;
+        if (host_out && nbytes >= bytes && bytes > 0) std::memcpy(host_out, src, (size_t)bytes);
+        return LFMM_OK;
+    });
+}
+
+}  // extern "C"

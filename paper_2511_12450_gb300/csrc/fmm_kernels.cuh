@@ -1,0 +1,344 @@
+// fmm_kernels.cuh -- device kernels of the far field (Sec. 4.1).
+//
+// One quadtree per layer carries one set of expansions with the layer's
+// wavenumber k:
+//   multipole  M_n = sum_j Q_j J_n(k rho_j) e^{-i n theta_j}     (about the box centre)
+//   local      u(r) = sum_n L_n J_n(k rho) e^{i n theta}         (about the box centre)
+// with Q_j = |Gamma_j| Phi_j.  The free-space part uses Graf's addition
+// theorem (M2M, M2L with H_{m-n}, L2L).  Every reaction component reuses the
+// same multipoles and locals: in the component's image frame (x, h) the
+// source-side expansion of the paper, alpha_n = sum Q J_n(k rho) e^{i n theta'}
+// (eq. MEcoefficients), is M_n when the height is measured downward
+// (theta' = -theta) and (-1)^n M_{-n} when it is measured upward; likewise the
+// target-side local expansion (eq. LEformula) lands in L_m or, with (-1)^m, in
+// L_{-m}.  The reaction M2L is then the paper's dense translation
+// beta_m = sum_n I_{nm} alpha_n (eq. metoleimage) with the moments I_{nm} of
+// eq. generalintegral tabulated per box-pair geometry.
+#pragma once
+#include "devmath.cuh"
+#include "sommerfeld.cuh"
+
+namespace lfmm {
+
+#define LFMM_PMAX 80
+
+// P2M on the leaves: one CTA (128 threads) per leaf; points in chunks of 32.
+__global__ void k_p2m(const int* __restrict__ box_begin, const int* __restrict__ box_end,
+                      const int* __restrict__ box_layer, const double* __restrict__ bcx,
+                      const double* __restrict__ bcy, const int64_t* __restrict__ coef_off, int leaf0,
+                      int p, MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
+                      const double* __restrict__ pw, const cd* __restrict__ phi, int64_t n, int nrhs,
+                      int64_t ncoef, cd* __restrict__ M) {
+    extern __shared__ double sm[];
+    const int np1 = p + 1;
+    double* J = sm;                          // [32][p+1]
+    cd* zp = (cd*)(sm + 32 * np1);           // [32][p+1]   z^n, z = e^{-i theta}
+    cd* q = zp + 32 * np1;                   // [32] charges of the current column
+    const int B = leaf0 + blockIdx.x;
+    const int b0 = box_begin[B], nb = box_end[B] - b0;
+    const double k = m.k[box_layer[B]];
+    const double cx = bcx[B], cy = bcy[B];
+    const int64_t off = coef_off[B];
+    const int nco = 2 * p + 1;
+    for (int col = 0; col < nrhs; ++col) {
+        // accumulators: thread t owns coefficient indices t, t+128, ...
+        cd acc[2] = {mk(0, 0), mk(0, 0)};
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const int cnt = min(32, nb - c0);
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                const int j = b0 + c0 + threadIdx.x;
+                double dx = px[j] - cx, dy = py[j] - cy;
+                double rho = hypot(dx, dy);
+                bessel_j_seq(k * rho, p, J + threadIdx.x * np1);
+                cd z = (rho > 0.0) ? mk(dx / rho, -dy / rho) : mk(1.0, 0.0);
+                cd zz = mk(1.0, 0.0);
+                for (int t = 0; t <= p; ++t) { zp[threadIdx.x * np1 + t] = zz; zz = zz * z; }
+                q[threadIdx.x] = pw[j] * phi[(int64_t)col * n + j];
+            }
+            __syncthreads();
+            for (int s = 0; s < 2; ++s) {
+                int idx = threadIdx.x + 128 * s;
+                if (idx >= nco) break;
+                int nn = idx - p;
+                int an = nn < 0 ? -nn : nn;
+                cd a = acc[s];
+                for (int j = 0; j < cnt; ++j) {
+                    double jv = J[j * np1 + an];
+                    cd zn = zp[j * np1 + an];
+                    if (nn < 0) { zn = conjc(zn); if (an & 1) jv = -jv; }
+                    cfma(a, jv * q[j], zn);
+                }
+                acc[s] = a;
+            }
+        }
+        for (int s = 0; s < 2; ++s) {
+            int idx = threadIdx.x + 128 * s;
+            if (idx < nco) M[(int64_t)col * ncoef + off + idx] = acc[s];
+        }
+    }
+}
+
+// M2M for the parents at one level: M^P_n = sum_C sum_m M^C_m S^{quad(C)}_{n-m}
+__global__ void k_m2m(int lev_par_start, const int* __restrict__ child_begin, const int* __restrict__ child_end,
+                      const int* __restrict__ box_ix, const int* __restrict__ box_iy,
+                      const int* __restrict__ box_layer, const int64_t* __restrict__ coef_off, int pP, int pC,
+                      const cd* __restrict__ tab, const int64_t* __restrict__ tab_off, int lev_child, int nlev,
+                      int nrhs, int64_t ncoef, cd* __restrict__ M) {
+    extern __shared__ cd smc[];  // child coefficients
+    const int P = lev_par_start + blockIdx.x;
+    const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
+    const int layer = box_layer[P];
+    for (int col = 0; col < nrhs; ++col) {
+        cd acc[2] = {mk(0, 0), mk(0, 0)};
+        for (int C = child_begin[P]; C < child_end[P]; ++C) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < ncC; i += blockDim.x) smc[i] = M[(int64_t)col * ncoef + coef_off[C] + i];
+            __syncthreads();
+            int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
+            const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];   // index k + hw
+            for (int s = 0; s < 2; ++s) {
+                int idx = threadIdx.x + blockDim.x * s;
+                if (idx >= ncP) break;
+                int nn = idx - pP;
+                cd a = acc[s];
+                for (int mm = -pC; mm <= pC; ++mm) cfma(a, smc[mm + pC], S[nn - mm + hw]);
+                acc[s] = a;
+            }
+        }
+        for (int s = 0; s < 2; ++s) {
+            int idx = threadIdx.x + blockDim.x * s;
+            if (idx < ncP) M[(int64_t)col * ncoef + coef_off[P] + idx] = acc[s];
+        }
+    }
+}
+
+// M2L into every target box of levels >= l0 (free space and reaction components).
+// One CTA per target box; threads over output coefficients.
+__global__ void k_m2l(int box_first, const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ vf_ptr,
+                      const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
+                      const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
+                      const int* __restrict__ vr_ptr, const int* __restrict__ vr_src,
+                      const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
+                      const int* __restrict__ comp, const ReactKey* __restrict__ rkeys,
+                      const cd* __restrict__ m2lr, int nrhs, int64_t ncoef, const cd* __restrict__ Min,
+                      cd* __restrict__ Lout) {
+    extern __shared__ cd sms[];   // source coefficients
+    const int T = box_first + blockIdx.x;
+    const int l = box_level[T];
+    const int p = p_level[l];
+    const int nco = 2 * p + 1;
+    for (int col = 0; col < nrhs; ++col) {
+        const cd* Mc = Min + (int64_t)col * ncoef;
+        cd acc[2] = {mk(0, 0), mk(0, 0)};
+        // free space: L_n += sum_m M_m Tab[m - n]
+        for (int e = vf_ptr[T]; e < vf_ptr[T + 1]; ++e) {
+            __syncthreads();
+            const int64_t so = coef_off[vf_src[e]];
+            for (int i = threadIdx.x; i < nco; i += blockDim.x) sms[i] = Mc[so + i];
+            __syncthreads();
+            const cd* tb = m2lf + m2lf_off[vf_tab[e]] + 2 * p;   // index k + 2p
+            for (int s = 0; s < 2; ++s) {
+                int idx = threadIdx.x + blockDim.x * s;
+                if (idx >= nco) break;
+                int nn = idx - p;
+                cd a = acc[s];
+                for (int mm = -p; mm <= p; ++mm) cfma(a, sms[mm + p], tb[mm - nn]);
+                acc[s] = a;
+            }
+        }
+        // reaction components
+        for (int e = vr_ptr[T]; e < vr_ptr[T + 1]; ++e) {
+            __syncthreads();
+            const int64_t so = coef_off[vr_src[e]];
+            const int c = vr_comp[e];
+            const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
+            // alpha_n = M_n (arrival down) or (-1)^n M_{-n} (arrival up)
+            for (int i = threadIdx.x; i < nco; i += blockDim.x) {
+                int nn = i - p;
+                cd v;
+                if (a_dir == 1) v = Mc[so + i];
+                else { v = Mc[so + (-nn + p)]; if (nn & 1) v = -v; }
+                sms[i] = v;
+            }
+            __syncthreads();
+            const ReactKey rk = rkeys[vr_key[e]];
+            const cd* I = m2lr + rk.off;
+            for (int s = 0; s < 2; ++s) {
+                int idx = threadIdx.x + blockDim.x * s;
+                if (idx >= nco) break;
+                int nout = idx - p;
+                // departure down: L_m += beta_m;  departure up: L_{-m} += (-1)^m beta_m
+                int mrow = (b_dir == 1) ? nout : -nout;
+                const cd* row = I + (int64_t)(mrow + p) * nco;
+                cd bsum = mk(0, 0);
+                for (int i = 0; i < nco; ++i) cfma(bsum, row[i], sms[i]);
+                if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
+                acc[s] += bsum;
+            }
+        }
+        for (int s = 0; s < 2; ++s) {
+            int idx = threadIdx.x + blockDim.x * s;
+            if (idx < nco) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[s];
+        }
+    }
+}
+
+// L2L for the children at one level: L^C_n += sum_m L^P_m S'^{quad(C)}_{m-n}
+__global__ void k_l2l(int lev_child_start, const int* __restrict__ box_parent, const int* __restrict__ box_ix,
+                      const int* __restrict__ box_iy, const int* __restrict__ box_layer,
+                      const int64_t* __restrict__ coef_off, int pP, int pC, const cd* __restrict__ tab,
+                      const int64_t* __restrict__ tab_off, int lev_child, int nlev, int nrhs, int64_t ncoef,
+                      cd* __restrict__ L) {
+    extern __shared__ cd smp[];
+    const int C = lev_child_start + blockIdx.x;
+    const int P = box_parent[C];
+    const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
+    const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
+    const cd* S = tab + tab_off[(box_layer[C] * nlev + lev_child) * 4 + quad];
+    for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncP; i += blockDim.x) smp[i] = L[(int64_t)col * ncoef + coef_off[P] + i];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < ncC; idx += blockDim.x) {
+            int nn = idx - pC;
+            cd a = mk(0, 0);
+            for (int mm = -pP; mm <= pP; ++mm) cfma(a, smp[mm + pP], S[mm - nn + hw]);
+            L[(int64_t)col * ncoef + coef_off[C] + idx] += a;
+        }
+    }
+}
+
+// L2P on the leaves: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
+__global__ void k_l2p(const int* __restrict__ box_begin, const int* __restrict__ box_end,
+                      const int* __restrict__ box_layer, const double* __restrict__ bcx,
+                      const double* __restrict__ bcy, const int64_t* __restrict__ coef_off, int leaf0, int p,
+                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n,
+                      int nrhs, int64_t ncoef, const cd* __restrict__ L, cd* __restrict__ y) {
+    extern __shared__ double sl[];
+    const int np1 = p + 1, nco = 2 * p + 1;
+    cd* Ls = (cd*)sl;                               // [nco]
+    double* Jall = sl + 2 * nco;                     // [blockDim][p+1]
+    const int B = leaf0 + blockIdx.x;
+    const int b0 = box_begin[B], nb = box_end[B] - b0;
+    const double k = m.k[box_layer[B]];
+    const double cx = bcx[B], cy = bcy[B];
+    double* J = Jall + threadIdx.x * np1;
+    for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
+        const int j = b0 + c0 + threadIdx.x;
+        const bool act = (c0 + threadIdx.x) < nb;
+        cd z = mk(1.0, 0.0);
+        if (act) {
+            double dx = px[j] - cx, dy = py[j] - cy;
+            double rho = hypot(dx, dy);
+            bessel_j_seq(k * rho, p, J);
+            if (rho > 0.0) z = mk(dx / rho, dy / rho);
+        }
+        for (int col = 0; col < nrhs; ++col) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < nco; i += blockDim.x) Ls[i] = L[(int64_t)col * ncoef + coef_off[B] + i];
+            __syncthreads();
+            if (act) {
+                cd acc = Ls[p] * J[0];
+                cd zz = mk(1.0, 0.0);
+                for (int t = 1; t <= p; ++t) {
+                    zz = zz * z;
+                    double jt = J[t];
+                    cfma(acc, jt * Ls[p + t], zz);
+                    cfma(acc, ((t & 1) ? -jt : jt) * Ls[p - t], conjc(zz));
+                }
+                y[(int64_t)col * n + j] += acc;
+            }
+        }
+    }
+}
+
+// Reaction M2L moment tables (eq. generalintegral): one CTA per (key, 32x32 tile).
+struct TableWork {
+    int key;
+    int m0, n0;   // first row / column of the tile (indices from -p)
+};
+
+__global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q, const ReactKey* __restrict__ keys,
+                                                      const TableWork* __restrict__ work,
+                                                      const int* __restrict__ comp, cd* __restrict__ out) {
+    extern __shared__ cd st[];
+    const TableWork wk = work[blockIdx.x];
+    const ReactKey K = keys[wk.key];
+    const int c = K.comp;
+    const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
+    const int pS = K.pS, pT = K.pT;
+    const int ncS = 2 * pS + 1, ncT = 2 * pT + 1;
+    const double ka = med.k[ls], kb = med.k[lt];
+    // smem layout for a chunk of CH nodes
+    const int CH = 16;
+    cd* Up = st;                       // [CH][32]  u^n  for the tile's n
+    cd* Um = Up + CH * 32;             // [CH][32]  u^-n
+    cd* Vp = Um + CH * 32;             // [CH][32]  v^-m for the tile's m
+    cd* Vm = Vp + CH * 32;             // [CH][32]  v^m
+    cd* Fp = Vm + CH * 32;             // [CH]
+    cd* Fm = Fp + CH;                  // [CH]
+    cd* uu = Fm + CH;                  // [CH] u
+    cd* vv = uu + CH;                  // [CH] v
+    double h;
+    const int P = detour_panels(q, K.X, K.D, &h);
+    const int ntot = P * 8 + 2 * q.nes;
+    const int tm = threadIdx.x >> 3;          // 0..31 row within tile
+    const int tn = (threadIdx.x & 7) * 4;     // 0..28 first column within tile
+    cd acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
+    for (int j0 = 0; j0 < ntot; j0 += CH) {
+        const int cnt = min(CH, ntot - j0);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            QuadNode nd = contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
+            cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
+            cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
+            cd E = eikh(kya, K.hS) * eikh(kyb, K.hT);
+            cd SE = S * E;
+            Fp[threadIdx.x] = SE * nd.fp;
+            Fm[threadIdx.x] = SE * nd.fm;
+            uu[threadIdx.x] = w_of(kya, nd.lam, ka);
+            vv[threadIdx.x] = w_of(kyb, nd.lam, kb);
+        }
+        __syncthreads();
+        // power tables: thread (node r, slot s) for 16 x 32 entries, 2 passes
+        for (int e = threadIdx.x; e < cnt * 32; e += blockDim.x) {
+            int r = e >> 5, s = e & 31;
+            int nn = wk.n0 + s, mm = wk.m0 + s;
+            cd u = uu[r], v = vv[r];
+            cd ui = cinv(u), vi = cinv(v);
+            // integer powers by binary exponentiation
+            auto ipow = [](cd base, int e2) {
+                cd r2 = mk(1.0, 0.0);
+                cd bb = base;
+                while (e2 > 0) { if (e2 & 1) r2 = r2 * bb; bb = bb * bb; e2 >>= 1; }
+                return r2;
+            };
+            Up[r * 32 + s] = (nn >= 0) ? ipow(u, nn) : ipow(ui, -nn);
+            Um[r * 32 + s] = (nn >= 0) ? ipow(ui, nn) : ipow(u, -nn);
+            Vp[r * 32 + s] = (mm >= 0) ? ipow(vi, mm) : ipow(v, -mm);
+            Vm[r * 32 + s] = (mm >= 0) ? ipow(v, mm) : ipow(vi, -mm);
+        }
+        __syncthreads();
+        for (int r = 0; r < cnt; ++r) {
+            cd a1 = Fp[r] * Vp[r * 32 + tm];
+            cd a2 = Fm[r] * Vm[r * 32 + tm];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                cfma(acc[t], a1, Up[r * 32 + tn + t]);
+                cfma(acc[t], a2, Um[r * 32 + tn + t]);
+            }
+        }
+    }
+    const int mm = wk.m0 + tm;
+    if (mm <= pT) {
+        for (int t = 0; t < 4; ++t) {
+            int nn = wk.n0 + tn + t;
+            if (nn <= pS) out[K.off + (int64_t)(mm + pT) * ncS + (nn + pS)] = acc[t];
+        }
+    }
+    (void)ncT;
+}
+
+}  // namespace lfmm

@@ -1,0 +1,148 @@
+// geometry.h -- the opaque handles behind the C ABI and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lfmm_internal.h"
+
+struct lfmm_medium_s {
+    MediumDev m;
+    int geometries = 0;   // live geometries referencing this medium
+};
+
+namespace lfmm {
+
+// device buffer owned by a geometry
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+// Sommerfeld quadrature parameters shared by host and device (passed by value)
+struct QuadRule {
+    double T;          // end of the real-axis detour
+    double es_v0;      // exp-sinh abscissae v0 + j hv, j = 0..nes-1
+    double es_hv;
+    int nes;           // nodes per ray
+    int min_panels;    // minimum number of detour panels
+    double gl_x[8];    // 8-point Gauss-Legendre rule on [-1, 1]
+    double gl_w[8];
+};
+
+// reaction M2L table key (built on the host, evaluated on the device)
+struct ReactKey {
+    int comp, level, pS, pT;   // component, level, orders of source/target expansions
+    double X, hS, hT, D;       // x_S - x_T, source-side and target-side heights, effective distance
+    int64_t off;               // offset of the (2pT+1) x (2pS+1) table (row m, column n)
+};
+
+}  // namespace lfmm
+
+struct lfmm_geometry_s {
+    lfmm_medium_s* med = nullptr;
+    MediumDev m;
+    int64_t n = 0;
+    int p = 20, leaf_size = 64;
+    lfmm::TreeHost tree;
+    lfmm::QuadRule quad;
+    std::vector<double> hx, hy, hw;   // sorted-order host copies
+    int nleaf = 0, leaf0 = 0;         // leaves are boxes [leaf0, leaf0 + nleaf)
+
+    // sorted-order point data
+    double *d_x = nullptr, *d_y = nullptr, *d_w = nullptr;
+    int *d_layer = nullptr, *d_perm = nullptr;
+    // boxes
+    int *d_box_begin = nullptr, *d_box_end = nullptr, *d_box_layer = nullptr, *d_box_level = nullptr;
+    double *d_box_cx = nullptr, *d_box_cy = nullptr;
+    int *d_box_ix = nullptr, *d_box_iy = nullptr, *d_box_parent = nullptr;
+    int *d_child_begin = nullptr, *d_child_end = nullptr;
+    int64_t *d_coef_off = nullptr;    // per box offset into M / L
+    int64_t ncoef = 0;
+    cd *d_M = nullptr, *d_L = nullptr;
+    // near field: block-sparse rows over target leaves
+    int *d_nb_ptr = nullptr;          // nleaf + 1
+    int *d_nb_src = nullptr;          // source leaf (box id) per block
+    int64_t *d_nb_off = nullptr;      // value offset per block
+    cd *d_nb_val = nullptr;           // blocks stored column-major (source index major)
+    int64_t nb_nnz = 0;
+    int n_blocks = 0;
+    // translation tables
+    int *d_p_level = nullptr;
+    cd *d_m2m = nullptr;              // per (layer, level, quadrant): Toeplitz vectors
+    int64_t *d_m2m_off = nullptr;
+    cd *d_l2l = nullptr;
+    int64_t *d_l2l_off = nullptr;
+    cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
+    int64_t *d_m2lf_off = nullptr;
+    int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids
+    cd *d_m2lr = nullptr;             // reaction M2L tables
+    int *d_vr_ptr = nullptr, *d_vr_src = nullptr, *d_vr_key = nullptr, *d_vr_comp = nullptr;
+    lfmm::ReactKey* d_rkeys = nullptr;
+    int n_rkeys = 0;
+    int* d_comp = nullptr;            // 4 ints per component
+    // level bookkeeping for launches
+    std::vector<int> level_start;
+    // scratch
+    cd *d_xs = nullptr, *d_ys = nullptr;   // sorted-order input/output (n * nrhs_cap)
+    int nrhs_cap = 0;
+    cd *d_hostbuf_x = nullptr, *d_hostbuf_y = nullptr;  // staging for host-pointer calls
+    size_t hostbuf_cap = 0;
+    // preconditioner (restricted overlapping DD, Sec. 4.2)
+    int *d_pc_ptr = nullptr;          // per leaf: offset of its gather list
+    int *d_pc_idx = nullptr;          // gather indices (sorted positions)
+    int64_t *d_pc_woff = nullptr;     // per leaf: offset of its (n_own x q) row block
+    cd *d_pc_W = nullptr;
+    int *pc_own_first = nullptr, *pc_own_cnt = nullptr;
+    bool pc_ready = false;
+    double setup_seconds = 0.0;
+    std::vector<void*> allocs;        // everything cudaMalloc'ed for this geometry
+};
+
+namespace lfmm {
+
+// error helpers (api.cu)
+void set_error(const std::string& msg);
+struct CudaError {
+    std::string msg;
+};
+void cuda_check(cudaError_t e, const char* what);
+template <class T>
+T* dalloc(lfmm_geometry_s* g, size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cuda_check(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+    g->allocs.push_back(p);
+    return (T*)p;
+}
+template <class T>
+T* dupload(lfmm_geometry_s* g, const std::vector<T>& v) {
+    T* p = dalloc<T>(g, v.size());
+    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    return p;
+}
+
+// near field (near.cu)
+void near_build(lfmm_geometry_s* g);
+void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+// FMM far field (fmm.cu)
+void fmm_build(lfmm_geometry_s* g);
+void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+// permutation helpers and the full operator (solver.cu)
+void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s);
+void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s);
+void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+void precond_build(lfmm_geometry_s* g);
+int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
+                 cudaStream_t s, lfmm_gmres_info* info);
+void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s);
+void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s);
+void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t m, const double* d_targets,
+                       cd* u, cudaStream_t s);
+
+QuadRule make_quad_rule(const MediumDev& m);
+
+}  // namespace lfmm

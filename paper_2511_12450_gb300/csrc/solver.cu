@@ -1,0 +1,384 @@
+// solver.cu -- the full operator, GMRES, the plane-wave right-hand side and the
+// scattered field (Secs. 2.2, 3.3, 4.1, 5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <stdexcept>
+#include <vector>
+
+#include "geometry.h"
+#include "sommerfeld.cuh"
+
+namespace lfmm {
+
+// ------------------------------------------------------------------ permutations
+__global__ void k_gather(const int* __restrict__ perm, const cd* __restrict__ in, cd* __restrict__ out, int64_t n,
+                         int nrhs) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nrhs) return;
+    int64_t col = t / n, s = t - col * n;
+    out[t] = in[col * n + perm[s]];
+}
+__global__ void k_scatter(const int* __restrict__ perm, const cd* __restrict__ in, cd* __restrict__ out,
+                          int64_t n, int nrhs) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nrhs) return;
+    int64_t col = t / n, s = t - col * n;
+    out[col * n + perm[s]] = in[t];
+}
+
+void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s) {
+    int64_t tot = g->n * nrhs;
+    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, x_in, x_sorted, g->n, nrhs);
+    cuda_check(cudaGetLastError(), "k_gather");
+}
+void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s) {
+    int64_t tot = g->n * nrhs;
+    k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, y_sorted, y_out, g->n, nrhs);
+    cuda_check(cudaGetLastError(), "k_scatter");
+}
+
+void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
+    cuda_check(cudaMemsetAsync(y_sorted, 0, sizeof(cd) * g->n * nrhs, s), "memset y");
+    fmm_apply(g, x_sorted, y_sorted, nrhs, s);
+    near_apply(g, x_sorted, y_sorted, nrhs, s);
+}
+
+// ------------------------------------------------------------------ BLAS-1/2 helpers for GMRES
+// partial[c * nb + blk] = sum_i conj(V[c][i]) w[i] over the block's slice
+__global__ void k_dots(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ w, int64_t n,
+                       cd* __restrict__ partial) {
+    __shared__ cd red[256];
+    const int c = blockIdx.y;
+    const cd* v = V + (int64_t)c * ld;
+    cd acc = mk(0, 0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cfma(acc, conjc(v[i]), w[i]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)c * gridDim.x + blockIdx.x] = red[0];
+}
+__global__ void k_reduce_partials(const cd* __restrict__ partial, int nb, int ncol, cd* __restrict__ out) {
+    int c = blockIdx.x;
+    __shared__ cd red[256];
+    cd acc = mk(0, 0);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[(int64_t)c * nb + i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+// w -= V h (ncol columns)
+__global__ void k_update(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ h,
+                         cd* __restrict__ w, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cd acc = w[i];
+    for (int c = 0; c < ncol; ++c) {
+        cd hc = h[c];
+        cfma(acc, -V[(int64_t)c * ld + i], hc);
+    }
+    w[i] = acc;
+}
+// out = V y  (ncol columns)
+__global__ void k_combine(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ y,
+                          cd* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cd acc = mk(0, 0);
+    for (int c = 0; c < ncol; ++c) cfma(acc, V[(int64_t)c * ld + i], y[c]);
+    out[i] = acc;
+}
+__global__ void k_scale(const cd* __restrict__ in, double s, cd* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = s * in[i];
+}
+__global__ void k_axpby(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // out = a - b
+    if (i < n) out[i] = a[i] - b[i];
+}
+
+struct Blas {
+    lfmm_geometry_s* g;
+    cudaStream_t s;
+    cd* partial;
+    cd* dres;
+    int nb;
+    std::vector<cd> host;
+    Blas(lfmm_geometry_s* g_, cudaStream_t s_, int maxcol) : g(g_), s(s_) {
+        nb = 120;
+        cuda_check(cudaMalloc(&partial, sizeof(cd) * nb * (maxcol + 1)), "malloc partial");
+        cuda_check(cudaMalloc(&dres, sizeof(cd) * (maxcol + 1)), "malloc dres");
+        host.resize(maxcol + 1);
+    }
+    ~Blas() { cudaFree(partial); cudaFree(dres); }
+    // h[0..ncol) = V^H w, left in dres and copied to host
+    void dots(const cd* V, int ncol, int64_t ld, const cd* w, int64_t n) {
+        dim3 grid(nb, ncol);
+        k_dots<<<grid, 256, 0, s>>>(V, ncol, ld, w, n, partial);
+        k_reduce_partials<<<ncol, 256, 0, s>>>(partial, nb, ncol, dres);
+        cuda_check(cudaMemcpyAsync(host.data(), dres, sizeof(cd) * ncol, cudaMemcpyDeviceToHost, s), "dots d2h");
+        cuda_check(cudaStreamSynchronize(s), "dots sync");
+    }
+    double norm(const cd* w, int64_t n) {
+        dots(w, 1, n, w, n);
+        return std::sqrt(std::max(host[0].x, 0.0));
+    }
+};
+
+static inline int nblk(int64_t n) { return (int)((n + 255) / 256); }
+
+// One right-hand side; vectors in sorted order on the device.
+static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int maxit, bool pre, cudaStream_t s,
+                     int* iters, double* res_out) {
+    const int64_t n = g->n;
+    Blas bl(g, s, maxit + 1);
+    cd *V = nullptr, *w = nullptr, *z = nullptr, *hd = nullptr;
+    cuda_check(cudaMalloc(&V, sizeof(cd) * n * (size_t)(maxit + 1)), "malloc V");
+    cuda_check(cudaMalloc(&w, sizeof(cd) * n), "malloc w");
+    cuda_check(cudaMalloc(&z, sizeof(cd) * n), "malloc z");
+    cuda_check(cudaMalloc(&hd, sizeof(cd) * (maxit + 2)), "malloc h");
+    struct Free { cd *a, *b, *c, *d; ~Free() { cudaFree(a); cudaFree(b); cudaFree(c); cudaFree(d); } } fr{V, w, z, hd};
+    double beta = bl.norm(b, n);
+    cuda_check(cudaMemsetAsync(x, 0, sizeof(cd) * n, s), "memset x");
+    if (beta == 0.0) { *iters = 0; *res_out = 0.0; return 1; }
+    k_scale<<<nblk(n), 256, 0, s>>>(b, 1.0 / beta, V, n);
+    typedef std::complex<double> C;
+    std::vector<std::vector<C>> H;
+    std::vector<C> cs, sn, gg(1, C(beta, 0.0));
+    int j = 0;
+    double res = 1.0;
+    for (j = 0; j < maxit; ++j) {
+        const cd* vj = V + (int64_t)j * n;
+        if (pre) { precond_apply_sorted(g, vj, z, s); apply_operator_sorted(g, z, w, 1, s); }
+        else apply_operator_sorted(g, vj, w, 1, s);
+        // classical Gram-Schmidt, twice
+        std::vector<C> h(j + 2, C(0, 0));
+        for (int pass = 0; pass < 2; ++pass) {
+            bl.dots(V, j + 1, n, w, n);
+            for (int c = 0; c <= j; ++c) h[c] += C(bl.host[c].x, bl.host[c].y);
+            k_update<<<nblk(n), 256, 0, s>>>(V, j + 1, n, bl.dres, w, n);
+        }
+        double hn = bl.norm(w, n);
+        h[j + 1] = C(hn, 0.0);
+        if (hn > 0) k_scale<<<nblk(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * n, n);
+        // Givens rotations
+        for (int i = 0; i < j; ++i) {
+            C t = cs[i] * h[i] + sn[i] * h[i + 1];
+            h[i + 1] = -std::conj(sn[i]) * h[i] + std::conj(cs[i]) * h[i + 1];
+            h[i] = t;
+        }
+        C a = h[j], c = h[j + 1];
+        double r = std::hypot(std::abs(a), std::abs(c));
+        C cj, sj;
+        if (r == 0) { cj = 1; sj = 0; }
+        else if (std::abs(a) == 0) { cj = 0; sj = std::conj(c) / std::abs(c); }
+        else { cj = std::abs(a) / r; sj = (a / std::abs(a)) * std::conj(c) / r; }
+        h[j] = cj * a + sj * c;
+        h[j + 1] = 0;
+        cs.push_back(cj); sn.push_back(sj);
+        gg.push_back(-std::conj(sj) * gg[j]);
+        gg[j] = cj * gg[j];
+        H.push_back(h);
+        res = std::abs(gg[j + 1]) / beta;
+        if (res <= tol || hn == 0.0) { ++j; break; }
+    }
+    int m = (int)H.size();
+    std::vector<C> y(m);
+    for (int i = m - 1; i >= 0; --i) {
+        C sacc = gg[i];
+        for (int k2 = i + 1; k2 < m; ++k2) sacc -= H[k2][i] * y[k2];
+        y[i] = sacc / H[i][i];
+    }
+    std::vector<cd> yh(m);
+    for (int i = 0; i < m; ++i) yh[i] = mk(y[i].real(), y[i].imag());
+    cuda_check(cudaMemcpyAsync(hd, yh.data(), sizeof(cd) * m, cudaMemcpyHostToDevice, s), "y h2d");
+    if (pre) {
+        k_combine<<<nblk(n), 256, 0, s>>>(V, m, n, hd, z, n);
+        precond_apply_sorted(g, z, x, s);
+    } else {
+        k_combine<<<nblk(n), 256, 0, s>>>(V, m, n, hd, x, n);
+    }
+    cuda_check(cudaStreamSynchronize(s), "gmres end");
+    *iters = m;
+    *res_out = res;
+    return res <= tol ? 1 : 0;
+}
+
+int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
+                 cudaStream_t s, lfmm_gmres_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    int all = 1, it = 0;
+    double worst = 0.0, worst_true = 0.0;
+    cd* r = nullptr;
+    cuda_check(cudaMalloc(&r, sizeof(cd) * g->n), "malloc r");
+    Blas bl(g, s, 2);
+    for (int c = 0; c < nrhs; ++c) {
+        const cd* bc = b + (int64_t)c * g->n;
+        cd* xc = x + (int64_t)c * g->n;
+        double res;
+        int ok = gmres_one(g, bc, xc, tol, maxit, pre, s, &it, &res);
+        all &= ok;
+        worst = std::max(worst, res);
+        apply_operator_sorted(g, xc, r, 1, s);
+        k_axpby<<<nblk(g->n), 256, 0, s>>>(bc, r, r, g->n);
+        double rn = bl.norm(r, g->n), bn = bl.norm(bc, g->n);
+        worst_true = std::max(worst_true, bn > 0 ? rn / bn : 0.0);
+    }
+    cudaFree(r);
+    if (info) {
+        info->iterations = it;
+        info->converged = all;
+        info->rel_residual = worst;
+        info->true_rel_residual = worst_true;
+        info->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return all;
+}
+
+// ------------------------------------------------------------------ right-hand side (Sec. 2.2)
+// Background field of a plane wave, by the generalized reflection/transmission
+// recursions of the paper (A_l, B_l after eq. TLhelmholtztotallayer2) written
+// with each layer's waves referenced at its own interfaces.
+__global__ void k_rhs(MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
+                      const int* __restrict__ layer, const double* __restrict__ angles, int nrhs, int64_t n,
+                      cd* __restrict__ b) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const int col = (int)(t / n);
+    const int64_t i = t - (int64_t)col * n;
+    const int L = m.nl - 1;
+    const double th = angles[col];
+    const double kx = m.k[0] * cos(th);
+    const int l = layer[i];
+    const double x = px[i], y = py[i];
+    cd lam = mk(kx, 0.0);
+    cd kyv[LFMM_MAXLAY], e[LFMM_MAXLAY], Rl[LFMM_MAXLAY], Rd[LFMM_MAXLAY];
+    for (int q = 0; q <= L; ++q) {
+        kyv[q] = ky_of(m.k[q], lam);
+        e[q] = (q >= 1 && q <= L - 1) ? eikh(kyv[q], m.yint[q - 1] - m.yint[q]) : mk(0.0, 0.0);
+    }
+    for (int q = 0; q < L; ++q) {
+        cd A = m.eta[q] * kyv[q], B = m.eta[q + 1] * kyv[q + 1];
+        Rl[q] = cdiv(A - B, A + B);
+    }
+    for (int q = 0; q <= L; ++q) Rd[q] = mk(0.0, 0.0);
+    for (int q = L - 1; q >= 0; --q) {
+        if (q == L - 1) Rd[q] = Rl[q];
+        else {
+            cd tt = Rd[q + 1] * (e[q + 1] * e[q + 1]);
+            Rd[q] = cdiv(Rl[q] + tt, mk(1.0, 0.0) + Rl[q] * tt);
+        }
+    }
+    cd phx = cexpd(mk(0.0, kx * x));
+    cd u = mk(0.0, 0.0);
+    if (L == 0) {
+        u = phx * cexpd(mk(0.0, -kyv[0].x * y));
+    } else {
+        // incident wave: down-going in layer 0 with amplitude c at interface 0
+        cd c = cexpd(mk(0.0, -kyv[0].x * m.yint[0]));
+        if (l == 0) {
+            cd inc = c * eikh(kyv[0], -(y - m.yint[0]));          // e^{-i k0y (y - y_0)}
+            cd refl = Rd[0] * c * eikh(kyv[0], y - m.yint[0]);    // R~_{01} c e^{i k0y (y - y_0)}
+            u = phx * (inc + refl);
+        } else {
+            // down-going amplitude in layer q, referenced at its top interface
+            cd Bq = mk(0.0, 0.0);
+            cd prev = c;   // down-going amplitude arriving at the top of the next layer
+            for (int q = 1; q <= l; ++q) {
+                cd A = m.eta[q - 1] * kyv[q - 1], Bk = m.eta[q] * kyv[q];
+                cd Tdn = cdiv(2.0 * A, A + Bk);                              // T_{q-1,q}
+                cd den = mk(1.0, 0.0) + Rl[q - 1] * Rd[q] * (e[q] * e[q]);  // 1 - R_{q,q-1} R~_{q,q+1} e^2
+                Bq = cdiv(Tdn * prev, den);
+                prev = Bq * e[q];
+            }
+            cd down = Bq * eikh(kyv[l], m.yint[l - 1] - y);
+            cd up = mk(0.0, 0.0);
+            if (l <= L - 1) up = Rd[l] * Bq * e[l] * eikh(kyv[l], y - m.yint[l]);
+            u = phx * (down + up);
+        }
+    }
+    // b = eta_l g, g = -(u_inc + u^b)
+    b[t] = -m.eta[l] * u;
+}
+
+void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s) {
+    double* d_ang = nullptr;
+    cuda_check(cudaMalloc(&d_ang, sizeof(double) * nrhs), "malloc angles");
+    cuda_check(cudaMemcpyAsync(d_ang, angles_host, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "angles h2d");
+    int64_t tot = g->n * nrhs;
+    k_rhs<<<nblk(tot), 256, 0, s>>>(g->m, g->d_x, g->d_y, g->d_layer, d_ang, nrhs, g->n, b_sorted);
+    cuda_check(cudaGetLastError(), "k_rhs");
+    cuda_check(cudaStreamSynchronize(s), "rhs");
+    cudaFree(d_ang);
+}
+
+// ------------------------------------------------------------------ scattered field (eq. integralrep)
+// one warp per (target, source) pair; u[target] += |Gamma_e| Phi_e G(c_e, r) / eta
+__global__ void k_field(MediumDev m, QuadRule q, const double* __restrict__ px, const double* __restrict__ py,
+                        const double* __restrict__ pw, const int* __restrict__ layer, const int* __restrict__ comp,
+                        const double* __restrict__ compH, int ncomp, const cd* __restrict__ phi, int64_t n,
+                        int nrhs, const double* __restrict__ tgt, int64_t mt, cd* __restrict__ u) {
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t wk = warp; wk < mt * n; wk += nw) {
+        const int64_t it = wk / n, e = wk - it * n;
+        const double xt = tgt[2 * it], yt = tgt[2 * it + 1];
+        int lt = 0;
+        while (lt < m.nl - 1 && yt < m.yint[lt]) ++lt;
+        const int ls = layer[e];
+        cd G = mk(0.0, 0.0);
+        for (int c = 0; c < ncomp; ++c) {
+            const int cls = comp[4 * c], a = comp[4 * c + 1], clt = comp[4 * c + 2], b = comp[4 * c + 3];
+            if (cls != ls || clt != lt) continue;
+            const double hs = (a == 0) ? (py[e] - m.yint[ls]) : (m.yint[ls - 1] - py[e]);
+            const double ht = (b == 0) ? (m.yint[lt - 1] - yt) : (yt - m.yint[lt]);
+            G += react_kernel_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht);
+        }
+        if (lane == 0) {
+            if (ls == lt) {
+                double z = m.k[ls] * hypot(px[e] - xt, py[e] - yt);
+                G += mk(-0.25 * y0(z), 0.25 * j0(z));
+            }
+            double sc = pw[e] / m.eta[lt];
+            for (int col = 0; col < nrhs; ++col) {
+                cd v = (sc * G) * phi[(int64_t)col * n + e];
+                atomicAdd(&u[(int64_t)col * mt + it].x, v.x);
+                atomicAdd(&u[(int64_t)col * mt + it].y, v.y);
+            }
+        }
+    }
+}
+
+void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t mt, const double* d_targets,
+                       cd* u, cudaStream_t s) {
+    std::vector<double> compH(g->tree.comps.size());
+    for (size_t c = 0; c < compH.size(); ++c) compH[c] = g->tree.comps[c].Hc;
+    double* d_compH = nullptr;
+    cuda_check(cudaMalloc(&d_compH, sizeof(double) * std::max<size_t>(1, compH.size())), "malloc compH");
+    if (!compH.empty())
+        cuda_check(cudaMemcpyAsync(d_compH, compH.data(), sizeof(double) * compH.size(), cudaMemcpyHostToDevice, s),
+                   "compH");
+    cuda_check(cudaMemsetAsync(u, 0, sizeof(cd) * mt * nrhs, s), "memset u");
+    int64_t work = mt * g->n;
+    int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
+    k_field<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g->m, g->quad, g->d_x, g->d_y, g->d_w, g->d_layer,
+                                                             g->d_comp, d_compH, (int)compH.size(), phi_sorted, g->n,
+                                                             nrhs, d_targets, mt, u);
+    cuda_check(cudaGetLastError(), "k_field");
+    cuda_check(cudaStreamSynchronize(s), "field");
+    cudaFree(d_compH);
+}
+
+}  // namespace lfmm

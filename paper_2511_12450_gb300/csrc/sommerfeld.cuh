@@ -1,0 +1,118 @@
+// sommerfeld.cuh -- Sommerfeld-integral quadrature of the reaction kernels.
+//
+// A reaction component (Sec. 3.1, eq. fourreactions in the interface-referenced
+// form of devmath.cuh) is
+//   K_c(X, h_s, h_t) = (1/2pi) int_R Sigma_c(lambda) e^{i lambda X}
+//                      e^{i k_{ls,y} h_s} e^{i k_{lt,y} h_t} d lambda,
+// X = x_s - x_t (matvec source minus matvec target).  Sigma_c and the two
+// exponentials are even in lambda, so
+//   K_c = (1/pi) int_0^T (...) cos(lambda X) d lambda                (detour)
+//       + (1/2pi) int_T^inf (...) e^{+i lambda X} + (...) e^{-i lambda X}   (rays)
+// The detour lambda(t) = t - i h sin(pi t / T), t in [0, T], passes below the
+// real-axis poles and branch points (T = 1.2 k_max + 1, h = min(1/2, 1/|X|));
+// it is integrated with 8-point Gauss-Legendre panels whose number grows with
+// the oscillation (|X| + D).  Past T each half is rotated onto the ray
+// lambda = T + t u, u = (D_+ +- i X)/rho (D_+ = max(D, 0), rho = |D_+ + iX|),
+// along which e^{+-i lambda X - lambda D} decays like e^{-rho t} without
+// oscillating; the ray is integrated with the exp-sinh (double-exponential)
+// rule, which resolves both the fast decay and the near-singular behaviour of
+// points close to an interface.  D = h_s + h_t + H_c is the effective
+// transmission distance of the pair (Sec. 3.2).
+//
+// The M2L moments of Sec. 4.1 (eq. generalintegral) use the same contour:
+//   I_{nm} = (1/2pi) int Sigma e^{i lambda X} e^{i k_a h_S} e^{i k_b h_T}
+//            w(lambda,k_a)^n w(lambda,k_b)^{-m} d lambda,
+// split into the two halves e^{+i lambda X} w_a^n w_b^{-m} and
+// e^{-i lambda X} w_a^{-n} w_b^{m} (w(-lambda) = 1/w(lambda)).
+#pragma once
+#include "devmath.cuh"
+#include "geometry.h"
+
+namespace lfmm {
+
+struct QuadNode {
+    cd lam;     // node
+    cd fp;      // weight multiplying the e^{+i lambda X} half (already includes e^{+i lambda X})
+    cd fm;      // weight multiplying the e^{-i lambda X} half (already includes e^{-i lambda X})
+};
+
+__device__ __forceinline__ int detour_panels(const QuadRule& q, double X, double D, double* h_out) {
+    double ax = fabs(X);
+    double h = fmin(0.5, 1.0 / fmax(ax, 1e-3));
+    *h_out = h;
+    double need = q.T * (1.0 / h + 0.6 * (fmax(D, 0.0) + ax));
+    int P = (int)ceil(need);
+    return P > q.min_panels ? P : q.min_panels;
+}
+
+// Node j of the contour for a pair with horizontal offset X and effective
+// distance D: j < 8P on the detour, then nes nodes on the + ray, then nes on
+// the - ray.  Returns lambda and the weights (with dlambda, 1/(2pi) and the
+// oscillatory factor) of the two halves.
+__device__ __forceinline__ QuadNode contour_node(const QuadRule& q, int j, int P, double h, double X, double D) {
+    QuadNode out;
+    const int ndet = P * 8;
+    const double inv2pi = 0.15915494309189533577;
+    if (j < ndet) {
+        int pan = j >> 3, r = j & 7;
+        double a0 = q.T * (double)pan / P, a1 = q.T * (double)(pan + 1) / P;
+        double hl = 0.5 * (a1 - a0);
+        double t = 0.5 * (a0 + a1) + hl * q.gl_x[r];
+        double wt = hl * q.gl_w[r];
+        double s, c;
+        sincospi(t / q.T, &s, &c);
+        out.lam = mk(t, -h * s);
+        cd dl = mk(1.0, -h * (M_PI / q.T) * c);
+        // e^{+i lambda X} and e^{-i lambda X}
+        cd ep = cexpd(mk(-out.lam.y * X, out.lam.x * X));
+        cd em = cexpd(mk(out.lam.y * X, -out.lam.x * X));
+        cd base = (wt * inv2pi) * dl;
+        out.fp = base * ep;
+        out.fm = base * em;
+        return out;
+    }
+    int jj = j - ndet;
+    int sg = (jj < q.nes) ? 1 : -1;
+    int k = (jj < q.nes) ? jj : jj - q.nes;
+    double v = q.es_v0 + k * q.es_hv;
+    double tt = exp(M_PI_2 * sinh(v));
+    double dtt = tt * M_PI_2 * cosh(v) * q.es_hv;
+    double Dp = fmax(D, 0.0);
+    double rr = fmax(hypot(Dp, X), 1e-300);
+    cd u = mk(Dp / rr, sg * X / rr);
+    out.lam = mk(q.T, 0.0) + (tt / rr) * u;
+    cd e = cexpd(mk(-sg * X * out.lam.y, sg * X * out.lam.x));
+    cd f = ((dtt / rr) * inv2pi) * (e * u);
+    if (sg > 0) { out.fp = f; out.fm = mk(0.0, 0.0); }
+    else { out.fm = f; out.fp = mk(0.0, 0.0); }
+    return out;
+}
+
+__device__ __forceinline__ cd warp_sum(cd v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Reaction kernel value K_c(X, h_s, h_t); all 32 lanes of the warp must call
+// it with the same arguments; every lane receives the result.
+__device__ inline cd react_kernel_warp(const MediumDev& m, const QuadRule& q, int ls, int a, int lt, int b,
+                                       double Hc, double X, double hs, double ht) {
+    const int lane = threadIdx.x & 31;
+    double D = hs + ht + Hc;
+    double h;
+    int P = detour_panels(q, X, D, &h);
+    int ntot = P * 8 + 2 * q.nes;
+    cd acc = mk(0.0, 0.0);
+    for (int j = lane; j < ntot; j += 32) {
+        QuadNode nd = contour_node(q, j, P, h, X, D);
+        cd S = sigma_comp(m, nd.lam, ls, a, lt, b);
+        cd E = eikh(ky_of(m.k[ls], nd.lam), hs) * eikh(ky_of(m.k[lt], nd.lam), ht);
+        acc += (S * E) * (nd.fp + nd.fm);
+    }
+    return warp_sum(acc);
+}
+
+}  // namespace lfmm

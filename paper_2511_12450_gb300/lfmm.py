@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in include/lfmm.h (argument marshalling only).
+
+Every function here has the name of the C entry point without the ``lfmm_``
+prefix and does nothing but check/convert arguments and call the library:
+all computation happens in the CUDA library.  Vectors may be numpy arrays
+(host memory) or CUDA torch tensors (device memory, passed with
+LFMM_DEVICE_PTRS on the current torch stream).  Complex vectors are
+complex128, column-major [n x nrhs] (a 1-D array is one column).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblfmm.so")
+
+LFMM_OK = 0
+LFMM_NOT_CONVERGED = 1
+LFMM_ERR_INVALID_ARG = -1
+LFMM_ERR_OUT_OF_MEMORY = -2
+LFMM_ERR_CUDA = -3
+LFMM_ERR_NODE_ON_INTERFACE = -4
+LFMM_ERR_QUADRATURE = -5
+LFMM_ERR_TIMEOUT = -6
+LFMM_ERR_HBM_BUDGET = -7
+LFMM_DEVICE_PTRS = 1
+
+EXPORTED = [
+    "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
+    "lfmm_rhs_plane_wave", "lfmm_matvec", "lfmm_gmres_solve", "lfmm_eval_field",
+    "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error",
+]
+
+
+class LfmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lfmm status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class GmresParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GmresInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("solve_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB = None
+
+
+def library():
+    """Load the compiled library; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, dp, i32, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int64
+        lib.lfmm_medium_create.argtypes = [i32, dp, dp, dp, ctypes.POINTER(vp)]
+        lib.lfmm_medium_destroy.argtypes = [vp]
+        lib.lfmm_geometry_build.argtypes = [vp, i64, dp, dp, dp, ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        lib.lfmm_geometry_destroy.argtypes = [vp]
+        lib.lfmm_rhs_plane_wave.argtypes = [vp, i32, dp, vp, i32, vp]
+        lib.lfmm_matvec.argtypes = [vp, i32, vp, vp, i32, vp]
+        lib.lfmm_gmres_solve.argtypes = [vp, i32, vp, vp, ctypes.POINTER(GmresParams), ctypes.POINTER(GmresInfo), vp]
+        lib.lfmm_eval_field.argtypes = [vp, i32, vp, i64, dp, vp, i32, vp]
+        lib.lfmm_polygon_elements.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]
+        lib.lfmm_geometry_query.argtypes = [vp, ctypes.c_char_p, vp, i64, ctypes.POINTER(i64)]
+        lib.lfmm_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name != "lfmm_last_error":
+                getattr(lib, name).restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int):
+    if status < 0:
+        raise LfmmError(status, library().lfmm_last_error().decode())
+    return status
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _stream_of(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Medium:
+    def __init__(self, handle, interfaces, k, eta):
+        self.handle = handle
+        self.interfaces, self.k, self.eta = interfaces, k, eta
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.lfmm_medium_destroy(self.handle)
+            self.handle = None
+
+
+class Geometry:
+    def __init__(self, handle, medium: Medium, n: int):
+        self.handle = handle
+        self.medium = medium   # keeps the medium alive
+        self.n = n
+
+    def destroy(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.lfmm_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.destroy()
+
+
+def medium_create(interfaces, k, eta) -> Medium:
+    yint = _f64(interfaces).reshape(-1)
+    kk = np.asarray(k)
+    kc = np.ascontiguousarray(kk.astype(np.complex128).reshape(-1))
+    et = _f64(eta).reshape(-1)
+    h = ctypes.c_void_p()
+    _check(library().lfmm_medium_create(int(kc.size), _dp(yint) if yint.size else None,
+                                        _dp(kc.view(np.float64)), _dp(et), ctypes.byref(h)))
+    return Medium(h, yint, kc, et)
+
+
+def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, leaf_size: int = 64) -> Geometry:
+    pts = _f64(points).reshape(-1, 2)
+    w = _f64(weights).reshape(-1)
+    nrm = _f64(normals).reshape(-1, 2) if normals is not None else None
+    prm = Params(int(p), int(leaf_size), 0, 0)
+    h = ctypes.c_void_p()
+    _check(library().lfmm_geometry_build(medium.handle, pts.shape[0], _dp(pts), _dp(w),
+                                         _dp(nrm) if nrm is not None else None, ctypes.byref(prm),
+                                         ctypes.byref(h)))
+    return Geometry(h, medium, pts.shape[0])
+
+
+def _vec_args(v, n):
+    """(pointer, nrhs, flags, keepalive) for a complex vector argument."""
+    if _is_torch_cuda(v):
+        import torch
+
+        assert v.dtype == torch.complex128 and v.is_contiguous()
+        nrhs = 1 if v.dim() == 1 else v.shape[1 if v.shape[0] == n else 0]
+        return ctypes.c_void_p(v.data_ptr()), v.numel() // n, LFMM_DEVICE_PTRS, v
+    a = np.asarray(v)
+    if a.dtype != np.complex128:
+        raise TypeError("complex128 expected")
+    if not a.flags["F_CONTIGUOUS" if a.ndim == 2 else "C_CONTIGUOUS"]:
+        raise ValueError("vector must be column-major contiguous")
+    return ctypes.c_void_p(a.ctypes.data), a.size // n, 0, a
+
+
+def _empty_like(v, n, nrhs):
+    if _is_torch_cuda(v):
+        import torch
+
+        return torch.empty((n,) if nrhs == 1 else (nrhs, n), dtype=torch.complex128, device=v.device)
+    return np.zeros(n, dtype=np.complex128) if nrhs == 1 else np.zeros((n, nrhs), dtype=np.complex128, order="F")
+
+
+def rhs_plane_wave(g: Geometry, angles_rad, out=None, stream=None, device=False):
+    ang = _f64(angles_rad).reshape(-1)
+    nrhs = ang.size
+    if out is None:
+        if device:
+            import torch
+
+            out = torch.empty((nrhs, g.n) if nrhs > 1 else (g.n,), dtype=torch.complex128, device="cuda")
+        else:
+            out = _empty_like(np.zeros(1, np.complex128), g.n, nrhs)
+    ptr, _, flags, keep = _vec_args(out, g.n)
+    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    _check(library().lfmm_rhs_plane_wave(g.handle, nrhs, _dp(ang), ptr, flags, st))
+    return out
+
+
+def matvec(g: Geometry, x, y=None, stream=None):
+    xp, nrhs, flags, keep = _vec_args(x, g.n)
+    if y is None:
+        y = _empty_like(x, g.n, nrhs)
+    yp, _, flags_y, keep_y = _vec_args(y, g.n)
+    if flags != flags_y:
+        raise ValueError("x and y must both be host arrays or both device tensors")
+    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
+    return y
+
+
+def gmres_solve(g: Geometry, b, x=None, tol: float = 1e-8, max_iter: int = 1000, precond: bool = True,
+                stream=None):
+    bp, nrhs, flags, keep = _vec_args(b, g.n)
+    if x is None:
+        x = _empty_like(b, g.n, nrhs)
+    xp, _, _, keep_x = _vec_args(x, g.n)
+    prm = GmresParams(float(tol), int(max_iter), 0, 1 if precond else 0, 0)
+    info = GmresInfo()
+    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    status = _check(library().lfmm_gmres_solve(g.handle, nrhs, bp, xp, ctypes.byref(prm), ctypes.byref(info), st))
+    d = info.as_dict()
+    d["status"] = status
+    return x, d
+
+
+def eval_field(g: Geometry, density, targets, stream=None):
+    dpp, nrhs, flags, keep = _vec_args(density, g.n)
+    tg = _f64(targets).reshape(-1, 2)
+    m = tg.shape[0]
+    u = np.zeros(m, dtype=np.complex128) if nrhs == 1 else np.zeros((m, nrhs), dtype=np.complex128, order="F")
+    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    _check(library().lfmm_eval_field(g.handle, nrhs, dpp, m, _dp(tg), ctypes.c_void_p(u.ctypes.data), flags, st))
+    return u
+
+
+def polygon_elements(polygons):
+    polys = [_f64(p).reshape(-1, 2) for p in polygons]
+    counts = np.array([p.shape[0] for p in polys], dtype=np.int32)
+    verts = np.ascontiguousarray(np.concatenate(polys, axis=0))
+    n = int(counts.sum())
+    pts = np.zeros((n, 2))
+    w = np.zeros(n)
+    nrm = np.zeros((n, 2))
+    _check(library().lfmm_polygon_elements(len(polys), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           _dp(verts), _dp(pts), _dp(w), _dp(nrm)))
+    return pts, w, nrm
+
+
+def geometry_query(g: Geometry, name: str, dtype=np.int32) -> np.ndarray:
+    need = ctypes.c_int64(0)
+    _check(library().lfmm_geometry_query(g.handle, name.encode(), None, 0, ctypes.byref(need)))
+    out = np.zeros(need.value // np.dtype(dtype).itemsize, dtype=dtype)
+    _check(library().lfmm_geometry_query(g.handle, name.encode(), ctypes.c_void_p(out.ctypes.data), need.value,
+                                         ctypes.byref(need)))
+    return out

@@ -1,0 +1,57 @@
+"""C-ABI checks that need no GPU: the library loads and exports every declared symbol;
+host-only helpers and argument validation."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "lfmm.h")) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"\b(lfmm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_12450_gb300 import _build, lfmm
+
+    _build.build()
+    return lfmm
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "lfmm_matvec" in names and "lfmm_gmres_solve" in names
+    so = lib.library()
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(names) == set(lib.EXPORTED)
+
+
+def test_polygon_elements_host_helper(lib):
+    sq = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=float)
+    pts, w, nrm = lib.polygon_elements([sq])
+    np.testing.assert_allclose(pts, [[0.5, 0], [1, 0.5], [0.5, 1], [0, 0.5]])
+    np.testing.assert_allclose(w, [1, 1, 1, 1])
+    np.testing.assert_allclose(nrm, [[0, -1], [1, 0], [0, 1], [-1, 0]])
+    with pytest.raises(lib.LfmmError):
+        lib.polygon_elements([np.array([[0, 0], [0, 0], [1, 1]], dtype=float)])
+
+
+def test_medium_validation(lib):
+    m = lib.medium_create([0.0, -2.0], [4.0, 6.0, 8.0], [1.0, 2.0, 3.0])
+    assert m.handle
+    for bad in [
+        dict(interfaces=[0.0, 1.0], k=[1, 2, 3], eta=[1, 1, 1]),       # not decreasing
+        dict(interfaces=[0.0], k=[1.0, -2.0], eta=[1, 1]),             # k <= 0
+        dict(interfaces=[0.0], k=[1.0, 2.0 + 0.1j], eta=[1, 1]),       # complex k unsupported
+        dict(interfaces=[0.0], k=[1.0, 2.0], eta=[1, 0.0]),            # eta <= 0
+    ]:
+        with pytest.raises(lib.LfmmError) as ei:
+            lib.medium_create(**bad)
+        assert ei.value.status == lib.LFMM_ERR_INVALID_ARG

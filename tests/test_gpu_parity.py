@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import background as obg
+from oracle import nystrom as onys
+from oracle import tree as otree
+from workloads import config_c1, layered_small
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module")
+def c1(gpu_lib):
+    lf = gpu_lib
+    wl = config_c1()
+    med = wl.medium
+    pts, w, _, _ = onys.elements(wl.bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    p2, w2, n2 = lf.polygon_elements(wl.bodies)
+    G = lf.geometry_build(M, p2, w2, n2, p=20, leaf_size=64)
+    return dict(lf=lf, wl=wl, med=med, pts=pts, w=w, K=K, G=G, M=M)
+
+
+def test_c1_matvec_matches_dense_oracle(c1):
+    lf, G, K = c1["lf"], c1["G"], c1["K"]
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((G.n, 2)) + 1j * rng.standard_normal((G.n, 2))
+    x = np.asfortranarray(x)
+    y = lf.matvec(G, x)
+    for c in range(2):
+        assert relerr(y[:, c], K @ x[:, c]) <= 1e-10
+
+
+def test_c1_rhs_matches_oracle(c1):
+    lf, G, med, pts = c1["lf"], c1["G"], c1["med"], c1["pts"]
+    angs = np.deg2rad([45.0, 100.0])
+    b = lf.rhs_plane_wave(G, angs)
+    for c, a in enumerate(angs):
+        assert relerr(b[:, c], obg.rhs(med, a, pts[:, 0], pts[:, 1])) <= 1e-12
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_c1_gmres_matches_lu(c1, precond):
+    lf, G, K, med, pts = c1["lf"], c1["G"], c1["K"], c1["med"], c1["pts"]
+    th = np.deg2rad(45.0)
+    b = obg.rhs(med, th, pts[:, 0], pts[:, 1])
+    x, info = lf.gmres_solve(G, b, tol=1e-10, precond=precond)
+    assert info["converged"] == 1
+    assert info["true_rel_residual"] <= 1.5e-10
+    assert relerr(x, np.linalg.solve(K, b)) <= 1e-8
+
+
+def test_c1_field_matches_oracle(c1):
+    lf, G, med, pts, w = c1["lf"], c1["G"], c1["med"], c1["pts"], c1["w"]
+    rng = np.random.default_rng(2)
+    phi = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    tg = np.array([[0.0, 2.1], [1.3, 0.4], [-0.8, -0.7], [2.0, -1.5], [0.2, 0.05]])
+    u = lf.eval_field(G, phi, tg)
+    ref = onys.field(med, pts, w, phi, tg)
+    assert relerr(u, ref) <= 1e-10
+
+
+def test_device_pointer_path(c1):
+    import torch
+
+    lf, G, K = c1["lf"], c1["G"], c1["K"]
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    xt = torch.from_numpy(x).cuda()
+    yt = lf.matvec(G, xt)
+    torch.cuda.synchronize()
+    assert relerr(yt.cpu().numpy(), K @ x) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def small3(gpu_lib):
+    lf = gpu_lib
+    wl = layered_small(n_bodies=3, nodes=150, seed=7)
+    med = wl.medium
+    pts, w, _, _ = onys.elements(wl.bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    return dict(lf=lf, wl=wl, med=med, pts=pts, w=w, K=K, M=M)
+
+
+def test_multilayer_all_near_matches_dense_oracle(small3):
+    # a leaf size larger than N puts every pair in the near field: every reaction
+    # component of the three-layer medium goes through the GPU Sommerfeld quadrature
+    lf, pts, w, K = small3["lf"], small3["pts"], small3["w"], small3["K"]
+    G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=1024)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    assert relerr(lf.matvec(G, x), K @ x) <= 1e-10
+
+
+def test_tree_and_lists_bit_exact(small3):
+    lf, pts, med = small3["lf"], small3["pts"], small3["med"]
+    G = lf.geometry_build(small3["M"], pts, small3["w"], p=6, leaf_size=12)
+    T = otree.Tree(pts, med.interfaces, med.k, p=6, leaf_size=12)
+    q = lambda name: lf.geometry_query(G, name)
+    assert np.array_equal(q("perm"), T.perm)
+    for nm in ["box_level", "box_layer", "box_ix", "box_iy", "box_begin", "box_end", "box_parent"]:
+        assert np.array_equal(q(nm), np.array(getattr(T, nm))), nm
+    tp = lf.geometry_query(G, "tree_params", np.float64)
+    assert tp[0] == T.x0 and tp[1] == T.y0 and tp[2] == T.W and int(tp[3]) == T.D and int(tp[4]) == T.l0
+    assert np.array_equal(q("p_level"), np.array(T.p_level))
+    vp, vi = q("vfree_ptr"), q("vfree_idx")
+    for b in range(T.nbox):
+        assert list(vi[vp[b]:vp[b + 1]]) == T.V_free[b]
+    up, ui = q("ufree_ptr"), q("ufree_idx")
+    for b in T.boxes_at(T.D):
+        assert list(ui[up[b]:up[b + 1]]) == T.U_free[b]
+    comps = q("components").reshape(-1, 4)
+    assert [tuple(c) for c in comps] == T.comps
+    rp, ri, rc = q("vreact_ptr"), q("vreact_idx"), q("vreact_comp")
+    urp, uri, urc = q("ureact_ptr"), q("ureact_idx"), q("ureact_comp")
+    for b in range(T.nbox):
+        got = {}
+        for e in range(rp[b], rp[b + 1]):
+            got.setdefault(int(rc[e]), []).append(int(ri[e]))
+        want = {c: T.V_react[c][b] for c in range(len(T.comps)) if b in T.V_react[c]}
+        assert got == want, b
+    for b in T.boxes_at(T.D):
+        got = {}
+        for e in range(urp[b], urp[b + 1]):
+            got.setdefault(int(urc[e]), []).append(int(uri[e]))
+        want = {c: T.U_react[c][b] for c in range(len(T.comps)) if T.U_react[c].get(b)}
+        assert got == want, b
+
+
+@pytest.mark.parametrize("p,tol", [(10, 1e-4), (20, 1e-7)])
+def test_fmm_matvec_within_truncation_tolerance(small3, p, tol):
+    # leaf size 16 gives several levels of far field for the free-space part and
+    # for the reaction components; the error must stay within the stated
+    # truncation tolerance of the expansion order p
+    lf, pts, w, K = small3["lf"], small3["pts"], small3["w"], small3["K"]
+    G = lf.geometry_build(small3["M"], pts, w, p=p, leaf_size=16)
+    tp = lf.geometry_query(G, "tree_params", np.float64)
+    assert tp[4] <= tp[3], "far field must be active"
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    err = relerr(lf.matvec(G, x), K @ x)
+    print(f"p={p}: FMM matvec rel l2 error {err:.3e}, tree params {tp}")
+    assert err <= tol
+
+
+def test_fmm_gmres_with_preconditioner(small3):
+    lf, pts, w, K, med = small3["lf"], small3["pts"], small3["w"], small3["K"], small3["med"]
+    G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=16)
+    b = obg.rhs(med, np.deg2rad(45.0), pts[:, 0], pts[:, 1])
+    x0, i0 = lf.gmres_solve(G, b, tol=1e-8, precond=False)
+    x1, i1 = lf.gmres_solve(G, b, tol=1e-8, precond=True)
+    ref = np.linalg.solve(K, b)
+    print("iterations plain/precond", i0["iterations"], i1["iterations"], relerr(x0, ref), relerr(x1, ref))
+    assert i0["converged"] and i1["converged"]
+    assert i1["iterations"] < i0["iterations"]
+    assert relerr(x1, ref) <= 1e-5 and relerr(x0, ref) <= 1e-5
