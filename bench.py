@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark: layered-media FMM matvec throughput (Mpts/s) on the C2 workload.
+
+Workload (synthetic, seeded): three-layer medium with interfaces y = 0, -2,
+k = (4, 6, 8), eta = (1, 2, 3); 64 circles/ellipses (radii in [0.2, 0.6],
+centres in [-10, 10] x [-4, 2], seed 12452, some crossing interfaces) with
+1024 boundary nodes each, N = 65536 Nystrom points; FMM order p = 20; FP64.
+
+One step = one application of the Nystrom operator y = K x through
+lfmm_matvec (gather, P2M, M2M, M2L free-space + reaction, L2L, L2P, near
+field, scatter) with x and y resident in HBM; the L2 cache is flushed before
+every step.  The GMRES solve to 1e-8 with the DD preconditioner and the
+set-up time are reported beside it.  With --gpus N > 1 each rank solves its
+own replica of the workload (the matvec of one geometry does not shard), and
+`value` sums the ranks' throughput over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (dense Nystrom rows with direct
+Sommerfeld quadrature) on the host cores on a bounded sample of rows.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate stated in the profiling recipe (not in MEASURED_PEAKS.json)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def workload(name):
+    from workloads import config_c1, config_c2
+
+    wl = config_c2() if name == "c2" else config_c1()
+    desc = ("C2: 3-layer medium (interfaces y=0,-2; k=4,6,8; eta=1,2,3), 64 circles/ellipses x 1024 nodes, "
+            "N=65536, p=20, FP64") if name == "c2" else "C1: 2-layer medium, 1 circle, N=256"
+    return wl, desc
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def algorithmic_work(lf, G, n):
+    """Per-launch algorithmic FLOPs of M2L and bytes of the near field (one RHS column)."""
+    lev = lf.geometry_query(G, "box_level")
+    pl = lf.geometry_query(G, "p_level")
+    vfp = lf.geometry_query(G, "vfree_ptr")
+    vrp = lf.geometry_query(G, "vreact_ptr")
+    nf = np.diff(vfp)
+    nr = np.diff(vrp)
+    coef = (2 * pl[lev] + 1).astype(np.float64)
+    m2l_flops = float(np.sum((nf + nr) * 8.0 * coef * coef))
+    tp = lf.geometry_query(G, "tree_params", np.float64)
+    nnz = float(tp[8])
+    near_bytes = 16.0 * nnz + 48.0 * n
+    return {"m2l_flops": m2l_flops, "near_bytes": near_bytes, "near_nnz": nnz,
+            "m2l_pairs_free": int(nf.sum()), "m2l_pairs_reaction": int(nr.sum()),
+            "D": int(tp[3]), "l0": int(tp[4]), "reaction_tables": int(tp[9])}
+
+
+def cpu_baseline(wl, rows_per_sample, n_samples=1):
+    """Time the oracle on a bounded sample of full rows of K (FP64, host cores)."""
+    from oracle import core, nystrom
+
+    pts, w, _, _ = nystrom.elements(wl.bodies)
+    n = pts.shape[0]
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    cnt = 0.0
+    for _ in range(n_samples):
+        r = rng.integers(0, n)
+        cols = rng.permutation(n)[: int(rows_per_sample * n)] if rows_per_sample < 1 else None
+        if cols is None:
+            nystrom.dense_rows(wl.medium, pts, w, [r])
+            cnt += 1.0
+        else:
+            # a fraction of a row: the same per-entry work (free-space + Sommerfeld reaction)
+            core.gr_block(wl.medium, pts[cols, 0], pts[cols, 1], pts[r:r + 1, 0], pts[r:r + 1, 1])
+            cnt += cols.size / n
+    dt = time.perf_counter() - t0
+    # full dense matvec time extrapolated from the per-row time: N rows
+    t_full = dt / cnt * n
+    return {"value": n / t_full / 1e6, "unit": "Mpts/s", "cores": core.num_threads(), "kind": "oracle",
+            "sample": f"{cnt:g} full row(s) of the dense {n}x{n} Nystrom matrix with direct Sommerfeld "
+                      f"quadrature, {dt:.1f} s; full matvec extrapolated to {t_full:.3g} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl, desc = workload(args.workload)
+    frac = 0.25 if args.workload == "c2" else 1.0
+    for _ in range(args.warmup):
+        cpu_baseline(wl, min(frac, 0.02))
+    res = cpu_baseline(wl, frac, n_samples=args.steps)
+    n = wl.n_elements
+    line = {
+        "impl": "reference",
+        "metric": "FMM matvec Mpts/s", "value": res["value"], "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * res["seconds"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "N": n},
+        "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": res["value"], "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2511_12450_gb300 import lfmm
+
+    wl, desc = workload(args.workload)
+    med = wl.medium
+    M = lfmm.medium_create(med.interfaces, med.k, med.eta)
+    pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+    n = pts.shape[0]
+    t0 = time.perf_counter()
+    G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size, profile=True)
+    setup_s = time.perf_counter() - t0
+    work = algorithmic_work(lfmm, G, n)
+    gen = torch.Generator(device="cpu").manual_seed(1234 + rank)
+    x = torch.complex(torch.randn(n, generator=gen, dtype=torch.float64),
+                      torch.randn(n, generator=gen, dtype=torch.float64)).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        lfmm.matvec(G, x, y)
+    torch.cuda.synchronize()
+    st0 = lfmm.stage_times(G)
+    clocks = Clocks(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lfmm.matvec(G, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    st1 = lfmm.stage_times(G)
+    total_ms = float(np.sum(times))
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms * 1e-3) / 1e6
+    stages = {k: {"count": st1[k]["count"] - st0[k]["count"], "ms": st1[k]["ms"] - st0[k]["ms"]} for k in st1}
+
+    # end to end through the C ABI with host (pinned) buffers: H2D + matvec + D2H per step
+    xh = torch.empty(n, dtype=torch.complex128).pin_memory()
+    yh = torch.empty(n, dtype=torch.complex128).pin_memory()
+    xh.copy_(x.cpu())
+    xa, ya = xh.numpy(), yh.numpy()
+    for _ in range(2):
+        lfmm.matvec(G, xa, ya)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lfmm.matvec(G, xa, ya)
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_value = world * n * args.steps / float(np.sum(e2e_times)) / 1e6
+    assert np.allclose(ya, y.cpu().numpy(), rtol=1e-12, atol=1e-12 * float(np.abs(ya).max()))
+
+    # roofline of the dominant stage
+    peaks, src = measured_peaks()
+    dom = max(("m2l", "near"), key=lambda k: stages[k]["ms"])
+    if dom == "m2l":
+        avg_s = stages["m2l"]["ms"] / max(stages["m2l"]["count"], 1) * 1e-3
+        achieved = work["m2l_flops"] / avg_s / 1e12
+        roof = {"kernel": "k_m2l", "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 (profiling recipe), not measured"}
+    else:
+        avg_s = stages["near"]["ms"] / max(stages["near"]["count"], 1) * 1e-3
+        peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+        achieved = work["near_bytes"] / avg_s / 1e9
+        roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src}
+
+    solve = None
+    if not args.no_solve:
+        b = lfmm.rhs_plane_wave(G, [math.radians(float(wl.angles_deg[0]))], device=True)
+        xs, info = lfmm.gmres_solve(G, b, tol=1e-8, max_iter=1000, precond=True)
+        solve = {"metric": "GMRES solve s @1e-8 resid", "seconds": info["solve_seconds"],
+                 "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+                 "converged": bool(info["converged"]), "precond": "overlapping DD (Sec. 4.2)",
+                 "setup_seconds": setup_s}
+
+    launches_per_step = 6 + 2 * max(work["D"] - work["l0"], 0) if work["l0"] <= work["D"] else 3
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, 1 if args.workload == "c2" else 1.0)
+        cpu.pop("seconds", None)
+    if rank == 0:
+        line = {
+            "metric": "FMM matvec Mpts/s", "value": value, "unit": "Mpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "N": n, "p": wl.p, "leaf_size": wl.leaf_size,
+                       "l2": "flushed (512 MB write) before every step",
+                       "parallelism": f"{world} independent replica(s), one per GPU"},
+            "e2e": {"value": e2e_value, "unit": "Mpts/s", "h2d_bytes_per_step": 16 * n,
+                    "d2h_bytes_per_step": 16 * n},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "stages_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in stages.items()},
+            "work": work,
+            "solve": solve,
+            "setup_seconds": setup_s,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -56,6 +56,13 @@ enum {
     LFMM_DEVICE_PTRS = 1    /* vector arguments are device pointers */
 };
 
+/* lfmm_params.flags */
+enum {
+    LFMM_PROFILE_STAGES = 1 /* time every stage of lfmm_matvec with CUDA events on the call's
+                               stream (adds one stream synchronisation per call); read the
+                               totals with lfmm_geometry_query("stage_times") */
+};
+
 typedef struct lfmm_medium_s *lfmm_medium;
 typedef struct lfmm_geometry_s *lfmm_geometry;
 
@@ -64,7 +71,7 @@ typedef struct {
     int32_t p;          /* expansion order at the fine levels (default 20); coarse levels
                            raise it with k*w (wide-band rule), up to 80 */
     int32_t leaf_size;  /* max points per leaf box (default 64) */
-    int32_t flags;      /* reserved, 0 */
+    int32_t flags;      /* LFMM_PROFILE_STAGES or 0 */
     int32_t reserved;
 } lfmm_params;
 
@@ -173,7 +180,10 @@ lfmm_status lfmm_polygon_elements(int32_t n_poly, const int32_t *counts, const d
  * NULL or nbytes is too small nothing is copied.  Names: "perm" (int32[n],
  * sorted position -> input index), "box_level", "box_layer", "box_ix",
  * "box_iy", "box_begin", "box_end", "box_parent" (int32[nbox]),
- * "tree_params" (double[8]: x0, y0, W, D, l0, nbox, ncomp, n_near_blocks),
+ * "tree_params" (double[11]: x0, y0, W, D, l0, nbox, ncomp, n_near_blocks,
+ * near-field entries, reaction M2L tables, set-up seconds),
+ * "stage_times" (double[2*8]: per stage p2m, m2m, m2l, l2l, l2p, near, gather,
+ * scatter the number of timed launches and their total milliseconds),
  * "p_level" (int32[D+1]), "vfree_ptr"/"vfree_idx", "ufree_ptr"/"ufree_idx",
  * "vreact_ptr"/"vreact_idx"/"vreact_comp", "ureact_ptr"/"ureact_idx"/"ureact_comp"
  * (CSR over boxes), "components" (int32[4*ncomp]: ls, a, lt, b).

@@ -29,10 +29,14 @@ framework without giving its parameters; this is the reading used here):
   * reaction lists, one set per non-zero component (l, *, l', star) of
     Sec. 3.1 (the remark on zero components): source boxes of layer l and
     target boxes of layer l'; the image-frame vertical offset of a box pair is
-    D = h_*(y_S) + h_star(y_T) + H_c (heights of the box centres above/below the
-    interface each wave last met, plus the thickness of the layers the wave
-    must cross, Sec. 3.2); a candidate is far (M2L) if its cell column differs
-    from T's by at least 2 or D >= 2 w_l (1 - 1e-9), otherwise near.
+    D = h_*(S) + h_star(T) + H_c: heights above/below the interface each wave
+    last met of the reaction expansion centres, plus the thickness of the
+    layers the wave must cross (the effective transmission distance of
+    Sec. 3.2).  A box's reaction expansion centre is its cell centre, moved
+    for a cell that straddles that interface to the middle of the part of the
+    cell on the layer's side (cell bounds lo = y0 + iy w, hi = y0 + (iy+1) w);
+    a candidate is far (M2L) if its cell column differs from T's by at least 2
+    or D >= 2 w_l (1 - 1e-9), otherwise near.
 """
 
 from __future__ import annotations
@@ -107,6 +111,24 @@ def src_height(yint, ls, a, y):
 
 def tgt_height(yint, lt, b, y):
     return (yint[lt - 1] - y) if b == 0 else (y - yint[lt])
+
+
+def clipped_height(y_if, above, lo, hi):
+    """Height above (or below) the interface y_if of the centre of the part of the
+    cell [lo, hi] that lies on the valid side (the side holding the layer's points)."""
+    if above:
+        return 0.5 * (max(lo, y_if) + hi) - y_if
+    return y_if - 0.5 * (lo + min(hi, y_if))
+
+
+def src_height_box(yint, ls, a, lo, hi):
+    # arrival up: heights above the layer's bottom interface; down: below its top one
+    return clipped_height(yint[ls], True, lo, hi) if a == 0 else clipped_height(yint[ls - 1], False, lo, hi)
+
+
+def tgt_height_box(yint, lt, b, lo, hi):
+    # departure up: depth below the layer's top interface; down: height above its bottom one
+    return clipped_height(yint[lt - 1], False, lo, hi) if b == 0 else clipped_height(yint[lt], True, lo, hi)
 
 
 class Tree:
@@ -228,11 +250,15 @@ class Tree:
                         self.V_free[T].append(S)
         self.U_free = {T: near[T] for T in self.boxes_at(self.D)}
 
+    def cell_y(self, b):
+        w = self.width(self.box_level[b])
+        return self.y0 + self.box_iy[b] * w, self.y0 + (self.box_iy[b] + 1) * w
+
     def comp_D(self, c, S, T):
         ls, a, lt, b = self.comps[c]
-        yS = self.centre(S)[1]
-        yT = self.centre(T)[1]
-        return (src_height(self.yint, ls, a, yS) + tgt_height(self.yint, lt, b, yT)) + \
+        loS, hiS = self.cell_y(S)
+        loT, hiT = self.cell_y(T)
+        return (src_height_box(self.yint, ls, a, loS, hiS) + tgt_height_box(self.yint, lt, b, loT, hiT)) + \
             comp_extra_thickness(self.yint, self.comps[c])
 
     def _reaction_lists(self):

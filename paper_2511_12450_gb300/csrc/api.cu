@@ -65,8 +65,34 @@ QuadRule make_quad_rule(const MediumDev& m) {
     q.es_hv = 0.07;
     q.nes = 84;          // v in [-3.6, 2.21]
     q.min_panels = 16;
+    q.tab_es_v0 = -3.6;
+    q.tab_es_hv = 0.0175;
+    q.tab_nes = 340;     // v in [-3.6, 2.33]
+    q.tab_panel_mult = 3;
     gauss_legendre8(q.gl_x, q.gl_w);
     return q;
+}
+
+void prof_begin(lfmm_geometry_s* g, Stage st, cudaStream_t s) {
+    if (!g->prof.on) return;
+    cuda_check(cudaEventRecord(g->prof.ev[2 * st], s), "event record");
+    g->prof.armed[st] = true;
+}
+void prof_end(lfmm_geometry_s* g, Stage st, cudaStream_t s) {
+    if (!g->prof.on) return;
+    cuda_check(cudaEventRecord(g->prof.ev[2 * st + 1], s), "event record");
+}
+void prof_flush(lfmm_geometry_s* g, cudaStream_t s) {
+    if (!g->prof.on) return;
+    cuda_check(cudaStreamSynchronize(s), "profile sync");
+    for (int k = 0; k < ST_COUNT; ++k) {
+        if (!g->prof.armed[k]) continue;
+        float ms = 0.f;
+        cuda_check(cudaEventElapsedTime(&ms, g->prof.ev[2 * k], g->prof.ev[2 * k + 1]), "event elapsed");
+        g->prof.ms[k] += ms;
+        g->prof.cnt[k] += 1.0;
+        g->prof.armed[k] = false;
+    }
 }
 
 template <class F>
@@ -101,6 +127,10 @@ static void require(bool c, const char* msg) {
 }
 
 static void free_geometry(lfmm_geometry_s* g) {
+    if (g->prof.on)
+        for (int k = 0; k < 2 * ST_COUNT; ++k) cudaEventDestroy(g->prof.ev[k]);
+    g->prof.on = false;
+    fmm_free(g);
     for (void* p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->d_xs) cudaFree(g->d_xs);
@@ -221,6 +251,11 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         g->p = p;
         g->leaf_size = leaf;
         g->quad = make_quad_rule(m);
+        if (prm && (prm->flags & LFMM_PROFILE_STAGES)) {
+            for (int k = 0; k < 2 * ST_COUNT; ++k)
+                cuda_check(cudaEventCreate(&g->prof.ev[k]), "event create");
+            g->prof.on = true;
+        }
         build_tree(g->tree, px, py, layer, m, p, leaf);
         TreeHost& t = g->tree;
         // sorted-order copies
@@ -297,9 +332,14 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
             xin = g->d_hostbuf_x;
             yout = g->d_hostbuf_y;
         }
+        prof_begin(g, ST_GATHER, s);
         gather_sorted(g, xin, g->d_xs, nrhs, s);
+        prof_end(g, ST_GATHER, s);
         apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s);
+        prof_begin(g, ST_SCATTER, s);
         scatter_sorted(g, g->d_ys, yout, nrhs, s);
+        prof_end(g, ST_SCATTER, s);
+        prof_flush(g, s);
         if (!dev) {
             cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "y d2h");
             cuda_check(cudaStreamSynchronize(s), "matvec sync");
@@ -458,6 +498,10 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
         } else if (nm == "tree_params") {
             dtmp = {t.x0, t.y0, t.W, (double)t.D, (double)t.l0, (double)t.nbox, (double)t.comps.size(),
                     (double)g->n_blocks, (double)g->nb_nnz, (double)g->n_rkeys, g->setup_seconds};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "stage_times") {
+            for (int k = 0; k < ST_COUNT; ++k) { dtmp.push_back(g->prof.cnt[k]); dtmp.push_back(g->prof.ms[k]); }
             src = dtmp.data();
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else {

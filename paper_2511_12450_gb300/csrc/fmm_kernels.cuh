@@ -22,33 +22,37 @@ namespace lfmm {
 
 #define LFMM_PMAX 80
 
-// P2M on the leaves: one CTA (128 threads) per leaf; points in chunks of 32.
-__global__ void k_p2m(const int* __restrict__ box_begin, const int* __restrict__ box_end,
-                      const int* __restrict__ box_layer, const double* __restrict__ bcx,
-                      const double* __restrict__ bcy, const int64_t* __restrict__ coef_off, int leaf0,
-                      int p, MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
-                      const double* __restrict__ pw, const cd* __restrict__ phi, int64_t n, int nrhs,
-                      int64_t ncoef, cd* __restrict__ M) {
+// P2M over a list of point ranges: entry e expands the points [beg, end) of
+// layer lay about (cx, cy) to order p: M_n = sum_j Q_j J_n(k rho_j) e^{-i n theta_j}.
+// Used for the leaves (about the cell centres) and for the cells that straddle an
+// interface (about their reaction centres).  One CTA (128 threads) per entry.
+struct ExpEntry {
+    int beg, end, lay, p;
+    double cx, cy;
+    int64_t off;   // coefficient offset in the output/input array
+};
+
+__global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const double* __restrict__ px,
+                      const double* __restrict__ py, const double* __restrict__ pw, const cd* __restrict__ phi,
+                      int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
     extern __shared__ double sm[];
-    const int np1 = p + 1;
+    const ExpEntry E = ent[blockIdx.x];
+    const int p = E.p, np1 = p + 1;
     double* J = sm;                          // [32][p+1]
     cd* zp = (cd*)(sm + 32 * np1);           // [32][p+1]   z^n, z = e^{-i theta}
     cd* q = zp + 32 * np1;                   // [32] charges of the current column
-    const int B = leaf0 + blockIdx.x;
-    const int b0 = box_begin[B], nb = box_end[B] - b0;
-    const double k = m.k[box_layer[B]];
-    const double cx = bcx[B], cy = bcy[B];
-    const int64_t off = coef_off[B];
+    const int b0 = E.beg, nb = E.end - E.beg;
+    const double k = m.k[E.lay];
     const int nco = 2 * p + 1;
     for (int col = 0; col < nrhs; ++col) {
-        // accumulators: thread t owns coefficient indices t, t+128, ...
+        // accumulators: thread t owns coefficient indices t, t+128
         cd acc[2] = {mk(0, 0), mk(0, 0)};
         for (int c0 = 0; c0 < nb; c0 += 32) {
             const int cnt = min(32, nb - c0);
             __syncthreads();
             if (threadIdx.x < cnt) {
                 const int j = b0 + c0 + threadIdx.x;
-                double dx = px[j] - cx, dy = py[j] - cy;
+                double dx = px[j] - E.cx, dy = py[j] - E.cy;
                 double rho = hypot(dx, dy);
                 bessel_j_seq(k * rho, p, J + threadIdx.x * np1);
                 cd z = (rho > 0.0) ? mk(dx / rho, -dy / rho) : mk(1.0, 0.0);
@@ -74,7 +78,7 @@ __global__ void k_p2m(const int* __restrict__ box_begin, const int* __restrict__
         }
         for (int s = 0; s < 2; ++s) {
             int idx = threadIdx.x + 128 * s;
-            if (idx < nco) M[(int64_t)col * ncoef + off + idx] = acc[s];
+            if (idx < nco) M[(int64_t)col * stride + E.off + idx] = acc[s];
         }
     }
 }
@@ -123,15 +127,19 @@ __global__ void k_m2l(int box_first, const int* __restrict__ box_level, const in
                       const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
                       const int* __restrict__ comp, const ReactKey* __restrict__ rkeys,
                       const cd* __restrict__ m2lr, int nrhs, int64_t ncoef, const cd* __restrict__ Min,
-                      cd* __restrict__ Lout) {
+                      cd* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
+                      int64_t nslotcoef, const cd* __restrict__ Mp, cd* __restrict__ Lp) {
     extern __shared__ cd sms[];   // source coefficients
     const int T = box_first + blockIdx.x;
     const int l = box_level[T];
     const int p = p_level[l];
     const int nco = 2 * p + 1;
+    const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
     for (int col = 0; col < nrhs; ++col) {
         const cd* Mc = Min + (int64_t)col * ncoef;
+        const cd* Mpc = Mp + (int64_t)col * nslotcoef;
         cd acc[2] = {mk(0, 0), mk(0, 0)};
+        cd accs[2][2] = {{mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}};   // [side][s]
         // free space: L_n += sum_m M_m Tab[m - n]
         for (int e = vf_ptr[T]; e < vf_ptr[T + 1]; ++e) {
             __syncthreads();
@@ -151,15 +159,18 @@ __global__ void k_m2l(int box_first, const int* __restrict__ box_level, const in
         // reaction components
         for (int e = vr_ptr[T]; e < vr_ptr[T + 1]; ++e) {
             __syncthreads();
-            const int64_t so = coef_off[vr_src[e]];
+            const int S = vr_src[e];
             const int c = vr_comp[e];
             const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
+            // source expansion: about the moved centre if S straddles the arrival interface
+            const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
+            const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
             // alpha_n = M_n (arrival down) or (-1)^n M_{-n} (arrival up)
             for (int i = threadIdx.x; i < nco; i += blockDim.x) {
                 int nn = i - p;
                 cd v;
-                if (a_dir == 1) v = Mc[so + i];
-                else { v = Mc[so + (-nn + p)]; if (nn & 1) v = -v; }
+                if (a_dir == 1) v = src[i];
+                else { v = src[-nn + p]; if (nn & 1) v = -v; }
                 sms[i] = v;
             }
             __syncthreads();
@@ -175,12 +186,19 @@ __global__ void k_m2l(int box_first, const int* __restrict__ box_level, const in
                 cd bsum = mk(0, 0);
                 for (int i = 0; i < nco; ++i) cfma(bsum, row[i], sms[i]);
                 if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
-                acc[s] += bsum;
+                // target expansion about the moved centre if T straddles the departure interface
+                const int side = (b_dir == 0) ? 1 : 0;
+                if (tslot[side] >= 0) accs[side][s] += bsum;
+                else acc[s] += bsum;
             }
         }
         for (int s = 0; s < 2; ++s) {
             int idx = threadIdx.x + blockDim.x * s;
-            if (idx < nco) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[s];
+            if (idx < nco) {
+                Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[s];
+                for (int side = 0; side < 2; ++side)
+                    if (tslot[side] >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[tslot[side]] + idx] = accs[side][s];
+            }
         }
     }
 }
@@ -210,34 +228,32 @@ __global__ void k_l2l(int lev_child_start, const int* __restrict__ box_parent, c
     }
 }
 
-// L2P on the leaves: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
-__global__ void k_l2p(const int* __restrict__ box_begin, const int* __restrict__ box_end,
-                      const int* __restrict__ box_layer, const double* __restrict__ bcx,
-                      const double* __restrict__ bcy, const int64_t* __restrict__ coef_off, int leaf0, int p,
-                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n,
-                      int nrhs, int64_t ncoef, const cd* __restrict__ L, cd* __restrict__ y) {
+// L2P over a list of point ranges: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
+// about (cx, cy).  Leaves (cell centres) and straddling leaves (reaction centres).
+__global__ void k_l2p(const ExpEntry* __restrict__ ent, MediumDev m, const double* __restrict__ px,
+                      const double* __restrict__ py, int64_t n, int nrhs, int64_t stride,
+                      const cd* __restrict__ L, cd* __restrict__ y) {
     extern __shared__ double sl[];
-    const int np1 = p + 1, nco = 2 * p + 1;
+    const ExpEntry E = ent[blockIdx.x];
+    const int p = E.p, np1 = p + 1, nco = 2 * p + 1;
     cd* Ls = (cd*)sl;                               // [nco]
     double* Jall = sl + 2 * nco;                     // [blockDim][p+1]
-    const int B = leaf0 + blockIdx.x;
-    const int b0 = box_begin[B], nb = box_end[B] - b0;
-    const double k = m.k[box_layer[B]];
-    const double cx = bcx[B], cy = bcy[B];
+    const int b0 = E.beg, nb = E.end - E.beg;
+    const double k = m.k[E.lay];
     double* J = Jall + threadIdx.x * np1;
     for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
         const int j = b0 + c0 + threadIdx.x;
         const bool act = (c0 + threadIdx.x) < nb;
         cd z = mk(1.0, 0.0);
         if (act) {
-            double dx = px[j] - cx, dy = py[j] - cy;
+            double dx = px[j] - E.cx, dy = py[j] - E.cy;
             double rho = hypot(dx, dy);
             bessel_j_seq(k * rho, p, J);
             if (rho > 0.0) z = mk(dx / rho, dy / rho);
         }
         for (int col = 0; col < nrhs; ++col) {
             __syncthreads();
-            for (int i = threadIdx.x; i < nco; i += blockDim.x) Ls[i] = L[(int64_t)col * ncoef + coef_off[B] + i];
+            for (int i = threadIdx.x; i < nco; i += blockDim.x) Ls[i] = L[(int64_t)col * stride + E.off + i];
             __syncthreads();
             if (act) {
                 cd acc = Ls[p] * J[0];
@@ -250,6 +266,84 @@ __global__ void k_l2p(const int* __restrict__ box_begin, const int* __restrict__
                 }
                 y[(int64_t)col * n + j] += acc;
             }
+        }
+    }
+}
+
+// Multipoles about the reaction centres of straddling parents from their
+// children (reaction centre of a straddling child, else its cell centre):
+// dst_n = sum_children sum_m src_m S_{n-m}, S_k = J_k(k |d|) e^{-i k theta_d},
+// d = (child centre) - (parent reaction centre).  One CTA per parent slot.
+struct M2MChild {
+    int pC;
+    int src_in_slots;
+    int64_t src_off, vec_off;
+};
+struct M2MSlot {
+    int pP;
+    int child_begin, child_end;   // range in the M2MChild array
+    int64_t dst_off;              // slot coefficient offset
+};
+
+__global__ void k_m2m_slots(const M2MSlot* __restrict__ par, const M2MChild* __restrict__ ch,
+                            const cd* __restrict__ vec, int nrhs, int64_t ncoef, int64_t nslotcoef,
+                            const cd* __restrict__ M, cd* __restrict__ Mp) {
+    extern __shared__ cd smk[];
+    const M2MSlot P = par[blockIdx.x];
+    const int ncP = 2 * P.pP + 1;
+    for (int col = 0; col < nrhs; ++col) {
+        cd acc[2] = {mk(0, 0), mk(0, 0)};
+        for (int c = P.child_begin; c < P.child_end; ++c) {
+            const M2MChild C = ch[c];
+            const int ncC = 2 * C.pC + 1, hw = P.pP + C.pC;
+            const cd* src = C.src_in_slots ? (Mp + (int64_t)col * nslotcoef + C.src_off) : (M + (int64_t)col * ncoef + C.src_off);
+            __syncthreads();
+            for (int i = threadIdx.x; i < ncC; i += blockDim.x) smk[i] = src[i];
+            __syncthreads();
+            const cd* S = vec + C.vec_off;
+            for (int s = 0; s < 2; ++s) {
+                int idx = threadIdx.x + blockDim.x * s;
+                if (idx >= ncP) break;
+                int nn = idx - P.pP;
+                cd a = acc[s];
+                for (int mm = -C.pC; mm <= C.pC; ++mm) cfma(a, smk[mm + C.pC], S[nn - mm + hw]);
+                acc[s] = a;
+            }
+        }
+        for (int s = 0; s < 2; ++s) {
+            int idx = threadIdx.x + blockDim.x * s;
+            if (idx < ncP) Mp[(int64_t)col * nslotcoef + P.dst_off + idx] = acc[s];
+        }
+    }
+}
+
+// Local-to-local translations with per-task vectors (reaction centres of
+// straddling cells): dst_n += sum_m src_m S_{m-n}, S_k = J_k(k |u|) e^{i k theta_u},
+// u = (destination centre) - (source centre).  Tasks of one level per launch;
+// no two tasks of a launch share a destination.
+struct L2LTask {
+    int pS, pD;
+    int64_t src_off, dst_off, vec_off;
+    int src_in_slots, dst_in_slots;   // 1: the coefficient lives in the slot arrays
+};
+
+__global__ void k_l2l_tasks(const L2LTask* __restrict__ tasks, const cd* __restrict__ vec, int nrhs,
+                            int64_t ncoef, int64_t nslotcoef, cd* __restrict__ L, cd* __restrict__ Lp) {
+    extern __shared__ cd stk[];
+    const L2LTask tk = tasks[blockIdx.x];
+    const int ncS = 2 * tk.pS + 1, ncD = 2 * tk.pD + 1, hw = tk.pS + tk.pD;
+    const cd* S = vec + tk.vec_off;
+    for (int col = 0; col < nrhs; ++col) {
+        const cd* src = tk.src_in_slots ? (Lp + (int64_t)col * nslotcoef + tk.src_off) : (L + (int64_t)col * ncoef + tk.src_off);
+        cd* dst = tk.dst_in_slots ? (Lp + (int64_t)col * nslotcoef + tk.dst_off) : (L + (int64_t)col * ncoef + tk.dst_off);
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncS; i += blockDim.x) stk[i] = src[i];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < ncD; idx += blockDim.x) {
+            int nn = idx - tk.pD;
+            cd a = mk(0, 0);
+            for (int mm = -tk.pS; mm <= tk.pS; ++mm) cfma(a, stk[mm + tk.pS], S[mm - nn + hw]);
+            dst[idx] += a;
         }
     }
 }
@@ -281,9 +375,14 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     cd* Fm = Fp + CH;                  // [CH]
     cd* uu = Fm + CH;                  // [CH] u
     cd* vv = uu + CH;                  // [CH] v
+    // table rule: finer detour (panels grow with the orders) and finer rays
+    QuadRule qt = q;
+    qt.es_v0 = q.tab_es_v0;
+    qt.es_hv = q.tab_es_hv;
+    qt.nes = q.tab_nes;
     double h;
-    const int P = detour_panels(q, K.X, K.D, &h);
-    const int ntot = P * 8 + 2 * q.nes;
+    const int P = detour_panels(q, K.X, K.D, &h) * q.tab_panel_mult + (pS + pT);
+    const int ntot = P * 8 + 2 * qt.nes;
     const int tm = threadIdx.x >> 3;          // 0..31 row within tile
     const int tn = (threadIdx.x & 7) * 4;     // 0..28 first column within tile
     cd acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
@@ -291,7 +390,7 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
         const int cnt = min(CH, ntot - j0);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            QuadNode nd = contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
+            QuadNode nd = contour_node(qt, j0 + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
             cd E = eikh(kya, K.hS) * eikh(kyb, K.hT);

@@ -29,9 +29,20 @@ struct QuadRule {
     double es_hv;
     int nes;           // nodes per ray
     int min_panels;    // minimum number of detour panels
+    // finer rule for the M2L moment tables, whose integrands carry w^n factors
+    // up to |n - m| = 2p: more detour panels per unit of oscillation and a
+    // smaller exp-sinh step
+    double tab_es_v0, tab_es_hv;
+    int tab_nes;
+    int tab_panel_mult;
     double gl_x[8];    // 8-point Gauss-Legendre rule on [-1, 1]
     double gl_w[8];
 };
+
+struct ExpEntry;
+struct L2LTask;
+struct M2MSlot;
+struct M2MChild;
 
 // reaction M2L table key (built on the host, evaluated on the device)
 struct ReactKey {
@@ -42,7 +53,19 @@ struct ReactKey {
 
 }  // namespace lfmm
 
+namespace lfmm {
+enum Stage { ST_P2M = 0, ST_M2M, ST_M2L, ST_L2L, ST_L2P, ST_NEAR, ST_GATHER, ST_SCATTER, ST_COUNT };
+struct StageProfiler {
+    bool on = false;
+    cudaEvent_t ev[2 * ST_COUNT] = {};
+    bool armed[ST_COUNT] = {};
+    double ms[ST_COUNT] = {};
+    double cnt[ST_COUNT] = {};
+};
+}  // namespace lfmm
+
 struct lfmm_geometry_s {
+    lfmm::StageProfiler prof;
     lfmm_medium_s* med = nullptr;
     MediumDev m;
     int64_t n = 0;
@@ -62,7 +85,28 @@ struct lfmm_geometry_s {
     int *d_child_begin = nullptr, *d_child_end = nullptr;
     int64_t *d_coef_off = nullptr;    // per box offset into M / L
     int64_t ncoef = 0;
-    cd *d_M = nullptr, *d_L = nullptr;
+    cd *d_M = nullptr, *d_L = nullptr;   // [coef_cols][ncoef]
+    int coef_cols = 0;
+    // reaction expansion centres moved off the cell centre (cells straddling an interface):
+    // one slot per (box, side), side 0 = the layer's bottom interface, 1 = its top interface
+    int n_slots = 0;
+    int64_t nslotcoef = 0;
+    int *d_slot_of = nullptr;          // [2 * nbox] slot index or -1
+    int64_t *d_slot_coef = nullptr;
+    cd *d_Mp = nullptr, *d_Lp = nullptr;   // [coef_cols][nslotcoef]
+    // P2M/L2P work lists (leaves about cell centres; straddling boxes/leaves about reaction centres)
+    int n_leaf_entries = 0, n_slot_entries = 0, n_slot_leaf_entries = 0;
+    lfmm::ExpEntry *d_leaf_entries = nullptr, *d_slot_entries = nullptr, *d_slot_leaf_entries = nullptr;
+    // multipole translations into reaction centres of straddling parents, per (level, side)
+    std::vector<int> m2m_slot_start;
+    lfmm::M2MSlot* d_m2m_slots = nullptr;
+    lfmm::M2MChild* d_m2m_children = nullptr;
+    cd* d_m2m_vecs = nullptr;
+    // local translations out of reaction centres, per (level, side)
+    std::vector<int> task_start;
+    int n_l2l_tasks = 0;
+    lfmm::L2LTask* d_l2l_tasks = nullptr;
+    cd* d_l2l_vecs = nullptr;
     // near field: block-sparse rows over target leaves
     int *d_nb_ptr = nullptr;          // nleaf + 1
     int *d_nb_src = nullptr;          // source leaf (box id) per block
@@ -131,6 +175,7 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
 // FMM far field (fmm.cu)
 void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+void fmm_free(lfmm_geometry_s* g);   // per-nrhs coefficient buffers
 // permutation helpers and the full operator (solver.cu)
 void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s);
 void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s);
@@ -144,5 +189,11 @@ void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64
                        cd* u, cudaStream_t s);
 
 QuadRule make_quad_rule(const MediumDev& m);
+
+// stage timers (api.cu): begin/end record events on the stream when profiling is on;
+// flush synchronises the stream and accumulates the elapsed times.
+void prof_begin(lfmm_geometry_s* g, Stage st, cudaStream_t s);
+void prof_end(lfmm_geometry_s* g, Stage st, cudaStream_t s);
+void prof_flush(lfmm_geometry_s* g, cudaStream_t s);
 
 }  // namespace lfmm

@@ -49,5 +49,8 @@ void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<do
 double comp_extra_thickness(const MediumDev& m, int ls, int a, int lt, int b);
 double src_height(const MediumDev& m, int ls, int a, double y);
 double tgt_height(const MediumDev& m, int lt, int b, double y);
+double clipped_height(double yif, bool above, double lo, double hi);
+double src_height_box(const MediumDev& m, int ls, int a, double lo, double hi);
+double tgt_height_box(const MediumDev& m, int lt, int b, double lo, double hi);
 
 }  // namespace lfmm

@@ -206,9 +206,11 @@ void near_build(lfmm_geometry_s* g) {
 
 void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
     if (g->nleaf == 0) return;
+    prof_begin(g, ST_NEAR, s);
     k_near_apply<<<g->nleaf, 128, 0, s>>>(g->d_nb_ptr, g->d_nb_src, g->d_nb_off, g->d_nb_val, g->d_box_begin,
                                           g->d_box_end, g->leaf0, x_sorted, y_sorted, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_near_apply");
+    prof_end(g, ST_NEAR, s);
 }
 
 }  // namespace lfmm

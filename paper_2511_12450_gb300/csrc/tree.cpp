@@ -16,9 +16,11 @@
 //    list; near = touching cells), and one set of lists per non-zero reaction
 //    component, with the near/far decision taken in the image frame of the
 //    component: horizontal cell offset, and vertical offset
-//    D = h_*(y_S) + h_star(y_T) + H_c (the effective transmission distance of
-//    Sec. 3.2 between box centres).  A pair is far if the column offset is at
-//    least 2 or D >= 2 w_l.
+//    D = h_*(S) + h_star(T) + H_c (the effective transmission distance of
+//    Sec. 3.2 between the reaction expansion centres: cell centres, moved for
+//    cells that straddle the interface to the middle of the part of the cell
+//    on the layer's side).  A pair is far if the column offset is at least 2
+//    or D >= 2 w_l.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -65,6 +67,23 @@ double src_height(const MediumDev& m, int ls, int a, double y) {
 
 double tgt_height(const MediumDev& m, int lt, int b, double y) {
     return (b == 0) ? (m.yint[lt - 1] - y) : (y - m.yint[lt]);
+}
+
+// Height above (above = true) or below the interface y_if of the centre of the
+// part of the cell [lo, hi] on the valid side: the reaction expansion centre of
+// a box whose cell straddles the interface is moved there, so that every
+// expansion centre lies on the side of its points.
+double clipped_height(double yif, bool above, double lo, double hi) {
+    if (above) return 0.5 * (std::max(lo, yif) + hi) - yif;
+    return yif - 0.5 * (lo + std::min(hi, yif));
+}
+
+double src_height_box(const MediumDev& m, int ls, int a, double lo, double hi) {
+    return (a == 0) ? clipped_height(m.yint[ls], true, lo, hi) : clipped_height(m.yint[ls - 1], false, lo, hi);
+}
+
+double tgt_height_box(const MediumDev& m, int lt, int b, double lo, double hi) {
+    return (b == 0) ? clipped_height(m.yint[lt - 1], false, lo, hi) : clipped_height(m.yint[lt], true, lo, hi);
 }
 
 void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<double>& py,
@@ -247,9 +266,10 @@ void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<do
                 }
                 for (int S : cands) {
                     if (l < t.l0) { nearl[T].push_back(S); continue; }
-                    double yS = t.y0 + (t.box_iy[S] + 0.5) * w;
-                    double yT = t.y0 + (t.box_iy[T] + 0.5) * w;
-                    double Dc = (src_height(med, C.ls, C.a, yS) + tgt_height(med, C.lt, C.b, yT)) + C.Hc;
+                    double loS = t.y0 + t.box_iy[S] * w, hiS = t.y0 + (t.box_iy[S] + 1) * w;
+                    double loT = t.y0 + t.box_iy[T] * w, hiT = t.y0 + (t.box_iy[T] + 1) * w;
+                    double Dc = (src_height_box(med, C.ls, C.a, loS, hiS) + tgt_height_box(med, C.lt, C.b, loT, hiT)) +
+                                C.Hc;
                     bool far = std::abs(t.box_ix[S] - t.box_ix[T]) >= 2 || Dc >= 2.0 * w * (1.0 - 1e-9);
                     if (far) vr[T].push_back({c, S});
                     else nearl[T].push_back(S);

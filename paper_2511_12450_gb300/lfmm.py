@@ -28,6 +28,8 @@ LFMM_ERR_QUADRATURE = -5
 LFMM_ERR_TIMEOUT = -6
 LFMM_ERR_HBM_BUDGET = -7
 LFMM_DEVICE_PTRS = 1
+LFMM_PROFILE_STAGES = 1
+STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
 EXPORTED = [
     "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
@@ -152,11 +154,12 @@ def medium_create(interfaces, k, eta) -> Medium:
     return Medium(h, yint, kc, et)
 
 
-def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, leaf_size: int = 64) -> Geometry:
+def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, leaf_size: int = 64,
+                   profile: bool = False) -> Geometry:
     pts = _f64(points).reshape(-1, 2)
     w = _f64(weights).reshape(-1)
     nrm = _f64(normals).reshape(-1, 2) if normals is not None else None
-    prm = Params(int(p), int(leaf_size), 0, 0)
+    prm = Params(int(p), int(leaf_size), LFMM_PROFILE_STAGES if profile else 0, 0)
     h = ctypes.c_void_p()
     _check(library().lfmm_geometry_build(medium.handle, pts.shape[0], _dp(pts), _dp(w),
                                          _dp(nrm) if nrm is not None else None, ctypes.byref(prm),
@@ -261,3 +264,9 @@ def geometry_query(g: Geometry, name: str, dtype=np.int32) -> np.ndarray:
     _check(library().lfmm_geometry_query(g.handle, name.encode(), ctypes.c_void_p(out.ctypes.data), need.value,
                                          ctypes.byref(need)))
     return out
+
+
+def stage_times(g: Geometry) -> dict:
+    """Per-stage launch counts and total milliseconds (geometries built with profile=True)."""
+    v = geometry_query(g, "stage_times", np.float64).reshape(-1, 2)
+    return {name: {"count": int(v[i, 0]), "ms": float(v[i, 1])} for i, name in enumerate(STAGES)}

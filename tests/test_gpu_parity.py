@@ -162,3 +162,63 @@ def test_fmm_gmres_with_preconditioner(small3):
     assert i0["converged"] and i1["converged"]
     assert i1["iterations"] < i0["iterations"]
     assert relerr(x1, ref) <= 1e-5 and relerr(x0, ref) <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def wide(gpu_lib):
+    from workloads import layered_wide
+
+    lf = gpu_lib
+    wl = layered_wide()
+    med = wl.medium
+    pts, w, _, _ = onys.elements(wl.bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    return dict(lf=lf, wl=wl, med=med, pts=pts, w=w, K=K, M=M)
+
+
+@pytest.mark.parametrize("p,tol", [(20, 1e-8)])
+def test_fmm_wide_band_straddling_cells(wide, p, tol):
+    # C2's medium and region with few points: the coarse levels are many
+    # wavelengths wide (p up to ~57) and many cells straddle the interfaces
+    lf, pts, w, K = wide["lf"], wide["pts"], wide["w"], wide["K"]
+    G = lf.geometry_build(wide["M"], pts, w, p=p, leaf_size=8)
+    tp = lf.geometry_query(G, "tree_params", np.float64)
+    pl = lf.geometry_query(G, "p_level")
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    err = relerr(lf.matvec(G, x), K @ x)
+    print(f"wide: N={G.n} D={int(tp[3])} l0={int(tp[4])} p_level={pl.tolist()} rel err {err:.3e}")
+    assert err <= tol
+
+
+def test_fmm_multiple_rhs_columns_match_single(small3):
+    lf, pts, w = small3["lf"], small3["pts"], small3["w"]
+    G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=16)
+    rng = np.random.default_rng(7)
+    X = np.asfortranarray(rng.standard_normal((G.n, 3)) + 1j * rng.standard_normal((G.n, 3)))
+    Y = lf.matvec(G, X)
+    for c in range(3):
+        y1 = lf.matvec(G, np.ascontiguousarray(X[:, c]))
+        assert relerr(Y[:, c], y1) <= 1e-14
+
+
+def test_c2_full_size_sampled_rows(gpu_lib):
+    # full-size C2 (N = 65536) in the launch configuration the benchmark times,
+    # against full rows of the dense oracle matrix
+    from workloads import config_c2
+
+    lf = gpu_lib
+    wl = config_c2()
+    med = wl.medium
+    pts, w, nrm = lf.polygon_elements(wl.bodies)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    y = lf.matvec(G, x)
+    rows = rng.integers(0, G.n, 3)
+    ref = onys.dense_rows(med, pts, w, rows) @ x
+    err = np.max(np.abs(y[rows] - ref) / np.abs(ref))
+    print(f"C2 sampled rows: max rel err {err:.3e}")
+    assert err <= 1e-7

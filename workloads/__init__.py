@@ -25,4 +25,5 @@ from .geometry import (  # noqa: F401
     example3,
     random_bodies,
     layered_small,
+    layered_wide,
 )

@@ -276,3 +276,17 @@ def layered_small(n_bodies: int = 3, nodes: int = 200, seed: int = 7, n_layers: 
         if not interfaces or any(_crosses(p, med.interfaces) for p in polys):
             break
     return Workload(f"small_{n_layers}L", med, polys, np.array([45.0]), p=20, leaf_size=32)
+
+
+def layered_wide(n_bodies: int = 5, nodes: int = 80, seed: int = 21) -> Workload:
+    """Few small bodies spread over the C2 region (same medium): coarse tree levels are
+    many wavelengths wide and their cells straddle interfaces, at a size the oracle
+    can still evaluate densely."""
+    med = Medium(interfaces=[0.0, -2.0], k=[4.0, 6.0, 8.0], eta=[1.0, 2.0, 3.0])
+    rng = np.random.default_rng(seed)
+    while True:
+        polys = random_bodies(rng, n_bodies, ((-10.0, 10.0), (-4.0, 2.0)), med.interfaces, nodes,
+                              rmin=0.2, rmax=0.6, iface_tol=1e-3)
+        if any(_crosses(p, med.interfaces) for p in polys):
+            break
+    return Workload("wide_c2_medium", med, polys, np.array([45.0]), p=20, leaf_size=8)
