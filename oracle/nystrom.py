@@ -107,6 +107,26 @@ def dense_rows(medium, pts, w, rows, tol_rel: float = 1e-13) -> np.ndarray:
     return out
 
 
+def dense_row_block(medium, pts, w, row: int, cols, tol_rel: float = 1e-13) -> np.ndarray:
+    """Entries K[row, cols] of one row (a bounded sample of the dense definition)."""
+    pts = np.asarray(pts, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    cols = np.asarray(cols, dtype=np.int64)
+    lay = layer_of(medium, pts[:, 1])
+    k = np.asarray(medium.k, dtype=np.float64)
+    out = np.zeros(cols.size, dtype=np.complex128)
+    same = lay[cols] == lay[row]
+    r = np.hypot(pts[cols, 0] - pts[row, 0], pts[cols, 1] - pts[row, 1])
+    sel = same & (r > 0)
+    out[sel] = gf(k[lay[row]], r[sel]) * w[cols[sel]]
+    if np.asarray(medium.interfaces).size > 0:
+        g = core.gr_block(medium, pts[cols, 0], pts[cols, 1], pts[row:row + 1, 0], pts[row:row + 1, 1],
+                          tol_rel=tol_rel)
+        out += g[:, 0] * w[cols]
+    out[cols == row] += self_term(k[lay[row]], w[row])
+    return out
+
+
 def field(medium, pts, w, Phi, targets, tol_rel: float = 1e-13) -> np.ndarray:
     """Scattered field u^s at off-boundary targets from the unknown Phi = eta phi."""
     pts = np.asarray(pts, dtype=np.float64)
