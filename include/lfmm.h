@@ -143,6 +143,28 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
                         int32_t flags, void *stream);
 
 /*
+ * y = K x like lfmm_matvec (one right-hand side, DEVICE pointers on `stream`),
+ * but allocating nothing.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory when they need a matvec -- code
+ * running while a stream is captured into a CUDA graph, real-time threads that
+ * must stay out of the allocator, hosts with a fixed memory budget.  lfmm_matvec
+ * allocates its work buffers on first use; this call uses instead one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits.
+ *   - The array's device address is looked up on the first call made on each
+ *     device (with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the array and it keeps the last call's contents; calls
+ *     that overlap on the GPU (other streams or threads) race and must be
+ *     serialised by the caller.
+ *   - Geometries whose work buffers (sorted x and y, multipole and local
+ *     coefficients) exceed the array are rejected with LFMM_ERR_INVALID_ARG
+ *     before any device work (C2-sized problems, N = 65536, need about 16 MiB).
+ *   - The stage profiler is not run by this call.
+ */
+lfmm_status lfmm_matvec_static(lfmm_geometry g, const void *x, void *y, void *stream);
+
+/*
  * Solve K x = b by GMRES (x0 = 0), right-preconditioned by the overlapping
  * domain-decomposition preconditioner when prm->precond is set (Sec. 4.2).
  * Returns LFMM_NOT_CONVERGED (with the best iterate in x and info filled) if

@@ -34,7 +34,7 @@ STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 EXPORTED = [
     "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
     "lfmm_rhs_plane_wave", "lfmm_matvec", "lfmm_gmres_solve", "lfmm_eval_field",
-    "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error",
+    "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error", "lfmm_matvec_static",
 ]
 
 
@@ -79,6 +79,7 @@ def library():
         lib.lfmm_geometry_destroy.argtypes = [vp]
         lib.lfmm_rhs_plane_wave.argtypes = [vp, i32, dp, vp, i32, vp]
         lib.lfmm_matvec.argtypes = [vp, i32, vp, vp, i32, vp]
+        lib.lfmm_matvec_static.argtypes = [vp, vp, vp, vp]
         lib.lfmm_gmres_solve.argtypes = [vp, i32, vp, vp, ctypes.POINTER(GmresParams), ctypes.POINTER(GmresInfo), vp]
         lib.lfmm_eval_field.argtypes = [vp, i32, vp, i64, dp, vp, i32, vp]
         lib.lfmm_polygon_elements.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]
@@ -216,6 +217,17 @@ def matvec(g: Geometry, x, y=None, stream=None):
         raise ValueError("x and y must both be host arrays or both device tensors")
     st = _stream_of(stream) if flags else ctypes.c_void_p(0)
     _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
+    return y
+
+
+def matvec_static(g: Geometry, x, y, stream=None):
+    """y = K x with the library's fixed device work array (device tensors, one column, no allocation)."""
+    if not (_is_torch_cuda(x) and _is_torch_cuda(y)):
+        raise TypeError("matvec_static takes CUDA tensors")
+    if x.numel() != g.n or y.numel() != g.n:
+        raise ValueError("one column of n entries expected")
+    _check(library().lfmm_matvec_static(g.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                        _stream_of(stream)))
     return y
 
 
