@@ -79,26 +79,25 @@ __host__ __device__ inline void bessel_j_seq(double x, int p, double* out) {
         for (int n = 1; n <= p; ++n) out[n] = 0.0;
         return;
     }
-    int big = (int)x;
-    int start = (p > big ? p : big) + 24 + (int)sqrt(40.0 * ((p > big ? p : big) + 1));
+    const int m = (p > (int)x) ? p : (int)x;
+    int start = m + 16 + (int)(3.0 * sqrt((double)m));
     if (start & 1) ++start;
+    const double tx = 2.0 / x;
     double jp1 = 0.0, j = 1e-280, norm = 0.0;
     // walk down from start to 0; store entries n <= p
     for (int n = start; n >= 0; --n) {
         if (n <= p) out[n] = j;
-        if (n % 2 == 0) norm += (n == 0 ? j : 2.0 * j);
-        double jm1 = (n > 0) ? (2.0 * n / x) * j - jp1 : 0.0;
+        if ((n & 1) == 0) norm += (n == 0 ? j : 2.0 * j);
+        double jm1 = (n > 0) ? (n * tx) * j - jp1 : 0.0;
         jp1 = j;
         j = jm1;
         if (fabs(j) > 1e250) {  // rescale to avoid overflow
-            const double s = 1e-250;
-            j *= s; jp1 *= s; norm *= s;
-            int top = (n - 1 <= p) ? n - 1 : p;
-            for (int m = n; m <= p; ++m) if (m >= 0) out[m] *= s;
-            (void)top;
+            const double sc = 1e-250;
+            j *= sc; jp1 *= sc; norm *= sc;
+            for (int q = n; q <= p; ++q) if (q >= 0) out[q] *= sc;
         }
     }
-    double inv = 1.0 / norm;
+    const double inv = 1.0 / norm;
     for (int n = 0; n <= p; ++n) out[n] *= inv;
 }
 

@@ -400,7 +400,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     for (int l = D; l > l0; --l) {   // M2M: children at l -> parents at l-1
         int npar = t.level_start[l] - t.level_start[l - 1];
         int pC = t.p_level[l];
-        size_t smem = (size_t)(2 * pC + 1) * sizeof(cd);
+        size_t smem = (size_t)(4 * (2 * pC + 1) + 4 * (2 * t.p_level[l - 1] + 1)) * sizeof(cd);
         k_m2m<<<npar, 128, smem, s>>>(t.level_start[l - 1], g->d_child_begin, g->d_child_end, g->d_box_ix,
                                       g->d_box_iy, g->d_box_layer, g->d_coef_off, t.p_level[l - 1], pC, g->d_m2m,
                                       g->d_m2m_off, l, nlev, nrhs, g->ncoef, g->d_M);
@@ -421,7 +421,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         prof_begin(g, ST_M2L, s);
         int first = t.level_start[l0];
         int nbx = t.level_start[D + 1] - first;
-        size_t smem = (size_t)(2 * pmax + 1) * sizeof(cd);
+        size_t smem = (size_t)(M2L_CH * (2 * pmax + 1) + 3 * 4 * (2 * pmax + 1)) * sizeof(cd);
         k_m2l<<<nbx, 128, smem, s>>>(first, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
                                      g->d_vf_tab, g->d_m2lf, g->d_m2lf_off, g->d_vr_ptr, g->d_vr_src, g->d_vr_key,
                                      g->d_vr_comp, g->d_comp, g->d_rkeys, g->d_m2lr, nrhs, g->ncoef, g->d_M,
@@ -431,10 +431,10 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     }
     prof_begin(g, ST_L2L, s);
     for (int l = l0 + 1; l <= D; ++l) {   // L2L: parents at l-1 -> children at l
-        int nch = t.level_start[l + 1] - t.level_start[l];
+        int npar = t.level_start[l] - t.level_start[l - 1];
         int pP = t.p_level[l - 1];
         size_t smem = (size_t)(2 * pP + 1) * sizeof(cd);
-        k_l2l<<<nch, 128, smem, s>>>(t.level_start[l], g->d_box_parent, g->d_box_ix, g->d_box_iy, g->d_box_layer,
+        k_l2l<<<npar, 128, smem, s>>>(t.level_start[l - 1], g->d_child_begin, g->d_child_end, g->d_box_ix, g->d_box_iy, g->d_box_layer,
                                      g->d_coef_off, pP, t.p_level[l], g->d_l2l, g->d_l2l_off, l, nlev, nrhs,
                                      g->ncoef, g->d_L);
         cuda_check(cudaGetLastError(), "k_l2l");

@@ -83,45 +83,71 @@ __global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const doubl
     }
 }
 
-// M2M for the parents at one level: M^P_n = sum_C sum_m M^C_m S^{quad(C)}_{n-m}
-__global__ void k_m2m(int lev_par_start, const int* __restrict__ child_begin, const int* __restrict__ child_end,
-                      const int* __restrict__ box_ix, const int* __restrict__ box_iy,
-                      const int* __restrict__ box_layer, const int64_t* __restrict__ coef_off, int pP, int pC,
-                      const cd* __restrict__ tab, const int64_t* __restrict__ tab_off, int lev_child, int nlev,
-                      int nrhs, int64_t ncoef, cd* __restrict__ M) {
-    extern __shared__ cd smc[];  // child coefficients
+// M2M for the parents at one level: M^P_n = sum_C sum_m M^C_m S^{quad(C)}_{n-m}.
+// One CTA (128 threads) per parent; all children's coefficients are staged in
+// shared memory at once; thread groups split the children and are reduced at the end.
+__global__ void __launch_bounds__(128) k_m2m(int lev_par_start, const int* __restrict__ child_begin,
+                      const int* __restrict__ child_end, const int* __restrict__ box_ix,
+                      const int* __restrict__ box_iy, const int* __restrict__ box_layer,
+                      const int64_t* __restrict__ coef_off, int pP, int pC, const cd* __restrict__ tab,
+                      const int64_t* __restrict__ tab_off, int lev_child, int nlev, int nrhs, int64_t ncoef,
+                      cd* __restrict__ M) {
+    extern __shared__ cd smc[];  // [4][ncC] children, then [G][ncP] partial sums
     const int P = lev_par_start + blockIdx.x;
     const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
     const int layer = box_layer[P];
+    const int c0 = child_begin[P], nch = child_end[P] - c0;
+    const int tpg = min(128, ((ncP + 31) / 32) * 32);
+    const int G = 128 / tpg;
+    const int g = threadIdx.x / tpg, lt = threadIdx.x % tpg;
+    cd* part = smc + 4 * ncC;
     for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nch * ncC; t += blockDim.x) {
+            int c = t / ncC, i = t - c * ncC;
+            smc[c * ncC + i] = M[(int64_t)col * ncoef + coef_off[c0 + c] + i];
+        }
+        __syncthreads();
         cd acc[2] = {mk(0, 0), mk(0, 0)};
-        for (int C = child_begin[P]; C < child_end[P]; ++C) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < ncC; i += blockDim.x) smc[i] = M[(int64_t)col * ncoef + coef_off[C] + i];
-            __syncthreads();
-            int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
-            const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];   // index k + hw
-            for (int s = 0; s < 2; ++s) {
-                int idx = threadIdx.x + blockDim.x * s;
-                if (idx >= ncP) break;
-                int nn = idx - pP;
-                cd a = acc[s];
-                for (int mm = -pC; mm <= pC; ++mm) cfma(a, smc[mm + pC], S[nn - mm + hw]);
-                acc[s] = a;
+        if (g < G) {
+            for (int c = g; c < nch; c += G) {
+                const int C = c0 + c;
+                const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
+                const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];
+                const cd* src = smc + c * ncC;
+                for (int s = 0; s < 2; ++s) {
+                    int idx = lt + tpg * s;
+                    if (idx >= ncP) break;
+                    int nn = idx - pP;
+                    cd a = acc[s];
+                    for (int mm = -pC; mm <= pC; ++mm) cfma(a, src[mm + pC], S[nn - mm + hw]);
+                    acc[s] = a;
+                }
             }
         }
-        for (int s = 0; s < 2; ++s) {
-            int idx = threadIdx.x + blockDim.x * s;
-            if (idx < ncP) M[(int64_t)col * ncoef + coef_off[P] + idx] = acc[s];
+        if (G > 1) {
+            for (int s = 0; s < 2; ++s) { int idx = lt + tpg * s; if (g < G && idx < ncP) part[g * ncP + idx] = acc[s]; }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < ncP; idx += blockDim.x) {
+                cd t = part[idx];
+                for (int gg = 1; gg < G; ++gg) t += part[gg * ncP + idx];
+                M[(int64_t)col * ncoef + coef_off[P] + idx] = t;
+            }
+        } else if (g == 0) {   // threads beyond the single group (tpg < 128) hold nothing
+            for (int s = 0; s < 2; ++s) { int idx = lt + tpg * s; if (idx < ncP) M[(int64_t)col * ncoef + coef_off[P] + idx] = acc[s]; }
         }
     }
 }
 
 // M2L into every target box of levels >= l0 (free space and reaction components).
-// One CTA per target box; threads over output coefficients.
-__global__ void k_m2l(int box_first, const int* __restrict__ box_level, const int* __restrict__ p_level,
-                      const int64_t* __restrict__ coef_off, const int* __restrict__ vf_ptr,
-                      const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
+// One CTA (128 threads) per target box.  The source vectors of up to M2L_CH list
+// entries are staged in shared memory per round (reaction entries with the
+// index flip already applied); thread groups of tpg threads (one thread per
+// output coefficient) split the staged entries and are reduced at the end.
+#define M2L_CH 8
+__global__ void __launch_bounds__(128) k_m2l(int box_first, const int* __restrict__ box_level,
+                      const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
+                      const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
                       const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
                       const int* __restrict__ vr_ptr, const int* __restrict__ vr_src,
                       const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
@@ -129,98 +155,138 @@ __global__ void k_m2l(int box_first, const int* __restrict__ box_level, const in
                       const cd* __restrict__ m2lr, int nrhs, int64_t ncoef, const cd* __restrict__ Min,
                       cd* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
                       int64_t nslotcoef, const cd* __restrict__ Mp, cd* __restrict__ Lp) {
-    extern __shared__ cd sms[];   // source coefficients
+    extern __shared__ cd sms[];   // [M2L_CH][nco] staged sources, then [3][G][nco] partial sums
     const int T = box_first + blockIdx.x;
     const int l = box_level[T];
     const int p = p_level[l];
     const int nco = 2 * p + 1;
+    const int tpg = min(128, ((nco + 31) / 32) * 32);
+    const int G = 128 / tpg;
+    const int g = threadIdx.x / tpg, lt = threadIdx.x % tpg;
     const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
+    const int f0 = vf_ptr[T], nf = vf_ptr[T + 1] - f0;
+    const int r0 = vr_ptr[T], nr = vr_ptr[T + 1] - r0;
+    const int ne = nf + nr;
+    cd* part = sms + M2L_CH * nco;
     for (int col = 0; col < nrhs; ++col) {
         const cd* Mc = Min + (int64_t)col * ncoef;
         const cd* Mpc = Mp + (int64_t)col * nslotcoef;
-        cd acc[2] = {mk(0, 0), mk(0, 0)};
-        cd accs[2][2] = {{mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}};   // [side][s]
-        // free space: L_n += sum_m M_m Tab[m - n]
-        for (int e = vf_ptr[T]; e < vf_ptr[T + 1]; ++e) {
+        cd acc[3][2] = {{mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}};   // [L, side 0, side 1][pass]
+        for (int e0 = 0; e0 < ne; e0 += M2L_CH) {
+            const int cnt = min(M2L_CH, ne - e0);
             __syncthreads();
-            const int64_t so = coef_off[vf_src[e]];
-            for (int i = threadIdx.x; i < nco; i += blockDim.x) sms[i] = Mc[so + i];
-            __syncthreads();
-            const cd* tb = m2lf + m2lf_off[vf_tab[e]] + 2 * p;   // index k + 2p
-            for (int s = 0; s < 2; ++s) {
-                int idx = threadIdx.x + blockDim.x * s;
-                if (idx >= nco) break;
-                int nn = idx - p;
-                cd a = acc[s];
-                for (int mm = -p; mm <= p; ++mm) cfma(a, sms[mm + p], tb[mm - nn]);
-                acc[s] = a;
-            }
-        }
-        // reaction components
-        for (int e = vr_ptr[T]; e < vr_ptr[T + 1]; ++e) {
-            __syncthreads();
-            const int S = vr_src[e];
-            const int c = vr_comp[e];
-            const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
-            // source expansion: about the moved centre if S straddles the arrival interface
-            const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
-            const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
-            // alpha_n = M_n (arrival down) or (-1)^n M_{-n} (arrival up)
-            for (int i = threadIdx.x; i < nco; i += blockDim.x) {
-                int nn = i - p;
+            for (int t = threadIdx.x; t < cnt * nco; t += blockDim.x) {
+                const int q = t / nco, i = t - q * nco;
+                const int e = e0 + q;
                 cd v;
-                if (a_dir == 1) v = src[i];
-                else { v = src[-nn + p]; if (nn & 1) v = -v; }
-                sms[i] = v;
+                if (e < nf) {
+                    v = Mc[coef_off[vf_src[f0 + e]] + i];
+                } else {
+                    const int er = r0 + (e - nf);
+                    const int S = vr_src[er], c = vr_comp[er];
+                    const int a_dir = comp[4 * c + 1];
+                    // source expansion about the reaction centre if S straddles the arrival interface
+                    const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
+                    const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
+                    // alpha_n = M_n (arrival down) or (-1)^n M_{-n} (arrival up)
+                    const int nn = i - p;
+                    if (a_dir == 1) v = src[i];
+                    else { v = src[-nn + p]; if (nn & 1) v = -v; }
+                }
+                sms[q * nco + i] = v;
             }
             __syncthreads();
-            const ReactKey rk = rkeys[vr_key[e]];
-            const cd* I = m2lr + rk.off;
-            for (int s = 0; s < 2; ++s) {
-                int idx = threadIdx.x + blockDim.x * s;
-                if (idx >= nco) break;
-                int nout = idx - p;
-                // departure down: L_m += beta_m;  departure up: L_{-m} += (-1)^m beta_m
-                int mrow = (b_dir == 1) ? nout : -nout;
-                const cd* row = I + (int64_t)(mrow + p) * nco;
-                cd bsum = mk(0, 0);
-                for (int i = 0; i < nco; ++i) cfma(bsum, row[i], sms[i]);
-                if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
-                // target expansion about the moved centre if T straddles the departure interface
-                const int side = (b_dir == 0) ? 1 : 0;
-                if (tslot[side] >= 0) accs[side][s] += bsum;
-                else acc[s] += bsum;
+            // threads beyond G * tpg (when tpg does not divide 128) only help staging
+            for (int q = g; g < G && q < cnt; q += G) {
+                const int e = e0 + q;
+                const cd* sv = sms + q * nco;
+                if (e < nf) {
+                    // free space: L_n += sum_m M_m Tab[m - n]
+                    const cd* tb = m2lf + m2lf_off[vf_tab[f0 + e]] + 2 * p;   // index k + 2p
+                    for (int s = 0; s < 2; ++s) {
+                        const int idx = lt + tpg * s;
+                        if (idx >= nco) break;
+                        const int nn = idx - p;
+                        cd a = acc[0][s];
+                        for (int mm = -p; mm <= p; ++mm) cfma(a, sv[mm + p], tb[mm - nn]);
+                        acc[0][s] = a;
+                    }
+                } else {
+                    const int er = r0 + (e - nf);
+                    const int c = vr_comp[er];
+                    const int b_dir = comp[4 * c + 3];
+                    const cd* I = m2lr + rkeys[vr_key[er]].off;
+                    const int side = (b_dir == 0) ? 1 : 0;
+                    const int dst = (tslot[side] >= 0) ? 1 + side : 0;
+                    for (int s = 0; s < 2; ++s) {
+                        const int idx = lt + tpg * s;
+                        if (idx >= nco) break;
+                        const int nout = idx - p;
+                        // departure down: L_m += beta_m;  departure up: L_{-m} += (-1)^m beta_m
+                        const int mrow = (b_dir == 1) ? nout : -nout;
+                        const cd* row = I + (int64_t)(mrow + p) * nco;
+                        cd bsum = mk(0, 0);
+                        for (int i = 0; i < nco; ++i) cfma(bsum, row[i], sv[i]);
+                        if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
+                        acc[dst][s] += bsum;
+                    }
+                }
             }
         }
-        for (int s = 0; s < 2; ++s) {
-            int idx = threadIdx.x + blockDim.x * s;
-            if (idx < nco) {
-                Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[s];
+        // reduce the groups and write L (and the reaction-centre locals of straddling targets)
+        if (G > 1) {
+            __syncthreads();
+            for (int k = 0; k < 3; ++k)
+                for (int s = 0; s < 2; ++s) {
+                    const int idx = lt + tpg * s;
+                    if (idx < nco) part[(k * G + g) * nco + idx] = acc[k][s];
+                }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nco; idx += blockDim.x) {
+                for (int k = 0; k < 3; ++k) {
+                    if (k > 0 && tslot[k - 1] < 0) continue;
+                    cd t = part[(k * G) * nco + idx];
+                    for (int gg = 1; gg < G; ++gg) t += part[(k * G + gg) * nco + idx];
+                    if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
+                    else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
+                }
+            }
+        } else if (g == 0) {
+            for (int s = 0; s < 2; ++s) {
+                const int idx = lt + tpg * s;
+                if (idx >= nco) continue;
+                Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[0][s];
                 for (int side = 0; side < 2; ++side)
-                    if (tslot[side] >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[tslot[side]] + idx] = accs[side][s];
+                    if (tslot[side] >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[tslot[side]] + idx] = acc[1 + side][s];
             }
         }
     }
 }
 
-// L2L for the children at one level: L^C_n += sum_m L^P_m S'^{quad(C)}_{m-n}
-__global__ void k_l2l(int lev_child_start, const int* __restrict__ box_parent, const int* __restrict__ box_ix,
+// L2L from the parents at one level to all their children:
+// L^C_n += sum_m L^P_m S'^{quad(C)}_{m-n}.  One CTA (128 threads) per parent; the
+// parent's coefficients are staged once, threads run over (child, output index).
+__global__ void __launch_bounds__(128) k_l2l(int lev_par_start, const int* __restrict__ child_begin,
+                      const int* __restrict__ child_end, const int* __restrict__ box_ix,
                       const int* __restrict__ box_iy, const int* __restrict__ box_layer,
                       const int64_t* __restrict__ coef_off, int pP, int pC, const cd* __restrict__ tab,
                       const int64_t* __restrict__ tab_off, int lev_child, int nlev, int nrhs, int64_t ncoef,
                       cd* __restrict__ L) {
     extern __shared__ cd smp[];
-    const int C = lev_child_start + blockIdx.x;
-    const int P = box_parent[C];
+    const int P = lev_par_start + blockIdx.x;
     const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
-    const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
-    const cd* S = tab + tab_off[(box_layer[C] * nlev + lev_child) * 4 + quad];
+    const int c0 = child_begin[P], nch = child_end[P] - c0;
+    const int layer = box_layer[P];
     for (int col = 0; col < nrhs; ++col) {
         __syncthreads();
         for (int i = threadIdx.x; i < ncP; i += blockDim.x) smp[i] = L[(int64_t)col * ncoef + coef_off[P] + i];
         __syncthreads();
-        for (int idx = threadIdx.x; idx < ncC; idx += blockDim.x) {
-            int nn = idx - pC;
+        for (int t = threadIdx.x; t < nch * ncC; t += blockDim.x) {
+            const int c = t / ncC, idx = t - c * ncC;
+            const int C = c0 + c;
+            const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
+            const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];
+            const int nn = idx - pC;
             cd a = mk(0, 0);
             for (int mm = -pP; mm <= pP; ++mm) cfma(a, smp[mm + pP], S[mm - nn + hw]);
             L[(int64_t)col * ncoef + coef_off[C] + idx] += a;
