@@ -206,6 +206,9 @@ lfmm_status lfmm_polygon_elements(int32_t n_poly, const int32_t *counts, const d
  * near-field entries, reaction M2L tables, set-up seconds),
  * "stage_times" (double[2*8]: per stage p2m, m2m, m2l, l2l, l2p, near, gather,
  * scatter the number of timed launches and their total milliseconds),
+ * "launch_count" (double[1]: kernels launched so far by this geometry's
+ * matvec path -- gather, P2M, M2M, M2L, L2L, L2P, near field, scatter --
+ * counted on the host as they are enqueued),
  * "p_level" (int32[D+1]), "vfree_ptr"/"vfree_idx", "ufree_ptr"/"ufree_idx",
  * "vreact_ptr"/"vreact_idx"/"vreact_comp", "ureact_ptr"/"ureact_idx"/"ureact_comp"
  * (CSR over boxes), "components" (int32[4*ncomp]: ls, a, lt, b).

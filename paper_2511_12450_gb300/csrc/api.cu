@@ -500,6 +500,10 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
                     (double)g->n_blocks, (double)g->nb_nnz, (double)g->n_rkeys, g->setup_seconds};
             src = dtmp.data();
             bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "launch_count") {
+            dtmp = {(double)g->n_launches};
+            src = dtmp.data();
+            bytes = (int64_t)sizeof(double);
         } else if (nm == "stage_times") {
             for (int k = 0; k < ST_COUNT; ++k) { dtmp.push_back(g->prof.cnt[k]); dtmp.push_back(g->prof.ms[k]); }
             src = dtmp.data();

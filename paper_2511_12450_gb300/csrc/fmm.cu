@@ -126,98 +126,32 @@ void fmm_build(lfmm_geometry_s* g) {
                        slot_coef[q]};
             if (t.box_level[b] == D) { slot_e.push_back(e); slot_leaf_e.push_back(e); }
         }
-        // upward translations into the reaction centres of straddling non-leaf boxes,
-        // one list per (parent level, side)
-        {
-            std::vector<M2MSlot> par;
-            std::vector<M2MChild> chl;
-            std::vector<cd> vecs;
-            g->m2m_slot_start.assign((D + 2) * 2, 0);
-            for (int l = l0; l < D; ++l) {
-                for (int side = 0; side < 2; ++side) {
-                    g->m2m_slot_start[l * 2 + side] = (int)par.size();
-                    for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-                        int sp = slot_of[2 * b + side];
-                        if (sp < 0) continue;
-                        M2MSlot P;
-                        P.pP = t.p_level[l];
-                        P.dst_off = slot_coef[sp];
-                        P.child_begin = (int)chl.size();
-                        for (int c = t.child_begin[b]; c < t.child_end[b]; ++c) {
-                            int sc2 = slot_of[2 * c + side];
-                            M2MChild C;
-                            C.pC = t.p_level[l + 1];
-                            C.src_in_slots = (sc2 >= 0) ? 1 : 0;
-                            C.src_off = (sc2 >= 0) ? slot_coef[sc2] : off[c];
-                            double dx = t.cx(c) - t.cx(b);
-                            double dy = (sc2 >= 0 ? slot_cy[sc2] : t.cy(c)) - slot_cy[sp];
-                            int hw = P.pP + C.pC;
-                            C.vec_off = (int64_t)vecs.size();
-                            std::vector<cd> v(2 * hw + 1);
-                            graf_j_vector(g->m.k[t.box_layer[b]], dx, dy, hw, -1, v.data());
-                            vecs.insert(vecs.end(), v.begin(), v.end());
-                            chl.push_back(C);
-                        }
-                        P.child_end = (int)chl.size();
-                        par.push_back(P);
-                    }
-                }
-            }
-            g->m2m_slot_start[D * 2] = (int)par.size();
-            g->m2m_slot_start[D * 2 + 1] = (int)par.size();
-            g->d_m2m_slots = dupload(g, par);
-            g->d_m2m_children = dupload(g, chl);
-            g->d_m2m_vecs = dupload(g, vecs);
-        }
         g->n_leaf_entries = (int)leaf_e.size();
         g->n_slot_entries = (int)slot_e.size();
         g->n_slot_leaf_entries = (int)slot_leaf_e.size();
         g->d_leaf_entries = dupload(g, leaf_e);
         g->d_slot_entries = dupload(g, slot_e);
         g->d_slot_leaf_entries = dupload(g, slot_leaf_e);
-        // L2L tasks from the reaction centre of a straddling parent to its children
-        // (to the child's reaction centre if it straddles the same interface, else
-        // to its cell centre), one list per (level, side)
-        std::vector<L2LTask> tasks;
-        std::vector<cd> vecs;
-        g->task_start.assign((D + 2) * 2, 0);
-        for (int l = l0 + 1; l <= D; ++l) {
-            for (int side = 0; side < 2; ++side) {
-                g->task_start[l * 2 + side] = (int)tasks.size();
-                for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-                    int P = t.box_parent[b];
-                    int sp = slot_of[2 * P + side];
-                    if (sp < 0) continue;
-                    int sb = slot_of[2 * b + side];
-                    int pP = t.p_level[l - 1], pC = t.p_level[l];
-                    double ux = t.cx(b) - t.cx(P);
-                    double uy = (sb >= 0 ? slot_cy[sb] : t.cy(b)) - slot_cy[sp];
-                    int hw = pP + pC;
-                    L2LTask tk;
-                    tk.pS = pP; tk.pD = pC;
-                    tk.src_off = slot_coef[sp];
-                    tk.src_in_slots = 1;
-                    tk.dst_off = (sb >= 0) ? slot_coef[sb] : off[b];
-                    tk.dst_in_slots = (sb >= 0) ? 1 : 0;
-                    tk.vec_off = (int64_t)vecs.size();
-                    std::vector<cd> v(2 * hw + 1);
-                    graf_j_vector(g->m.k[t.box_layer[b]], ux, uy, hw, +1, v.data());
-                    vecs.insert(vecs.end(), v.begin(), v.end());
-                    tasks.push_back(tk);
-                }
-            }
-        }
-        g->task_start[(D + 1) * 2] = (int)tasks.size();
-        g->task_start[(D + 1) * 2 + 1] = (int)tasks.size();
-        g->n_l2l_tasks = (int)tasks.size();
-        g->d_l2l_tasks = dupload(g, tasks);
-        g->d_l2l_vecs = dupload(g, vecs);
-    }
-
-    // M2M and L2L tables per (layer, child level, quadrant)
-    {
-        std::vector<int64_t> toff(nl * nlev * 4, -1);
-        std::vector<cd> m2m, l2l;
+        // Upward (M2M) and downward (L2L) passes.  Each level's pass is a list of
+        // destination vectors (cell centres and reaction centres alike), each with
+        // its sources and one translation vector per source:
+        //   dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
+        // M2M uses V_k = J_k(k|d|) e^{-i k theta_d} (d = source centre - destination
+        // centre); L2L uses J_k(k|u|) e^{+i k theta_u} (u = destination - source)
+        // stored reversed, so both passes index n - m.
+        std::vector<cd> xvec;
+        std::vector<XDst> xd;
+        std::vector<XSrc> xs;
+        auto put_vec = [&](double k, double dx, double dy, int hw, int sign, bool reverse) -> int64_t {
+            std::vector<cd> v(2 * hw + 1);
+            graf_j_vector(k, dx, dy, hw, sign, v.data());
+            if (reverse) std::reverse(v.begin(), v.end());
+            int64_t o = (int64_t)xvec.size();
+            xvec.insert(xvec.end(), v.begin(), v.end());
+            return o;
+        };
+        // cell-to-cell vectors, shared per (layer, child level, quadrant of the child)
+        std::vector<int64_t> up_tab(nl * nlev * 4, -1), dn_tab(nl * nlev * 4, -1);
         for (int lay = 0; lay < nl; ++lay)
             for (int l = l0 + 1; l <= D; ++l) {
                 int hw = t.p_level[l - 1] + t.p_level[l];
@@ -225,19 +159,77 @@ void fmm_build(lfmm_geometry_s* g) {
                 for (int quad = 0; quad < 4; ++quad) {
                     double dx = (quad & 1) ? 0.5 * w : -0.5 * w;
                     double dy = (quad & 2) ? 0.5 * w : -0.5 * w;
-                    toff[(lay * nlev + l) * 4 + quad] = (int64_t)m2m.size();
-                    std::vector<cd> v(2 * hw + 1);
-                    graf_j_vector(g->m.k[lay], dx, dy, hw, -1, v.data());   // J_k e^{-i k theta_d}
-                    m2m.insert(m2m.end(), v.begin(), v.end());
-                    graf_j_vector(g->m.k[lay], dx, dy, hw, +1, v.data());   // J_k e^{+i k theta_u}
-                    l2l.insert(l2l.end(), v.begin(), v.end());
+                    up_tab[(lay * nlev + l) * 4 + quad] = put_vec(g->m.k[lay], dx, dy, hw, -1, false);
+                    dn_tab[(lay * nlev + l) * 4 + quad] = put_vec(g->m.k[lay], dx, dy, hw, +1, true);
                 }
             }
-        g->d_m2m = dupload(g, m2m);
-        g->d_l2l = dupload(g, l2l);
-        g->d_m2m_off = dupload(g, toff);
-        g->d_l2l_off = g->d_m2m_off;
+        auto quad_of = [&](int c) { return (t.box_ix[c] & 1) | ((t.box_iy[c] & 1) << 1); };
+        auto slot_y = [&](int b, int sl) { return sl >= 0 ? slot_cy[sl] : t.cy(b); };
+        g->up_begin.assign(nlev + 1, 0); g->up_end.assign(nlev + 1, 0);
+        g->dn_begin.assign(nlev + 1, 0); g->dn_end.assign(nlev + 1, 0);
+        for (int lp = D - 1; lp >= l0; --lp) {   // M2M into parents at level lp
+            const int pP = t.p_level[lp], pC = t.p_level[lp + 1], hw = pP + pC;
+            g->up_begin[lp] = (int)xd.size();
+            for (int b = t.level_start[lp]; b < t.level_start[lp + 1]; ++b) {
+                XDst d{off[b], pP, 0, (int)xs.size(), 0};
+                for (int c = t.child_begin[b]; c < t.child_end[b]; ++c)
+                    xs.push_back(XSrc{off[c], up_tab[(t.box_layer[b] * nlev + lp + 1) * 4 + quad_of(c)], pC, 0});
+                d.src_end = (int)xs.size();
+                xd.push_back(d);
+            }
+            for (int side = 0; side < 2; ++side)
+                for (int b = t.level_start[lp]; b < t.level_start[lp + 1]; ++b) {
+                    const int sp = slot_of[2 * b + side];
+                    if (sp < 0) continue;
+                    XDst d{slot_coef[sp], pP, 1, (int)xs.size(), 0};
+                    for (int c = t.child_begin[b]; c < t.child_end[b]; ++c) {
+                        const int sc2 = slot_of[2 * c + side];
+                        const int64_t v = put_vec(g->m.k[t.box_layer[b]], t.cx(c) - t.cx(b), slot_y(c, sc2) - slot_cy[sp],
+                                                  hw, -1, false);
+                        xs.push_back(XSrc{sc2 >= 0 ? slot_coef[sc2] : off[c], v, pC, sc2 >= 0 ? 1 : 0});
+                    }
+                    d.src_end = (int)xs.size();
+                    xd.push_back(d);
+                }
+            g->up_end[lp] = (int)xd.size();
+        }
+        for (int l = l0 + 1; l <= D; ++l) {   // L2L into children at level l
+            const int pP = t.p_level[l - 1], pC = t.p_level[l], hw = pP + pC;
+            g->dn_begin[l] = (int)xd.size();
+            for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
+                const int P = t.box_parent[b];
+                XDst d{off[b], pC, 0, (int)xs.size(), 0};
+                xs.push_back(XSrc{off[P], dn_tab[(t.box_layer[b] * nlev + l) * 4 + quad_of(b)], pP, 0});
+                for (int side = 0; side < 2; ++side) {   // reaction locals of a straddling parent
+                    const int sp = slot_of[2 * P + side];
+                    if (sp < 0 || slot_of[2 * b + side] >= 0) continue;
+                    const int64_t v = put_vec(g->m.k[t.box_layer[b]], t.cx(b) - t.cx(P), t.cy(b) - slot_cy[sp], hw, +1, true);
+                    xs.push_back(XSrc{slot_coef[sp], v, pP, 1});
+                }
+                d.src_end = (int)xs.size();
+                xd.push_back(d);
+            }
+            for (int side = 0; side < 2; ++side)
+                for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
+                    const int sb = slot_of[2 * b + side];
+                    if (sb < 0) continue;
+                    const int P = t.box_parent[b];
+                    const int sp = slot_of[2 * P + side];
+                    // a cell that contains the interface lies in a parent that contains it too
+                    if (sp < 0) throw CudaError{"internal: straddling cell under a non-straddling parent"};
+                    XDst d{slot_coef[sb], pC, 1, (int)xs.size(), 0};
+                    const int64_t v = put_vec(g->m.k[t.box_layer[b]], t.cx(b) - t.cx(P), slot_cy[sb] - slot_cy[sp], hw, +1, true);
+                    xs.push_back(XSrc{slot_coef[sp], v, pP, 1});
+                    d.src_end = (int)xs.size();
+                    xd.push_back(d);
+                }
+            g->dn_end[l] = (int)xd.size();
+        }
+        g->d_xdst = dupload(g, xd);
+        g->d_xsrc = dupload(g, xs);
+        g->d_xvec = dupload(g, xvec);
     }
+
     // free-space M2L tables per (layer, level, offset) and the V lists with table ids
     {
         std::vector<int> tl, tlev, tdx, tdy, tp;
@@ -388,33 +380,25 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         k_p2m<<<g->n_leaf_entries, 128, smem, s>>>(g->d_leaf_entries, g->m, g->d_x, g->d_y, g->d_w, x_sorted, g->n,
                                                    nrhs, g->ncoef, g->d_M);
         cuda_check(cudaGetLastError(), "k_p2m");
+        ++g->n_launches;
         if (g->n_slot_entries > 0) {
             size_t sm2 = (size_t)(32 * (pmax + 1)) * sizeof(double) + (size_t)(32 * (pmax + 1) + 32) * sizeof(cd);
             k_p2m<<<g->n_slot_entries, 128, sm2, s>>>(g->d_slot_entries, g->m, g->d_x, g->d_y, g->d_w, x_sorted,
                                                       g->n, nrhs, g->nslotcoef, g->d_Mp);
             cuda_check(cudaGetLastError(), "k_p2m slots");
+            ++g->n_launches;
         }
         prof_end(g, ST_P2M, s);
     }
     prof_begin(g, ST_M2M, s);
-    for (int l = D; l > l0; --l) {   // M2M: children at l -> parents at l-1
-        int npar = t.level_start[l] - t.level_start[l - 1];
-        int pC = t.p_level[l];
-        size_t smem = (size_t)(4 * (2 * pC + 1) + 4 * (2 * t.p_level[l - 1] + 1)) * sizeof(cd);
-        k_m2m<<<npar, 128, smem, s>>>(t.level_start[l - 1], g->d_child_begin, g->d_child_end, g->d_box_ix,
-                                      g->d_box_iy, g->d_box_layer, g->d_coef_off, t.p_level[l - 1], pC, g->d_m2m,
-                                      g->d_m2m_off, l, nlev, nrhs, g->ncoef, g->d_M);
-        cuda_check(cudaGetLastError(), "k_m2m");
-        for (int side = 0; side < 2; ++side) {   // reaction centres of straddling parents at l-1
-            int a0 = g->m2m_slot_start[(l - 1) * 2 + side];
-            int a1 = (side == 0) ? g->m2m_slot_start[(l - 1) * 2 + 1] : g->m2m_slot_start[l * 2];
-            if (a1 > a0) {
-                k_m2m_slots<<<a1 - a0, 128, (size_t)(2 * pmax + 1) * sizeof(cd), s>>>(
-                    g->d_m2m_slots + a0, g->d_m2m_children, g->d_m2m_vecs, nrhs, g->ncoef, g->nslotcoef, g->d_M,
-                    g->d_Mp);
-                cuda_check(cudaGetLastError(), "k_m2m_slots");
-            }
-        }
+    for (int lp = D - 1; lp >= l0; --lp) {   // M2M: children at lp + 1 -> parents (cells and reaction centres) at lp
+        const int nd = g->up_end[lp] - g->up_begin[lp];
+        if (nd == 0) continue;
+        dim3 grid(nd, (2 * t.p_level[lp] + 1 + XT_W - 1) / XT_W);
+        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, nrhs, g->ncoef,
+                                         g->nslotcoef, g->d_M, g->d_Mp);
+        cuda_check(cudaGetLastError(), "k_translate (M2M)");
+        ++g->n_launches;
     }
     prof_end(g, ST_M2M, s);
     {   // M2L, all levels
@@ -427,26 +411,18 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
                                      g->d_vr_comp, g->d_comp, g->d_rkeys, g->d_m2lr, nrhs, g->ncoef, g->d_M,
                                      g->d_L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, g->d_Mp, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_m2l");
+        ++g->n_launches;
         prof_end(g, ST_M2L, s);
     }
     prof_begin(g, ST_L2L, s);
-    for (int l = l0 + 1; l <= D; ++l) {   // L2L: parents at l-1 -> children at l
-        int npar = t.level_start[l] - t.level_start[l - 1];
-        int pP = t.p_level[l - 1];
-        size_t smem = (size_t)(2 * pP + 1) * sizeof(cd);
-        k_l2l<<<npar, 128, smem, s>>>(t.level_start[l - 1], g->d_child_begin, g->d_child_end, g->d_box_ix, g->d_box_iy, g->d_box_layer,
-                                     g->d_coef_off, pP, t.p_level[l], g->d_l2l, g->d_l2l_off, l, nlev, nrhs,
-                                     g->ncoef, g->d_L);
-        cuda_check(cudaGetLastError(), "k_l2l");
-        for (int side = 0; side < 2; ++side) {
-            int t0 = g->task_start[l * 2 + side];
-            int t1 = (side == 0) ? g->task_start[l * 2 + 1] : g->task_start[(l + 1) * 2];
-            if (t1 > t0) {
-                k_l2l_tasks<<<t1 - t0, 128, (size_t)(2 * pmax + 1) * sizeof(cd), s>>>(
-                    g->d_l2l_tasks + t0, g->d_l2l_vecs, nrhs, g->ncoef, g->nslotcoef, g->d_L, g->d_Lp);
-                cuda_check(cudaGetLastError(), "k_l2l_tasks");
-            }
-        }
+    for (int l = l0 + 1; l <= D; ++l) {   // L2L: parents at l - 1 -> children (cells and reaction centres) at l
+        const int nd = g->dn_end[l] - g->dn_begin[l];
+        if (nd == 0) continue;
+        dim3 grid(nd, (2 * t.p_level[l] + 1 + XT_W - 1) / XT_W);
+        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, nrhs, g->ncoef,
+                                         g->nslotcoef, g->d_L, g->d_Lp);
+        cuda_check(cudaGetLastError(), "k_translate (L2L)");
+        ++g->n_launches;
     }
     prof_end(g, ST_L2L, s);
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
@@ -456,10 +432,12 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         k_l2p<<<g->n_leaf_entries, threads, smem, s>>>(g->d_leaf_entries, g->m, g->d_x, g->d_y, g->n, nrhs, g->ncoef,
                                                        g->d_L, y_sorted);
         cuda_check(cudaGetLastError(), "k_l2p");
+        ++g->n_launches;
         if (g->n_slot_leaf_entries > 0) {
             k_l2p<<<g->n_slot_leaf_entries, threads, smem, s>>>(g->d_slot_leaf_entries, g->m, g->d_x, g->d_y, g->n,
                                                                 nrhs, g->nslotcoef, g->d_Lp, y_sorted);
             cuda_check(cudaGetLastError(), "k_l2p slots");
+            ++g->n_launches;
         }
         prof_end(g, ST_L2P, s);
     }

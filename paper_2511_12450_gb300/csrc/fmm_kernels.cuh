@@ -83,62 +83,6 @@ __global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const doubl
     }
 }
 
-// M2M for the parents at one level: M^P_n = sum_C sum_m M^C_m S^{quad(C)}_{n-m}.
-// One CTA (128 threads) per parent; all children's coefficients are staged in
-// shared memory at once; thread groups split the children and are reduced at the end.
-__global__ void __launch_bounds__(128) k_m2m(int lev_par_start, const int* __restrict__ child_begin,
-                      const int* __restrict__ child_end, const int* __restrict__ box_ix,
-                      const int* __restrict__ box_iy, const int* __restrict__ box_layer,
-                      const int64_t* __restrict__ coef_off, int pP, int pC, const cd* __restrict__ tab,
-                      const int64_t* __restrict__ tab_off, int lev_child, int nlev, int nrhs, int64_t ncoef,
-                      cd* __restrict__ M) {
-    extern __shared__ cd smc[];  // [4][ncC] children, then [G][ncP] partial sums
-    const int P = lev_par_start + blockIdx.x;
-    const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
-    const int layer = box_layer[P];
-    const int c0 = child_begin[P], nch = child_end[P] - c0;
-    const int tpg = min(128, ((ncP + 31) / 32) * 32);
-    const int G = 128 / tpg;
-    const int g = threadIdx.x / tpg, lt = threadIdx.x % tpg;
-    cd* part = smc + 4 * ncC;
-    for (int col = 0; col < nrhs; ++col) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < nch * ncC; t += blockDim.x) {
-            int c = t / ncC, i = t - c * ncC;
-            smc[c * ncC + i] = M[(int64_t)col * ncoef + coef_off[c0 + c] + i];
-        }
-        __syncthreads();
-        cd acc[2] = {mk(0, 0), mk(0, 0)};
-        if (g < G) {
-            for (int c = g; c < nch; c += G) {
-                const int C = c0 + c;
-                const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
-                const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];
-                const cd* src = smc + c * ncC;
-                for (int s = 0; s < 2; ++s) {
-                    int idx = lt + tpg * s;
-                    if (idx >= ncP) break;
-                    int nn = idx - pP;
-                    cd a = acc[s];
-                    for (int mm = -pC; mm <= pC; ++mm) cfma(a, src[mm + pC], S[nn - mm + hw]);
-                    acc[s] = a;
-                }
-            }
-        }
-        if (G > 1) {
-            for (int s = 0; s < 2; ++s) { int idx = lt + tpg * s; if (g < G && idx < ncP) part[g * ncP + idx] = acc[s]; }
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < ncP; idx += blockDim.x) {
-                cd t = part[idx];
-                for (int gg = 1; gg < G; ++gg) t += part[gg * ncP + idx];
-                M[(int64_t)col * ncoef + coef_off[P] + idx] = t;
-            }
-        } else if (g == 0) {   // threads beyond the single group (tpg < 128) hold nothing
-            for (int s = 0; s < 2; ++s) { int idx = lt + tpg * s; if (idx < ncP) M[(int64_t)col * ncoef + coef_off[P] + idx] = acc[s]; }
-        }
-    }
-}
-
 // M2L into every target box of levels >= l0 (free space and reaction components).
 // One CTA (128 threads) per target box.  The source vectors of up to M2L_CH list
 // entries are staged in shared memory per round (reaction entries with the
@@ -263,37 +207,6 @@ __global__ void __launch_bounds__(128) k_m2l(int box_first, const int* __restric
     }
 }
 
-// L2L from the parents at one level to all their children:
-// L^C_n += sum_m L^P_m S'^{quad(C)}_{m-n}.  One CTA (128 threads) per parent; the
-// parent's coefficients are staged once, threads run over (child, output index).
-__global__ void __launch_bounds__(128) k_l2l(int lev_par_start, const int* __restrict__ child_begin,
-                      const int* __restrict__ child_end, const int* __restrict__ box_ix,
-                      const int* __restrict__ box_iy, const int* __restrict__ box_layer,
-                      const int64_t* __restrict__ coef_off, int pP, int pC, const cd* __restrict__ tab,
-                      const int64_t* __restrict__ tab_off, int lev_child, int nlev, int nrhs, int64_t ncoef,
-                      cd* __restrict__ L) {
-    extern __shared__ cd smp[];
-    const int P = lev_par_start + blockIdx.x;
-    const int ncP = 2 * pP + 1, ncC = 2 * pC + 1, hw = pP + pC;
-    const int c0 = child_begin[P], nch = child_end[P] - c0;
-    const int layer = box_layer[P];
-    for (int col = 0; col < nrhs; ++col) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < ncP; i += blockDim.x) smp[i] = L[(int64_t)col * ncoef + coef_off[P] + i];
-        __syncthreads();
-        for (int t = threadIdx.x; t < nch * ncC; t += blockDim.x) {
-            const int c = t / ncC, idx = t - c * ncC;
-            const int C = c0 + c;
-            const int quad = (box_ix[C] & 1) | ((box_iy[C] & 1) << 1);
-            const cd* S = tab + tab_off[(layer * nlev + lev_child) * 4 + quad];
-            const int nn = idx - pC;
-            cd a = mk(0, 0);
-            for (int mm = -pP; mm <= pP; ++mm) cfma(a, smp[mm + pP], S[mm - nn + hw]);
-            L[(int64_t)col * ncoef + coef_off[C] + idx] += a;
-        }
-    }
-}
-
 // L2P over a list of point ranges: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
 // about (cx, cy).  Leaves (cell centres) and straddling leaves (reaction centres).
 __global__ void k_l2p(const ExpEntry* __restrict__ ent, MediumDev m, const double* __restrict__ px,
@@ -336,81 +249,58 @@ __global__ void k_l2p(const ExpEntry* __restrict__ ent, MediumDev m, const doubl
     }
 }
 
-// Multipoles about the reaction centres of straddling parents from their
-// children (reaction centre of a straddling child, else its cell centre):
-// dst_n = sum_children sum_m src_m S_{n-m}, S_k = J_k(k |d|) e^{-i k theta_d},
-// d = (child centre) - (parent reaction centre).  One CTA per parent slot.
-struct M2MChild {
-    int pC;
-    int src_in_slots;
-    int64_t src_off, vec_off;
+// Multipole-to-multipole and local-to-local translations (Graf's addition
+// theorem) into the destinations of one level: cell centres and reaction
+// centres of straddling cells alike, each with its own list of sources:
+//   dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
+// A CTA of 128 threads owns XT_W consecutive output indices of one
+// destination (one per lane of a 16-lane row) and 8 slices of the sum over
+// m; the slices are reduced in a fixed order, so results are reproducible.
+// Spreading a destination over several CTAs keeps the coarse levels (few
+// boxes, orders up to 2p+1 ~ 115) from running on a handful of SMs.
+struct XDst {
+    int64_t off;          // coefficient offset of the destination
+    int p;                // its order
+    int in_slots;         // 1: the destination lives in the reaction-centre arrays
+    int src_begin, src_end;
 };
-struct M2MSlot {
-    int pP;
-    int child_begin, child_end;   // range in the M2MChild array
-    int64_t dst_off;              // slot coefficient offset
+struct XSrc {
+    int64_t off;          // coefficient offset of the source
+    int64_t vec_off;      // translation vector V (2 (pS + pD) + 1 entries)
+    int p;                // source order
+    int in_slots;
 };
-
-__global__ void k_m2m_slots(const M2MSlot* __restrict__ par, const M2MChild* __restrict__ ch,
-                            const cd* __restrict__ vec, int nrhs, int64_t ncoef, int64_t nslotcoef,
-                            const cd* __restrict__ M, cd* __restrict__ Mp) {
-    extern __shared__ cd smk[];
-    const M2MSlot P = par[blockIdx.x];
-    const int ncP = 2 * P.pP + 1;
+#define XT_W 16
+__global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
+                                                   const cd* __restrict__ vec, int accumulate, int nrhs,
+                                                   int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
+    __shared__ cd red[128 / XT_W][XT_W];
+    const XDst d = dsts[blockIdx.x];
+    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
+    const int idx = blockIdx.y * XT_W + lane;
+    const int ncD = 2 * d.p + 1;
     for (int col = 0; col < nrhs; ++col) {
-        cd acc[2] = {mk(0, 0), mk(0, 0)};
-        for (int c = P.child_begin; c < P.child_end; ++c) {
-            const M2MChild C = ch[c];
-            const int ncC = 2 * C.pC + 1, hw = P.pP + C.pC;
-            const cd* src = C.src_in_slots ? (Mp + (int64_t)col * nslotcoef + C.src_off) : (M + (int64_t)col * ncoef + C.src_off);
-            __syncthreads();
-            for (int i = threadIdx.x; i < ncC; i += blockDim.x) smk[i] = src[i];
-            __syncthreads();
-            const cd* S = vec + C.vec_off;
-            for (int s = 0; s < 2; ++s) {
-                int idx = threadIdx.x + blockDim.x * s;
-                if (idx >= ncP) break;
-                int nn = idx - P.pP;
-                cd a = acc[s];
-                for (int mm = -C.pC; mm <= C.pC; ++mm) cfma(a, smk[mm + C.pC], S[nn - mm + hw]);
-                acc[s] = a;
+        cd a = mk(0, 0);
+        if (idx < ncD) {
+            for (int j = d.src_begin; j < d.src_end; ++j) {
+                const XSrc sr = srcs[j];
+                const cd* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
+                // V[n - m + hw] with n = idx - pD, m = mi - pS, hw = pS + pD
+                const cd* Vb = vec + sr.vec_off + idx + 2 * sr.p;
+                const int ncS = 2 * sr.p + 1;
+                for (int mi = sl; mi < ncS; mi += 128 / XT_W) cfma(a, src[mi], Vb[-mi]);
             }
         }
-        for (int s = 0; s < 2; ++s) {
-            int idx = threadIdx.x + blockDim.x * s;
-            if (idx < ncP) Mp[(int64_t)col * nslotcoef + P.dst_off + idx] = acc[s];
-        }
-    }
-}
-
-// Local-to-local translations with per-task vectors (reaction centres of
-// straddling cells): dst_n += sum_m src_m S_{m-n}, S_k = J_k(k |u|) e^{i k theta_u},
-// u = (destination centre) - (source centre).  Tasks of one level per launch;
-// no two tasks of a launch share a destination.
-struct L2LTask {
-    int pS, pD;
-    int64_t src_off, dst_off, vec_off;
-    int src_in_slots, dst_in_slots;   // 1: the coefficient lives in the slot arrays
-};
-
-__global__ void k_l2l_tasks(const L2LTask* __restrict__ tasks, const cd* __restrict__ vec, int nrhs,
-                            int64_t ncoef, int64_t nslotcoef, cd* __restrict__ L, cd* __restrict__ Lp) {
-    extern __shared__ cd stk[];
-    const L2LTask tk = tasks[blockIdx.x];
-    const int ncS = 2 * tk.pS + 1, ncD = 2 * tk.pD + 1, hw = tk.pS + tk.pD;
-    const cd* S = vec + tk.vec_off;
-    for (int col = 0; col < nrhs; ++col) {
-        const cd* src = tk.src_in_slots ? (Lp + (int64_t)col * nslotcoef + tk.src_off) : (L + (int64_t)col * ncoef + tk.src_off);
-        cd* dst = tk.dst_in_slots ? (Lp + (int64_t)col * nslotcoef + tk.dst_off) : (L + (int64_t)col * ncoef + tk.dst_off);
+        red[sl][lane] = a;
         __syncthreads();
-        for (int i = threadIdx.x; i < ncS; i += blockDim.x) stk[i] = src[i];
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < ncD; idx += blockDim.x) {
-            int nn = idx - tk.pD;
-            cd a = mk(0, 0);
-            for (int mm = -tk.pS; mm <= tk.pS; ++mm) cfma(a, stk[mm + tk.pS], S[mm - nn + hw]);
-            dst[idx] += a;
+        if (sl == 0 && idx < ncD) {
+            cd t = red[0][lane];
+            for (int q = 1; q < 128 / XT_W; ++q) t += red[q][lane];
+            cd* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
+            if (accumulate) *dst += t;
+            else *dst = t;
         }
+        __syncthreads();
     }
 }
 

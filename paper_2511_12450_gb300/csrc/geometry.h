@@ -40,9 +40,8 @@ struct QuadRule {
 };
 
 struct ExpEntry;
-struct L2LTask;
-struct M2MSlot;
-struct M2MChild;
+struct XDst;
+struct XSrc;
 
 // reaction M2L table key (built on the host, evaluated on the device)
 struct ReactKey {
@@ -66,6 +65,7 @@ struct StageProfiler {
 
 struct lfmm_geometry_s {
     lfmm::StageProfiler prof;
+    int64_t n_launches = 0;           // kernels this geometry's matvec path has launched (host count)
     lfmm_medium_s* med = nullptr;
     MediumDev m;
     int64_t n = 0;
@@ -97,16 +97,12 @@ struct lfmm_geometry_s {
     // P2M/L2P work lists (leaves about cell centres; straddling boxes/leaves about reaction centres)
     int n_leaf_entries = 0, n_slot_entries = 0, n_slot_leaf_entries = 0;
     lfmm::ExpEntry *d_leaf_entries = nullptr, *d_slot_entries = nullptr, *d_slot_leaf_entries = nullptr;
-    // multipole translations into reaction centres of straddling parents, per (level, side)
-    std::vector<int> m2m_slot_start;
-    lfmm::M2MSlot* d_m2m_slots = nullptr;
-    lfmm::M2MChild* d_m2m_children = nullptr;
-    cd* d_m2m_vecs = nullptr;
-    // local translations out of reaction centres, per (level, side)
-    std::vector<int> task_start;
-    int n_l2l_tasks = 0;
-    lfmm::L2LTask* d_l2l_tasks = nullptr;
-    cd* d_l2l_vecs = nullptr;
+    // M2M (up) and L2L (down) passes: per level, a range of destinations
+    // (cells and reaction centres) with their sources and translation vectors
+    std::vector<int> up_begin, up_end, dn_begin, dn_end;
+    lfmm::XDst* d_xdst = nullptr;
+    lfmm::XSrc* d_xsrc = nullptr;
+    cd* d_xvec = nullptr;
     // near field: block-sparse rows over target leaves
     int *d_nb_ptr = nullptr;          // nleaf + 1
     int *d_nb_src = nullptr;          // source leaf (box id) per block
@@ -116,10 +112,6 @@ struct lfmm_geometry_s {
     int n_blocks = 0;
     // translation tables
     int *d_p_level = nullptr;
-    cd *d_m2m = nullptr;              // per (layer, level, quadrant): Toeplitz vectors
-    int64_t *d_m2m_off = nullptr;
-    cd *d_l2l = nullptr;
-    int64_t *d_l2l_off = nullptr;
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
     int64_t *d_m2lf_off = nullptr;
     int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids

@@ -210,6 +210,7 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
     k_near_apply<<<g->nleaf, 128, 0, s>>>(g->d_nb_ptr, g->d_nb_src, g->d_nb_off, g->d_nb_val, g->d_box_begin,
                                           g->d_box_end, g->leaf0, x_sorted, y_sorted, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_near_apply");
+    ++g->n_launches;
     prof_end(g, ST_NEAR, s);
 }
 

@@ -34,11 +34,13 @@ void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, c
     int64_t tot = g->n * nrhs;
     k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, x_in, x_sorted, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_gather");
+    ++g->n_launches;
 }
 void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s) {
     int64_t tot = g->n * nrhs;
     k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, y_sorted, y_out, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_scatter");
+    ++g->n_launches;
 }
 
 void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
