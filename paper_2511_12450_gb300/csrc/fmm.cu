@@ -266,6 +266,14 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_vf_ptr = dupload(g, vf_ptr);
         g->d_vf_src = dupload(g, vf_src);
         g->d_vf_tab = dupload(g, vf_tab);
+        // M2L work items (target box, chunk of output indices), coarse levels first
+        std::vector<M2LItem> items;
+        for (int T = t.level_start[l0]; T < t.nbox; ++T) {
+            const int nco = 2 * t.p_level[t.box_level[T]] + 1;
+            for (int c = 0; c * XT_W < nco; ++c) items.push_back(M2LItem{T, c});
+        }
+        g->n_m2l_items = (int)items.size();
+        g->d_m2l_items = dupload(g, items);
         int ntab = (int)tl.size();
         if (ntab > 0) {
             int* d_tl = dupload(g, tl); int* d_tlev = dupload(g, tlev);
@@ -403,10 +411,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     prof_end(g, ST_M2M, s);
     {   // M2L, all levels
         prof_begin(g, ST_M2L, s);
-        int first = t.level_start[l0];
-        int nbx = t.level_start[D + 1] - first;
-        size_t smem = (size_t)(M2L_CH * (2 * pmax + 1) + 3 * 4 * (2 * pmax + 1)) * sizeof(cd);
-        k_m2l<<<nbx, 128, smem, s>>>(first, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
+        k_m2l<<<g->n_m2l_items, 128, 0, s>>>(g->d_m2l_items, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
                                      g->d_vf_tab, g->d_m2lf, g->d_m2lf_off, g->d_vr_ptr, g->d_vr_src, g->d_vr_key,
                                      g->d_vr_comp, g->d_comp, g->d_rkeys, g->d_m2lr, nrhs, g->ncoef, g->d_M,
                                      g->d_L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, g->d_Mp, g->d_Lp);

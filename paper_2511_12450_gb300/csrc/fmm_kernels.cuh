@@ -84,12 +84,18 @@ __global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const doubl
 }
 
 // M2L into every target box of levels >= l0 (free space and reaction components).
-// One CTA (128 threads) per target box.  The source vectors of up to M2L_CH list
-// entries are staged in shared memory per round (reaction entries with the
-// index flip already applied); thread groups of tpg threads (one thread per
-// output coefficient) split the staged entries and are reduced at the end.
-#define M2L_CH 8
-__global__ void __launch_bounds__(128) k_m2l(int box_first, const int* __restrict__ box_level,
+// Work item = (target box, chunk of XT_W output indices); a CTA of 128 threads
+// holds XT_W output lanes x 8 slices of the sum over the source index, for
+// every list entry of the target in turn, and reduces the slices in a fixed
+// order at the end.  Free space (Graf): L_n += sum_m M_m T[m - n].  Reaction
+// (eq. generalintegral): beta_m = sum_n I[m][n] alpha_n with the arrival and
+// departure index flips; tables are stored column-major (entry (m, n) at
+// n (2p+1) + m) so the lanes of a row read consecutive addresses.
+#define XT_W 16
+struct M2LItem {
+    int box, chunk;
+};
+__global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const int* __restrict__ box_level,
                       const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
                       const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
                       const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
@@ -99,111 +105,69 @@ __global__ void __launch_bounds__(128) k_m2l(int box_first, const int* __restric
                       const cd* __restrict__ m2lr, int nrhs, int64_t ncoef, const cd* __restrict__ Min,
                       cd* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
                       int64_t nslotcoef, const cd* __restrict__ Mp, cd* __restrict__ Lp) {
-    extern __shared__ cd sms[];   // [M2L_CH][nco] staged sources, then [3][G][nco] partial sums
-    const int T = box_first + blockIdx.x;
-    const int l = box_level[T];
-    const int p = p_level[l];
+    constexpr int NS = 128 / XT_W;
+    __shared__ cd red[3][NS][XT_W];
+    const M2LItem it = items[blockIdx.x];
+    const int T = it.box;
+    const int p = p_level[box_level[T]];
     const int nco = 2 * p + 1;
-    const int tpg = min(128, ((nco + 31) / 32) * 32);
-    const int G = 128 / tpg;
-    const int g = threadIdx.x / tpg, lt = threadIdx.x % tpg;
+    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
+    const int idx = it.chunk * XT_W + lane;
+    const bool live = idx < nco;
+    const int nn = idx - p;
     const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
-    const int f0 = vf_ptr[T], nf = vf_ptr[T + 1] - f0;
-    const int r0 = vr_ptr[T], nr = vr_ptr[T + 1] - r0;
-    const int ne = nf + nr;
-    cd* part = sms + M2L_CH * nco;
+    const int f0 = vf_ptr[T], f1 = vf_ptr[T + 1];
+    const int r0 = vr_ptr[T], r1 = vr_ptr[T + 1];
     for (int col = 0; col < nrhs; ++col) {
         const cd* Mc = Min + (int64_t)col * ncoef;
         const cd* Mpc = Mp + (int64_t)col * nslotcoef;
-        cd acc[3][2] = {{mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}, {mk(0, 0), mk(0, 0)}};   // [L, side 0, side 1][pass]
-        for (int e0 = 0; e0 < ne; e0 += M2L_CH) {
-            const int cnt = min(M2L_CH, ne - e0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < cnt * nco; t += blockDim.x) {
-                const int q = t / nco, i = t - q * nco;
-                const int e = e0 + q;
-                cd v;
-                if (e < nf) {
-                    v = Mc[coef_off[vf_src[f0 + e]] + i];
-                } else {
-                    const int er = r0 + (e - nf);
-                    const int S = vr_src[er], c = vr_comp[er];
-                    const int a_dir = comp[4 * c + 1];
-                    // source expansion about the reaction centre if S straddles the arrival interface
-                    const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
-                    const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
-                    // alpha_n = M_n (arrival down) or (-1)^n M_{-n} (arrival up)
-                    const int nn = i - p;
-                    if (a_dir == 1) v = src[i];
-                    else { v = src[-nn + p]; if (nn & 1) v = -v; }
-                }
-                sms[q * nco + i] = v;
+        cd acc0 = mk(0, 0), acc1 = mk(0, 0), acc2 = mk(0, 0);   // L, side-0 slot, side-1 slot
+        if (live) {
+            for (int e = f0; e < f1; ++e) {
+                const cd* src = Mc + coef_off[vf_src[e]];
+                const cd* tb = m2lf + m2lf_off[vf_tab[e]] + p - nn;   // T[m - n], index (mi - p) - nn + 2p
+                for (int mi = sl; mi < nco; mi += NS) cfma(acc0, src[mi], tb[mi]);
             }
-            __syncthreads();
-            // threads beyond G * tpg (when tpg does not divide 128) only help staging
-            for (int q = g; g < G && q < cnt; q += G) {
-                const int e = e0 + q;
-                const cd* sv = sms + q * nco;
-                if (e < nf) {
-                    // free space: L_n += sum_m M_m Tab[m - n]
-                    const cd* tb = m2lf + m2lf_off[vf_tab[f0 + e]] + 2 * p;   // index k + 2p
-                    for (int s = 0; s < 2; ++s) {
-                        const int idx = lt + tpg * s;
-                        if (idx >= nco) break;
-                        const int nn = idx - p;
-                        cd a = acc[0][s];
-                        for (int mm = -p; mm <= p; ++mm) cfma(a, sv[mm + p], tb[mm - nn]);
-                        acc[0][s] = a;
-                    }
-                } else {
-                    const int er = r0 + (e - nf);
-                    const int c = vr_comp[er];
-                    const int b_dir = comp[4 * c + 3];
-                    const cd* I = m2lr + rkeys[vr_key[er]].off;
-                    const int side = (b_dir == 0) ? 1 : 0;
-                    const int dst = (tslot[side] >= 0) ? 1 + side : 0;
-                    for (int s = 0; s < 2; ++s) {
-                        const int idx = lt + tpg * s;
-                        if (idx >= nco) break;
-                        const int nout = idx - p;
-                        // departure down: L_m += beta_m;  departure up: L_{-m} += (-1)^m beta_m
-                        const int mrow = (b_dir == 1) ? nout : -nout;
-                        const cd* row = I + (int64_t)(mrow + p) * nco;
-                        cd bsum = mk(0, 0);
-                        for (int i = 0; i < nco; ++i) cfma(bsum, row[i], sv[i]);
-                        if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
-                        acc[dst][s] += bsum;
+            for (int e = r0; e < r1; ++e) {
+                const int S = vr_src[e], c = vr_comp[e];
+                const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
+                // source expansion about the reaction centre if S straddles the arrival interface
+                const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
+                const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
+                // departure down: L_n += beta_n;  departure up: L_{-n} += (-1)^n beta_n
+                const int mrow = (b_dir == 1) ? nn : -nn;
+                const cd* col_m = m2lr + rkeys[vr_key[e]].off + (mrow + p);
+                cd bsum = mk(0, 0);
+                if (a_dir == 1) {   // alpha_i = M_i
+                    for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[(int64_t)mi * nco], src[mi]);
+                } else {            // alpha_i = (-1)^(i-p) M_{2p-i}
+                    for (int mi = sl; mi < nco; mi += NS) {
+                        cd v = src[2 * p - mi];
+                        if ((mi - p) & 1) v = -v;
+                        cfma(bsum, col_m[(int64_t)mi * nco], v);
                     }
                 }
+                if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
+                const int side = (b_dir == 0) ? 1 : 0;
+                if (tslot[side] < 0) acc0 += bsum;
+                else if (side == 0) acc1 += bsum;
+                else acc2 += bsum;
             }
         }
-        // reduce the groups and write L (and the reaction-centre locals of straddling targets)
-        if (G > 1) {
-            __syncthreads();
-            for (int k = 0; k < 3; ++k)
-                for (int s = 0; s < 2; ++s) {
-                    const int idx = lt + tpg * s;
-                    if (idx < nco) part[(k * G + g) * nco + idx] = acc[k][s];
-                }
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < nco; idx += blockDim.x) {
-                for (int k = 0; k < 3; ++k) {
-                    if (k > 0 && tslot[k - 1] < 0) continue;
-                    cd t = part[(k * G) * nco + idx];
-                    for (int gg = 1; gg < G; ++gg) t += part[(k * G + gg) * nco + idx];
-                    if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
-                    else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
-                }
-            }
-        } else if (g == 0) {
-            for (int s = 0; s < 2; ++s) {
-                const int idx = lt + tpg * s;
-                if (idx >= nco) continue;
-                Lout[(int64_t)col * ncoef + coef_off[T] + idx] = acc[0][s];
-                for (int side = 0; side < 2; ++side)
-                    if (tslot[side] >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[tslot[side]] + idx] = acc[1 + side][s];
+        red[0][sl][lane] = acc0;
+        red[1][sl][lane] = acc1;
+        red[2][sl][lane] = acc2;
+        __syncthreads();
+        if (live && sl < 3) {
+            const int k = sl;
+            if (k == 0 || tslot[k - 1] >= 0) {
+                cd t = red[k][0][lane];
+                for (int q = 1; q < NS; ++q) t += red[k][q][lane];
+                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
+                else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
             }
         }
+        __syncthreads();
     }
 }
 
@@ -270,7 +234,6 @@ struct XSrc {
     int p;                // source order
     int in_slots;
 };
-#define XT_W 16
 __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
                                                    const cd* __restrict__ vec, int accumulate, int nrhs,
                                                    int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
@@ -390,10 +353,9 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     if (mm <= pT) {
         for (int t = 0; t < 4; ++t) {
             int nn = wk.n0 + tn + t;
-            if (nn <= pS) out[K.off + (int64_t)(mm + pT) * ncS + (nn + pS)] = acc[t];
+            if (nn <= pS) out[K.off + (int64_t)(nn + pS) * ncT + (mm + pT)] = acc[t];
         }
     }
-    (void)ncT;
 }
 
 }  // namespace lfmm

@@ -42,12 +42,13 @@ struct QuadRule {
 struct ExpEntry;
 struct XDst;
 struct XSrc;
+struct M2LItem;
 
 // reaction M2L table key (built on the host, evaluated on the device)
 struct ReactKey {
     int comp, level, pS, pT;   // component, level, orders of source/target expansions
     double X, hS, hT, D;       // x_S - x_T, source-side and target-side heights, effective distance
-    int64_t off;               // offset of the (2pT+1) x (2pS+1) table (row m, column n)
+    int64_t off;               // offset of the (2pT+1) x (2pS+1) table, column-major: (m, n) at n (2pT+1) + m
 };
 
 }  // namespace lfmm
@@ -115,6 +116,8 @@ struct lfmm_geometry_s {
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
     int64_t *d_m2lf_off = nullptr;
     int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids
+    lfmm::M2LItem* d_m2l_items = nullptr;   // (target box, output chunk), coarse levels first
+    int n_m2l_items = 0;
     cd *d_m2lr = nullptr;             // reaction M2L tables
     int *d_vr_ptr = nullptr, *d_vr_src = nullptr, *d_vr_key = nullptr, *d_vr_comp = nullptr;
     lfmm::ReactKey* d_rkeys = nullptr;
