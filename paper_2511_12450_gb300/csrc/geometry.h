@@ -132,6 +132,7 @@ struct lfmm_geometry_s {
     size_t hostbuf_cap = 0;
     // preconditioner (restricted overlapping DD, Sec. 4.2)
     int *d_pc_ptr = nullptr;          // per leaf: offset of its gather list
+    int pc_qmax = 0;                  // largest gather list
     int *d_pc_idx = nullptr;          // gather indices (sorted positions)
     int64_t *d_pc_woff = nullptr;     // per leaf: offset of its (n_own x q) row block
     cd *d_pc_W = nullptr;

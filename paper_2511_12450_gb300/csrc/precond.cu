@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "geometry.h"
@@ -116,19 +117,40 @@ __global__ void __launch_bounds__(256) k_pc_setup(MediumDev m, const int* __rest
     }
 }
 
-// z[own point t of leaf B] = sum_b W_B[b][t] v[J_b]
-__global__ void k_pc_apply(const int* __restrict__ pc_ptr, const int* __restrict__ pc_idx,
+// z[own point t of leaf B] = sum_b W_B[b][t] v[J_b].  One CTA of 128 threads per
+// leaf: the q gathered entries of v are staged in shared memory, then two
+// halves of the threads split the sum over b for 64 rows at a time and are
+// added in a fixed order.
+__global__ void __launch_bounds__(128) k_pc_apply(const int* __restrict__ pc_ptr, const int* __restrict__ pc_idx,
                            const int* __restrict__ own_first, const int* __restrict__ own_cnt,
                            const int64_t* __restrict__ woff, const cd* __restrict__ W, const cd* __restrict__ v,
                            cd* __restrict__ z) {
+    extern __shared__ cd vloc[];   // [q] gathered v, then [64] partial sums
     const int B = blockIdx.x;
     const int jb = pc_ptr[B], q = pc_ptr[B + 1] - jb;
     const int s = own_cnt[B];
     const cd* Wb = W + woff[B];
-    for (int t = threadIdx.x; t < s; t += blockDim.x) {
-        cd acc = mk(0.0, 0.0);
-        for (int b = 0; b < q; ++b) cfma(acc, Wb[(int64_t)b * s + t], v[pc_idx[jb + b]]);
-        z[own_first[B] + t] = acc;
+    for (int b = threadIdx.x; b < q; b += blockDim.x) vloc[b] = v[pc_idx[jb + b]];
+    cd* part = vloc + q;
+    __syncthreads();
+    const int half = threadIdx.x >> 6, tl = threadIdx.x & 63;
+    const int bh = (q + 1) / 2, b0 = min(q, half * bh), b1 = min(q, b0 + bh);
+    for (int t0 = 0; t0 < s; t0 += 64) {
+        const int t = t0 + tl;
+        cd a[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
+        if (t < s) {
+            int b = b0;
+            for (; b + 8 <= b1; b += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) cfma(a[u & 3], Wb[(int64_t)(b + u) * s + t], vloc[b + u]);
+            }
+            for (; b < b1; ++b) cfma(a[0], Wb[(int64_t)b * s + t], vloc[b]);
+        }
+        const cd acc = (a[0] + a[1]) + (a[2] + a[3]);
+        if (half == 1) part[tl] = acc;
+        __syncthreads();
+        if (half == 0 && t < s) z[own_first[B] + t] = acc + part[tl];
+        __syncthreads();
     }
 }
 
@@ -156,6 +178,15 @@ void precond_build(lfmm_geometry_s* g) {
         woff[li] = wt;
         wt += (int64_t)q * own_cnt[li];
     }
+    int qmax = 0;
+    for (int li = 0; li < nleaf; ++li) qmax = std::max(qmax, ptr[li + 1] - ptr[li]);
+    const size_t smem = (size_t)(qmax + 64) * sizeof(cd);
+    if (smem > 227 * 1024) throw CudaError{"preconditioner: neighbourhood of " + std::to_string(qmax) +
+                                           " points does not fit in shared memory (use a smaller leaf size)"};
+    if (smem > 48 * 1024)
+        cuda_check(cudaFuncSetAttribute(k_pc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "pc smem");
+    g->pc_qmax = qmax;
     g->d_pc_ptr = dupload(g, ptr);
     g->d_pc_idx = dupload(g, idx);
     g->d_pc_woff = dupload(g, woff);
@@ -183,7 +214,8 @@ void precond_build(lfmm_geometry_s* g) {
 }
 
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s) {
-    k_pc_apply<<<g->nleaf, 64, 0, s>>>(g->d_pc_ptr, g->d_pc_idx, g->pc_own_first, g->pc_own_cnt, g->d_pc_woff,
+    const size_t smem = (size_t)(g->pc_qmax + 64) * sizeof(cd);
+    k_pc_apply<<<g->nleaf, 128, smem, s>>>(g->d_pc_ptr, g->d_pc_idx, g->pc_own_first, g->pc_own_cnt, g->d_pc_woff,
                                        g->d_pc_W, v_sorted, z_sorted);
     cuda_check(cudaGetLastError(), "k_pc_apply");
 }

@@ -49,61 +49,90 @@ void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted,
     near_apply(g, x_sorted, y_sorted, nrhs, s);
 }
 
-// ------------------------------------------------------------------ BLAS-1/2 helpers for GMRES
-// partial[c * nb + blk] = sum_i conj(V[c][i]) w[i] over the block's slice
-__global__ void k_dots(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ w, int64_t n,
-                       cd* __restrict__ partial) {
-    __shared__ cd red[256];
-    const int c = blockIdx.y;
+// ------------------------------------------------------------------ BLAS-2 helpers for GMRES
+// The Arnoldi step streams the Krylov basis V (n x ncol, column-major, complex128)
+// from HBM: h = V^H w reads it once, w -= V h reads it once more.
+#define VH_ROWS 512    // rows per block of the V^H w kernel
+#define VH_COLS 8      // columns per block (one warp each)
+
+// partial[c * nchunk + chunk] = sum over the chunk's rows of conj(V[c][i]) w[i]
+__global__ void __launch_bounds__(256) k_vh_partial(const cd* __restrict__ V, int ncol, int64_t ld,
+                                                    const cd* __restrict__ w, int64_t n, cd* __restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.y * VH_COLS + warp;
+    const int64_t r0 = (int64_t)blockIdx.x * VH_ROWS;
+    const int64_t r1 = min(r0 + VH_ROWS, n);
+    if (c >= ncol) return;   // whole warps only: no block-level synchronisation below
     const cd* v = V + (int64_t)c * ld;
-    cd acc = mk(0, 0);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        cfma(acc, conjc(v[i]), w[i]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    // 16 rows per lane, four loads of V and w in flight
+    cd a0 = mk(0, 0), a1 = mk(0, 0), a2 = mk(0, 0), a3 = mk(0, 0);
+    int64_t i = r0 + lane;
+    for (; i + 96 < r1; i += 128) {
+        cfma(a0, conjc(v[i]), w[i]);
+        cfma(a1, conjc(v[i + 32]), w[i + 32]);
+        cfma(a2, conjc(v[i + 64]), w[i + 64]);
+        cfma(a3, conjc(v[i + 96]), w[i + 96]);
     }
-    if (threadIdx.x == 0) partial[(int64_t)c * gridDim.x + blockIdx.x] = red[0];
-}
-__global__ void k_reduce_partials(const cd* __restrict__ partial, int nb, int ncol, cd* __restrict__ out) {
-    int c = blockIdx.x;
-    __shared__ cd red[256];
-    cd acc = mk(0, 0);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[(int64_t)c * nb + i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    for (; i < r1; i += 32) cfma(a0, conjc(v[i]), w[i]);
+    a0 += a1;
+    a2 += a3;
+    a0 += a2;
+    for (int o = 16; o > 0; o >>= 1) {
+        a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o);
+        a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o);
     }
-    if (threadIdx.x == 0) out[c] = red[0];
+    if (lane == 0) partial[(int64_t)c * gridDim.x + blockIdx.x] = a0;
 }
-// w -= V h (ncol columns)
+// out[c] = sum of the column's partials (one warp per column)
+__global__ void k_reduce_partials(const cd* __restrict__ partial, int nchunk, int ncol, cd* __restrict__ out) {
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= ncol) return;
+    cd acc = mk(0, 0);
+    for (int i = lane; i < nchunk; i += 32) acc += partial[(int64_t)c * nchunk + i];
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) out[c] = acc;
+}
+// w -= V h (ncol columns); one thread per row, eight columns per round
 __global__ void k_update(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ h,
                          cd* __restrict__ w, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cd acc = w[i];
-    for (int c = 0; c < ncol; ++c) {
-        cd hc = h[c];
-        cfma(acc, -V[(int64_t)c * ld + i], hc);
+    cd a[4] = {w[i], mk(0, 0), mk(0, 0), mk(0, 0)};
+    int c = 0;
+    for (; c + 8 <= ncol; c += 8) {   // eight loads of V in flight
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(a[q & 3], -V[(int64_t)(c + q) * ld + i], h[c + q]);
     }
-    w[i] = acc;
+    for (; c < ncol; ++c) cfma(a[0], -V[(int64_t)c * ld + i], h[c]);
+    w[i] = (a[0] + a[1]) + (a[2] + a[3]);
 }
 // out = V y  (ncol columns)
 __global__ void k_combine(const cd* __restrict__ V, int ncol, int64_t ld, const cd* __restrict__ y,
                           cd* __restrict__ out, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cd acc = mk(0, 0);
-    for (int c = 0; c < ncol; ++c) cfma(acc, V[(int64_t)c * ld + i], y[c]);
-    out[i] = acc;
+    cd a[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
+    int c = 0;
+    for (; c + 8 <= ncol; c += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(a[q & 3], V[(int64_t)(c + q) * ld + i], y[c + q]);
+    }
+    for (; c < ncol; ++c) cfma(a[0], V[(int64_t)c * ld + i], y[c]);
+    out[i] = (a[0] + a[1]) + (a[2] + a[3]);
 }
 __global__ void k_scale(const cd* __restrict__ in, double s, cd* __restrict__ out, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = s * in[i];
+}
+// out = in / sqrt(Re nrm2[0]) (the norm is read on the device; nothing is written if it is 0)
+__global__ void k_scale_by_norm(const cd* __restrict__ in, const cd* __restrict__ nrm2, cd* __restrict__ out,
+                                int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double h = sqrt(fmax(nrm2[0].x, 0.0));
+    if (i < n && h > 0.0) out[i] = (1.0 / h) * in[i];
 }
 __global__ void k_axpby(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ out, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // out = a - b
@@ -114,26 +143,28 @@ struct Blas {
     lfmm_geometry_s* g;
     cudaStream_t s;
     cd* partial;
-    cd* dres;
-    int nb;
+    cd* dres;     // device results: [0, cap) first pass, [cap, 2 cap) second pass, [2 cap] norm^2
+    int cap;
     std::vector<cd> host;
-    Blas(lfmm_geometry_s* g_, cudaStream_t s_, int maxcol) : g(g_), s(s_) {
-        nb = 120;
-        cuda_check(cudaMalloc(&partial, sizeof(cd) * nb * (maxcol + 1)), "malloc partial");
-        cuda_check(cudaMalloc(&dres, sizeof(cd) * (maxcol + 1)), "malloc dres");
-        host.resize(maxcol + 1);
+    Blas(lfmm_geometry_s* g_, cudaStream_t s_, int maxcol) : g(g_), s(s_), cap(maxcol + 1) {
+        const int64_t nchunk = (g->n + VH_ROWS - 1) / VH_ROWS;
+        cuda_check(cudaMalloc(&partial, sizeof(cd) * nchunk * cap), "malloc partial");
+        cuda_check(cudaMalloc(&dres, sizeof(cd) * (2 * cap + 1)), "malloc dres");
+        host.resize(2 * cap + 1);
     }
     ~Blas() { cudaFree(partial); cudaFree(dres); }
-    // h[0..ncol) = V^H w, left in dres and copied to host
-    void dots(const cd* V, int ncol, int64_t ld, const cd* w, int64_t n) {
-        dim3 grid(nb, ncol);
-        k_dots<<<grid, 256, 0, s>>>(V, ncol, ld, w, n, partial);
-        k_reduce_partials<<<ncol, 256, 0, s>>>(partial, nb, ncol, dres);
-        cuda_check(cudaMemcpyAsync(host.data(), dres, sizeof(cd) * ncol, cudaMemcpyDeviceToHost, s), "dots d2h");
-        cuda_check(cudaStreamSynchronize(s), "dots sync");
+    // out_dev[0..ncol) = V^H w, on the device, no synchronisation
+    void vh(const cd* V, int ncol, int64_t ld, const cd* w, int64_t n, cd* out_dev) {
+        const int nchunk = (int)((n + VH_ROWS - 1) / VH_ROWS);
+        dim3 grid(nchunk, (ncol + VH_COLS - 1) / VH_COLS);
+        k_vh_partial<<<grid, 256, 0, s>>>(V, ncol, ld, w, n, partial);
+        k_reduce_partials<<<(ncol + 7) / 8, 256, 0, s>>>(partial, nchunk, ncol, out_dev);
+        cuda_check(cudaGetLastError(), "k_vh");
     }
     double norm(const cd* w, int64_t n) {
-        dots(w, 1, n, w, n);
+        vh(w, 1, n, w, n, dres + 2 * cap);
+        cuda_check(cudaMemcpyAsync(host.data(), dres + 2 * cap, sizeof(cd), cudaMemcpyDeviceToHost, s), "norm d2h");
+        cuda_check(cudaStreamSynchronize(s), "norm sync");
         return std::sqrt(std::max(host[0].x, 0.0));
     }
 };
@@ -164,16 +195,22 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
         const cd* vj = V + (int64_t)j * n;
         if (pre) { precond_apply_sorted(g, vj, z, s); apply_operator_sorted(g, z, w, 1, s); }
         else apply_operator_sorted(g, vj, w, 1, s);
-        // classical Gram-Schmidt, twice
+        // classical Gram-Schmidt, twice, then the norm; one synchronisation per step
         std::vector<C> h(j + 2, C(0, 0));
         for (int pass = 0; pass < 2; ++pass) {
-            bl.dots(V, j + 1, n, w, n);
-            for (int c = 0; c <= j; ++c) h[c] += C(bl.host[c].x, bl.host[c].y);
-            k_update<<<nblk(n), 256, 0, s>>>(V, j + 1, n, bl.dres, w, n);
+            cd* hp = bl.dres + pass * bl.cap;
+            bl.vh(V, j + 1, n, w, n, hp);
+            k_update<<<nblk(n), 256, 0, s>>>(V, j + 1, n, hp, w, n);
         }
-        double hn = bl.norm(w, n);
+        bl.vh(w, 1, n, w, n, bl.dres + 2 * bl.cap);
+        k_scale_by_norm<<<nblk(n), 256, 0, s>>>(w, bl.dres + 2 * bl.cap, V + (int64_t)(j + 1) * n, n);
+        cuda_check(cudaMemcpyAsync(bl.host.data(), bl.dres, sizeof(cd) * (2 * bl.cap + 1), cudaMemcpyDeviceToHost, s),
+                   "arnoldi d2h");
+        cuda_check(cudaStreamSynchronize(s), "arnoldi sync");
+        for (int c = 0; c <= j; ++c)
+            h[c] = C(bl.host[c].x, bl.host[c].y) + C(bl.host[bl.cap + c].x, bl.host[bl.cap + c].y);
+        const double hn = std::sqrt(std::max(bl.host[2 * bl.cap].x, 0.0));
         h[j + 1] = C(hn, 0.0);
-        if (hn > 0) k_scale<<<nblk(n), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)(j + 1) * n, n);
         // Givens rotations
         for (int i = 0; i < j; ++i) {
             C t = cs[i] * h[i] + sn[i] * h[i + 1];
