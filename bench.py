@@ -305,6 +305,26 @@ def run_ours(args):
         roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("k_near_apply"), "peak_source": src}
 
+    # precision form: the same matvec with FP32 multipole-to-local translations
+    ym = torch.empty_like(x)
+    for _ in range(args.warmup):
+        lfmm.matvec(G, x, ym, mixed=True)
+    torch.cuda.synchronize()
+    mtimes = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lfmm.matvec(G, x, ym, mixed=True)
+        e1.record(stream)
+        e1.synchronize()
+        mtimes.append(e0.elapsed_time(e1))
+    mixed_value, mixed_s = whole_job_throughput(float(np.sum(mtimes)) * 1e-3, n * args.steps, dist, "cuda")
+    mixed = {"metric": "FMM matvec Mpts/s, precision form (FP32 M2L on scaled expansions)",
+             "value": mixed_value, "ms_per_step": mixed_s * 1e3 / args.steps,
+             "op_rel_diff": float(torch.linalg.norm(ym - y) / torch.linalg.norm(y))}
+
     solve = None
     if not args.no_solve:
         b = lfmm.rhs_plane_wave(G, [math.radians(float(wl.angles_deg[0]))], device=True)
@@ -313,6 +333,12 @@ def run_ours(args):
                  "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
                  "converged": bool(info["converged"]), "precond": "overlapping DD (Sec. 4.2)",
                  "setup_seconds": setup_s}
+        xm, im = lfmm.gmres_solve(G, b, tol=1e-8, max_iter=1000, precond=True, precision=1)
+        mixed["solve"] = {"metric": "GMRES solve s @1e-8 resid (FP64 residual), mixed-precision refinement",
+                          "seconds": im["solve_seconds"], "iterations": im["iterations"],
+                          "refinements": im["refinements"], "true_rel_residual": im["true_rel_residual"],
+                          "converged": bool(im["converged"]), "op_rel_diff_at_solution": im["op_rel_diff"],
+                          "rel_diff_to_fp64_solution": float(torch.linalg.norm(xm - xs) / torch.linalg.norm(xs))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -336,6 +362,7 @@ def run_ours(args):
             "stages_ms_per_step": {k: v["ms"] / max(v["count"], 1) for k, v in stages.items()},
             "work": work,
             "solve": solve,
+            "mixed": mixed,
             "setup_seconds": setup_s,
         }
         print(json.dumps(line))

@@ -131,6 +131,7 @@ static void free_geometry(lfmm_geometry_s* g) {
         for (int k = 0; k < 2 * ST_COUNT; ++k) cudaEventDestroy(g->prof.ev[k]);
     g->prof.on = false;
     fmm_free(g);
+    mixed_destroy(g);
     for (void* p : g->allocs) cudaFree(p);
     g->allocs.clear();
     if (g->d_xs) cudaFree(g->d_xs);
@@ -335,7 +336,7 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
         prof_begin(g, ST_GATHER, s);
         gather_sorted(g, xin, g->d_xs, nrhs, s);
         prof_end(g, ST_GATHER, s);
-        apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s);
+        apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s, (flags & LFMM_MIXED) != 0);
         prof_begin(g, ST_SCATTER, s);
         scatter_sorted(g, g->d_ys, yout, nrhs, s);
         prof_end(g, ST_SCATTER, s);
@@ -356,7 +357,9 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         double tol = prm ? prm->tol : 1e-8;
         int maxit = prm ? prm->max_iter : 1000;
         int pre = prm ? prm->precond : 1;
+        const int precision = prm ? prm->precision : 0;
         require(tol > 0.0 && maxit >= 1, "invalid GMRES parameters");
+        require(precision == 0 || precision == 1, "precision must be 0 (FP64) or 1 (mixed with refinement)");
         require(!prm || prm->restart == 0, "restarted GMRES is not available in this build (restart must be 0)");
         cudaStream_t s = as_stream(stream);
         if (pre && !g->pc_ready) precond_build(g);
@@ -370,7 +373,7 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         cuda_check(cudaMemcpyAsync(g->d_ys, b, sizeof(cd) * elems, cudaMemcpyDefault, s), "b copy");
         gather_sorted(g, g->d_ys, bb, nrhs, s);
         lfmm_gmres_info local;
-        int ok = gmres_sorted(g, bb, xx, nrhs, tol, maxit, pre != 0, s, info ? info : &local);
+        int ok = gmres_sorted(g, bb, xx, nrhs, tol, maxit, pre != 0, s, info ? info : &local, precision);
         scatter_sorted(g, xx, g->d_ys, nrhs, s);
         cuda_check(cudaMemcpyAsync(x, g->d_ys, sizeof(cd) * elems, cudaMemcpyDefault, s), "x copy");
         cuda_check(cudaStreamSynchronize(s), "gmres sync");

@@ -79,6 +79,7 @@ void fmm_build(lfmm_geometry_s* g) {
     }
     g->ncoef = nc;
     g->d_coef_off = dupload(g, off);
+    g->box_coef_off_host = off;
     if (l0 > D) return;   // no far field: everything is in the near field
 
     // Reaction centres of cells that straddle their layer's interfaces: the
@@ -113,6 +114,8 @@ void fmm_build(lfmm_geometry_s* g) {
             }
         }
         g->n_slots = (int)slot_box.size();
+        g->slot_box_host = slot_box;
+        g->slot_coef_host = slot_coef;
         g->nslotcoef = sc;
         g->d_slot_of = dupload(g, slot_of);
         g->d_slot_coef = dupload(g, slot_coef);
@@ -263,14 +266,23 @@ void fmm_build(lfmm_geometry_s* g) {
         }
         g->d_m2lf = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
         g->d_m2lf_off = dupload(g, toff);
+        g->ftab_lay = tl;
+        g->ftab_lev = tlev;
         g->d_vf_ptr = dupload(g, vf_ptr);
         g->d_vf_src = dupload(g, vf_src);
         g->d_vf_tab = dupload(g, vf_tab);
         // M2L work items (target box, chunk of output indices), coarse levels first
         std::vector<M2LItem> items;
+        g->m2l_item_level_start.assign(nlev + 1, 0);
         for (int T = t.level_start[l0]; T < t.nbox; ++T) {
             const int nco = 2 * t.p_level[t.box_level[T]] + 1;
             for (int c = 0; c * XT_W < nco; ++c) items.push_back(M2LItem{T, c});
+        }
+        for (int l = 0; l <= nlev; ++l) {   // first item of each level (items follow box order)
+            int cnt = 0;
+            for (int T = t.level_start[l0]; T < (l <= D ? t.level_start[std::max(l, l0)] : t.nbox); ++T)
+                cnt += (2 * t.p_level[t.box_level[T]] + 1 + XT_W - 1) / XT_W;
+            g->m2l_item_level_start[l] = cnt;
         }
         g->n_m2l_items = (int)items.size();
         g->d_m2l_items = dupload(g, items);
@@ -311,6 +323,8 @@ void fmm_build(lfmm_geometry_s* g) {
                     rk.hT = tgt_height_box(g->m, C.lt, C.b, loT, hiT);
                     rk.D = rk.hS + rk.hT + C.Hc;
                     rk.off = tot;
+                    g->rkey_lay_s.push_back(t.box_layer[S]);
+                    g->rkey_lay_t.push_back(t.box_layer[T]);
                     tot += (int64_t)(2 * rk.pT + 1) * (2 * rk.pS + 1);
                     keys.push_back(rk);
                 } else {
@@ -326,6 +340,7 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_vr_key = dupload(g, vr_key);
         g->d_vr_comp = dupload(g, vr_comp);
         g->d_rkeys = dupload(g, keys);
+        g->rkeys_host = keys;
         g->d_m2lr = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
         if (!keys.empty()) {
             std::vector<TableWork> work;
@@ -373,7 +388,7 @@ void fmm_free(lfmm_geometry_s* g) {
     g->coef_cols = 0;
 }
 
-void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
+void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed) {
     set_smem_limits();
     TreeHost& t = g->tree;
     const int D = t.D, l0 = t.l0, nlev = D + 1;
@@ -411,12 +426,18 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     prof_end(g, ST_M2M, s);
     {   // M2L, all levels
         prof_begin(g, ST_M2L, s);
-        k_m2l<<<g->n_m2l_items, 128, 0, s>>>(g->d_m2l_items, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
+        // precision form: levels coarser than mixed_min_level keep the FP64 kernel
+        const int lm = mixed ? std::max(l0, std::min(mixed_level(g), D + 1)) : D + 1;
+        const int n64 = g->m2l_item_level_start[lm];
+        if (mixed) mixed_m2l(g, nrhs, lm, s);
+        if (n64 > 0) {
+        k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
                                      g->d_vf_tab, g->d_m2lf, g->d_m2lf_off, g->d_vr_ptr, g->d_vr_src, g->d_vr_key,
                                      g->d_vr_comp, g->d_comp, g->d_rkeys, g->d_m2lr, nrhs, g->ncoef, g->d_M,
                                      g->d_L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, g->d_Mp, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_m2l");
         ++g->n_launches;
+        }
         prof_end(g, ST_M2L, s);
     }
     prof_begin(g, ST_L2L, s);

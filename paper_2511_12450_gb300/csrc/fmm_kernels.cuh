@@ -91,10 +91,6 @@ __global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const doubl
 // (eq. generalintegral): beta_m = sum_n I[m][n] alpha_n with the arrival and
 // departure index flips; tables are stored column-major (entry (m, n) at
 // n (2p+1) + m) so the lanes of a row read consecutive addresses.
-#define XT_W 16
-struct M2LItem {
-    int box, chunk;
-};
 __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const int* __restrict__ box_level,
                       const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
                       const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,

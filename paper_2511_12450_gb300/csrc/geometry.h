@@ -42,7 +42,12 @@ struct QuadRule {
 struct ExpEntry;
 struct XDst;
 struct XSrc;
-struct M2LItem;
+// M2L work item: one target box and one chunk of XT_W output coefficients
+#define XT_W 16
+struct M2LItem {
+    int box, chunk;
+};
+struct MixedState;
 
 // reaction M2L table key (built on the host, evaluated on the device)
 struct ReactKey {
@@ -118,9 +123,19 @@ struct lfmm_geometry_s {
     int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids
     lfmm::M2LItem* d_m2l_items = nullptr;   // (target box, output chunk), coarse levels first
     int n_m2l_items = 0;
+    std::vector<int> m2l_item_level_start;  // [nlev + 1]: first item of each level (level D + 1: the end)
     cd *d_m2lr = nullptr;             // reaction M2L tables
     int *d_vr_ptr = nullptr, *d_vr_src = nullptr, *d_vr_key = nullptr, *d_vr_comp = nullptr;
     lfmm::ReactKey* d_rkeys = nullptr;
+    // host copies kept for the precision form's tables
+    std::vector<lfmm::ReactKey> rkeys_host;
+    std::vector<int> rkey_lay_s, rkey_lay_t;       // layers of the source / target boxes of each key
+    std::vector<int> ftab_lay, ftab_lev;           // layer and level of each free-space M2L table
+    std::vector<int> slot_box_host;
+    std::vector<int64_t> box_coef_off_host;
+    std::vector<int64_t> slot_coef_host;
+    // precision form (FP32 M2L with scaled coefficients), built on first use
+    lfmm::MixedState* mixed = nullptr;
     int n_rkeys = 0;
     int* d_comp = nullptr;            // 4 ints per component
     // level bookkeeping for launches
@@ -170,15 +185,20 @@ void near_build(lfmm_geometry_s* g);
 void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
 // FMM far field (fmm.cu)
 void fmm_build(lfmm_geometry_s* g);
-void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false);
+// precision form: M2L in FP32 on scaled expansions (mixed.cu)
+void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s);
+int mixed_level(lfmm_geometry_s* g);   // first level whose M2L runs in FP32
+void mixed_destroy(lfmm_geometry_s* g);
 void fmm_free(lfmm_geometry_s* g);   // per-nrhs coefficient buffers
 // permutation helpers and the full operator (solver.cu)
 void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s);
 void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s);
-void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
+                           bool mixed = false);
 void precond_build(lfmm_geometry_s* g);
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
-                 cudaStream_t s, lfmm_gmres_info* info);
+                 cudaStream_t s, lfmm_gmres_info* info, int precision = 0);
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s);
 void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s);
 void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t m, const double* d_targets,

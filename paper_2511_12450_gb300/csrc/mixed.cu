@@ -1,0 +1,397 @@
+// mixed.cu -- the precision form of the operator: the multipole-to-local
+// translations (free space, Graf's addition theorem, and the reaction
+// components' moment tables of eq. generalintegral) in FP32, everything else
+// (P2M, M2M, L2L, L2P, the stored near field with its singular and Sommerfeld
+// entries) in FP64.
+//
+// FP32 has 8 exponent bits; the expansions span far more.  At the fine levels
+// the multipole coefficients decay like (k rho / 2)^n / n! and the Hankel
+// translation entries H_{m-n}(k R) grow like (|m-n| - 1)! (2 / k R)^{|m-n|}
+// (J_20(0.2) ~ 1e-38 and H_40(0.6) ~ 1e66 at the C2 leaf level).  Every
+// expansion of a (layer, level) is therefore carried scaled,
+//     M~_n = M_n / s^|n|,     L~_n = L_n s^|n|,
+// and the translation operators accordingly,
+//     free:      L~_n = sum_m [s^(|n| + |m|) T_{m-n}] M~_m,
+//     reaction:  beta~_m = sum_n [s_T^|m| s_S^|n| I_{mn}] alpha~_n,
+// with s <= 1 chosen per (layer, level) on the host so that the largest scaled
+// translation entry and the smallest scaled order-p multipole basis value stay
+// equally far inside the FP32 range.  The scaled operators are stored as dense
+// FP32 matrices (column-major), the free-space ones per (layer, level, offset).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "geometry.h"
+
+namespace lfmm {
+
+struct cf {
+    float x, y;
+};
+__device__ __forceinline__ cf mkf(float a, float b) { cf r; r.x = a; r.y = b; return r; }
+__device__ __forceinline__ void cfmaf(cf& a, cf b, cf c) {
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+__device__ __forceinline__ cf addf(cf a, cf b) { return mkf(a.x + b.x, a.y + b.y); }
+
+struct MixedState {
+    int cols = 0;                       // right-hand-side columns the FP32 buffers hold
+    cf *M = nullptr, *L = nullptr;      // [cols][ncoef]   scaled multipoles / locals
+    cf *Mp = nullptr, *Lp = nullptr;    // [cols][nslotcoef]
+    double *ispow = nullptr;            // [ncoef]      s^-|n| per coefficient
+    double *ispow_slot = nullptr;       // [nslotcoef]
+    cf *ftab = nullptr;                 // scaled dense free-space tables
+    int64_t *ftab_off = nullptr;        // per table id
+    cf *rtab = nullptr;                 // scaled dense reaction tables (offsets as ReactKey::off)
+    std::vector<double> scale;          // [layer * nlev + level]
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Choice of the scale s for one (layer, level).
+// log10 of the largest scaled translation entry: max_{j <= 2p} s^j |Y_j(k 2w)|
+// (2w is the smallest centre distance of an M2L pair; |H_j| ~ |Y_j| where it is
+// large), by the forward recurrence of Y_j with running rescaling.
+static double log10_max_scaled_y(double x, int jmax, double s) {
+    double y0 = std::cyl_neumann(0.0, x), y1 = std::cyl_neumann(1.0, x);
+    double lsc = 0.0;   // log10 of the factor divided out of (y0, y1)
+    double best = std::log10(std::max(std::fabs(y0), 1e-300));
+    best = std::max(best, std::log10(std::max(std::fabs(y1), 1e-300)) + std::log10(s));
+    for (int j = 1; j < jmax; ++j) {
+        double y2 = (2.0 * j / x) * y1 - y0;
+        y0 = y1;
+        y1 = y2;
+        double a = std::fabs(y1);
+        if (a > 1e200) { y0 *= 1e-200; y1 *= 1e-200; lsc += 200.0; a = std::fabs(y1); }
+        best = std::max(best, std::log10(std::max(a, 1e-300)) + lsc + (j + 1) * std::log10(s));
+    }
+    return best;
+}
+// log10 of the envelope of |J_n(x)|: 0 while n <= x, else the leading term of the
+// power series, (x/2)^n / n! (the envelope avoids the zeros of J_n).
+static double log10_env_j(double x, int n) {
+    const double lead = n * std::log10(0.5 * x) - std::lgamma(n + 1.0) / std::log(10.0);
+    return std::min(0.0, lead);
+}
+// The scale keeps three magnitudes inside the FP32 range at once: the largest
+// scaled multipole basis value max_n |J_n(x)| / s^n, the smallest one
+// |J_p(x)| / s^p (x = k w / sqrt(2), the farthest point of the box), and the
+// largest scaled translation entry.  s is a power of two in (0, 1]; the chosen
+// one minimises the largest of the three log-magnitudes.
+static double choose_scale(double k, double w, int p) {
+    const double x = k * w / std::sqrt(2.0);
+    double best_s = 1.0, best_v = 1e300;
+    for (int j = 0; j <= 80; ++j) {
+        const double s = std::ldexp(1.0, -j), ls = std::log10(s);
+        double big_m = -1e300;
+        for (int n = 0; n <= p; ++n) big_m = std::max(big_m, log10_env_j(x, n) - n * ls);
+        const double small_m = log10_env_j(x, p) - p * ls;
+        const double big_t = log10_max_scaled_y(2.0 * k * w, 2 * p, s);
+        const double v = std::max(std::max(big_m, big_t), -small_m);
+        if (v < best_v) { best_v = v; best_s = s; }
+    }
+    return best_s;
+}
+
+// ---------------------------------------------------------------------------
+// Table and coefficient conversions.
+__global__ void k_free32_tables(const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
+                                const int* __restrict__ tab_p, const double* __restrict__ tab_s,
+                                const int64_t* __restrict__ off32, cf* __restrict__ out) {
+    const int id = blockIdx.x;
+    const int p = tab_p[id], nco = 2 * p + 1;
+    const double s = tab_s[id];
+    const cd* base = m2lf + m2lf_off[id];
+    for (int e = threadIdx.x; e < nco * nco; e += blockDim.x) {
+        const int mi = e / nco, ni = e - mi * nco;   // column-major: (n_out, m_in) at m_in nco + n_out
+        const int n = ni - p, m = mi - p;
+        const double f = pow(s, (double)(abs(n) + abs(m)));
+        const cd v = base[mi - ni + 2 * p];          // T_{m-n}
+        out[off32[id] + e] = mkf((float)(f * v.x), (float)(f * v.y));
+    }
+}
+__global__ void k_react32_tables(const cd* __restrict__ m2lr, const ReactKey* __restrict__ keys,
+                                 const double* __restrict__ key_ss, const double* __restrict__ key_st,
+                                 cf* __restrict__ out) {
+    const ReactKey K = keys[blockIdx.x];
+    const int ncT = 2 * K.pT + 1, ncS = 2 * K.pS + 1;
+    const double ss = key_ss[blockIdx.x], st = key_st[blockIdx.x];
+    for (int e = threadIdx.x; e < ncT * ncS; e += blockDim.x) {
+        const int ni = e / ncT, mi = e - ni * ncT;   // column-major: (m_out, n_in) at n_in ncT + m_out
+        const double f = pow(st, (double)abs(mi - K.pT)) * pow(ss, (double)abs(ni - K.pS));
+        const cd v = m2lr[K.off + e];
+        out[K.off + e] = mkf((float)(f * v.x), (float)(f * v.y));
+    }
+}
+// out (FP32) = in (FP64) * ispow, column by column
+__global__ void k_to32(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t n, int nrhs,
+                       cf* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const double f = ispow[t % n];
+    const cd v = in[t];
+    out[t] = mkf((float)(f * v.x), (float)(f * v.y));
+}
+// out (FP64) = in (FP32) * ispow
+__global__ void k_from32(const cf* __restrict__ in, const double* __restrict__ ispow, int64_t n, int nrhs,
+                         cd* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nrhs) return;
+    const double f = ispow[t % n];
+    const cf v = in[t];
+    out[t] = mk(f * (double)v.x, f * (double)v.y);
+}
+
+// ---------------------------------------------------------------------------
+// M2L in FP32 on the scaled expansions; the same work items, lane/slice split and
+// index flips as the FP64 kernel, with dense tables for the free-space part too.
+__global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items, const int* __restrict__ box_level,
+                        const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
+                        const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
+                        const cf* __restrict__ ftab, const int64_t* __restrict__ ftab_off,
+                        const int* __restrict__ vr_ptr, const int* __restrict__ vr_src,
+                        const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
+                        const int* __restrict__ comp, const ReactKey* __restrict__ rkeys,
+                        const cf* __restrict__ rtab, int nrhs, int64_t ncoef, const cf* __restrict__ Min,
+                        cf* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
+                        int64_t nslotcoef, const cf* __restrict__ Mp, cf* __restrict__ Lp) {
+    constexpr int NS = 128 / XT_W;
+    __shared__ cf red[3][NS][XT_W];
+    const M2LItem it = items[blockIdx.x];
+    const int T = it.box;
+    const int p = p_level[box_level[T]];
+    const int nco = 2 * p + 1;
+    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
+    const int idx = it.chunk * XT_W + lane;
+    const bool live = idx < nco;
+    const int nn = idx - p;
+    const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
+    const int f0 = vf_ptr[T], f1 = vf_ptr[T + 1];
+    const int r0 = vr_ptr[T], r1 = vr_ptr[T + 1];
+    for (int col = 0; col < nrhs; ++col) {
+        const cf* Mc = Min + (int64_t)col * ncoef;
+        const cf* Mpc = Mp + (int64_t)col * nslotcoef;
+        cf acc0 = mkf(0, 0), acc1 = mkf(0, 0), acc2 = mkf(0, 0);   // L, side-0 slot, side-1 slot
+        if (live) {
+            for (int e = f0; e < f1; ++e) {
+                const cf* src = Mc + coef_off[vf_src[e]];
+                const cf* tb = ftab + ftab_off[vf_tab[e]] + idx;   // (n_out, m_in) at m_in nco + n_out
+                for (int mi = sl; mi < nco; mi += NS) cfmaf(acc0, src[mi], tb[(int64_t)mi * nco]);
+            }
+            for (int e = r0; e < r1; ++e) {
+                const int S = vr_src[e], c = vr_comp[e];
+                const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
+                const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
+                const cf* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
+                const int mrow = (b_dir == 1) ? nn : -nn;
+                const cf* col_m = rtab + rkeys[vr_key[e]].off + (mrow + p);
+                cf bsum = mkf(0, 0);
+                if (a_dir == 1) {
+                    for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[(int64_t)mi * nco], src[mi]);
+                } else {
+                    for (int mi = sl; mi < nco; mi += NS) {
+                        cf v = src[2 * p - mi];
+                        if ((mi - p) & 1) v = mkf(-v.x, -v.y);
+                        cfmaf(bsum, col_m[(int64_t)mi * nco], v);
+                    }
+                }
+                if (b_dir == 0 && (mrow & 1)) bsum = mkf(-bsum.x, -bsum.y);
+                const int side = (b_dir == 0) ? 1 : 0;
+                if (tslot[side] < 0) acc0 = addf(acc0, bsum);
+                else if (side == 0) acc1 = addf(acc1, bsum);
+                else acc2 = addf(acc2, bsum);
+            }
+        }
+        red[0][sl][lane] = acc0;
+        red[1][sl][lane] = acc1;
+        red[2][sl][lane] = acc2;
+        __syncthreads();
+        if (live && sl < 3) {
+            const int k = sl;
+            if (k == 0 || tslot[k - 1] >= 0) {
+                cf t = red[k][0][lane];
+                for (int q = 1; q < NS; ++q) t = addf(t, red[k][q][lane]);
+                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
+                else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+static void mixed_free_buffers(MixedState* ms) {
+    cudaFree(ms->M); cudaFree(ms->L); cudaFree(ms->Mp); cudaFree(ms->Lp);
+    ms->M = ms->L = ms->Mp = ms->Lp = nullptr;
+    ms->cols = 0;
+}
+
+void mixed_destroy(lfmm_geometry_s* g) {
+    if (!g->mixed) return;
+    MixedState* ms = g->mixed;
+    mixed_free_buffers(ms);
+    cudaFree(ms->ispow); cudaFree(ms->ispow_slot); cudaFree(ms->ftab); cudaFree(ms->ftab_off); cudaFree(ms->rtab);
+    delete ms;
+    g->mixed = nullptr;
+}
+
+template <typename T>
+static T* upload_raw(const std::vector<T>& v, size_t& bytes) {
+    T* p = nullptr;
+    const size_t b = sizeof(T) * std::max<size_t>(v.size(), 1);
+    cuda_check(cudaMalloc(&p, b), "cudaMalloc (precision form)");
+    bytes += b;
+    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
+    return p;
+}
+
+// Scales and FP32 tables of the precision form (once per geometry, on first use).
+static void mixed_build(lfmm_geometry_s* g) {
+    TreeHost& t = g->tree;
+    const int D = t.D, l0 = t.l0, nlev = D + 1, nl = g->m.nl;
+    MixedState* ms = new MixedState();
+    g->mixed = ms;
+    ms->scale.assign((size_t)nl * nlev, 1.0);
+    for (int lay = 0; lay < nl; ++lay)
+        for (int l = l0; l <= D; ++l)
+            ms->scale[lay * nlev + l] = choose_scale(g->m.k[lay], t.width(l), t.p_level[l]);
+    // s^-|n| per coefficient of every box and reaction centre
+    std::vector<double> isp((size_t)std::max<int64_t>(g->ncoef, 1), 1.0);
+    for (int b = t.level_start[l0]; b < t.nbox; ++b) {
+        const int l = t.box_level[b], p = t.p_level[l];
+        const double s = ms->scale[t.box_layer[b] * nlev + l];
+        for (int i = 0; i <= 2 * p; ++i) isp[g->box_coef_off_host[b] + i] = std::pow(s, -(double)std::abs(i - p));
+    }
+    std::vector<double> isps((size_t)std::max<int64_t>(g->nslotcoef, 1), 1.0);
+    for (size_t q = 0; q < g->slot_box_host.size(); ++q) {
+        const int b = g->slot_box_host[q];
+        const int l = t.box_level[b], p = t.p_level[l];
+        const double s = ms->scale[t.box_layer[b] * nlev + l];
+        for (int i = 0; i <= 2 * p; ++i) isps[g->slot_coef_host[q] + i] = std::pow(s, -(double)std::abs(i - p));
+    }
+    ms->ispow = upload_raw(isp, ms->bytes);
+    ms->ispow_slot = upload_raw(isps, ms->bytes);
+    // free-space tables
+    const int ntab = (int)g->ftab_lay.size();
+    std::vector<int> tp(ntab);
+    std::vector<double> ts(ntab);
+    std::vector<int64_t> off32(ntab);
+    int64_t tot = 0;
+    for (int id = 0; id < ntab; ++id) {
+        const int l = g->ftab_lev[id];
+        tp[id] = t.p_level[l];
+        ts[id] = ms->scale[g->ftab_lay[id] * nlev + l];
+        off32[id] = tot;
+        tot += (int64_t)(2 * tp[id] + 1) * (2 * tp[id] + 1);
+    }
+    size_t scratch = 0;
+    int* d_tp = upload_raw(tp, scratch);
+    double* d_ts = upload_raw(ts, scratch);
+    ms->ftab_off = upload_raw(off32, ms->bytes);
+    cuda_check(cudaMalloc(&ms->ftab, sizeof(cf) * std::max<int64_t>(tot, 1)), "cudaMalloc ftab32");
+    ms->bytes += sizeof(cf) * std::max<int64_t>(tot, 1);
+    if (ntab > 0) k_free32_tables<<<ntab, 256>>>(g->d_m2lf, g->d_m2lf_off, d_tp, d_ts, ms->ftab_off, ms->ftab);
+    cuda_check(cudaGetLastError(), "k_free32_tables");
+    // reaction tables
+    const int nk = (int)g->rkeys_host.size();
+    int64_t rtot = 0;
+    std::vector<double> kss(nk), kst(nk);
+    for (int kk = 0; kk < nk; ++kk) {
+        const ReactKey& K = g->rkeys_host[kk];
+        rtot = std::max<int64_t>(rtot, K.off + (int64_t)(2 * K.pT + 1) * (2 * K.pS + 1));
+        kss[kk] = ms->scale[g->rkey_lay_s[kk] * nlev + K.level];
+        kst[kk] = ms->scale[g->rkey_lay_t[kk] * nlev + K.level];
+    }
+    double* d_kss = upload_raw(kss, scratch);
+    double* d_kst = upload_raw(kst, scratch);
+    cuda_check(cudaMalloc(&ms->rtab, sizeof(cf) * std::max<int64_t>(rtot, 1)), "cudaMalloc rtab32");
+    ms->bytes += sizeof(cf) * std::max<int64_t>(rtot, 1);
+    if (nk > 0) k_react32_tables<<<nk, 256>>>(g->d_m2lr, g->d_rkeys, d_kss, d_kst, ms->rtab);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaFree(d_tp); cudaFree(d_ts); cudaFree(d_kss); cudaFree(d_kst);
+    cuda_check(e1, "k_react32_tables");
+    cuda_check(e2, "precision form tables");
+}
+
+// First level whose M2L runs in FP32: the levels where the expansion order is
+// the base order p, i.e. the wide-band rule did not raise it.  On coarser
+// levels (boxes many wavelengths wide, orders up to 2-3 times p) the local
+// coefficients of orders well above k rho reach 1e8 and more relative to the
+// field, FP32 carries them to about 1e-4, and the local-to-local translations
+// pass those absolute errors down the tree; there the FP64 kernel stays.
+int mixed_level(lfmm_geometry_s* g) {
+    const TreeHost& t = g->tree;
+    for (int l = t.l0; l <= t.D; ++l)
+        if (t.p_level[l] <= g->p) return l;
+    return t.D + 1;
+}
+
+// M2L of the precision form for the levels >= min_level: scale M (FP64) into
+// FP32, translate, scale L back (those levels' coefficients only).
+void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
+    if (!g->mixed) mixed_build(g);
+    MixedState* ms = g->mixed;
+    const TreeHost& t = g->tree;
+    if (min_level > t.D) return;
+    if (ms->cols < nrhs) {
+        mixed_free_buffers(ms);
+        const size_t nc = (size_t)std::max<int64_t>(g->ncoef, 1) * nrhs;
+        const size_t ns = (size_t)std::max<int64_t>(g->nslotcoef, 1) * nrhs;
+        cuda_check(cudaMalloc(&ms->M, sizeof(cf) * nc), "cudaMalloc M32");
+        cuda_check(cudaMalloc(&ms->L, sizeof(cf) * nc), "cudaMalloc L32");
+        cuda_check(cudaMalloc(&ms->Mp, sizeof(cf) * ns), "cudaMalloc Mp32");
+        cuda_check(cudaMalloc(&ms->Lp, sizeof(cf) * ns), "cudaMalloc Lp32");
+        ms->cols = nrhs;
+    }
+    // coefficient ranges of the levels >= min_level (boxes and slots follow box order)
+    const int64_t c0 = g->box_coef_off_host[t.level_start[min_level]];
+    int64_t s0 = g->nslotcoef;
+    for (size_t q = 0; q < g->slot_box_host.size(); ++q)
+        if (t.box_level[g->slot_box_host[q]] >= min_level) { s0 = g->slot_coef_host[q]; break; }
+    const int64_t ncl = g->ncoef - c0, nsl = g->nslotcoef - s0;
+    for (int col = 0; col < nrhs; ++col) {   // scale in (per column: the ranges are not contiguous)
+        if (ncl > 0) {
+            k_to32<<<(unsigned)((ncl + 255) / 256), 256, 0, s>>>(g->d_M + col * g->ncoef + c0, ms->ispow + c0, ncl, 1,
+                                                                 ms->M + col * g->ncoef + c0);
+            ++g->n_launches;
+        }
+        if (nsl > 0) {
+            k_to32<<<(unsigned)((nsl + 255) / 256), 256, 0, s>>>(g->d_Mp + col * g->nslotcoef + s0,
+                                                                 ms->ispow_slot + s0, nsl, 1,
+                                                                 ms->Mp + col * g->nslotcoef + s0);
+            ++g->n_launches;
+        }
+    }
+    cuda_check(cudaGetLastError(), "k_to32");
+    const int i0 = g->m2l_item_level_start[min_level];
+    const int ni = g->n_m2l_items - i0;
+    if (ni > 0) {
+        k_m2l32<<<ni, 128, 0, s>>>(g->d_m2l_items + i0, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr,
+                                   g->d_vf_src, g->d_vf_tab, ms->ftab, ms->ftab_off, g->d_vr_ptr, g->d_vr_src,
+                                   g->d_vr_key, g->d_vr_comp, g->d_comp, g->d_rkeys, ms->rtab, nrhs, g->ncoef, ms->M,
+                                   ms->L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, ms->Mp, ms->Lp);
+        cuda_check(cudaGetLastError(), "k_m2l32");
+        ++g->n_launches;
+    }
+    for (int col = 0; col < nrhs; ++col) {   // scale back
+        if (ncl > 0) {
+            k_from32<<<(unsigned)((ncl + 255) / 256), 256, 0, s>>>(ms->L + col * g->ncoef + c0, ms->ispow + c0, ncl, 1,
+                                                                   g->d_L + col * g->ncoef + c0);
+            ++g->n_launches;
+        }
+        if (nsl > 0) {
+            k_from32<<<(unsigned)((nsl + 255) / 256), 256, 0, s>>>(ms->Lp + col * g->nslotcoef + s0,
+                                                                   ms->ispow_slot + s0, nsl, 1,
+                                                                   g->d_Lp + col * g->nslotcoef + s0);
+            ++g->n_launches;
+        }
+    }
+    cuda_check(cudaGetLastError(), "k_from32");
+}
+
+}  // namespace lfmm

@@ -43,9 +43,10 @@ void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs,
     ++g->n_launches;
 }
 
-void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
+void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
+                           bool mixed) {
     cuda_check(cudaMemsetAsync(y_sorted, 0, sizeof(cd) * g->n * nrhs, s), "memset y");
-    fmm_apply(g, x_sorted, y_sorted, nrhs, s);
+    fmm_apply(g, x_sorted, y_sorted, nrhs, s, mixed);
     near_apply(g, x_sorted, y_sorted, nrhs, s);
 }
 
@@ -173,7 +174,7 @@ static inline int nblk(int64_t n) { return (int)((n + 255) / 256); }
 
 // One right-hand side; vectors in sorted order on the device.
 static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int maxit, bool pre, cudaStream_t s,
-                     int* iters, double* res_out) {
+                     int* iters, double* res_out, bool mixed = false) {
     const int64_t n = g->n;
     Blas bl(g, s, maxit + 1);
     cd *V = nullptr, *w = nullptr, *z = nullptr, *hd = nullptr;
@@ -193,8 +194,8 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
     double res = 1.0;
     for (j = 0; j < maxit; ++j) {
         const cd* vj = V + (int64_t)j * n;
-        if (pre) { precond_apply_sorted(g, vj, z, s); apply_operator_sorted(g, z, w, 1, s); }
-        else apply_operator_sorted(g, vj, w, 1, s);
+        if (pre) { precond_apply_sorted(g, vj, z, s); apply_operator_sorted(g, z, w, 1, s, mixed); }
+        else apply_operator_sorted(g, vj, w, 1, s, mixed);
         // classical Gram-Schmidt, twice, then the norm; one synchronisation per step
         std::vector<C> h(j + 2, C(0, 0));
         for (int pass = 0; pass < 2; ++pass) {
@@ -254,33 +255,88 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
     return res <= tol ? 1 : 0;
 }
 
+__global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + d[i];
+}
+
+// GMRES for every column.  precision 0: the FP64 operator throughout.
+// precision 1: iterative refinement -- each outer step solves A_mixed d = r by
+// GMRES on the precision-form operator (FP32 M2L) to a relative tolerance no
+// finer than what the outer tolerance still needs, adds d to x and recomputes
+// r = b - A x with the FP64 operator; it stops when ||r|| <= tol ||b||, when the
+// Krylov iterations reach max_iter, or when an outer step no longer halves ||r||.
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
-                 cudaStream_t s, lfmm_gmres_info* info) {
+                 cudaStream_t s, lfmm_gmres_info* info, int precision) {
     auto t0 = std::chrono::steady_clock::now();
-    int all = 1, it = 0;
-    double worst = 0.0, worst_true = 0.0;
-    cd* r = nullptr;
-    cuda_check(cudaMalloc(&r, sizeof(cd) * g->n), "malloc r");
+    const int64_t n = g->n;
+    int all = 1, it = 0, outer_last = 0, f64_last = 0;
+    double worst = 0.0, worst_true = 0.0, worst_opdiff = 0.0;
+    cd *r = nullptr, *d = nullptr, *y2 = nullptr;
+    cuda_check(cudaMalloc(&r, sizeof(cd) * n), "malloc r");
+    cuda_check(cudaMalloc(&d, sizeof(cd) * n), "malloc d");
+    cuda_check(cudaMalloc(&y2, sizeof(cd) * n), "malloc y2");
+    struct Free { cd *a, *b, *c; ~Free() { cudaFree(a); cudaFree(b); cudaFree(c); } } fr{r, d, y2};
     Blas bl(g, s, 2);
     for (int c = 0; c < nrhs; ++c) {
-        const cd* bc = b + (int64_t)c * g->n;
-        cd* xc = x + (int64_t)c * g->n;
-        double res;
-        int ok = gmres_one(g, bc, xc, tol, maxit, pre, s, &it, &res);
+        const cd* bc = b + (int64_t)c * n;
+        cd* xc = x + (int64_t)c * n;
+        double res = 0.0, rn = 0.0;
+        const double bn = bl.norm(bc, n);
+        int ok = 0, outer = 0, f64 = 0;
+        if (precision == 0) {
+            ok = gmres_one(g, bc, xc, tol, maxit, pre, s, &it, &res);
+            apply_operator_sorted(g, xc, r, 1, s);
+            k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+            rn = bl.norm(r, n);
+            f64 = 1;
+        } else {
+            cuda_check(cudaMemsetAsync(xc, 0, sizeof(cd) * n, s), "memset x");
+            cuda_check(cudaMemcpyAsync(r, bc, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "r = b");
+            rn = bn;
+            int total = 0;
+            while (bn > 0.0 && rn > tol * bn && total < maxit) {
+                const double tol_in = std::min(0.5, std::max(0.5 * tol * bn / rn, 1e-6));
+                int its = 0;
+                double rr = 0.0;
+                gmres_one(g, r, d, tol_in, maxit - total, pre, s, &its, &rr, true);
+                total += its;
+                k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
+                apply_operator_sorted(g, xc, r, 1, s);
+                k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+                ++f64;
+                ++outer;
+                const double rn_new = bl.norm(r, n);
+                const bool stalled = rn_new > 0.5 * rn;
+                rn = rn_new;
+                if (stalled) break;
+            }
+            it = total;
+            ok = (bn == 0.0 || rn <= tol * bn) ? 1 : 0;
+            res = bn > 0.0 ? rn / bn : 0.0;
+            // difference of the two operators at the solution, ||(A_mixed - A) x|| / ||A x||
+            apply_operator_sorted(g, xc, y2, 1, s, true);
+            apply_operator_sorted(g, xc, d, 1, s);
+            const double an = bl.norm(d, n);
+            k_axpby<<<nblk(n), 256, 0, s>>>(y2, d, d, n);
+            const double dn = bl.norm(d, n);
+            worst_opdiff = std::max(worst_opdiff, an > 0.0 ? dn / an : 0.0);
+        }
         all &= ok;
         worst = std::max(worst, res);
-        apply_operator_sorted(g, xc, r, 1, s);
-        k_axpby<<<nblk(g->n), 256, 0, s>>>(bc, r, r, g->n);
-        double rn = bl.norm(r, g->n), bn = bl.norm(bc, g->n);
         worst_true = std::max(worst_true, bn > 0 ? rn / bn : 0.0);
+        outer_last = outer;
+        f64_last = f64;
     }
-    cudaFree(r);
     if (info) {
         info->iterations = it;
         info->converged = all;
         info->rel_residual = worst;
         info->true_rel_residual = worst_true;
         info->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->refinements = outer_last;
+        info->fp64_matvecs = f64_last;
+        info->op_rel_diff = worst_opdiff;
     }
     return all;
 }

@@ -28,6 +28,7 @@ LFMM_ERR_QUADRATURE = -5
 LFMM_ERR_TIMEOUT = -6
 LFMM_ERR_HBM_BUDGET = -7
 LFMM_DEVICE_PTRS = 1
+LFMM_MIXED = 2
 LFMM_PROFILE_STAGES = 1
 STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
@@ -51,12 +52,13 @@ class Params(ctypes.Structure):
 
 class GmresParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class GmresInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("true_rel_residual", ctypes.c_double), ("solve_seconds", ctypes.c_double)]
+                ("true_rel_residual", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+                ("refinements", ctypes.c_int32), ("fp64_matvecs", ctypes.c_int32), ("op_rel_diff", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -208,7 +210,8 @@ def rhs_plane_wave(g: Geometry, angles_rad, out=None, stream=None, device=False)
     return out
 
 
-def matvec(g: Geometry, x, y=None, stream=None):
+def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False):
+    """y = K x.  mixed=True applies the precision form (FP32 multipole-to-local translations)."""
     xp, nrhs, flags, keep = _vec_args(x, g.n)
     if y is None:
         y = _empty_like(x, g.n, nrhs)
@@ -216,7 +219,7 @@ def matvec(g: Geometry, x, y=None, stream=None):
     if flags != flags_y:
         raise ValueError("x and y must both be host arrays or both device tensors")
     st = _stream_of(stream) if flags else ctypes.c_void_p(0)
-    _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
+    _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags | (LFMM_MIXED if mixed else 0), st))
     return y
 
 
@@ -232,12 +235,13 @@ def matvec_static(g: Geometry, x, y, stream=None):
 
 
 def gmres_solve(g: Geometry, b, x=None, tol: float = 1e-8, max_iter: int = 1000, precond: bool = True,
-                stream=None):
+                stream=None, precision: int = 0):
+    """GMRES to tol.  precision=1: iterative refinement with inner solves on the precision form."""
     bp, nrhs, flags, keep = _vec_args(b, g.n)
     if x is None:
         x = _empty_like(b, g.n, nrhs)
     xp, _, _, keep_x = _vec_args(x, g.n)
-    prm = GmresParams(float(tol), int(max_iter), 0, 1 if precond else 0, 0)
+    prm = GmresParams(float(tol), int(max_iter), 0, 1 if precond else 0, int(precision))
     info = GmresInfo()
     st = _stream_of(stream) if flags else ctypes.c_void_p(0)
     status = _check(library().lfmm_gmres_solve(g.handle, nrhs, bp, xp, ctypes.byref(prm), ctypes.byref(info), st))

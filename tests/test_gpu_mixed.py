@@ -1,0 +1,98 @@
+"""Precision form (FP32 multipole-to-local translations on scaled expansions) and the
+mixed-precision GMRES with iterative refinement, against the FP64 path and the oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nystrom as onys
+from workloads import config_c2, layered_wide
+
+pytestmark = pytest.mark.gpu
+
+# bound on ||(A_mixed - A) x|| / ||A x||: FP32 rounding (2^-24 ~ 6e-8) of sums of a
+# few thousand terms through the far field, which carries a fraction of the operator
+OP_TOL = 2e-6
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module")
+def wide(gpu_lib):
+    lf = gpu_lib
+    wl = layered_wide()
+    med = wl.medium
+    pts, w, _, _ = onys.elements(wl.bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, p=20, leaf_size=8)
+    return dict(lf=lf, wl=wl, med=med, pts=pts, w=w, K=K, M=M, G=G)
+
+
+@pytest.fixture(scope="module")
+def c2(gpu_lib):
+    lf = gpu_lib
+    wl = config_c2()
+    med = wl.medium
+    pts, w, nrm = lf.polygon_elements(wl.bodies)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size)
+    return dict(lf=lf, wl=wl, med=med, pts=pts, w=w, M=M, G=G)
+
+
+def test_mixed_matvec_wide_band_against_fp64_and_oracle(wide):
+    lf, G, K = wide["lf"], wide["G"], wide["K"]
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    y64 = lf.matvec(G, x)
+    y32 = lf.matvec(G, x, mixed=True)
+    d64, d32 = relerr(y32, y64), relerr(y32, K @ x)
+    print(f"wide: mixed vs FP64 {d64:.3e}, mixed vs oracle {d32:.3e}")
+    assert d64 <= OP_TOL
+    assert d32 <= OP_TOL + 1e-8
+    # the FP64 path is untouched by the precision form having been built
+    assert np.array_equal(lf.matvec(G, x), y64)
+
+
+def test_mixed_matvec_c2_against_fp64(c2):
+    lf, G = c2["lf"], c2["G"]
+    rng = np.random.default_rng(22)
+    X = np.asfortranarray(rng.standard_normal((G.n, 2)) + 1j * rng.standard_normal((G.n, 2)))
+    y64 = lf.matvec(G, X)
+    y32 = lf.matvec(G, X, mixed=True)
+    for c in range(2):
+        d = relerr(y32[:, c], y64[:, c])
+        print(f"C2 column {c}: mixed vs FP64 {d:.3e}")
+        assert d <= OP_TOL
+    # reproducible
+    assert np.array_equal(lf.matvec(G, X, mixed=True), y32)
+
+
+def test_mixed_gmres_refinement_reaches_fp64_residual_wide(wide):
+    lf, G, K = wide["lf"], wide["G"], wide["K"]
+    wl = wide["wl"]
+    b = lf.rhs_plane_wave(G, [math.radians(float(wl.angles_deg[0]))])
+    x1, i1 = lf.gmres_solve(G, b, tol=1e-8, precision=1)
+    ref = np.linalg.solve(K, b)
+    print("mixed GMRES:", i1)
+    assert i1["converged"] and i1["refinements"] >= 1
+    assert i1["true_rel_residual"] <= 1e-8
+    assert 0.0 < i1["op_rel_diff"] <= OP_TOL
+    # residual of the dense oracle matrix
+    assert relerr(K @ x1, b) <= 2e-8
+    assert relerr(x1, ref) <= 1e-5
+
+
+def test_mixed_gmres_refinement_c2(c2):
+    lf, G, wl = c2["lf"], c2["G"], c2["wl"]
+    b = lf.rhs_plane_wave(G, [math.radians(float(wl.angles_deg[0]))])
+    x0, i0 = lf.gmres_solve(G, b, tol=1e-8, precision=0)
+    x1, i1 = lf.gmres_solve(G, b, tol=1e-8, precision=1)
+    print("C2 FP64:", i0)
+    print("C2 mixed:", i1)
+    assert i0["converged"] and i1["converged"]
+    assert i1["true_rel_residual"] <= 1e-8
+    assert relerr(x1, x0) <= 1e-5
