@@ -171,9 +171,9 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
  *     that overlap on the GPU (other streams or threads) race and must be
  *     serialised by the caller.
  *   - Geometries whose work buffers (sorted x and y, multipole and local
- *     coefficients) exceed the array are rejected with LFMM_ERR_INVALID_ARG
+ *     coefficients, M2L partial sums) exceed the array are rejected with LFMM_ERR_INVALID_ARG
  *     before any device work (C2-sized problems, N = 65536, need about 16 MiB).
- *   - The stage profiler is not run by this call.
+ *   - The stage profiler is not run by this call; the operator is the FP64 one.
  */
 lfmm_status lfmm_matvec_static(lfmm_geometry g, const void *x, void *y, void *stream);
 

@@ -64,6 +64,100 @@ __global__ void k_m2lf_tables(MediumDev m, const int* __restrict__ tl, const int
     }
 }
 
+// Groups of consecutive expansion entries for P2M / L2P: at most
+// EXP_GROUP_PTS points and EXP_GROUP_ENTRIES entries, or one larger entry.
+static std::vector<ExpGroup> make_groups(const std::vector<ExpEntry>& e, int* max_pts, int* max_ent) {
+    std::vector<ExpGroup> gs;
+    int i = 0;
+    while (i < (int)e.size()) {
+        ExpGroup G{i, i + 1, e[i].end - e[i].beg};
+        while (G.e1 < (int)e.size() && G.e1 - G.e0 < EXP_GROUP_ENTRIES && e[G.e1].p == e[G.e0].p &&
+               G.npts + (e[G.e1].end - e[G.e1].beg) <= EXP_GROUP_PTS) {
+            G.npts += e[G.e1].end - e[G.e1].beg;
+            ++G.e1;
+        }
+        *max_pts = std::max(*max_pts, G.npts);
+        *max_ent = std::max(*max_ent, G.e1 - G.e0);
+        gs.push_back(G);
+        i = G.e1;
+    }
+    return gs;
+}
+
+// M2L entry descriptors and work items.  Every list entry of a target box
+// becomes one M2LEnt (source coefficient offset, table, flags: reaction,
+// source in the reaction-centre arrays, arrival/departure directions, output
+// array) so the kernels read one descriptor instead of a chain of lookups.
+// A work item is (target box, chunk of XT_W outputs, range of entries); the
+// entries of a heavy (box, chunk) are split over several items -- at most
+// M2L_ITEM_WORK entry x coefficient units each -- whose partial sums a second
+// kernel adds in a fixed order, so the few large boxes of the coarse levels
+// spread over the GPU instead of running as a handful of long CTAs.
+#define M2L_ITEM_WORK 2048
+static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, const std::vector<int>& vr_src,
+                           const std::vector<int>& vr_key, const std::vector<int>& vr_comp,
+                           const std::vector<ReactKey>& keys) {
+    TreeHost& t = g->tree;
+    const int D = t.D, l0 = t.l0, nlev = D + 1;
+    std::vector<M2LEnt> ents;
+    std::vector<int> ent_ptr(t.nbox + 1, 0);
+    for (int T = 0; T < t.nbox; ++T) {
+        for (int e = g->vf_ptr_host[T]; e < g->vf_ptr_host[T + 1]; ++e)
+            ents.push_back(M2LEnt{g->box_coef_off_host[g->vf_src_host[e]], (int64_t)g->vf_tab_host[e], 0, 0});
+        for (int e = vr_ptr[T]; e < vr_ptr[T + 1]; ++e) {
+            const int S = vr_src[e];
+            const Component& C = t.comps[vr_comp[e]];
+            const int a_dir = C.a, b_dir = C.b;
+            const int ssl = g->slot_of_host[2 * S + (a_dir == 0 ? 0 : 1)];
+            const int side = (b_dir == 0) ? 1 : 0;
+            const int dst = (g->slot_of_host[2 * T + side] >= 0) ? 1 + side : 0;
+            M2LEnt E;
+            E.src = (ssl >= 0) ? g->slot_coef_host[ssl] : g->box_coef_off_host[S];
+            E.tab = keys[vr_key[e]].off;
+            E.flags = M2L_REACT | (ssl >= 0 ? M2L_SRC_SLOT : 0) | (a_dir ? M2L_A_DOWN : 0) | (b_dir ? M2L_B_DOWN : 0) |
+                      (dst << M2L_DST_SHIFT);
+            E.pad = 0;
+            ents.push_back(E);
+        }
+        ent_ptr[T + 1] = (int)ents.size();
+    }
+    std::vector<M2LItem> items;
+    std::vector<M2LReduce> reds;
+    int nparts = 0;
+    g->m2l_item_level_start.assign(nlev + 2, 0);
+    g->m2l_red_level_start.assign(nlev + 2, 0);
+    for (int l = l0; l <= D; ++l) {
+        g->m2l_item_level_start[l] = (int)items.size();
+        g->m2l_red_level_start[l] = (int)reds.size();
+        for (int T = t.level_start[l]; T < t.level_start[l + 1]; ++T) {
+            const int nco = 2 * t.p_level[l] + 1;
+            const int e0 = ent_ptr[T], e1 = ent_ptr[T + 1], ne = e1 - e0;
+            const int per = std::max(1, M2L_ITEM_WORK / nco);   // entries per item
+            const int np = std::max(1, (ne + per - 1) / per);
+            for (int c = 0; c * XT_W < nco; ++c) {
+                if (np == 1) {
+                    items.push_back(M2LItem{T, c, e0, e1, -1});
+                } else {
+                    reds.push_back(M2LReduce{T, c, nparts, np});
+                    for (int q = 0; q < np; ++q)
+                        items.push_back(M2LItem{T, c, e0 + q * per, std::min(e1, e0 + (q + 1) * per), nparts + q});
+                    nparts += np;
+                }
+            }
+        }
+    }
+    for (int l = D + 1; l <= nlev + 1; ++l) {
+        g->m2l_item_level_start[l] = (int)items.size();
+        g->m2l_red_level_start[l] = (int)reds.size();
+    }
+    for (int l = 0; l < l0; ++l) { g->m2l_item_level_start[l] = 0; g->m2l_red_level_start[l] = 0; }
+    g->n_m2l_items = (int)items.size();
+    g->n_m2l_parts = nparts;
+    g->d_m2l_items = dupload(g, items);
+    g->d_m2l_ents = dupload(g, ents);
+    g->d_m2l_reds = dupload(g, reds);
+}
+
 void fmm_build(lfmm_geometry_s* g) {
     TreeHost& t = g->tree;
     const int D = t.D, l0 = t.l0;
@@ -118,6 +212,7 @@ void fmm_build(lfmm_geometry_s* g) {
         g->slot_coef_host = slot_coef;
         g->nslotcoef = sc;
         g->d_slot_of = dupload(g, slot_of);
+        g->slot_of_host = slot_of;
         g->d_slot_coef = dupload(g, slot_coef);
         // P2M entries: leaves about cell centres, straddling boxes about reaction centres
         std::vector<ExpEntry> leaf_e, slot_e, slot_leaf_e;
@@ -132,6 +227,17 @@ void fmm_build(lfmm_geometry_s* g) {
         g->n_leaf_entries = (int)leaf_e.size();
         g->n_slot_entries = (int)slot_e.size();
         g->n_slot_leaf_entries = (int)slot_leaf_e.size();
+        {
+            int mp = 1, me = 1;
+            std::vector<ExpGroup> lg = make_groups(leaf_e, &mp, &me);
+            std::vector<ExpGroup> sg = make_groups(slot_e, &mp, &me);
+            g->n_leaf_groups = (int)lg.size();
+            g->n_slot_groups = (int)sg.size();
+            g->d_leaf_groups = dupload(g, lg);
+            g->d_slot_groups = dupload(g, sg);
+            g->group_max_pts = mp;
+            g->group_max_ent = me;
+        }
         g->d_leaf_entries = dupload(g, leaf_e);
         g->d_slot_entries = dupload(g, slot_e);
         g->d_slot_leaf_entries = dupload(g, slot_leaf_e);
@@ -271,21 +377,9 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_vf_ptr = dupload(g, vf_ptr);
         g->d_vf_src = dupload(g, vf_src);
         g->d_vf_tab = dupload(g, vf_tab);
-        // M2L work items (target box, chunk of output indices), coarse levels first
-        std::vector<M2LItem> items;
-        g->m2l_item_level_start.assign(nlev + 1, 0);
-        for (int T = t.level_start[l0]; T < t.nbox; ++T) {
-            const int nco = 2 * t.p_level[t.box_level[T]] + 1;
-            for (int c = 0; c * XT_W < nco; ++c) items.push_back(M2LItem{T, c});
-        }
-        for (int l = 0; l <= nlev; ++l) {   // first item of each level (items follow box order)
-            int cnt = 0;
-            for (int T = t.level_start[l0]; T < (l <= D ? t.level_start[std::max(l, l0)] : t.nbox); ++T)
-                cnt += (2 * t.p_level[t.box_level[T]] + 1 + XT_W - 1) / XT_W;
-            g->m2l_item_level_start[l] = cnt;
-        }
-        g->n_m2l_items = (int)items.size();
-        g->d_m2l_items = dupload(g, items);
+        g->vf_ptr_host = vf_ptr;
+        g->vf_src_host = vf_src;
+        g->vf_tab_host = vf_tab;
         int ntab = (int)tl.size();
         if (ntab > 0) {
             int* d_tl = dupload(g, tl); int* d_tlev = dupload(g, tlev);
@@ -339,6 +433,7 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_vr_src = dupload(g, vr_src);
         g->d_vr_key = dupload(g, vr_key);
         g->d_vr_comp = dupload(g, vr_comp);
+        build_m2l_work(g, vr_ptr, vr_src, vr_key, vr_comp, keys);
         g->d_rkeys = dupload(g, keys);
         g->rkeys_host = keys;
         g->d_m2lr = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
@@ -382,6 +477,9 @@ static void ensure_coef(lfmm_geometry_s* g, int nrhs) {
 }
 
 void fmm_free(lfmm_geometry_s* g) {
+    if (g->d_m2l_part) cudaFree(g->d_m2l_part);
+    g->d_m2l_part = nullptr;
+    g->m2l_part_cols = 0;
     if (g->d_M) { cudaFree(g->d_M); cudaFree(g->d_L); }
     if (g->d_Mp) { cudaFree(g->d_Mp); cudaFree(g->d_Lp); }
     g->d_M = g->d_L = g->d_Mp = g->d_Lp = nullptr;
@@ -397,17 +495,27 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     const int pD = t.p_level[D];
     int pmax = 0;
     for (int l = l0; l <= D; ++l) pmax = std::max(pmax, t.p_level[l]);
-    {   // P2M: leaves about cell centres, straddling boxes about reaction centres
+    // shared memory of the grouped P2M / L2P kernels (same order p = p_D for every entry)
+    const int gp = g->group_max_pts, ge = g->group_max_ent;
+    const size_t smem_p2m = (size_t)gp * (pD + 1) * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
+    const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * (2 * pD + 1) * sizeof(cd);
+    if (smem_p2m > g->smem_p2m_set) {
+        cuda_check(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2m), "p2m smem");
+        g->smem_p2m_set = smem_p2m;
+    }
+    if (smem_l2p > g->smem_l2p_set) {
+        cuda_check(cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l2p), "l2p smem");
+        g->smem_l2p_set = smem_l2p;
+    }
+    {   // P2M: leaves about cell centres, straddling leaves about reaction centres
         prof_begin(g, ST_P2M, s);
-        size_t smem = (size_t)(32 * (pD + 1)) * sizeof(double) + (size_t)(32 * (pD + 1) + 32) * sizeof(cd);
-        k_p2m<<<g->n_leaf_entries, 128, smem, s>>>(g->d_leaf_entries, g->m, g->d_x, g->d_y, g->d_w, x_sorted, g->n,
-                                                   nrhs, g->ncoef, g->d_M);
+        k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
+                                                      g->d_w, x_sorted, g->n, nrhs, g->ncoef, g->d_M);
         cuda_check(cudaGetLastError(), "k_p2m");
         ++g->n_launches;
-        if (g->n_slot_entries > 0) {
-            size_t sm2 = (size_t)(32 * (pmax + 1)) * sizeof(double) + (size_t)(32 * (pmax + 1) + 32) * sizeof(cd);
-            k_p2m<<<g->n_slot_entries, 128, sm2, s>>>(g->d_slot_entries, g->m, g->d_x, g->d_y, g->d_w, x_sorted,
-                                                      g->n, nrhs, g->nslotcoef, g->d_Mp);
+        if (g->n_slot_groups > 0) {
+            k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x, g->d_y,
+                                                          g->d_w, x_sorted, g->n, nrhs, g->nslotcoef, g->d_Mp);
             cuda_check(cudaGetLastError(), "k_p2m slots");
             ++g->n_launches;
         }
@@ -424,20 +532,34 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         ++g->n_launches;
     }
     prof_end(g, ST_M2M, s);
-    {   // M2L, all levels
+    {   // M2L, all levels (precision form: the levels >= mixed_level in FP32)
         prof_begin(g, ST_M2L, s);
-        // precision form: levels coarser than mixed_min_level keep the FP64 kernel
         const int lm = mixed ? std::max(l0, std::min(mixed_level(g), D + 1)) : D + 1;
         const int n64 = g->m2l_item_level_start[lm];
-        if (mixed) mixed_m2l(g, nrhs, lm, s);
-        if (n64 > 0) {
-        k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr, g->d_vf_src,
-                                     g->d_vf_tab, g->d_m2lf, g->d_m2lf_off, g->d_vr_ptr, g->d_vr_src, g->d_vr_key,
-                                     g->d_vr_comp, g->d_comp, g->d_rkeys, g->d_m2lr, nrhs, g->ncoef, g->d_M,
-                                     g->d_L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, g->d_Mp, g->d_Lp);
-        cuda_check(cudaGetLastError(), "k_m2l");
-        ++g->n_launches;
+        const int r64 = g->m2l_red_level_start[lm];
+        if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
+            if (g->d_m2l_part) cudaFree(g->d_m2l_part);
+            g->d_m2l_part = nullptr;
+            cuda_check(cudaMalloc(&g->d_m2l_part, sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * nrhs),
+                       "cudaMalloc M2L partial sums");
+            g->m2l_part_cols = nrhs;
         }
+        if (n64 > 0) {
+            k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                      g->d_slot_of, g->d_slot_coef, g->d_m2lf, g->d_m2lf_off, g->d_m2lr, nrhs,
+                                      g->ncoef, g->nslotcoef, g->n_m2l_parts, g->d_M, g->d_Mp, g->d_L, g->d_Lp,
+                                      g->d_m2l_part);
+            cuda_check(cudaGetLastError(), "k_m2l");
+            ++g->n_launches;
+        }
+        if (r64 > 0) {
+            k_m2l_reduce<<<r64, 64, 0, s>>>(g->d_m2l_reds, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_slot_of,
+                                            g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts,
+                                            g->d_m2l_part, g->d_L, g->d_Lp);
+            cuda_check(cudaGetLastError(), "k_m2l_reduce");
+            ++g->n_launches;
+        }
+        if (mixed) mixed_m2l(g, nrhs, lm, s);
         prof_end(g, ST_M2L, s);
     }
     prof_begin(g, ST_L2L, s);
@@ -453,15 +575,13 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     prof_end(g, ST_L2L, s);
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
         prof_begin(g, ST_L2P, s);
-        int threads = 64;
-        size_t smem = (size_t)(2 * (2 * pD + 1)) * sizeof(double) + (size_t)threads * (pD + 1) * sizeof(double);
-        k_l2p<<<g->n_leaf_entries, threads, smem, s>>>(g->d_leaf_entries, g->m, g->d_x, g->d_y, g->n, nrhs, g->ncoef,
-                                                       g->d_L, y_sorted);
+        k_l2p<<<g->n_leaf_groups, 128, smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
+                                                      g->n, nrhs, g->ncoef, g->d_L, y_sorted);
         cuda_check(cudaGetLastError(), "k_l2p");
         ++g->n_launches;
-        if (g->n_slot_leaf_entries > 0) {
-            k_l2p<<<g->n_slot_leaf_entries, threads, smem, s>>>(g->d_slot_leaf_entries, g->m, g->d_x, g->d_y, g->n,
-                                                                nrhs, g->nslotcoef, g->d_Lp, y_sorted);
+        if (g->n_slot_groups > 0) {
+            k_l2p<<<g->n_slot_groups, 128, smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->m, g->d_x,
+                                                          g->d_y, g->n, nrhs, g->nslotcoef, g->d_Lp, y_sorted);
             cuda_check(cudaGetLastError(), "k_l2p slots");
             ++g->n_launches;
         }

@@ -32,77 +32,105 @@ struct ExpEntry {
     int64_t off;   // coefficient offset in the output/input array
 };
 
-__global__ void k_p2m(const ExpEntry* __restrict__ ent, MediumDev m, const double* __restrict__ px,
-                      const double* __restrict__ py, const double* __restrict__ pw, const cd* __restrict__ phi,
-                      int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
-    extern __shared__ double sm[];
-    const ExpEntry E = ent[blockIdx.x];
-    const int p = E.p, np1 = p + 1;
-    double* J = sm;                          // [32][p+1]
-    cd* zp = (cd*)(sm + 32 * np1);           // [32][p+1]   z^n, z = e^{-i theta}
-    cd* q = zp + 32 * np1;                   // [32] charges of the current column
-    const int b0 = E.beg, nb = E.end - E.beg;
-    const double k = m.k[E.lay];
-    const int nco = 2 * p + 1;
-    for (int col = 0; col < nrhs; ++col) {
-        // accumulators: thread t owns coefficient indices t, t+128
-        cd acc[2] = {mk(0, 0), mk(0, 0)};
-        for (int c0 = 0; c0 < nb; c0 += 32) {
-            const int cnt = min(32, nb - c0);
-            __syncthreads();
-            if (threadIdx.x < cnt) {
-                const int j = b0 + c0 + threadIdx.x;
-                double dx = px[j] - E.cx, dy = py[j] - E.cy;
-                double rho = hypot(dx, dy);
-                bessel_j_seq(k * rho, p, J + threadIdx.x * np1);
-                cd z = (rho > 0.0) ? mk(dx / rho, -dy / rho) : mk(1.0, 0.0);
-                cd zz = mk(1.0, 0.0);
-                for (int t = 0; t <= p; ++t) { zp[threadIdx.x * np1 + t] = zz; zz = zz * z; }
-                q[threadIdx.x] = pw[j] * phi[(int64_t)col * n + j];
-            }
-            __syncthreads();
-            for (int s = 0; s < 2; ++s) {
-                int idx = threadIdx.x + 128 * s;
-                if (idx >= nco) break;
-                int nn = idx - p;
-                int an = nn < 0 ? -nn : nn;
-                cd a = acc[s];
-                for (int j = 0; j < cnt; ++j) {
-                    double jv = J[j * np1 + an];
-                    cd zn = zp[j * np1 + an];
-                    if (nn < 0) { zn = conjc(zn); if (an & 1) jv = -jv; }
-                    cfma(a, jv * q[j], zn);
-                }
-                acc[s] = a;
-            }
+// Consecutive expansion entries whose points are processed by one CTA together
+// (at most EXP_GROUP_PTS points, or a single larger entry).
+#define EXP_GROUP_PTS 128
+#define EXP_GROUP_ENTRIES 16
+struct ExpGroup {
+    int e0, e1;    // entry range
+    int npts;      // points of the group
+};
+
+// Point t of a group: its entry (relative index) and point index.
+__device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, int e0, int e1, int t, int* er, int* j) {
+    int e = e0, base = 0;
+    while (e + 1 < e1 && t >= base + (ent[e].end - ent[e].beg)) { base += ent[e].end - ent[e].beg; ++e; }
+    *er = e - e0;
+    *j = ent[e].beg + (t - base);
+}
+
+// P2M about the entries' centres (leaves about cell centres, straddling leaves
+// about their reaction centres): M_n = sum_j q_j J_n(k rho_j) e^{-i n theta_j},
+// q_j = |Gamma_j| phi_j.  Phase 1, one thread per point of the group:
+// u_{j,n} = J_n(k rho_j) e^{-i n theta_j}, n = 0..p, into shared memory.
+// Phase 2, one thread per (entry, coefficient): the sum over the entry's points,
+// with M_{-n} from u_{j,n} by J_{-n} = (-1)^n J_n and e^{+i n theta} = conj.
+__global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
+                      const double* __restrict__ pw, const cd* __restrict__ phi, int64_t n, int nrhs,
+                      int64_t stride, cd* __restrict__ M) {
+    extern __shared__ cd su[];   // [npts][p+1] u, then [npts] q, then [nent + 1] point offsets (as ints)
+    const ExpGroup G = groups[blockIdx.x];
+    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int ne = G.e1 - G.e0;
+    cd* sq = su + (size_t)G.npts * np1;
+    int* soff = (int*)(sq + G.npts);
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int e = 0; e < ne; ++e) { soff[e] = o; o += ent[G.e0 + e].end - ent[G.e0 + e].beg; }
+        soff[ne] = o;
+    }
+    for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+        int er, j;
+        group_point(ent, G.e0, G.e1, t, &er, &j);
+        const ExpEntry& E = ent[G.e0 + er];
+        const double dx = px[j] - E.cx, dy = py[j] - E.cy;
+        const double rho = hypot(dx, dy);
+        cd* u = su + (size_t)t * np1;
+        bessel_j_seq(m.k[E.lay] * rho, p, (double*)u);   // J_0..J_p packed in the first p+1 doubles
+        // spread J_n into u_n = J_n z^n, z = e^{-i theta}, from the top so nothing is overwritten early
+        const cd z = (rho > 0.0) ? mk(dx / rho, -dy / rho) : mk(1.0, 0.0);
+        // z^p by repeated squaring, then walk down with z^{n-1} = z^n conj(z)
+        cd zp = mk(1.0, 0.0), bb = z;
+        for (int e2 = p; e2 > 0; e2 >>= 1) { if (e2 & 1) zp = zp * bb; bb = bb * bb; }
+        const double* Jd = (const double*)u;
+        for (int k2 = p; k2 >= 0; --k2) {
+            const double jv = Jd[k2];   // read before u[k2] (which covers doubles 2k2, 2k2+1 >= k2) is written
+            u[k2] = jv * zp;
+            zp = zp * conjc(z);
         }
-        for (int s = 0; s < 2; ++s) {
-            int idx = threadIdx.x + 128 * s;
-            if (idx < nco) M[(int64_t)col * stride + E.off + idx] = acc[s];
+    }
+    for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+            int er, j;
+            group_point(ent, G.e0, G.e1, t, &er, &j);
+            sq[t] = pw[j] * phi[(int64_t)col * n + j];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < ne * nco; task += blockDim.x) {
+            const int er = task / nco, idx = task - er * nco;
+            const int nn = idx - p, an = nn < 0 ? -nn : nn;
+            cd a = mk(0, 0);
+            for (int t = soff[er]; t < soff[er + 1]; ++t) {
+                cd v = su[(size_t)t * np1 + an];
+                if (nn < 0) { v = conjc(v); if (an & 1) v = -v; }
+                cfma(a, sq[t], v);
+            }
+            M[(int64_t)col * stride + ent[G.e0 + er].off + idx] = a;
         }
     }
 }
 
-// M2L into every target box of levels >= l0 (free space and reaction components).
-// Work item = (target box, chunk of XT_W output indices); a CTA of 128 threads
-// holds XT_W output lanes x 8 slices of the sum over the source index, for
-// every list entry of the target in turn, and reduces the slices in a fixed
-// order at the end.  Free space (Graf): L_n += sum_m M_m T[m - n].  Reaction
-// (eq. generalintegral): beta_m = sum_n I[m][n] alpha_n with the arrival and
-// departure index flips; tables are stored column-major (entry (m, n) at
-// n (2p+1) + m) so the lanes of a row read consecutive addresses.
-__global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const int* __restrict__ box_level,
-                      const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
-                      const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
-                      const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
-                      const int* __restrict__ vr_ptr, const int* __restrict__ vr_src,
-                      const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
-                      const int* __restrict__ comp, const ReactKey* __restrict__ rkeys,
-                      const cd* __restrict__ m2lr, int nrhs, int64_t ncoef, const cd* __restrict__ Min,
-                      cd* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
-                      int64_t nslotcoef, const cd* __restrict__ Mp, cd* __restrict__ Lp) {
+// M2L into the target boxes of levels >= l0 (free space and reaction components).
+// A CTA of 128 threads takes one work item: XT_W output lanes x 8 slices of the
+// sum over the source index, over the item's range of list entries, whose
+// descriptors are staged in shared memory 64 at a time; the slices are reduced
+// in a fixed order at the end.  Free space (Graf): L_n += sum_m M_m T[m - n]
+// (Toeplitz vector per table).  Reaction (eq. generalintegral): beta_m =
+// sum_n I[m][n] alpha_n with the arrival and departure index flips; moment
+// tables are column-major (entry (m, n) at n (2p+1) + m).
+#define M2L_STAGE 64
+__global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
+                      const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                      const int64_t* __restrict__ slot_coef, const cd* __restrict__ m2lf,
+                      const int64_t* __restrict__ m2lf_off, const cd* __restrict__ m2lr, int nrhs, int64_t ncoef,
+                      int64_t nslotcoef, int nparts, const cd* __restrict__ Min, const cd* __restrict__ Mp,
+                      cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
     constexpr int NS = 128 / XT_W;
     __shared__ cd red[3][NS][XT_W];
+    __shared__ M2LEnt se[M2L_STAGE];
     const M2LItem it = items[blockIdx.x];
     const int T = it.box;
     const int p = p_level[box_level[T]];
@@ -111,43 +139,44 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
     const int idx = it.chunk * XT_W + lane;
     const bool live = idx < nco;
     const int nn = idx - p;
-    const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
-    const int f0 = vf_ptr[T], f1 = vf_ptr[T + 1];
-    const int r0 = vr_ptr[T], r1 = vr_ptr[T + 1];
     for (int col = 0; col < nrhs; ++col) {
         const cd* Mc = Min + (int64_t)col * ncoef;
         const cd* Mpc = Mp + (int64_t)col * nslotcoef;
-        cd acc0 = mk(0, 0), acc1 = mk(0, 0), acc2 = mk(0, 0);   // L, side-0 slot, side-1 slot
-        if (live) {
-            for (int e = f0; e < f1; ++e) {
-                const cd* src = Mc + coef_off[vf_src[e]];
-                const cd* tb = m2lf + m2lf_off[vf_tab[e]] + p - nn;   // T[m - n], index (mi - p) - nn + 2p
-                for (int mi = sl; mi < nco; mi += NS) cfma(acc0, src[mi], tb[mi]);
-            }
-            for (int e = r0; e < r1; ++e) {
-                const int S = vr_src[e], c = vr_comp[e];
-                const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
-                // source expansion about the reaction centre if S straddles the arrival interface
-                const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
-                const cd* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
-                // departure down: L_n += beta_n;  departure up: L_{-n} += (-1)^n beta_n
-                const int mrow = (b_dir == 1) ? nn : -nn;
-                const cd* col_m = m2lr + rkeys[vr_key[e]].off + (mrow + p);
-                cd bsum = mk(0, 0);
-                if (a_dir == 1) {   // alpha_i = M_i
-                    for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[(int64_t)mi * nco], src[mi]);
-                } else {            // alpha_i = (-1)^(i-p) M_{2p-i}
-                    for (int mi = sl; mi < nco; mi += NS) {
-                        cd v = src[2 * p - mi];
-                        if ((mi - p) & 1) v = -v;
-                        cfma(bsum, col_m[(int64_t)mi * nco], v);
+        cd acc0 = mk(0, 0), acc1 = mk(0, 0), acc2 = mk(0, 0);   // L, side-0 / side-1 reaction centre
+        for (int eb = it.e0; eb < it.e1; eb += M2L_STAGE) {
+            const int cnt = min(M2L_STAGE, it.e1 - eb);
+            __syncthreads();
+            if (threadIdx.x < cnt) se[threadIdx.x] = ents[eb + threadIdx.x];
+            __syncthreads();
+            if (!live) continue;
+            for (int q = 0; q < cnt; ++q) {
+                const M2LEnt E = se[q];
+                if (!(E.flags & M2L_REACT)) {
+                    const cd* src = Mc + E.src;
+                    const cd* tb = m2lf + m2lf_off[E.tab] + p - nn;   // T[m - n] at (mi - p) - nn + 2p
+                    for (int mi = sl; mi < nco; mi += NS) cfma(acc0, src[mi], tb[mi]);
+                } else {
+                    const cd* src = ((E.flags & M2L_SRC_SLOT) ? Mpc : Mc) + E.src;
+                    const bool bdown = (E.flags & M2L_B_DOWN) != 0;
+                    // departure down: L_n += beta_n;  departure up: L_{-n} += (-1)^n beta_n
+                    const int mrow = bdown ? nn : -nn;
+                    const cd* col_m = m2lr + E.tab + (mrow + p);
+                    cd bsum = mk(0, 0);
+                    if (E.flags & M2L_A_DOWN) {   // alpha_i = M_i
+                        for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[(int64_t)mi * nco], src[mi]);
+                    } else {                      // alpha_i = (-1)^(i-p) M_{2p-i}
+                        for (int mi = sl; mi < nco; mi += NS) {
+                            cd v = src[2 * p - mi];
+                            if ((mi - p) & 1) v = -v;
+                            cfma(bsum, col_m[(int64_t)mi * nco], v);
+                        }
                     }
+                    if (!bdown && (mrow & 1)) bsum = -bsum;
+                    const int dst = E.flags >> M2L_DST_SHIFT;
+                    if (dst == 0) acc0 += bsum;
+                    else if (dst == 1) acc1 += bsum;
+                    else acc2 += bsum;
                 }
-                if (b_dir == 0 && (mrow & 1)) bsum = -bsum;
-                const int side = (b_dir == 0) ? 1 : 0;
-                if (tslot[side] < 0) acc0 += bsum;
-                else if (side == 0) acc1 += bsum;
-                else acc2 += bsum;
             }
         }
         red[0][sl][lane] = acc0;
@@ -156,55 +185,76 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
         __syncthreads();
         if (live && sl < 3) {
             const int k = sl;
-            if (k == 0 || tslot[k - 1] >= 0) {
-                cd t = red[k][0][lane];
-                for (int q = 1; q < NS; ++q) t += red[k][q][lane];
+            cd t = red[k][0][lane];
+            for (int q = 1; q < NS; ++q) t += red[k][q][lane];
+            if (it.part >= 0) {
+                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + lane] = t;
+            } else {
+                const int ts = (k == 0) ? -1 : slot_of[2 * T + k - 1];
                 if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
-                else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
+                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
             }
         }
         __syncthreads();
     }
 }
+// Sum the partial results of split (box, chunk)s in part order and write them.
+__global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__ reds,
+                      const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                      const int64_t* __restrict__ slot_coef, int nrhs, int64_t ncoef, int64_t nslotcoef, int nparts,
+                      const cd* __restrict__ part, cd* __restrict__ Lout, cd* __restrict__ Lp) {
+    const M2LReduce r = reds[blockIdx.x];
+    const int p = p_level[box_level[r.box]];
+    const int lane = threadIdx.x % XT_W, k = threadIdx.x / XT_W;   // k < 4; 3 used
+    const int idx = r.chunk * XT_W + lane;
+    if (k >= 3 || idx >= 2 * p + 1) return;
+    const int ts = (k == 0) ? -1 : slot_of[2 * r.box + k - 1];
+    if (k > 0 && ts < 0) return;
+    for (int col = 0; col < nrhs; ++col) {
+        cd t = mk(0, 0);
+        for (int q = 0; q < r.nparts; ++q) t += part[(((int64_t)col * nparts + r.part0 + q) * 3 + k) * XT_W + lane];
+        if (k == 0) Lout[(int64_t)col * ncoef + coef_off[r.box] + idx] = t;
+        else Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
+    }
+}
 
 // L2P over a list of point ranges: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
 // about (cx, cy).  Leaves (cell centres) and straddling leaves (reaction centres).
-__global__ void k_l2p(const ExpEntry* __restrict__ ent, MediumDev m, const double* __restrict__ px,
-                      const double* __restrict__ py, int64_t n, int nrhs, int64_t stride,
-                      const cd* __restrict__ L, cd* __restrict__ y) {
-    extern __shared__ double sl[];
-    const ExpEntry E = ent[blockIdx.x];
-    const int p = E.p, np1 = p + 1, nco = 2 * p + 1;
-    cd* Ls = (cd*)sl;                               // [nco]
-    double* Jall = sl + 2 * nco;                     // [blockDim][p+1]
-    const int b0 = E.beg, nb = E.end - E.beg;
-    const double k = m.k[E.lay];
-    double* J = Jall + threadIdx.x * np1;
-    for (int c0 = 0; c0 < nb; c0 += blockDim.x) {
-        const int j = b0 + c0 + threadIdx.x;
-        const bool act = (c0 + threadIdx.x) < nb;
-        cd z = mk(1.0, 0.0);
-        if (act) {
-            double dx = px[j] - E.cx, dy = py[j] - E.cy;
-            double rho = hypot(dx, dy);
-            bessel_j_seq(k * rho, p, J);
-            if (rho > 0.0) z = mk(dx / rho, dy / rho);
+__global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
+                      int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
+    extern __shared__ double sj[];   // [npts][p+1] J_n, then [nent][2p+1] coefficients
+    const ExpGroup G = groups[blockIdx.x];
+    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int ne = G.e1 - G.e0;
+    cd* sL = (cd*)(sj + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
+    for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < ne * nco; i += blockDim.x) {
+            const int er = i / nco, idx = i - er * nco;
+            sL[i] = L[(int64_t)col * stride + ent[G.e0 + er].off + idx];
         }
-        for (int col = 0; col < nrhs; ++col) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < nco; i += blockDim.x) Ls[i] = L[(int64_t)col * stride + E.off + i];
-            __syncthreads();
-            if (act) {
-                cd acc = Ls[p] * J[0];
-                cd zz = mk(1.0, 0.0);
-                for (int t = 1; t <= p; ++t) {
-                    zz = zz * z;
-                    double jt = J[t];
-                    cfma(acc, jt * Ls[p + t], zz);
-                    cfma(acc, ((t & 1) ? -jt : jt) * Ls[p - t], conjc(zz));
-                }
-                y[(int64_t)col * n + j] += acc;
+        __syncthreads();
+        for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+            int er, j;
+            group_point(ent, G.e0, G.e1, t, &er, &j);
+            const ExpEntry& E = ent[G.e0 + er];
+            const double dx = px[j] - E.cx, dy = py[j] - E.cy;
+            const double rho = hypot(dx, dy);
+            double* J = sj + (size_t)t * np1;
+            if (col == 0) bessel_j_seq(m.k[E.lay] * rho, p, J);
+            const cd z = (rho > 0.0) ? mk(dx / rho, dy / rho) : mk(1.0, 0.0);
+            const cd* Le = sL + er * nco;
+            cd acc = Le[p] * J[0];
+            cd zz = mk(1.0, 0.0);
+            for (int k2 = 1; k2 <= p; ++k2) {
+                zz = zz * z;
+                const double jt = J[k2];
+                cfma(acc, jt * Le[p + k2], zz);
+                cfma(acc, ((k2 & 1) ? -jt : jt) * Le[p - k2], conjc(zz));
             }
+            y[(int64_t)col * n + j] += acc;
         }
     }
 }

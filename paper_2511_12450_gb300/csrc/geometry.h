@@ -40,12 +40,28 @@ struct QuadRule {
 };
 
 struct ExpEntry;
+struct ExpGroup;
 struct XDst;
 struct XSrc;
-// M2L work item: one target box and one chunk of XT_W output coefficients
+// M2L work: XT_W output coefficients of one target box over a range of its
+// list entries; part >= 0 sends the partial sums to the reduction buffer.
 #define XT_W 16
 struct M2LItem {
     int box, chunk;
+    int e0, e1;       // entry range (M2LEnt indices)
+    int part;         // -1: write L directly; else partial-sum slot
+};
+// one list entry of a target box
+enum { M2L_REACT = 1, M2L_SRC_SLOT = 2, M2L_A_DOWN = 4, M2L_B_DOWN = 8, M2L_DST_SHIFT = 4 };
+struct M2LEnt {
+    int64_t src;      // source coefficient offset (M, or Mp with M2L_SRC_SLOT)
+    int64_t tab;      // free space: table id; reaction: offset of the moment table
+    int flags;        // M2L_* bits; output array (0 = L, 1/2 = side-0/1 reaction centre) at M2L_DST_SHIFT
+    int pad;
+};
+// a (box, chunk) whose entries were split: parts [part0, part0 + nparts)
+struct M2LReduce {
+    int box, chunk, part0, nparts;
 };
 struct MixedState;
 
@@ -103,6 +119,9 @@ struct lfmm_geometry_s {
     // P2M/L2P work lists (leaves about cell centres; straddling boxes/leaves about reaction centres)
     int n_leaf_entries = 0, n_slot_entries = 0, n_slot_leaf_entries = 0;
     lfmm::ExpEntry *d_leaf_entries = nullptr, *d_slot_entries = nullptr, *d_slot_leaf_entries = nullptr;
+    lfmm::ExpGroup *d_leaf_groups = nullptr, *d_slot_groups = nullptr;   // P2M / L2P work groups
+    int n_leaf_groups = 0, n_slot_groups = 0, group_max_pts = 1, group_max_ent = 1;
+    size_t smem_p2m_set = 48 * 1024, smem_l2p_set = 48 * 1024;   // opt-in shared memory already granted
     // M2M (up) and L2L (down) passes: per level, a range of destinations
     // (cells and reaction centres) with their sources and translation vectors
     std::vector<int> up_begin, up_end, dn_begin, dn_end;
@@ -121,9 +140,15 @@ struct lfmm_geometry_s {
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
     int64_t *d_m2lf_off = nullptr;
     int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids
-    lfmm::M2LItem* d_m2l_items = nullptr;   // (target box, output chunk), coarse levels first
-    int n_m2l_items = 0;
-    std::vector<int> m2l_item_level_start;  // [nlev + 1]: first item of each level (level D + 1: the end)
+    lfmm::M2LItem* d_m2l_items = nullptr;   // coarse levels first
+    lfmm::M2LEnt* d_m2l_ents = nullptr;     // entry descriptors, per target box in list order
+    lfmm::M2LReduce* d_m2l_reds = nullptr;  // split (box, chunk)s
+    int n_m2l_items = 0, n_m2l_parts = 0;
+    std::vector<int> m2l_item_level_start;  // [nlev + 2]: first item of each level (levels > D: the end)
+    std::vector<int> m2l_red_level_start;   // same for the reductions
+    cd* d_m2l_part = nullptr;               // partial sums [cols][n_m2l_parts][3][XT_W]
+    int m2l_part_cols = 0;
+    std::vector<int> vf_ptr_host, vf_src_host, vf_tab_host, slot_of_host;
     cd *d_m2lr = nullptr;             // reaction M2L tables
     int *d_vr_ptr = nullptr, *d_vr_src = nullptr, *d_vr_key = nullptr, *d_vr_comp = nullptr;
     lfmm::ReactKey* d_rkeys = nullptr;

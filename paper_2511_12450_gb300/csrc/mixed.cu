@@ -42,6 +42,7 @@ struct MixedState {
     int cols = 0;                       // right-hand-side columns the FP32 buffers hold
     cf *M = nullptr, *L = nullptr;      // [cols][ncoef]   scaled multipoles / locals
     cf *Mp = nullptr, *Lp = nullptr;    // [cols][nslotcoef]
+    cf *part = nullptr;                 // M2L partial sums [cols][parts][3][XT_W]
     double *ispow = nullptr;            // [ncoef]      s^-|n| per coefficient
     double *ispow_slot = nullptr;       // [nslotcoef]
     cf *ftab = nullptr;                 // scaled dense free-space tables
@@ -147,20 +148,20 @@ __global__ void k_from32(const cf* __restrict__ in, const double* __restrict__ i
 }
 
 // ---------------------------------------------------------------------------
-// M2L in FP32 on the scaled expansions; the same work items, lane/slice split and
-// index flips as the FP64 kernel, with dense tables for the free-space part too.
-__global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items, const int* __restrict__ box_level,
-                        const int* __restrict__ p_level, const int64_t* __restrict__ coef_off,
-                        const int* __restrict__ vf_ptr, const int* __restrict__ vf_src, const int* __restrict__ vf_tab,
-                        const cf* __restrict__ ftab, const int64_t* __restrict__ ftab_off,
-                        const int* __restrict__ vr_ptr, const int* __restrict__ vr_src,
-                        const int* __restrict__ vr_key, const int* __restrict__ vr_comp,
-                        const int* __restrict__ comp, const ReactKey* __restrict__ rkeys,
-                        const cf* __restrict__ rtab, int nrhs, int64_t ncoef, const cf* __restrict__ Min,
-                        cf* __restrict__ Lout, const int* __restrict__ slot_of, const int64_t* __restrict__ slot_coef,
-                        int64_t nslotcoef, const cf* __restrict__ Mp, cf* __restrict__ Lp) {
+// M2L in FP32 on the scaled expansions: the same work items, entry descriptors,
+// lane/slice split, index flips and partial-sum reduction as the FP64 kernel,
+// with dense tables for the free-space part too.
+#define M2L_STAGE32 64
+__global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
+                        const int* __restrict__ box_level, const int* __restrict__ p_level,
+                        const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                        const int64_t* __restrict__ slot_coef, const cf* __restrict__ ftab,
+                        const int64_t* __restrict__ ftab_off, const cf* __restrict__ rtab, int nrhs, int64_t ncoef,
+                        int64_t nslotcoef, int nparts, const cf* __restrict__ Min, const cf* __restrict__ Mp,
+                        cf* __restrict__ Lout, cf* __restrict__ Lp, cf* __restrict__ part) {
     constexpr int NS = 128 / XT_W;
     __shared__ cf red[3][NS][XT_W];
+    __shared__ M2LEnt se[M2L_STAGE32];
     const M2LItem it = items[blockIdx.x];
     const int T = it.box;
     const int p = p_level[box_level[T]];
@@ -169,41 +170,43 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
     const int idx = it.chunk * XT_W + lane;
     const bool live = idx < nco;
     const int nn = idx - p;
-    const int tslot[2] = {slot_of[2 * T], slot_of[2 * T + 1]};
-    const int f0 = vf_ptr[T], f1 = vf_ptr[T + 1];
-    const int r0 = vr_ptr[T], r1 = vr_ptr[T + 1];
     for (int col = 0; col < nrhs; ++col) {
         const cf* Mc = Min + (int64_t)col * ncoef;
         const cf* Mpc = Mp + (int64_t)col * nslotcoef;
-        cf acc0 = mkf(0, 0), acc1 = mkf(0, 0), acc2 = mkf(0, 0);   // L, side-0 slot, side-1 slot
-        if (live) {
-            for (int e = f0; e < f1; ++e) {
-                const cf* src = Mc + coef_off[vf_src[e]];
-                const cf* tb = ftab + ftab_off[vf_tab[e]] + idx;   // (n_out, m_in) at m_in nco + n_out
-                for (int mi = sl; mi < nco; mi += NS) cfmaf(acc0, src[mi], tb[(int64_t)mi * nco]);
-            }
-            for (int e = r0; e < r1; ++e) {
-                const int S = vr_src[e], c = vr_comp[e];
-                const int a_dir = comp[4 * c + 1], b_dir = comp[4 * c + 3];
-                const int ssl = slot_of[2 * S + (a_dir == 0 ? 0 : 1)];
-                const cf* src = (ssl >= 0) ? (Mpc + slot_coef[ssl]) : (Mc + coef_off[S]);
-                const int mrow = (b_dir == 1) ? nn : -nn;
-                const cf* col_m = rtab + rkeys[vr_key[e]].off + (mrow + p);
-                cf bsum = mkf(0, 0);
-                if (a_dir == 1) {
-                    for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[(int64_t)mi * nco], src[mi]);
+        cf acc0 = mkf(0, 0), acc1 = mkf(0, 0), acc2 = mkf(0, 0);
+        for (int eb = it.e0; eb < it.e1; eb += M2L_STAGE32) {
+            const int cnt = min(M2L_STAGE32, it.e1 - eb);
+            __syncthreads();
+            if (threadIdx.x < cnt) se[threadIdx.x] = ents[eb + threadIdx.x];
+            __syncthreads();
+            if (!live) continue;
+            for (int q = 0; q < cnt; ++q) {
+                const M2LEnt E = se[q];
+                if (!(E.flags & M2L_REACT)) {
+                    const cf* src = Mc + E.src;
+                    const cf* tb = ftab + ftab_off[E.tab] + idx;   // (n_out, m_in) at m_in nco + n_out
+                    for (int mi = sl; mi < nco; mi += NS) cfmaf(acc0, src[mi], tb[mi * nco]);
                 } else {
-                    for (int mi = sl; mi < nco; mi += NS) {
-                        cf v = src[2 * p - mi];
-                        if ((mi - p) & 1) v = mkf(-v.x, -v.y);
-                        cfmaf(bsum, col_m[(int64_t)mi * nco], v);
+                    const cf* src = ((E.flags & M2L_SRC_SLOT) ? Mpc : Mc) + E.src;
+                    const bool bdown = (E.flags & M2L_B_DOWN) != 0;
+                    const int mrow = bdown ? nn : -nn;
+                    const cf* col_m = rtab + E.tab + (mrow + p);
+                    cf bsum = mkf(0, 0);
+                    if (E.flags & M2L_A_DOWN) {
+                        for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[mi * nco], src[mi]);
+                    } else {
+                        for (int mi = sl; mi < nco; mi += NS) {
+                            cf v = src[2 * p - mi];
+                            if ((mi - p) & 1) v = mkf(-v.x, -v.y);
+                            cfmaf(bsum, col_m[mi * nco], v);
+                        }
                     }
+                    if (!bdown && (mrow & 1)) bsum = mkf(-bsum.x, -bsum.y);
+                    const int dst = E.flags >> M2L_DST_SHIFT;
+                    if (dst == 0) acc0 = addf(acc0, bsum);
+                    else if (dst == 1) acc1 = addf(acc1, bsum);
+                    else acc2 = addf(acc2, bsum);
                 }
-                if (b_dir == 0 && (mrow & 1)) bsum = mkf(-bsum.x, -bsum.y);
-                const int side = (b_dir == 0) ? 1 : 0;
-                if (tslot[side] < 0) acc0 = addf(acc0, bsum);
-                else if (side == 0) acc1 = addf(acc1, bsum);
-                else acc2 = addf(acc2, bsum);
             }
         }
         red[0][sl][lane] = acc0;
@@ -212,21 +215,43 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
         __syncthreads();
         if (live && sl < 3) {
             const int k = sl;
-            if (k == 0 || tslot[k - 1] >= 0) {
-                cf t = red[k][0][lane];
-                for (int q = 1; q < NS; ++q) t = addf(t, red[k][q][lane]);
+            cf t = red[k][0][lane];
+            for (int q = 1; q < NS; ++q) t = addf(t, red[k][q][lane]);
+            if (it.part >= 0) {
+                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + lane] = t;
+            } else {
+                const int ts = (k == 0) ? -1 : slot_of[2 * T + k - 1];
                 if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
-                else Lp[(int64_t)col * nslotcoef + slot_coef[tslot[k - 1]] + idx] = t;
+                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
             }
         }
         __syncthreads();
     }
 }
+__global__ void __launch_bounds__(64) k_m2l32_reduce(const M2LReduce* __restrict__ reds,
+                        const int* __restrict__ box_level, const int* __restrict__ p_level,
+                        const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                        const int64_t* __restrict__ slot_coef, int nrhs, int64_t ncoef, int64_t nslotcoef, int nparts,
+                        const cf* __restrict__ part, cf* __restrict__ Lout, cf* __restrict__ Lp) {
+    const M2LReduce r = reds[blockIdx.x];
+    const int p = p_level[box_level[r.box]];
+    const int lane = threadIdx.x % XT_W, k = threadIdx.x / XT_W;
+    const int idx = r.chunk * XT_W + lane;
+    if (k >= 3 || idx >= 2 * p + 1) return;
+    const int ts = (k == 0) ? -1 : slot_of[2 * r.box + k - 1];
+    if (k > 0 && ts < 0) return;
+    for (int col = 0; col < nrhs; ++col) {
+        cf t = mkf(0, 0);
+        for (int q = 0; q < r.nparts; ++q) t = addf(t, part[(((int64_t)col * nparts + r.part0 + q) * 3 + k) * XT_W + lane]);
+        if (k == 0) Lout[(int64_t)col * ncoef + coef_off[r.box] + idx] = t;
+        else Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
+    }
+}
 
 // ---------------------------------------------------------------------------
 static void mixed_free_buffers(MixedState* ms) {
-    cudaFree(ms->M); cudaFree(ms->L); cudaFree(ms->Mp); cudaFree(ms->Lp);
-    ms->M = ms->L = ms->Mp = ms->Lp = nullptr;
+    cudaFree(ms->M); cudaFree(ms->L); cudaFree(ms->Mp); cudaFree(ms->Lp); cudaFree(ms->part);
+    ms->M = ms->L = ms->Mp = ms->Lp = ms->part = nullptr;
     ms->cols = 0;
 }
 
@@ -346,6 +371,8 @@ void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
         cuda_check(cudaMalloc(&ms->L, sizeof(cf) * nc), "cudaMalloc L32");
         cuda_check(cudaMalloc(&ms->Mp, sizeof(cf) * ns), "cudaMalloc Mp32");
         cuda_check(cudaMalloc(&ms->Lp, sizeof(cf) * ns), "cudaMalloc Lp32");
+        cuda_check(cudaMalloc(&ms->part, sizeof(cf) * (size_t)std::max(g->n_m2l_parts, 1) * 3 * XT_W * nrhs),
+                   "cudaMalloc M2L partial sums 32");
         ms->cols = nrhs;
     }
     // coefficient ranges of the levels >= min_level (boxes and slots follow box order)
@@ -370,12 +397,20 @@ void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
     cuda_check(cudaGetLastError(), "k_to32");
     const int i0 = g->m2l_item_level_start[min_level];
     const int ni = g->n_m2l_items - i0;
+    const int r0 = g->m2l_red_level_start[min_level];
+    const int nr = g->m2l_red_level_start[t.D + 1] - r0;
     if (ni > 0) {
-        k_m2l32<<<ni, 128, 0, s>>>(g->d_m2l_items + i0, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_vf_ptr,
-                                   g->d_vf_src, g->d_vf_tab, ms->ftab, ms->ftab_off, g->d_vr_ptr, g->d_vr_src,
-                                   g->d_vr_key, g->d_vr_comp, g->d_comp, g->d_rkeys, ms->rtab, nrhs, g->ncoef, ms->M,
-                                   ms->L, g->d_slot_of, g->d_slot_coef, g->nslotcoef, ms->Mp, ms->Lp);
+        k_m2l32<<<ni, 128, 0, s>>>(g->d_m2l_items + i0, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                   g->d_slot_of, g->d_slot_coef, ms->ftab, ms->ftab_off, ms->rtab, nrhs, g->ncoef,
+                                   g->nslotcoef, g->n_m2l_parts, ms->M, ms->Mp, ms->L, ms->Lp, ms->part);
         cuda_check(cudaGetLastError(), "k_m2l32");
+        ++g->n_launches;
+    }
+    if (nr > 0) {
+        k_m2l32_reduce<<<nr, 64, 0, s>>>(g->d_m2l_reds + r0, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                         g->d_slot_of, g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts,
+                                         ms->part, ms->L, ms->Lp);
+        cuda_check(cudaGetLastError(), "k_m2l32_reduce");
         ++g->n_launches;
     }
     for (int col = 0; col < nrhs; ++col) {   // scale back

@@ -262,10 +262,11 @@ __global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t n) {
 
 // GMRES for every column.  precision 0: the FP64 operator throughout.
 // precision 1: iterative refinement -- each outer step solves A_mixed d = r by
-// GMRES on the precision-form operator (FP32 M2L) to a relative tolerance no
-// finer than what the outer tolerance still needs, adds d to x and recomputes
-// r = b - A x with the FP64 operator; it stops when ||r|| <= tol ||b||, when the
-// Krylov iterations reach max_iter, or when an outer step no longer halves ||r||.
+// GMRES on the precision-form operator (FP32 M2L), adds d to x and recomputes
+// r = b - A x with the FP64 operator.  The first inner solve runs to tol itself,
+// later ones to the reduction the FP64 residual still needs; it stops when
+// ||r|| <= tol ||b||, when the Krylov iterations reach max_iter, or when an
+// outer step no longer halves ||r||.
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
                  cudaStream_t s, lfmm_gmres_info* info, int precision) {
     auto t0 = std::chrono::steady_clock::now();
@@ -296,7 +297,10 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
             rn = bn;
             int total = 0;
             while (bn > 0.0 && rn > tol * bn && total < maxit) {
-                const double tol_in = std::min(0.5, std::max(0.5 * tol * bn / rn, 1e-6));
+                // the first solve goes straight for tol (a restarted Krylov space converges
+                // more slowly than one kept); later ones only remove what the operator
+                // difference left behind
+                const double tol_in = (outer == 0) ? tol : std::min(0.5, 0.5 * tol * bn / rn);
                 int its = 0;
                 double rr = 0.0;
                 gmres_one(g, r, d, tol_in, maxit - total, pre, s, &its, &rr, true);

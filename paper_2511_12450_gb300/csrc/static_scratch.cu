@@ -62,12 +62,14 @@ extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* 
     set_error("");
     if (!g || !x || !y) { set_error("NULL argument"); return LFMM_ERR_INVALID_ARG; }
     if (x == y) { set_error("x and y must not overlap"); return LFMM_ERR_INVALID_ARG; }
-    // work buffers: sorted x and y, multipoles/locals (cell centres and reaction centres), one column
+    // work buffers: sorted x and y, multipoles/locals (cell centres and reaction centres), M2L partial
+    // sums, one column
     const size_t n = (size_t)g->n;
     const size_t b_xs = align256(sizeof(cd) * n), b_ys = b_xs;
     const size_t b_m = align256(sizeof(cd) * (size_t)(g->ncoef > 0 ? g->ncoef : 1));
     const size_t b_mp = align256(sizeof(cd) * (size_t)(g->nslotcoef > 0 ? g->nslotcoef : 1));
-    const size_t need = b_xs + b_ys + 2 * b_m + 2 * b_mp;
+    const size_t b_part = align256(sizeof(cd) * (size_t)(g->n_m2l_parts > 0 ? g->n_m2l_parts : 1) * 3 * XT_W);
+    const size_t need = b_xs + b_ys + 2 * b_m + 2 * b_mp + b_part;
     if (need > LFMM_STATIC_SCRATCH_BYTES) {
         set_error("geometry needs " + std::to_string(need) + " bytes of work memory; lfmm_matvec_static holds " +
                   std::to_string((size_t)LFMM_STATIC_SCRATCH_BYTES) + " (use lfmm_matvec)");
@@ -75,7 +77,8 @@ extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* 
     }
     // save the geometry's own (lazily allocated) buffers and point it at the array
     cd *sxs = g->d_xs, *sys = g->d_ys, *sM = g->d_M, *sL = g->d_L, *sMp = g->d_Mp, *sLp = g->d_Lp;
-    int s_nrhs = g->nrhs_cap, s_cols = g->coef_cols;
+    cd* spart = g->d_m2l_part;
+    int s_nrhs = g->nrhs_cap, s_cols = g->coef_cols, s_pcols = g->m2l_part_cols;
     bool s_prof = g->prof.on;
     g->prof.on = false;   // the stage timers synchronise the stream; this entry point never does
     lfmm_status st = LFMM_OK;
@@ -88,8 +91,10 @@ extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* 
         g->d_L = (cd*)(base + o); o += b_m;
         g->d_Mp = (cd*)(base + o); o += b_mp;
         g->d_Lp = (cd*)(base + o); o += b_mp;
+        g->d_m2l_part = (cd*)(base + o); o += b_part;
         g->nrhs_cap = 1;
         g->coef_cols = 1;
+        g->m2l_part_cols = 1;
         cudaStream_t s = (cudaStream_t)stream;
         gather_sorted(g, (const cd*)x, g->d_xs, 1, s);
         apply_operator_sorted(g, g->d_xs, g->d_ys, 1, s);
@@ -102,8 +107,10 @@ extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* 
         st = LFMM_ERR_CUDA;
     }
     g->d_xs = sxs; g->d_ys = sys; g->d_M = sM; g->d_L = sL; g->d_Mp = sMp; g->d_Lp = sLp;
+    g->d_m2l_part = spart;
     g->nrhs_cap = s_nrhs;
     g->coef_cols = s_cols;
+    g->m2l_part_cols = s_pcols;
     g->prof.on = s_prof;
     return st;
 }
