@@ -334,10 +334,11 @@ def run_ours(args):
                  "converged": bool(info["converged"]), "precond": "overlapping DD (Sec. 4.2)",
                  "setup_seconds": setup_s}
         xm, im = lfmm.gmres_solve(G, b, tol=1e-8, max_iter=1000, precond=True, precision=1)
-        mixed["solve"] = {"metric": "GMRES solve s @1e-8 resid (FP64 residual), mixed-precision refinement",
+        mixed["solve"] = {"metric": "GMRES solve s @1e-8 resid (FP64 residual), relaxed mixed precision",
                           "seconds": im["solve_seconds"], "iterations": im["iterations"],
-                          "refinements": im["refinements"], "true_rel_residual": im["true_rel_residual"],
-                          "converged": bool(im["converged"]), "op_rel_diff_at_solution": im["op_rel_diff"],
+                          "refinements": im["refinements"], "fp64_matvecs": im["fp64_matvecs"],
+                          "true_rel_residual": im["true_rel_residual"],
+                          "converged": bool(im["converged"]), "op_rel_diff_on_b": im["op_rel_diff"],
                           "rel_diff_to_fp64_solution": float(torch.linalg.norm(xm - xs) / torch.linalg.norm(xs))}
 
     cpu = None

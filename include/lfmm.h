@@ -55,11 +55,12 @@ typedef enum {
 enum {
     LFMM_DEVICE_PTRS = 1,   /* vector arguments are device pointers */
     LFMM_MIXED = 2          /* lfmm_matvec: apply the precision form of the operator --
-                               the multipole-to-local translations (free space and
-                               reaction components) in FP32 on scaled expansions, every
-                               other stage in FP64; its relative difference from the FP64
-                               operator is about 1e-7 (no counterpart in the paper, which
-                               works in FP64 throughout) */
+                               the far field (P2M, M2M, M2L free space and reaction, L2L,
+                               L2P) in FP32 on scaled expansions on the levels whose order
+                               is the base p; the coarser wide-band levels, the stored near
+                               field and every sum into y stay FP64.  Its relative
+                               difference from the FP64 operator is a few 1e-7 (no
+                               counterpart in the paper, which works in FP64 throughout) */
 };
 
 /* lfmm_params.flags */
@@ -87,9 +88,12 @@ typedef struct {
     int32_t max_iter;   /* default 1000 */
     int32_t restart;    /* 0 = full GMRES (default) */
     int32_t precond;    /* 1 = overlapping DD preconditioner (Sec. 4.2, default), 0 = none */
-    int32_t precision;  /* 0 = FP64 operator (default).  1 = iterative refinement: each
-                           outer step runs GMRES on the LFMM_MIXED operator, adds the
-                           correction and recomputes the residual with the FP64 operator;
+    int32_t precision;  /* 0 = FP64 operator (default).  1 = relaxed mixed precision:
+                           the relative difference eps of the LFMM_MIXED and FP64
+                           operators is measured on b; GMRES multiplies by the FP64
+                           operator until its residual falls below 0.03 tol / eps and by
+                           the LFMM_MIXED one after that, to 0.3 tol; the FP64 residual is then
+                           recomputed and refinement steps run while it exceeds tol.
                            tol applies to that FP64 residual */
 } lfmm_gmres_params;
 
@@ -99,10 +103,11 @@ typedef struct {
     double rel_residual;       /* final GMRES residual estimate (max over columns) */
     double true_rel_residual;  /* ||b - K x|| / ||b|| recomputed with lfmm_matvec (max over columns) */
     double solve_seconds;      /* wall time of the solve */
-    int32_t refinements;       /* outer refinement steps (precision 1; 0 otherwise) */
-    int32_t fp64_matvecs;      /* FP64 operator applications for residuals (last column) */
-    double op_rel_diff;        /* precision 1: ||(A_mixed - A) x|| / ||A x|| at the solution
-                                  (max over columns); 0 otherwise */
+    int32_t refinements;       /* GMRES passes (precision 1: 1 + refinement steps; 0 otherwise) */
+    int32_t fp64_matvecs;      /* FP64 operator applications, Krylov steps and residuals
+                                  (last column) */
+    double op_rel_diff;        /* precision 1: ||(A_mixed - A) b|| / ||A b|| (max over columns),
+                                  the operator difference the relaxation was set from */
 } lfmm_gmres_info;
 
 /*

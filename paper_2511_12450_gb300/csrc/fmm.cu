@@ -251,6 +251,7 @@ void fmm_build(lfmm_geometry_s* g) {
         std::vector<cd> xvec;
         std::vector<XDst> xd;
         std::vector<XSrc> xs;
+        std::vector<int> xd_layer;   // layer of each destination (its sources share it)
         auto put_vec = [&](double k, double dx, double dy, int hw, int sign, bool reverse) -> int64_t {
             std::vector<cd> v(2 * hw + 1);
             graf_j_vector(k, dx, dy, hw, sign, v.data());
@@ -285,6 +286,7 @@ void fmm_build(lfmm_geometry_s* g) {
                     xs.push_back(XSrc{off[c], up_tab[(t.box_layer[b] * nlev + lp + 1) * 4 + quad_of(c)], pC, 0});
                 d.src_end = (int)xs.size();
                 xd.push_back(d);
+                xd_layer.push_back(t.box_layer[b]);
             }
             for (int side = 0; side < 2; ++side)
                 for (int b = t.level_start[lp]; b < t.level_start[lp + 1]; ++b) {
@@ -299,6 +301,7 @@ void fmm_build(lfmm_geometry_s* g) {
                     }
                     d.src_end = (int)xs.size();
                     xd.push_back(d);
+                    xd_layer.push_back(t.box_layer[b]);
                 }
             g->up_end[lp] = (int)xd.size();
         }
@@ -317,6 +320,7 @@ void fmm_build(lfmm_geometry_s* g) {
                 }
                 d.src_end = (int)xs.size();
                 xd.push_back(d);
+                xd_layer.push_back(t.box_layer[b]);
             }
             for (int side = 0; side < 2; ++side)
                 for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
@@ -331,12 +335,16 @@ void fmm_build(lfmm_geometry_s* g) {
                     xs.push_back(XSrc{slot_coef[sp], v, pP, 1});
                     d.src_end = (int)xs.size();
                     xd.push_back(d);
+                    xd_layer.push_back(t.box_layer[b]);
                 }
             g->dn_end[l] = (int)xd.size();
         }
         g->d_xdst = dupload(g, xd);
         g->d_xsrc = dupload(g, xs);
         g->d_xvec = dupload(g, xvec);
+        g->xdst_host = xd;
+        g->xsrc_host = xs;
+        g->xd_layer_host = xd_layer;
     }
 
     // free-space M2L tables per (layer, level, offset) and the V lists with table ids
@@ -507,22 +515,32 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         cuda_check(cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l2p), "l2p smem");
         g->smem_l2p_set = smem_l2p;
     }
+    // precision form: the levels >= lm run in FP32 on scaled expansions (lm > D: none)
+    const int lm = mixed ? std::max(l0, std::min(mixed_level(g), D + 1)) : D + 1;
+    if (lm <= D) mixed_setup(g, nrhs);
     {   // P2M: leaves about cell centres, straddling leaves about reaction centres
         prof_begin(g, ST_P2M, s);
-        k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
-                                                      g->d_w, x_sorted, g->n, nrhs, g->ncoef, g->d_M);
-        cuda_check(cudaGetLastError(), "k_p2m");
-        ++g->n_launches;
-        if (g->n_slot_groups > 0) {
-            k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x, g->d_y,
-                                                          g->d_w, x_sorted, g->n, nrhs, g->nslotcoef, g->d_Mp);
-            cuda_check(cudaGetLastError(), "k_p2m slots");
+        if (lm <= D) {
+            mixed_p2m(g, x_sorted, nrhs, s);
+        } else {
+            k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
+                                                          g->d_w, x_sorted, g->n, nrhs, g->ncoef, g->d_M);
+            cuda_check(cudaGetLastError(), "k_p2m");
             ++g->n_launches;
+            if (g->n_slot_groups > 0) {
+                k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x,
+                                                              g->d_y, g->d_w, x_sorted, g->n, nrhs, g->nslotcoef,
+                                                              g->d_Mp);
+                cuda_check(cudaGetLastError(), "k_p2m slots");
+                ++g->n_launches;
+            }
         }
         prof_end(g, ST_P2M, s);
     }
     prof_begin(g, ST_M2M, s);
     for (int lp = D - 1; lp >= l0; --lp) {   // M2M: children at lp + 1 -> parents (cells and reaction centres) at lp
+        if (lp >= lm) { mixed_m2m(g, lp, nrhs, s); continue; }
+        if (lp == lm - 1) mixed_m_to64(g, lm, nrhs, s);   // the FP64 levels start from the FP32 ones' multipoles
         const int nd = g->up_end[lp] - g->up_begin[lp];
         if (nd == 0) continue;
         dim3 grid(nd, (2 * t.p_level[lp] + 1 + XT_W - 1) / XT_W);
@@ -532,9 +550,8 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         ++g->n_launches;
     }
     prof_end(g, ST_M2M, s);
-    {   // M2L, all levels (precision form: the levels >= mixed_level in FP32)
+    {   // M2L, all levels (precision form: the levels >= lm in FP32)
         prof_begin(g, ST_M2L, s);
-        const int lm = mixed ? std::max(l0, std::min(mixed_level(g), D + 1)) : D + 1;
         const int n64 = g->m2l_item_level_start[lm];
         const int r64 = g->m2l_red_level_start[lm];
         if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
@@ -559,31 +576,41 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
             cuda_check(cudaGetLastError(), "k_m2l_reduce");
             ++g->n_launches;
         }
-        if (mixed) mixed_m2l(g, nrhs, lm, s);
+        if (lm <= D) mixed_m2l(g, nrhs, lm, s);
         prof_end(g, ST_M2L, s);
     }
     prof_begin(g, ST_L2L, s);
     for (int l = l0 + 1; l <= D; ++l) {   // L2L: parents at l - 1 -> children (cells and reaction centres) at l
+        if (l > lm) { mixed_l2l(g, l, nrhs, s); continue; }
         const int nd = g->dn_end[l] - g->dn_begin[l];
         if (nd == 0) continue;
+        // at the first FP32 level the FP64 translation writes (not adds) and is then added
+        // into the FP32 locals, which the FP32 M2L has written
+        const int acc = (l == lm) ? 0 : 1;
         dim3 grid(nd, (2 * t.p_level[l] + 1 + XT_W - 1) / XT_W);
-        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, nrhs, g->ncoef,
+        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, acc, nrhs, g->ncoef,
                                          g->nslotcoef, g->d_L, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_translate (L2L)");
         ++g->n_launches;
+        if (l == lm) mixed_l_add(g, lm, nrhs, s);
     }
     prof_end(g, ST_L2L, s);
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
         prof_begin(g, ST_L2P, s);
-        k_l2p<<<g->n_leaf_groups, 128, smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
-                                                      g->n, nrhs, g->ncoef, g->d_L, y_sorted);
-        cuda_check(cudaGetLastError(), "k_l2p");
-        ++g->n_launches;
-        if (g->n_slot_groups > 0) {
-            k_l2p<<<g->n_slot_groups, 128, smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->m, g->d_x,
-                                                          g->d_y, g->n, nrhs, g->nslotcoef, g->d_Lp, y_sorted);
-            cuda_check(cudaGetLastError(), "k_l2p slots");
+        if (lm <= D) {
+            mixed_l2p(g, y_sorted, nrhs, s);
+        } else {
+            k_l2p<<<g->n_leaf_groups, 128, smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
+                                                          g->n, nrhs, g->ncoef, g->d_L, y_sorted);
+            cuda_check(cudaGetLastError(), "k_l2p");
             ++g->n_launches;
+            if (g->n_slot_groups > 0) {
+                k_l2p<<<g->n_slot_groups, 128, smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->m,
+                                                              g->d_x, g->d_y, g->n, nrhs, g->nslotcoef, g->d_Lp,
+                                                              y_sorted);
+                cuda_check(cudaGetLastError(), "k_l2p slots");
+                ++g->n_launches;
+            }
         }
         prof_end(g, ST_L2P, s);
     }

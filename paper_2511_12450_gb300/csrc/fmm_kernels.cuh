@@ -26,20 +26,9 @@ namespace lfmm {
 // layer lay about (cx, cy) to order p: M_n = sum_j Q_j J_n(k rho_j) e^{-i n theta_j}.
 // Used for the leaves (about the cell centres) and for the cells that straddle an
 // interface (about their reaction centres).  One CTA (128 threads) per entry.
-struct ExpEntry {
-    int beg, end, lay, p;
-    double cx, cy;
-    int64_t off;   // coefficient offset in the output/input array
-};
 
 // Consecutive expansion entries whose points are processed by one CTA together
 // (at most EXP_GROUP_PTS points, or a single larger entry).
-#define EXP_GROUP_PTS 128
-#define EXP_GROUP_ENTRIES 16
-struct ExpGroup {
-    int e0, e1;    // entry range
-    int npts;      // points of the group
-};
 
 // Point t of a group: its entry (relative index) and point index.
 __device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, int e0, int e1, int t, int* er, int* j) {
@@ -268,18 +257,6 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
 // m; the slices are reduced in a fixed order, so results are reproducible.
 // Spreading a destination over several CTAs keeps the coarse levels (few
 // boxes, orders up to 2p+1 ~ 115) from running on a handful of SMs.
-struct XDst {
-    int64_t off;          // coefficient offset of the destination
-    int p;                // its order
-    int in_slots;         // 1: the destination lives in the reaction-centre arrays
-    int src_begin, src_end;
-};
-struct XSrc {
-    int64_t off;          // coefficient offset of the source
-    int64_t vec_off;      // translation vector V (2 (pS + pD) + 1 entries)
-    int p;                // source order
-    int in_slots;
-};
 __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
                                                    const cd* __restrict__ vec, int accumulate, int nrhs,
                                                    int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {

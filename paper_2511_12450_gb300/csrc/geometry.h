@@ -39,10 +39,33 @@ struct QuadRule {
     double gl_w[8];
 };
 
-struct ExpEntry;
-struct ExpGroup;
-struct XDst;
-struct XSrc;
+// point range expanded about one centre (P2M / L2P)
+struct ExpEntry {
+    int beg, end, lay, p;
+    double cx, cy;
+    int64_t off;   // coefficient offset in the output/input array
+};
+// consecutive entries processed by one CTA (at most EXP_GROUP_PTS points and
+// EXP_GROUP_ENTRIES entries, or a single larger entry)
+#define EXP_GROUP_PTS 128
+#define EXP_GROUP_ENTRIES 16
+struct ExpGroup {
+    int e0, e1;    // entry range
+    int npts;      // points of the group
+};
+// M2M / L2L pass records (see k_translate)
+struct XDst {
+    int64_t off;          // coefficient offset of the destination
+    int p;                // its order
+    int in_slots;         // 1: the destination lives in the reaction-centre arrays
+    int src_begin, src_end;
+};
+struct XSrc {
+    int64_t off;          // coefficient offset of the source
+    int64_t vec_off;      // translation vector V (2 (pS + pD) + 1 entries)
+    int p;                // source order
+    int in_slots;
+};
 // M2L work: XT_W output coefficients of one target box over a range of its
 // list entries; part >= 0 sends the partial sums to the reduction buffer.
 #define XT_W 16
@@ -128,6 +151,9 @@ struct lfmm_geometry_s {
     lfmm::XDst* d_xdst = nullptr;
     lfmm::XSrc* d_xsrc = nullptr;
     cd* d_xvec = nullptr;
+    std::vector<lfmm::XDst> xdst_host;
+    std::vector<lfmm::XSrc> xsrc_host;
+    std::vector<int> xd_layer_host;
     // near field: block-sparse rows over target leaves
     int *d_nb_ptr = nullptr;          // nleaf + 1
     int *d_nb_src = nullptr;          // source leaf (box id) per block
@@ -212,7 +238,14 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
 void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false);
 // precision form: M2L in FP32 on scaled expansions (mixed.cu)
+void mixed_setup(lfmm_geometry_s* g, int nrhs);                       // tables, scales, FP32 buffers
+void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s);
+void mixed_m2m(lfmm_geometry_s* g, int parent_level, int nrhs, cudaStream_t s);
+void mixed_m_to64(lfmm_geometry_s* g, int level, int nrhs, cudaStream_t s);   // FP32 multipoles -> FP64
 void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s);
+void mixed_l_add(lfmm_geometry_s* g, int level, int nrhs, cudaStream_t s);    // FP64 locals += into FP32
+void mixed_l2l(lfmm_geometry_s* g, int child_level, int nrhs, cudaStream_t s);
+void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s);
 int mixed_level(lfmm_geometry_s* g);   // first level whose M2L runs in FP32
 void mixed_destroy(lfmm_geometry_s* g);
 void fmm_free(lfmm_geometry_s* g);   // per-nrhs coefficient buffers

@@ -1,8 +1,9 @@
-// mixed.cu -- the precision form of the operator: the multipole-to-local
+// mixed.cu -- the precision form of the operator: on the levels whose order is
+// the base p, the whole far field -- P2M, M2M, the multipole-to-local
 // translations (free space, Graf's addition theorem, and the reaction
-// components' moment tables of eq. generalintegral) in FP32, everything else
-// (P2M, M2M, L2L, L2P, the stored near field with its singular and Sommerfeld
-// entries) in FP64.
+// components' moment tables of eq. generalintegral), L2L and L2P -- in FP32;
+// the coarser wide-band levels, the stored near field with its singular and
+// Sommerfeld entries, and every sum into the FP64 output stay FP64.
 //
 // FP32 has 8 exponent bits; the expansions span far more.  At the fine levels
 // the multipole coefficients decay like (k rho / 2)^n / n! and the Hankel
@@ -13,10 +14,13 @@
 // and the translation operators accordingly,
 //     free:      L~_n = sum_m [s^(|n| + |m|) T_{m-n}] M~_m,
 //     reaction:  beta~_m = sum_n [s_T^|m| s_S^|n| I_{mn}] alpha~_n,
-// with s <= 1 chosen per (layer, level) on the host so that the largest scaled
-// translation entry and the smallest scaled order-p multipole basis value stay
-// equally far inside the FP32 range.  The scaled operators are stored as dense
-// FP32 matrices (column-major), the free-space ones per (layer, level, offset).
+// with s <= 1 chosen per (layer, level) on the host so that the scaled basis
+// values and translation entries stay well inside the FP32 range.  The scaled
+// operators are stored as dense FP32 matrices (column-major): free-space M2L per
+// (layer, level, offset), reaction M2L per moment table, M2M / L2L per source of
+// every destination of the FP32 passes.  At the first FP32 level the FP32
+// multipoles are converted to FP64 for the coarser levels, and the FP64
+// parent-to-child locals are added into the FP32 ones.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,6 +41,14 @@ __device__ __forceinline__ void cfmaf(cf& a, cf b, cf c) {
     a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
 }
 __device__ __forceinline__ cf addf(cf a, cf b) { return mkf(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cf mulf(cf a, cf b) { return mkf(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)); }
+// point t of a P2M / L2P group: its entry (relative index) and point index
+__device__ __forceinline__ void group_point32(const ExpEntry* __restrict__ ent, int e0, int e1, int t, int* er, int* j) {
+    int e = e0, base = 0;
+    while (e + 1 < e1 && t >= base + (ent[e].end - ent[e].beg)) { base += ent[e].end - ent[e].beg; ++e; }
+    *er = e - e0;
+    *j = ent[e].beg + (t - base);
+}
 
 struct MixedState {
     int cols = 0;                       // right-hand-side columns the FP32 buffers hold
@@ -49,6 +61,12 @@ struct MixedState {
     int64_t *ftab_off = nullptr;        // per table id
     cf *rtab = nullptr;                 // scaled dense reaction tables (offsets as ReactKey::off)
     std::vector<double> scale;          // [layer * nlev + level]
+    double* d_scale = nullptr;          // device copy
+    int lm = 0;                         // first FP32 level
+    cf* wtab = nullptr;                 // dense scaled M2M / L2L tables of the FP32 passes
+    int64_t* wtab_off = nullptr;        // per XSrc (-1 outside the FP32 passes)
+    int* d_xd_layer = nullptr;          // layer per XDst
+    size_t smem_p2m = 0, smem_l2p = 0;
     size_t bytes = 0;
 };
 
@@ -137,12 +155,13 @@ __global__ void k_to32(const cd* __restrict__ in, const double* __restrict__ isp
     const cd v = in[t];
     out[t] = mkf((float)(f * v.x), (float)(f * v.y));
 }
-// out (FP64) = in (FP32) * ispow
+// out (FP64) = in (FP32) * ispow (locals: L = L~ s^-|n|), or in / ispow with
+// multipole = 1 (M = M~ s^|n|)
 __global__ void k_from32(const cf* __restrict__ in, const double* __restrict__ ispow, int64_t n, int nrhs,
-                         cd* __restrict__ out) {
+                         cd* __restrict__ out, int multipole = 0) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * nrhs) return;
-    const double f = ispow[t % n];
+    const double f = multipole ? 1.0 / ispow[t % n] : ispow[t % n];
     const cf v = in[t];
     out[t] = mk(f * (double)v.x, f * (double)v.y);
 }
@@ -249,6 +268,209 @@ __global__ void __launch_bounds__(64) k_m2l32_reduce(const M2LReduce* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Scaled Bessel values in FP32: out[n] = J_n(x) / s^n, n = 0..p, from the power
+// series J_n(x) = (x/2)^n / n! sum_k (-x^2/4)^k / (k! (n+1)...(n+k)) (A&S 9.1.10),
+// i.e. t_n S_n with t_n = a^n / n!, a = x / (2 s).  Used at the leaves of the
+// levels that run in FP32, where x = k rho stays below the order p; no overflow
+// (t_n and the series terms are bounded there by the choice of s), no
+// normalisation step.
+__device__ __forceinline__ void bessel_j_scaled_f(float x, float s, int p, float* out) {
+    const float a = x / (2.0f * s);
+    const float q = -0.25f * x * x;
+    float t = 1.0f;
+    for (int n = 0; n <= p; ++n) {
+        if (n > 0) t *= a / (float)n;
+        float c = 1.0f, S = 1.0f;
+        for (int k = 1; k <= 40; ++k) {
+            c *= q / (float)(k * (n + k));
+            S += c;
+            if (fabsf(c) <= 1e-9f * fabsf(S)) break;
+        }
+        out[n] = t * S;
+    }
+}
+
+// P2M in FP32 at the leaves (cell centres and straddling leaves' reaction centres):
+// M~_n = sum_j q_j J_n(k rho_j) e^{-i n theta_j} / s^|n|.  Same grouping and
+// phases as the FP64 kernel.
+__global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                        MediumDev m, const double* __restrict__ sc, int lev, int nlev,
+                        const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pw,
+                        const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cf* __restrict__ M) {
+    extern __shared__ cf su32[];   // [npts][p+1] u, then [npts] q, then [nent + 1] offsets
+    const ExpGroup G = groups[blockIdx.x];
+    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int ne = G.e1 - G.e0;
+    cf* sq = su32 + (size_t)G.npts * np1;
+    int* soff = (int*)(sq + G.npts);
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int e = 0; e < ne; ++e) { soff[e] = o; o += ent[G.e0 + e].end - ent[G.e0 + e].beg; }
+        soff[ne] = o;
+    }
+    for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+        int er, j;
+        group_point32(ent, G.e0, G.e1, t, &er, &j);
+        const ExpEntry& E = ent[G.e0 + er];
+        const double dx = px[j] - E.cx, dy = py[j] - E.cy;
+        const double rho = hypot(dx, dy);
+        cf* u = su32 + (size_t)t * np1;
+        // u_n = J~_n z^n, z = e^{-i theta}, upward from z^0 = 1 so the low orders carry
+        // the least rounding
+        const float x = (float)(m.k[E.lay] * rho), sf = (float)sc[E.lay * nlev + lev];
+        const float a = x / (2.0f * sf), q = -0.25f * x * x;
+        const cf z = (rho > 0.0) ? mkf((float)(dx / rho), (float)(-dy / rho)) : mkf(1.0f, 0.0f);
+        cf zn = mkf(1.0f, 0.0f);
+        float tn = 1.0f;
+        for (int k2 = 0; k2 <= p; ++k2) {
+            if (k2 > 0) { tn *= a / (float)k2; zn = mulf(zn, z); }
+            float c = 1.0f, S = 1.0f;
+            for (int k = 1; k <= 40; ++k) {
+                c *= q / (float)(k * (k2 + k));
+                S += c;
+                if (fabsf(c) <= 1e-9f * fabsf(S)) break;
+            }
+            const float jv = tn * S;
+            u[k2] = mkf(jv * zn.x, jv * zn.y);
+        }
+    }
+    for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+            int er, j;
+            group_point32(ent, G.e0, G.e1, t, &er, &j);
+            const cd qv = pw[j] * phi[(int64_t)col * n + j];
+            sq[t] = mkf((float)qv.x, (float)qv.y);
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < ne * nco; task += blockDim.x) {
+            const int er = task / nco, idx = task - er * nco;
+            const int nn = idx - p, an = nn < 0 ? -nn : nn;
+            cf acc = mkf(0, 0);
+            for (int t = soff[er]; t < soff[er + 1]; ++t) {
+                cf v = su32[(size_t)t * np1 + an];
+                if (nn < 0) { v.y = -v.y; if (an & 1) { v.x = -v.x; v.y = -v.y; } }
+                cfmaf(acc, sq[t], v);
+            }
+            M[(int64_t)col * stride + ent[G.e0 + er].off + idx] = acc;
+        }
+    }
+}
+
+// L2P in FP32 at the leaves: y_j += sum_n L~_n J_n(k rho_j) e^{i n theta_j} / s^|n|
+// (the result is added to the FP64 output).
+__global__ void __launch_bounds__(128) k_l2p32(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                        MediumDev m, const double* __restrict__ sc, int lev, int nlev,
+                        const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
+                        int64_t stride, const cf* __restrict__ L, cd* __restrict__ y) {
+    extern __shared__ float sj32[];   // [npts][p+1] J~, then [nent][2p+1] coefficients
+    const ExpGroup G = groups[blockIdx.x];
+    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int ne = G.e1 - G.e0;
+    cf* sL = (cf*)(sj32 + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
+    for (int col = 0; col < nrhs; ++col) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < ne * nco; i += blockDim.x) {
+            const int er = i / nco, idx = i - er * nco;
+            sL[i] = L[(int64_t)col * stride + ent[G.e0 + er].off + idx];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+            int er, j;
+            group_point32(ent, G.e0, G.e1, t, &er, &j);
+            const ExpEntry& E = ent[G.e0 + er];
+            const double dx = px[j] - E.cx, dy = py[j] - E.cy;
+            const double rho = hypot(dx, dy);
+            float* J = sj32 + (size_t)t * np1;
+            if (col == 0) bessel_j_scaled_f((float)(m.k[E.lay] * rho), (float)sc[E.lay * nlev + lev], p, J);
+            const cf z = (rho > 0.0) ? mkf((float)(dx / rho), (float)(dy / rho)) : mkf(1.0f, 0.0f);
+            const cf* Le = sL + er * nco;
+            cf acc = mkf(Le[p].x * J[0], Le[p].y * J[0]);
+            cf zz = mkf(1.0f, 0.0f);
+            for (int k2 = 1; k2 <= p; ++k2) {
+                zz = mulf(zz, z);
+                const float jt = J[k2];
+                const cf a1 = Le[p + k2], a2 = Le[p - k2];
+                const float js = (k2 & 1) ? -jt : jt;
+                cfmaf(acc, mkf(jt * a1.x, jt * a1.y), zz);
+                cfmaf(acc, mkf(js * a2.x, js * a2.y), mkf(zz.x, -zz.y));
+            }
+            cd* yo = y + (int64_t)col * n + j;
+            *yo = *yo + mk((double)acc.x, (double)acc.y);
+        }
+    }
+}
+
+// M2M / L2L in FP32 on scaled expansions: out_n (= or +=) sum_j sum_m src_j[m] W_j[m][n],
+// W_j dense (column-major, (n, m) at m ncD + n) with the scale factors folded in.
+__global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
+                        const int64_t* __restrict__ wtab_off, const cf* __restrict__ wtab, int accumulate, int nrhs,
+                        int64_t ncoef, int64_t nslotcoef, cf* X, cf* Xp) {
+    __shared__ cf red[128 / XT_W][XT_W];
+    const XDst d = dsts[blockIdx.x];
+    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
+    const int idx = blockIdx.y * XT_W + lane;
+    const int ncD = 2 * d.p + 1;
+    for (int col = 0; col < nrhs; ++col) {
+        cf a = mkf(0, 0);
+        if (idx < ncD) {
+            for (int j = d.src_begin; j < d.src_end; ++j) {
+                const XSrc sr = srcs[j];
+                const cf* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
+                const cf* W = wtab + wtab_off[j] + idx;
+                const int ncS = 2 * sr.p + 1;
+                for (int mi = sl; mi < ncS; mi += 128 / XT_W) cfmaf(a, src[mi], W[mi * ncD]);
+            }
+        }
+        red[sl][lane] = a;
+        __syncthreads();
+        if (sl == 0 && idx < ncD) {
+            cf t = red[0][lane];
+            for (int q = 1; q < 128 / XT_W; ++q) t = addf(t, red[q][lane]);
+            cf* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
+            if (accumulate) *dst = addf(*dst, t);
+            else *dst = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Dense scaled FP32 tables of one pass: W[m][n] = f_src(|m|) f_dst(|n|) V[n - m + pS + pD],
+// f = s^|.| or s^-|.| as the expansion kind requires (up: multipoles M = M~ s^|m|,
+// M~_n = M_n / s^|n|; down: locals L = L~ s^-|m|, L~_n = L_n s^|n|).
+__global__ void k_xtab32(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs, const int* __restrict__ dlay,
+                         const cd* __restrict__ xvec, const double* __restrict__ sc, int nlev, int lev_src,
+                         int lev_dst, int down, const int64_t* __restrict__ wtab_off, cf* __restrict__ wtab) {
+    const XDst d = dsts[blockIdx.x];
+    const int lay = dlay[blockIdx.x];
+    const double ss = sc[lay * nlev + lev_src], sd = sc[lay * nlev + lev_dst];
+    const int ncD = 2 * d.p + 1;
+    for (int j = d.src_begin; j < d.src_end; ++j) {
+        const XSrc sr = srcs[j];
+        const int ncS = 2 * sr.p + 1;
+        const cd* V = xvec + sr.vec_off;
+        for (int e = threadIdx.x; e < ncS * ncD; e += blockDim.x) {
+            const int mi = e / ncD, ni = e - mi * ncD;
+            const int m = mi - sr.p, nn = ni - d.p;
+            const double f = down ? pow(ss, -(double)abs(m)) * pow(sd, (double)abs(nn))
+                                  : pow(ss, (double)abs(m)) * pow(sd, -(double)abs(nn));
+            const cd v = V[nn - m + sr.p + d.p];
+            wtab[wtab_off[j] + e] = mkf((float)(f * v.x), (float)(f * v.y));
+        }
+    }
+}
+
+// L~ (FP32) += L (FP64) / ispow over a coefficient range
+__global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t n,
+                           cf* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double f = 1.0 / ispow[t];
+    const cd v = in[t];
+    out[t] = addf(out[t], mkf((float)(f * v.x), (float)(f * v.y)));
+}
+
+// ---------------------------------------------------------------------------
 static void mixed_free_buffers(MixedState* ms) {
     cudaFree(ms->M); cudaFree(ms->L); cudaFree(ms->Mp); cudaFree(ms->Lp); cudaFree(ms->part);
     ms->M = ms->L = ms->Mp = ms->Lp = ms->part = nullptr;
@@ -260,6 +482,7 @@ void mixed_destroy(lfmm_geometry_s* g) {
     MixedState* ms = g->mixed;
     mixed_free_buffers(ms);
     cudaFree(ms->ispow); cudaFree(ms->ispow_slot); cudaFree(ms->ftab); cudaFree(ms->ftab_off); cudaFree(ms->rtab);
+    cudaFree(ms->d_scale); cudaFree(ms->wtab); cudaFree(ms->wtab_off); cudaFree(ms->d_xd_layer);
     delete ms;
     g->mixed = nullptr;
 }
@@ -336,6 +559,49 @@ static void mixed_build(lfmm_geometry_s* g) {
     cuda_check(cudaMalloc(&ms->rtab, sizeof(cf) * std::max<int64_t>(rtot, 1)), "cudaMalloc rtab32");
     ms->bytes += sizeof(cf) * std::max<int64_t>(rtot, 1);
     if (nk > 0) k_react32_tables<<<nk, 256>>>(g->d_m2lr, g->d_rkeys, d_kss, d_kst, ms->rtab);
+    // dense scaled tables of the FP32 M2M passes (parents at levels >= lm) and L2L
+    // passes (children at levels > lm)
+    ms->lm = std::max(l0, std::min(mixed_level(g), D + 1));
+    ms->d_scale = upload_raw(ms->scale, ms->bytes);
+    ms->d_xd_layer = upload_raw(g->xd_layer_host, ms->bytes);
+    std::vector<int64_t> woff(std::max<size_t>(g->xsrc_host.size(), 1), -1);
+    int64_t wtot = 0;
+    auto plan = [&](int b0, int b1) {
+        for (int i = b0; i < b1; ++i) {
+            const XDst& d = g->xdst_host[i];
+            for (int j = d.src_begin; j < d.src_end; ++j) {
+                woff[j] = wtot;
+                wtot += (int64_t)(2 * d.p + 1) * (2 * g->xsrc_host[j].p + 1);
+            }
+        }
+    };
+    for (int lp = D - 1; lp >= ms->lm; --lp) plan(g->up_begin[lp], g->up_end[lp]);
+    for (int l = ms->lm + 1; l <= D; ++l) plan(g->dn_begin[l], g->dn_end[l]);
+    ms->wtab_off = upload_raw(woff, ms->bytes);
+    cuda_check(cudaMalloc(&ms->wtab, sizeof(cf) * std::max<int64_t>(wtot, 1)), "cudaMalloc pass tables 32");
+    ms->bytes += sizeof(cf) * std::max<int64_t>(wtot, 1);
+    for (int lp = D - 1; lp >= ms->lm; --lp) {
+        const int nd = g->up_end[lp] - g->up_begin[lp];
+        if (nd > 0)
+            k_xtab32<<<nd, 256>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, ms->d_xd_layer + g->up_begin[lp], g->d_xvec,
+                                  ms->d_scale, nlev, lp + 1, lp, 0, ms->wtab_off, ms->wtab);
+    }
+    for (int l = ms->lm + 1; l <= D; ++l) {
+        const int nd = g->dn_end[l] - g->dn_begin[l];
+        if (nd > 0)
+            k_xtab32<<<nd, 256>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, ms->d_xd_layer + g->dn_begin[l], g->d_xvec,
+                                  ms->d_scale, nlev, l - 1, l, 1, ms->wtab_off, ms->wtab);
+    }
+    // shared memory of the FP32 P2M / L2P (all entries at the leaf order)
+    const int pD = t.p_level[D], gp = g->group_max_pts, ge = g->group_max_ent;
+    ms->smem_p2m = (size_t)gp * (pD + 1) * sizeof(cf) + (size_t)gp * sizeof(cf) + (size_t)(gp + 1) * sizeof(int);
+    ms->smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(float) + (size_t)ge * (2 * pD + 1) * sizeof(cf);
+    if (ms->smem_p2m > 48 * 1024)
+        cuda_check(cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_p2m),
+                   "p2m32 smem");
+    if (ms->smem_l2p > 48 * 1024)
+        cuda_check(cudaFuncSetAttribute(k_l2p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_l2p),
+                   "l2p32 smem");
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaDeviceSynchronize();
     cudaFree(d_tp); cudaFree(d_ts); cudaFree(d_kss); cudaFree(d_kst);
@@ -356,13 +622,9 @@ int mixed_level(lfmm_geometry_s* g) {
     return t.D + 1;
 }
 
-// M2L of the precision form for the levels >= min_level: scale M (FP64) into
-// FP32, translate, scale L back (those levels' coefficients only).
-void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
+void mixed_setup(lfmm_geometry_s* g, int nrhs) {
     if (!g->mixed) mixed_build(g);
     MixedState* ms = g->mixed;
-    const TreeHost& t = g->tree;
-    if (min_level > t.D) return;
     if (ms->cols < nrhs) {
         mixed_free_buffers(ms);
         const size_t nc = (size_t)std::max<int64_t>(g->ncoef, 1) * nrhs;
@@ -375,26 +637,118 @@ void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
                    "cudaMalloc M2L partial sums 32");
         ms->cols = nrhs;
     }
-    // coefficient ranges of the levels >= min_level (boxes and slots follow box order)
-    const int64_t c0 = g->box_coef_off_host[t.level_start[min_level]];
-    int64_t s0 = g->nslotcoef;
-    for (size_t q = 0; q < g->slot_box_host.size(); ++q)
-        if (t.box_level[g->slot_box_host[q]] >= min_level) { s0 = g->slot_coef_host[q]; break; }
-    const int64_t ncl = g->ncoef - c0, nsl = g->nslotcoef - s0;
-    for (int col = 0; col < nrhs; ++col) {   // scale in (per column: the ranges are not contiguous)
-        if (ncl > 0) {
-            k_to32<<<(unsigned)((ncl + 255) / 256), 256, 0, s>>>(g->d_M + col * g->ncoef + c0, ms->ispow + c0, ncl, 1,
-                                                                 ms->M + col * g->ncoef + c0);
+}
+
+void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const int D = g->tree.D, nlev = D + 1;
+    k_p2m32<<<g->n_leaf_groups, 128, ms->smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, ms->d_scale, D, nlev,
+                                                       g->d_x, g->d_y, g->d_w, x_sorted, g->n, nrhs, g->ncoef, ms->M);
+    cuda_check(cudaGetLastError(), "k_p2m32");
+    ++g->n_launches;
+    if (g->n_slot_groups > 0) {
+        k_p2m32<<<g->n_slot_groups, 128, ms->smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, ms->d_scale, D,
+                                                           nlev, g->d_x, g->d_y, g->d_w, x_sorted, g->n, nrhs,
+                                                           g->nslotcoef, ms->Mp);
+        cuda_check(cudaGetLastError(), "k_p2m32 slots");
+        ++g->n_launches;
+    }
+}
+
+static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate, int nrhs, cf* X, cf* Xp,
+                   cudaStream_t s) {
+    const int nd = b1 - b0;
+    if (nd == 0) return;
+    dim3 grid(nd, (2 * p_dst + 1 + XT_W - 1) / XT_W);
+    k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, nrhs,
+                                       g->ncoef, g->nslotcoef, X, Xp);
+    cuda_check(cudaGetLastError(), "k_translate32");
+    ++g->n_launches;
+}
+
+void mixed_m2m(lfmm_geometry_s* g, int lp, int nrhs, cudaStream_t s) {
+    pass32(g, g->up_begin[lp], g->up_end[lp], g->tree.p_level[lp], 0, nrhs, g->mixed->M, g->mixed->Mp, s);
+}
+
+void mixed_l2l(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
+    pass32(g, g->dn_begin[l], g->dn_end[l], g->tree.p_level[l], 1, nrhs, g->mixed->L, g->mixed->Lp, s);
+}
+
+// coefficient ranges of one level: boxes, then reaction centres (both follow box order)
+static void level_ranges(lfmm_geometry_s* g, int l, int64_t* c0, int64_t* c1, int64_t* s0, int64_t* s1) {
+    const TreeHost& t = g->tree;
+    *c0 = g->box_coef_off_host[t.level_start[l]];
+    *c1 = (l < t.D) ? g->box_coef_off_host[t.level_start[l + 1]] : g->ncoef;
+    *s0 = g->nslotcoef;
+    *s1 = g->nslotcoef;
+    for (size_t q = 0; q < g->slot_box_host.size(); ++q) {
+        const int lv = t.box_level[g->slot_box_host[q]];
+        if (lv >= l && *s0 == g->nslotcoef) *s0 = g->slot_coef_host[q];
+        if (lv > l) { *s1 = g->slot_coef_host[q]; break; }
+    }
+    if (*s1 < *s0) *s1 = *s0;
+}
+
+void mixed_m_to64(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    int64_t c0, c1, s0, s1;
+    level_ranges(g, l, &c0, &c1, &s0, &s1);
+    for (int col = 0; col < nrhs; ++col) {
+        if (c1 > c0) {
+            k_from32<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(ms->M + col * g->ncoef + c0, ms->ispow + c0,
+                                                                       c1 - c0, 1, g->d_M + col * g->ncoef + c0, 1);
             ++g->n_launches;
         }
-        if (nsl > 0) {
-            k_to32<<<(unsigned)((nsl + 255) / 256), 256, 0, s>>>(g->d_Mp + col * g->nslotcoef + s0,
-                                                                 ms->ispow_slot + s0, nsl, 1,
-                                                                 ms->Mp + col * g->nslotcoef + s0);
+        if (s1 > s0) {
+            k_from32<<<(unsigned)((s1 - s0 + 255) / 256), 256, 0, s>>>(ms->Mp + col * g->nslotcoef + s0,
+                                                                       ms->ispow_slot + s0, s1 - s0, 1,
+                                                                       g->d_Mp + col * g->nslotcoef + s0, 1);
             ++g->n_launches;
         }
     }
-    cuda_check(cudaGetLastError(), "k_to32");
+    cuda_check(cudaGetLastError(), "k_from32 (multipoles)");
+}
+
+void mixed_l_add(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    int64_t c0, c1, s0, s1;
+    level_ranges(g, l, &c0, &c1, &s0, &s1);
+    for (int col = 0; col < nrhs; ++col) {
+        if (c1 > c0) {
+            k_add_to32<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(g->d_L + col * g->ncoef + c0, ms->ispow + c0,
+                                                                         c1 - c0, ms->L + col * g->ncoef + c0);
+            ++g->n_launches;
+        }
+        if (s1 > s0) {
+            k_add_to32<<<(unsigned)((s1 - s0 + 255) / 256), 256, 0, s>>>(g->d_Lp + col * g->nslotcoef + s0,
+                                                                         ms->ispow_slot + s0, s1 - s0,
+                                                                         ms->Lp + col * g->nslotcoef + s0);
+            ++g->n_launches;
+        }
+    }
+    cuda_check(cudaGetLastError(), "k_add_to32");
+}
+
+void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const int D = g->tree.D, nlev = D + 1;
+    k_l2p32<<<g->n_leaf_groups, 128, ms->smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, ms->d_scale, D, nlev,
+                                                       g->d_x, g->d_y, g->n, nrhs, g->ncoef, ms->L, y_sorted);
+    cuda_check(cudaGetLastError(), "k_l2p32");
+    ++g->n_launches;
+    if (g->n_slot_groups > 0) {
+        k_l2p32<<<g->n_slot_groups, 128, ms->smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->m,
+                                                           ms->d_scale, D, nlev, g->d_x, g->d_y, g->n, nrhs,
+                                                           g->nslotcoef, ms->Lp, y_sorted);
+        cuda_check(cudaGetLastError(), "k_l2p32 slots");
+        ++g->n_launches;
+    }
+}
+
+// M2L of the precision form on the levels >= min_level (their multipoles are FP32 already).
+void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const TreeHost& t = g->tree;
     const int i0 = g->m2l_item_level_start[min_level];
     const int ni = g->n_m2l_items - i0;
     const int r0 = g->m2l_red_level_start[min_level];
@@ -413,20 +767,6 @@ void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
         cuda_check(cudaGetLastError(), "k_m2l32_reduce");
         ++g->n_launches;
     }
-    for (int col = 0; col < nrhs; ++col) {   // scale back
-        if (ncl > 0) {
-            k_from32<<<(unsigned)((ncl + 255) / 256), 256, 0, s>>>(ms->L + col * g->ncoef + c0, ms->ispow + c0, ncl, 1,
-                                                                   g->d_L + col * g->ncoef + c0);
-            ++g->n_launches;
-        }
-        if (nsl > 0) {
-            k_from32<<<(unsigned)((nsl + 255) / 256), 256, 0, s>>>(ms->Lp + col * g->nslotcoef + s0,
-                                                                   ms->ispow_slot + s0, nsl, 1,
-                                                                   g->d_Lp + col * g->nslotcoef + s0);
-            ++g->n_launches;
-        }
-    }
-    cuda_check(cudaGetLastError(), "k_from32");
 }
 
 }  // namespace lfmm

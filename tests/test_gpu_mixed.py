@@ -78,7 +78,7 @@ def test_mixed_gmres_refinement_reaches_fp64_residual_wide(wide):
     x1, i1 = lf.gmres_solve(G, b, tol=1e-8, precision=1)
     ref = np.linalg.solve(K, b)
     print("mixed GMRES:", i1)
-    assert i1["converged"] and i1["refinements"] >= 1
+    assert i1["converged"] and i1["refinements"] >= 1 and i1["fp64_matvecs"] < i1["iterations"]
     assert i1["true_rel_residual"] <= 1e-8
     assert 0.0 < i1["op_rel_diff"] <= OP_TOL
     # residual of the dense oracle matrix
