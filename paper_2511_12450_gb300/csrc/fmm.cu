@@ -96,7 +96,7 @@ static std::vector<ExpGroup> make_groups(const std::vector<ExpEntry>& e, int* ma
 #define M2L_ITEM_WORK 2048
 static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, const std::vector<int>& vr_src,
                            const std::vector<int>& vr_key, const std::vector<int>& vr_comp,
-                           const std::vector<ReactKey>& keys) {
+                           const std::vector<int>& vr_flip, const std::vector<ReactKey>& keys) {
     TreeHost& t = g->tree;
     const int D = t.D, l0 = t.l0, nlev = D + 1;
     std::vector<M2LEnt> ents;
@@ -115,7 +115,7 @@ static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, c
             E.src = (ssl >= 0) ? g->slot_coef_host[ssl] : g->box_coef_off_host[S];
             E.tab = keys[vr_key[e]].off;
             E.flags = M2L_REACT | (ssl >= 0 ? M2L_SRC_SLOT : 0) | (a_dir ? M2L_A_DOWN : 0) | (b_dir ? M2L_B_DOWN : 0) |
-                      (dst << M2L_DST_SHIFT);
+                      (vr_flip[e] ? M2L_FLIP : 0) | (dst << M2L_DST_SHIFT);
             E.pad = 0;
             ents.push_back(E);
         }
@@ -402,13 +402,19 @@ void fmm_build(lfmm_geometry_s* g) {
     {
         std::map<std::tuple<int, int, int, int, int>, int> id;
         std::vector<ReactKey> keys;
-        std::vector<int> vr_ptr(t.nbox + 1, 0), vr_src, vr_key, vr_comp;
+        std::vector<int> vr_ptr(t.nbox + 1, 0), vr_src, vr_key, vr_comp, vr_flip;
         int64_t tot = 0;
         for (int T = 0; T < t.nbox; ++T) {
             for (int e = t.vreact_ptr[T]; e < t.vreact_ptr[T + 1]; ++e) {
                 int S = t.vreact_idx[e], c = t.vreact_comp[e];
                 int l = t.box_level[T];
-                auto key = std::make_tuple(c, l, t.box_ix[S] - t.box_ix[T], t.box_iy[S], t.box_iy[T]);
+                // a pair at horizontal offset -X uses the table of +X with both indices
+                // reversed: lambda -> -lambda maps e^{i lambda X} to e^{-i lambda X} and
+                // w(lambda, k) to 1 / w(lambda, k) (k_y is even in lambda), so
+                // I(-X)_{mn} = I(X)_{-m,-n}
+                const int dix = t.box_ix[S] - t.box_ix[T];
+                const int flip = dix < 0 ? 1 : 0;
+                auto key = std::make_tuple(c, l, flip ? -dix : dix, t.box_iy[S], t.box_iy[T]);
                 auto it = id.find(key);
                 int kid;
                 if (it == id.end()) {
@@ -418,7 +424,7 @@ void fmm_build(lfmm_geometry_s* g) {
                     ReactKey rk;
                     rk.comp = c; rk.level = l; rk.pS = t.p_level[l]; rk.pT = t.p_level[l];
                     double w = t.width(l);
-                    rk.X = (t.box_ix[S] - t.box_ix[T]) * w;
+                    rk.X = (flip ? -dix : dix) * w;
                     double loS = t.y0 + t.box_iy[S] * w, hiS = t.y0 + (t.box_iy[S] + 1) * w;
                     double loT = t.y0 + t.box_iy[T] * w, hiT = t.y0 + (t.box_iy[T] + 1) * w;
                     rk.hS = src_height_box(g->m, C.ls, C.a, loS, hiS);
@@ -432,7 +438,7 @@ void fmm_build(lfmm_geometry_s* g) {
                 } else {
                     kid = it->second;
                 }
-                vr_src.push_back(S); vr_key.push_back(kid); vr_comp.push_back(c);
+                vr_src.push_back(S); vr_key.push_back(kid); vr_comp.push_back(c); vr_flip.push_back(flip);
             }
             vr_ptr[T + 1] = (int)vr_src.size();
         }
@@ -441,22 +447,44 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_vr_src = dupload(g, vr_src);
         g->d_vr_key = dupload(g, vr_key);
         g->d_vr_comp = dupload(g, vr_comp);
-        build_m2l_work(g, vr_ptr, vr_src, vr_key, vr_comp, keys);
+        build_m2l_work(g, vr_ptr, vr_src, vr_key, vr_comp, vr_flip, keys);
         g->d_rkeys = dupload(g, keys);
         g->rkeys_host = keys;
         g->d_m2lr = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
         if (!keys.empty()) {
+            // same-layer components: Toeplitz tables from 4p+1 moments; others tile by tile
             std::vector<TableWork> work;
+            std::vector<int> same;
+            int pmax_same = 0;
             for (int kk = 0; kk < (int)keys.size(); ++kk) {
+                const Component& C = t.comps[keys[kk].comp];
                 int p = keys[kk].pS;
+                if (C.ls == C.lt && keys[kk].pS == keys[kk].pT) {
+                    same.push_back(kk);
+                    pmax_same = std::max(pmax_same, p);
+                    continue;
+                }
                 for (int m0 = -p; m0 <= p; m0 += 32)
                     for (int n0 = -p; n0 <= p; n0 += 32) work.push_back(TableWork{kk, m0, n0});
             }
-            TableWork* d_work = dupload(g, work);
-            size_t smem = (size_t)(16 * 32 * 4 + 16 * 4) * sizeof(cd);
-            k_react_tables<<<(int)work.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_work, g->d_comp,
-                                                            g->d_m2lr);
-            cuda_check(cudaGetLastError(), "k_react_tables");
+            if (!work.empty()) {
+                TableWork* d_work = dupload(g, work);
+                size_t smem = (size_t)(16 * 32 * 4 + 16 * 4) * sizeof(cd);
+                k_react_tables<<<(int)work.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_work, g->d_comp,
+                                                                g->d_m2lr);
+                cuda_check(cudaGetLastError(), "k_react_tables");
+            }
+            if (!same.empty()) {
+                int* d_same = dupload(g, same);
+                const int nd = 4 * pmax_same + 1;
+                const size_t smem = (size_t)(16 * nd + 32 + nd) * sizeof(cd);
+                if (smem > 48 * 1024)
+                    cuda_check(cudaFuncSetAttribute(k_react_tables_same, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem), "same-layer tables smem");
+                k_react_tables_same<<<(int)same.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_same, g->d_comp,
+                                                                     g->d_m2lr);
+                cuda_check(cudaGetLastError(), "k_react_tables_same");
+            }
         }
     }
     cuda_check(cudaDeviceSynchronize(), "fmm_build");

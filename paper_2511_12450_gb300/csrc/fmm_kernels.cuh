@@ -149,19 +149,22 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
                     const bool bdown = (E.flags & M2L_B_DOWN) != 0;
                     // departure down: L_n += beta_n;  departure up: L_{-n} += (-1)^n beta_n
                     const int mrow = bdown ? nn : -nn;
-                    const cd* col_m = m2lr + E.tab + (mrow + p);
+                    // column of row mrow; a mirrored table is read at (-mrow, -n)
+                    const bool flip = (E.flags & M2L_FLIP) != 0;
+                    const cd* col_m = m2lr + E.tab + (flip ? (p - mrow) + (int64_t)2 * p * nco : (mrow + p));
+                    const int64_t cs = flip ? -(int64_t)nco : (int64_t)nco;
                     cd bsum = mk(0, 0);
                     if (E.flags & M2L_A_DOWN) {   // alpha_i = M_i
-                        for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[(int64_t)mi * nco], src[mi]);
+                        for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[mi * cs], src[mi]);
                     } else {                      // alpha_i = (-1)^(i-p) M_{2p-i}
                         for (int mi = sl; mi < nco; mi += NS) {
                             cd v = src[2 * p - mi];
                             if ((mi - p) & 1) v = -v;
-                            cfma(bsum, col_m[(int64_t)mi * nco], v);
+                            cfma(bsum, col_m[mi * cs], v);
                         }
                     }
                     if (!bdown && (mrow & 1)) bsum = -bsum;
-                    const int dst = E.flags >> M2L_DST_SHIFT;
+                    const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
                     if (dst == 0) acc0 += bsum;
                     else if (dst == 1) acc1 += bsum;
                     else acc2 += bsum;
@@ -290,6 +293,74 @@ __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts
     }
 }
 
+// Reaction M2L moment tables of components whose source and field layers are the
+// same (k_S = k_T, so u = v on every node): I_{mn} = h_{n-m} with
+// h_d = sum_q (Fp_q u_q^d + Fm_q u_q^-d), d = -2p..2p -- 4p+1 moments per key
+// instead of (2p+1)^2.  One CTA per key; the table is then written out dense.
+__global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRule q,
+                                                           const ReactKey* __restrict__ keys,
+                                                           const int* __restrict__ key_list,
+                                                           const int* __restrict__ comp, cd* __restrict__ out) {
+    extern __shared__ cd sh[];
+    const ReactKey K = keys[key_list[blockIdx.x]];
+    const int c = K.comp;
+    const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
+    const int p = K.pS, nco = 2 * p + 1, nd = 4 * p + 1;
+    const double ka = med.k[ls];
+    const int CH = 16;
+    cd* Pw = sh;                 // [CH][nd]  u^d, d = -2p..2p
+    cd* Fp = Pw + CH * nd;       // [CH]
+    cd* Fm = Fp + CH;            // [CH]
+    cd* hs = Fm + CH;            // [nd] moments
+    QuadRule qt = q;
+    qt.es_v0 = q.tab_es_v0;
+    qt.es_hv = q.tab_es_hv;
+    qt.nes = q.tab_nes;
+    double h;
+    const int P = detour_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
+    const int ntot = P * 8 + 2 * qt.nes;
+    cd acc[2] = {mk(0, 0), mk(0, 0)};   // d = threadIdx.x and threadIdx.x + 256
+    for (int j0 = 0; j0 < ntot; j0 += CH) {
+        const int cnt = min(CH, ntot - j0);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            QuadNode nd2 = contour_node(qt, j0 + threadIdx.x, P, h, K.X, K.D);
+            cd S = sigma_comp(med, nd2.lam, ls, a, lt, b);
+            cd kya = ky_of(ka, nd2.lam);
+            cd SE = S * (eikh(kya, K.hS) * eikh(kya, K.hT));
+            Fp[threadIdx.x] = SE * nd2.fp;
+            Fm[threadIdx.x] = SE * nd2.fm;
+            // powers u^-2p .. u^2p
+            const cd u = w_of(kya, nd2.lam, ka);
+            cd bb = cinv(u), cur = mk(1.0, 0.0);
+            for (int k2 = 2 * p; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
+            cd* row = Pw + threadIdx.x * nd;
+            for (int d = 0; d < nd; ++d) { row[d] = cur; cur = cur * u; }
+        }
+        __syncthreads();
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int di = threadIdx.x + 256 * s2;
+            if (di >= nd) break;
+            cd ac = acc[s2];
+            for (int r = 0; r < cnt; ++r) {
+                cfma(ac, Fp[r], Pw[r * nd + di]);             // u^d
+                cfma(ac, Fm[r], Pw[r * nd + (nd - 1 - di)]);   // u^-d
+            }
+            acc[s2] = ac;
+        }
+    }
+    for (int s2 = 0; s2 < 2; ++s2) {
+        const int di = threadIdx.x + 256 * s2;
+        if (di < nd) hs[di] = acc[s2];
+    }
+    __syncthreads();
+    // I_{mn} = h_{n-m}, column-major (m, n) at (n + p) nco + (m + p)
+    for (int e = threadIdx.x; e < nco * nco; e += blockDim.x) {
+        const int ni = e / nco, mi = e - ni * nco;
+        out[K.off + e] = hs[(ni - mi) + 2 * p];
+    }
+}
+
 // Reaction M2L moment tables (eq. generalintegral): one CTA per (key, 32x32 tile).
 struct TableWork {
     int key;
@@ -343,23 +414,25 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
             vv[threadIdx.x] = w_of(kyb, nd.lam, kb);
         }
         __syncthreads();
-        // power tables: thread (node r, slot s) for 16 x 32 entries, 2 passes
-        for (int e = threadIdx.x; e < cnt * 32; e += blockDim.x) {
-            int r = e >> 5, s = e & 31;
-            int nn = wk.n0 + s, mm = wk.m0 + s;
-            cd u = uu[r], v = vv[r];
-            cd ui = cinv(u), vi = cinv(v);
-            // integer powers by binary exponentiation
-            auto ipow = [](cd base, int e2) {
-                cd r2 = mk(1.0, 0.0);
-                cd bb = base;
-                while (e2 > 0) { if (e2 & 1) r2 = r2 * bb; bb = bb * bb; e2 >>= 1; }
-                return r2;
-            };
-            Up[r * 32 + s] = (nn >= 0) ? ipow(u, nn) : ipow(ui, -nn);
-            Um[r * 32 + s] = (nn >= 0) ? ipow(ui, nn) : ipow(u, -nn);
-            Vp[r * 32 + s] = (mm >= 0) ? ipow(vi, mm) : ipow(v, -mm);
-            Vm[r * 32 + s] = (mm >= 0) ? ipow(v, mm) : ipow(vi, -mm);
+        // power tables of the tile: for each node four runs of 32 consecutive powers
+        // (u^n and u^-n over the tile's columns, v^-m and v^m over its rows), one
+        // thread per run: a starting power by binary exponentiation, then 31 products
+        for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
+            const int r = e >> 2, which = e & 3;
+            const cd u = uu[r], v = vv[r];
+            cd base, step;
+            int e0;
+            cd* dst;
+            if (which == 0) { base = u; step = u; e0 = wk.n0; dst = Up; }               // u^n
+            else if (which == 1) { base = u; step = cinv(u); e0 = -wk.n0; dst = Um; }   // u^-n
+            else if (which == 2) { base = v; step = cinv(v); e0 = -wk.m0; dst = Vp; }   // v^-m
+            else { base = v; step = v; e0 = wk.m0; dst = Vm; }                         // v^m
+            // start = base^e0 (e0 may be negative)
+            cd bb = (e0 >= 0) ? base : cinv(base);
+            int k2 = e0 >= 0 ? e0 : -e0;
+            cd cur = mk(1.0, 0.0);
+            while (k2 > 0) { if (k2 & 1) cur = cur * bb; bb = bb * bb; k2 >>= 1; }
+            for (int s2 = 0; s2 < 32; ++s2) { dst[r * 32 + s2] = cur; cur = cur * step; }
         }
         __syncthreads();
         for (int r = 0; r < cnt; ++r) {

@@ -75,7 +75,9 @@ struct M2LItem {
     int part;         // -1: write L directly; else partial-sum slot
 };
 // one list entry of a target box
-enum { M2L_REACT = 1, M2L_SRC_SLOT = 2, M2L_A_DOWN = 4, M2L_B_DOWN = 8, M2L_DST_SHIFT = 4 };
+// M2L_FLIP: the table is that of the mirrored pair (offset -X), read with both
+// indices reversed
+enum { M2L_REACT = 1, M2L_SRC_SLOT = 2, M2L_A_DOWN = 4, M2L_B_DOWN = 8, M2L_FLIP = 16, M2L_DST_SHIFT = 5 };
 struct M2LEnt {
     int64_t src;      // source coefficient offset (M, or Mp with M2L_SRC_SLOT)
     int64_t tab;      // free space: table id; reaction: offset of the moment table

@@ -209,19 +209,22 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
                     const cf* src = ((E.flags & M2L_SRC_SLOT) ? Mpc : Mc) + E.src;
                     const bool bdown = (E.flags & M2L_B_DOWN) != 0;
                     const int mrow = bdown ? nn : -nn;
-                    const cf* col_m = rtab + E.tab + (mrow + p);
+                    // column of row mrow; a mirrored table is read at (-mrow, -n)
+                    const bool flip = (E.flags & M2L_FLIP) != 0;
+                    const cf* col_m = rtab + E.tab + (flip ? (p - mrow) + (int64_t)2 * p * nco : (mrow + p));
+                    const int64_t cs = flip ? -(int64_t)nco : (int64_t)nco;
                     cf bsum = mkf(0, 0);
                     if (E.flags & M2L_A_DOWN) {
-                        for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[mi * nco], src[mi]);
+                        for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[mi * cs], src[mi]);
                     } else {
                         for (int mi = sl; mi < nco; mi += NS) {
                             cf v = src[2 * p - mi];
                             if ((mi - p) & 1) v = mkf(-v.x, -v.y);
-                            cfmaf(bsum, col_m[mi * nco], v);
+                            cfmaf(bsum, col_m[mi * cs], v);
                         }
                     }
                     if (!bdown && (mrow & 1)) bsum = mkf(-bsum.x, -bsum.y);
-                    const int dst = E.flags >> M2L_DST_SHIFT;
+                    const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
                     if (dst == 0) acc0 = addf(acc0, bsum);
                     else if (dst == 1) acc1 = addf(acc1, bsum);
                     else acc2 = addf(acc2, bsum);
