@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -186,6 +187,63 @@ def cpu_baseline(wl, rows_per_sample, n_samples=1):
             "sample": f"{cnt:g} full row(s) of the dense {n}x{n} Nystrom matrix with direct Sommerfeld "
                       f"quadrature, {dt:.1f} s; full matvec extrapolated to {t_full:.3g} s",
             "seconds": dt}
+
+
+def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
+    """Serving form on a bounded stand-in for the request stream (random 2-4 layer stacks,
+    k in [2, 12], N in [2k, 32k]): Poisson arrivals at 1.5x the FP64 one-at-a-time capacity.
+    Three arms see the same arrivals: FP64 one at a time (1 slot), FP64 served (``slots``
+    concurrent requests) and the served mixed-precision form; each solve to the FP64
+    residual 1e-8."""
+    from workloads import config_c5_stream
+
+    stream = config_c5_stream(n_requests, seed)
+    reqs = []
+    for wl in stream:
+        pts, w, _ = lfmm.polygon_elements(wl.bodies)
+        reqs.append((wl.medium, pts, w, math.radians(float(wl.angles_deg[0]))))
+    free, _total = __import__("torch").cuda.mem_get_info()
+    budget = int(0.5 * free)
+
+    def one_arm(n_slots, precision, arrivals):
+        srv = lfmm.Server(slots=n_slots, hbm_budget=budget)
+        t0 = time.perf_counter()
+        tickets = []
+        for (med, pts, w, ang), ta in zip(reqs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, tol=1e-8,
+                                      precision=precision, max_iter=1000))
+        lat, conv, res, its = [], 0, 0.0, 0
+        for t in tickets:
+            _x, info, tm = srv.wait(t)
+            lat.append(tm["latency_seconds"])
+            conv += int(info["converged"])
+            res = max(res, info["true_rel_residual"])
+            its += info["iterations"]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat) * 1e3
+        return {"slots": n_slots, "precision": "mixed" if precision else "fp64",
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "solves_per_s": len(reqs) / wall, "converged": conv, "max_true_rel_residual": res,
+                "iterations": its, "peak_running": st["peak_running"]}
+
+    # FP64 one-at-a-time capacity with back-to-back submission
+    cap = one_arm(1, 0, [0.0] * len(reqs))
+    rate = 1.5 * cap["solves_per_s"]
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    arms = [one_arm(1, 0, arrivals), one_arm(slots, 0, arrivals), one_arm(slots, 1, arrivals)]
+    sizes = [int(r[2].size) for r in reqs]
+    return {"metric": "served p50/p99 ms vs FP64 form",
+            "workload": f"{len(reqs)} requests, random 2-4 layer stacks, k in [2,12], N {min(sizes)}..{max(sizes)} "
+                        f"(Poisson arrivals at 1.5x the FP64 one-at-a-time capacity of "
+                        f"{cap['solves_per_s']:.2f} solves/s), tol 1e-8 on the FP64 residual",
+            "hbm_budget_bytes": budget, "fp64_one_at_a_time": arms[0], "fp64_served": arms[1],
+            "mixed_served": arms[2]}
 
 
 def run_reference(args):
@@ -341,6 +399,9 @@ def run_ours(args):
                           "converged": bool(im["converged"]), "op_rel_diff_on_b": im["op_rel_diff"],
                           "rel_diff_to_fp64_solution": float(torch.linalg.norm(xm - xs) / torch.linalg.norm(xs))}
 
+    serve = None
+    if rank == 0 and not args.no_serve and args.workload == "c2":
+        serve = run_serving(lfmm)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, 1 if args.workload == "c2" else 1.0)
@@ -364,6 +425,7 @@ def run_ours(args):
             "work": work,
             "solve": solve,
             "mixed": mixed,
+            "serve": serve,
             "setup_seconds": setup_s,
         }
         print(json.dumps(line))

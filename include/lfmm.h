@@ -215,6 +215,68 @@ lfmm_status lfmm_polygon_elements(int32_t n_poly, const int32_t *counts, const d
                                   double *points, double *weights, double *normals);
 
 /*
+ * Serving: a request loop for scattering solves (no counterpart in the paper,
+ * which solves one problem at a time).  Requests -- a layer stack, scatterer
+ * elements, one incidence angle, a tolerance and the precision -- queue in
+ * arrival order.  `slots` worker threads each drive one CUDA stream on the
+ * current device; a worker takes the request at the head of the queue as soon as
+ * the estimated device footprints of the running requests plus this one fit
+ * hbm_budget, and runs it end to end (lfmm_medium_create, lfmm_geometry_build,
+ * lfmm_rhs_plane_wave, lfmm_gmres_solve, copy of the solution, release).
+ * Requests that arrive while others run are admitted as slots and memory free
+ * up; their kernels overlap on the device.  Every kernel sums in a fixed order
+ * and each request has its own geometry and Krylov basis, so a result is the
+ * same alone and in the mix.
+ *   footprint estimate (bytes): 16 n (max_iter + 1) for the Krylov basis, plus
+ *   about 16 n (120 (1 + leaf/64) + 24) for near field, preconditioner and work
+ *   vectors, 4 n (2p + 1) for expansions, and 256 MiB for tables and scratch.
+ */
+typedef struct lfmm_server_s *lfmm_server;
+typedef struct {
+    int32_t slots;        /* concurrent requests (worker threads, one stream each), 1..64 */
+    int32_t reserved;
+    int64_t hbm_budget;   /* device bytes the running requests' footprints may total */
+} lfmm_server_params;
+typedef struct {
+    int32_t n_layers;            /* as lfmm_medium_create */
+    int32_t p;                   /* expansion order (<= 0: 20) */
+    const double *interface_y;   /* n_layers - 1 values */
+    const double *wavenumber;    /* 2 n_layers (re, im) */
+    const double *density;       /* n_layers */
+    int64_t n;                   /* elements */
+    const double *points;        /* 2n, host */
+    const double *weights;       /* n, host */
+    double angle_rad;            /* plane-wave incidence, (0, pi) */
+    double tol;                  /* GMRES relative residual (FP64 residual) */
+    int32_t precision;           /* 0: FP64 operator; 1: relaxed mixed precision */
+    int32_t leaf_size;           /* <= 0: 64 */
+    int32_t max_iter;
+    int32_t precond;             /* 1: DD preconditioner */
+} lfmm_request;                  /* every array is copied by lfmm_server_submit */
+typedef struct {
+    double queue_seconds;        /* submit -> admitted */
+    double service_seconds;      /* admitted -> solution in host memory */
+    double latency_seconds;      /* submit -> solution in host memory */
+    double setup_seconds;        /* geometry build inside the service time */
+    int64_t footprint_bytes;     /* the estimate admission used */
+} lfmm_request_times;
+
+/* Errors: LFMM_ERR_INVALID_ARG; LFMM_ERR_CUDA if no device is current. */
+lfmm_status lfmm_server_create(const lfmm_server_params *prm, lfmm_server *out);
+/* Queue a request; *ticket identifies it.  LFMM_ERR_HBM_BUDGET if its footprint
+ * estimate alone exceeds the budget (it could never be admitted). */
+lfmm_status lfmm_server_submit(lfmm_server s, const lfmm_request *req, int64_t *ticket);
+/* Block until the request is done; x (host, n complex) receives the solution Phi,
+ * info and times (either may be NULL) its GMRES record and timings.  Returns the
+ * request's status (the solve's, or the first error of its pipeline). */
+lfmm_status lfmm_server_wait(lfmm_server s, int64_t ticket, void *x, lfmm_gmres_info *info,
+                             lfmm_request_times *times);
+/* Largest total footprint admitted at once and largest number of requests run at once. */
+lfmm_status lfmm_server_stats(lfmm_server s, int64_t *peak_bytes, int32_t *peak_running);
+/* Runs the queued requests to completion, then stops the workers. */
+lfmm_status lfmm_server_destroy(lfmm_server s);
+
+/*
  * Introspection of a built geometry (used by the tests).  Copies the named
  * array to host memory: `needed` receives its size in bytes; if host_out is
  * NULL or nbytes is too small nothing is copied.  Names: "perm" (int32[n],

@@ -11,10 +11,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblfmm.so")
-SOURCES = ["api.cu", "near.cu", "fmm.cu", "solver.cu", "precond.cu", "tree.cpp", "static_scratch.cu", "mixed.cu"]
+SOURCES = ["api.cu", "near.cu", "fmm.cu", "solver.cu", "precond.cu", "tree.cpp", "static_scratch.cu", "mixed.cu", "serve.cpp"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--default-stream", "per-thread", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
 
 def _newest_input() -> float:

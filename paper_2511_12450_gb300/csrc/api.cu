@@ -306,7 +306,7 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
 lfmm_status lfmm_geometry_destroy(lfmm_geometry g) {
     return guarded([&]() -> lfmm_status {
         if (!g) return LFMM_OK;
-        cudaDeviceSynchronize();
+        cudaStreamSynchronize(cudaStreamPerThread);
         free_geometry(g);
         if (g->med) g->med->geometries -= 1;
         delete g;
@@ -367,9 +367,13 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         const size_t elems = (size_t)g->n * nrhs;
         cd* bb = nullptr;
         cd* xx = nullptr;
-        cuda_check(cudaMalloc(&bb, sizeof(cd) * elems), "malloc b");
-        cuda_check(cudaMalloc(&xx, sizeof(cd) * elems), "malloc x");
-        struct F { cd *a, *b; ~F() { cudaFree(a); cudaFree(b); } } fr{bb, xx};
+        cuda_check(cudaMallocAsync((void**)&bb, sizeof(cd) * elems, s), "malloc b");
+        cuda_check(cudaMallocAsync((void**)&xx, sizeof(cd) * elems, s), "malloc x");
+        struct F {
+            cd *a, *b;
+            cudaStream_t s;
+            ~F() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); }
+        } fr{bb, xx, s};
         cuda_check(cudaMemcpyAsync(g->d_ys, b, sizeof(cd) * elems, cudaMemcpyDefault, s), "b copy");
         gather_sorted(g, g->d_ys, bb, nrhs, s);
         lfmm_gmres_info local;

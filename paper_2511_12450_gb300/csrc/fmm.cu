@@ -487,7 +487,7 @@ void fmm_build(lfmm_geometry_s* g) {
             }
         }
     }
-    cuda_check(cudaDeviceSynchronize(), "fmm_build");
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "fmm_build");
 }
 
 static void set_smem_limits() {

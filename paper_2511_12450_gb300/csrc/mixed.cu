@@ -606,7 +606,7 @@ static void mixed_build(lfmm_geometry_s* g) {
         cuda_check(cudaFuncSetAttribute(k_l2p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_l2p),
                    "l2p32 smem");
     cudaError_t e1 = cudaGetLastError();
-    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
     cudaFree(d_tp); cudaFree(d_ts); cudaFree(d_kss); cudaFree(d_kst);
     cuda_check(e1, "k_react32_tables");
     cuda_check(e2, "precision form tables");

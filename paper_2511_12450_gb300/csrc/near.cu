@@ -201,7 +201,7 @@ void near_build(lfmm_geometry_s* g) {
                                                g->d_box_end, g->d_x, g->d_y, g->d_w, g->d_nb_val);
         cuda_check(cudaGetLastError(), "k_near_react");
     }
-    cuda_check(cudaDeviceSynchronize(), "near_build");
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "near_build");
 }
 
 void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {

@@ -203,7 +203,7 @@ void precond_build(lfmm_geometry_s* g) {
     k_pc_setup<<<nleaf, 256>>>(g->m, g->d_pc_ptr, g->d_pc_idx, d_own_pos, d_own_cnt, d_aoff, g->d_pc_woff, d_lay,
                                g->d_x, g->d_y, g->d_w, Ascr, piv, g->d_pc_W);
     cudaError_t e1 = cudaGetLastError();
-    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
     cudaFree(Ascr);
     cudaFree(piv);
     cuda_check(e1, "k_pc_setup");

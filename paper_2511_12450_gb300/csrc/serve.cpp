@@ -1,0 +1,251 @@
+// serve.cpp -- a request loop for scattering solves (lfmm_server_* in include/lfmm.h).
+//
+// Requests (a layer stack, scatterer elements, an incidence angle, a tolerance,
+// the precision) queue in arrival order.  `slots` worker threads each drive one
+// CUDA stream; a worker takes the request at the head of the queue as soon as
+// the estimated device footprints of the requests on the GPU plus this one fit
+// the HBM budget, and runs it end to end on its stream: medium, geometry (tree,
+// tables, near field, preconditioner), right-hand side, GMRES, copy of the
+// solution to host memory, release.  Requests that arrive while others run are
+// admitted as slots and memory free up, and their kernels overlap on the device
+// with the others'.  Each request keeps its own geometry and Krylov basis, and
+// every kernel sums in a fixed order, so a result is the same alone and in the
+// mix.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/lfmm.h"
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    int64_t ticket = 0;
+    int32_t n_layers = 0;
+    std::vector<double> yint, k, eta;
+    int64_t n = 0;
+    std::vector<double> pts, w;
+    double angle = 0.0, tol = 1e-8;
+    int32_t precision = 0, p = 20, leaf = 64, max_iter = 1000, precond = 1;
+    int64_t footprint = 0;
+    // results
+    std::vector<double> x;   // 2n (re, im)
+    lfmm_gmres_info info{};
+    lfmm_status status = LFMM_OK;
+    std::string err;
+    double t_submit = 0, t_admit = 0, t_done = 0, setup_s = 0;
+    bool done = false;
+};
+
+}  // namespace
+
+struct lfmm_server_s {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<int64_t, std::shared_ptr<Request>> tickets;
+    int64_t next_ticket = 1;
+    int64_t in_use = 0, budget = 0, peak_in_use = 0;
+    int running = 0, peak_running = 0;
+    bool stop = false;
+    int device = 0;
+    std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Device bytes one request holds while it runs: the Krylov basis (max_iter + 1
+// vectors), the stored near field and preconditioner (~62 and ~50 complex entries
+// per point at leaf size 64), multipoles/locals and work vectors, and the
+// reaction tables and set-up scratch (a fixed allowance).
+int64_t footprint_estimate(int64_t n, int p, int leaf, int max_iter) {
+    const double per_point = 16.0 * (max_iter + 1) + 16.0 * (1.0 + leaf / 64.0) * 120.0 + 16.0 * 24.0;
+    const double expansions = 16.0 * (2.0 * p + 1.0) * (double)n / 4.0;
+    return (int64_t)(per_point * (double)n + expansions) + ((int64_t)256 << 20);
+}
+
+void run_request(Request& r, cudaStream_t s) {
+    const double t0 = now_s();
+    lfmm_medium med = nullptr;
+    lfmm_geometry geo = nullptr;
+    void *db = nullptr, *dx = nullptr;
+    auto fail = [&](lfmm_status st) {
+        r.status = st;
+        r.err = lfmm_last_error();
+    };
+    do {
+        lfmm_status st = lfmm_medium_create(r.n_layers, r.yint.data(), r.k.data(), r.eta.data(), &med);
+        if (st < 0) { fail(st); break; }
+        lfmm_params prm{r.p, r.leaf, 0, 0};
+        st = lfmm_geometry_build(med, r.n, r.pts.data(), r.w.data(), nullptr, &prm, &geo);
+        if (st < 0) { fail(st); break; }
+        r.setup_s = now_s() - t0;
+        if (cudaMallocAsync(&db, 16 * (size_t)r.n, s) != cudaSuccess ||
+            cudaMallocAsync(&dx, 16 * (size_t)r.n, s) != cudaSuccess) {
+            r.status = LFMM_ERR_OUT_OF_MEMORY;
+            r.err = "cudaMallocAsync failed for the request's vectors";
+            break;
+        }
+        st = lfmm_rhs_plane_wave(geo, 1, &r.angle, db, LFMM_DEVICE_PTRS, s);
+        if (st < 0) { fail(st); break; }
+        lfmm_gmres_params gp{r.tol, r.max_iter, 0, r.precond, r.precision};
+        st = lfmm_gmres_solve(geo, 1, db, dx, &gp, &r.info, s);
+        if (st < 0) { fail(st); break; }
+        r.status = st;
+        r.x.resize(2 * (size_t)r.n);
+        if (cudaMemcpyAsync(r.x.data(), dx, 16 * (size_t)r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            r.status = LFMM_ERR_CUDA;
+            r.err = "copy of the solution failed";
+        }
+    } while (false);
+    if (db) cudaFreeAsync(db, s);
+    if (dx) cudaFreeAsync(dx, s);
+    cudaStreamSynchronize(s);
+    if (geo) lfmm_geometry_destroy(geo);
+    if (med) lfmm_medium_destroy(med);
+}
+
+void worker_main(lfmm_server_s* S) {
+    cudaSetDevice(S->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // admission: the head of the queue, once its footprint fits beside the running ones
+            S->cv_work.wait(lk, [&] {
+                return (S->stop && S->queue.empty()) ||
+                       (!S->queue.empty() && S->in_use + S->queue.front()->footprint <= S->budget);
+            });
+            if (S->queue.empty()) break;   // stopping, nothing left
+            r = S->queue.front();
+            S->queue.pop_front();
+            S->in_use += r->footprint;
+            S->peak_in_use = std::max(S->peak_in_use, S->in_use);
+            S->running += 1;
+            S->peak_running = std::max(S->peak_running, S->running);
+            r->t_admit = now_s();
+        }
+        run_request(*r, s);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->t_done = now_s();
+            r->done = true;
+            S->in_use -= r->footprint;
+            S->running -= 1;
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    if (s) cudaStreamDestroy(s);
+}
+
+}  // namespace
+
+extern "C" lfmm_status lfmm_server_create(const lfmm_server_params* prm, lfmm_server* out) {
+    if (!out || !prm) return LFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (prm->slots < 1 || prm->slots > 64 || prm->hbm_budget <= 0) return LFMM_ERR_INVALID_ARG;
+    lfmm_server_s* S = new lfmm_server_s();
+    S->budget = prm->hbm_budget;
+    if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return LFMM_ERR_CUDA; }
+    for (int i = 0; i < prm->slots; ++i) S->workers.emplace_back(worker_main, S);
+    *out = S;
+    return LFMM_OK;
+}
+
+extern "C" lfmm_status lfmm_server_submit(lfmm_server S, const lfmm_request* q, int64_t* ticket) {
+    if (!S || !q || !ticket) return LFMM_ERR_INVALID_ARG;
+    if (q->n_layers < 1 || q->n < 1 || !q->points || !q->weights || !q->wavenumber || !q->density ||
+        (q->n_layers > 1 && !q->interface_y) || !(q->tol > 0.0) || q->max_iter < 1 ||
+        (q->precision != 0 && q->precision != 1))
+        return LFMM_ERR_INVALID_ARG;
+    auto r = std::make_shared<Request>();
+    r->n_layers = q->n_layers;
+    r->yint.assign(q->interface_y, q->interface_y + (q->n_layers - 1));
+    r->k.assign(q->wavenumber, q->wavenumber + 2 * q->n_layers);
+    r->eta.assign(q->density, q->density + q->n_layers);
+    r->n = q->n;
+    r->pts.assign(q->points, q->points + 2 * q->n);
+    r->w.assign(q->weights, q->weights + q->n);
+    r->angle = q->angle_rad;
+    r->tol = q->tol;
+    r->precision = q->precision;
+    r->p = q->p > 0 ? q->p : 20;
+    r->leaf = q->leaf_size > 0 ? q->leaf_size : 64;
+    r->max_iter = q->max_iter;
+    r->precond = q->precond;
+    r->footprint = footprint_estimate(r->n, r->p, r->leaf, r->max_iter);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return LFMM_ERR_INVALID_ARG;
+        if (r->footprint > S->budget) return LFMM_ERR_HBM_BUDGET;   // would never be admitted
+        r->ticket = S->next_ticket++;
+        r->t_submit = now_s();
+        S->queue.push_back(r);
+        S->tickets[r->ticket] = r;
+        *ticket = r->ticket;
+    }
+    S->cv_work.notify_all();
+    return LFMM_OK;
+}
+
+extern "C" lfmm_status lfmm_server_wait(lfmm_server S, int64_t ticket, void* x, lfmm_gmres_info* info,
+                                        lfmm_request_times* times) {
+    if (!S) return LFMM_ERR_INVALID_ARG;
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->tickets.find(ticket);
+        if (it == S->tickets.end()) return LFMM_ERR_INVALID_ARG;
+        r = it->second;
+        S->cv_done.wait(lk, [&] { return r->done; });
+        S->tickets.erase(it);
+    }
+    if (info) *info = r->info;
+    if (times) {
+        times->queue_seconds = r->t_admit - r->t_submit;
+        times->service_seconds = r->t_done - r->t_admit;
+        times->latency_seconds = r->t_done - r->t_submit;
+        times->setup_seconds = r->setup_s;
+        times->footprint_bytes = r->footprint;
+    }
+    if (r->status < 0) return r->status;
+    if (x) std::memcpy(x, r->x.data(), 16 * (size_t)r->n);
+    return r->status;
+}
+
+extern "C" lfmm_status lfmm_server_stats(lfmm_server S, int64_t* peak_bytes, int32_t* peak_running) {
+    if (!S) return LFMM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (peak_bytes) *peak_bytes = S->peak_in_use;
+    if (peak_running) *peak_running = S->peak_running;
+    return LFMM_OK;
+}
+
+extern "C" lfmm_status lfmm_server_destroy(lfmm_server S) {
+    if (!S) return LFMM_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto& t : S->workers) t.join();
+    delete S;
+    return LFMM_OK;
+}

@@ -149,11 +149,11 @@ struct Blas {
     std::vector<cd> host;
     Blas(lfmm_geometry_s* g_, cudaStream_t s_, int maxcol) : g(g_), s(s_), cap(maxcol + 1) {
         const int64_t nchunk = (g->n + VH_ROWS - 1) / VH_ROWS;
-        cuda_check(cudaMalloc(&partial, sizeof(cd) * nchunk * cap), "malloc partial");
-        cuda_check(cudaMalloc(&dres, sizeof(cd) * (2 * cap + 1)), "malloc dres");
+        cuda_check(cudaMallocAsync((void**)&partial, sizeof(cd) * nchunk * cap, s), "malloc partial");
+        cuda_check(cudaMallocAsync((void**)&dres, sizeof(cd) * (2 * cap + 1), s), "malloc dres");
         host.resize(2 * cap + 1);
     }
-    ~Blas() { cudaFree(partial); cudaFree(dres); }
+    ~Blas() { cudaFreeAsync(partial, s); cudaFreeAsync(dres, s); }
     // out_dev[0..ncol) = V^H w, on the device, no synchronisation
     void vh(const cd* V, int ncol, int64_t ld, const cd* w, int64_t n, cd* out_dev) {
         const int nchunk = (int)((n + VH_ROWS - 1) / VH_ROWS);
@@ -183,11 +183,17 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
     const int64_t n = g->n;
     Blas bl(g, s, maxit + 1);
     cd *V = nullptr, *w = nullptr, *z = nullptr, *hd = nullptr;
-    cuda_check(cudaMalloc(&V, sizeof(cd) * n * (size_t)(maxit + 1)), "malloc V");
-    cuda_check(cudaMalloc(&w, sizeof(cd) * n), "malloc w");
-    cuda_check(cudaMalloc(&z, sizeof(cd) * n), "malloc z");
-    cuda_check(cudaMalloc(&hd, sizeof(cd) * (maxit + 2)), "malloc h");
-    struct Free { cd *a, *b, *c, *d; ~Free() { cudaFree(a); cudaFree(b); cudaFree(c); cudaFree(d); } } fr{V, w, z, hd};
+    // stream-ordered allocations: no device-wide synchronisation, so solves on other
+    // streams keep running
+    cuda_check(cudaMallocAsync((void**)&V, sizeof(cd) * n * (size_t)(maxit + 1), s), "malloc V");
+    cuda_check(cudaMallocAsync((void**)&w, sizeof(cd) * n, s), "malloc w");
+    cuda_check(cudaMallocAsync((void**)&z, sizeof(cd) * n, s), "malloc z");
+    cuda_check(cudaMallocAsync((void**)&hd, sizeof(cd) * (maxit + 2), s), "malloc h");
+    struct Free {
+        cd *a, *b, *c, *d;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); cudaFreeAsync(d, s); }
+    } fr{V, w, z, hd, s};
     double beta = bl.norm(b, n);
     cuda_check(cudaMemsetAsync(x, 0, sizeof(cd) * n, s), "memset x");
     if (beta == 0.0) { *iters = 0; *res_out = 0.0; return 1; }
@@ -281,10 +287,14 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
     int all = 1, it = 0, outer_last = 0, f64_last = 0;
     double worst = 0.0, worst_true = 0.0, worst_opdiff = 0.0;
     cd *r = nullptr, *d = nullptr, *y2 = nullptr;
-    cuda_check(cudaMalloc(&r, sizeof(cd) * n), "malloc r");
-    cuda_check(cudaMalloc(&d, sizeof(cd) * n), "malloc d");
-    cuda_check(cudaMalloc(&y2, sizeof(cd) * n), "malloc y2");
-    struct Free { cd *a, *b, *c; ~Free() { cudaFree(a); cudaFree(b); cudaFree(c); } } fr{r, d, y2};
+    cuda_check(cudaMallocAsync((void**)&r, sizeof(cd) * n, s), "malloc r");
+    cuda_check(cudaMallocAsync((void**)&d, sizeof(cd) * n, s), "malloc d");
+    cuda_check(cudaMallocAsync((void**)&y2, sizeof(cd) * n, s), "malloc y2");
+    struct Free {
+        cd *a, *b, *c;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); }
+    } fr{r, d, y2, s};
     Blas bl(g, s, 2);
     // ||(A_mixed - A) v|| / ||A v||
     auto op_diff = [&](const cd* v) {

@@ -36,6 +36,7 @@ EXPORTED = [
     "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
     "lfmm_rhs_plane_wave", "lfmm_matvec", "lfmm_gmres_solve", "lfmm_eval_field",
     "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error", "lfmm_matvec_static",
+    "lfmm_server_create", "lfmm_server_submit", "lfmm_server_wait", "lfmm_server_stats", "lfmm_server_destroy",
 ]
 
 
@@ -64,6 +65,27 @@ class GmresInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("interface_y", ctypes.c_void_p), ("wavenumber", ctypes.c_void_p), ("density", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("points", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("angle_rad", ctypes.c_double), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("precond", ctypes.c_int32)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("queue_seconds", ctypes.c_double), ("service_seconds", ctypes.c_double),
+                ("latency_seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _LIB = None
 
 
@@ -86,6 +108,11 @@ def library():
         lib.lfmm_eval_field.argtypes = [vp, i32, vp, i64, dp, vp, i32, vp]
         lib.lfmm_polygon_elements.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]
         lib.lfmm_geometry_query.argtypes = [vp, ctypes.c_char_p, vp, i64, ctypes.POINTER(i64)]
+        lib.lfmm_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)]
+        lib.lfmm_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(i64)]
+        lib.lfmm_server_wait.argtypes = [vp, i64, vp, ctypes.POINTER(GmresInfo), ctypes.POINTER(RequestTimes)]
+        lib.lfmm_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        lib.lfmm_server_destroy.argtypes = [vp]
         lib.lfmm_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "lfmm_last_error":
@@ -286,3 +313,57 @@ def stage_times(g: Geometry) -> dict:
     """Per-stage launch counts and total milliseconds (geometries built with profile=True)."""
     v = geometry_query(g, "stage_times", np.float64).reshape(-1, 2)
     return {name: {"count": int(v[i, 0]), "ms": float(v[i, 1])} for i, name in enumerate(STAGES)}
+
+
+class Server:
+    """Request loop for scattering solves (lfmm_server_*): ``slots`` concurrent requests,
+    admission by estimated device footprint within ``hbm_budget`` bytes."""
+
+    def __init__(self, slots: int, hbm_budget: int):
+        self.handle = ctypes.c_void_p()
+        _check(library().lfmm_server_create(ctypes.byref(ServerParams(int(slots), 0, int(hbm_budget))),
+                                            ctypes.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, interfaces, k, eta, points, weights, angle_rad: float, tol: float = 1e-8,
+               precision: int = 0, p: int = 20, leaf_size: int = 64, max_iter: int = 1000,
+               precond: bool = True) -> int:
+        yint = _f64(interfaces).reshape(-1)
+        kc = np.ascontiguousarray(np.asarray(k).astype(np.complex128).reshape(-1))
+        et = _f64(eta).reshape(-1)
+        pts = _f64(points).reshape(-1, 2)
+        w = _f64(weights).reshape(-1)
+        req = Request(int(kc.size), int(p), ctypes.c_void_p(yint.ctypes.data) if yint.size else None,
+                      ctypes.c_void_p(kc.ctypes.data), ctypes.c_void_p(et.ctypes.data), int(w.size),
+                      ctypes.c_void_p(pts.ctypes.data), ctypes.c_void_p(w.ctypes.data), float(angle_rad),
+                      float(tol), int(precision), int(leaf_size), int(max_iter), 1 if precond else 0)
+        t = ctypes.c_int64(0)
+        _check(library().lfmm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = w.size
+        return t.value
+
+    def wait(self, ticket: int):
+        n = self._keep.pop(ticket)
+        x = np.empty(n, dtype=np.complex128)
+        info, times = GmresInfo(), RequestTimes()
+        st = _check(library().lfmm_server_wait(self.handle, int(ticket), ctypes.c_void_p(x.ctypes.data),
+                                               ctypes.byref(info), ctypes.byref(times)))
+        d = info.as_dict()
+        d["status"] = st
+        return x, d, times.as_dict()
+
+    def stats(self):
+        b, r = ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(library().lfmm_server_stats(self.handle, ctypes.byref(b), ctypes.byref(r)))
+        return {"peak_bytes": b.value, "peak_running": r.value}
+
+    def close(self):
+        if self.handle:
+            library().lfmm_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,6 +20,7 @@ from .geometry import (  # noqa: F401
     config_c3,
     config_c4,
     config_c5_request,
+    config_c5_stream,
     example1,
     example2,
     example3,

@@ -217,19 +217,28 @@ def config_c4(seed: int = 12454):
     return out
 
 
-def config_c5_request(rng: np.random.Generator) -> Workload:
+def config_c5_request(rng: np.random.Generator, n_min: float = 2048.0, n_max: float = 262144.0,
+                      max_bodies: int = 512) -> Workload:
     """One serving request: random layer stack and a random field of bodies."""
     nlay = int(rng.integers(2, 5))
     interfaces = -2.0 * np.arange(nlay - 1)
     k = rng.uniform(2.0, 12.0, size=nlay)
     med = Medium(interfaces=interfaces, k=k, eta=np.arange(1, nlay + 1, dtype=float))
-    nb = int(rng.integers(1, 513))
-    n = float(np.exp(rng.uniform(np.log(2048.0), np.log(262144.0))))
+    nb = int(rng.integers(1, max_bodies + 1))
+    n = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
     nodes = max(64, int(round(n / nb)))
     side = 20.0 * math.sqrt(nb / 64.0)
     region = ((-side / 2, side / 2), (-side * 0.25 - 1.0, side * 0.25 + 1.0))
     polys = random_bodies(rng, nb, region, med.interfaces, nodes)
     return Workload("C5_req", med, polys, np.array([float(rng.uniform(5.0, 175.0))]), p=20)
+
+
+def config_c5_stream(n_requests: int = 24, seed: int = 12455, n_min: float = 2048.0, n_max: float = 32768.0,
+                     max_bodies: int = 32) -> list:
+    """A bounded stand-in for the serving stream: requests drawn like config_c5_request but
+    with N in [n_min, n_max] and at most ``max_bodies`` bodies, so a run takes about a minute."""
+    rng = np.random.default_rng(seed)
+    return [config_c5_request(rng, n_min, n_max, max_bodies) for _ in range(n_requests)]
 
 
 def example1(n: int = 12000) -> Workload:
