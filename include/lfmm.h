@@ -138,6 +138,8 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m);
 lfmm_status lfmm_geometry_build(lfmm_medium m, int64_t n, const double *points,
                                 const double *weights, const double *normals,
                                 const lfmm_params *prm, lfmm_geometry *out);
+/* Releases the geometry's device memory (stream-ordered, without a device-wide
+ * synchronisation): synchronise every stream passed to calls on it first. */
 lfmm_status lfmm_geometry_destroy(lfmm_geometry g);
 
 /*

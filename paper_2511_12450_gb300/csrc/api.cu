@@ -132,32 +132,33 @@ static void free_geometry(lfmm_geometry_s* g) {
     g->prof.on = false;
     fmm_free(g);
     mixed_destroy(g);
-    for (void* p : g->allocs) cudaFree(p);
+    for (void* p : g->allocs) dev_release(p);
     g->allocs.clear();
-    if (g->d_xs) cudaFree(g->d_xs);
-    if (g->d_ys) cudaFree(g->d_ys);
-    if (g->d_hostbuf_x) cudaFree(g->d_hostbuf_x);
-    if (g->d_hostbuf_y) cudaFree(g->d_hostbuf_y);
+    dev_release(g->d_xs);
+    dev_release(g->d_ys);
+    dev_release(g->d_hostbuf_x);
+    dev_release(g->d_hostbuf_y);
+    cudaStreamSynchronize(cudaStreamPerThread);
 }
 
 // sorted-order scratch and host staging for nrhs columns
 static void ensure_scratch(lfmm_geometry_s* g, int nrhs) {
     if (g->nrhs_cap < nrhs) {
-        if (g->d_xs) cudaFree(g->d_xs);
-        if (g->d_ys) cudaFree(g->d_ys);
+        dev_release_now(g->d_xs);
+        dev_release_now(g->d_ys);
         g->d_xs = g->d_ys = nullptr;
-        cuda_check(cudaMalloc(&g->d_xs, sizeof(cd) * g->n * nrhs), "cudaMalloc scratch");
-        cuda_check(cudaMalloc(&g->d_ys, sizeof(cd) * g->n * nrhs), "cudaMalloc scratch");
+        g->d_xs = (cd*)dev_alloc_ready(sizeof(cd) * g->n * nrhs, "scratch");
+        g->d_ys = (cd*)dev_alloc_ready(sizeof(cd) * g->n * nrhs, "scratch");
         g->nrhs_cap = nrhs;
     }
 }
 static void ensure_hostbuf(lfmm_geometry_s* g, size_t elems) {
     if (g->hostbuf_cap < elems) {
-        if (g->d_hostbuf_x) cudaFree(g->d_hostbuf_x);
-        if (g->d_hostbuf_y) cudaFree(g->d_hostbuf_y);
+        dev_release_now(g->d_hostbuf_x);
+        dev_release_now(g->d_hostbuf_y);
         g->d_hostbuf_x = g->d_hostbuf_y = nullptr;
-        cuda_check(cudaMalloc(&g->d_hostbuf_x, sizeof(cd) * elems), "cudaMalloc staging");
-        cuda_check(cudaMalloc(&g->d_hostbuf_y, sizeof(cd) * elems), "cudaMalloc staging");
+        g->d_hostbuf_x = (cd*)dev_alloc_ready(sizeof(cd) * elems, "staging");
+        g->d_hostbuf_y = (cd*)dev_alloc_ready(sizeof(cd) * elems, "staging");
         g->hostbuf_cap = elems;
     }
 }
@@ -429,9 +430,14 @@ lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void* density, 
         gather_sorted(g, g->d_ys, g->d_xs, nrhs, s);
         double* d_t = nullptr;
         cd* d_u = nullptr;
-        cuda_check(cudaMalloc(&d_t, sizeof(double) * 2 * m), "malloc targets");
-        cuda_check(cudaMalloc(&d_u, sizeof(cd) * m * nrhs), "malloc u");
-        struct F { double* a; cd* b; ~F() { cudaFree(a); cudaFree(b); } } fr{d_t, d_u};
+        cuda_check(cudaMallocAsync((void**)&d_t, sizeof(double) * 2 * m, s), "malloc targets");
+        cuda_check(cudaMallocAsync((void**)&d_u, sizeof(cd) * m * nrhs, s), "malloc u");
+        struct F {
+            double* a;
+            cd* b;
+            cudaStream_t s;
+            ~F() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); }
+        } fr{d_t, d_u, s};
         cuda_check(cudaMemcpyAsync(d_t, targets, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s), "targets");
         eval_field_direct(g, nrhs, g->d_xs, m, d_t, d_u, s);
         cuda_check(cudaMemcpyAsync(u, d_u, sizeof(cd) * m * nrhs, cudaMemcpyDefault, s), "u copy");

@@ -502,22 +502,22 @@ static void set_smem_limits() {
 
 static void ensure_coef(lfmm_geometry_s* g, int nrhs) {
     if (g->coef_cols >= nrhs) return;
-    if (g->d_M) { cudaFree(g->d_M); cudaFree(g->d_L); }
-    if (g->d_Mp) { cudaFree(g->d_Mp); cudaFree(g->d_Lp); }
+    dev_release_now(g->d_M); dev_release_now(g->d_L);
+    dev_release_now(g->d_Mp); dev_release_now(g->d_Lp);
     g->d_M = g->d_L = g->d_Mp = g->d_Lp = nullptr;
-    cuda_check(cudaMalloc(&g->d_M, sizeof(cd) * std::max<int64_t>(g->ncoef, 1) * nrhs), "cudaMalloc M");
-    cuda_check(cudaMalloc(&g->d_L, sizeof(cd) * std::max<int64_t>(g->ncoef, 1) * nrhs), "cudaMalloc L");
-    cuda_check(cudaMalloc(&g->d_Mp, sizeof(cd) * std::max<int64_t>(g->nslotcoef, 1) * nrhs), "cudaMalloc Mp");
-    cuda_check(cudaMalloc(&g->d_Lp, sizeof(cd) * std::max<int64_t>(g->nslotcoef, 1) * nrhs), "cudaMalloc Lp");
+    g->d_M = (cd*)dev_alloc_ready(sizeof(cd) * std::max<int64_t>(g->ncoef, 1) * nrhs, "M");
+    g->d_L = (cd*)dev_alloc_ready(sizeof(cd) * std::max<int64_t>(g->ncoef, 1) * nrhs, "L");
+    g->d_Mp = (cd*)dev_alloc_ready(sizeof(cd) * std::max<int64_t>(g->nslotcoef, 1) * nrhs, "Mp");
+    g->d_Lp = (cd*)dev_alloc_ready(sizeof(cd) * std::max<int64_t>(g->nslotcoef, 1) * nrhs, "Lp");
     g->coef_cols = nrhs;
 }
 
 void fmm_free(lfmm_geometry_s* g) {
-    if (g->d_m2l_part) cudaFree(g->d_m2l_part);
+    dev_release(g->d_m2l_part);
     g->d_m2l_part = nullptr;
     g->m2l_part_cols = 0;
-    if (g->d_M) { cudaFree(g->d_M); cudaFree(g->d_L); }
-    if (g->d_Mp) { cudaFree(g->d_Mp); cudaFree(g->d_Lp); }
+    dev_release(g->d_M); dev_release(g->d_L);
+    dev_release(g->d_Mp); dev_release(g->d_Lp);
     g->d_M = g->d_L = g->d_Mp = g->d_Lp = nullptr;
     g->coef_cols = 0;
 }
@@ -583,10 +583,10 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         const int n64 = g->m2l_item_level_start[lm];
         const int r64 = g->m2l_red_level_start[lm];
         if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
-            if (g->d_m2l_part) cudaFree(g->d_m2l_part);
+            dev_release_now(g->d_m2l_part);
             g->d_m2l_part = nullptr;
-            cuda_check(cudaMalloc(&g->d_m2l_part, sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * nrhs),
-                       "cudaMalloc M2L partial sums");
+            g->d_m2l_part = (cd*)dev_alloc_ready(sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * nrhs,
+                                                 "M2L partial sums");
             g->m2l_part_cols = nrhs;
         }
         if (n64 > 0) {

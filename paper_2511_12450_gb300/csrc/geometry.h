@@ -218,18 +218,43 @@ struct CudaError {
     std::string msg;
 };
 void cuda_check(cudaError_t e, const char* what);
+// Device memory of a geometry.  Allocations are stream-ordered on the calling
+// thread's default stream so that building or releasing one geometry does not
+// synchronise the device (other geometries' work keeps running).
+// dev_alloc_ready: a work buffer, ready for use on any stream when it returns.
+inline void* dev_alloc_ready(size_t bytes, const char* what) {
+    void* p = nullptr;
+    cuda_check(cudaMallocAsync(&p, bytes, cudaStreamPerThread), what);
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), what);
+    return p;
+}
+// dev_release_now: a work buffer being replaced by a larger one; work queued on
+// any stream may still read it, so the device is synchronised first (rare).
+inline void dev_release_now(void* p) {
+    if (p) { cudaDeviceSynchronize(); cudaFree(p); }
+}
+// dev_release: release at destroy; the caller guarantees that no work using the
+// geometry is in flight (every stream it passed has been synchronised).
+inline void dev_release(void* p) {
+    if (p) cudaFreeAsync(p, cudaStreamPerThread);
+}
 template <class T>
 T* dalloc(lfmm_geometry_s* g, size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    cuda_check(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+    // stream-ordered: no device-wide synchronisation, so work of other geometries keeps
+    // running while this one is built (the build synchronises its own stream at the end)
+    cuda_check(cudaMallocAsync(&p, count * sizeof(T), cudaStreamPerThread), "cudaMallocAsync");
     g->allocs.push_back(p);
     return (T*)p;
 }
 template <class T>
 T* dupload(lfmm_geometry_s* g, const std::vector<T>& v) {
     T* p = dalloc<T>(g, v.size());
-    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+    // from pageable memory the call returns once the source has been staged
+    if (!v.empty())
+        cuda_check(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, cudaStreamPerThread),
+                   "upload");
     return p;
 }
 

@@ -474,8 +474,13 @@ __global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-static void mixed_free_buffers(MixedState* ms) {
-    cudaFree(ms->M); cudaFree(ms->L); cudaFree(ms->Mp); cudaFree(ms->Lp); cudaFree(ms->part);
+// replacing (in_flight: queued work may still read them) or releasing at destroy
+static void mixed_free_buffers(MixedState* ms, bool in_flight) {
+    void* bufs[5] = {ms->M, ms->L, ms->Mp, ms->Lp, ms->part};
+    for (void* b : bufs) {
+        if (in_flight) dev_release_now(b);
+        else dev_release(b);
+    }
     ms->M = ms->L = ms->Mp = ms->Lp = ms->part = nullptr;
     ms->cols = 0;
 }
@@ -483,9 +488,10 @@ static void mixed_free_buffers(MixedState* ms) {
 void mixed_destroy(lfmm_geometry_s* g) {
     if (!g->mixed) return;
     MixedState* ms = g->mixed;
-    mixed_free_buffers(ms);
-    cudaFree(ms->ispow); cudaFree(ms->ispow_slot); cudaFree(ms->ftab); cudaFree(ms->ftab_off); cudaFree(ms->rtab);
-    cudaFree(ms->d_scale); cudaFree(ms->wtab); cudaFree(ms->wtab_off); cudaFree(ms->d_xd_layer);
+    mixed_free_buffers(ms, false);
+    dev_release(ms->ispow); dev_release(ms->ispow_slot); dev_release(ms->ftab); dev_release(ms->ftab_off);
+    dev_release(ms->rtab); dev_release(ms->d_scale); dev_release(ms->wtab); dev_release(ms->wtab_off);
+    dev_release(ms->d_xd_layer);
     delete ms;
     g->mixed = nullptr;
 }
@@ -494,9 +500,11 @@ template <typename T>
 static T* upload_raw(const std::vector<T>& v, size_t& bytes) {
     T* p = nullptr;
     const size_t b = sizeof(T) * std::max<size_t>(v.size(), 1);
-    cuda_check(cudaMalloc(&p, b), "cudaMalloc (precision form)");
+    cuda_check(cudaMallocAsync((void**)&p, b, cudaStreamPerThread), "cudaMallocAsync (precision form)");
     bytes += b;
-    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
+    if (!v.empty())
+        cuda_check(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, cudaStreamPerThread),
+                   "upload");
     return p;
 }
 
@@ -543,7 +551,8 @@ static void mixed_build(lfmm_geometry_s* g) {
     int* d_tp = upload_raw(tp, scratch);
     double* d_ts = upload_raw(ts, scratch);
     ms->ftab_off = upload_raw(off32, ms->bytes);
-    cuda_check(cudaMalloc(&ms->ftab, sizeof(cf) * std::max<int64_t>(tot, 1)), "cudaMalloc ftab32");
+    cuda_check(cudaMallocAsync((void**)&ms->ftab, sizeof(cf) * std::max<int64_t>(tot, 1), cudaStreamPerThread),
+               "cudaMallocAsync ftab32");
     ms->bytes += sizeof(cf) * std::max<int64_t>(tot, 1);
     if (ntab > 0) k_free32_tables<<<ntab, 256>>>(g->d_m2lf, g->d_m2lf_off, d_tp, d_ts, ms->ftab_off, ms->ftab);
     cuda_check(cudaGetLastError(), "k_free32_tables");
@@ -559,7 +568,8 @@ static void mixed_build(lfmm_geometry_s* g) {
     }
     double* d_kss = upload_raw(kss, scratch);
     double* d_kst = upload_raw(kst, scratch);
-    cuda_check(cudaMalloc(&ms->rtab, sizeof(cf) * std::max<int64_t>(rtot, 1)), "cudaMalloc rtab32");
+    cuda_check(cudaMallocAsync((void**)&ms->rtab, sizeof(cf) * std::max<int64_t>(rtot, 1), cudaStreamPerThread),
+               "cudaMallocAsync rtab32");
     ms->bytes += sizeof(cf) * std::max<int64_t>(rtot, 1);
     if (nk > 0) k_react32_tables<<<nk, 256>>>(g->d_m2lr, g->d_rkeys, d_kss, d_kst, ms->rtab);
     // dense scaled tables of the FP32 M2M passes (parents at levels >= lm) and L2L
@@ -581,7 +591,8 @@ static void mixed_build(lfmm_geometry_s* g) {
     for (int lp = D - 1; lp >= ms->lm; --lp) plan(g->up_begin[lp], g->up_end[lp]);
     for (int l = ms->lm + 1; l <= D; ++l) plan(g->dn_begin[l], g->dn_end[l]);
     ms->wtab_off = upload_raw(woff, ms->bytes);
-    cuda_check(cudaMalloc(&ms->wtab, sizeof(cf) * std::max<int64_t>(wtot, 1)), "cudaMalloc pass tables 32");
+    cuda_check(cudaMallocAsync((void**)&ms->wtab, sizeof(cf) * std::max<int64_t>(wtot, 1), cudaStreamPerThread),
+               "cudaMallocAsync pass tables 32");
     ms->bytes += sizeof(cf) * std::max<int64_t>(wtot, 1);
     for (int lp = D - 1; lp >= ms->lm; --lp) {
         const int nd = g->up_end[lp] - g->up_begin[lp];
@@ -607,7 +618,7 @@ static void mixed_build(lfmm_geometry_s* g) {
                    "l2p32 smem");
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
-    cudaFree(d_tp); cudaFree(d_ts); cudaFree(d_kss); cudaFree(d_kst);
+    dev_release(d_tp); dev_release(d_ts); dev_release(d_kss); dev_release(d_kst);
     cuda_check(e1, "k_react32_tables");
     cuda_check(e2, "precision form tables");
 }
@@ -629,15 +640,15 @@ void mixed_setup(lfmm_geometry_s* g, int nrhs) {
     if (!g->mixed) mixed_build(g);
     MixedState* ms = g->mixed;
     if (ms->cols < nrhs) {
-        mixed_free_buffers(ms);
+        mixed_free_buffers(ms, true);
         const size_t nc = (size_t)std::max<int64_t>(g->ncoef, 1) * nrhs;
         const size_t ns = (size_t)std::max<int64_t>(g->nslotcoef, 1) * nrhs;
-        cuda_check(cudaMalloc(&ms->M, sizeof(cf) * nc), "cudaMalloc M32");
-        cuda_check(cudaMalloc(&ms->L, sizeof(cf) * nc), "cudaMalloc L32");
-        cuda_check(cudaMalloc(&ms->Mp, sizeof(cf) * ns), "cudaMalloc Mp32");
-        cuda_check(cudaMalloc(&ms->Lp, sizeof(cf) * ns), "cudaMalloc Lp32");
-        cuda_check(cudaMalloc(&ms->part, sizeof(cf) * (size_t)std::max(g->n_m2l_parts, 1) * 3 * XT_W * nrhs),
-                   "cudaMalloc M2L partial sums 32");
+        ms->M = (cf*)dev_alloc_ready(sizeof(cf) * nc, "M32");
+        ms->L = (cf*)dev_alloc_ready(sizeof(cf) * nc, "L32");
+        ms->Mp = (cf*)dev_alloc_ready(sizeof(cf) * ns, "Mp32");
+        ms->Lp = (cf*)dev_alloc_ready(sizeof(cf) * ns, "Lp32");
+        ms->part = (cf*)dev_alloc_ready(sizeof(cf) * (size_t)std::max(g->n_m2l_parts, 1) * 3 * XT_W * nrhs,
+                                        "M2L partial sums 32");
         ms->cols = nrhs;
     }
 }

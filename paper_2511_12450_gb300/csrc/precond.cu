@@ -198,14 +198,16 @@ void precond_build(lfmm_geometry_s* g) {
     g->d_pc_W = dalloc<cd>(g, (size_t)wt);
     cd* Ascr = nullptr;
     int* piv = nullptr;
-    cuda_check(cudaMalloc(&Ascr, sizeof(cd) * std::max<int64_t>(at, 1)), "malloc pc scratch");
-    cuda_check(cudaMalloc(&piv, sizeof(int) * std::max<size_t>(idx.size(), 1)), "malloc pc piv");
+    cuda_check(cudaMallocAsync((void**)&Ascr, sizeof(cd) * std::max<int64_t>(at, 1), cudaStreamPerThread),
+               "malloc pc scratch");
+    cuda_check(cudaMallocAsync((void**)&piv, sizeof(int) * std::max<size_t>(idx.size(), 1), cudaStreamPerThread),
+               "malloc pc piv");
     k_pc_setup<<<nleaf, 256>>>(g->m, g->d_pc_ptr, g->d_pc_idx, d_own_pos, d_own_cnt, d_aoff, g->d_pc_woff, d_lay,
                                g->d_x, g->d_y, g->d_w, Ascr, piv, g->d_pc_W);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
-    cudaFree(Ascr);
-    cudaFree(piv);
+    dev_release(Ascr);
+    dev_release(piv);
     cuda_check(e1, "k_pc_setup");
     cuda_check(e2, "k_pc_setup sync");
     g->pc_own_first = d_own_first;

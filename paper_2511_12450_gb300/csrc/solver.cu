@@ -438,13 +438,13 @@ __global__ void k_rhs(MediumDev m, const double* __restrict__ px, const double* 
 
 void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s) {
     double* d_ang = nullptr;
-    cuda_check(cudaMalloc(&d_ang, sizeof(double) * nrhs), "malloc angles");
+    cuda_check(cudaMallocAsync((void**)&d_ang, sizeof(double) * nrhs, s), "malloc angles");
     cuda_check(cudaMemcpyAsync(d_ang, angles_host, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "angles h2d");
     int64_t tot = g->n * nrhs;
     k_rhs<<<nblk(tot), 256, 0, s>>>(g->m, g->d_x, g->d_y, g->d_layer, d_ang, nrhs, g->n, b_sorted);
     cuda_check(cudaGetLastError(), "k_rhs");
     cuda_check(cudaStreamSynchronize(s), "rhs");
-    cudaFree(d_ang);
+    cudaFreeAsync(d_ang, s);
 }
 
 // ------------------------------------------------------------------ scattered field (eq. integralrep)
@@ -490,7 +490,7 @@ void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64
     std::vector<double> compH(g->tree.comps.size());
     for (size_t c = 0; c < compH.size(); ++c) compH[c] = g->tree.comps[c].Hc;
     double* d_compH = nullptr;
-    cuda_check(cudaMalloc(&d_compH, sizeof(double) * std::max<size_t>(1, compH.size())), "malloc compH");
+    cuda_check(cudaMallocAsync((void**)&d_compH, sizeof(double) * std::max<size_t>(1, compH.size()), s), "malloc compH");
     if (!compH.empty())
         cuda_check(cudaMemcpyAsync(d_compH, compH.data(), sizeof(double) * compH.size(), cudaMemcpyHostToDevice, s),
                    "compH");
@@ -502,7 +502,7 @@ void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64
                                                              nrhs, d_targets, mt, u);
     cuda_check(cudaGetLastError(), "k_field");
     cuda_check(cudaStreamSynchronize(s), "field");
-    cudaFree(d_compH);
+    cudaFreeAsync(d_compH, s);
 }
 
 }  // namespace lfmm
