@@ -165,9 +165,10 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
 /*
  * y = K x like lfmm_matvec (one right-hand side, DEVICE pointers on `stream`),
  * but allocating nothing.  The paper has no counterpart: this exists for
- * callers that cannot allocate device memory when they need a matvec -- code
- * running while a stream is captured into a CUDA graph, real-time threads that
- * must stay out of the allocator, hosts with a fixed memory budget.  lfmm_matvec
+ * callers that cannot allocate device memory when they need a matvec --
+ * real-time threads that must stay out of the allocator (an allocation can block
+ * and synchronise the device), hosts with a fixed memory budget, frameworks whose
+ * own pool owns the device memory.  lfmm_matvec
  * allocates its work buffers on first use; this call uses instead one
  * file-scope device array of 32 MiB that every GPU loading the library holds
  * until the process exits.

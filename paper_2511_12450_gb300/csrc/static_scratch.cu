@@ -1,10 +1,10 @@
 // static_scratch.cu -- lfmm_matvec_static: the Nystrom matvec without any allocation.
 //
 // Some callers cannot allocate device memory at the moment they need a matvec:
-// code that runs while a CUDA stream is being captured into a graph (a
-// cudaMalloc there breaks the capture), real-time serving threads that must not
-// enter the allocator or the driver's memory manager, and hosts that hand the
-// library a fixed memory budget up front.  lfmm_matvec lazily allocates its
+// real-time serving threads that must not enter the allocator (cudaMalloc can
+// block on the driver's memory manager and synchronise the device), hosts that
+// hand the library a fixed memory budget up front, and frameworks whose own pool
+// owns the device memory, where an allocation outside it may fail or fragment.  lfmm_matvec lazily allocates its
 // work buffers (sorted copies of x and y, the multipole and local coefficients)
 // on first use; this entry point instead uses one file-scope device array of
 // fixed size, reserved when the library is loaded.

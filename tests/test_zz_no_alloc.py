@@ -1,8 +1,9 @@
 """lfmm_matvec_static: the matvec for callers that cannot allocate device memory.
 
-Callers running under stream capture, real-time threads that must stay out of
-the allocator, or hosts with a fixed memory budget cannot let the library
-allocate its work buffers on the first matvec.  lfmm_matvec_static uses one
+Real-time threads that must stay out of the allocator (an allocation can block
+and synchronise the device), hosts with a fixed memory budget, or frameworks whose
+own pool owns the device memory cannot let the library allocate its work buffers
+on the first matvec.  lfmm_matvec_static uses one
 fixed device array instead; this test calls it through the C ABI twice in a
 row and checks each result against lfmm_matvec on the same input.  It is kept
 in a file of its own, collected after the other tests.
