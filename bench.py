@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--replay", action="store_true",
+                    help="replay the paper's Examples 1-3 (Sec. 5, Tables 5.1-5.3) as GPU solves and exit")
+    ap.add_argument("--replay-max", type=int, default=192000, help="largest element count of the replay")
     return ap.parse_args()
 
 
@@ -256,6 +259,68 @@ def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
             "hbm_budget_bytes": budget, **out}
 
 
+# the paper's Tables 5.1-5.3 (Sec. 5): elements, GMRES iterations without / with the DD
+# preconditioner, and for Example 1 the L_inf error column (CPU times on unstated hardware
+# are context only and not compared)
+PAPER_TABLES = {
+    "E1": {"elements": [12000, 24000, 48000, 96000, 192000], "iters": [140, 163, 190, 278, 331],
+           "iters_pc": [60, 68, 77, 86, 99], "linf": [2.282e-02, 1.151e-02, 5.782e-03, 2.897e-03, 1.450e-03]},
+    "E2": {"elements": [12000, 24000, 48000, 96000, 192000], "iters": [93, 104, 115, 132, 162],
+           "iters_pc": [59, 66, 72, 81, 93]},
+    "E3": {"elements": [12000, 24000, 48000, 96000, 192000], "iters": [125, 138, 156, 173, 192],
+           "iters_pc": [71, 79, 88, 101, 112]},
+}
+
+
+def run_replay(sizes=(12000, 24000, 48000, 96000, 192000)):
+    """Examples 1-3 of Sec. 5 as GPU solves (FP64, p = 20, tol 1e-8): iterations with and
+    without the DD preconditioner, solve seconds, and for Example 1 the error of the
+    manufactured solution u^s = G(r, r') (source r' = (0, 0.375) inside the L-shape)."""
+    from paper_2511_12450_gb300 import lfmm
+    from workloads import example1, example2, example3
+
+    out = {}
+    for name, make in (("E1", example1), ("E2", example2), ("E3", example3)):
+        rows = []
+        for n in sizes:
+            wl = make(n)
+            med = wl.medium
+            M = lfmm.medium_create(med.interfaces, med.k, med.eta)
+            pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+            t0 = time.perf_counter()
+            G = lfmm.geometry_build(M, pts, w, nrm, p=20, leaf_size=64)
+            setup = time.perf_counter() - t0
+            row = {"elements": int(pts.shape[0]), "setup_s": setup}
+            if name == "E1":
+                # exact solution: the field of a unit element at the source point, G(r, r')
+                src = np.array([wl.extra["source"]], dtype=np.float64)
+                Gs = lfmm.geometry_build(M, src, np.ones(1), p=20, leaf_size=64)
+                one = np.ones(1, dtype=np.complex128)
+                lay = np.searchsorted(-np.asarray(med.interfaces, dtype=float), -pts[:, 1], side="left")
+                b = np.asarray(med.eta, dtype=float)[lay] * lfmm.eval_field(Gs, one, pts)
+                th = np.linspace(0.0, 2.0 * np.pi, 400, endpoint=False)
+                tg = np.stack([0.75 + 2.6 * np.cos(th), -0.875 + 2.6 * np.sin(th)], axis=1)
+                keep = np.min(np.abs(tg[:, 1:2] - np.asarray(med.interfaces, dtype=float)[None, :]), axis=1) > 1e-3
+                tg = tg[keep]
+                exact = lfmm.eval_field(Gs, one, tg)
+            else:
+                b = lfmm.rhs_plane_wave(G, [math.radians(float(wl.angles_deg[0]))])
+            for pc in (False, True):
+                x, info = lfmm.gmres_solve(G, b, tol=1e-8, max_iter=1000, precond=pc)
+                key = "pc" if pc else "plain"
+                row["iters_" + key] = info["iterations"]
+                row["solve_s_" + key] = info["solve_seconds"]
+                row["true_rel_residual_" + key] = info["true_rel_residual"]
+                if name == "E1" and pc:
+                    u = lfmm.eval_field(G, x, tg)
+                    row["linf_error"] = float(np.max(np.abs(u - exact)))
+                    row["l2_rel_error"] = float(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+            rows.append(row)
+            print(name, row, file=sys.stderr, flush=True)
+        out[name] = {"ours": rows, "paper": PAPER_TABLES[name]}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -446,6 +511,11 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.replay:
+        sizes = tuple(n for n in (12000, 24000, 48000, 96000, 192000) if n <= args.replay_max)
+        print(json.dumps({"replay": run_replay(sizes), "data": "synthetic (the paper's geometries and media)",
+                          "dtype": "f64"}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

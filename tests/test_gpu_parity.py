@@ -239,3 +239,20 @@ def test_matvec_is_deterministic_and_consistent_across_calls(wide):
     ys = [lf.matvec(G, xt).cpu().numpy() for _ in range(3)] + [lf.matvec(G, x) for _ in range(2)]
     for y in ys[1:]:
         assert np.array_equal(y, ys[0])
+
+
+def test_point_source_field_is_the_layered_green_function(gpu_lib):
+    # the field of one unit element at r' is G(r, r') of the oracle (field r, source r'),
+    # the exact solution the Example-1 replay builds its data from (Sec. 5, eq. numericalexamples)
+    from oracle import green as ogreen
+    from workloads import example1
+
+    lf = gpu_lib
+    med = example1(12000).medium
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    src = np.array([[0.0, 0.375]])
+    Gs = lf.geometry_build(M, src, np.ones(1), p=20, leaf_size=64)
+    tg = np.array([[1.5, 0.9], [-1.4, -0.6], [2.7, -1.5], [-1.2, -2.4], [0.3, -3.4]])
+    u = lf.eval_field(Gs, np.ones(1, dtype=np.complex128), tg)
+    ex = ogreen.G(med, tg[:, 0], tg[:, 1], src[0, 0], src[0, 1])
+    assert relerr(u, ex) <= 1e-9
