@@ -134,13 +134,17 @@ static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, c
             const int e0 = ent_ptr[T], e1 = ent_ptr[T + 1], ne = e1 - e0;
             const int per = std::max(1, M2L_ITEM_WORK / nco);   // entries per item
             const int np = std::max(1, (ne + per - 1) / per);
+            if (np == 1 && lane_width(nco) == nco) {   // one item holds every output coefficient
+                items.push_back(M2LItem{T, 0, e0, e1, -1, nco});
+                continue;
+            }
             for (int c = 0; c * XT_W < nco; ++c) {
                 if (np == 1) {
-                    items.push_back(M2LItem{T, c, e0, e1, -1});
+                    items.push_back(M2LItem{T, c, e0, e1, -1, XT_W});
                 } else {
                     reds.push_back(M2LReduce{T, c, nparts, np});
                     for (int q = 0; q < np; ++q)
-                        items.push_back(M2LItem{T, c, e0 + q * per, std::min(e1, e0 + (q + 1) * per), nparts + q});
+                        items.push_back(M2LItem{T, c, e0 + q * per, std::min(e1, e0 + (q + 1) * per), nparts + q, XT_W});
                     nparts += np;
                 }
             }
@@ -571,8 +575,9 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         if (lp == lm - 1) mixed_m_to64(g, lm, nrhs, s);   // the FP64 levels start from the FP32 ones' multipoles
         const int nd = g->up_end[lp] - g->up_begin[lp];
         if (nd == 0) continue;
-        dim3 grid(nd, (2 * t.p_level[lp] + 1 + XT_W - 1) / XT_W);
-        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, nrhs, g->ncoef,
+        const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco);
+        dim3 grid(nd, (nco + w - 1) / w);
+        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nrhs, g->ncoef,
                                          g->nslotcoef, g->d_M, g->d_Mp);
         cuda_check(cudaGetLastError(), "k_translate (M2M)");
         ++g->n_launches;
@@ -615,8 +620,9 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         // at the first FP32 level the FP64 translation writes (not adds) and is then added
         // into the FP32 locals, which the FP32 M2L has written
         const int acc = (l == lm) ? 0 : 1;
-        dim3 grid(nd, (2 * t.p_level[l] + 1 + XT_W - 1) / XT_W);
-        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, acc, nrhs, g->ncoef,
+        const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco);
+        dim3 grid(nd, (nco + w - 1) / w);
+        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, acc, w, nrhs, g->ncoef,
                                          g->nslotcoef, g->d_L, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_translate (L2L)");
         ++g->n_launches;

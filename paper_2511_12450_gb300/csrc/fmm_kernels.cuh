@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
 }
 
 // M2L into the target boxes of levels >= l0 (free space and reaction components).
-// A CTA of 128 threads takes one work item: XT_W output lanes x 8 slices of the
-// sum over the source index, over the item's range of list entries, whose
-// descriptors are staged in shared memory 64 at a time; the slices are reduced
+// A CTA of 128 threads takes one work item: W output lanes (W = XT_W, or every
+// coefficient, see lane_width) x 128 / W slices of the sum over the source
+// index, over the item's range of list entries, whose descriptors are staged in
+// shared memory 64 at a time; the slices are reduced
 // in a fixed order at the end.  Free space (Graf): L_n += sum_m M_m T[m - n]
 // (Toeplitz vector per table).  Reaction (eq. generalintegral): beta_m =
 // sum_n I[m][n] alpha_n with the arrival and departure index flips; moment
@@ -117,16 +118,16 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
                       const int64_t* __restrict__ m2lf_off, const cd* __restrict__ m2lr, int nrhs, int64_t ncoef,
                       int64_t nslotcoef, int nparts, const cd* __restrict__ Min, const cd* __restrict__ Mp,
                       cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
-    constexpr int NS = 128 / XT_W;
-    __shared__ cd red[3][NS][XT_W];
+    __shared__ cd red[3 * 128];
     __shared__ M2LEnt se[M2L_STAGE];
     const M2LItem it = items[blockIdx.x];
     const int T = it.box;
     const int p = p_level[box_level[T]];
     const int nco = 2 * p + 1;
-    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
-    const int idx = it.chunk * XT_W + lane;
-    const bool live = idx < nco;
+    const int W = it.w, NS = 128 / W;
+    const int lane = threadIdx.x % W, sl = threadIdx.x / W;
+    const int idx = it.chunk * W + lane;
+    const bool live = sl < NS && idx < nco;
     const int nn = idx - p;
     for (int col = 0; col < nrhs; ++col) {
         const cd* Mc = Min + (int64_t)col * ncoef;
@@ -171,20 +172,23 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
                 }
             }
         }
-        red[0][sl][lane] = acc0;
-        red[1][sl][lane] = acc1;
-        red[2][sl][lane] = acc2;
+        if (sl < NS) {
+            red[(0 * NS + sl) * W + lane] = acc0;
+            red[(1 * NS + sl) * W + lane] = acc1;
+            red[(2 * NS + sl) * W + lane] = acc2;
+        }
         __syncthreads();
-        if (live && sl < 3) {
-            const int k = sl;
-            cd t = red[k][0][lane];
-            for (int q = 1; q < NS; ++q) t += red[k][q][lane];
-            if (it.part >= 0) {
-                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + lane] = t;
+        for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) {
+            const int k = i / W, ln = i - k * W, ix = it.chunk * W + ln;
+            if (ix >= nco) continue;
+            cd t = red[(k * NS) * W + ln];
+            for (int q = 1; q < NS; ++q) t += red[(k * NS + q) * W + ln];
+            if (it.part >= 0) {   // split items are always XT_W lanes wide
+                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + ln] = t;
             } else {
                 const int ts = (k == 0) ? -1 : slot_of[2 * T + k - 1];
-                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
-                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
+                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + ix] = t;
+                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + ix] = t;
             }
         }
         __syncthreads();
@@ -255,36 +259,39 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
 // theorem) into the destinations of one level: cell centres and reaction
 // centres of straddling cells alike, each with its own list of sources:
 //   dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
-// A CTA of 128 threads owns XT_W consecutive output indices of one
-// destination (one per lane of a 16-lane row) and 8 slices of the sum over
-// m; the slices are reduced in a fixed order, so results are reproducible.
-// Spreading a destination over several CTAs keeps the coarse levels (few
-// boxes, orders up to 2p+1 ~ 115) from running on a handful of SMs.
+// A CTA of 128 threads owns w consecutive output indices of one destination
+// (one per lane of a w-lane row; w = XT_W or all 2p+1 of them, see lane_width)
+// and 128 / w slices of the sum over m; the slices are reduced in a fixed order,
+// so results are reproducible.  Spreading a destination over several CTAs keeps
+// the coarse levels (few boxes, orders up to 2p+1 ~ 115) from running on a
+// handful of SMs.
 __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
-                                                   const cd* __restrict__ vec, int accumulate, int nrhs,
+                                                   const cd* __restrict__ vec, int accumulate, int w, int nrhs,
                                                    int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
-    __shared__ cd red[128 / XT_W][XT_W];
+    __shared__ cd red[128];
     const XDst d = dsts[blockIdx.x];
-    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
-    const int idx = blockIdx.y * XT_W + lane;
+    const int ns = 128 / w;
+    const int lane = threadIdx.x % w, sl = threadIdx.x / w;
+    const int idx = blockIdx.y * w + lane;
     const int ncD = 2 * d.p + 1;
+    const bool live = sl < ns && idx < ncD;
     for (int col = 0; col < nrhs; ++col) {
         cd a = mk(0, 0);
-        if (idx < ncD) {
+        if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
                 const XSrc sr = srcs[j];
                 const cd* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
                 // V[n - m + hw] with n = idx - pD, m = mi - pS, hw = pS + pD
                 const cd* Vb = vec + sr.vec_off + idx + 2 * sr.p;
                 const int ncS = 2 * sr.p + 1;
-                for (int mi = sl; mi < ncS; mi += 128 / XT_W) cfma(a, src[mi], Vb[-mi]);
+                for (int mi = sl; mi < ncS; mi += ns) cfma(a, src[mi], Vb[-mi]);
             }
         }
-        red[sl][lane] = a;
+        if (sl < ns) red[sl * w + lane] = a;
         __syncthreads();
         if (sl == 0 && idx < ncD) {
-            cd t = red[0][lane];
-            for (int q = 1; q < 128 / XT_W; ++q) t += red[q][lane];
+            cd t = red[lane];
+            for (int q = 1; q < ns; ++q) t += red[q * w + lane];
             cd* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
             if (accumulate) *dst += t;
             else *dst = t;

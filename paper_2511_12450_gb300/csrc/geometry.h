@@ -72,8 +72,19 @@ struct XSrc {
 struct M2LItem {
     int box, chunk;
     int e0, e1;       // entry range (M2LEnt indices)
-    int part;         // -1: write L directly; else partial-sum slot
+    int part;         // -1: write L directly; else partial-sum slot (always XT_W lanes)
+    int w;            // output lanes per row: XT_W (chunks of XT_W coefficients) or 2p+1 (all of them)
 };
+// Lanes per output row for nco coefficients on a 128-thread CTA: chunks of XT_W
+// lanes (8 slices of the sum), or one lane per coefficient with 128 / nco slices,
+// whichever keeps more threads on an output (41 of 48 vs 123 of 128 at p = 20).
+inline int lane_width(int nco) {
+    if (nco > 128) return XT_W;
+    const int chunks = (nco + XT_W - 1) / XT_W;
+    const double u16 = (double)nco / (double)(XT_W * chunks);
+    const double uf = (double)(nco * (128 / nco)) / 128.0;
+    return (uf > u16 + 0.02) ? nco : XT_W;
+}
 // one list entry of a target box
 // M2L_FLIP: the table is that of the mirrored pair (offset -X), read with both
 // indices reversed

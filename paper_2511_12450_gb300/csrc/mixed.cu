@@ -178,16 +178,16 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
                         const int64_t* __restrict__ ftab_off, const cf* __restrict__ rtab, int nrhs, int64_t ncoef,
                         int64_t nslotcoef, int nparts, const cf* __restrict__ Min, const cf* __restrict__ Mp,
                         cf* __restrict__ Lout, cf* __restrict__ Lp, cf* __restrict__ part) {
-    constexpr int NS = 128 / XT_W;
-    __shared__ cf red[3][NS][XT_W];
+    __shared__ cf red[3 * 128];
     __shared__ M2LEnt se[M2L_STAGE32];
     const M2LItem it = items[blockIdx.x];
     const int T = it.box;
     const int p = p_level[box_level[T]];
     const int nco = 2 * p + 1;
-    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
-    const int idx = it.chunk * XT_W + lane;
-    const bool live = idx < nco;
+    const int W = it.w, NS = 128 / W;
+    const int lane = threadIdx.x % W, sl = threadIdx.x / W;
+    const int idx = it.chunk * W + lane;
+    const bool live = sl < NS && idx < nco;
     const int nn = idx - p;
     for (int col = 0; col < nrhs; ++col) {
         const cf* Mc = Min + (int64_t)col * ncoef;
@@ -231,20 +231,23 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
                 }
             }
         }
-        red[0][sl][lane] = acc0;
-        red[1][sl][lane] = acc1;
-        red[2][sl][lane] = acc2;
+        if (sl < NS) {
+            red[(0 * NS + sl) * W + lane] = acc0;
+            red[(1 * NS + sl) * W + lane] = acc1;
+            red[(2 * NS + sl) * W + lane] = acc2;
+        }
         __syncthreads();
-        if (live && sl < 3) {
-            const int k = sl;
-            cf t = red[k][0][lane];
-            for (int q = 1; q < NS; ++q) t = addf(t, red[k][q][lane]);
-            if (it.part >= 0) {
-                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + lane] = t;
+        for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) {
+            const int k = i / W, ln = i - k * W, ix = it.chunk * W + ln;
+            if (ix >= nco) continue;
+            cf t = red[(k * NS) * W + ln];
+            for (int q = 1; q < NS; ++q) t = addf(t, red[(k * NS + q) * W + ln]);
+            if (it.part >= 0) {   // split items are always XT_W lanes wide
+                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + ln] = t;
             } else {
                 const int ts = (k == 0) ? -1 : slot_of[2 * T + k - 1];
-                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + idx] = t;
-                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
+                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + ix] = t;
+                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + ix] = t;
             }
         }
         __syncthreads();
@@ -407,29 +410,31 @@ __global__ void __launch_bounds__(128) k_l2p32(const ExpGroup* __restrict__ grou
 // M2M / L2L in FP32 on scaled expansions: out_n (= or +=) sum_j sum_m src_j[m] W_j[m][n],
 // W_j dense (column-major, (n, m) at m ncD + n) with the scale factors folded in.
 __global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
-                        const int64_t* __restrict__ wtab_off, const cf* __restrict__ wtab, int accumulate, int nrhs,
-                        int64_t ncoef, int64_t nslotcoef, cf* X, cf* Xp) {
-    __shared__ cf red[128 / XT_W][XT_W];
+                        const int64_t* __restrict__ wtab_off, const cf* __restrict__ wtab, int accumulate, int w,
+                        int nrhs, int64_t ncoef, int64_t nslotcoef, cf* X, cf* Xp) {
+    __shared__ cf red[128];
     const XDst d = dsts[blockIdx.x];
-    const int lane = threadIdx.x % XT_W, sl = threadIdx.x / XT_W;
-    const int idx = blockIdx.y * XT_W + lane;
+    const int ns = 128 / w;
+    const int lane = threadIdx.x % w, sl = threadIdx.x / w;
+    const int idx = blockIdx.y * w + lane;
     const int ncD = 2 * d.p + 1;
+    const bool live = sl < ns && idx < ncD;
     for (int col = 0; col < nrhs; ++col) {
         cf a = mkf(0, 0);
-        if (idx < ncD) {
+        if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
                 const XSrc sr = srcs[j];
                 const cf* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
                 const cf* W = wtab + wtab_off[j] + idx;
                 const int ncS = 2 * sr.p + 1;
-                for (int mi = sl; mi < ncS; mi += 128 / XT_W) cfmaf(a, src[mi], W[mi * ncD]);
+                for (int mi = sl; mi < ncS; mi += ns) cfmaf(a, src[mi], W[mi * ncD]);
             }
         }
-        red[sl][lane] = a;
+        if (sl < ns) red[sl * w + lane] = a;
         __syncthreads();
         if (sl == 0 && idx < ncD) {
-            cf t = red[0][lane];
-            for (int q = 1; q < 128 / XT_W; ++q) t = addf(t, red[q][lane]);
+            cf t = red[lane];
+            for (int q = 1; q < ns; ++q) t = addf(t, red[q * w + lane]);
             cf* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
             if (accumulate) *dst = addf(*dst, t);
             else *dst = t;
@@ -673,9 +678,10 @@ static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate
                    cudaStream_t s) {
     const int nd = b1 - b0;
     if (nd == 0) return;
-    dim3 grid(nd, (2 * p_dst + 1 + XT_W - 1) / XT_W);
-    k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, nrhs,
-                                       g->ncoef, g->nslotcoef, X, Xp);
+    const int nco = 2 * p_dst + 1, w = lane_width(nco);
+    dim3 grid(nd, (nco + w - 1) / w);
+    k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, w,
+                                       nrhs, g->ncoef, g->nslotcoef, X, Xp);
     cuda_check(cudaGetLastError(), "k_translate32");
     ++g->n_launches;
 }
