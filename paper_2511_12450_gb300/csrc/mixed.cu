@@ -678,7 +678,9 @@ static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate
                    cudaStream_t s) {
     const int nd = b1 - b0;
     if (nd == 0) return;
-    const int nco = 2 * p_dst + 1, w = lane_width(nco);
+    // FP32 translations are not bound by an arithmetic pipe: 16-lane chunks (more CTAs)
+    // measured faster here than rows as wide as the coefficient count
+    const int nco = 2 * p_dst + 1, w = XT_W;
     dim3 grid(nd, (nco + w - 1) / w);
     k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, w,
                                        nrhs, g->ncoef, g->nslotcoef, X, Xp);
