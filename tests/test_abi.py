@@ -55,3 +55,26 @@ def test_medium_validation(lib):
         with pytest.raises(lib.LfmmError) as ei:
             lib.medium_create(**bad)
         assert ei.value.status == lib.LFMM_ERR_INVALID_ARG
+
+
+def test_geometry_argument_validation_before_device_work(lib):
+    # every check of lfmm_geometry_build runs on the host before any device call,
+    # so these need no GPU
+    m = lib.medium_create([0.0, -2.0], [4.0, 6.0, 8.0], [1.0, 2.0, 3.0])
+    good = np.array([[0.1, 0.5], [0.3, -1.0]])
+    w = np.array([0.1, 0.1])
+    cases = [
+        (np.zeros((0, 2)), np.zeros(0), {}, lib.LFMM_ERR_INVALID_ARG),                 # empty
+        (good, np.array([0.1, -0.1]), {}, lib.LFMM_ERR_INVALID_ARG),                   # weight <= 0
+        (np.array([[np.nan, 0.5], [0.3, -1.0]]), w, {}, lib.LFMM_ERR_INVALID_ARG),     # not finite
+        (good, w, {"p": 0}, lib.LFMM_ERR_INVALID_ARG),                                 # order < 1
+        (good, w, {"p": 81}, lib.LFMM_ERR_INVALID_ARG),                                # order > 80
+        (good, w, {"leaf_size": 0}, lib.LFMM_ERR_INVALID_ARG),
+        (good, w, {"leaf_size": 1025}, lib.LFMM_ERR_INVALID_ARG),
+        (np.array([[0.1, 0.0], [0.3, -1.0]]), w, {}, lib.LFMM_ERR_NODE_ON_INTERFACE),  # on y = 0
+        (np.array([[0.1, 0.5], [0.3, -2.0]]), w, {}, lib.LFMM_ERR_NODE_ON_INTERFACE),  # on y = -2
+    ]
+    for pts, ww, kw, code in cases:
+        with pytest.raises(lib.LfmmError) as ei:
+            lib.geometry_build(m, pts, ww, **kw)
+        assert ei.value.status == code, (pts, kw)

@@ -1,0 +1,56 @@
+"""Edge cases of the GPU path against the dense FP64 oracle: a medium without
+interfaces (the free-space Nystrom matrix, G^r = 0), ragged sizes with an odd leaf
+size, and one- and two-element geometries (self terms and a single cross pair)."""
+
+import numpy as np
+import pytest
+
+from oracle import nystrom as onys
+from workloads import Medium
+from workloads.geometry import random_bodies
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def test_one_layer_medium_is_the_free_space_operator(gpu_lib):
+    lf = gpu_lib
+    med = Medium(interfaces=[], k=[5.0], eta=[1.0])
+    bodies = random_bodies(np.random.default_rng(41), 3, ((-3.0, 3.0), (-3.0, 3.0)), [], 300)
+    pts, w, _, _ = onys.elements(bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create([], [5.0], [1.0])
+    G = lf.geometry_build(M, pts, w, p=20, leaf_size=32)
+    x = np.random.default_rng(42).standard_normal(G.n) + 1j * np.random.default_rng(43).standard_normal(G.n)
+    assert relerr(lf.matvec(G, x), K @ x) <= 1e-7
+
+
+def test_ragged_size_and_odd_leaf(gpu_lib):
+    # N = 393 (3 x 131) with leaves of at most 5 points: many ragged leaves and chunks
+    lf = gpu_lib
+    med = Medium(interfaces=[0.0, -1.5], k=[4.0, 6.0, 8.0], eta=[1.0, 2.0, 3.0])
+    bodies = random_bodies(np.random.default_rng(44), 3, ((-2.0, 2.0), (-2.7, 1.2)), med.interfaces, 131,
+                           rmin=0.25, rmax=0.7, iface_tol=1e-3)
+    pts, w, _, _ = onys.elements(bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, p=20, leaf_size=5)
+    rng = np.random.default_rng(45)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    assert G.n == 393
+    assert relerr(lf.matvec(G, x), K @ x) <= 1e-7
+
+
+@pytest.mark.parametrize("pts", [np.array([[0.2, 0.4]]), np.array([[0.2, 0.4], [-0.3, -0.8]])])
+def test_one_and_two_element_geometries(gpu_lib, pts):
+    lf = gpu_lib
+    med = Medium(interfaces=[0.0], k=[2.0, 4.0], eta=[1.0, 2.0])
+    w = np.full(pts.shape[0], 0.05)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, p=20, leaf_size=64)
+    x = np.array([1.0 + 0.5j, -0.25 + 2.0j][: pts.shape[0]])
+    assert relerr(lf.matvec(G, x), K @ x) <= 1e-10
