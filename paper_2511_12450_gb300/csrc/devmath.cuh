@@ -101,6 +101,53 @@ __host__ __device__ inline void bessel_j_seq(double x, int p, double* out) {
     for (int n = 0; n <= p; ++n) out[n] *= inv;
 }
 
+// 1/i for i = 0..127 (0 at i = 0): reciprocals as multiplications, since an FP64
+// division costs a dozen FP64-pipe instructions
+static __device__ const double k_inv_int[128] = {0.0,1.0 / 1,1.0 / 2,1.0 / 3,1.0 / 4,1.0 / 5,1.0 / 6,1.0 / 7,1.0 / 8,1.0 / 9,1.0 / 10,1.0 / 11,1.0 / 12,1.0 / 13,1.0 / 14,1.0 / 15,1.0 / 16,1.0 / 17,1.0 / 18,1.0 / 19,1.0 / 20,1.0 / 21,1.0 / 22,1.0 / 23,1.0 / 24,1.0 / 25,1.0 / 26,1.0 / 27,1.0 / 28,1.0 / 29,1.0 / 30,1.0 / 31,1.0 / 32,1.0 / 33,1.0 / 34,1.0 / 35,1.0 / 36,1.0 / 37,1.0 / 38,1.0 / 39,1.0 / 40,1.0 / 41,1.0 / 42,1.0 / 43,1.0 / 44,1.0 / 45,1.0 / 46,1.0 / 47,1.0 / 48,1.0 / 49,1.0 / 50,1.0 / 51,1.0 / 52,1.0 / 53,1.0 / 54,1.0 / 55,1.0 / 56,1.0 / 57,1.0 / 58,1.0 / 59,1.0 / 60,1.0 / 61,1.0 / 62,1.0 / 63,1.0 / 64,1.0 / 65,1.0 / 66,1.0 / 67,1.0 / 68,1.0 / 69,1.0 / 70,1.0 / 71,1.0 / 72,1.0 / 73,1.0 / 74,1.0 / 75,1.0 / 76,1.0 / 77,1.0 / 78,1.0 / 79,1.0 / 80,1.0 / 81,1.0 / 82,1.0 / 83,1.0 / 84,1.0 / 85,1.0 / 86,1.0 / 87,1.0 / 88,1.0 / 89,1.0 / 90,1.0 / 91,1.0 / 92,1.0 / 93,1.0 / 94,1.0 / 95,1.0 / 96,1.0 / 97,1.0 / 98,1.0 / 99,1.0 / 100,1.0 / 101,1.0 / 102,1.0 / 103,1.0 / 104,1.0 / 105,1.0 / 106,1.0 / 107,1.0 / 108,1.0 / 109,1.0 / 110,1.0 / 111,1.0 / 112,1.0 / 113,1.0 / 114,1.0 / 115,1.0 / 116,1.0 / 117,1.0 / 118,1.0 / 119,1.0 / 120,1.0 / 121,1.0 / 122,1.0 / 123,1.0 / 124,1.0 / 125,1.0 / 126,1.0 / 127};
+
+// J_0..J_p(x) where x is small against the order (x < p / 4, p <= 80): J_p and
+// J_{p-1} from the power series J_n(x) = (x/2)^n / n! sum_k (-x^2/4)^k / (k! (n+1)...(n+k))
+// (A&S 9.1.10; a few terms there), then the three-term recurrence downward,
+// J_{n-1} = (2n/x) J_n - J_{n+1}, which is stable in that direction for the
+// minimal solution J_n and needs no normalisation.  Elsewhere Miller's algorithm;
+// where (x/2)^p underflows, the two leading series terms.  Device only (uses the
+// reciprocal table).
+__device__ inline void bessel_j_seq_small(double x, int p, double* out) {
+    if (!(x < 0.25 * p) || p < 2 || p > 80) { bessel_j_seq(x, p, out); return; }
+    const double a = 0.5 * x, q = -a * a;
+    // everything carries the exact factor 2^600 (|J_n| <= 1, so nothing overflows) so
+    // that (x/2)^p / p! stays representable down to tiny x; it is removed at the end
+    const double up = 0x1p600, down = 0x1p-600;
+    double t = up;   // 2^600 a^p / p!
+    for (int i = 1; i <= p; ++i) t *= a * k_inv_int[i];
+    if (t < 1e-290) {   // x tiny: J_n = (x/2)^n / n! (1 + q / (n+1) + q^2 / (2 (n+1)(n+2))), error O(q^3)
+        double tn = 1.0;
+        for (int n = 0; n <= p; ++n) {
+            if (n > 0) tn *= a * k_inv_int[n];
+            out[n] = tn * (1.0 + q * k_inv_int[n + 1] * (1.0 + 0.5 * q * k_inv_int[n + 2]));
+        }
+        return;
+    }
+    double S1 = 1.0, S0 = 1.0, c1 = 1.0, c0 = 1.0;   // series of J_p and J_{p-1}
+    for (int k = 1; k <= 40; ++k) {
+        c1 *= q * k_inv_int[k] * k_inv_int[p + k];
+        c0 *= q * k_inv_int[k] * k_inv_int[p - 1 + k];
+        S1 += c1;
+        S0 += c0;
+        if (fabs(c1) <= 1e-17 * fabs(S1) && fabs(c0) <= 1e-17 * fabs(S0)) break;
+    }
+    const double ia = 1.0 / a;   // = 2 / x
+    double jp = t * S1, jn = t * (p * ia) * S0;
+    out[p] = jp * down;
+    out[p - 1] = jn * down;
+    for (int n = p - 1; n >= 1; --n) {
+        const double jm = (n * ia) * jn - jp;
+        out[n - 1] = jm * down;
+        jp = jn;
+        jn = jm;
+    }
+}
+
 // Hankel functions H_n^(1)(x) for n = 0..p by forward recurrence from
 // H_0 = J_0 + i Y_0 and H_1 = J_1 + i Y_1 (forward recurrence is stable for
 // the dominant Y_n; the J_n part is negligible there).  x > 0.

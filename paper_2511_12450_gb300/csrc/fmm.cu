@@ -537,8 +537,8 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     for (int l = l0; l <= D; ++l) pmax = std::max(pmax, t.p_level[l]);
     // shared memory of the grouped P2M / L2P kernels (same order p = p_D for every entry)
     const int gp = g->group_max_pts, ge = g->group_max_ent;
-    const size_t smem_p2m = (size_t)gp * (pD + 1) * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
-    const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * (2 * pD + 1) * sizeof(cd);
+    const size_t smem_p2m = (size_t)gp * (2 * pD + 1) * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
+    const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd);
     if (smem_p2m > g->smem_p2m_set) {
         cuda_check(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2m), "p2m smem");
         g->smem_p2m_set = smem_p2m;

@@ -40,19 +40,19 @@ __device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, in
 
 // P2M about the entries' centres (leaves about cell centres, straddling leaves
 // about their reaction centres): M_n = sum_j q_j J_n(k rho_j) e^{-i n theta_j},
-// q_j = |Gamma_j| phi_j.  Phase 1, one thread per point of the group:
-// u_{j,n} = J_n(k rho_j) e^{-i n theta_j}, n = 0..p, into shared memory.
-// Phase 2, one thread per (entry, coefficient): the sum over the entry's points,
-// with M_{-n} from u_{j,n} by J_{-n} = (-1)^n J_n and e^{+i n theta} = conj.
+// q_j = |Gamma_j| phi_j.  Phase 1, one thread per point of the group: its basis
+// row u_{j,n} = J_n(k rho_j) e^{-i n theta_j} for n = -p..p (J_{-n} = (-1)^n J_n,
+// e^{+i n theta} = conj) into shared memory.  Phase 2, one thread per (entry,
+// coefficient): the sum over the entry's points, pure complex FMAs.
 __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
                       MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
                       const double* __restrict__ pw, const cd* __restrict__ phi, int64_t n, int nrhs,
                       int64_t stride, cd* __restrict__ M) {
-    extern __shared__ cd su[];   // [npts][p+1] u, then [npts] q, then [nent + 1] point offsets (as ints)
+    extern __shared__ cd su[];   // [npts][2p+1] basis rows, then [npts] q, then [nent + 1] point offsets (ints)
     const ExpGroup G = groups[blockIdx.x];
-    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int p = ent[G.e0].p, nco = 2 * p + 1;
     const int ne = G.e1 - G.e0;
-    cd* sq = su + (size_t)G.npts * np1;
+    cd* sq = su + (size_t)G.npts * nco;
     int* soff = (int*)(sq + G.npts);
     if (threadIdx.x == 0) {
         int o = 0;
@@ -65,18 +65,22 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
         const ExpEntry& E = ent[G.e0 + er];
         const double dx = px[j] - E.cx, dy = py[j] - E.cy;
         const double rho = hypot(dx, dy);
-        cd* u = su + (size_t)t * np1;
-        bessel_j_seq(m.k[E.lay] * rho, p, (double*)u);   // J_0..J_p packed in the first p+1 doubles
-        // spread J_n into u_n = J_n z^n, z = e^{-i theta}, from the top so nothing is overwritten early
-        const cd z = (rho > 0.0) ? mk(dx / rho, -dy / rho) : mk(1.0, 0.0);
-        // z^p by repeated squaring, then walk down with z^{n-1} = z^n conj(z)
-        cd zp = mk(1.0, 0.0), bb = z;
-        for (int e2 = p; e2 > 0; e2 >>= 1) { if (e2 & 1) zp = zp * bb; bb = bb * bb; }
-        const double* Jd = (const double*)u;
-        for (int k2 = p; k2 >= 0; --k2) {
-            const double jv = Jd[k2];   // read before u[k2] (which covers doubles 2k2, 2k2+1 >= k2) is written
-            u[k2] = jv * zp;
-            zp = zp * conjc(z);
+        cd* u = su + (size_t)t * nco;
+        double* Jd = (double*)u;   // J_0..J_p in the first p+1 doubles of the row
+        bessel_j_seq_small(m.k[E.lay] * rho, p, Jd);
+        double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
+        const cd z = (rho > 0.0) ? mk(dx * irho, -dy * irho) : mk(1.0, 0.0);
+        // u_n, n = 0..p, into cd slots p..2p (doubles 2p.. , above the J's for p >= 1),
+        // z^n upward from z^0 = 1
+        cd zn = mk(1.0, 0.0);
+        for (int k2 = 0; k2 <= p; ++k2) {
+            if (k2 > 0) zn = zn * z;
+            u[p + k2] = Jd[k2] * zn;
+        }
+        // u_{-n} = (-1)^n conj(u_n) into slots p-1..0 (the J's are no longer needed)
+        for (int k2 = 1; k2 <= p; ++k2) {
+            const cd v = u[p + k2];
+            u[p - k2] = (k2 & 1) ? mk(-v.x, v.y) : mk(v.x, -v.y);
         }
     }
     for (int col = 0; col < nrhs; ++col) {
@@ -89,13 +93,8 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
         __syncthreads();
         for (int task = threadIdx.x; task < ne * nco; task += blockDim.x) {
             const int er = task / nco, idx = task - er * nco;
-            const int nn = idx - p, an = nn < 0 ? -nn : nn;
             cd a = mk(0, 0);
-            for (int t = soff[er]; t < soff[er + 1]; ++t) {
-                cd v = su[(size_t)t * np1 + an];
-                if (nn < 0) { v = conjc(v); if (an & 1) v = -v; }
-                cfma(a, sq[t], v);
-            }
+            for (int t = soff[er]; t < soff[er + 1]; ++t) cfma(a, sq[t], su[(size_t)t * nco + idx]);
             M[(int64_t)col * stride + ent[G.e0 + er].off + idx] = a;
         }
     }
@@ -220,16 +219,24 @@ __global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__
 __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
                       MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
                       int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
-    extern __shared__ double sj[];   // [npts][p+1] J_n, then [nent][2p+1] coefficients
+    // y_j += sum_n L_n J_n(k rho_j) e^{i n theta_j}.  Per entry, A_n = L_n and
+    // B_n = (-1)^n L_{-n} are folded into P_n = A_n + B_n and Q_n = A_n - B_n, so
+    // that A_n z^n + B_n conj(z^n) = P_n cos(n theta) + i Q_n sin(n theta).
+    extern __shared__ double sj[];   // [npts][p+1] J_n, then [nent][2][p+1] (P, Q)
     const ExpGroup G = groups[blockIdx.x];
-    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int p = ent[G.e0].p, np1 = p + 1;
     const int ne = G.e1 - G.e0;
-    cd* sL = (cd*)(sj + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
+    cd* sPQ = (cd*)(sj + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
     for (int col = 0; col < nrhs; ++col) {
         __syncthreads();
-        for (int i = threadIdx.x; i < ne * nco; i += blockDim.x) {
-            const int er = i / nco, idx = i - er * nco;
-            sL[i] = L[(int64_t)col * stride + ent[G.e0 + er].off + idx];
+        for (int i = threadIdx.x; i < ne * np1; i += blockDim.x) {
+            const int er = i / np1, k2 = i - er * np1;
+            const cd* Le = L + (int64_t)col * stride + ent[G.e0 + er].off;
+            const cd A = Le[p + k2];
+            cd B = Le[p - k2];
+            if (k2 & 1) B = -B;
+            if (k2 == 0) { sPQ[(er * 2) * np1] = A; sPQ[(er * 2 + 1) * np1] = mk(0, 0); }
+            else { sPQ[(er * 2) * np1 + k2] = A + B; sPQ[(er * 2 + 1) * np1 + k2] = A - B; }
         }
         __syncthreads();
         for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
@@ -239,16 +246,18 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
             const double dx = px[j] - E.cx, dy = py[j] - E.cy;
             const double rho = hypot(dx, dy);
             double* J = sj + (size_t)t * np1;
-            if (col == 0) bessel_j_seq(m.k[E.lay] * rho, p, J);
-            const cd z = (rho > 0.0) ? mk(dx / rho, dy / rho) : mk(1.0, 0.0);
-            const cd* Le = sL + er * nco;
-            cd acc = Le[p] * J[0];
+            if (col == 0) bessel_j_seq_small(m.k[E.lay] * rho, p, J);
+            const double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
+            const cd z = (rho > 0.0) ? mk(dx * irho, dy * irho) : mk(1.0, 0.0);
+            const cd* P = sPQ + (er * 2) * np1;
+            const cd* Q = P + np1;
+            cd acc = P[0] * J[0];
             cd zz = mk(1.0, 0.0);
             for (int k2 = 1; k2 <= p; ++k2) {
                 zz = zz * z;
-                const double jt = J[k2];
-                cfma(acc, jt * Le[p + k2], zz);
-                cfma(acc, ((k2 & 1) ? -jt : jt) * Le[p - k2], conjc(zz));
+                const double cj = J[k2] * zz.x, sjn = J[k2] * zz.y;
+                acc.x = fma(P[k2].x, cj, fma(-Q[k2].y, sjn, acc.x));
+                acc.y = fma(P[k2].y, cj, fma(Q[k2].x, sjn, acc.y));
             }
             y[(int64_t)col * n + j] += acc;
         }

@@ -47,7 +47,7 @@ struct ExpEntry {
 };
 // consecutive entries processed by one CTA (at most EXP_GROUP_PTS points and
 // EXP_GROUP_ENTRIES entries, or a single larger entry)
-#define EXP_GROUP_PTS 128
+#define EXP_GROUP_PTS 64
 #define EXP_GROUP_ENTRIES 16
 struct ExpGroup {
     int e0, e1;    // entry range
