@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--replay", action="store_true",
                     help="replay the paper's Examples 1-3 (Sec. 5, Tables 5.1-5.3) as GPU solves and exit")
     ap.add_argument("--replay-max", type=int, default=192000, help="largest element count of the replay")
@@ -257,6 +258,58 @@ def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
                         f"latency under Poisson arrivals at 1.5x the FP64 one-at-a-time capacity "
                         f"({rate:.2f} requests/s); tol 1e-8 on the FP64 residual",
             "hbm_budget_bytes": budget, **out}
+
+
+def run_batch(lfmm, index=10, steps=5):
+    """Block right-hand side: one geometry of the batching configuration (C4 geometry
+    `index`, 2-4 layers, k in [2, 12]) with its 32 incidence angles as one 32-column matvec,
+    against 32 single-column matvecs; L2 flushed before every timed call."""
+    import torch
+
+    from workloads import config_c4
+
+    wl = config_c4()[index]
+    med = wl.medium
+    M = lfmm.medium_create(med.interfaces, med.k, med.eta)
+    pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+    G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size)
+    n = G.n
+    ang = np.radians(wl.angles_deg)
+    B = lfmm.rhs_plane_wave(G, ang, device=True)          # [32, n]: column-major n x 32
+    Y = torch.empty_like(B)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / steps * 1e-3
+
+    t_block = timed(lambda: lfmm.matvec(G, B, Y))
+    cols = [B[c] for c in range(B.shape[0])]
+    outs = [torch.empty_like(c) for c in cols]
+
+    def singles():
+        for c, o in zip(cols, outs):
+            lfmm.matvec(G, c, o)
+
+    t_single = timed(singles)
+    same = max(float(torch.linalg.norm(Y[c] - outs[c]) / torch.linalg.norm(outs[c])) for c in range(len(cols)))
+    nr = B.shape[0]
+    return {"metric": "block right-hand side matvec, Mpts*rhs/s", "workload": f"C4 geometry {index}: {len(med.k)} layers, "
+            f"N={n}, {nr} incidence angles", "block_value": n * nr / t_block / 1e6,
+            "single_column_value": n * nr / t_single / 1e6, "block_ms": t_block * 1e3,
+            "single_columns_ms": t_single * 1e3, "max_rel_diff_block_vs_single": same}
 
 
 # the paper's Tables 5.1-5.3 (Sec. 5): elements, GMRES iterations without / with the DD
@@ -474,6 +527,9 @@ def run_ours(args):
                           "converged": bool(im["converged"]), "op_rel_diff_on_b": im["op_rel_diff"],
                           "rel_diff_to_fp64_solution": float(torch.linalg.norm(xm - xs) / torch.linalg.norm(xs))}
 
+    batch = None
+    if rank == 0 and not args.no_batch and args.workload == "c2":
+        batch = run_batch(lfmm)
     serve = None
     if rank == 0 and not args.no_serve and args.workload == "c2":
         serve = run_serving(lfmm)
@@ -500,6 +556,7 @@ def run_ours(args):
             "work": work,
             "solve": solve,
             "mixed": mixed,
+            "batch": batch,
             "serve": serve,
             "setup_seconds": setup_s,
         }

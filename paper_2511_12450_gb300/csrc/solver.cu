@@ -178,6 +178,45 @@ static inline int nblk(int64_t n) { return (int)((n + 255) / 256); }
 // once it is below (0: FP64 throughout; > 1: precision form throughout).  This is
 // the relaxation of inexact Krylov methods: the operator error a step may carry
 // grows as the residual falls, so the first steps get the exact operator.
+// The operator of one GMRES solve, always from the fixed vector z into the fixed
+// vector w: applied once with plain launches (which also makes every lazy work
+// buffer), then captured into a CUDA graph on a private stream and replayed, so
+// a Krylov step enqueues one graph instead of the ~25 kernels of a matvec.  A
+// geometry with the stage profiler on, or any capture failure, keeps the plain
+// launches.
+struct OpGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool tried = false;
+    void apply(lfmm_geometry_s* g, const cd* z, cd* w, bool mixed, cudaStream_t s) {
+        if (exec) {
+            cuda_check(cudaGraphLaunch(exec, s), "graph launch");
+            return;
+        }
+        apply_operator_sorted(g, z, w, 1, s, mixed);
+        if (tried || g->prof.on) return;
+        tried = true;
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            try {
+                apply_operator_sorted(g, z, w, 1, cs, mixed);
+            } catch (...) {
+                ok = false;
+            }
+            if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) ok = false;
+        }
+        if (ok && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        cudaGetLastError();   // a failed capture leaves plain launches in use
+    }
+    ~OpGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int maxit, bool pre, cudaStream_t s,
                      int* iters, double* res_out, double mixed_below = 0.0, int* mixed_steps = nullptr) {
     const int64_t n = g->n;
@@ -197,6 +236,7 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
     double beta = bl.norm(b, n);
     cuda_check(cudaMemsetAsync(x, 0, sizeof(cd) * n, s), "memset x");
     if (beta == 0.0) { *iters = 0; *res_out = 0.0; return 1; }
+    OpGraph ops[2];   // the operator z -> w, FP64 and precision form
     k_scale<<<nblk(n), 256, 0, s>>>(b, 1.0 / beta, V, n);
     typedef std::complex<double> C;
     std::vector<std::vector<C>> H;
@@ -207,8 +247,9 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
         const cd* vj = V + (int64_t)j * n;
         const bool mixed = res <= mixed_below;
         if (mixed && mixed_steps) ++*mixed_steps;
-        if (pre) { precond_apply_sorted(g, vj, z, s); apply_operator_sorted(g, z, w, 1, s, mixed); }
-        else apply_operator_sorted(g, vj, w, 1, s, mixed);
+        if (pre) precond_apply_sorted(g, vj, z, s);
+        else cuda_check(cudaMemcpyAsync(z, vj, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "z = v_j");
+        ops[mixed ? 1 : 0].apply(g, z, w, mixed, s);
         // classical Gram-Schmidt, twice, then the norm; one synchronisation per step
         std::vector<C> h(j + 2, C(0, 0));
         for (int pass = 0; pass < 2; ++pass) {
