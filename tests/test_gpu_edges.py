@@ -54,3 +54,21 @@ def test_one_and_two_element_geometries(gpu_lib, pts):
     G = lf.geometry_build(M, pts, w, p=20, leaf_size=64)
     x = np.array([1.0 + 0.5j, -0.25 + 2.0j][: pts.shape[0]])
     assert relerr(lf.matvec(G, x), K @ x) <= 1e-10
+
+
+def test_four_layers_high_wavenumbers_fmm_matches_dense_oracle(gpu_lib):
+    # a medium like the serving requests' (four layers, k up to 12): FMM with p = 20
+    # and the reaction moment tables' quadrature against the dense oracle
+    lf = gpu_lib
+    med = Medium(interfaces=[0.0, -2.0, -4.0], k=[11.0, 7.5, 12.0, 9.0], eta=[1.0, 2.0, 3.0, 4.0])
+    bodies = random_bodies(np.random.default_rng(46), 4, ((-3.0, 3.0), (-5.5, 1.5)), med.interfaces, 180,
+                           rmin=0.3, rmax=0.7, iface_tol=1e-3)
+    pts, w, _, _ = onys.elements(bodies)
+    K = onys.dense_matrix(med, pts, w)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, p=20, leaf_size=16)
+    rng = np.random.default_rng(47)
+    x = rng.standard_normal(G.n) + 1j * rng.standard_normal(G.n)
+    err = relerr(lf.matvec(G, x), K @ x)
+    print(f"4 layers, k up to 12, N={G.n}: rel err {err:.2e}")
+    assert err <= 1e-8
