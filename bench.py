@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="1: choose the M2L work-item schedule by timing at set-up")
     ap.add_argument("--replay", action="store_true",
                     help="replay the paper's Examples 1-3 (Sec. 5, Tables 5.1-5.3) as GPU solves and exit")
     ap.add_argument("--replay-max", type=int, default=192000, help="largest element count of the replay")
@@ -418,7 +420,8 @@ def run_ours(args):
     pts, w, nrm = lfmm.polygon_elements(wl.bodies)
     n = pts.shape[0]
     t0 = time.perf_counter()
-    G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size, profile=True)
+    G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size, profile=True,
+                            autotune=bool(args.autotune))
     setup_s = time.perf_counter() - t0
     work = algorithmic_work(lfmm, G, n)
     gen = torch.Generator(device="cpu").manual_seed(1234 + rank)
@@ -559,6 +562,7 @@ def run_ours(args):
             "batch": batch,
             "serve": serve,
             "setup_seconds": setup_s,
+            "m2l_schedule": lfmm.tuning(G),
         }
         print(json.dumps(line))
     if dist is not None:

@@ -67,7 +67,13 @@ enum {
 enum {
     LFMM_PROFILE_STAGES = 1 /* time every stage of lfmm_matvec with CUDA events on the call's
                                stream (adds one stream synchronisation per call); read the
-                               totals with lfmm_geometry_query("stage_times") */
+                               totals with lfmm_geometry_query("stage_times") */,
+    LFMM_AUTOTUNE = 2       /* choose the schedule of the M2L work items (cap on the work of
+                               one item, one row per narrow box or not) by timing the
+                               candidates on this geometry at set-up (some 40 M2L launches);
+                               read the choice with lfmm_geometry_query("tuning").  Results
+                               differ from the default schedule only in the order in which
+                               the parts of a split sum are added */
 };
 
 typedef struct lfmm_medium_s *lfmm_medium;
@@ -78,7 +84,7 @@ typedef struct {
     int32_t p;          /* expansion order at the fine levels (default 20); coarse levels
                            raise it with k*w (wide-band rule), up to 80 */
     int32_t leaf_size;  /* max points per leaf box (default 64) */
-    int32_t flags;      /* LFMM_PROFILE_STAGES or 0 */
+    int32_t flags;      /* LFMM_PROFILE_STAGES | LFMM_AUTOTUNE, or 0 */
     int32_t reserved;
 } lfmm_params;
 
@@ -292,6 +298,9 @@ lfmm_status lfmm_server_destroy(lfmm_server s);
  * "launch_count" (double[1]: kernels launched so far by this geometry's
  * matvec path -- gather, P2M, M2M, M2L, L2L, L2P, near field, scatter --
  * counted on the host as they are enqueued),
+ * "tuning" (double[4]: M2L item work cap, one row per narrow box (1/0), and
+ * with LFMM_AUTOTUNE the milliseconds of one FP64 M2L with the default and the
+ * chosen schedule, else 0, 0),
  * "p_level" (int32[D+1]), "vfree_ptr"/"vfree_idx", "ufree_ptr"/"ufree_idx",
  * "vreact_ptr"/"vreact_idx"/"vreact_comp", "ureact_ptr"/"ureact_idx"/"ureact_comp"
  * (CSR over boxes), "components" (int32[4*ncomp]: ls, a, lt, b).

@@ -296,6 +296,7 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         g->d_comp = dupload(g, comp);
         near_build(g);
         fmm_build(g);
+        if (prm && (prm->flags & LFMM_AUTOTUNE)) fmm_autotune(g);
         g->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         med->geometries += 1;
         *out = g;
@@ -521,6 +522,10 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
             dtmp = {(double)g->n_launches};
             src = dtmp.data();
             bytes = (int64_t)sizeof(double);
+        } else if (nm == "tuning") {
+            dtmp = {(double)g->m2l_item_work, (double)g->m2l_wide, g->tune_ms_default, g->tune_ms_best};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "stage_times") {
             for (int k = 0; k < ST_COUNT; ++k) { dtmp.push_back(g->prof.cnt[k]); dtmp.push_back(g->prof.ms[k]); }
             src = dtmp.data();

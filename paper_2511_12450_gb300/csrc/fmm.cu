@@ -84,6 +84,65 @@ static std::vector<ExpGroup> make_groups(const std::vector<ExpEntry>& e, int* ma
     return gs;
 }
 
+// M2L work items over the entry ranges: (box, chunk of output coefficients,
+// entry range).  item_work caps the entry x coefficient units of one item (heavy
+// (box, chunk)s are split, their parts reduced by k_m2l_reduce); with wide = 1 an
+// unsplit box whose coefficients fill a 128-thread CTA better as one row
+// (lane_width) gets a single item.  Replaces the geometry's items.
+static void make_m2l_items(lfmm_geometry_s* g, int item_work, int wide) {
+    TreeHost& t = g->tree;
+    const int D = t.D, l0 = t.l0, nlev = D + 1;
+    const std::vector<int>& ent_ptr = g->m2l_ent_ptr_host;
+    std::vector<M2LItem> items;
+    std::vector<M2LReduce> reds;
+    int nparts = 0;
+    g->m2l_item_level_start.assign(nlev + 2, 0);
+    g->m2l_red_level_start.assign(nlev + 2, 0);
+    for (int l = l0; l <= D; ++l) {
+        g->m2l_item_level_start[l] = (int)items.size();
+        g->m2l_red_level_start[l] = (int)reds.size();
+        for (int T = t.level_start[l]; T < t.level_start[l + 1]; ++T) {
+            const int nco = 2 * t.p_level[l] + 1;
+            const int e0 = ent_ptr[T], e1 = ent_ptr[T + 1], ne = e1 - e0;
+            const int per = std::max(1, item_work / nco);   // entries per item
+            const int np = std::max(1, (ne + per - 1) / per);
+            if (wide && np == 1 && lane_width(nco) == nco) {   // one item holds every output coefficient
+                items.push_back(M2LItem{T, 0, e0, e1, -1, nco});
+                continue;
+            }
+            for (int c = 0; c * XT_W < nco; ++c) {
+                if (np == 1) {
+                    items.push_back(M2LItem{T, c, e0, e1, -1, XT_W});
+                } else {
+                    reds.push_back(M2LReduce{T, c, nparts, np});
+                    for (int q = 0; q < np; ++q)
+                        items.push_back(M2LItem{T, c, e0 + q * per, std::min(e1, e0 + (q + 1) * per), nparts + q, XT_W});
+                    nparts += np;
+                }
+            }
+        }
+    }
+    for (int l = D + 1; l <= nlev + 1; ++l) {
+        g->m2l_item_level_start[l] = (int)items.size();
+        g->m2l_red_level_start[l] = (int)reds.size();
+    }
+    for (int l = 0; l < l0; ++l) { g->m2l_item_level_start[l] = 0; g->m2l_red_level_start[l] = 0; }
+    g->n_m2l_items = (int)items.size();
+    g->n_m2l_parts = nparts;
+    for (void* q : {(void*)g->d_m2l_items, (void*)g->d_m2l_reds}) {   // a schedule being replaced
+        auto it = std::find(g->allocs.begin(), g->allocs.end(), q);
+        if (q && it != g->allocs.end()) { g->allocs.erase(it); dev_release(q); }
+    }
+    g->d_m2l_items = dupload(g, items);
+    g->d_m2l_reds = dupload(g, reds);
+    g->m2l_item_work = item_work;
+    g->m2l_wide = wide;
+    // the partial-sum buffer is sized for the parts: make the next matvec size it again
+    dev_release_now(g->d_m2l_part);
+    g->d_m2l_part = nullptr;
+    g->m2l_part_cols = 0;
+}
+
 // M2L entry descriptors and work items.  Every list entry of a target box
 // becomes one M2LEnt (source coefficient offset, table, flags: reaction,
 // source in the reaction-centre arrays, arrival/departure directions, output
@@ -121,46 +180,11 @@ static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, c
         }
         ent_ptr[T + 1] = (int)ents.size();
     }
-    std::vector<M2LItem> items;
-    std::vector<M2LReduce> reds;
-    int nparts = 0;
-    g->m2l_item_level_start.assign(nlev + 2, 0);
-    g->m2l_red_level_start.assign(nlev + 2, 0);
-    for (int l = l0; l <= D; ++l) {
-        g->m2l_item_level_start[l] = (int)items.size();
-        g->m2l_red_level_start[l] = (int)reds.size();
-        for (int T = t.level_start[l]; T < t.level_start[l + 1]; ++T) {
-            const int nco = 2 * t.p_level[l] + 1;
-            const int e0 = ent_ptr[T], e1 = ent_ptr[T + 1], ne = e1 - e0;
-            const int per = std::max(1, M2L_ITEM_WORK / nco);   // entries per item
-            const int np = std::max(1, (ne + per - 1) / per);
-            if (np == 1 && lane_width(nco) == nco) {   // one item holds every output coefficient
-                items.push_back(M2LItem{T, 0, e0, e1, -1, nco});
-                continue;
-            }
-            for (int c = 0; c * XT_W < nco; ++c) {
-                if (np == 1) {
-                    items.push_back(M2LItem{T, c, e0, e1, -1, XT_W});
-                } else {
-                    reds.push_back(M2LReduce{T, c, nparts, np});
-                    for (int q = 0; q < np; ++q)
-                        items.push_back(M2LItem{T, c, e0 + q * per, std::min(e1, e0 + (q + 1) * per), nparts + q, XT_W});
-                    nparts += np;
-                }
-            }
-        }
-    }
-    for (int l = D + 1; l <= nlev + 1; ++l) {
-        g->m2l_item_level_start[l] = (int)items.size();
-        g->m2l_red_level_start[l] = (int)reds.size();
-    }
-    for (int l = 0; l < l0; ++l) { g->m2l_item_level_start[l] = 0; g->m2l_red_level_start[l] = 0; }
-    g->n_m2l_items = (int)items.size();
-    g->n_m2l_parts = nparts;
-    g->d_m2l_items = dupload(g, items);
+    g->m2l_ent_ptr_host = ent_ptr;
     g->d_m2l_ents = dupload(g, ents);
-    g->d_m2l_reds = dupload(g, reds);
+    make_m2l_items(g, M2L_ITEM_WORK, 1);
 }
+
 
 void fmm_build(lfmm_geometry_s* g) {
     TreeHost& t = g->tree;
@@ -526,6 +550,33 @@ void fmm_free(lfmm_geometry_s* g) {
     g->coef_cols = 0;
 }
 
+// FP64 M2L over the first n64 work items and the first r64 reductions of split
+// items (the levels below the precision form's first FP32 level, or all levels).
+static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStream_t s) {
+    if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
+        dev_release_now(g->d_m2l_part);
+        g->d_m2l_part = nullptr;
+        g->d_m2l_part = (cd*)dev_alloc_ready(sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * nrhs,
+                                             "M2L partial sums");
+        g->m2l_part_cols = nrhs;
+    }
+    if (n64 > 0) {
+        k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                  g->d_slot_of, g->d_slot_coef, g->d_m2lf, g->d_m2lf_off, g->d_m2lr, nrhs,
+                                  g->ncoef, g->nslotcoef, g->n_m2l_parts, g->d_M, g->d_Mp, g->d_L, g->d_Lp,
+                                  g->d_m2l_part);
+        cuda_check(cudaGetLastError(), "k_m2l");
+        ++g->n_launches;
+    }
+    if (r64 > 0) {
+        k_m2l_reduce<<<r64, 64, 0, s>>>(g->d_m2l_reds, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_slot_of,
+                                        g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts,
+                                        g->d_m2l_part, g->d_L, g->d_Lp);
+        cuda_check(cudaGetLastError(), "k_m2l_reduce");
+        ++g->n_launches;
+    }
+}
+
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed) {
     set_smem_limits();
     TreeHost& t = g->tree;
@@ -587,28 +638,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         prof_begin(g, ST_M2L, s);
         const int n64 = g->m2l_item_level_start[lm];
         const int r64 = g->m2l_red_level_start[lm];
-        if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
-            dev_release_now(g->d_m2l_part);
-            g->d_m2l_part = nullptr;
-            g->d_m2l_part = (cd*)dev_alloc_ready(sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * nrhs,
-                                                 "M2L partial sums");
-            g->m2l_part_cols = nrhs;
-        }
-        if (n64 > 0) {
-            k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
-                                      g->d_slot_of, g->d_slot_coef, g->d_m2lf, g->d_m2lf_off, g->d_m2lr, nrhs,
-                                      g->ncoef, g->nslotcoef, g->n_m2l_parts, g->d_M, g->d_Mp, g->d_L, g->d_Lp,
-                                      g->d_m2l_part);
-            cuda_check(cudaGetLastError(), "k_m2l");
-            ++g->n_launches;
-        }
-        if (r64 > 0) {
-            k_m2l_reduce<<<r64, 64, 0, s>>>(g->d_m2l_reds, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_slot_of,
-                                            g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts,
-                                            g->d_m2l_part, g->d_L, g->d_Lp);
-            cuda_check(cudaGetLastError(), "k_m2l_reduce");
-            ++g->n_launches;
-        }
+        launch_m2l64(g, nrhs, n64, r64, s);
         if (lm <= D) mixed_m2l(g, nrhs, lm, s);
         prof_end(g, ST_M2L, s);
     }
@@ -648,6 +678,54 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         }
         prof_end(g, ST_L2P, s);
     }
+}
+
+// Schedule of the M2L work items chosen by measurement on this geometry: the cap
+// on the work of one item (entries x output coefficients; heavier (box, chunk)s
+// are split and their parts reduced) and whether an unsplit box with a narrow
+// coefficient row gets one item for all of its coefficients.  Each candidate's
+// FP64 M2L (items plus reductions) runs twice untimed and three times timed with
+// CUDA events on the calling thread's stream, on zeroed expansions (the time of
+// the FP64 pipe does not depend on the values), and the fastest is kept.  The
+// schedule changes only the order in which the parts of a split sum are added.
+void fmm_autotune(lfmm_geometry_s* g) {
+    TreeHost& t = g->tree;
+    if (t.l0 > t.D || g->n_m2l_items == 0) return;
+    set_smem_limits();
+    cudaStream_t s = cudaStreamPerThread;
+    ensure_coef(g, 1);
+    cuda_check(cudaMemsetAsync(g->d_M, 0, sizeof(cd) * std::max<int64_t>(g->ncoef, 1), s), "tune memset");
+    cuda_check(cudaMemsetAsync(g->d_Mp, 0, sizeof(cd) * std::max<int64_t>(g->nslotcoef, 1), s), "tune memset");
+    const int64_t launches = g->n_launches;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cuda_check(cudaEventCreate(&e0), "event");
+    cuda_check(cudaEventCreate(&e1), "event");
+    const int works[] = {1024, 2048, 4096, 8192};
+    int best_work = g->m2l_item_work, best_wide = g->m2l_wide;
+    double best = 1e300, dflt = 0.0;
+    for (int wide = 1; wide >= 0; --wide) {
+        for (int work : works) {
+            make_m2l_items(g, work, wide);
+            const int n64 = g->n_m2l_items, r64 = g->m2l_red_level_start[t.D + 2];
+            for (int r = 0; r < 2; ++r) launch_m2l64(g, 1, n64, r64, s);
+            cuda_check(cudaEventRecord(e0, s), "event");
+            for (int r = 0; r < 3; ++r) launch_m2l64(g, 1, n64, r64, s);
+            cuda_check(cudaEventRecord(e1, s), "event");
+            cuda_check(cudaEventSynchronize(e1), "tune sync");
+            float ms = 0.f;
+            cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+            const double per = ms / 3.0;
+            if (work == M2L_ITEM_WORK && wide == 1) dflt = per;
+            if (per < best) { best = per; best_work = work; best_wide = wide; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    make_m2l_items(g, best_work, best_wide);
+    cuda_check(cudaStreamSynchronize(s), "tune");
+    g->n_launches = launches;
+    g->tune_ms_default = dflt;
+    g->tune_ms_best = best;
 }
 
 }  // namespace lfmm

@@ -188,6 +188,9 @@ struct lfmm_geometry_s {
     cd* d_m2l_part = nullptr;               // partial sums [cols][n_m2l_parts][3][XT_W]
     int m2l_part_cols = 0;
     std::vector<int> vf_ptr_host, vf_src_host, vf_tab_host, slot_of_host;
+    std::vector<int> m2l_ent_ptr_host;      // entry range per target box
+    int m2l_item_work = 0, m2l_wide = 1;    // schedule of the items (see make_m2l_items)
+    double tune_ms_default = 0.0, tune_ms_best = 0.0;   // M2L launch times measured by the autotuner
     cd *d_m2lr = nullptr;             // reaction M2L tables
     int *d_vr_ptr = nullptr, *d_vr_src = nullptr, *d_vr_key = nullptr, *d_vr_comp = nullptr;
     lfmm::ReactKey* d_rkeys = nullptr;
@@ -275,6 +278,7 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
 // FMM far field (fmm.cu)
 void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false);
+void fmm_autotune(lfmm_geometry_s* g);
 // precision form: M2L in FP32 on scaled expansions (mixed.cu)
 void mixed_setup(lfmm_geometry_s* g, int nrhs);                       // tables, scales, FP32 buffers
 void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s);

@@ -30,6 +30,7 @@ LFMM_ERR_HBM_BUDGET = -7
 LFMM_DEVICE_PTRS = 1
 LFMM_MIXED = 2
 LFMM_PROFILE_STAGES = 1
+LFMM_AUTOTUNE = 2
 STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
 EXPORTED = [
@@ -185,11 +186,12 @@ def medium_create(interfaces, k, eta) -> Medium:
 
 
 def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, leaf_size: int = 64,
-                   profile: bool = False) -> Geometry:
+                   profile: bool = False, autotune: bool = False) -> Geometry:
     pts = _f64(points).reshape(-1, 2)
     w = _f64(weights).reshape(-1)
     nrm = _f64(normals).reshape(-1, 2) if normals is not None else None
-    prm = Params(int(p), int(leaf_size), LFMM_PROFILE_STAGES if profile else 0, 0)
+    flags = (LFMM_PROFILE_STAGES if profile else 0) | (LFMM_AUTOTUNE if autotune else 0)
+    prm = Params(int(p), int(leaf_size), flags, 0)
     h = ctypes.c_void_p()
     _check(library().lfmm_geometry_build(medium.handle, pts.shape[0], _dp(pts), _dp(w),
                                          _dp(nrm) if nrm is not None else None, ctypes.byref(prm),
@@ -307,6 +309,14 @@ def geometry_query(g: Geometry, name: str, dtype=np.int32) -> np.ndarray:
     _check(library().lfmm_geometry_query(g.handle, name.encode(), ctypes.c_void_p(out.ctypes.data), need.value,
                                          ctypes.byref(need)))
     return out
+
+
+def tuning(g: Geometry) -> dict:
+    """The M2L work-item schedule of a geometry and, when it was built with
+    autotune=True, the measured milliseconds of one FP64 M2L with the default and
+    the chosen schedule."""
+    v = geometry_query(g, "tuning", np.float64)
+    return {"item_work": int(v[0]), "wide_rows": bool(v[1]), "ms_default": float(v[2]), "ms_best": float(v[3])}
 
 
 def stage_times(g: Geometry) -> dict:
