@@ -15,6 +15,9 @@ Modules
                 a direct interface solve + adaptive Sommerfeld contour quadrature
   green         free-space kernel (i/4) H_0^(1) and the full layered G
   nystrom       elements, self term I^s, dense K, matvec, field evaluation
+  combined      combined-field (double + single layer) operator and field, an
+                opt-in second-kind form; needs the field-point gradient of G^r
+                (core.gr_grad_block)
   background    plane incidence and the background field u^b (transfer solve)
   paper_forms   the paper's own recursions (R~, T~, sigma, A_l, B_l), used only
                 to pin them against the direct solves

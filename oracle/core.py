@@ -25,6 +25,8 @@ def _lib():
                                         ctypes.c_double, dp, ip]
         lib.oracle_gr_block.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp,
                                         ctypes.c_long, dp, dp, ctypes.c_double, dp]
+        lib.oracle_gr_grad_block.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp,
+                                             ctypes.c_long, dp, dp, ctypes.c_double, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -93,3 +95,19 @@ def gr_block(medium, xr, yr, xc, yc, tol_rel: float = 1e-13) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("oracle G^r block: quadrature or interface-solve failure")
     return out
+
+
+def gr_grad_block(medium, xr, yr, xc, yc, tol_rel: float = 1e-13):
+    """Gradient of G^r with respect to the FIELD point (xr, yr): two dense blocks
+    (d/dx, d/dy), rows are field points, columns source points."""
+    xr, yr, xc, yc = (np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+                      for a in (xr, yr, xc, yc))
+    yint, k, eta = _medium_arrays(medium)
+    gx = np.zeros((xr.size, xc.size), dtype=np.complex128)
+    gy = np.zeros((xr.size, xc.size), dtype=np.complex128)
+    rc = _lib().oracle_gr_grad_block(int(k.size), _dp(yint), _dp(k), _dp(eta), xr.size, _dp(xr),
+                                     _dp(yr), xc.size, _dp(xc), _dp(yc), float(tol_rel),
+                                     _dp(gx.view(np.float64)), _dp(gy.view(np.float64)))
+    if rc != 0:
+        raise RuntimeError("oracle grad G^r block: quadrature or interface-solve failure")
+    return gx, gy

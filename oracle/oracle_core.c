@@ -41,6 +41,12 @@
  *     D the smallest vertical travel distance of the reflected waves; along it
  *     e^{+-i lambda X} e^{-lambda D} decays like e^{-rho t} without oscillating
  *     (Jordan's lemma: no singularity lies in the swept sector).
+ * Gradient with respect to the FIELD point (x, y), for the double-layer
+ * (combined-field) kernel: d/dx multiplies the spectral integrand by i lambda
+ * (cos(lambda X) becomes -lambda sin(lambda X) on the detour, e^{+-i lambda X}
+ * gains +-i lambda on the rays); d/dy multiplies the wave arriving from below
+ * (referenced at the field layer's bottom, e^{i k_y (y + d)}) by +i k_y and the
+ * wave arriving from above (e^{i k_y (-d' - y)}) by -i k_y.
  * Both pieces use adaptive Gauss-Kronrod (7,15) quadrature (Kronrod 1965;
  * the node/weight values are the standard published ones), the ray after the
  * map t = s/((1-s) rho), s in [0,1).
@@ -200,6 +206,7 @@ typedef struct {
     int lf, ls;
     double y, ys, X, D;
     double hf_up, hf_dn, hs_up, hs_dn; /* heights (valid where the term exists) */
+    int mode;                          /* 0: G^r, 1: dG^r/dx, 2: dG^r/dy (field point) */
     int err;
 } pair_ctx;
 
@@ -211,7 +218,10 @@ static cplx gt_r(pair_ctx *c, cplx lam) {
     cplx ef_dn = (S[2] != 0.0 || S[3] != 0.0) ? cexp(I * kf * c->hf_dn) : 0.0;
     cplx es_up = (S[0] != 0.0 || S[2] != 0.0) ? cexp(I * ks * c->hs_up) : 0.0;
     cplx es_dn = (S[1] != 0.0 || S[3] != 0.0) ? cexp(I * ks * c->hs_dn) : 0.0;
-    return S[0] * ef_up * es_up + S[1] * ef_up * es_dn + S[2] * ef_dn * es_up + S[3] * ef_dn * es_dn;
+    cplx up = S[0] * ef_up * es_up + S[1] * ef_up * es_dn;   /* arriving from below */
+    cplx dn = S[2] * ef_dn * es_up + S[3] * ef_dn * es_dn;   /* arriving from above */
+    if (c->mode == 2) return I * kf * (up - dn);
+    return up + dn;
 }
 
 /* integrand pieces */
@@ -229,7 +239,8 @@ static cplx integrand(integ_ctx *ic, double s) {
         double t = s;
         cplx lam = t - I * ic->h * sin(PI * t / ic->T);
         cplx dlam = 1.0 - I * ic->h * (PI / ic->T) * cos(PI * t / ic->T);
-        return gt_r(pc, lam) * ccos(lam * pc->X) * dlam / PI;
+        cplx osc = (pc->mode == 1) ? -lam * csin(lam * pc->X) : ccos(lam * pc->X);
+        return gt_r(pc, lam) * osc * dlam / PI;
     }
     if (s >= 1.0) return 0.0;
     double t = s / ((1.0 - s) * ic->rho);
@@ -237,6 +248,7 @@ static cplx integrand(integ_ctx *ic, double s) {
     cplx lam = ic->T + t * ic->u;
     double sg = (ic->kind == 1) ? 1.0 : -1.0;
     cplx v = gt_r(pc, lam) * cexp(I * sg * lam * pc->X) * ic->u * dt / (2.0 * PI);
+    if (pc->mode == 1) v *= I * sg * lam;
     return v;
 }
 
@@ -291,13 +303,14 @@ static int layer_of(const medium_t *m, double y) {
  * (a point on an interface), 3 on a singular interface system.
  */
 static int gr_pair(const medium_t *m, double x, double y, double xs, double ys,
-                   double tol_rel, cplx *out) {
+                   double tol_rel, int mode, cplx *out) {
     *out = 0.0;
     int L = m->nl - 1;
     if (L == 0) return 0;
     pair_ctx pc;
     memset(&pc, 0, sizeof(pc));
     pc.m = m;
+    pc.mode = mode;
     pc.lf = layer_of(m, y);
     pc.ls = layer_of(m, ys);
     pc.y = y; pc.ys = ys; pc.X = x - xs;
@@ -373,7 +386,7 @@ int oracle_gr_pairs(int nl, const double *yint, const double *k, const double *e
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
     for (long i = 0; i < n; ++i) {
         cplx v;
-        int st = gr_pair(&m, x[i], y[i], xs[i], ys[i], tol_rel, &v);
+        int st = gr_pair(&m, x[i], y[i], xs[i], ys[i], tol_rel, 0, &v);
         out_ri[2 * i] = creal(v);
         out_ri[2 * i + 1] = cimag(v);
         if (status) status[i] = st;
@@ -384,10 +397,10 @@ int oracle_gr_pairs(int nl, const double *yint, const double *k, const double *e
 
 /* Dense block of G^r: rows = field points (nr), columns = source points (nc);
  * out is row-major (nr, nc) complex interleaved. */
-int oracle_gr_block(int nl, const double *yint, const double *k, const double *eta,
-                    long nr, const double *xr, const double *yr,
-                    long nc, const double *xc, const double *yc,
-                    double tol_rel, double *out_ri) {
+static int gr_block_mode(int nl, const double *yint, const double *k, const double *eta,
+                         long nr, const double *xr, const double *yr,
+                         long nc, const double *xc, const double *yc,
+                         double tol_rel, int mode, double *out_ri) {
     medium_t m;
     if (make_medium(&m, nl, yint, k, eta)) return -1;
     int bad = 0;
@@ -395,13 +408,31 @@ int oracle_gr_block(int nl, const double *yint, const double *k, const double *e
     for (long i = 0; i < nr; ++i) {
         for (long j = 0; j < nc; ++j) {
             cplx v;
-            int st = gr_pair(&m, xr[i], yr[i], xc[j], yc[j], tol_rel, &v);
+            int st = gr_pair(&m, xr[i], yr[i], xc[j], yc[j], tol_rel, mode, &v);
             out_ri[2 * (i * nc + j)] = creal(v);
             out_ri[2 * (i * nc + j) + 1] = cimag(v);
             if (st != 0) bad = 1;
         }
     }
     return bad;
+}
+
+int oracle_gr_block(int nl, const double *yint, const double *k, const double *eta,
+                    long nr, const double *xr, const double *yr,
+                    long nc, const double *xc, const double *yc,
+                    double tol_rel, double *out_ri) {
+    return gr_block_mode(nl, yint, k, eta, nr, xr, yr, nc, xc, yc, tol_rel, 0, out_ri);
+}
+
+/* Gradient of G^r with respect to the field point: out_dx, out_dy as in
+ * oracle_gr_block (rows = field points, columns = source points). */
+int oracle_gr_grad_block(int nl, const double *yint, const double *k, const double *eta,
+                         long nr, const double *xr, const double *yr,
+                         long nc, const double *xc, const double *yc,
+                         double tol_rel, double *out_dx, double *out_dy) {
+    int a = gr_block_mode(nl, yint, k, eta, nr, xr, yr, nc, xc, yc, tol_rel, 1, out_dx);
+    int b = gr_block_mode(nl, yint, k, eta, nr, xr, yr, nc, xc, yc, tol_rel, 2, out_dy);
+    return a | b;
 }
 
 int oracle_num_threads(void) {
