@@ -73,7 +73,14 @@ enum {
                                candidates on this geometry at set-up (some 40 M2L launches);
                                read the choice with lfmm_geometry_query("tuning").  Results
                                differ from the default schedule only in the order in which
-                               the parts of a split sum are added */
+                               the parts of a split sum are added */,
+    LFMM_COMBINED_FIELD = 4 /* combined-field operator instead of the paper's single layer
+                               (needs the normals): 1/2 I + D - i k S with D the double
+                               layer of the layered Green's function (normal derivative at
+                               the element, outward normals) and the coupling k of the
+                               element's layer; the unknown, the right-hand side and the
+                               field keep their single-layer meaning otherwise.  Second
+                               kind: GMRES iterations stay nearly flat under refinement */
 };
 
 typedef struct lfmm_medium_s *lfmm_medium;
@@ -84,7 +91,7 @@ typedef struct {
     int32_t p;          /* expansion order at the fine levels (default 20); coarse levels
                            raise it with k*w (wide-band rule), up to 80 */
     int32_t leaf_size;  /* max points per leaf box (default 64) */
-    int32_t flags;      /* LFMM_PROFILE_STAGES | LFMM_AUTOTUNE, or 0 */
+    int32_t flags;      /* LFMM_PROFILE_STAGES | LFMM_AUTOTUNE | LFMM_COMBINED_FIELD, or 0 */
     int32_t reserved;
 } lfmm_params;
 
@@ -136,7 +143,8 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m);
  *   n       : number of elements/collocation points (>= 1)
  *   points  : 2n doubles, collocation points (x, y) (element centres)
  *   weights : n doubles, element lengths |Gamma_e| > 0
- *   normals : 2n doubles or NULL (unused by the single-layer formulation)
+ *   normals : 2n doubles, outward unit normals (needed with LFMM_COMBINED_FIELD,
+ *             else NULL or ignored)
  *   prm     : NULL for defaults
  * Errors: LFMM_ERR_INVALID_ARG, LFMM_ERR_NODE_ON_INTERFACE, LFMM_ERR_OUT_OF_MEMORY,
  *         LFMM_ERR_CUDA, LFMM_ERR_QUADRATURE.

@@ -73,6 +73,7 @@ QuadRule make_quad_rule(const MediumDev& m) {
     // neither the wide-band nor the C2 parity (1.2e-10, a few 1e-9) and cost 1.6x
     // the set-up time
     q.tab_panel_mult = 1;
+    q.tab_T = m.kmax + 0.75;
     gauss_legendre8(q.gl_x, q.gl_w);
     return q;
 }
@@ -221,7 +222,6 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m) {
 
 lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points, const double* weights,
                                 const double* normals, const lfmm_params* prm, lfmm_geometry* out) {
-    (void)normals;
     lfmm_geometry_s* g = nullptr;
     lfmm_status st = guarded([&]() -> lfmm_status {
         auto t0 = std::chrono::steady_clock::now();
@@ -232,6 +232,13 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         int leaf = prm ? prm->leaf_size : 64;
         require(p >= 1 && p <= 80, "p must be in [1, 80]");
         require(leaf >= 1 && leaf <= 1024, "leaf_size must be in [1, 1024]");
+        const bool cf = prm && (prm->flags & LFMM_COMBINED_FIELD);
+        require(!cf || normals != nullptr, "the combined-field operator needs the normals");
+        if (cf)
+            for (int64_t i = 0; i < n; ++i) {
+                const double nn = std::hypot(normals[2 * i], normals[2 * i + 1]);
+                require(std::isfinite(nn) && std::fabs(nn - 1.0) <= 1e-8, "normals must be unit vectors");
+            }
         const MediumDev& m = med->m;
         std::vector<double> px(n), py(n), pw(n);
         std::vector<int> layer(n);
@@ -264,6 +271,17 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         }
         build_tree(g->tree, px, py, layer, m, p, leaf);
         TreeHost& t = g->tree;
+        if (t.l0 <= t.D) {   // the leaf P2M / L2P stage a group's basis rows in shared memory
+            int mx = EXP_GROUP_PTS;
+            for (int b = t.level_start[t.D]; b < t.level_start[t.D + 1]; ++b)
+                mx = std::max(mx, t.box_end[b] - t.box_begin[b]);
+            const size_t pD = (size_t)t.p_level[t.D];
+            const size_t p2m = (size_t)mx * (2 * pD + 3) * sizeof(cd) + (size_t)mx * sizeof(cd) + (mx + 1) * sizeof(int);
+            const size_t l2p = ((size_t)mx * (pD + 1) + 1) * sizeof(double) + EXP_GROUP_ENTRIES * 2 * (pD + 1) * sizeof(cd);
+            require(std::max(p2m, l2p) <= 227 * 1024,
+                    "leaf_size too large for the expansion order at the leaves (their P2M / L2P stage a leaf's "
+                    "basis rows in shared memory): lower leaf_size or p");
+        }
         // sorted-order copies
         g->hx.resize(n); g->hy.resize(n); g->hw.resize(n);
         for (int64_t s = 0; s < n; ++s) {
@@ -273,6 +291,16 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         g->d_x = dupload(g, g->hx);
         g->d_y = dupload(g, g->hy);
         g->d_w = dupload(g, g->hw);
+        if (cf) {
+            std::vector<double> hnx(n), hny(n);
+            for (int64_t s = 0; s < n; ++s) {
+                hnx[s] = normals[2 * t.perm[s]];
+                hny[s] = normals[2 * t.perm[s] + 1];
+            }
+            g->combined = true;
+            g->d_nx = dupload(g, hnx);
+            g->d_ny = dupload(g, hny);
+        }
         g->d_layer = dupload(g, t.layer_sorted);
         g->d_perm = dupload(g, t.perm);
         g->d_box_begin = dupload(g, t.box_begin);

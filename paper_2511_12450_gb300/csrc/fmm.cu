@@ -588,7 +588,8 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     for (int l = l0; l <= D; ++l) pmax = std::max(pmax, t.p_level[l]);
     // shared memory of the grouped P2M / L2P kernels (same order p = p_D for every entry)
     const int gp = g->group_max_pts, ge = g->group_max_ent;
-    const size_t smem_p2m = (size_t)gp * (2 * pD + 1) * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
+    const int rs_p2m = 2 * (g->combined ? pD + 1 : pD) + 1;   // basis row length (k_p2m)
+    const size_t smem_p2m = (size_t)gp * rs_p2m * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
     const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd);
     if (smem_p2m > g->smem_p2m_set) {
         cuda_check(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2m), "p2m smem");
@@ -607,13 +608,14 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
             mixed_p2m(g, x_sorted, nrhs, s);
         } else {
             k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
-                                                          g->d_w, x_sorted, g->n, nrhs, g->ncoef, g->d_M);
+                                                          g->d_w, g->d_nx, g->d_ny, x_sorted, g->n, nrhs, g->ncoef,
+                                                          g->d_M);
             cuda_check(cudaGetLastError(), "k_p2m");
             ++g->n_launches;
             if (g->n_slot_groups > 0) {
                 k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x,
-                                                              g->d_y, g->d_w, x_sorted, g->n, nrhs, g->nslotcoef,
-                                                              g->d_Mp);
+                                                              g->d_y, g->d_w, g->d_nx, g->d_ny, x_sorted, g->n, nrhs,
+                                                              g->nslotcoef, g->d_Mp);
                 cuda_check(cudaGetLastError(), "k_p2m slots");
                 ++g->n_launches;
             }

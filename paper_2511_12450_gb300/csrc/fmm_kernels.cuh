@@ -44,15 +44,22 @@ __device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, in
 // row u_{j,n} = J_n(k rho_j) e^{-i n theta_j} for n = -p..p (J_{-n} = (-1)^n J_n,
 // e^{+i n theta} = conj) into shared memory.  Phase 2, one thread per (entry,
 // coefficient): the sum over the entry's points, pure complex FMAs.
+// Combined field (normals given): the row is the basis of a dipole along n_j
+// plus -i k times the charge's, E_n = n_j . grad u_n - i k u_n, with
+// n . grad u_n = (k/2)(conj(nu) u_{n-1} - nu u_{n+1}), nu = n_x + i n_y (from
+// (d_x +- i d_y) J_m e^{i m theta} = -+k J_{m+-1} e^{i (m+-1) theta}); the
+// translations are linear and carry it unchanged.
 __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
                       MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
-                      const double* __restrict__ pw, const cd* __restrict__ phi, int64_t n, int nrhs,
-                      int64_t stride, cd* __restrict__ M) {
-    extern __shared__ cd su[];   // [npts][2p+1] basis rows, then [npts] q, then [nent + 1] point offsets (ints)
+                      const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
+                      const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
+    extern __shared__ cd su[];   // [npts][rs] basis rows, then [npts] q, then [nent + 1] point offsets (ints)
     const ExpGroup G = groups[blockIdx.x];
     const int p = ent[G.e0].p, nco = 2 * p + 1;
+    const bool cf = nx != nullptr;
+    const int pb = cf ? p + 1 : p, rs = 2 * pb + 1;   // order and length of the plain basis rows
     const int ne = G.e1 - G.e0;
-    cd* sq = su + (size_t)G.npts * nco;
+    cd* sq = su + (size_t)G.npts * rs;
     int* soff = (int*)(sq + G.npts);
     if (threadIdx.x == 0) {
         int o = 0;
@@ -65,22 +72,32 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
         const ExpEntry& E = ent[G.e0 + er];
         const double dx = px[j] - E.cx, dy = py[j] - E.cy;
         const double rho = hypot(dx, dy);
-        cd* u = su + (size_t)t * nco;
-        double* Jd = (double*)u;   // J_0..J_p in the first p+1 doubles of the row
-        bessel_j_seq_small(m.k[E.lay] * rho, p, Jd);
+        cd* u = su + (size_t)t * rs;
+        double* Jd = (double*)u;   // J_0..J_pb in the first pb+1 doubles of the row
+        bessel_j_seq_small(m.k[E.lay] * rho, pb, Jd);
         double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
         const cd z = (rho > 0.0) ? mk(dx * irho, -dy * irho) : mk(1.0, 0.0);
-        // u_n, n = 0..p, into cd slots p..2p (doubles 2p.. , above the J's for p >= 1),
+        // u_n, n = 0..pb, into cd slots pb..2pb (doubles 2pb.., above the J's),
         // z^n upward from z^0 = 1
         cd zn = mk(1.0, 0.0);
-        for (int k2 = 0; k2 <= p; ++k2) {
+        for (int k2 = 0; k2 <= pb; ++k2) {
             if (k2 > 0) zn = zn * z;
-            u[p + k2] = Jd[k2] * zn;
+            u[pb + k2] = Jd[k2] * zn;
         }
-        // u_{-n} = (-1)^n conj(u_n) into slots p-1..0 (the J's are no longer needed)
-        for (int k2 = 1; k2 <= p; ++k2) {
-            const cd v = u[p + k2];
-            u[p - k2] = (k2 & 1) ? mk(-v.x, v.y) : mk(v.x, -v.y);
+        // u_{-n} = (-1)^n conj(u_n) into slots pb-1..0 (the J's are no longer needed)
+        for (int k2 = 1; k2 <= pb; ++k2) {
+            const cd v = u[pb + k2];
+            u[pb - k2] = (k2 & 1) ? mk(-v.x, v.y) : mk(v.x, -v.y);
+        }
+        if (cf) {   // E_n into slot n + p from u_{n-1}, u_n, u_{n+1} (slots n+p, n+p+1, n+p+2);
+                    // ascending n overwrites only u_{n-1}, which later n do not read
+            const double k = m.k[E.lay];
+            const cd nu = mk(nx[j], ny[j]), nub = conjc(nu);
+            for (int s2 = 0; s2 < nco; ++s2) {
+                const cd um = u[s2], u0 = u[s2 + 1], up = u[s2 + 2];
+                const cd d = 0.5 * (nub * um - nu * up);
+                u[s2] = k * mk(d.x + u0.y, d.y - u0.x);   // k (d - i u_n)
+            }
         }
     }
     for (int col = 0; col < nrhs; ++col) {
@@ -94,7 +111,7 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
         for (int task = threadIdx.x; task < ne * nco; task += blockDim.x) {
             const int er = task / nco, idx = task - er * nco;
             cd a = mk(0, 0);
-            for (int t = soff[er]; t < soff[er + 1]; ++t) cfma(a, sq[t], su[(size_t)t * nco + idx]);
+            for (int t = soff[er]; t < soff[er + 1]; ++t) cfma(a, sq[t], su[(size_t)t * rs + idx]);
             M[(int64_t)col * stride + ent[G.e0 + er].off + idx] = a;
         }
     }
@@ -328,19 +345,15 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
     cd* Fp = Pw + CH * nd;       // [CH]
     cd* Fm = Fp + CH;            // [CH]
     cd* hs = Fm + CH;            // [nd] moments
-    QuadRule qt = q;
-    qt.es_v0 = q.tab_es_v0;
-    qt.es_hv = q.tab_es_hv;
-    qt.nes = q.tab_nes;
     double h;
-    const int P = detour_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
-    const int ntot = P * 8 + 2 * qt.nes;
+    const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
+    const int ntot = P * 8 + 2 * q.tab_nes;
     cd acc[2] = {mk(0, 0), mk(0, 0)};   // d = threadIdx.x and threadIdx.x + 256
     for (int j0 = 0; j0 < ntot; j0 += CH) {
         const int cnt = min(CH, ntot - j0);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            QuadNode nd2 = contour_node(qt, j0 + threadIdx.x, P, h, K.X, K.D);
+            QuadNode nd2 = table_contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd2.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd2.lam);
             cd SE = S * (eikh(kya, K.hS) * eikh(kya, K.hT));
@@ -404,14 +417,11 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     cd* Fm = Fp + CH;                  // [CH]
     cd* uu = Fm + CH;                  // [CH] u
     cd* vv = uu + CH;                  // [CH] v
-    // table rule: finer detour (panels grow with the orders) and finer rays
-    QuadRule qt = q;
-    qt.es_v0 = q.tab_es_v0;
-    qt.es_hv = q.tab_es_hv;
-    qt.nes = q.tab_nes;
+    // table rule: its own contour (table_contour_node), panels growing with the
+    // orders, finer rays
     double h;
-    const int P = detour_panels(q, K.X, K.D, &h) * q.tab_panel_mult + (pS + pT);
-    const int ntot = P * 8 + 2 * qt.nes;
+    const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + (pS + pT);
+    const int ntot = P * 8 + 2 * q.tab_nes;
     const int tm = threadIdx.x >> 3;          // 0..31 row within tile
     const int tn = (threadIdx.x & 7) * 4;     // 0..28 first column within tile
     cd acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
         const int cnt = min(CH, ntot - j0);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            QuadNode nd = contour_node(qt, j0 + threadIdx.x, P, h, K.X, K.D);
+            QuadNode nd = table_contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
             cd E = eikh(kya, K.hS) * eikh(kyb, K.hT);

@@ -35,6 +35,11 @@ struct QuadRule {
     double tab_es_v0, tab_es_hv;
     int tab_nes;
     int tab_panel_mult;
+    // end of the tables' detour, just past the largest branch point: the moments of
+    // an expansion layer with k < k_max carry |w|^{-n} ~ (2 lambda / k)^n over its
+    // evanescent range (k, T), which largely cancels, so a shorter real-axis
+    // stretch keeps the rounding of the moments small
+    double tab_T;
     double gl_x[8];    // 8-point Gauss-Legendre rule on [-1, 1]
     double gl_w[8];
 };
@@ -135,6 +140,8 @@ struct lfmm_geometry_s {
 
     // sorted-order point data
     double *d_x = nullptr, *d_y = nullptr, *d_w = nullptr;
+    bool combined = false;                   // combined-field operator (LFMM_COMBINED_FIELD)
+    double *d_nx = nullptr, *d_ny = nullptr; // outward unit normals (sorted order), combined field only
     int *d_layer = nullptr, *d_perm = nullptr;
     // boxes
     int *d_box_begin = nullptr, *d_box_end = nullptr, *d_box_layer = nullptr, *d_box_level = nullptr;

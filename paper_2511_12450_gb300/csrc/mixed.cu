@@ -298,16 +298,23 @@ __device__ __forceinline__ void bessel_j_scaled_f(float x, float s, int p, float
 
 // P2M in FP32 at the leaves (cell centres and straddling leaves' reaction centres):
 // M~_n = sum_j q_j J_n(k rho_j) e^{-i n theta_j} / s^|n|.  Same grouping and
-// phases as the FP64 kernel.
+// phases as the FP64 kernel.  Combined field (normals given): the scaled dipole +
+// charge basis E_n / s^|n| = k [ (conj(nu) u~_{n-1} s^{|n-1|-|n|} - nu u~_{n+1}
+// s^{|n+1|-|n|}) / 2 - i u~_n ] with u~_m = u_m / s^|m|, stored for every n.
 __global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
                         MediumDev m, const double* __restrict__ sc, int lev, int nlev,
                         const double* __restrict__ px, const double* __restrict__ py, const double* __restrict__ pw,
+                        const double* __restrict__ nx, const double* __restrict__ ny,
                         const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cf* __restrict__ M) {
-    extern __shared__ cf su32[];   // [npts][p+1] u, then [npts] q, then [nent + 1] offsets
+    extern __shared__ cf su32[];   // [npts][rs] u, then [npts] q, then [nent + 1] offsets
     const ExpGroup G = groups[blockIdx.x];
-    const int p = ent[G.e0].p, np1 = p + 1, nco = 2 * p + 1;
+    const int p = ent[G.e0].p, nco = 2 * p + 1;
+    const bool cfm = nx != nullptr;
+    // rows: u~_0..u~_p (single layer; negative orders by symmetry in phase 2), or the
+    // combined-field basis for n = -p..p in a row of 2p + 3 (room for u~_{-p-1..p+1})
+    const int pb = cfm ? p + 1 : p, rs = cfm ? 2 * p + 3 : p + 1, o0 = cfm ? p + 1 : 0;
     const int ne = G.e1 - G.e0;
-    cf* sq = su32 + (size_t)G.npts * np1;
+    cf* sq = su32 + (size_t)G.npts * rs;
     int* soff = (int*)(sq + G.npts);
     if (threadIdx.x == 0) {
         int o = 0;
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ grou
         const ExpEntry& E = ent[G.e0 + er];
         const double dx = px[j] - E.cx, dy = py[j] - E.cy;
         const double rho = hypot(dx, dy);
-        cf* u = su32 + (size_t)t * np1;
+        cf* u = su32 + (size_t)t * rs + o0;
         // u_n = J~_n z^n, z = e^{-i theta}, upward from z^0 = 1 so the low orders carry
         // the least rounding
         const float x = (float)(m.k[E.lay] * rho), sf = (float)sc[E.lay * nlev + lev];
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ grou
         const cf z = (rho > 0.0) ? mkf((float)(dx / rho), (float)(-dy / rho)) : mkf(1.0f, 0.0f);
         cf zn = mkf(1.0f, 0.0f);
         float tn = 1.0f;
-        for (int k2 = 0; k2 <= p; ++k2) {
+        for (int k2 = 0; k2 <= pb; ++k2) {
             if (k2 > 0) { tn *= a / (float)k2; zn = mulf(zn, z); }
             float c = 1.0f, S = 1.0f;
             for (int k = 1; k <= 40; ++k) {
@@ -338,6 +345,26 @@ __global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ grou
             }
             const float jv = tn * S;
             u[k2] = mkf(jv * zn.x, jv * zn.y);
+        }
+        if (cfm) {
+            for (int k2 = 1; k2 <= pb; ++k2) {   // u~_{-m} = (-1)^m conj(u~_m)
+                const cf v = u[k2];
+                u[-k2] = (k2 & 1) ? mkf(-v.x, v.y) : mkf(v.x, -v.y);
+            }
+            // E~_n into row slot n + p from u~_{n-1}, u~_n, u~_{n+1} (row slots n+p .. n+p+2);
+            // ascending n overwrites only u~_{n-1}
+            cf* row = u - o0;
+            const float k = (float)m.k[E.lay], isf = 1.0f / sf;
+            const cf nu = mkf((float)nx[j], (float)ny[j]);
+            for (int s2 = 0; s2 < nco; ++s2) {
+                const int nn = s2 - p;
+                const float fm = (nn >= 1) ? isf : sf, fp = (nn <= -1) ? isf : sf;
+                const cf um = row[s2], u0 = row[s2 + 1], up = row[s2 + 2];
+                // conj(nu) um fm - nu up fp
+                const float dx2 = fm * (nu.x * um.x + nu.y * um.y) - fp * (nu.x * up.x - nu.y * up.y);
+                const float dy2 = fm * (nu.x * um.y - nu.y * um.x) - fp * (nu.x * up.y + nu.y * up.x);
+                row[s2] = mkf(k * (0.5f * dx2 + u0.y), k * (0.5f * dy2 - u0.x));
+            }
         }
     }
     for (int col = 0; col < nrhs; ++col) {
@@ -353,10 +380,14 @@ __global__ void __launch_bounds__(128) k_p2m32(const ExpGroup* __restrict__ grou
             const int er = task / nco, idx = task - er * nco;
             const int nn = idx - p, an = nn < 0 ? -nn : nn;
             cf acc = mkf(0, 0);
-            for (int t = soff[er]; t < soff[er + 1]; ++t) {
-                cf v = su32[(size_t)t * np1 + an];
-                if (nn < 0) { v.y = -v.y; if (an & 1) { v.x = -v.x; v.y = -v.y; } }
-                cfmaf(acc, sq[t], v);
+            if (cfm) {
+                for (int t = soff[er]; t < soff[er + 1]; ++t) cfmaf(acc, sq[t], su32[(size_t)t * rs + idx]);
+            } else {
+                for (int t = soff[er]; t < soff[er + 1]; ++t) {
+                    cf v = su32[(size_t)t * rs + an];
+                    if (nn < 0) { v.y = -v.y; if (an & 1) { v.x = -v.x; v.y = -v.y; } }
+                    cfmaf(acc, sq[t], v);
+                }
             }
             M[(int64_t)col * stride + ent[G.e0 + er].off + idx] = acc;
         }
@@ -613,7 +644,8 @@ static void mixed_build(lfmm_geometry_s* g) {
     }
     // shared memory of the FP32 P2M / L2P (all entries at the leaf order)
     const int pD = t.p_level[D], gp = g->group_max_pts, ge = g->group_max_ent;
-    ms->smem_p2m = (size_t)gp * (pD + 1) * sizeof(cf) + (size_t)gp * sizeof(cf) + (size_t)(gp + 1) * sizeof(int);
+    const int rs_p2m = g->combined ? 2 * pD + 3 : pD + 1;   // basis row length (k_p2m32)
+    ms->smem_p2m = (size_t)gp * rs_p2m * sizeof(cf) + (size_t)gp * sizeof(cf) + (size_t)(gp + 1) * sizeof(int);
     ms->smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(float) + (size_t)ge * (2 * pD + 1) * sizeof(cf);
     if (ms->smem_p2m > 48 * 1024)
         cuda_check(cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_p2m),
@@ -662,13 +694,14 @@ void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s)
     MixedState* ms = g->mixed;
     const int D = g->tree.D, nlev = D + 1;
     k_p2m32<<<g->n_leaf_groups, 128, ms->smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, ms->d_scale, D, nlev,
-                                                       g->d_x, g->d_y, g->d_w, x_sorted, g->n, nrhs, g->ncoef, ms->M);
+                                                       g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny, x_sorted, g->n,
+                                                       nrhs, g->ncoef, ms->M);
     cuda_check(cudaGetLastError(), "k_p2m32");
     ++g->n_launches;
     if (g->n_slot_groups > 0) {
         k_p2m32<<<g->n_slot_groups, 128, ms->smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, ms->d_scale, D,
-                                                           nlev, g->d_x, g->d_y, g->d_w, x_sorted, g->n, nrhs,
-                                                           g->nslotcoef, ms->Mp);
+                                                           nlev, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
+                                                           x_sorted, g->n, nrhs, g->nslotcoef, ms->Mp);
         cuda_check(cudaGetLastError(), "k_p2m32 slots");
         ++g->n_launches;
     }

@@ -8,7 +8,10 @@
 //   |Gamma_j| (i/4) H_0(k |c_i - c_j|)                 free space, same layer, j != i
 //   I^s_i                                               j == i (analytic self term)
 //   |Gamma_j| sum_c K_c(x_j - x_i, h_s(y_j), h_t(y_i))  reaction components near in the image frame
-// and acts on Phi directly.  The blocks are computed once at set-up (Sommerfeld
+// and acts on Phi directly.  In the combined-field form (opt-in) every entry is
+// |Gamma_j| [n_j . grad_{c_j} - i k] of the same kernels, and the diagonal is
+// 1/2 - i k I^s (devmath.cuh: free_kernel, self_entry; sommerfeld.cuh:
+// react_kernel_grad_warp).  The blocks are computed once at set-up (Sommerfeld
 // quadrature for the reaction entries) and stored column-major, so the per
 // matvec near field is one streaming block-sparse product bounded by HBM
 // bandwidth.
@@ -23,8 +26,6 @@
 
 namespace lfmm {
 
-static const double EULER_GAMMA = 0.57721566490153286060651209008240243;
-
 struct NearTask {   // one (block, component) reaction task
     int blk;        // block index
     int comp;
@@ -36,7 +37,9 @@ __global__ void k_near_free(MediumDev m, const int* __restrict__ blk_tgt, const 
                             const int64_t* __restrict__ blk_off, const unsigned char* __restrict__ blk_free,
                             const int* __restrict__ box_begin, const int* __restrict__ box_end,
                             const int* __restrict__ box_layer, const double* __restrict__ px,
-                            const double* __restrict__ py, const double* __restrict__ pw, cd* __restrict__ val) {
+                            const double* __restrict__ py, const double* __restrict__ pw,
+                            const double* __restrict__ nx, const double* __restrict__ ny, cd* __restrict__ val) {
+    const bool cf = nx != nullptr;
     const int blk = blockIdx.x;
     const int T = blk_tgt[blk], S = blk_src[blk];
     const int tb = box_begin[T], nT = box_end[T] - tb;
@@ -50,13 +53,10 @@ __global__ void k_near_free(MediumDev m, const int* __restrict__ blk_tgt, const 
         if (fr) {
             int pi = tb + i, pj = sb + j;
             if (pi == pj) {
-                double wl = pw[pi];
-                out = mk(-(EULER_GAMMA + log(k * wl / 4.0) - 1.0) / (2.0 * M_PI) * wl, 0.25 * wl);
+                out = self_entry(k, pw[pi], cf);
             } else {
-                double r = hypot(px[pi] - px[pj], py[pi] - py[pj]);
-                double z = k * r;
-                // (i/4) H_0(z) = (i/4)(J_0 + i Y_0) = (-Y_0/4, J_0/4)
-                out = mk(-0.25 * y0(z) * pw[pj], 0.25 * j0(z) * pw[pj]);
+                out = pw[pj] * free_kernel(k, px[pj] - px[pi], py[pj] - py[pi], cf, cf ? nx[pj] : 0.0,
+                                           cf ? ny[pj] : 0.0);
             }
         }
         v[(int64_t)j * nT + i] = out;
@@ -69,7 +69,9 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
                              const int64_t* __restrict__ blk_off, const int* __restrict__ comp,
                              const double* __restrict__ comp_H, const int* __restrict__ box_begin,
                              const int* __restrict__ box_end, const double* __restrict__ px,
-                             const double* __restrict__ py, const double* __restrict__ pw, cd* __restrict__ val) {
+                             const double* __restrict__ py, const double* __restrict__ pw,
+                             const double* __restrict__ nx, const double* __restrict__ ny, cd* __restrict__ val) {
+    const bool cf = nx != nullptr;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t wk = warp; wk < nwork; wk += nwarps) {
@@ -91,7 +93,14 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
         const double X = px[pj] - px[pi];
         const double hs = (a == 0) ? (py[pj] - m.yint[ls]) : (m.yint[ls - 1] - py[pj]);
         const double ht = (b == 0) ? (m.yint[lt - 1] - py[pi]) : (py[pi] - m.yint[lt]);
-        cd K = react_kernel_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht);
+        cd K;
+        if (cf) {
+            cd gk[3];
+            react_kernel_grad_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht, gk);
+            K = react_cf_combine(gk, a, m.k[ls], nx[pj], ny[pj]);
+        } else {
+            K = react_kernel_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht);
+        }
         if ((threadIdx.x & 31) == 0) {
             cd* dst = val + blk_off[tk.blk] + (int64_t)j * nT + i;
             double wj = pw[pj];
@@ -188,7 +197,8 @@ void near_build(lfmm_geometry_s* g) {
     double* d_compH = dupload(g, compH);
     if (g->n_blocks > 0) {
         k_near_free<<<g->n_blocks, 128>>>(g->m, d_bt, g->d_nb_src, g->d_nb_off, d_bf, g->d_box_begin,
-                                          g->d_box_end, g->d_box_layer, g->d_x, g->d_y, g->d_w, g->d_nb_val);
+                                          g->d_box_end, g->d_box_layer, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
+                                          g->d_nb_val);
         cuda_check(cudaGetLastError(), "k_near_free");
     }
     if (!tasks.empty()) {
@@ -198,7 +208,8 @@ void near_build(lfmm_geometry_s* g) {
         int64_t blocks = std::min<int64_t>((warps_needed * 32 + threads - 1) / threads, 152 * 64);
         k_near_react<<<(int)blocks, threads>>>(g->m, g->quad, d_tasks, (int)tasks.size(), work, d_bt,
                                                g->d_nb_src, g->d_nb_off, g->d_comp, d_compH, g->d_box_begin,
-                                               g->d_box_end, g->d_x, g->d_y, g->d_w, g->d_nb_val);
+                                               g->d_box_end, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
+                                               g->d_nb_val);
         cuda_check(cudaGetLastError(), "k_near_react");
     }
     cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "near_build");

@@ -4,8 +4,10 @@
 // localmatix is assembled on the points J of B and of its neighbour leaves
 // (the leaf's free-space near list), with the free-space entries
 // |Gamma_j| G^f(c_j, c_i) off the diagonal and the self terms I^s on it (the
-// reaction part is left out, as in the paper's K~).  Only the rows of
-// P_B^{-1} that belong to B's own points are kept (restriction Q_B), so
+// reaction part is left out, as in the paper's K~); in the combined-field form
+// the same entries of that operator (devmath.cuh: free_kernel, self_entry).
+// Only the rows of P_B^{-1} that belong to B's own points are kept
+// (restriction Q_B), so
 //   P^{-1} v = sum_B S_B Q_B P_B^{-1} R_B v
 // is one gather, one small dense product and one scatter per leaf.  The rows
 // are obtained from an LU factorisation with partial pivoting of P_B^T.
@@ -19,15 +21,14 @@
 
 namespace lfmm {
 
-static const double EG = 0.57721566490153286060651209008240243;
-
 // one CTA per leaf: assemble A = P_B^T, factor, solve A X = E_own, store W (column-major: W[b * s + i])
 __global__ void __launch_bounds__(256) k_pc_setup(MediumDev m, const int* __restrict__ pc_ptr,
                                                   const int* __restrict__ pc_idx, const int* __restrict__ own_pos,
                                                   const int* __restrict__ own_cnt, const int64_t* __restrict__ aoff,
                                                   const int64_t* __restrict__ woff, const int* __restrict__ layer_of_leaf,
                                                   const double* __restrict__ px, const double* __restrict__ py,
-                                                  const double* __restrict__ pw, cd* __restrict__ Ascr,
+                                                  const double* __restrict__ pw, const double* __restrict__ nx,
+                                                  const double* __restrict__ ny, cd* __restrict__ Ascr,
                                                   int* __restrict__ pivscr, cd* __restrict__ W) {
     const int B = blockIdx.x;
     const int jb = pc_ptr[B], q = pc_ptr[B + 1] - jb;
@@ -41,15 +42,9 @@ __global__ void __launch_bounds__(256) k_pc_setup(MediumDev m, const int* __rest
     for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
         int a = e / q, b = e % q;
         int i = pc_idx[jb + b], j = pc_idx[jb + a];   // P[i=b][j=a]
-        cd v;
-        if (a == b) {
-            double wl = pw[i];
-            v = mk(-(EG + log(k * wl / 4.0) - 1.0) / (2.0 * M_PI) * wl, 0.25 * wl);
-        } else {
-            double z = k * hypot(px[i] - px[j], py[i] - py[j]);
-            v = mk(-0.25 * y0(z) * pw[j], 0.25 * j0(z) * pw[j]);
-        }
-        A[e] = v;
+        const bool cf = nx != nullptr;
+        A[e] = (a == b) ? self_entry(k, pw[i], cf)
+                        : pw[j] * free_kernel(k, px[j] - px[i], py[j] - py[i], cf, cf ? nx[j] : 0.0, cf ? ny[j] : 0.0);
     }
     __syncthreads();
     // LU with partial pivoting
@@ -203,7 +198,7 @@ void precond_build(lfmm_geometry_s* g) {
     cuda_check(cudaMallocAsync((void**)&piv, sizeof(int) * std::max<size_t>(idx.size(), 1), cudaStreamPerThread),
                "malloc pc piv");
     k_pc_setup<<<nleaf, 256>>>(g->m, g->d_pc_ptr, g->d_pc_idx, d_own_pos, d_own_cnt, d_aoff, g->d_pc_woff, d_lay,
-                               g->d_x, g->d_y, g->d_w, Ascr, piv, g->d_pc_W);
+                               g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny, Ascr, piv, g->d_pc_W);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
     dev_release(Ascr);

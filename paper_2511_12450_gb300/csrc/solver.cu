@@ -489,9 +489,11 @@ void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_ho
 }
 
 // ------------------------------------------------------------------ scattered field (eq. integralrep)
-// one warp per (target, source) pair; u[target] += |Gamma_e| Phi_e G(c_e, r) / eta
+// one warp per (target, source) pair; u[target] += |Gamma_e| Phi_e G(c_e, r) / eta, or in
+// the combined-field form |Gamma_e| Phi_e [n_e . grad_{c_e} - i k] G(c_e, r) / eta
 __global__ void k_field(MediumDev m, QuadRule q, const double* __restrict__ px, const double* __restrict__ py,
-                        const double* __restrict__ pw, const int* __restrict__ layer, const int* __restrict__ comp,
+                        const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
+                        const int* __restrict__ layer, const int* __restrict__ comp,
                         const double* __restrict__ compH, int ncomp, const cd* __restrict__ phi, int64_t n,
                         int nrhs, const double* __restrict__ tgt, int64_t mt, cd* __restrict__ u) {
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -509,13 +511,17 @@ __global__ void k_field(MediumDev m, QuadRule q, const double* __restrict__ px, 
             if (cls != ls || clt != lt) continue;
             const double hs = (a == 0) ? (py[e] - m.yint[ls]) : (m.yint[ls - 1] - py[e]);
             const double ht = (b == 0) ? (m.yint[lt - 1] - yt) : (yt - m.yint[lt]);
-            G += react_kernel_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht);
+            if (nx) {
+                cd gk[3];
+                react_kernel_grad_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht, gk);
+                G += react_cf_combine(gk, a, m.k[ls], nx[e], ny[e]);
+            } else {
+                G += react_kernel_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht);
+            }
         }
         if (lane == 0) {
-            if (ls == lt) {
-                double z = m.k[ls] * hypot(px[e] - xt, py[e] - yt);
-                G += mk(-0.25 * y0(z), 0.25 * j0(z));
-            }
+            if (ls == lt)
+                G += free_kernel(m.k[ls], px[e] - xt, py[e] - yt, nx != nullptr, nx ? nx[e] : 0.0, nx ? ny[e] : 0.0);
             double sc = pw[e] / m.eta[lt];
             for (int col = 0; col < nrhs; ++col) {
                 cd v = (sc * G) * phi[(int64_t)col * n + e];
@@ -538,7 +544,8 @@ void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64
     cuda_check(cudaMemsetAsync(u, 0, sizeof(cd) * mt * nrhs, s), "memset u");
     int64_t work = mt * g->n;
     int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
-    k_field<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g->m, g->quad, g->d_x, g->d_y, g->d_w, g->d_layer,
+    k_field<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g->m, g->quad, g->d_x, g->d_y, g->d_w, g->d_nx,
+                                                             g->d_ny, g->d_layer,
                                                              g->d_comp, d_compH, (int)compH.size(), phi_sorted, g->n,
                                                              nrhs, d_targets, mt, u);
     cuda_check(cudaGetLastError(), "k_field");

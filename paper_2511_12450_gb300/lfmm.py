@@ -31,6 +31,7 @@ LFMM_DEVICE_PTRS = 1
 LFMM_MIXED = 2
 LFMM_PROFILE_STAGES = 1
 LFMM_AUTOTUNE = 2
+LFMM_COMBINED_FIELD = 4
 STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
 EXPORTED = [
@@ -186,11 +187,16 @@ def medium_create(interfaces, k, eta) -> Medium:
 
 
 def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, leaf_size: int = 64,
-                   profile: bool = False, autotune: bool = False) -> Geometry:
+                   profile: bool = False, autotune: bool = False, combined: bool = False) -> Geometry:
+    """Tree, tables, near field and preconditioner for the elements (points, weights).
+
+    combined=True builds the combined-field operator 1/2 I + D - i k S (second kind;
+    needs the outward unit normals) instead of the paper's single layer."""
     pts = _f64(points).reshape(-1, 2)
     w = _f64(weights).reshape(-1)
     nrm = _f64(normals).reshape(-1, 2) if normals is not None else None
-    flags = (LFMM_PROFILE_STAGES if profile else 0) | (LFMM_AUTOTUNE if autotune else 0)
+    flags = ((LFMM_PROFILE_STAGES if profile else 0) | (LFMM_AUTOTUNE if autotune else 0)
+             | (LFMM_COMBINED_FIELD if combined else 0))
     prm = Params(int(p), int(leaf_size), flags, 0)
     h = ctypes.c_void_p()
     _check(library().lfmm_geometry_build(medium.handle, pts.shape[0], _dp(pts), _dp(w),
