@@ -44,6 +44,40 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC_BYTES = {"k_m2l": 84.689664e6 + 4.259328e6, "k_near_apply": 67.088128e6 + 0.403968e6}
 
 
+def run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n):
+    """The combined-field operator (opt-in second-kind form) on the same workload:
+    matvec throughput timed like the headline, and the GMRES solve."""
+    import torch
+
+    t0 = time.perf_counter()
+    Gc = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size, combined=True)
+    setup_s = time.perf_counter() - t0
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        lfmm.matvec(Gc, x, y)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lfmm.matvec(Gc, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    value, slowest = whole_job_throughput(float(np.sum(times)) * 1e-3, n * args.steps, dist, "cuda")
+    b = lfmm.rhs_plane_wave(Gc, [math.radians(float(wl.angles_deg[0]))], device=True)
+    _, info = lfmm.gmres_solve(Gc, b, tol=1e-8, max_iter=1000, precond=True)
+    _, im = lfmm.gmres_solve(Gc, b, tol=1e-8, max_iter=1000, precond=True, precision=1)
+    return {"metric": "FMM matvec Mpts/s, combined-field operator", "value": value,
+            "ms_per_step": slowest * 1e3 / args.steps, "setup_seconds": setup_s,
+            "solve": {"seconds": info["solve_seconds"], "iterations": info["iterations"],
+                      "true_rel_residual": info["true_rel_residual"], "converged": bool(info["converged"])},
+            "solve_mixed": {"seconds": im["solve_seconds"], "iterations": im["iterations"],
+                            "true_rel_residual": im["true_rel_residual"], "converged": bool(im["converged"])}}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,29 +232,29 @@ def cpu_baseline(wl, rows_per_sample, n_samples=1):
 def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
     """Serving form on a bounded stand-in for the request stream (random 2-4 layer stacks,
     k in [2, 12], N in [2k, 32k]): Poisson arrivals at 1.5x the FP64 one-at-a-time capacity.
-    Three arms see the same arrivals: FP64 one at a time (1 slot), FP64 served (``slots``
-    concurrent requests) and the served mixed-precision form; each solve to the FP64
-    residual 1e-8."""
+    The arms see the same arrivals: FP64 one at a time (1 slot), FP64 served (``slots``
+    concurrent requests), the served mixed-precision form and the served combined-field
+    operator (second kind, opt-in); each solve to the FP64 residual 1e-8."""
     from workloads import config_c5_stream
 
     stream = config_c5_stream(n_requests, seed)
     reqs = []
     for wl in stream:
-        pts, w, _ = lfmm.polygon_elements(wl.bodies)
-        reqs.append((wl.medium, pts, w, math.radians(float(wl.angles_deg[0]))))
+        pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+        reqs.append((wl.medium, pts, w, nrm, math.radians(float(wl.angles_deg[0]))))
     free, _total = __import__("torch").cuda.mem_get_info()
     budget = int(0.5 * free)
 
-    def one_arm(n_slots, precision, arrivals):
+    def one_arm(n_slots, precision, arrivals, combined=False):
         srv = lfmm.Server(slots=n_slots, hbm_budget=budget)
         t0 = time.perf_counter()
         tickets = []
-        for (med, pts, w, ang), ta in zip(reqs, arrivals):
+        for (med, pts, w, nrm, ang), ta in zip(reqs, arrivals):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
             tickets.append(srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, tol=1e-8,
-                                      precision=precision, max_iter=1000))
+                                      precision=precision, max_iter=1000, normals=nrm, combined=combined))
         lat, conv, res, its = [], 0, 0.0, 0
         for t in tickets:
             _x, info, tm = srv.wait(t)
@@ -244,11 +278,12 @@ def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
     rng = np.random.default_rng(seed + 1)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     out = {}
-    for name, n_slots, prec in (("fp64_one_at_a_time", 1, 0), ("fp64_served", slots, 0),
-                                ("mixed_served", slots, 1)):
-        cap = cap64 if name == "fp64_one_at_a_time" else one_arm(n_slots, prec, [0.0] * len(reqs))
-        lat = one_arm(n_slots, prec, arrivals)
+    for name, n_slots, prec, cf in (("fp64_one_at_a_time", 1, 0, False), ("fp64_served", slots, 0, False),
+                                    ("mixed_served", slots, 1, False), ("combined_field_served", slots, 0, True)):
+        cap = cap64 if name == "fp64_one_at_a_time" else one_arm(n_slots, prec, [0.0] * len(reqs), cf)
+        lat = one_arm(n_slots, prec, arrivals, cf)
         out[name] = {"slots": n_slots, "precision": "mixed" if prec else "fp64",
+                     "operator": "combined field" if cf else "single layer",
                      "capacity_solves_per_s": cap["solves_per_s"],
                      "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
                      "stream_solves_per_s": lat["solves_per_s"],
@@ -530,6 +565,10 @@ def run_ours(args):
                           "converged": bool(im["converged"]), "op_rel_diff_on_b": im["op_rel_diff"],
                           "rel_diff_to_fp64_solution": float(torch.linalg.norm(xm - xs) / torch.linalg.norm(xs))}
 
+    combined = None
+    if not args.no_solve:
+        combined = run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n)
+
     batch = None
     if rank == 0 and not args.no_batch and args.workload == "c2":
         batch = run_batch(lfmm)
@@ -559,6 +598,7 @@ def run_ours(args):
             "work": work,
             "solve": solve,
             "mixed": mixed,
+            "combined_field": combined,
             "batch": batch,
             "serve": serve,
             "setup_seconds": setup_s,

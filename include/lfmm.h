@@ -269,6 +269,9 @@ typedef struct {
     int32_t leaf_size;           /* <= 0: 64 */
     int32_t max_iter;
     int32_t precond;             /* 1: DD preconditioner */
+    const double *normals;       /* 2n outward unit normals, host; needed with LFMM_COMBINED_FIELD */
+    int32_t flags;               /* 0 or LFMM_COMBINED_FIELD (the geometry's operator) */
+    int32_t reserved;
 } lfmm_request;                  /* every array is copied by lfmm_server_submit */
 typedef struct {
     double queue_seconds;        /* submit -> admitted */

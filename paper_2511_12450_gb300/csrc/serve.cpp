@@ -1,10 +1,11 @@
 // serve.cpp -- a request loop for scattering solves (lfmm_server_* in include/lfmm.h).
 //
 // Requests (a layer stack, scatterer elements, an incidence angle, a tolerance,
-// the precision) queue in arrival order.  `slots` worker threads each drive one
-// CUDA stream; a worker takes the request at the head of the queue as soon as
-// the estimated device footprints of the requests on the GPU plus this one fit
-// the HBM budget, and runs it end to end on its stream: medium, geometry (tree,
+// the precision, the operator: single layer or combined field) queue in arrival
+// order.  `slots` worker threads each drive one CUDA stream; a worker takes the
+// request at the head of the queue as soon as the estimated device footprints of
+// the requests on the GPU plus this one fit the HBM budget, and runs it end to
+// end on its stream: medium, geometry (tree,
 // tables, near field, preconditioner), right-hand side, GMRES, copy of the
 // solution to host memory, release.  Requests that arrive while others run are
 // admitted as slots and memory free up, and their kernels overlap on the device
@@ -37,7 +38,8 @@ struct Request {
     int32_t n_layers = 0;
     std::vector<double> yint, k, eta;
     int64_t n = 0;
-    std::vector<double> pts, w;
+    std::vector<double> pts, w, nrm;   // nrm: combined field only
+    int32_t flags = 0;
     double angle = 0.0, tol = 1e-8;
     int32_t precision = 0, p = 20, leaf = 64, max_iter = 1000, precond = 1;
     int64_t footprint = 0;
@@ -89,8 +91,9 @@ void run_request(Request& r, cudaStream_t s) {
     do {
         lfmm_status st = lfmm_medium_create(r.n_layers, r.yint.data(), r.k.data(), r.eta.data(), &med);
         if (st < 0) { fail(st); break; }
-        lfmm_params prm{r.p, r.leaf, 0, 0};
-        st = lfmm_geometry_build(med, r.n, r.pts.data(), r.w.data(), nullptr, &prm, &geo);
+        lfmm_params prm{r.p, r.leaf, r.flags, 0};
+        st = lfmm_geometry_build(med, r.n, r.pts.data(), r.w.data(), r.nrm.empty() ? nullptr : r.nrm.data(), &prm,
+                                 &geo);
         if (st < 0) { fail(st); break; }
         r.setup_s = now_s() - t0;
         if (cudaMallocAsync(&db, 16 * (size_t)r.n, s) != cudaSuccess ||
@@ -173,7 +176,8 @@ extern "C" lfmm_status lfmm_server_submit(lfmm_server S, const lfmm_request* q, 
     if (!S || !q || !ticket) return LFMM_ERR_INVALID_ARG;
     if (q->n_layers < 1 || q->n < 1 || !q->points || !q->weights || !q->wavenumber || !q->density ||
         (q->n_layers > 1 && !q->interface_y) || !(q->tol > 0.0) || q->max_iter < 1 ||
-        (q->precision != 0 && q->precision != 1))
+        (q->precision != 0 && q->precision != 1) || (q->flags & ~LFMM_COMBINED_FIELD) != 0 ||
+        ((q->flags & LFMM_COMBINED_FIELD) && !q->normals))
         return LFMM_ERR_INVALID_ARG;
     auto r = std::make_shared<Request>();
     r->n_layers = q->n_layers;
@@ -183,6 +187,8 @@ extern "C" lfmm_status lfmm_server_submit(lfmm_server S, const lfmm_request* q, 
     r->n = q->n;
     r->pts.assign(q->points, q->points + 2 * q->n);
     r->w.assign(q->weights, q->weights + q->n);
+    r->flags = q->flags;
+    if (q->flags & LFMM_COMBINED_FIELD) r->nrm.assign(q->normals, q->normals + 2 * q->n);
     r->angle = q->angle_rad;
     r->tol = q->tol;
     r->precision = q->precision;

@@ -76,7 +76,8 @@ class Request(ctypes.Structure):
                 ("interface_y", ctypes.c_void_p), ("wavenumber", ctypes.c_void_p), ("density", ctypes.c_void_p),
                 ("n", ctypes.c_int64), ("points", ctypes.c_void_p), ("weights", ctypes.c_void_p),
                 ("angle_rad", ctypes.c_double), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("leaf_size", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("leaf_size", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("normals", ctypes.c_void_p), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RequestTimes(ctypes.Structure):
@@ -343,7 +344,9 @@ class Server:
 
     def submit(self, interfaces, k, eta, points, weights, angle_rad: float, tol: float = 1e-8,
                precision: int = 0, p: int = 20, leaf_size: int = 64, max_iter: int = 1000,
-               precond: bool = True) -> int:
+               precond: bool = True, normals=None, combined: bool = False) -> int:
+        """Queue a scattering solve; combined=True solves with the combined-field
+        operator (needs the outward unit normals)."""
         yint = _f64(interfaces).reshape(-1)
         kc = np.ascontiguousarray(np.asarray(k).astype(np.complex128).reshape(-1))
         et = _f64(eta).reshape(-1)
@@ -353,6 +356,10 @@ class Server:
                       ctypes.c_void_p(kc.ctypes.data), ctypes.c_void_p(et.ctypes.data), int(w.size),
                       ctypes.c_void_p(pts.ctypes.data), ctypes.c_void_p(w.ctypes.data), float(angle_rad),
                       float(tol), int(precision), int(leaf_size), int(max_iter), 1 if precond else 0)
+        nrm = _f64(normals).reshape(-1, 2) if normals is not None else None
+        if nrm is not None:
+            req.normals = ctypes.c_void_p(nrm.ctypes.data)
+        req.flags = LFMM_COMBINED_FIELD if combined else 0
         t = ctypes.c_int64(0)
         _check(library().lfmm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
         self._keep[t.value] = w.size

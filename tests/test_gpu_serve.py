@@ -83,3 +83,25 @@ def test_server_matches_direct_solve_and_admits_by_footprint(gpu_lib):
     srv.close()
     for x in xs:
         assert np.array_equal(x, xd)
+
+
+def test_combined_field_request_matches_direct_solve(gpu_lib):
+    lf = gpu_lib
+    wl = layered_small()
+    med = wl.medium
+    pts, w, nrm = lf.polygon_elements(wl.bodies)
+    ang = math.radians(float(wl.angles_deg[0]))
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, nrm, p=20, leaf_size=64, combined=True)
+    b = lf.rhs_plane_wave(G, [ang])
+    xd, infod = lf.gmres_solve(G, b, tol=1e-8, max_iter=600)
+    srv = lf.Server(slots=2, hbm_budget=64 << 30)
+    with pytest.raises(lf.LfmmError):   # the combined field needs the normals
+        srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, combined=True)
+    t1 = srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, max_iter=600, normals=nrm, combined=True)
+    t2 = srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, max_iter=600)
+    x1, i1, _ = srv.wait(t1)
+    x2, i2, _ = srv.wait(t2)
+    srv.close()
+    assert np.array_equal(x1, xd) and i1["iterations"] == infod["iterations"]
+    assert i1["converged"] and i2["converged"] and i1["iterations"] < i2["iterations"]
