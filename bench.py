@@ -343,10 +343,19 @@ def run_batch(lfmm, index=10, steps=5):
     t_single = timed(singles)
     same = max(float(torch.linalg.norm(Y[c] - outs[c]) / torch.linalg.norm(outs[c])) for c in range(len(cols)))
     nr = B.shape[0]
+    # precision form of the block: M2L of the FP32 levels on the tensor cores (3xTF32)
+    # against the same operator with its M2L on the SIMT kernel
+    Ym, Ys = torch.empty_like(B), torch.empty_like(B)
+    t_mixed_tc = timed(lambda: lfmm.matvec(G, B, Ym, mixed=True))
+    t_mixed_simt = timed(lambda: lfmm.matvec(G, B, Ys, mixed=True, simt_m2l=True))
+    rel = lambda a, b: max(float(torch.linalg.norm(a[c] - b[c]) / torch.linalg.norm(b[c])) for c in range(nr))
     return {"metric": "block right-hand side matvec, Mpts*rhs/s", "workload": f"C4 geometry {index}: {len(med.k)} layers, "
             f"N={n}, {nr} incidence angles", "block_value": n * nr / t_block / 1e6,
             "single_column_value": n * nr / t_single / 1e6, "block_ms": t_block * 1e3,
-            "single_columns_ms": t_single * 1e3, "max_rel_diff_block_vs_single": same}
+            "single_columns_ms": t_single * 1e3, "max_rel_diff_block_vs_single": same,
+            "mixed_block_tensor_core_value": n * nr / t_mixed_tc / 1e6, "mixed_block_tensor_core_ms": t_mixed_tc * 1e3,
+            "mixed_block_simt_value": n * nr / t_mixed_simt / 1e6, "mixed_block_simt_ms": t_mixed_simt * 1e3,
+            "mixed_tensor_core_vs_fp64_max_rel_diff": rel(Ym, Y), "mixed_tensor_core_vs_simt_max_rel_diff": rel(Ym, Ys)}
 
 
 # the paper's Tables 5.1-5.3 (Sec. 5): elements, GMRES iterations without / with the DD

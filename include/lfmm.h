@@ -60,7 +60,11 @@ enum {
                                is the base p; the coarser wide-band levels, the stored near
                                field and every sum into y stay FP64.  Its relative
                                difference from the FP64 operator is a few 1e-7 (no
-                               counterpart in the paper, which works in FP64 throughout) */
+                               counterpart in the paper, which works in FP64 throughout).
+                               With 16 or more columns its M2L runs on the tensor cores
+                               (3xTF32, tcgen05) */,
+    LFMM_SIMT_M2L = 8       /* with LFMM_MIXED: keep the FP32 M2L on the SIMT kernel for
+                               any number of columns (same operator to FP32 rounding) */
 };
 
 /* lfmm_params.flags */

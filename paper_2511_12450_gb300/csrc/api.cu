@@ -370,7 +370,9 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
         prof_begin(g, ST_GATHER, s);
         gather_sorted(g, xin, g->d_xs, nrhs, s);
         prof_end(g, ST_GATHER, s);
+        g->m2l_simt = (flags & LFMM_SIMT_M2L) != 0;
         apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s, (flags & LFMM_MIXED) != 0);
+        g->m2l_simt = false;
         prof_begin(g, ST_SCATTER, s);
         scatter_sorted(g, g->d_ys, yout, nrhs, s);
         prof_end(g, ST_SCATTER, s);

@@ -141,6 +141,7 @@ struct lfmm_geometry_s {
     // sorted-order point data
     double *d_x = nullptr, *d_y = nullptr, *d_w = nullptr;
     bool combined = false;                   // combined-field operator (LFMM_COMBINED_FIELD)
+    bool m2l_simt = false;                   // this call: FP32 M2L on the SIMT kernel only (LFMM_SIMT_M2L)
     double *d_nx = nullptr, *d_ny = nullptr; // outward unit normals (sorted order), combined field only
     int *d_layer = nullptr, *d_perm = nullptr;
     // boxes

@@ -68,6 +68,14 @@ struct MixedState {
     int* d_xd_layer = nullptr;          // layer per XDst
     size_t smem_p2m = 0, smem_l2p = 0;
     size_t bytes = 0;
+    // block right-hand-side M2L on the tensor cores (m2l_tc.cuh)
+    int* tc_boxes = nullptr;            // boxes of the FP32 levels, one CTA each
+    int n_tc_boxes = 0;
+    int* tc_ent_ptr = nullptr;          // list-entry range per box
+    int tc_p = 0;                       // expansion order of the FP32 levels
+    int* tc_err = nullptr;              // set when an mbarrier wait of k_m2l32_tc gave up
+    int* tc_err_host = nullptr;         // pinned copy, read at the next call
+    size_t tc_smem_set = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -272,6 +280,8 @@ __global__ void __launch_bounds__(64) k_m2l32_reduce(const M2LReduce* __restrict
         else Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
     }
 }
+
+#include "m2l_tc.cuh"
 
 // ---------------------------------------------------------------------------
 // Scaled Bessel values in FP32: out[n] = J_n(x) / s^n, n = 0..p, from the power
@@ -528,6 +538,8 @@ void mixed_destroy(lfmm_geometry_s* g) {
     dev_release(ms->ispow); dev_release(ms->ispow_slot); dev_release(ms->ftab); dev_release(ms->ftab_off);
     dev_release(ms->rtab); dev_release(ms->d_scale); dev_release(ms->wtab); dev_release(ms->wtab_off);
     dev_release(ms->d_xd_layer);
+    dev_release(ms->tc_boxes); dev_release(ms->tc_ent_ptr); dev_release(ms->tc_err);
+    if (ms->tc_err_host) cudaFreeHost(ms->tc_err_host);
     delete ms;
     g->mixed = nullptr;
 }
@@ -612,6 +624,18 @@ static void mixed_build(lfmm_geometry_s* g) {
     // passes (children at levels > lm)
     ms->lm = std::max(l0, std::min(mixed_level(g), D + 1));
     ms->d_scale = upload_raw(ms->scale, ms->bytes);
+    {   // the tensor-core M2L's boxes: every box of the FP32 levels (all at the base order)
+        std::vector<int> tb;
+        for (int b = (ms->lm <= D ? t.level_start[ms->lm] : t.nbox); b < t.nbox; ++b) tb.push_back(b);
+        ms->n_tc_boxes = (int)tb.size();
+        ms->tc_boxes = upload_raw(tb, ms->bytes);
+        ms->tc_ent_ptr = upload_raw(g->m2l_ent_ptr_host, ms->bytes);
+        ms->tc_p = ms->lm <= D ? t.p_level[ms->lm] : 0;
+        const std::vector<int> zero(1, 0);
+        ms->tc_err = upload_raw(zero, ms->bytes);
+        cuda_check(cudaMallocHost((void**)&ms->tc_err_host, sizeof(int)), "cudaMallocHost");
+        *ms->tc_err_host = 0;
+    }
     ms->d_xd_layer = upload_raw(g->xd_layer_host, ms->bytes);
     std::vector<int64_t> woff(std::max<size_t>(g->xsrc_host.size(), 1), -1);
     int64_t wtot = 0;
@@ -801,9 +825,43 @@ void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s) {
 }
 
 // M2L of the precision form on the levels >= min_level (their multipoles are FP32 already).
+// The tensor-core path: many columns (TC_MIN_COLS or more), every FP32 level at
+// an order whose real-form rows 2(2p+1) fit one 128-row MMA.
+#define TC_MIN_COLS 16
+static bool m2l_tc(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const int nco = 2 * ms->tc_p + 1;
+    if (nrhs < TC_MIN_COLS || g->m2l_simt || ms->n_tc_boxes == 0 || 2 * nco > 128 || min_level != ms->lm)
+        return false;
+    if (*ms->tc_err_host != 0) throw CudaError{"tensor-core M2L: an mbarrier wait gave up"};
+    const int kp = (2 * nco + 7) / 8 * 8;
+    for (int c0 = 0; c0 < nrhs; c0 += TC_MAXN) {
+        const int nc = std::min(TC_MAXN, nrhs - c0);
+        const int np = nc <= 16 ? 16 : 32;
+        const size_t smem = (size_t)(2 * 128 + 2 * np) * kp * sizeof(float);
+        if (smem > ms->tc_smem_set) {   // one attribute per instantiation
+            cuda_check(cudaFuncSetAttribute(k_m2l32_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "m2l tc smem");
+            cuda_check(cudaFuncSetAttribute(k_m2l32_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "m2l tc smem");
+            ms->tc_smem_set = smem;
+        }
+        auto kern = np == 16 ? k_m2l32_tc<16> : k_m2l32_tc<32>;
+        kern<<<ms->n_tc_boxes, 128, smem, s>>>(ms->tc_boxes, ms->tc_ent_ptr, g->d_m2l_ents, g->d_box_level,
+                                               g->d_p_level, g->d_coef_off, g->d_slot_of, g->d_slot_coef, ms->ftab,
+                                               ms->ftab_off, ms->rtab, c0, nc, kp, g->ncoef, g->nslotcoef, ms->M,
+                                               ms->Mp, ms->L, ms->Lp, ms->tc_err);
+        cuda_check(cudaGetLastError(), "k_m2l32_tc");
+        ++g->n_launches;
+    }
+    cuda_check(cudaMemcpyAsync(ms->tc_err_host, ms->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s), "tc status");
+    return true;
+}
+
 void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
     MixedState* ms = g->mixed;
     const TreeHost& t = g->tree;
+    if (m2l_tc(g, nrhs, min_level, s)) return;
     const int i0 = g->m2l_item_level_start[min_level];
     const int ni = g->n_m2l_items - i0;
     const int r0 = g->m2l_red_level_start[min_level];

@@ -32,6 +32,7 @@ LFMM_MIXED = 2
 LFMM_PROFILE_STAGES = 1
 LFMM_AUTOTUNE = 2
 LFMM_COMBINED_FIELD = 4
+LFMM_SIMT_M2L = 8
 STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
 EXPORTED = [
@@ -246,8 +247,9 @@ def rhs_plane_wave(g: Geometry, angles_rad, out=None, stream=None, device=False)
     return out
 
 
-def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False):
-    """y = K x.  mixed=True applies the precision form (FP32 multipole-to-local translations)."""
+def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False, simt_m2l: bool = False):
+    """y = K x.  mixed=True applies the precision form (FP32 far field; its M2L on the
+    tensor cores for 16 or more columns unless simt_m2l=True)."""
     xp, nrhs, flags, keep = _vec_args(x, g.n)
     if y is None:
         y = _empty_like(x, g.n, nrhs)
@@ -255,7 +257,8 @@ def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False):
     if flags != flags_y:
         raise ValueError("x and y must both be host arrays or both device tensors")
     st = _stream_of(stream) if flags else ctypes.c_void_p(0)
-    _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags | (LFMM_MIXED if mixed else 0), st))
+    flags |= (LFMM_MIXED if mixed else 0) | (LFMM_SIMT_M2L if simt_m2l else 0)
+    _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
     return y
 
 

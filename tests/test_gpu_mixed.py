@@ -96,3 +96,34 @@ def test_mixed_gmres_refinement_c2(c2):
     assert i0["converged"] and i1["converged"]
     assert i1["true_rel_residual"] <= 1e-8
     assert relerr(x1, x0) <= 1e-5
+
+
+@pytest.mark.parametrize("ncols", [32, 70])
+def test_block_m2l_on_tensor_cores_c2(c2, ncols):
+    # 16 or more columns: the FP32 levels' M2L runs on tcgen05 (3xTF32); 70 columns
+    # take two launches (64 + 6, the second padded to 16)
+    lf, G = c2["lf"], c2["G"]
+    rng = np.random.default_rng(24)
+    X = np.asfortranarray(rng.standard_normal((G.n, ncols)) + 1j * rng.standard_normal((G.n, ncols)))
+    y64 = lf.matvec(G, X)
+    ytc = lf.matvec(G, X, mixed=True)
+    ysimt = lf.matvec(G, X, mixed=True, simt_m2l=True)
+    d64 = max(relerr(ytc[:, c], y64[:, c]) for c in range(ncols))
+    dsimt = max(relerr(ytc[:, c], ysimt[:, c]) for c in range(ncols))
+    print(f"C2 {ncols} columns: tensor-core mixed vs FP64 {d64:.3e}, vs SIMT mixed {dsimt:.3e}")
+    assert d64 <= OP_TOL
+    assert dsimt <= 5e-7
+    assert np.array_equal(lf.matvec(G, X, mixed=True), ytc)
+
+
+def test_block_m2l_on_tensor_cores_wide_band(wide):
+    # straddling cells (reaction centres), mirrored tables and both departure/arrival flips
+    lf, G, K = wide["lf"], wide["G"], wide["K"]
+    rng = np.random.default_rng(25)
+    X = np.asfortranarray(rng.standard_normal((G.n, 20)) + 1j * rng.standard_normal((G.n, 20)))
+    ytc = lf.matvec(G, X, mixed=True)
+    ysimt = lf.matvec(G, X, mixed=True, simt_m2l=True)
+    ref = K @ X
+    for c in range(20):
+        assert relerr(ytc[:, c], ref[:, c]) <= OP_TOL + 1e-8
+        assert relerr(ytc[:, c], ysimt[:, c]) <= 5e-7
