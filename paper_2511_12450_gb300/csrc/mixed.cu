@@ -684,16 +684,17 @@ static void mixed_build(lfmm_geometry_s* g) {
     cuda_check(e2, "precision form tables");
 }
 
-// First level whose M2L runs in FP32: the levels where the expansion order is
-// the base order p, i.e. the wide-band rule did not raise it.  On coarser
-// levels (boxes many wavelengths wide, orders up to 2-3 times p) the local
-// coefficients of orders well above k rho reach 1e8 and more relative to the
-// field, FP32 carries them to about 1e-4, and the local-to-local translations
-// pass those absolute errors down the tree; there the FP64 kernel stays.
+// First level whose far field runs in FP32: the levels whose expansion order is
+// at most 1.5 p, i.e. the wide-band rule raised it little.  On coarser levels
+// (boxes many wavelengths wide, orders 2-3 times p) the local coefficients of
+// orders well above k rho reach 1e8 and more relative to the field, FP32
+// carries them to about 1e-4, and the local-to-local translations pass those
+// absolute errors down the tree; there the FP64 kernels stay.  (C2: orders 25
+// and 20 run in FP32, 37 and 57 in FP64; operator difference 2.9e-7.)
 int mixed_level(lfmm_geometry_s* g) {
     const TreeHost& t = g->tree;
     for (int l = t.l0; l <= t.D; ++l)
-        if (t.p_level[l] <= g->p) return l;
+        if (2 * t.p_level[l] <= 3 * g->p) return l;
     return t.D + 1;
 }
 
