@@ -57,7 +57,7 @@ enum {
     LFMM_MIXED = 2          /* lfmm_matvec: apply the precision form of the operator --
                                the far field (P2M, M2M, M2L free space and reaction, L2L,
                                L2P) in FP32 on scaled expansions on the levels whose order
-                               is the base p; the coarser wide-band levels, the stored near
+                               is at most 1.5 p; the coarser wide-band levels, the stored near
                                field and every sum into y stay FP64.  Its relative
                                difference from the FP64 operator is a few 1e-7 (no
                                counterpart in the paper, which works in FP64 throughout).

@@ -1,5 +1,5 @@
 // mixed.cu -- the precision form of the operator: on the levels whose order is
-// the base p, the whole far field -- P2M, M2M, the multipole-to-local
+// at most 1.5 p, the whole far field -- P2M, M2M, the multipole-to-local
 // translations (free space, Graf's addition theorem, and the reaction
 // components' moment tables of eq. generalintegral), L2L and L2P -- in FP32;
 // the coarser wide-band levels, the stored near field with its singular and
@@ -72,7 +72,7 @@ struct MixedState {
     int* tc_boxes = nullptr;            // boxes of the FP32 levels, one CTA each
     int n_tc_boxes = 0;
     int* tc_ent_ptr = nullptr;          // list-entry range per box
-    int tc_p = 0;                       // expansion order of the FP32 levels
+    int tc_p = 0;                       // largest expansion order of the FP32 levels (the coarsest)
     int* tc_err = nullptr;              // set when an mbarrier wait of k_m2l32_tc gave up
     int* tc_err_host = nullptr;         // pinned copy, read at the next call
     size_t tc_smem_set = 0;
@@ -624,7 +624,7 @@ static void mixed_build(lfmm_geometry_s* g) {
     // passes (children at levels > lm)
     ms->lm = std::max(l0, std::min(mixed_level(g), D + 1));
     ms->d_scale = upload_raw(ms->scale, ms->bytes);
-    {   // the tensor-core M2L's boxes: every box of the FP32 levels (all at the base order)
+    {   // the tensor-core M2L's boxes: every box of the FP32 levels
         std::vector<int> tb;
         for (int b = (ms->lm <= D ? t.level_start[ms->lm] : t.nbox); b < t.nbox; ++b) tb.push_back(b);
         ms->n_tc_boxes = (int)tb.size();
