@@ -497,7 +497,7 @@ void fmm_build(lfmm_geometry_s* g) {
             }
             if (!work.empty()) {
                 TableWork* d_work = dupload(g, work);
-                size_t smem = (size_t)(16 * 32 * 4 + 16 * 4) * sizeof(cd);
+                size_t smem = (size_t)(16 * 32 * 4 + 4 * 256) * sizeof(cd);   // k_react_tables layout
                 k_react_tables<<<(int)work.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_work, g->d_comp,
                                                                 g->d_m2lr);
                 cuda_check(cudaGetLastError(), "k_react_tables");
@@ -505,7 +505,7 @@ void fmm_build(lfmm_geometry_s* g) {
             if (!same.empty()) {
                 int* d_same = dupload(g, same);
                 const int nd = 4 * pmax_same + 1;
-                const size_t smem = (size_t)(16 * nd + 32 + nd) * sizeof(cd);
+                const size_t smem = (size_t)(16 * nd + 3 * 256 + nd) * sizeof(cd);   // k_react_tables_same layout
                 if (smem > 48 * 1024)
                     cuda_check(cudaFuncSetAttribute(k_react_tables_same, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)smem), "same-layer tables smem");

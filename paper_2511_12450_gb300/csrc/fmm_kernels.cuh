@@ -340,42 +340,57 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
     const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
     const int p = K.pS, nco = 2 * p + 1, nd = 4 * p + 1;
     const double ka = med.k[ls];
-    const int CH = 16;
+    // nodes in batches of NB = 256 (all threads evaluate the spectral density, one
+    // node each), then in chunks of CH for the power rows and the moment sums
+    const int CH = 16, NB = 256;
     cd* Pw = sh;                 // [CH][nd]  u^d, d = -2p..2p
-    cd* Fp = Pw + CH * nd;       // [CH]
-    cd* Fm = Fp + CH;            // [CH]
-    cd* hs = Fm + CH;            // [nd] moments
+    cd* Fp = Pw + CH * nd;       // [NB]
+    cd* Fm = Fp + NB;            // [NB]
+    cd* uu = Fm + NB;            // [NB]
+    cd* hs = uu + NB;            // [nd] moments
     double h;
     const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
     const int ntot = P * 8 + 2 * q.tab_nes;
+    const int nseg = (nd + 15) / 16;   // runs of 16 consecutive powers per node
     cd acc[2] = {mk(0, 0), mk(0, 0)};   // d = threadIdx.x and threadIdx.x + 256
-    for (int j0 = 0; j0 < ntot; j0 += CH) {
-        const int cnt = min(CH, ntot - j0);
+    for (int jb = 0; jb < ntot; jb += NB) {
+        const int cntB = min(NB, ntot - jb);
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            QuadNode nd2 = table_contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
+        if (threadIdx.x < cntB) {
+            QuadNode nd2 = table_contour_node(q, jb + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd2.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd2.lam);
             cd SE = S * (eikh(kya, K.hS) * eikh(kya, K.hT));
             Fp[threadIdx.x] = SE * nd2.fp;
             Fm[threadIdx.x] = SE * nd2.fm;
-            // powers u^-2p .. u^2p
-            const cd u = w_of(kya, nd2.lam, ka);
-            cd bb = cinv(u), cur = mk(1.0, 0.0);
-            for (int k2 = 2 * p; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
-            cd* row = Pw + threadIdx.x * nd;
-            for (int d = 0; d < nd; ++d) { row[d] = cur; cur = cur * u; }
+            uu[threadIdx.x] = w_of(kya, nd2.lam, ka);
         }
-        __syncthreads();
-        for (int s2 = 0; s2 < 2; ++s2) {
-            const int di = threadIdx.x + 256 * s2;
-            if (di >= nd) break;
-            cd ac = acc[s2];
-            for (int r = 0; r < cnt; ++r) {
-                cfma(ac, Fp[r], Pw[r * nd + di]);             // u^d
-                cfma(ac, Fm[r], Pw[r * nd + (nd - 1 - di)]);   // u^-d
+        for (int j0 = 0; j0 < cntB; j0 += CH) {
+            const int cnt = min(CH, cntB - j0);
+            __syncthreads();
+            // powers u^-2p .. u^2p: one thread per run of 16, its first power by binary
+            // exponentiation, then 15 products
+            for (int e = threadIdx.x; e < cnt * nseg; e += blockDim.x) {
+                const int r = e / nseg, sg = e - r * nseg, d0 = sg * 16;
+                const cd u = uu[j0 + r];
+                const int e0 = d0 - 2 * p;
+                cd bb = (e0 >= 0) ? u : cinv(u), cur = mk(1.0, 0.0);
+                for (int k2 = e0 >= 0 ? e0 : -e0; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
+                cd* row = Pw + r * nd;
+                const int d1 = min(nd, d0 + 16);
+                for (int d = d0; d < d1; ++d) { row[d] = cur; cur = cur * u; }
             }
-            acc[s2] = ac;
+            __syncthreads();
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int di = threadIdx.x + 256 * s2;
+                if (di >= nd) break;
+                cd ac = acc[s2];
+                for (int r = 0; r < cnt; ++r) {
+                    cfma(ac, Fp[j0 + r], Pw[r * nd + di]);             // u^d
+                    cfma(ac, Fm[j0 + r], Pw[r * nd + (nd - 1 - di)]);   // u^-d
+                }
+                acc[s2] = ac;
+            }
         }
     }
     for (int s2 = 0; s2 < 2; ++s2) {
@@ -407,16 +422,17 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     const int pS = K.pS, pT = K.pT;
     const int ncS = 2 * pS + 1, ncT = 2 * pT + 1;
     const double ka = med.k[ls], kb = med.k[lt];
-    // smem layout for a chunk of CH nodes
-    const int CH = 16;
+    // nodes in batches of NB = 256 (all threads evaluate the spectral density, one
+    // node each), then in chunks of CH for the power tables and the tile update
+    const int CH = 16, NB = 256;
     cd* Up = st;                       // [CH][32]  u^n  for the tile's n
     cd* Um = Up + CH * 32;             // [CH][32]  u^-n
     cd* Vp = Um + CH * 32;             // [CH][32]  v^-m for the tile's m
     cd* Vm = Vp + CH * 32;             // [CH][32]  v^m
-    cd* Fp = Vm + CH * 32;             // [CH]
-    cd* Fm = Fp + CH;                  // [CH]
-    cd* uu = Fm + CH;                  // [CH] u
-    cd* vv = uu + CH;                  // [CH] v
+    cd* Fp = Vm + CH * 32;             // [NB]
+    cd* Fm = Fp + NB;                  // [NB]
+    cd* uu = Fm + NB;                  // [NB] u
+    cd* vv = uu + NB;                  // [NB] v
     // table rule: its own contour (table_contour_node), panels growing with the
     // orders, finer rays
     double h;
@@ -425,11 +441,11 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     const int tm = threadIdx.x >> 3;          // 0..31 row within tile
     const int tn = (threadIdx.x & 7) * 4;     // 0..28 first column within tile
     cd acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
-    for (int j0 = 0; j0 < ntot; j0 += CH) {
-        const int cnt = min(CH, ntot - j0);
+    for (int jb = 0; jb < ntot; jb += NB) {
+        const int cntB = min(NB, ntot - jb);
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            QuadNode nd = table_contour_node(q, j0 + threadIdx.x, P, h, K.X, K.D);
+        if (threadIdx.x < cntB) {
+            QuadNode nd = table_contour_node(q, jb + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
             cd E = eikh(kya, K.hS) * eikh(kyb, K.hT);
@@ -439,35 +455,38 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
             uu[threadIdx.x] = w_of(kya, nd.lam, ka);
             vv[threadIdx.x] = w_of(kyb, nd.lam, kb);
         }
-        __syncthreads();
-        // power tables of the tile: for each node four runs of 32 consecutive powers
-        // (u^n and u^-n over the tile's columns, v^-m and v^m over its rows), one
-        // thread per run: a starting power by binary exponentiation, then 31 products
-        for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
-            const int r = e >> 2, which = e & 3;
-            const cd u = uu[r], v = vv[r];
-            cd base, step;
-            int e0;
-            cd* dst;
-            if (which == 0) { base = u; step = u; e0 = wk.n0; dst = Up; }               // u^n
-            else if (which == 1) { base = u; step = cinv(u); e0 = -wk.n0; dst = Um; }   // u^-n
-            else if (which == 2) { base = v; step = cinv(v); e0 = -wk.m0; dst = Vp; }   // v^-m
-            else { base = v; step = v; e0 = wk.m0; dst = Vm; }                         // v^m
-            // start = base^e0 (e0 may be negative)
-            cd bb = (e0 >= 0) ? base : cinv(base);
-            int k2 = e0 >= 0 ? e0 : -e0;
-            cd cur = mk(1.0, 0.0);
-            while (k2 > 0) { if (k2 & 1) cur = cur * bb; bb = bb * bb; k2 >>= 1; }
-            for (int s2 = 0; s2 < 32; ++s2) { dst[r * 32 + s2] = cur; cur = cur * step; }
-        }
-        __syncthreads();
-        for (int r = 0; r < cnt; ++r) {
-            cd a1 = Fp[r] * Vp[r * 32 + tm];
-            cd a2 = Fm[r] * Vm[r * 32 + tm];
+        for (int j0 = 0; j0 < cntB; j0 += CH) {
+            const int cnt = min(CH, cntB - j0);
+            __syncthreads();
+            // power tables of the tile: for each node four runs of 32 consecutive powers
+            // (u^n and u^-n over the tile's columns, v^-m and v^m over its rows), one
+            // thread per run: a starting power by binary exponentiation, then 31 products
+            for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
+                const int r = e >> 2, which = e & 3;
+                const cd u = uu[j0 + r], v = vv[j0 + r];
+                cd base, step;
+                int e0;
+                cd* dst;
+                if (which == 0) { base = u; step = u; e0 = wk.n0; dst = Up; }               // u^n
+                else if (which == 1) { base = u; step = cinv(u); e0 = -wk.n0; dst = Um; }   // u^-n
+                else if (which == 2) { base = v; step = cinv(v); e0 = -wk.m0; dst = Vp; }   // v^-m
+                else { base = v; step = v; e0 = wk.m0; dst = Vm; }                         // v^m
+                // start = base^e0 (e0 may be negative)
+                cd bb = (e0 >= 0) ? base : cinv(base);
+                int k2 = e0 >= 0 ? e0 : -e0;
+                cd cur = mk(1.0, 0.0);
+                while (k2 > 0) { if (k2 & 1) cur = cur * bb; bb = bb * bb; k2 >>= 1; }
+                for (int s2 = 0; s2 < 32; ++s2) { dst[r * 32 + s2] = cur; cur = cur * step; }
+            }
+            __syncthreads();
+            for (int r = 0; r < cnt; ++r) {
+                cd a1 = Fp[j0 + r] * Vp[r * 32 + tm];
+                cd a2 = Fm[j0 + r] * Vm[r * 32 + tm];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                cfma(acc[t], a1, Up[r * 32 + tn + t]);
-                cfma(acc[t], a2, Um[r * 32 + tn + t]);
+                for (int t = 0; t < 4; ++t) {
+                    cfma(acc[t], a1, Up[r * 32 + tn + t]);
+                    cfma(acc[t], a2, Um[r * 32 + tn + t]);
+                }
             }
         }
     }
