@@ -29,9 +29,8 @@ struct QuadRule {
     double es_hv;
     int nes;           // nodes per ray
     int min_panels;    // minimum number of detour panels
-    // finer rule for the M2L moment tables, whose integrands carry w^n factors
-    // up to |n - m| = 2p: more detour panels per unit of oscillation and a
-    // smaller exp-sinh step
+    // rule of the M2L moment tables, whose integrands carry w^n factors up to
+    // |n - m| = 2p: more detour panels (pS + pT more) and their own rays
     double tab_es_v0, tab_es_hv;
     int tab_nes;
     int tab_panel_mult;
