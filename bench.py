@@ -41,7 +41,7 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch from the committed ncu captures (profiles/); null once the
 # kernel changes after the capture
-NCU_TRAFFIC_BYTES = {"k_m2l": 84.689664e6 + 4.259328e6, "k_near_apply": 67.088128e6 + 0.403968e6}
+NCU_TRAFFIC_BYTES = {"k_m2l": 84.714752e6 + 3.439104e6, "k_near_apply": 67.088128e6 + 0.403968e6}
 
 
 def run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n):

@@ -127,6 +127,14 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
 // sum_n I[m][n] alpha_n with the arrival and departure index flips; moment
 // tables are column-major (entry (m, n) at n (2p+1) + m).
 #define M2L_STAGE 64
+// v or -v by flipping the sign bits with integer instructions: a conditional
+// negation of a double otherwise costs an FP64 instruction, and the FP64 pipe is
+// what bounds the M2L
+__device__ __forceinline__ cd csign(cd v, int neg) {
+    const long long msk = (long long)(neg & 1) << 63;
+    return mk(__longlong_as_double(__double_as_longlong(v.x) ^ msk),
+              __longlong_as_double(__double_as_longlong(v.y) ^ msk));
+}
 __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
                       const int* __restrict__ box_level, const int* __restrict__ p_level,
                       const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
@@ -174,13 +182,9 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
                     if (E.flags & M2L_A_DOWN) {   // alpha_i = M_i
                         for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[mi * cs], src[mi]);
                     } else {                      // alpha_i = (-1)^(i-p) M_{2p-i}
-                        for (int mi = sl; mi < nco; mi += NS) {
-                            cd v = src[2 * p - mi];
-                            if ((mi - p) & 1) v = -v;
-                            cfma(bsum, col_m[mi * cs], v);
-                        }
+                        for (int mi = sl; mi < nco; mi += NS) cfma(bsum, col_m[mi * cs], csign(src[2 * p - mi], mi - p));
                     }
-                    if (!bdown && (mrow & 1)) bsum = -bsum;
+                    bsum = csign(bsum, (!bdown) & mrow);
                     const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
                     if (dst == 0) acc0 += bsum;
                     else if (dst == 1) acc1 += bsum;
