@@ -179,6 +179,12 @@ __global__ void k_from32(const cf* __restrict__ in, const double* __restrict__ i
 // lane/slice split, index flips and partial-sum reduction as the FP64 kernel,
 // with dense tables for the free-space part too.
 #define M2L_STAGE32 64
+// v or -v by flipping the sign bits with integer instructions (a conditional
+// negation otherwise takes a floating-point instruction in the inner loop)
+__device__ __forceinline__ cf csignf(cf v, int neg) {
+    const unsigned msk = (unsigned)(neg & 1) << 31;
+    return mkf(__uint_as_float(__float_as_uint(v.x) ^ msk), __uint_as_float(__float_as_uint(v.y) ^ msk));
+}
 __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
                         const int* __restrict__ box_level, const int* __restrict__ p_level,
                         const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
@@ -225,13 +231,9 @@ __global__ void __launch_bounds__(128) k_m2l32(const M2LItem* __restrict__ items
                     if (E.flags & M2L_A_DOWN) {
                         for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[mi * cs], src[mi]);
                     } else {
-                        for (int mi = sl; mi < nco; mi += NS) {
-                            cf v = src[2 * p - mi];
-                            if ((mi - p) & 1) v = mkf(-v.x, -v.y);
-                            cfmaf(bsum, col_m[mi * cs], v);
-                        }
+                        for (int mi = sl; mi < nco; mi += NS) cfmaf(bsum, col_m[mi * cs], csignf(src[2 * p - mi], mi - p));
                     }
-                    if (!bdown && (mrow & 1)) bsum = mkf(-bsum.x, -bsum.y);
+                    bsum = csignf(bsum, (!bdown) & mrow);
                     const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
                     if (dst == 0) acc0 = addf(acc0, bsum);
                     else if (dst == 1) acc1 = addf(acc1, bsum);
