@@ -135,6 +135,14 @@ static void require(bool c, const char* msg) {
 }
 
 static void free_geometry(lfmm_geometry_s* g) {
+    if (g->side) {
+        cudaStreamSynchronize(g->side);
+        cudaStreamDestroy(g->side);
+        g->side = nullptr;
+    }
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    g->ev_fork = g->ev_join = nullptr;
     if (g->prof.on)
         for (int k = 0; k < 2 * ST_COUNT; ++k) cudaEventDestroy(g->prof.ev[k]);
     g->prof.on = false;
@@ -325,6 +333,9 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
             comp[4 * c + 2] = t.comps[c].lt; comp[4 * c + 3] = t.comps[c].b;
         }
         g->d_comp = dupload(g, comp);
+        cuda_check(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
+        cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "event");
+        cuda_check(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "event");
         near_build(g);
         fmm_build(g);
         if (prm && (prm->flags & LFMM_AUTOTUNE)) fmm_autotune(g);

@@ -577,7 +577,8 @@ static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStr
     }
 }
 
-void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed) {
+void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed,
+               cudaEvent_t before_l2p) {
     set_smem_limits();
     TreeHost& t = g->tree;
     const int D = t.D, l0 = t.l0, nlev = D + 1;
@@ -662,6 +663,8 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     }
     prof_end(g, ST_L2L, s);
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
+        // (after the near field, which adds into the same y on the side stream)
+        if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");
         prof_begin(g, ST_L2P, s);
         if (lm <= D) {
             mixed_l2p(g, y_sorted, nrhs, s);

@@ -141,6 +141,8 @@ struct lfmm_geometry_s {
     double *d_x = nullptr, *d_y = nullptr, *d_w = nullptr;
     bool combined = false;                   // combined-field operator (LFMM_COMBINED_FIELD)
     bool m2l_simt = false;                   // this call: FP32 M2L on the SIMT kernel only (LFMM_SIMT_M2L)
+    cudaStream_t side = nullptr;             // near field beside the far field (apply_operator_sorted)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double *d_nx = nullptr, *d_ny = nullptr; // outward unit normals (sorted order), combined field only
     int *d_layer = nullptr, *d_perm = nullptr;
     // boxes
@@ -284,7 +286,8 @@ void near_build(lfmm_geometry_s* g);
 void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
 // FMM far field (fmm.cu)
 void fmm_build(lfmm_geometry_s* g);
-void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false);
+void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false,
+               cudaEvent_t before_l2p = nullptr);
 void fmm_autotune(lfmm_geometry_s* g);
 // precision form: M2L in FP32 on scaled expansions (mixed.cu)
 void mixed_setup(lfmm_geometry_s* g, int nrhs);                       // tables, scales, FP32 buffers

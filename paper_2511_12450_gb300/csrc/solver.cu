@@ -46,8 +46,14 @@ void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs,
 void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
                            bool mixed) {
     cuda_check(cudaMemsetAsync(y_sorted, 0, sizeof(cd) * g->n * nrhs, s), "memset y");
-    fmm_apply(g, x_sorted, y_sorted, nrhs, s, mixed);
-    near_apply(g, x_sorted, y_sorted, nrhs, s);
+    // the stored near field (bound by HBM) on the geometry's side stream, beside the far
+    // field (bound by the FP64 pipe); both add into y, the leaf evaluations after it
+    cuda_check(cudaEventRecord(g->ev_fork, s), "fork");
+    cuda_check(cudaStreamWaitEvent(g->side, g->ev_fork, 0), "fork");
+    near_apply(g, x_sorted, y_sorted, nrhs, g->side);
+    cuda_check(cudaEventRecord(g->ev_join, g->side), "join");
+    fmm_apply(g, x_sorted, y_sorted, nrhs, s, mixed, g->ev_join);
+    cuda_check(cudaStreamWaitEvent(s, g->ev_join, 0), "join");   // also when there is no far field
 }
 
 // ------------------------------------------------------------------ BLAS-2 helpers for GMRES
