@@ -22,11 +22,12 @@
 // tcgen05.commit arrives on an mbarrier, which every thread waits on (bounded).
 // Each warp then reads its 32 rows of the product with tcgen05.ld and adds them
 // to register sums for the entry's output (cell centre or one of the two
-// reaction centres), so that the tensor cores' accumulation covers one entry's
-// 3 x kp/8 MMAs only: over a box's ~40 entries that accumulation alone loses
-// about 5e-6 relative, against 2e-7 for round-to-nearest FP32 sums of the
-// per-entry products.  At the end row r < 2p+1 holds real parts, the next
-// 2p+1 rows imaginary parts.
+// reaction centres).  The tensor cores thus accumulate one entry's 3 x kp/8 MMAs
+// only: accumulating a whole box (~40 entries) in TMEM lost about 5e-6 relative,
+// their accumulation drifting faster than round-to-nearest FP32, while the
+// per-entry register sums keep about 4e-7.  At the end row r < 2p+1 holds real
+// parts, the next 2p+1 rows imaginary parts.  If a wait gives up, the box's
+// outputs are written as zeros and *err is set (the host reports it).
 #pragma once
 
 #define TC_MAXN 32          // columns per launch (N of the MMA)
