@@ -21,6 +21,15 @@ __host__ __device__ __forceinline__ cd operator*(double s, cd a) { return mk(s *
 __host__ __device__ __forceinline__ cd operator*(cd a, double s) { return mk(s * a.x, s * a.y); }
 __host__ __device__ __forceinline__ cd& operator+=(cd& a, cd b) { a.x += b.x; a.y += b.y; return a; }
 __host__ __device__ __forceinline__ cd conjc(cd a) { return mk(a.x, -a.y); }
+#ifdef __CUDACC__
+// x or -x (neg odd) and v or -v by flipping sign bits with integer instructions: a
+// conditional negation of a double otherwise costs an instruction on the FP64 pipe,
+// which bounds the expansion kernels
+__device__ __forceinline__ double dsign(double x, int neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(neg & 1) << 63));
+}
+__device__ __forceinline__ cd csign(cd v, int neg) { return mk(dsign(v.x, neg), dsign(v.y, neg)); }
+#endif
 __host__ __device__ __forceinline__ double absc(cd a) { return hypot(a.x, a.y); }
 __host__ __device__ __forceinline__ cd cdiv(cd a, cd b) {
     // scaled division (Smith's method)

@@ -84,10 +84,11 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
             if (k2 > 0) zn = zn * z;
             u[pb + k2] = Jd[k2] * zn;
         }
-        // u_{-n} = (-1)^n conj(u_n) into slots pb-1..0 (the J's are no longer needed)
+        // u_{-n} = (-1)^n conj(u_n) into slots pb-1..0 (the J's are no longer needed);
+        // the signs by integer bit flips (no FP64 instruction)
         for (int k2 = 1; k2 <= pb; ++k2) {
             const cd v = u[pb + k2];
-            u[pb - k2] = (k2 & 1) ? mk(-v.x, v.y) : mk(v.x, -v.y);
+            u[pb - k2] = mk(dsign(v.x, k2), dsign(v.y, k2 + 1));
         }
         if (cf) {   // E_n into slot n + p from u_{n-1}, u_n, u_{n+1} (slots n+p, n+p+1, n+p+2);
                     // ascending n overwrites only u_{n-1}, which later n do not read
@@ -127,14 +128,7 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
 // sum_n I[m][n] alpha_n with the arrival and departure index flips; moment
 // tables are column-major (entry (m, n) at n (2p+1) + m).
 #define M2L_STAGE 64
-// v or -v by flipping the sign bits with integer instructions: a conditional
-// negation of a double otherwise costs an FP64 instruction, and the FP64 pipe is
-// what bounds the M2L
-__device__ __forceinline__ cd csign(cd v, int neg) {
-    const long long msk = (long long)(neg & 1) << 63;
-    return mk(__longlong_as_double(__double_as_longlong(v.x) ^ msk),
-              __longlong_as_double(__double_as_longlong(v.y) ^ msk));
-}
+
 __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
                       const int* __restrict__ box_level, const int* __restrict__ p_level,
                       const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
@@ -254,8 +248,7 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
             const int er = i / np1, k2 = i - er * np1;
             const cd* Le = L + (int64_t)col * stride + ent[G.e0 + er].off;
             const cd A = Le[p + k2];
-            cd B = Le[p - k2];
-            if (k2 & 1) B = -B;
+            const cd B = csign(Le[p - k2], k2);
             if (k2 == 0) { sPQ[(er * 2) * np1] = A; sPQ[(er * 2 + 1) * np1] = mk(0, 0); }
             else { sPQ[(er * 2) * np1 + k2] = A + B; sPQ[(er * 2 + 1) * np1 + k2] = A - B; }
         }
