@@ -130,7 +130,7 @@ typedef struct {
 /*
  * Layered medium (Sec. 2.1).  n_layers = L+1 >= 1 layers, top layer first.
  *   interface_y : L interface heights y = -d_l, strictly decreasing
- *   wavenumber  : 2*(L+1) doubles, complex k_l (re, im); Re k > 0.  This build
+ *   wavenumber  : 2*(L+1) doubles, complex k_l (re, im); Re k > 0.  The library
  *                 supports real wavenumbers only (Im k must be 0).
  *   density     : L+1 values eta_l > 0 (the paper's "reflection index")
  * Errors: LFMM_ERR_INVALID_ARG for any violated condition.

@@ -5,7 +5,7 @@ solves (core.spectral_amp, background.background_coefficients).  Everything is
 in the paper's absolute coordinates (waves e^{+- i k_y y}), so it is evaluated
 only at moderate depths and moderate lambda in the tests.
 
-Readings of the printed formulas (listed in the design doc):
+Readings of the printed formulas:
   * exponents e^{-2 k_y (d_l - d_{l-1})} in the R~ and T~ recursions and in
     Case I are read as e^{2 i k_y (d_l - d_{l-1})} (as printed in Cases II/III);
   * the downward recursion starts from R~_{L,L+1} = 0 (the Remark of Sec. 3.1);

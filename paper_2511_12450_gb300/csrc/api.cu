@@ -410,7 +410,7 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         const int precision = prm ? prm->precision : 0;
         require(tol > 0.0 && maxit >= 1, "invalid GMRES parameters");
         require(precision == 0 || precision == 1, "precision must be 0 (FP64) or 1 (mixed with refinement)");
-        require(!prm || prm->restart == 0, "restarted GMRES is not available in this build (restart must be 0)");
+        require(!prm || prm->restart == 0, "restarted GMRES is not available (restart must be 0)");
         cudaStream_t s = as_stream(stream);
         if (pre && !g->pc_ready) precond_build(g);
         ensure_scratch(g, nrhs);
