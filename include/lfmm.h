@@ -206,8 +206,11 @@ lfmm_status lfmm_matvec_static(lfmm_geometry g, const void *x, void *y, void *st
 /*
  * Solve K x = b by GMRES (x0 = 0), right-preconditioned by the overlapping
  * domain-decomposition preconditioner when prm->precond is set (Sec. 4.2).
- * Returns LFMM_NOT_CONVERGED (with the best iterate in x and info filled) if
- * max_iter is reached.
+ * Several columns with the FP64 operator advance together -- one Krylov space
+ * per column, every step one block matvec of the active columns -- when their
+ * bases fit in a quarter of the free device memory; each column's result equals
+ * its separate solve.  Returns LFMM_NOT_CONVERGED (with the best iterate in x and
+ * info filled) if max_iter is reached.
  */
 lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void *b, void *x,
                              const lfmm_gmres_params *prm, lfmm_gmres_info *info,

@@ -315,6 +315,137 @@ static int gmres_one(lfmm_geometry_s* g, const cd* b, cd* x, double tol, int max
     return res <= tol ? 1 : 0;
 }
 
+// Several right-hand sides with the FP64 operator, advanced together: one Krylov
+// space per column, and every step multiplies the active columns' preconditioned
+// vectors in one block matvec (the block right-hand side of the far field, which
+// amortises the translations' loads and launches over the columns).  Each
+// column's CGS2 Arnoldi step, Givens rotations and stopping test are those of
+// gmres_one and use the same kernels, and a column of a block matvec equals its
+// single-column product, so every column's iterates equal a separate solve's.  A
+// converged column stops taking steps (its slot in the block is zero).  Returns 1
+// if every column reached tol; *last_iters is the last column's step count and
+// *worst_res the largest residual estimate.
+static int gmres_simul(lfmm_geometry_s* g, const cd* B, cd* X, int nrhs, double tol, int maxit, bool pre,
+                       cudaStream_t s, int* last_iters, double* worst_res) {
+    const int64_t n = g->n;
+    const int64_t ldv = n * (int64_t)(maxit + 1);   // column c's basis at V + c ldv
+    const int cap = maxit + 2, per = 2 * cap + 1;   // per column: two CGS passes and the norm
+    Blas bl(g, s, maxit + 1);                      // its chunk partials (its results are unused)
+    cd *V = nullptr, *Z = nullptr, *W = nullptr, *dres = nullptr, *hd = nullptr;
+    cuda_check(cudaMallocAsync((void**)&V, sizeof(cd) * ldv * nrhs, s), "malloc V");
+    cuda_check(cudaMallocAsync((void**)&Z, sizeof(cd) * n * nrhs, s), "malloc Z");
+    cuda_check(cudaMallocAsync((void**)&W, sizeof(cd) * n * nrhs, s), "malloc W");
+    cuda_check(cudaMallocAsync((void**)&dres, sizeof(cd) * per * nrhs, s), "malloc dres");
+    cuda_check(cudaMallocAsync((void**)&hd, sizeof(cd) * cap * nrhs, s), "malloc y");
+    struct Free {
+        cd *a, *b, *c, *d, *e;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); cudaFreeAsync(d, s); cudaFreeAsync(e, s); }
+    } fr{V, Z, W, dres, hd, s};
+    typedef std::complex<double> C;
+    std::vector<double> beta(nrhs), res(nrhs, 0.0);
+    std::vector<char> active(nrhs, 0);
+    std::vector<std::vector<std::vector<C>>> H(nrhs);
+    std::vector<std::vector<C>> cs(nrhs), sn(nrhs), gg(nrhs);
+    cuda_check(cudaMemsetAsync(X, 0, sizeof(cd) * n * nrhs, s), "memset x");
+    for (int c = 0; c < nrhs; ++c) {
+        beta[c] = bl.norm(B + (int64_t)c * n, n);
+        gg[c].assign(1, C(beta[c], 0.0));
+        if (beta[c] > 0.0) {
+            active[c] = 1;
+            res[c] = 1.0;
+            k_scale<<<nblk(n), 256, 0, s>>>(B + (int64_t)c * n, 1.0 / beta[c], V + (int64_t)c * ldv, n);
+        }
+    }
+    std::vector<cd> hres((size_t)per * nrhs);
+    for (int j = 0; j < maxit; ++j) {
+        bool any = false;
+        for (int c = 0; c < nrhs; ++c) any |= active[c] != 0;
+        if (!any) break;
+        for (int c = 0; c < nrhs; ++c) {
+            cd* zc = Z + (int64_t)c * n;
+            const cd* vj = V + (int64_t)c * ldv + (int64_t)j * n;
+            if (!active[c]) cuda_check(cudaMemsetAsync(zc, 0, sizeof(cd) * n, s), "z = 0");
+            else if (pre) precond_apply_sorted(g, vj, zc, s);
+            else cuda_check(cudaMemcpyAsync(zc, vj, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "z = v_j");
+        }
+        apply_operator_sorted(g, Z, W, nrhs, s, false);
+        for (int c = 0; c < nrhs; ++c) {
+            if (!active[c]) continue;
+            cd* wc = W + (int64_t)c * n;
+            const cd* Vc = V + (int64_t)c * ldv;
+            cd* base = dres + (int64_t)c * per;
+            for (int pass = 0; pass < 2; ++pass) {
+                bl.vh(Vc, j + 1, n, wc, n, base + pass * cap);
+                k_update<<<nblk(n), 256, 0, s>>>(Vc, j + 1, n, base + pass * cap, wc, n);
+            }
+            bl.vh(wc, 1, n, wc, n, base + 2 * cap);
+            k_scale_by_norm<<<nblk(n), 256, 0, s>>>(wc, base + 2 * cap, V + (int64_t)c * ldv + (int64_t)(j + 1) * n, n);
+        }
+        cuda_check(cudaMemcpyAsync(hres.data(), dres, sizeof(cd) * per * nrhs, cudaMemcpyDeviceToHost, s), "arnoldi d2h");
+        cuda_check(cudaStreamSynchronize(s), "arnoldi sync");
+        for (int c = 0; c < nrhs; ++c) {
+            if (!active[c]) continue;
+            const cd* hr = hres.data() + (size_t)c * per;
+            std::vector<C> h(j + 2, C(0, 0));
+            for (int q = 0; q <= j; ++q) h[q] = C(hr[q].x, hr[q].y) + C(hr[cap + q].x, hr[cap + q].y);
+            const double hn = std::sqrt(std::max(hr[2 * cap].x, 0.0));
+            h[j + 1] = C(hn, 0.0);
+            for (int i = 0; i < j; ++i) {
+                C t = cs[c][i] * h[i] + sn[c][i] * h[i + 1];
+                h[i + 1] = -std::conj(sn[c][i]) * h[i] + std::conj(cs[c][i]) * h[i + 1];
+                h[i] = t;
+            }
+            C a = h[j], e = h[j + 1];
+            double r = std::hypot(std::abs(a), std::abs(e));
+            C cj, sj;
+            if (r == 0) { cj = 1; sj = 0; }
+            else if (std::abs(a) == 0) { cj = 0; sj = std::conj(e) / std::abs(e); }
+            else { cj = std::abs(a) / r; sj = (a / std::abs(a)) * std::conj(e) / r; }
+            h[j] = cj * a + sj * e;
+            h[j + 1] = 0;
+            cs[c].push_back(cj); sn[c].push_back(sj);
+            gg[c].push_back(-std::conj(sj) * gg[c][j]);
+            gg[c][j] = cj * gg[c][j];
+            H[c].push_back(h);
+            res[c] = std::abs(gg[c][j + 1]) / beta[c];
+            if (res[c] <= tol || hn == 0.0) active[c] = 0;
+        }
+    }
+    int all = 1;
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+        worst = std::max(worst, res[c]);
+        if (beta[c] == 0.0) continue;
+        all &= res[c] <= tol ? 1 : 0;
+        const int m = (int)H[c].size();
+        std::vector<C> y(m);
+        for (int i = m - 1; i >= 0; --i) {
+            C sacc = gg[c][i];
+            for (int k2 = i + 1; k2 < m; ++k2) sacc -= H[c][k2][i] * y[k2];
+            y[i] = sacc / H[c][i][i];
+        }
+        std::vector<cd> yh(m);
+        for (int i = 0; i < m; ++i) yh[i] = mk(y[i].real(), y[i].imag());
+        cd* yd = hd + (int64_t)c * cap;
+        cuda_check(cudaMemcpyAsync(yd, yh.data(), sizeof(cd) * m, cudaMemcpyHostToDevice, s), "y h2d");
+        cuda_check(cudaStreamSynchronize(s), "y h2d");   // yh is a local host buffer
+        const cd* Vc = V + (int64_t)c * ldv;
+        cd* xc = X + (int64_t)c * n;
+        if (pre) {
+            cd* zc = Z + (int64_t)c * n;
+            k_combine<<<nblk(n), 256, 0, s>>>(Vc, m, n, yd, zc, n);
+            precond_apply_sorted(g, zc, xc, s);
+        } else {
+            k_combine<<<nblk(n), 256, 0, s>>>(Vc, m, n, yd, xc, n);
+        }
+    }
+    cuda_check(cudaStreamSynchronize(s), "gmres end");
+    *last_iters = (int)H[nrhs - 1].size();
+    *worst_res = worst;
+    return all;
+}
+
 __global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = x[i] + d[i];
@@ -343,6 +474,39 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
         ~Free() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); }
     } fr{r, d, y2, s};
     Blas bl(g, s, 2);
+    if (precision == 0 && nrhs > 1) {
+        // all columns at once when their Krylov bases fit in a quarter of the free memory
+        size_t free_b = 0, total_b = 0;
+        cuda_check(cudaMemGetInfo(&free_b, &total_b), "memory info");
+        const double need = 16.0 * (double)n * (double)(maxit + 1) * nrhs + 48.0 * (double)n * nrhs;
+        if (need <= 0.25 * (double)free_b) {
+            double est = 0.0;
+            int ok = gmres_simul(g, b, x, nrhs, tol, maxit, pre, s, &it, &est);
+            // true residuals: one block product
+            cd* R = nullptr;
+            cuda_check(cudaMallocAsync((void**)&R, sizeof(cd) * n * nrhs, s), "malloc R");
+            apply_operator_sorted(g, x, R, nrhs, s);
+            for (int c = 0; c < nrhs; ++c) {
+                const cd* bc = b + (int64_t)c * n;
+                cd* rc = R + (int64_t)c * n;
+                k_axpby<<<nblk(n), 256, 0, s>>>(bc, rc, rc, n);
+                const double bn = bl.norm(bc, n), rn = bl.norm(rc, n);
+                worst_true = std::max(worst_true, bn > 0.0 ? rn / bn : 0.0);
+            }
+            cudaFreeAsync(R, s);
+            if (info) {
+                info->iterations = it;
+                info->converged = ok;
+                info->rel_residual = est;
+                info->true_rel_residual = worst_true;
+                info->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                info->refinements = 0;
+                info->fp64_matvecs = 1;
+                info->op_rel_diff = 0.0;
+            }
+            return ok;
+        }
+    }
     // ||(A_mixed - A) v|| / ||A v||
     auto op_diff = [&](const cd* v) {
         apply_operator_sorted(g, v, y2, 1, s, true);

@@ -192,6 +192,20 @@ def test_fmm_wide_band_straddling_cells(wide, p, tol):
     assert err <= tol
 
 
+def test_several_angles_solved_together(small3):
+    # several right-hand sides with the FP64 operator: one Krylov space per column,
+    # advanced together with block matvecs; every column equals its separate solve
+    lf, pts, w = small3["lf"], small3["pts"], small3["w"]
+    G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=16)
+    B = lf.rhs_plane_wave(G, np.radians([30.0, 75.0, 120.0, 160.0]))
+    X, info = lf.gmres_solve(G, B, tol=1e-8)
+    assert info["converged"] and info["true_rel_residual"] <= 1e-8
+    for c in range(B.shape[1]):
+        xc, ic = lf.gmres_solve(G, np.ascontiguousarray(B[:, c]), tol=1e-8)
+        assert np.array_equal(X[:, c], xc), c
+    assert info["iterations"] == ic["iterations"]   # the last column's count
+
+
 def test_fmm_multiple_rhs_columns_match_single(small3):
     lf, pts, w = small3["lf"], small3["pts"], small3["w"]
     G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=16)
