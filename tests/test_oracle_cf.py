@@ -130,3 +130,31 @@ def test_rows_match_dense():
     K = combined.dense_matrix_cf(m, pts, w, nrm)
     rows = np.array([0, 7, 30])
     np.testing.assert_allclose(combined.dense_rows_cf(m, pts, w, nrm, rows), K[rows], rtol=0, atol=1e-14)
+
+
+def test_gradient_transmission_conditions():
+    # the analytic field-point gradient obeys the interface conditions of Sec. 3.1:
+    # d/dx G and eta dG/dy are continuous across every interface (free part included
+    # when the field point's layer holds the source)
+    m = Medium(interfaces=[0.0, -0.9, -1.7], k=[3.0, 5.5, 2.0, 4.2], eta=[1.0, 2.5, 1.3, 3.0])
+    rng = np.random.default_rng(8)
+    bands = [(0.1, 1.5), (-0.8, -0.1), (-1.6, -1.0), (-3.0, -1.8)]
+
+    def grad(x, y, xs, ys):
+        gx, gy = core.gr_grad_block(m, [x], [y], [xs], [ys])
+        gx, gy = gx[0, 0], gy[0, 0]
+        lf, ls = green.layer_of(m, y), green.layer_of(m, ys)
+        if lf == ls:
+            fx, fy = dH0i(m.k[lf], x - xs, y - ys)
+            gx, gy = gx + fx, gy + fy
+        return gx, gy
+
+    for ls in range(4):
+        xs, ys = rng.uniform(-1, 1), rng.uniform(*bands[ls])
+        for j, yi in enumerate(m.interfaces):
+            x = rng.uniform(-1, 1)
+            ax, ay = grad(x, yi + 1e-12, xs, ys)
+            bx, by = grad(x, yi - 1e-12, xs, ys)
+            sc = max(abs(ay), abs(ax), 1e-3)
+            assert abs(ax - bx) < 1e-9 * sc, (ls, j, ax, bx)
+            assert abs(m.eta[j] * ay - m.eta[j + 1] * by) < 1e-9 * max(abs(m.eta[j] * ay), 1e-3), (ls, j)
