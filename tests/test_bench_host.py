@@ -1,5 +1,6 @@
 """Host logic of bench.py: the N > 1 aggregation over replicas, on CPU with gloo."""
 
+import json
 import os
 import socket
 
@@ -55,3 +56,18 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = type("A", (), {"workload": "c1", "warmup": 3, "steps": 1, "gpus": 2})()
     assert bench.run_reference(args) == 0
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys(monkeypatch, capsys):
+    # rank 0 times the oracle on a bounded sample of the workload (C1, N = 256, here) and
+    # prints the same line as the main arm, with impl = reference and its own e2e
+    monkeypatch.setenv("RANK", "0")
+    args = type("A", (), {"workload": "c1", "warmup": 3, "steps": 1, "gpus": 1})()
+    assert bench.run_reference(args) == 0
+    out = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(out) == 1
+    line = json.loads(out[0])
+    assert line["impl"] == "reference" and line["metric"] == "FMM matvec Mpts/s" and line["unit"] == "Mpts/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
