@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <map>
 #include <stdexcept>
@@ -506,9 +507,7 @@ void fmm_build(lfmm_geometry_s* g) {
                 int* d_same = dupload(g, same);
                 const int nd = 4 * pmax_same + 1;
                 const size_t smem = (size_t)(16 * nd + 3 * 256 + nd) * sizeof(cd);   // k_react_tables_same layout
-                if (smem > 48 * 1024)
-                    cuda_check(cudaFuncSetAttribute(k_react_tables_same, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem), "same-layer tables smem");
+                raise_smem_limit((const void*)k_react_tables_same, smem, "same-layer tables smem");
                 k_react_tables_same<<<(int)same.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_same, g->d_comp,
                                                                      g->d_m2lr);
                 cuda_check(cudaGetLastError(), "k_react_tables_same");
@@ -518,14 +517,24 @@ void fmm_build(lfmm_geometry_s* g) {
     cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "fmm_build");
 }
 
+void raise_smem_limit(const void* func, size_t bytes, const char* what) {
+    if (bytes <= 48 * 1024) return;   // no opt-in needed
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> granted;
+    int dev = 0;
+    cuda_check(cudaGetDevice(&dev), what);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = granted[std::make_pair(func, dev)];
+    if (bytes <= cur) return;
+    cuda_check(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes), what);
+    cur = bytes;
+}
+
 static void set_smem_limits() {
-    static bool done = false;
-    if (done) return;
-    const int lim = 200 * 1024;
-    cuda_check(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, lim), "smem p2m");
-    cuda_check(cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, lim), "smem l2p");
-    cuda_check(cudaFuncSetAttribute(k_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, lim), "smem m2l");
-    done = true;
+    const size_t lim = 200 * 1024;
+    raise_smem_limit((const void*)k_p2m, lim, "smem p2m");
+    raise_smem_limit((const void*)k_l2p, lim, "smem l2p");
+    raise_smem_limit((const void*)k_m2l, lim, "smem m2l");
 }
 
 static void ensure_coef(lfmm_geometry_s* g, int nrhs) {
@@ -592,14 +601,8 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     const int rs_p2m = 2 * (g->combined ? pD + 1 : pD) + 1;   // basis row length (k_p2m)
     const size_t smem_p2m = (size_t)gp * rs_p2m * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
     const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd);
-    if (smem_p2m > g->smem_p2m_set) {
-        cuda_check(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p2m), "p2m smem");
-        g->smem_p2m_set = smem_p2m;
-    }
-    if (smem_l2p > g->smem_l2p_set) {
-        cuda_check(cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l2p), "l2p smem");
-        g->smem_l2p_set = smem_l2p;
-    }
+    raise_smem_limit((const void*)k_p2m, smem_p2m, "p2m smem");
+    raise_smem_limit((const void*)k_l2p, smem_l2p, "l2p smem");
     // precision form: the levels >= lm run in FP32 on scaled expansions (lm > D: none)
     const int lm = mixed ? std::max(l0, std::min(mixed_level(g), D + 1)) : D + 1;
     if (lm <= D) mixed_setup(g, nrhs);

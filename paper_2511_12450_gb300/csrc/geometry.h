@@ -166,7 +166,6 @@ struct lfmm_geometry_s {
     lfmm::ExpEntry *d_leaf_entries = nullptr, *d_slot_entries = nullptr, *d_slot_leaf_entries = nullptr;
     lfmm::ExpGroup *d_leaf_groups = nullptr, *d_slot_groups = nullptr;   // P2M / L2P work groups
     int n_leaf_groups = 0, n_slot_groups = 0, group_max_pts = 1, group_max_ent = 1;
-    size_t smem_p2m_set = 48 * 1024, smem_l2p_set = 48 * 1024;   // opt-in shared memory already granted
     // M2M (up) and L2L (down) passes: per level, a range of destinations
     // (cells and reaction centres) with their sources and translation vectors
     std::vector<int> up_begin, up_end, dn_begin, dn_end;
@@ -289,6 +288,10 @@ void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false,
                cudaEvent_t before_l2p = nullptr);
 void fmm_autotune(lfmm_geometry_s* g);
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current device.
+// The attribute is process-wide, shared by every geometry and thread, so a
+// geometry that needs less must not undo what another one was granted.
+void raise_smem_limit(const void* func, size_t bytes, const char* what);
 // precision form: M2L in FP32 on scaled expansions (mixed.cu)
 void mixed_setup(lfmm_geometry_s* g, int nrhs);                       // tables, scales, FP32 buffers
 void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s);

@@ -75,7 +75,6 @@ struct MixedState {
     int tc_p = 0;                       // largest expansion order of the FP32 levels (the coarsest)
     int* tc_err = nullptr;              // set when an mbarrier wait of k_m2l32_tc gave up
     int* tc_err_host = nullptr;         // pinned copy, read at the next call
-    size_t tc_smem_set = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -673,12 +672,8 @@ static void mixed_build(lfmm_geometry_s* g) {
     const int rs_p2m = g->combined ? 2 * pD + 3 : pD + 1;   // basis row length (k_p2m32)
     ms->smem_p2m = (size_t)gp * rs_p2m * sizeof(cf) + (size_t)gp * sizeof(cf) + (size_t)(gp + 1) * sizeof(int);
     ms->smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(float) + (size_t)ge * (2 * pD + 1) * sizeof(cf);
-    if (ms->smem_p2m > 48 * 1024)
-        cuda_check(cudaFuncSetAttribute(k_p2m32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_p2m),
-                   "p2m32 smem");
-    if (ms->smem_l2p > 48 * 1024)
-        cuda_check(cudaFuncSetAttribute(k_l2p32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms->smem_l2p),
-                   "l2p32 smem");
+    raise_smem_limit((const void*)k_p2m32, ms->smem_p2m, "p2m32 smem");
+    raise_smem_limit((const void*)k_l2p32, ms->smem_l2p, "l2p32 smem");
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(cudaStreamPerThread);
     dev_release(d_tp); dev_release(d_ts); dev_release(d_kss); dev_release(d_kst);
@@ -842,14 +837,8 @@ static bool m2l_tc(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) 
         const int nc = std::min(TC_MAXN, nrhs - c0);
         const int np = nc <= 16 ? 16 : 32;
         const size_t smem = (size_t)(2 * 128 + 2 * np) * kp * sizeof(float);
-        if (smem > ms->tc_smem_set) {   // one attribute per instantiation
-            cuda_check(cudaFuncSetAttribute(k_m2l32_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       "m2l tc smem");
-            cuda_check(cudaFuncSetAttribute(k_m2l32_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       "m2l tc smem");
-            ms->tc_smem_set = smem;
-        }
         auto kern = np == 16 ? k_m2l32_tc<16> : k_m2l32_tc<32>;
+        raise_smem_limit((const void*)kern, smem, "m2l tc smem");
         kern<<<ms->n_tc_boxes, 128, smem, s>>>(ms->tc_boxes, ms->tc_ent_ptr, g->d_m2l_ents, g->d_box_level,
                                                g->d_p_level, g->d_coef_off, g->d_slot_of, g->d_slot_coef, ms->ftab,
                                                ms->ftab_off, ms->rtab, c0, nc, kp, g->ncoef, g->nslotcoef, ms->M,

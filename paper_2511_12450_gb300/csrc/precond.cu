@@ -178,9 +178,7 @@ void precond_build(lfmm_geometry_s* g) {
     const size_t smem = (size_t)(qmax + 64) * sizeof(cd);
     if (smem > 227 * 1024) throw CudaError{"preconditioner: neighbourhood of " + std::to_string(qmax) +
                                            " points does not fit in shared memory (use a smaller leaf size)"};
-    if (smem > 48 * 1024)
-        cuda_check(cudaFuncSetAttribute(k_pc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                   "pc smem");
+    raise_smem_limit((const void*)k_pc_apply, smem, "pc smem");
     g->pc_qmax = qmax;
     g->d_pc_ptr = dupload(g, ptr);
     g->d_pc_idx = dupload(g, idx);

@@ -127,3 +127,19 @@ def test_block_m2l_on_tensor_cores_wide_band(wide):
     for c in range(20):
         assert relerr(ytc[:, c], ref[:, c]) <= OP_TOL + 1e-8
         assert relerr(ytc[:, c], ysimt[:, c]) <= 5e-7
+
+
+def test_kernel_shared_memory_limits_only_grow_across_geometries(c2):
+    # The dynamic shared-memory limit of a kernel is process-wide: building and running a
+    # geometry with smaller expansions (smaller P2M/L2P/tensor-core tiles) between two runs of
+    # one with larger expansions must leave the larger geometry launchable, with unchanged results.
+    lf, G, med, pts, w = c2["lf"], c2["G"], c2["med"], c2["pts"], c2["w"]
+    rng = np.random.default_rng(26)
+    X = np.asfortranarray(rng.standard_normal((G.n, 16)) + 1j * rng.standard_normal((G.n, 16)))
+    y_big = lf.matvec(G, X, mixed=True)
+    y_big64 = lf.matvec(G, X)
+    small = lf.geometry_build(c2["M"], pts, w, p=12, leaf_size=32)
+    y_small = lf.matvec(small, X, mixed=True)
+    assert max(relerr(y_small[:, c], y_big64[:, c]) for c in range(16)) <= 1e-2
+    assert np.array_equal(lf.matvec(G, X, mixed=True), y_big)
+    assert np.array_equal(lf.matvec(G, X), y_big64)
