@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -10,7 +11,7 @@
 
 struct lfmm_medium_s {
     MediumDev m;
-    int geometries = 0;   // live geometries referencing this medium
+    std::atomic<int> geometries{0};   // live geometries referencing this medium (built on any thread)
 };
 
 namespace lfmm {
