@@ -15,8 +15,10 @@
  *    On error, lfmm_last_error() returns a thread-local message valid until
  *    the next call on the same thread.  Argument errors are reported before
  *    any device work.
- *  - Complex vectors are interleaved (re, im) double precision, column-major
- *    [n x nrhs] (column j starts at element j*n).
+ *  - Complex vectors are interleaved (re, im) double precision (single
+ *    precision with LFMM_C64, where a call takes flags), column-major
+ *    [n x nrhs] (column j starts at element j*n).  Device vectors must be
+ *    8-byte aligned.
  *  - The unknown is the paper's Phi = eta * phi and the right-hand side is
  *    b = eta_{l'} g (Sec. 3.3, eq. matrixandvec); element order is the order
  *    of the points passed to lfmm_geometry_build.
@@ -63,8 +65,15 @@ enum {
                                counterpart in the paper, which works in FP64 throughout).
                                With 16 or more columns its M2L runs on the tensor cores
                                (3xTF32, tcgen05) */,
-    LFMM_SIMT_M2L = 8       /* with LFMM_MIXED: keep the FP32 M2L on the SIMT kernel for
+    LFMM_SIMT_M2L = 8,      /* with LFMM_MIXED: keep the FP32 M2L on the SIMT kernel for
                                any number of columns (same operator to FP32 rounding) */
+    LFMM_C64 = 16           /* lfmm_matvec, lfmm_rhs_plane_wave, lfmm_eval_field: the complex
+                               vector arguments are single precision (interleaved float re,
+                               im; same column-major layout).  They are widened to FP64 on the
+                               device, the call computes exactly as without the flag, and its
+                               outputs are rounded to the nearest single-precision value.
+                               Halves the vectors' host-device traffic.  lfmm_gmres_solve
+                               takes double-precision vectors only */
 };
 
 /* lfmm_params.flags */
@@ -103,7 +112,12 @@ typedef struct {
 typedef struct {
     double tol;         /* relative residual ||b - K x|| / ||b|| (default 1e-8, Sec. 5) */
     int32_t max_iter;   /* default 1000 */
-    int32_t restart;    /* 0 = full GMRES (default) */
+    int32_t restart;    /* 0 = full GMRES (default).  m > 0: GMRES(m): a pass builds at
+                           most m Krylov vectors for the correction of the residual
+                           b - K x, which is recomputed with the FP64 operator before the
+                           next pass; max_iter counts the steps of all passes.  Bounds the
+                           Krylov basis to (m + 1) n complex values per column.  Columns are
+                           then solved one after another */
     int32_t precond;    /* 1 = overlapping DD preconditioner (Sec. 4.2, default), 0 = none */
     int32_t precision;  /* 0 = FP64 operator (default).  1 = relaxed mixed precision:
                            the relative difference eps of the LFMM_MIXED and FP64
@@ -120,7 +134,8 @@ typedef struct {
     double rel_residual;       /* final GMRES residual estimate (max over columns) */
     double true_rel_residual;  /* ||b - K x|| / ||b|| recomputed with lfmm_matvec (max over columns) */
     double solve_seconds;      /* wall time of the solve */
-    int32_t refinements;       /* GMRES passes (precision 1: 1 + refinement steps; 0 otherwise) */
+    int32_t refinements;       /* GMRES passes of the last column: restart cycles and
+                                  refinement steps included (0 for full FP64 GMRES) */
     int32_t fp64_matvecs;      /* FP64 operator applications, Krylov steps and residuals
                                   (last column) */
     double op_rel_diff;        /* precision 1: ||(A_mixed - A) b|| / ||A b|| (max over columns),

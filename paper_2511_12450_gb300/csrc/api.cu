@@ -369,30 +369,35 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
         require(g != nullptr && x != nullptr && y != nullptr, "NULL argument");
         require(nrhs >= 1, "nrhs must be >= 1");
         require(x != y, "x and y must not overlap");
+        const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
+        const bool c64 = (flags & LFMM_C64) != 0;
+        require(!dev || ((uintptr_t)x % 8 == 0 && (uintptr_t)y % 8 == 0), "device vectors must be 8-byte aligned");
         cudaStream_t s = as_stream(stream);
         ensure_scratch(g, nrhs);
         const size_t elems = (size_t)g->n * nrhs;
-        const cd* xin = (const cd*)x;
-        cd* yout = (cd*)y;
-        const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
+        const size_t esz = c64 ? sizeof(float2) : sizeof(cd);
+        const void* xin = x;
+        void* yout = y;
         if (!dev) {
             ensure_hostbuf(g, elems);
-            cuda_check(cudaMemcpyAsync(g->d_hostbuf_x, x, sizeof(cd) * elems, cudaMemcpyHostToDevice, s), "x h2d");
+            cuda_check(cudaMemcpyAsync(g->d_hostbuf_x, x, esz * elems, cudaMemcpyHostToDevice, s), "x h2d");
             xin = g->d_hostbuf_x;
             yout = g->d_hostbuf_y;
         }
         prof_begin(g, ST_GATHER, s);
-        gather_sorted(g, xin, g->d_xs, nrhs, s);
+        if (c64) gather_sorted_c64(g, (const float2*)xin, g->d_xs, nrhs, s);
+        else gather_sorted(g, (const cd*)xin, g->d_xs, nrhs, s);
         prof_end(g, ST_GATHER, s);
         g->m2l_simt = (flags & LFMM_SIMT_M2L) != 0;
         apply_operator_sorted(g, g->d_xs, g->d_ys, nrhs, s, (flags & LFMM_MIXED) != 0);
         g->m2l_simt = false;
         prof_begin(g, ST_SCATTER, s);
-        scatter_sorted(g, g->d_ys, yout, nrhs, s);
+        if (c64) scatter_sorted_c64(g, g->d_ys, (float2*)yout, nrhs, s);
+        else scatter_sorted(g, g->d_ys, (cd*)yout, nrhs, s);
         prof_end(g, ST_SCATTER, s);
         prof_flush(g, s);
         if (!dev) {
-            cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "y d2h");
+            cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, esz * elems, cudaMemcpyDeviceToHost, s), "y d2h");
             cuda_check(cudaStreamSynchronize(s), "matvec sync");
         }
         return LFMM_OK;
@@ -410,7 +415,8 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         const int precision = prm ? prm->precision : 0;
         require(tol > 0.0 && maxit >= 1, "invalid GMRES parameters");
         require(precision == 0 || precision == 1, "precision must be 0 (FP64) or 1 (mixed with refinement)");
-        require(!prm || prm->restart == 0, "restarted GMRES is not available (restart must be 0)");
+        const int restart = prm ? prm->restart : 0;
+        require(restart >= 0, "restart must be >= 0 (0 = full GMRES)");
         cudaStream_t s = as_stream(stream);
         if (pre && !g->pc_ready) precond_build(g);
         ensure_scratch(g, nrhs);
@@ -427,7 +433,8 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void*
         cuda_check(cudaMemcpyAsync(g->d_ys, b, sizeof(cd) * elems, cudaMemcpyDefault, s), "b copy");
         gather_sorted(g, g->d_ys, bb, nrhs, s);
         lfmm_gmres_info local;
-        int ok = gmres_sorted(g, bb, xx, nrhs, tol, maxit, pre != 0, s, info ? info : &local, precision);
+        int ok = gmres_sorted(g, bb, xx, nrhs, tol, maxit, pre != 0, s, info ? info : &local, precision,
+                              restart);
         scatter_sorted(g, xx, g->d_ys, nrhs, s);
         cuda_check(cudaMemcpyAsync(x, g->d_ys, sizeof(cd) * elems, cudaMemcpyDefault, s), "x copy");
         cuda_check(cudaStreamSynchronize(s), "gmres sync");
@@ -443,15 +450,19 @@ lfmm_status lfmm_rhs_plane_wave(lfmm_geometry g, int32_t nrhs, const double* ang
         for (int c = 0; c < nrhs; ++c)
             require(std::isfinite(angle_rad[c]) && angle_rad[c] > 0.0 && angle_rad[c] < M_PI,
                     "incidence angles must lie in (0, pi)");
+        const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
+        const bool c64 = (flags & LFMM_C64) != 0;
+        require(!dev || (uintptr_t)b % 8 == 0, "device vectors must be 8-byte aligned");
         cudaStream_t s = as_stream(stream);
         ensure_scratch(g, nrhs);
         rhs_plane_wave_sorted(g, nrhs, angle_rad, g->d_xs, s);
         const size_t elems = (size_t)g->n * nrhs;
-        if (flags & LFMM_DEVICE_PTRS) {
-            scatter_sorted(g, g->d_xs, (cd*)b, nrhs, s);
-        } else {
-            scatter_sorted(g, g->d_xs, g->d_ys, nrhs, s);
-            cuda_check(cudaMemcpyAsync(b, g->d_ys, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "b d2h");
+        void* out = dev ? b : (void*)g->d_ys;
+        if (c64) scatter_sorted_c64(g, g->d_xs, (float2*)out, nrhs, s);
+        else scatter_sorted(g, g->d_xs, (cd*)out, nrhs, s);
+        if (!dev) {
+            cuda_check(cudaMemcpyAsync(b, g->d_ys, (c64 ? sizeof(float2) : sizeof(cd)) * elems, cudaMemcpyDeviceToHost,
+                                       s), "b d2h");
             cuda_check(cudaStreamSynchronize(s), "rhs sync");
         }
         return LFMM_OK;
@@ -472,26 +483,38 @@ lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void* density, 
                     throw InterfaceError{"a target lies on an interface"};
             }
         }
+        const bool c64 = (flags & LFMM_C64) != 0;
         cudaStream_t s = as_stream(stream);
         ensure_scratch(g, nrhs);
         const size_t elems = (size_t)g->n * nrhs;
-        cuda_check(cudaMemcpyAsync(g->d_ys, density, sizeof(cd) * elems, cudaMemcpyDefault, s), "density copy");
-        gather_sorted(g, g->d_ys, g->d_xs, nrhs, s);
+        // density and u may be host or device memory (cudaMemcpyDefault); the
+        // single-precision forms are widened and rounded on the device
+        cuda_check(cudaMemcpyAsync(g->d_ys, density, (c64 ? sizeof(float2) : sizeof(cd)) * elems, cudaMemcpyDefault,
+                                   s), "density copy");
+        if (c64) gather_sorted_c64(g, (const float2*)g->d_ys, g->d_xs, nrhs, s);
+        else gather_sorted(g, g->d_ys, g->d_xs, nrhs, s);
         double* d_t = nullptr;
         cd* d_u = nullptr;
+        float2* d_u32 = nullptr;
         cuda_check(cudaMallocAsync((void**)&d_t, sizeof(double) * 2 * m, s), "malloc targets");
         cuda_check(cudaMallocAsync((void**)&d_u, sizeof(cd) * m * nrhs, s), "malloc u");
+        if (c64) cuda_check(cudaMallocAsync((void**)&d_u32, sizeof(float2) * m * nrhs, s), "malloc u");
         struct F {
             double* a;
             cd* b;
+            float2* c;
             cudaStream_t s;
-            ~F() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); }
-        } fr{d_t, d_u, s};
+            ~F() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); if (c) cudaFreeAsync(c, s); }
+        } fr{d_t, d_u, d_u32, s};
         cuda_check(cudaMemcpyAsync(d_t, targets, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s), "targets");
         eval_field_direct(g, nrhs, g->d_xs, m, d_t, d_u, s);
-        cuda_check(cudaMemcpyAsync(u, d_u, sizeof(cd) * m * nrhs, cudaMemcpyDefault, s), "u copy");
+        if (c64) {
+            round_to_c64(d_u, d_u32, (int64_t)m * nrhs, s);
+            cuda_check(cudaMemcpyAsync(u, d_u32, sizeof(float2) * m * nrhs, cudaMemcpyDefault, s), "u copy");
+        } else {
+            cuda_check(cudaMemcpyAsync(u, d_u, sizeof(cd) * m * nrhs, cudaMemcpyDefault, s), "u copy");
+        }
         cuda_check(cudaStreamSynchronize(s), "field sync");
-        (void)flags;
         return LFMM_OK;
     });
 }

@@ -308,11 +308,14 @@ void fmm_free(lfmm_geometry_s* g);   // per-nrhs coefficient buffers
 // permutation helpers and the full operator (solver.cu)
 void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s);
 void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s);
+void gather_sorted_c64(lfmm_geometry_s* g, const float2* x_in, cd* x_sorted, int nrhs, cudaStream_t s);
+void scatter_sorted_c64(lfmm_geometry_s* g, const cd* y_sorted, float2* y_out, int nrhs, cudaStream_t s);
+void round_to_c64(const cd* in, float2* out, int64_t n, cudaStream_t s);
 void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
                            bool mixed = false);
 void precond_build(lfmm_geometry_s* g);
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
-                 cudaStream_t s, lfmm_gmres_info* info, int precision = 0);
+                 cudaStream_t s, lfmm_gmres_info* info, int precision = 0, int restart = 0);
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s);
 void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s);
 void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t m, const double* d_targets,

@@ -15,32 +15,64 @@
 namespace lfmm {
 
 // ------------------------------------------------------------------ permutations
-__global__ void k_gather(const int* __restrict__ perm, const cd* __restrict__ in, cd* __restrict__ out, int64_t n,
+// caller-order vectors in FP64 (cd) or, with LFMM_C64, single precision (float2):
+// widened on the way in, rounded to nearest on the way out
+__device__ __forceinline__ cd widen(cd v) { return v; }
+__device__ __forceinline__ cd widen(float2 v) { return mk((double)v.x, (double)v.y); }
+__device__ __forceinline__ void store_as(cd* p, cd v) { *p = v; }
+__device__ __forceinline__ void store_as(float2* p, cd v) { *p = make_float2((float)v.x, (float)v.y); }
+
+template <class T>
+__global__ void k_gather(const int* __restrict__ perm, const T* __restrict__ in, cd* __restrict__ out, int64_t n,
                          int nrhs) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * nrhs) return;
     int64_t col = t / n, s = t - col * n;
-    out[t] = in[col * n + perm[s]];
+    out[t] = widen(in[col * n + perm[s]]);
 }
-__global__ void k_scatter(const int* __restrict__ perm, const cd* __restrict__ in, cd* __restrict__ out,
+template <class T>
+__global__ void k_scatter(const int* __restrict__ perm, const cd* __restrict__ in, T* __restrict__ out,
                           int64_t n, int nrhs) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * nrhs) return;
     int64_t col = t / n, s = t - col * n;
-    out[col * n + perm[s]] = in[t];
+    store_as(out + col * n + perm[s], in[t]);
 }
 
-void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s) {
+template <class T>
+static void gather_t(lfmm_geometry_s* g, const T* x_in, cd* x_sorted, int nrhs, cudaStream_t s) {
     int64_t tot = g->n * nrhs;
-    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, x_in, x_sorted, g->n, nrhs);
+    k_gather<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, x_in, x_sorted, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_gather");
     ++g->n_launches;
 }
-void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s) {
+template <class T>
+static void scatter_t(lfmm_geometry_s* g, const cd* y_sorted, T* y_out, int nrhs, cudaStream_t s) {
     int64_t tot = g->n * nrhs;
-    k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, y_sorted, y_out, g->n, nrhs);
+    k_scatter<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g->d_perm, y_sorted, y_out, g->n, nrhs);
     cuda_check(cudaGetLastError(), "k_scatter");
     ++g->n_launches;
+}
+void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s) {
+    gather_t(g, x_in, x_sorted, nrhs, s);
+}
+void scatter_sorted(lfmm_geometry_s* g, const cd* y_sorted, cd* y_out, int nrhs, cudaStream_t s) {
+    scatter_t(g, y_sorted, y_out, nrhs, s);
+}
+void gather_sorted_c64(lfmm_geometry_s* g, const float2* x_in, cd* x_sorted, int nrhs, cudaStream_t s) {
+    gather_t(g, x_in, x_sorted, nrhs, s);
+}
+void scatter_sorted_c64(lfmm_geometry_s* g, const cd* y_sorted, float2* y_out, int nrhs, cudaStream_t s) {
+    scatter_t(g, y_sorted, y_out, nrhs, s);
+}
+__global__ void k_round_c64(const cd* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) store_as(out + t, in[t]);
+}
+void round_to_c64(const cd* in, float2* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_round_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+    cuda_check(cudaGetLastError(), "k_round_c64");
 }
 
 void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
@@ -458,8 +490,13 @@ __global__ void k_add(cd* __restrict__ x, const cd* __restrict__ d, int64_t n) {
 // that, in one Krylov space.  The FP64 residual b - A x is then recomputed; while it
 // is above tol, refinement steps solve A d = r the same way (at most 4, stopping
 // when a step no longer halves ||r||).
+// restart m > 0: GMRES(m).  A pass (the first solve, a restart cycle or a refinement
+// step) builds at most m Krylov vectors for the correction d of A d = r, with
+// r = b - A x recomputed with the FP64 operator before each pass, and passes repeat
+// until that residual reaches tol or max_iter steps have been taken in all.  With the
+// precision form, a pass that ends at m steps is a restart, not a stall.
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
-                 cudaStream_t s, lfmm_gmres_info* info, int precision) {
+                 cudaStream_t s, lfmm_gmres_info* info, int precision, int restart) {
     auto t0 = std::chrono::steady_clock::now();
     const int64_t n = g->n;
     int all = 1, it = 0, outer_last = 0, f64_last = 0;
@@ -474,7 +511,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
         ~Free() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); }
     } fr{r, d, y2, s};
     Blas bl(g, s, 2);
-    if (precision == 0 && nrhs > 1) {
+    if (precision == 0 && nrhs > 1 && restart == 0) {
         // all columns at once when their Krylov bases fit in a quarter of the free memory
         size_t free_b = 0, total_b = 0;
         cuda_check(cudaMemGetInfo(&free_b, &total_b), "memory info");
@@ -522,12 +559,35 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
         double res = 0.0, rn = 0.0;
         const double bn = bl.norm(bc, n);
         int ok = 0, outer = 0, f64 = 0;
-        if (precision == 0) {
+        if (precision == 0 && restart == 0) {
             ok = gmres_one(g, bc, xc, tol, maxit, pre, s, &it, &res);
             apply_operator_sorted(g, xc, r, 1, s);
             k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
             rn = bl.norm(r, n);
             f64 = 1;
+        } else if (precision == 0) {
+            // GMRES(m): each cycle solves A d = r from a fresh Krylov space of at most m vectors
+            cuda_check(cudaMemsetAsync(xc, 0, sizeof(cd) * n, s), "memset x");
+            cuda_check(cudaMemcpyAsync(r, bc, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "r = b");
+            rn = bn;
+            int total = 0;
+            while (bn > 0.0 && rn > tol * bn && total < maxit) {
+                const double tol_in = (outer == 0) ? tol : tol * bn / rn;
+                int its = 0;
+                double rr = 0.0;
+                gmres_one(g, r, d, tol_in, std::min(restart, maxit - total), pre, s, &its, &rr);
+                total += its;
+                f64 += its;
+                k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
+                apply_operator_sorted(g, xc, r, 1, s);
+                k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+                ++f64;
+                ++outer;
+                rn = bl.norm(r, n);
+            }
+            it = total;
+            ok = (bn == 0.0 || rn <= tol * bn) ? 1 : 0;
+            res = bn > 0.0 ? rn / bn : 0.0;
         } else {
             const double eps = (bn > 0.0) ? std::max(op_diff(bc), 1e-300) : 1e-300;
             f64 += 1;
@@ -539,12 +599,13 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
             cuda_check(cudaMemcpyAsync(r, bc, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "r = b");
             rn = bn;
             int total = 0;
-            while (bn > 0.0 && rn > tol * bn && total < maxit && outer < 5) {
+            while (bn > 0.0 && rn > tol * bn && total < maxit && (restart > 0 || outer < 5)) {
                 const double tol_in = (outer == 0) ? tol1 : std::min(0.5, 0.5 * tol * bn / rn);
                 const double below_in = (outer == 0) ? below : below * bn / rn;
+                const int cap = restart > 0 ? std::min(restart, maxit - total) : maxit - total;
                 int its = 0, msteps = 0;
                 double rr = 0.0;
-                gmres_one(g, r, d, tol_in, maxit - total, pre, s, &its, &rr, below_in, &msteps);
+                const int reached = gmres_one(g, r, d, tol_in, cap, pre, s, &its, &rr, below_in, &msteps);
                 total += its;
                 f64 += its - msteps;
                 k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
@@ -553,7 +614,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
                 ++f64;
                 ++outer;
                 const double rn_new = bl.norm(r, n);
-                const bool stalled = rn_new > 0.5 * rn;
+                const bool stalled = rn_new > 0.5 * rn && (restart == 0 || reached);
                 rn = rn_new;
                 if (stalled) break;
             }

@@ -33,6 +33,7 @@ LFMM_PROFILE_STAGES = 1
 LFMM_AUTOTUNE = 2
 LFMM_COMBINED_FIELD = 4
 LFMM_SIMT_M2L = 8
+LFMM_C64 = 16
 STAGES = ["p2m", "m2m", "m2l", "l2l", "l2p", "near", "gather", "scatter"]
 
 EXPORTED = [
@@ -207,42 +208,48 @@ def geometry_build(medium: Medium, points, weights, normals=None, p: int = 20, l
     return Geometry(h, medium, pts.shape[0])
 
 
-def _vec_args(v, n):
-    """(pointer, nrhs, flags, keepalive) for a complex vector argument."""
+def _vec_args(v, n, allow_c64=True):
+    """(pointer, nrhs, flags, keepalive) for a complex vector argument; complex64
+    vectors (where the call takes them) add LFMM_C64 to the flags."""
     if _is_torch_cuda(v):
         import torch
 
-        assert v.dtype == torch.complex128 and v.is_contiguous()
-        nrhs = 1 if v.dim() == 1 else v.shape[1 if v.shape[0] == n else 0]
-        return ctypes.c_void_p(v.data_ptr()), v.numel() // n, LFMM_DEVICE_PTRS, v
+        c64 = v.dtype == torch.complex64
+        if not (v.dtype == torch.complex128 or (c64 and allow_c64)) or not v.is_contiguous():
+            raise TypeError("contiguous complex128 tensor expected" + (" (or complex64)" if allow_c64 else ""))
+        return ctypes.c_void_p(v.data_ptr()), v.numel() // n, LFMM_DEVICE_PTRS | (LFMM_C64 if c64 else 0), v
     a = np.asarray(v)
-    if a.dtype != np.complex128:
-        raise TypeError("complex128 expected")
+    c64 = a.dtype == np.complex64
+    if not (a.dtype == np.complex128 or (c64 and allow_c64)):
+        raise TypeError("complex128 expected" + (" (or complex64)" if allow_c64 else ""))
     if not a.flags["F_CONTIGUOUS" if a.ndim == 2 else "C_CONTIGUOUS"]:
         raise ValueError("vector must be column-major contiguous")
-    return ctypes.c_void_p(a.ctypes.data), a.size // n, 0, a
+    return ctypes.c_void_p(a.ctypes.data), a.size // n, LFMM_C64 if c64 else 0, a
 
 
 def _empty_like(v, n, nrhs):
     if _is_torch_cuda(v):
         import torch
 
-        return torch.empty((n,) if nrhs == 1 else (nrhs, n), dtype=torch.complex128, device=v.device)
-    return np.zeros(n, dtype=np.complex128) if nrhs == 1 else np.zeros((n, nrhs), dtype=np.complex128, order="F")
+        return torch.empty((n,) if nrhs == 1 else (nrhs, n), dtype=v.dtype, device=v.device)
+    dt = np.asarray(v).dtype
+    return np.zeros(n, dtype=dt) if nrhs == 1 else np.zeros((n, nrhs), dtype=dt, order="F")
 
 
-def rhs_plane_wave(g: Geometry, angles_rad, out=None, stream=None, device=False):
+def rhs_plane_wave(g: Geometry, angles_rad, out=None, stream=None, device=False, single=False):
+    """b for plane waves at the given angles; single=True returns complex64 (LFMM_C64)."""
     ang = _f64(angles_rad).reshape(-1)
     nrhs = ang.size
     if out is None:
         if device:
             import torch
 
-            out = torch.empty((nrhs, g.n) if nrhs > 1 else (g.n,), dtype=torch.complex128, device="cuda")
+            out = torch.empty((nrhs, g.n) if nrhs > 1 else (g.n,),
+                              dtype=torch.complex64 if single else torch.complex128, device="cuda")
         else:
-            out = _empty_like(np.zeros(1, np.complex128), g.n, nrhs)
+            out = _empty_like(np.zeros(1, np.complex64 if single else np.complex128), g.n, nrhs)
     ptr, _, flags, keep = _vec_args(out, g.n)
-    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    st = _stream_of(stream) if flags & LFMM_DEVICE_PTRS else ctypes.c_void_p(0)
     _check(library().lfmm_rhs_plane_wave(g.handle, nrhs, _dp(ang), ptr, flags, st))
     return out
 
@@ -255,8 +262,8 @@ def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False, simt_m2l: b
         y = _empty_like(x, g.n, nrhs)
     yp, _, flags_y, keep_y = _vec_args(y, g.n)
     if flags != flags_y:
-        raise ValueError("x and y must both be host arrays or both device tensors")
-    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+        raise ValueError("x and y must both be host arrays or both device tensors, of one complex dtype")
+    st = _stream_of(stream) if flags & LFMM_DEVICE_PTRS else ctypes.c_void_p(0)
     flags |= (LFMM_MIXED if mixed else 0) | (LFMM_SIMT_M2L if simt_m2l else 0)
     _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
     return y
@@ -274,13 +281,14 @@ def matvec_static(g: Geometry, x, y, stream=None):
 
 
 def gmres_solve(g: Geometry, b, x=None, tol: float = 1e-8, max_iter: int = 1000, precond: bool = True,
-                stream=None, precision: int = 0):
-    """GMRES to tol.  precision=1: iterative refinement with inner solves on the precision form."""
-    bp, nrhs, flags, keep = _vec_args(b, g.n)
+                stream=None, precision: int = 0, restart: int = 0):
+    """GMRES to tol.  precision=1: iterative refinement with inner solves on the precision form.
+    restart=m > 0: GMRES(m), each pass from the recomputed residual with at most m Krylov vectors."""
+    bp, nrhs, flags, keep = _vec_args(b, g.n, allow_c64=False)
     if x is None:
         x = _empty_like(b, g.n, nrhs)
-    xp, _, _, keep_x = _vec_args(x, g.n)
-    prm = GmresParams(float(tol), int(max_iter), 0, 1 if precond else 0, int(precision))
+    xp, _, _, keep_x = _vec_args(x, g.n, allow_c64=False)
+    prm = GmresParams(float(tol), int(max_iter), int(restart), 1 if precond else 0, int(precision))
     info = GmresInfo()
     st = _stream_of(stream) if flags else ctypes.c_void_p(0)
     status = _check(library().lfmm_gmres_solve(g.handle, nrhs, bp, xp, ctypes.byref(prm), ctypes.byref(info), st))
@@ -293,8 +301,9 @@ def eval_field(g: Geometry, density, targets, stream=None):
     dpp, nrhs, flags, keep = _vec_args(density, g.n)
     tg = _f64(targets).reshape(-1, 2)
     m = tg.shape[0]
-    u = np.zeros(m, dtype=np.complex128) if nrhs == 1 else np.zeros((m, nrhs), dtype=np.complex128, order="F")
-    st = _stream_of(stream) if flags else ctypes.c_void_p(0)
+    dt = np.complex64 if flags & LFMM_C64 else np.complex128
+    u = np.zeros(m, dtype=dt) if nrhs == 1 else np.zeros((m, nrhs), dtype=dt, order="F")
+    st = _stream_of(stream) if flags & LFMM_DEVICE_PTRS else ctypes.c_void_p(0)
     _check(library().lfmm_eval_field(g.handle, nrhs, dpp, m, _dp(tg), ctypes.c_void_p(u.ctypes.data), flags, st))
     return u
 

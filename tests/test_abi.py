@@ -92,3 +92,34 @@ def test_geometry_argument_validation_before_device_work(lib):
     with pytest.raises(lib.LfmmError) as ei:
         lib.geometry_build(m1, ring, np.full(th.size, 2 * np.pi * 10 / th.size), leaf_size=1000)
     assert ei.value.status == lib.LFMM_ERR_INVALID_ARG and "leaf_size" in str(ei.value)
+
+
+def test_binding_constants_match_the_header(lib):
+    with open(os.path.join(ROOT, "include", "lfmm.h")) as f:
+        txt = f.read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(LFMM_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt))
+    assert "LFMM_C64" in consts and "LFMM_DEVICE_PTRS" in consts
+    for k, v in consts.items():
+        if hasattr(lib, k):
+            assert getattr(lib, k) == v, k
+    missing = [k for k in consts if not hasattr(lib, k)]
+    assert not missing, missing
+
+
+def test_single_precision_vectors_marshal_with_the_c64_flag(lib):
+    n = 8
+    x = np.zeros(n, dtype=np.complex64)
+    _, nrhs, flags, _ = lib._vec_args(x, n)
+    assert nrhs == 1 and flags == lib.LFMM_C64
+    X = np.zeros((n, 3), dtype=np.complex128, order="F")
+    _, nrhs, flags, _ = lib._vec_args(X, n)
+    assert nrhs == 3 and flags == 0
+    with pytest.raises(TypeError):
+        lib._vec_args(np.zeros(n, dtype=np.float64), n)
+
+    class FakeGeometry:   # gmres_solve checks its vectors before calling the library
+        n = 8
+        handle = None
+
+    with pytest.raises(TypeError):
+        lib.gmres_solve(FakeGeometry(), x)

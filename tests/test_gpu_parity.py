@@ -79,6 +79,32 @@ def test_device_pointer_path(c1):
     assert relerr(yt.cpu().numpy(), K @ x) <= 1e-10
 
 
+def test_single_precision_vectors(c1):
+    # LFMM_C64: complex64 vectors are widened on the device, the call computes in FP64 as
+    # without the flag, and its outputs are rounded to nearest, as numpy's cast rounds
+    import torch
+
+    lf, G = c1["lf"], c1["G"]
+    rng = np.random.default_rng(4)
+    x32 = np.asfortranarray((rng.standard_normal((G.n, 2)) + 1j * rng.standard_normal((G.n, 2))).astype(np.complex64))
+    y64 = lf.matvec(G, np.asfortranarray(x32.astype(np.complex128)))
+    y32 = lf.matvec(G, x32)
+    assert y32.dtype == np.complex64 and np.array_equal(y32, y64.astype(np.complex64))
+    yt = lf.matvec(G, torch.from_numpy(np.ascontiguousarray(x32.T)).cuda())   # device, [n x 2] column-major
+    torch.cuda.synchronize()
+    assert yt.dtype == torch.complex64 and np.array_equal(yt.cpu().numpy().T, y32)
+    angs = np.deg2rad([45.0, 100.0])
+    b64 = lf.rhs_plane_wave(G, angs)
+    assert np.array_equal(lf.rhs_plane_wave(G, angs, single=True), b64.astype(np.complex64))
+    bt = lf.rhs_plane_wave(G, angs, device=True, single=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(bt.cpu().numpy().T, b64.astype(np.complex64))
+    tg = np.array([[0.0, 2.1], [1.3, 0.4], [-0.8, -0.7]])
+    u64 = lf.eval_field(G, np.ascontiguousarray(x32[:, 0].astype(np.complex128)), tg)
+    u32 = lf.eval_field(G, np.ascontiguousarray(x32[:, 0]), tg)
+    assert u32.dtype == np.complex64 and np.array_equal(u32, u64.astype(np.complex64))
+
+
 @pytest.fixture(scope="module")
 def small3(gpu_lib):
     lf = gpu_lib
@@ -204,6 +230,38 @@ def test_several_angles_solved_together(small3):
         xc, ic = lf.gmres_solve(G, np.ascontiguousarray(B[:, c]), tol=1e-8)
         assert np.array_equal(X[:, c], xc), c
     assert info["iterations"] == ic["iterations"]   # the last column's count
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_restarted_gmres(small3, precision):
+    # GMRES(m): passes of at most m Krylov steps from the recomputed residual reach the same
+    # tolerance and the same solution as full GMRES (within the tolerance's reach)
+    lf, pts, w, K, med = small3["lf"], small3["pts"], small3["w"], small3["K"], small3["med"]
+    G = lf.geometry_build(small3["M"], pts, w, p=20, leaf_size=16)
+    b = obg.rhs(med, np.deg2rad(45.0), pts[:, 0], pts[:, 1])
+    ref = np.linalg.solve(K, b)
+    xf, inf = lf.gmres_solve(G, b, tol=1e-8, precision=precision)
+    m = max(2, inf["iterations"] // 3)
+    xr, inr = lf.gmres_solve(G, b, tol=1e-8, precision=precision, restart=m)
+    print(f"precision {precision}: full {inf['iterations']} steps, GMRES({m}) {inr['iterations']} steps "
+          f"in {inr['refinements']} passes, true residual {inr['true_rel_residual']:.2e}")
+    assert inr["converged"] == 1 and inr["true_rel_residual"] <= 1e-8
+    assert inr["refinements"] >= 2
+    assert relerr(xr, ref) <= 1e-5 and relerr(xr, xf) <= 1e-5
+    if precision == 0:
+        # a restart length the solve never reaches: one pass, the full GMRES iterate
+        xb, inb = lf.gmres_solve(G, b, tol=1e-8, restart=inf["iterations"] + 5)
+        if inf["true_rel_residual"] <= 0.9e-8:   # the recomputed residual also meets tol
+            assert inb["refinements"] == 1 and inb["iterations"] == inf["iterations"]
+            assert np.array_equal(xb, xf)
+        else:   # estimate below tol, recomputed residual not: one more pass
+            assert inb["converged"] == 1 and relerr(xb, xf) <= 1e-7
+        # several columns with a restart are solved one by one, each as alone
+        B = np.asfortranarray(np.stack([b, 1j * b[::-1]], axis=1))
+        XB, _ = lf.gmres_solve(G, B, tol=1e-8, restart=m)
+        assert np.array_equal(XB[:, 0], xr)
+        x1, _ = lf.gmres_solve(G, np.ascontiguousarray(B[:, 1]), tol=1e-8, restart=m)
+        assert np.array_equal(XB[:, 1], x1)
 
 
 def test_fmm_multiple_rhs_columns_match_single(small3):
