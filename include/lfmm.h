@@ -49,8 +49,15 @@ typedef enum {
     LFMM_ERR_OUT_OF_MEMORY = -2,
     LFMM_ERR_CUDA = -3,
     LFMM_ERR_NODE_ON_INTERFACE = -4,  /* a point lies on (or within 1e-12*scale of) an interface */
-    LFMM_ERR_QUADRATURE = -5,
-    LFMM_ERR_TIMEOUT = -6,
+    LFMM_ERR_QUADRATURE = -5,         /* reserved: the library's quadrature rules are fixed
+                                         (no adaptive step that could fail to converge) */
+    LFMM_ERR_TIMEOUT = -6,            /* a bounded device wait gave up: the tensor-core
+                                         M2L of LFMM_MIXED (16+ columns) waits on its own
+                                         MMAs.  The affected products were computed with
+                                         those M2L contributions zeroed.  A call with host
+                                         vectors reports it itself; with device vectors the
+                                         next lfmm_matvec on the geometry does.  Reported
+                                         once, after which the geometry is usable again */
     LFMM_ERR_HBM_BUDGET = -7
 } lfmm_status;
 
@@ -166,7 +173,7 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m);
  *             else NULL or ignored)
  *   prm     : NULL for defaults
  * Errors: LFMM_ERR_INVALID_ARG, LFMM_ERR_NODE_ON_INTERFACE, LFMM_ERR_OUT_OF_MEMORY,
- *         LFMM_ERR_CUDA, LFMM_ERR_QUADRATURE.
+ *         LFMM_ERR_CUDA.
  */
 lfmm_status lfmm_geometry_build(lfmm_medium m, int64_t n, const double *points,
                                 const double *weights, const double *normals,

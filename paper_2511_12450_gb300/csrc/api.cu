@@ -114,6 +114,9 @@ static lfmm_status guarded(F&& f) {
     } catch (const InterfaceError& e) {
         set_error(e.msg);
         return LFMM_ERR_NODE_ON_INTERFACE;
+    } catch (const TimeoutError& e) {
+        set_error(e.msg);
+        return LFMM_ERR_TIMEOUT;
     } catch (const CudaError& e) {
         set_error(e.msg);
         if (e.msg.find("out of memory") != std::string::npos) return LFMM_ERR_OUT_OF_MEMORY;
@@ -399,6 +402,7 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
         if (!dev) {
             cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, esz * elems, cudaMemcpyDeviceToHost, s), "y d2h");
             cuda_check(cudaStreamSynchronize(s), "matvec sync");
+            mixed_check_waits(g);
         }
         return LFMM_OK;
     });

@@ -240,6 +240,9 @@ void set_error(const std::string& msg);
 struct CudaError {
     std::string msg;
 };
+struct TimeoutError {   // a bounded device wait gave up (LFMM_ERR_TIMEOUT)
+    std::string msg;
+};
 void cuda_check(cudaError_t e, const char* what);
 // Device memory of a geometry.  Allocations are stream-ordered on the calling
 // thread's default stream so that building or releasing one geometry does not
@@ -304,6 +307,10 @@ void mixed_l2l(lfmm_geometry_s* g, int child_level, int nrhs, cudaStream_t s);
 void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s);
 int mixed_level(lfmm_geometry_s* g);   // first level whose M2L runs in FP32
 void mixed_destroy(lfmm_geometry_s* g);
+// Throws TimeoutError, once, if a bounded wait of the tensor-core M2L gave up in work
+// this geometry's host copy of the status has seen (copied after every launch; current
+// once the launching stream has been synchronised).  Clears the status.
+void mixed_check_waits(lfmm_geometry_s* g);
 void fmm_free(lfmm_geometry_s* g);   // per-nrhs coefficient buffers
 // permutation helpers and the full operator (solver.cu)
 void gather_sorted(lfmm_geometry_s* g, const cd* x_in, cd* x_sorted, int nrhs, cudaStream_t s);

@@ -831,7 +831,7 @@ static bool m2l_tc(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) 
     const int nco = 2 * ms->tc_p + 1;
     if (nrhs < TC_MIN_COLS || g->m2l_simt || ms->n_tc_boxes == 0 || 2 * nco > 128 || min_level != ms->lm)
         return false;
-    if (*ms->tc_err_host != 0) throw CudaError{"tensor-core M2L: an mbarrier wait gave up"};
+    mixed_check_waits(g);
     const int kp = (2 * nco + 7) / 8 * 8;
     for (int c0 = 0; c0 < nrhs; c0 += TC_MAXN) {
         const int nc = std::min(TC_MAXN, nrhs - c0);
@@ -848,6 +848,17 @@ static bool m2l_tc(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) 
     }
     cuda_check(cudaMemcpyAsync(ms->tc_err_host, ms->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s), "tc status");
     return true;
+}
+
+void mixed_check_waits(lfmm_geometry_s* g) {
+    MixedState* ms = g->mixed;
+    if (!ms || !ms->tc_err_host || *ms->tc_err_host == 0) return;
+    // no launch of this geometry is in flight that could set it again (the caller's
+    // stream has been synchronised, or the status is from an earlier call's)
+    cuda_check(cudaMemsetAsync(ms->tc_err, 0, sizeof(int), cudaStreamPerThread), "tc status reset");
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "tc status reset");
+    *ms->tc_err_host = 0;
+    throw TimeoutError{"tensor-core M2L: an mbarrier wait gave up; that product's M2L contributions were zeroed"};
 }
 
 void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {
