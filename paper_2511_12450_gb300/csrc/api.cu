@@ -8,6 +8,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "geometry.h"
@@ -104,7 +105,7 @@ void prof_flush(lfmm_geometry_s* g, cudaStream_t s) {
 }
 
 template <class F>
-static lfmm_status guarded(F&& f) {
+static lfmm_status guarded_body(F&& f) {
     try {
         t_last_error.clear();
         return f();
@@ -131,6 +132,15 @@ static lfmm_status guarded(F&& f) {
         set_error("unknown error");
         return LFMM_ERR_CUDA;
     }
+}
+// A failed runtime call (an allocation that ran out of memory, say) stays the
+// thread's last CUDA error; it is cleared when a call fails, so that the launch
+// checks (cudaGetLastError) of the next call on this thread do not report it again.
+template <class F>
+static lfmm_status guarded(F&& f) {
+    const lfmm_status st = guarded_body(std::forward<F>(f));
+    if (st < 0) (void)cudaGetLastError();
+    return st;
 }
 
 static void require(bool c, const char* msg) {

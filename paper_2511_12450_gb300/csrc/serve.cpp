@@ -20,6 +20,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -98,6 +99,7 @@ void run_request(Request& r, cudaStream_t s) {
         r.setup_s = now_s() - t0;
         if (cudaMallocAsync(&db, 16 * (size_t)r.n, s) != cudaSuccess ||
             cudaMallocAsync(&dx, 16 * (size_t)r.n, s) != cudaSuccess) {
+            (void)cudaGetLastError();   // not this worker's next request's error
             r.status = LFMM_ERR_OUT_OF_MEMORY;
             r.err = "cudaMallocAsync failed for the request's vectors";
             break;
@@ -111,6 +113,7 @@ void run_request(Request& r, cudaStream_t s) {
         r.x.resize(2 * (size_t)r.n);
         if (cudaMemcpyAsync(r.x.data(), dx, 16 * (size_t)r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
+            (void)cudaGetLastError();
             r.status = LFMM_ERR_CUDA;
             r.err = "copy of the solution failed";
         }
@@ -144,7 +147,12 @@ void worker_main(lfmm_server_s* S) {
             S->peak_running = std::max(S->peak_running, S->running);
             r->t_admit = now_s();
         }
-        run_request(*r, s);
+        try {
+            run_request(*r, s);
+        } catch (const std::bad_alloc&) {   // the host copy of the solution
+            r->status = LFMM_ERR_OUT_OF_MEMORY;
+            r->err = "host allocation failed";
+        }
         {
             std::lock_guard<std::mutex> lk(S->mu);
             r->t_done = now_s();
@@ -172,7 +180,17 @@ extern "C" lfmm_status lfmm_server_create(const lfmm_server_params* prm, lfmm_se
     return LFMM_OK;
 }
 
+static lfmm_status server_submit(lfmm_server S, const lfmm_request* q, int64_t* ticket);
+
 extern "C" lfmm_status lfmm_server_submit(lfmm_server S, const lfmm_request* q, int64_t* ticket) {
+    try {
+        return server_submit(S, q, ticket);
+    } catch (const std::bad_alloc&) {   // the request's copies of its inputs
+        return LFMM_ERR_OUT_OF_MEMORY;
+    }
+}
+
+static lfmm_status server_submit(lfmm_server S, const lfmm_request* q, int64_t* ticket) {
     if (!S || !q || !ticket) return LFMM_ERR_INVALID_ARG;
     if (q->n_layers < 1 || q->n < 1 || !q->points || !q->weights || !q->wavenumber || !q->density ||
         (q->n_layers > 1 && !q->interface_y) || !(q->tol > 0.0) || q->max_iter < 1 ||
