@@ -173,7 +173,7 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m);
  *             else NULL or ignored)
  *   prm     : NULL for defaults
  * Errors: LFMM_ERR_INVALID_ARG, LFMM_ERR_NODE_ON_INTERFACE, LFMM_ERR_OUT_OF_MEMORY,
- *         LFMM_ERR_CUDA.
+ *         LFMM_ERR_CUDA; *out is then NULL and whatever was built is released.
  */
 lfmm_status lfmm_geometry_build(lfmm_medium m, int64_t n, const double *points,
                                 const double *weights, const double *normals,

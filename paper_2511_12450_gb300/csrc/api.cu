@@ -361,6 +361,7 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         free_geometry(g);
         delete g;
     }
+    if (st != LFMM_OK && out) *out = nullptr;
     return st;
 }
 

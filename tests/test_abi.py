@@ -123,3 +123,16 @@ def test_single_precision_vectors_marshal_with_the_c64_flag(lib):
 
     with pytest.raises(TypeError):
         lib.gmres_solve(FakeGeometry(), x)
+
+
+def test_failed_geometry_build_returns_a_null_handle(lib):
+    import ctypes
+
+    m = lib.medium_create([0.0], [4.0, 6.0], [1.0, 2.0])
+    pts = np.array([[0.1, 0.0], [0.3, -1.0]])   # the first point lies on the interface
+    w = np.array([0.1, 0.1])
+    h = ctypes.c_void_p(12345)
+    st = lib.library().lfmm_geometry_build(m.handle, 2, lib._dp(pts), lib._dp(w), None, None, ctypes.byref(h))
+    assert st == lib.LFMM_ERR_NODE_ON_INTERFACE
+    assert not h.value
+    assert "interface" in lib.library().lfmm_last_error().decode()
