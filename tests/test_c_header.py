@@ -49,13 +49,16 @@ def libdir():
     return d
 
 
-def test_header_is_strict_c99_and_links(libdir, tmp_path):
+def test_header_is_strict_c99_and_links(libdir):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    src = tmp_path / "use_lfmm.c"
-    src.write_text(C_PROGRAM)
-    exe = tmp_path / "use_lfmm"
+    work = os.path.join(ROOT, "tests", "_build")   # git-ignored
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, "use_lfmm.c")
+    with open(src, "w") as f:
+        f.write(C_PROGRAM)
+    exe = os.path.join(work, "use_lfmm")
     cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
            str(src), "-o", str(exe), "-L", libdir, "-llfmm", "-Wl,-rpath," + libdir]
     res = subprocess.run(cmd, capture_output=True, text=True)
