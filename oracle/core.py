@@ -23,6 +23,8 @@ def _lib():
                                             ctypes.c_long, dp, dp]
         lib.oracle_gr_pairs.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp, dp, dp,
                                         ctypes.c_double, dp, ip]
+        lib.oracle_gr_pairs_contour.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp, dp, dp,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, ip]
         lib.oracle_gr_block.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp,
                                         ctypes.c_long, dp, dp, ctypes.c_double, dp]
         lib.oracle_gr_grad_block.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_long, dp, dp,
@@ -80,6 +82,24 @@ def gr_pairs(medium, x, y, xs, ys, tol_rel: float = 1e-13, check: bool = True) -
     if check and np.any(st != 0):
         bad = np.flatnonzero(st)
         raise RuntimeError(f"oracle G^r failed for {bad.size} pairs (status {np.unique(st[bad])})")
+    return out
+
+
+def gr_pairs_contour(medium, x, y, xs, ys, t_scale: float, h_scale: float, tol_rel: float = 1e-13) -> np.ndarray:
+    """gr_pairs on a deformed contour: detour end T times t_scale (>= 1), depth h times
+    h_scale (in (0, 1]).  The integral is contour independent (Cauchy), so this is a
+    self-check of the contour and the quadrature, not a different quantity."""
+    x, y, xs, ys = (np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+                    for a in np.broadcast_arrays(x, y, xs, ys))
+    n = x.size
+    yint, k, eta = _medium_arrays(medium)
+    out = np.zeros(n, dtype=np.complex128)
+    st = np.zeros(n, dtype=np.int32)
+    rc = _lib().oracle_gr_pairs_contour(int(k.size), _dp(yint), _dp(k), _dp(eta), n, _dp(x), _dp(y),
+                                        _dp(xs), _dp(ys), float(tol_rel), float(t_scale), float(h_scale),
+                                        _dp(out.view(np.float64)), st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc != 0:
+        raise RuntimeError(f"oracle G^r on the scaled contour failed ({rc}, status {np.unique(st)})")
     return out
 
 

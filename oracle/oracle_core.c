@@ -302,8 +302,8 @@ static int layer_of(const medium_t *m, double y) {
  * 1 if the quadrature did not reach tolerance, 2 on a degenerate pair
  * (a point on an interface), 3 on a singular interface system.
  */
-static int gr_pair(const medium_t *m, double x, double y, double xs, double ys,
-                   double tol_rel, int mode, cplx *out) {
+static int gr_pair_contour(const medium_t *m, double x, double y, double xs, double ys,
+                           double tol_rel, int mode, double t_scale, double h_scale, cplx *out) {
     *out = 0.0;
     int L = m->nl - 1;
     if (L == 0) return 0;
@@ -331,9 +331,9 @@ static int gr_pair(const medium_t *m, double x, double y, double xs, double ys,
     pc.D = D;
     double kmax = 0.0;
     for (int l = 0; l <= L; ++l) kmax = fmax(kmax, m->k[l]);
-    double T = 1.2 * kmax + 1.0;
+    double T = (1.2 * kmax + 1.0) * t_scale;
     double ax = fabs(pc.X);
-    double h = fmin(0.5, 1.0 / fmax(ax, 1e-3));
+    double h = fmin(0.5, 1.0 / fmax(ax, 1e-3)) * h_scale;
     double rho = sqrt(pc.X * pc.X + D * D);
     int fail = 0;
     const double tol_abs = 1e-15;
@@ -346,6 +346,11 @@ static int gr_pair(const medium_t *m, double x, double y, double xs, double ys,
     *out = v;
     if (pc.err) return 3;
     return fail ? 1 : 0;
+}
+
+static int gr_pair(const medium_t *m, double x, double y, double xs, double ys,
+                   double tol_rel, int mode, cplx *out) {
+    return gr_pair_contour(m, x, y, xs, ys, tol_rel, mode, 1.0, 1.0, out);
 }
 
 /* ---------------------------------------------------------------------------- */
@@ -387,6 +392,30 @@ int oracle_gr_pairs(int nl, const double *yint, const double *k, const double *e
     for (long i = 0; i < n; ++i) {
         cplx v;
         int st = gr_pair(&m, x[i], y[i], xs[i], ys[i], tol_rel, 0, &v);
+        out_ri[2 * i] = creal(v);
+        out_ri[2 * i + 1] = cimag(v);
+        if (status) status[i] = st;
+        if (st != 0) bad = 1;
+    }
+    return bad;
+}
+
+/* As oracle_gr_pairs on a contour whose detour end T is scaled by t_scale and
+ * whose depth h by h_scale (both 1 for the default contour).  By Cauchy's theorem
+ * the integral does not depend on the contour, so any admissible scales must
+ * reproduce the default values to the quadrature tolerance: a self-check of the
+ * contour and the quadrature. */
+int oracle_gr_pairs_contour(int nl, const double *yint, const double *k, const double *eta,
+                            long n, const double *x, const double *y, const double *xs, const double *ys,
+                            double tol_rel, double t_scale, double h_scale, double *out_ri, int *status) {
+    medium_t m;
+    if (make_medium(&m, nl, yint, k, eta)) return -1;
+    if (!(t_scale >= 1.0) || !(h_scale > 0.0 && h_scale <= 1.0)) return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (long i = 0; i < n; ++i) {
+        cplx v;
+        int st = gr_pair_contour(&m, x[i], y[i], xs[i], ys[i], tol_rel, 0, t_scale, h_scale, &v);
         out_ri[2 * i] = creal(v);
         out_ri[2 * i + 1] = cimag(v);
         if (status) status[i] = st;

@@ -188,3 +188,29 @@ def test_zero_components_vanish(med3):
                     assert np.all(S[:, q] == 0)
                 else:
                     assert np.all(np.abs(S[:, q]) > 0)
+
+
+def test_sommerfeld_integral_does_not_depend_on_the_contour(med3):
+    # Cauchy's theorem: the detour's end T and depth h are choices of the quadrature, not of
+    # the quantity.  T x 1.5 and h / 2 move the contour across a region free of poles and
+    # branch points (all below T and off the fourth-quadrant detour), so the values must
+    # agree to the quadrature tolerance.  A detour that crossed a pole, or a tail that
+    # missed part of the integrand, would differ at O(1).
+    rng = np.random.default_rng(11)
+    xs, ys, xf, yf = [], [], [], []
+    for lf in range(4):
+        for ls in range(4):
+            for _ in range(3):
+                yf.append(_rand_in_layer(rng, lf, 1)[0])
+                ys.append(_rand_in_layer(rng, ls, 1)[0])
+                xf.append(rng.uniform(-2.0, 2.0))
+                xs.append(rng.uniform(-2.0, 2.0))
+    xf.append(0.4); yf.append(0.3); xs.append(0.4); ys.append(0.6)   # X = 0: real-axis tail rule
+    ref = core.gr_pairs(med3, xf, yf, xs, ys)
+    scale = np.max(np.abs(ref))
+    for t_scale, h_scale in [(1.5, 1.0), (1.0, 0.5), (1.5, 0.5)]:
+        g = core.gr_pairs_contour(med3, xf, yf, xs, ys, t_scale, h_scale)
+        err = np.abs(g - ref) / np.maximum(np.abs(ref), 1e-3 * scale)
+        assert np.max(err) <= 1e-12, (t_scale, h_scale, float(np.max(err)))
+    # the default scales are the default contour, bit for bit
+    assert np.array_equal(core.gr_pairs_contour(med3, xf, yf, xs, ys, 1.0, 1.0), ref)
