@@ -1,5 +1,8 @@
 """Plane incidence and background field (Sec. 2.2, eqs. incidentwave, homogeneousscattering).
 
+Test infrastructure only: used by tests/, the smoke check and bench.py's CPU
+baseline; the library never imports or calls it.
+
 The incident wave lives in the top layer:
     u_inc = exp(i (k0x x - k0y y)),  k0x = k0 cos(theta), k0y = k0 sin(theta) > 0,
 with theta in (0, pi) measured from the +x axis (reading of the incidence

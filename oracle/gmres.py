@@ -1,5 +1,8 @@
 """Dense GMRES (Sec. 3.3: K Phi = b solved by GMRES to a relative tolerance, Sec. 5).
 
+Test infrastructure only: used by tests/, the smoke check and bench.py's CPU
+baseline; the library never imports or calls it.
+
 Plain textbook GMRES: Arnoldi with modified Gram-Schmidt, Givens rotations
 for the Hessenberg least-squares problem, x0 = 0, no restart, optional RIGHT
 preconditioner M (so that the monitored residual is the true residual

@@ -1,5 +1,8 @@
 """Layered Green's function, plain definition (Sec. 3.1, eqs. layeredGreensfun, freegreensfun).
 
+Test infrastructure only: used by tests/, the smoke check and bench.py's CPU
+baseline; the library never imports or calls it.
+
 G_{ll'}(r, r') = delta_{ll'} (i/4) H_0^(1)(k_l |r - r'|) + G^r_{ll'}(r, r')
 
 r = (x, y) is the field point (layer l), r' = (xs, ys) the source point

@@ -1,5 +1,8 @@
 """Lowest-order Nystrom discretisation, plain dense form (Sec. 3.3).
 
+Test infrastructure only: used by tests/, the smoke check and bench.py's CPU
+baseline; the library never imports or calls it.
+
 Boundaries are split into straight elements (chords between consecutive
 polygon vertices); the density is constant on each element and collocated at
 the element centre, read as the chord midpoint with weight |Gamma_e| = chord

@@ -1,5 +1,8 @@
 """The paper's own closed forms, written out as printed (with the readings noted).
 
+Test infrastructure only: used by tests/, the smoke check and bench.py's CPU
+baseline; the library never imports or calls it.
+
 Used only to pin the paper's formulas against the oracle's direct interface
 solves (core.spectral_amp, background.background_coefficients).  Everything is
 in the paper's absolute coordinates (waves e^{+- i k_y y}), so it is evaluated
