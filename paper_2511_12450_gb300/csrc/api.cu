@@ -1,4 +1,19 @@
 // api.cu -- the C ABI (include/lfmm.h): validation, handles, host/device marshalling.
+//
+// The passages each entry point follows:
+//   lfmm_medium_create     Sec. 2.1 (layers between interfaces y = -d_l, wavenumbers k_l,
+//                          densities eta_l; eq. TLhelmholtztotallayer1)
+//   lfmm_geometry_build    Sec. 3.3 (straight elements collocated at their centres,
+//                          eq. linearSystem), Sec. 4.1 (tree and interaction lists, the
+//                          moment tables of eq. generalintegral), Sec. 4.2 (the local
+//                          matrices of eq. localmatix for the preconditioner)
+//   lfmm_rhs_plane_wave    Sec. 2.2 (eqs. incidentwave, homogeneousscattering), scaled as
+//                          b = eta g (eq. matrixandvec)
+//   lfmm_matvec            eq. Llayerscomponent (Sec. 3.3), the near part stored and the
+//                          far part by the FMM of Sec. 4.1
+//   lfmm_gmres_solve       Sec. 3.3 (GMRES on eq. EquationSet) with the preconditioner of
+//                          Sec. 4.2, tolerance as in Sec. 5
+//   lfmm_eval_field        eq. integralrep
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,4 +1,11 @@
 // fmm.cu -- set-up and application of the far field (Sec. 4.1).
+//
+// Set-up: the free-space Graf shift vectors (multipole-to-multipole as in eq. metome,
+// local-to-local as in eq. letole1, multipole-to-local with (i/4) H_{m-n}), the
+// reaction components' moment tables I_nm of eq. generalintegral (one per distinct
+// box-pair geometry, on the GPU), and the M2L descriptors and work items.
+// Application (fmm_apply): P2M (eqs. MEformula, MEcoefficients), M2M, M2L (free space,
+// and eq. metoleimage for every reaction component), L2L, L2P (eq. LEformula).
 #include <cuda_runtime.h>
 
 #include <algorithm>

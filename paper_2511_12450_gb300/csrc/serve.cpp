@@ -1,4 +1,7 @@
 // serve.cpp -- a request loop for scattering solves (lfmm_server_* in include/lfmm.h).
+// Each request is one solve of the paper's problem (Sec. 2, the system of Sec. 3.3 by
+// GMRES with the preconditioner of Sec. 4.2); the loop itself has no counterpart in
+// the paper, which solves one problem at a time.
 //
 // Requests (a layer stack, scatterer elements, an incidence angle, a tolerance,
 // the precision, the operator: single layer or combined field) queue in arrival
