@@ -84,3 +84,43 @@ def test_c5_stream_recipe():
         if wl.medium.n_layers > 1:
             assert min(_clearance(b, wl.medium.interfaces) for b in wl.bodies) >= 1e-6
     assert [wl.n_elements for wl in reqs] == [wl.n_elements for wl in config_c5_stream(8)]
+
+
+def _polar_residual(poly, c, a, b, kk, th0):
+    d = poly - np.asarray(c)[None, :]
+    r, th = np.hypot(d[:, 0], d[:, 1]), np.arctan2(d[:, 1], d[:, 0])
+    return np.max(np.abs(r - (a * np.sin(kk * (th - th0)) + b)))
+
+
+def test_paper_example_geometries():
+    # Sec. 5: the L-shape of Example 1, the peanuts of Example 2 and the flowers of Example 3
+    # (r = a sin k (theta - theta0) + b about each centre), at the replay sizes
+    from workloads import example1, example2, example3
+
+    e1 = example1(12000)
+    L = e1.bodies[0]
+    assert L.shape[0] == 12000
+    assert np.isclose(np.sum(np.hypot(*(np.roll(L, -1, axis=0) - L).T)), 12.5)   # perimeter
+    assert np.isclose(_signed_area(L), 1.5 * 3.25 + 1.5 * 1.0)                  # area, counter-clockwise
+    e2, e3 = example2(12000), example3(12000)
+    for b, c in zip(e2.bodies, [(0.0, -1.0), (2.0, -3.0)]):
+        assert _polar_residual(b, c, 0.5, 1.0, 2, np.pi / 4) < 1e-12
+    centres = [(-1.5, 0.0), (1.5, 0.0), (0.0, -2.0), (-1.5, -4.0), (1.5, 4.0)]
+    for b, c in zip(e3.bodies, centres):
+        assert _polar_residual(b, c, 0.2, 0.7, 5, 0.0) < 1e-12
+    for wl in (e1, e2, e3):
+        assert all(_signed_area(b) > 0 for b in wl.bodies)
+        for i in range(len(wl.bodies)):
+            for j in range(i):   # disjoint bodies
+                d = np.hypot(wl.bodies[i][:, None, 0] - wl.bodies[j][None, :, 0],
+                             wl.bodies[i][:, None, 1] - wl.bodies[j][None, :, 1])
+                assert d.min() > 0.1
+    # every element centre (chord midpoint, the collocation point) of every replay size keeps
+    # clear of the interfaces; vertices may lie on them (the L-shape's do)
+    for make in (example1, example2, example3):
+        for n in (12000, 24000, 48000, 96000, 192000):
+            wl = make(n)
+            mid = np.concatenate([0.5 * (b + np.roll(b, -1, axis=0)) for b in wl.bodies])
+            gap = np.min(np.abs(mid[:, 1][:, None] - np.asarray(wl.medium.interfaces)[None, :]))
+            assert gap >= 1e-6, (make.__name__, n, gap)
+            assert wl.n_elements == n
