@@ -47,7 +47,7 @@ __host__ __device__ __forceinline__ void cfma(cd& a, cd b, cd c) {
     a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
     a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
 }
-__device__ __forceinline__ cd cexpd(cd z) {
+__host__ __device__ __forceinline__ cd cexpd(cd z) {
     double s, c;
     sincos(z.y, &s, &c);
     double e = exp(z.x);
@@ -73,7 +73,7 @@ __host__ __device__ __forceinline__ cd ky_of(double k, cd lam) {
     return s;
 }
 // w(lambda, k) = (k_y + i lambda) / k   (Sec. 4.1, Proposition)
-__device__ __forceinline__ cd w_of(cd kyv, cd lam, double k) {
+__host__ __device__ __forceinline__ cd w_of(cd kyv, cd lam, double k) {
     return mk((kyv.x - lam.y) / k, (kyv.y + lam.x) / k);
 }
 
@@ -160,7 +160,7 @@ __device__ inline void bessel_j_seq_small(double x, int p, double* out) {
 // Hankel functions H_n^(1)(x) for n = 0..p by forward recurrence from
 // H_0 = J_0 + i Y_0 and H_1 = J_1 + i Y_1 (forward recurrence is stable for
 // the dominant Y_n; the J_n part is negligible there).  x > 0.
-__device__ inline void hankel_seq(double x, int p, cd* out) {
+__host__ __device__ inline void hankel_seq(double x, int p, cd* out) {
     out[0] = mk(j0(x), y0(x));
     if (p >= 1) out[1] = mk(j1(x), y1(x));
     for (int n = 1; n < p; ++n) {
@@ -196,7 +196,7 @@ struct MediumDev {
 //                             e^{i k_{l,y} h_*(y)} e^{i k_{l',y} h_star(y')} d lambda
 // with h_up(y) = y - y_l (field point above its bottom interface), h_down(y) =
 // y_{l-1} - y, and at the source h_up(y') = y_{l'-1} - y', h_down(y') = y' - y_{l'}.
-__device__ inline cd sigma_comp(const MediumDev& m, cd lam, int ls, int a, int lt, int b) {
+__host__ __device__ inline cd sigma_comp(const MediumDev& m, cd lam, int ls, int a, int lt, int b) {
     const int L = m.nl - 1;
     cd kyv[LFMM_MAXLAY], e[LFMM_MAXLAY];
     for (int q = 0; q <= L; ++q) {
@@ -271,7 +271,7 @@ __device__ inline cd sigma_comp(const MediumDev& m, cd lam, int ls, int a, int l
 }
 
 // e^{i k_y h} for real h (h may be slightly negative for box centres)
-__device__ __forceinline__ cd eikh(cd kyv, double h) {
+__host__ __device__ __forceinline__ cd eikh(cd kyv, double h) {
     return cexpd(mk(-kyv.y * h, kyv.x * h));
 }
 
