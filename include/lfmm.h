@@ -228,11 +228,13 @@ lfmm_status lfmm_matvec_static(lfmm_geometry g, const void *x, void *y, void *st
 /*
  * Solve K x = b by GMRES (x0 = 0), right-preconditioned by the overlapping
  * domain-decomposition preconditioner when prm->precond is set (Sec. 4.2).
- * Several columns with the FP64 operator advance together -- one Krylov space
- * per column, every step one block matvec of the active columns -- when their
- * bases fit in a quarter of the free device memory; each column's result equals
- * its separate solve.  Returns LFMM_NOT_CONVERGED (with the best iterate in x and
- * info filled) if max_iter is reached.
+ * Several columns with the FP64 operator and full GMRES (restart 0) advance
+ * together -- one Krylov space per column, every step one block matvec of the
+ * active columns -- when their bases fit in a quarter of the free device memory;
+ * each column's result equals its separate solve.  Otherwise columns are solved
+ * one after another.  b and x are complex128, in host or device memory.  Returns
+ * LFMM_NOT_CONVERGED (with the best iterate in x and info filled) if max_iter is
+ * reached.
  */
 lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void *b, void *x,
                              const lfmm_gmres_params *prm, lfmm_gmres_info *info,
@@ -241,10 +243,12 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void *b, void 
 /*
  * Scattered field u^s at m off-boundary targets from the density Phi
  * (eq. integralrep):  u^s(r) = (1/eta_{l(r)}) sum_e Phi_e |Gamma_e| G_{l_e l(r)}(c_e, r).
- *   density : [n x nrhs] complex Phi
+ *   density : [n x nrhs] complex Phi (host or device memory)
  *   targets : 2m doubles (host)
- *   u       : [m x nrhs] complex output
- * A target on an interface returns LFMM_ERR_NODE_ON_INTERFACE.
+ *   u       : [m x nrhs] complex output (host or device memory)
+ *   flags   : LFMM_C64 for single-precision density and u, else 0
+ * The field is summed directly over all elements (no FMM).  A target on an
+ * interface returns LFMM_ERR_NODE_ON_INTERFACE.  Synchronises the stream.
  */
 lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void *density, int64_t m,
                             const double *targets, void *u, int32_t flags, void *stream);
