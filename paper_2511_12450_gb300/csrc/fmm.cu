@@ -165,7 +165,6 @@ static void build_m2l_work(lfmm_geometry_s* g, const std::vector<int>& vr_ptr, c
                            const std::vector<int>& vr_key, const std::vector<int>& vr_comp,
                            const std::vector<int>& vr_flip, const std::vector<ReactKey>& keys) {
     TreeHost& t = g->tree;
-    const int D = t.D, l0 = t.l0, nlev = D + 1;
     std::vector<M2LEnt> ents;
     std::vector<int> ent_ptr(t.nbox + 1, 0);
     for (int T = 0; T < t.nbox; ++T) {
@@ -597,7 +596,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
                cudaEvent_t before_l2p) {
     set_smem_limits();
     TreeHost& t = g->tree;
-    const int D = t.D, l0 = t.l0, nlev = D + 1;
+    const int D = t.D, l0 = t.l0;
     if (l0 > D) return;
     ensure_coef(g, nrhs);
     const int pD = t.p_level[D];

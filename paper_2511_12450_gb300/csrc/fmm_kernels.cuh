@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
     const int c = K.comp;
     const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
     const int pS = K.pS, pT = K.pT;
-    const int ncS = 2 * pS + 1, ncT = 2 * pT + 1;
+    const int ncT = 2 * pT + 1;
     const double ka = med.k[ls], kb = med.k[lt];
     // nodes in batches of NB = 256 (all threads evaluate the spectral density, one
     // node each), then in chunks of CH for the power tables and the tile update

@@ -173,9 +173,9 @@ __global__ void k_scale_by_norm(const cd* __restrict__ in, const cd* __restrict_
     const double h = sqrt(fmax(nrm2[0].x, 0.0));
     if (i < n && h > 0.0) out[i] = (1.0 / h) * in[i];
 }
-__global__ void k_axpby(const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ out, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // out = a - b
-    if (i < n) out[i] = a[i] - b[i];
+__global__ void k_sub_from(const cd* __restrict__ a, cd* y, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // y = a - y (a residual in place)
+    if (i < n) y[i] = a[i] - y[i];
 }
 
 struct Blas {
@@ -526,7 +526,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
             for (int c = 0; c < nrhs; ++c) {
                 const cd* bc = b + (int64_t)c * n;
                 cd* rc = R + (int64_t)c * n;
-                k_axpby<<<nblk(n), 256, 0, s>>>(bc, rc, rc, n);
+                k_sub_from<<<nblk(n), 256, 0, s>>>(bc, rc, n);
                 const double bn = bl.norm(bc, n), rn = bl.norm(rc, n);
                 worst_true = std::max(worst_true, bn > 0.0 ? rn / bn : 0.0);
             }
@@ -549,7 +549,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
         apply_operator_sorted(g, v, y2, 1, s, true);
         apply_operator_sorted(g, v, d, 1, s);
         const double an = bl.norm(d, n);
-        k_axpby<<<nblk(n), 256, 0, s>>>(y2, d, d, n);
+        k_sub_from<<<nblk(n), 256, 0, s>>>(y2, d, n);
         const double dn = bl.norm(d, n);
         return an > 0.0 ? dn / an : 0.0;
     };
@@ -562,7 +562,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
         if (precision == 0 && restart == 0) {
             ok = gmres_one(g, bc, xc, tol, maxit, pre, s, &it, &res);
             apply_operator_sorted(g, xc, r, 1, s);
-            k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+            k_sub_from<<<nblk(n), 256, 0, s>>>(bc, r, n);
             rn = bl.norm(r, n);
             f64 = 1;
         } else if (precision == 0) {
@@ -580,7 +580,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
                 f64 += its;
                 k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
                 apply_operator_sorted(g, xc, r, 1, s);
-                k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+                k_sub_from<<<nblk(n), 256, 0, s>>>(bc, r, n);
                 ++f64;
                 ++outer;
                 rn = bl.norm(r, n);
@@ -610,7 +610,7 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
                 f64 += its - msteps;
                 k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
                 apply_operator_sorted(g, xc, r, 1, s);
-                k_axpby<<<nblk(n), 256, 0, s>>>(bc, r, r, n);
+                k_sub_from<<<nblk(n), 256, 0, s>>>(bc, r, n);
                 ++f64;
                 ++outer;
                 const double rn_new = bl.norm(r, n);
