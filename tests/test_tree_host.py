@@ -129,3 +129,16 @@ def test_four_layer_and_wide_band_trees_are_bit_exact(harness):
     for p, leaf in [(20, 8), (6, 3)]:
         Tw = otree.Tree(ptsw, ww.medium.interfaces, ww.medium.k, p=p, leaf_size=leaf)
         _compare(_run(harness, ptsw, ww.medium, p, leaf, f"wide{p}"), Tw)
+
+
+def test_largest_workload_tree_is_bit_exact(harness):
+    # the precision form's workload: N = 1,048,576 in four layers (k up to 12), 150k boxes,
+    # depth 11, expansions from level 4 (order 75) down to order 20, 36 reaction components
+    from workloads import config_c3
+
+    wl = config_c3()
+    pts, _, _, _ = onys.elements(wl.bodies)
+    h = _run(harness, pts, wl.medium, wl.p, wl.leaf_size, "c3")
+    T = otree.Tree(pts, wl.medium.interfaces, wl.medium.k, p=wl.p, leaf_size=wl.leaf_size)
+    assert pts.shape[0] == 1 << 20 and T.D == 11 and T.l0 == 4 and len(T.comps) == 36
+    _compare(h, T)
