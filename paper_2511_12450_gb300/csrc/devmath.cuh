@@ -280,7 +280,7 @@ __host__ __device__ __forceinline__ cd eikh(cd kyv, double h) {
 // double layer n_e . grad_{c_e} (i/4) H_0(k |c_e - c_i|) = -(i/4) k H_1(k r)
 // n_e . (c_e - c_i) / r plus -i kappa (i/4) H_0(k r) with the coupling kappa = k
 // of the element's layer.  (dx, dy) = c_e - c_i != 0; (nx, ny) is n_e.
-__device__ __forceinline__ cd free_kernel(double k, double dx, double dy, bool cf, double nx, double ny) {
+__host__ __device__ __forceinline__ cd free_kernel(double k, double dx, double dy, bool cf, double nx, double ny) {
     const double r = hypot(dx, dy), z = k * r;
     const cd g = mk(-0.25 * y0(z), 0.25 * j0(z));   // (i/4)(J_0 + i Y_0)
     if (!cf) return g;
@@ -290,7 +290,7 @@ __device__ __forceinline__ cd free_kernel(double k, double dx, double dy, bool c
 // Diagonal entry: the single-layer self term I^s (eq. ApproximateComputation) or,
 // for the combined field, 1/2 (the exterior jump of the double layer; the double
 // layer of a straight element on its own centre vanishes) - i k I^s.
-__device__ __forceinline__ cd self_entry(double k, double w, bool cf) {
+__host__ __device__ __forceinline__ cd self_entry(double k, double w, bool cf) {
     const double eg = 0.57721566490153286060651209008240243;
     const cd is = mk(-(eg + log(k * w / 4.0) - 1.0) / (2.0 * M_PI) * w, 0.25 * w);
     if (!cf) return is;

@@ -10,6 +10,12 @@
 //   devmath_harness bessel <input> <output>
 //     input : int32 nx, p; float64 x[nx]
 //     output: nx x (p+1) float64 J_n(x), then nx x (p+1) complex128 H_n^(1)(x)
+//   devmath_harness free <input> <output>
+//     input : int32 nq; nq x float64 (k, dx, dy, cf, nx, ny)   (cf: 0 or 1)
+//     output: nq x complex128 free-space Nystrom kernel values
+//   devmath_harness self <input> <output>
+//     input : int32 nq; nq x float64 (k, w, cf)
+//     output: nq x complex128 diagonal entries
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -59,9 +65,33 @@ static int run_bessel(FILE* in, FILE* out) {
     return 0;
 }
 
+static int run_free(FILE* in, FILE* out) {
+    int32_t nq = 0;
+    if (!rd(in, &nq, 1) || nq < 0) return 2;
+    for (int i = 0; i < nq; ++i) {
+        double q[6];
+        if (!rd(in, q, 6)) return 2;
+        const cd v = free_kernel(q[0], q[1], q[2], q[3] != 0.0, q[4], q[5]);
+        std::fwrite(&v, sizeof(cd), 1, out);
+    }
+    return 0;
+}
+
+static int run_self(FILE* in, FILE* out) {
+    int32_t nq = 0;
+    if (!rd(in, &nq, 1) || nq < 0) return 2;
+    for (int i = 0; i < nq; ++i) {
+        double q[3];
+        if (!rd(in, q, 3)) return 2;
+        const cd v = self_entry(q[0], q[1], q[2] != 0.0);
+        std::fwrite(&v, sizeof(cd), 1, out);
+    }
+    return 0;
+}
+
 int main(int argc, char** argv) {
     if (argc != 4) {
-        std::fprintf(stderr, "usage: devmath_harness sigma|bessel <input> <output>\n");
+        std::fprintf(stderr, "usage: devmath_harness sigma|bessel|free|self <input> <output>\n");
         return 2;
     }
     FILE* in = std::fopen(argv[2], "rb");
@@ -70,6 +100,8 @@ int main(int argc, char** argv) {
     int rc = 2;
     if (std::strcmp(argv[1], "sigma") == 0) rc = run_sigma(in, out);
     else if (std::strcmp(argv[1], "bessel") == 0) rc = run_bessel(in, out);
+    else if (std::strcmp(argv[1], "free") == 0) rc = run_free(in, out);
+    else if (std::strcmp(argv[1], "self") == 0) rc = run_self(in, out);
     std::fclose(in);
     std::fclose(out);
     return rc;

@@ -134,3 +134,51 @@ def test_bessel_and_hankel_sequences_against_scipy(harness):
     ok = np.isfinite(Href) & (np.abs(Href) < 1e250)
     errH = np.abs(H - Href) / np.abs(Href)
     assert np.max(errH[ok]) <= 1e-12, float(np.max(errH[ok]))
+
+
+def test_free_space_entries_equal_the_oracles(harness):
+    # single layer (i/4) H_0(k r) and the combined field's n_e . grad_{c_e} (i/4) H_0 - i k (i/4) H_0
+    # (Sec. 3.3; the combined-field reading), (dx, dy) = c_e - c_i, against oracle/nystrom.gf and
+    # oracle/combined.grad_free
+    from oracle import combined as ocf
+    from oracle import nystrom as onys
+
+    rng = np.random.default_rng(50)
+    m = 400
+    k = rng.uniform(1.0, 12.0, m)
+    r = np.geomspace(1e-4, 30.0, m)
+    th = rng.uniform(0, 2 * np.pi, m)
+    dx, dy = r * np.cos(th), r * np.sin(th)
+    ph = rng.uniform(0, 2 * np.pi, m)
+    nx, ny = np.cos(ph), np.sin(ph)
+    for cf in (0.0, 1.0):
+        q = np.stack([k, dx, dy, np.full(m, cf), nx, ny], axis=1)
+        out = _call(harness, "free", np.array([m], np.int32).tobytes() + q.tobytes(), f"free{int(cf)}")
+        got = np.frombuffer(out, np.complex128)
+        g = np.array([onys.gf(k[i], r[i]) for i in range(m)])
+        if cf:
+            ce = np.stack([dx, dy], axis=1)
+            grad = [ocf.grad_free(k[i], ce[i:i + 1], np.zeros((1, 2))) for i in range(m)]
+            want = np.array([nx[i] * gx[0, 0] + ny[i] * gy[0, 0] for i, (gx, gy) in enumerate(grad)]) - 1j * k * g
+        else:
+            want = g
+        err = np.abs(got - want) / np.abs(want)
+        assert np.max(err) <= 1e-12, (cf, float(np.max(err)))
+
+
+def test_diagonal_entries_equal_the_oracles(harness):
+    # I^s = [i/4 - (1/2 pi)(gamma + ln(k w / 4) - 1)] w (eq. ApproximateComputation), and the
+    # combined field's 1/2 - i k I^s
+    from oracle import nystrom as onys
+
+    rng = np.random.default_rng(51)
+    m = 200
+    k = rng.uniform(1.0, 12.0, m)
+    w = np.geomspace(1e-5, 0.5, m)
+    for cf in (0.0, 1.0):
+        q = np.stack([k, w, np.full(m, cf)], axis=1)
+        out = _call(harness, "self", np.array([m], np.int32).tobytes() + q.tobytes(), f"self{int(cf)}")
+        got = np.frombuffer(out, np.complex128)
+        Is = onys.self_term(k, w)
+        want = 0.5 - 1j * k * Is if cf else Is
+        assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-13
