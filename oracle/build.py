@@ -12,7 +12,8 @@ LIB = os.path.join(HERE, "_oracle_core.so")
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", SRC, "-o", LIB, "-lm"]
+    # -ffp-contract=off: the same IEEE rounding on x86 and aarch64 (GCC contracts a*b+c there)
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", SRC, "-o", LIB, "-lm"]
     subprocess.run(cmd, check=True)
     return LIB
 

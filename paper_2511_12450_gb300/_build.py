@@ -14,7 +14,11 @@ LIB = os.path.join(OUT_DIR, "liblfmm.so")
 SOURCES = ["api.cu", "near.cu", "fmm.cu", "solver.cu", "precond.cu", "tree.cpp", "static_scratch.cu", "mixed.cu", "serve.cpp"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--default-stream", "per-thread", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
+# host code without contraction of a*b+c into FMA (GCC's default on aarch64, not on x86): the
+# tree builder's quantisation, order and near/far decisions then round as the oracle's numpy
+# does on both machines; device code is unaffected (nvcc's --fmad governs it)
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--default-stream", "per-thread", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+         "-Xcompiler", "-ffp-contract=off"]
 
 
 def _newest_input() -> float:

@@ -35,7 +35,7 @@ def harness():
         pytest.skip("needs a C++ compiler and the CUDA headers")
     os.makedirs(WORK, exist_ok=True)
     exe = os.path.join(WORK, "devmath_harness")
-    res = subprocess.run([cxx, "-std=c++17", "-O2", "-Wall", "-I", inc, "-I", CSRC,
+    res = subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-Wall", "-I", inc, "-I", CSRC,
                           os.path.join(ROOT, "tests", "devmath_harness.cpp"), "-o", exe],
                          capture_output=True, text=True)
     assert res.returncode == 0, res.stderr

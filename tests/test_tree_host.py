@@ -37,7 +37,7 @@ def harness():
         pytest.skip("needs a C++ compiler and the CUDA headers")
     os.makedirs(WORK, exist_ok=True)
     exe = os.path.join(WORK, "tree_harness")
-    cmd = [cxx, "-std=c++17", "-O2", "-Wall", "-I", inc, "-I", CSRC, os.path.join(ROOT, "tests", "tree_harness.cpp"),
+    cmd = [cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-Wall", "-I", inc, "-I", CSRC, os.path.join(ROOT, "tests", "tree_harness.cpp"),
            os.path.join(CSRC, "tree.cpp"), "-o", exe]
     res = subprocess.run(cmd, capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
