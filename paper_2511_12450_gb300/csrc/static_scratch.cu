@@ -2,7 +2,7 @@
 //
 // Some callers cannot allocate device memory at the moment they need a matvec:
 // real-time serving threads that must not enter the allocator (cudaMalloc can
-// block on the driver's memory manager and synchronise the device), hosts that
+// block in the CUDA memory manager and synchronise the device), hosts that
 // hand the library a fixed memory budget up front, and frameworks whose own pool
 // owns the device memory, where an allocation outside it may fail or fragment.  lfmm_matvec lazily allocates its
 // work buffers (sorted copies of x and y, the multipole and local coefficients)
