@@ -35,8 +35,14 @@ framework without giving its parameters; this is the reading used here):
     Sec. 3.2).  A box's reaction expansion centre is its cell centre, moved
     for a cell that straddles that interface to the middle of the part of the
     cell on the layer's side (cell bounds lo = y0 + iy w, hi = y0 + (iy+1) w);
-    a candidate is far (M2L) if its cell column differs from T's by at least 2
-    or D >= 2 w_l (1 - 1e-9), otherwise near.
+    a candidate is far (M2L) if D >= 2 w_l (1 - 1e-9), or if its cell column
+    differs from T's by at least 2 while |k_y(T')| (w_l - D) <= 16, with
+    T' = k_max + 0.75 (where the moment tables' contour leaves the real axis)
+    and k_y = sqrt(T'^2 - k^2) for the smaller wavenumber of the two layers;
+    otherwise near.  (The second bound keeps the spectral integrand of the
+    pair's moment table bounded; the paper's admissibility by the effective
+    distance alone does not say how far apart horizontally separated boxes
+    must be.)
 """
 
 from __future__ import annotations
@@ -48,6 +54,7 @@ import numpy as np
 QBITS = 20
 D_CAP = 18
 P_CAP = 80
+COND_EXP = 16.0   # bound on log of the moment-table integrand growth of column-separated pairs
 L0_MIN = 2
 
 
@@ -138,6 +145,7 @@ class Tree:
         self.L = len(self.yint)
         self.n = pts.shape[0]
         self.layer = layer_of(self.yint, pts[:, 1])
+        self.k = [float(v) for v in np.asarray(k, dtype=np.float64).reshape(-1)]
         xmin, xmax = float(pts[:, 0].min()), float(pts[:, 0].max())
         ymin, ymax = float(pts[:, 1].min()), float(pts[:, 1].max())
         ext = max(xmax - xmin, ymax - ymin)
@@ -262,9 +270,20 @@ class Tree:
             comp_extra_thickness(self.yint, self.comps[c])
 
     def _reaction_lists(self):
+        # A pair that only the column offset separates is admitted while the spectral
+        # integrand of its moment table stays bounded: on the real stretch of the
+        # contour, up to T' = k_max + 0.75, the expansions' vertical extent (at most
+        # w / 2 on either side) against the effective distance D lets it grow like
+        # exp(|k_y(T')| (w - D)), k_y for the smaller of the two layers' wavenumbers.
+        # The bound exp(16) keeps the cancellation in the tables far below the
+        # truncation error; larger growth (wide-band cells with D << w) lost up to
+        # 3e-5 of an entry in the four-layer medium k = 6, 10, 8, 12.
         self.V_react = []
         self.U_react = []
+        t_tab = max(self.k) + 0.75
         for c, (ls, a, lt, b) in enumerate(self.comps):
+            kl = min(self.k[ls], self.k[lt])
+            ky_tab = math.sqrt(t_tab * t_tab - kl * kl)
             near = {}
             V = {}
             for l in range(self.D + 1):
@@ -280,7 +299,8 @@ class Tree:
                             nl.append(S)
                             continue
                         Dc = self.comp_D(c, S, T)
-                        far = abs(self.box_ix[S] - self.box_ix[T]) >= 2 or Dc >= 2.0 * w * (1.0 - 1e-9)
+                        far = (abs(self.box_ix[S] - self.box_ix[T]) >= 2 and ky_tab * (w - Dc) <= COND_EXP) or \
+                            Dc >= 2.0 * w * (1.0 - 1e-9)
                         (vl if far else nl).append(S)
                     near[T] = nl
                     if vl:

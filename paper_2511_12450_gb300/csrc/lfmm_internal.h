@@ -46,6 +46,13 @@ struct TreeHost {
 void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<double>& py,
                 const std::vector<int>& layer, const MediumDev& med, int p, int leaf_size);
 
+// End of the real-axis stretch of the moment tables' contour, just past the largest
+// branch point (the M2L table rule and the tree's admissibility test share it).
+inline double table_detour_end(const MediumDev& m) { return m.kmax + 0.75; }
+// Largest admitted log-growth of a column-separated reaction pair's table integrand
+// (tree.cpp, reaction lists).
+constexpr double REACT_COND_EXP = 16.0;
+
 double comp_extra_thickness(const MediumDev& m, int ls, int a, int lt, int b);
 double src_height(const MediumDev& m, int ls, int a, double y);
 double tgt_height(const MediumDev& m, int lt, int b, double y);

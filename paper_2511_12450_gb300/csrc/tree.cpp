@@ -19,8 +19,14 @@
 //    D = h_*(S) + h_star(T) + H_c (the effective transmission distance of
 //    Sec. 3.2 between the reaction expansion centres: cell centres, moved for
 //    cells that straddle the interface to the middle of the part of the cell
-//    on the layer's side).  A pair is far if the column offset is at least 2
-//    or D >= 2 w_l.
+//    on the layer's side).  A pair is far if D >= 2 w_l, or if the column
+//    offset is at least 2 while |k_y(T')| (w_l - D) <= 16, T' = k_max + 0.75
+//    the end of the moment tables' real-axis stretch, k_y for the smaller of
+//    the two layers' wavenumbers: on that stretch the table integrand grows
+//    like exp(|k_y| (w - D)) (the expansions' vertical extent, up to w / 2 on
+//    each side, against the effective distance), and beyond exp(16) the
+//    cancellation in the table costs accuracy (up to 3e-5 of an entry in the
+//    four-layer medium k = 6, 10, 8, 12, wide-band cells with D << w).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -249,8 +255,11 @@ void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<do
         }
     const int nc = (int)t.comps.size();
     std::vector<std::vector<std::pair<int, int>>> vr(nb), ur(nb);  // (comp, S)
+    const double t_tab = table_detour_end(med);
     for (int c = 0; c < nc; ++c) {
         const Component& C = t.comps[c];
+        const double kl = std::min(med.k[C.ls], med.k[C.lt]);
+        const double ky_tab = std::sqrt(t_tab * t_tab - kl * kl);
         std::vector<std::vector<int>> nearl(nb);
         for (int l = 0; l <= D; ++l) {
             double w = t.width(l);
@@ -270,7 +279,8 @@ void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<do
                     double loT = t.y0 + t.box_iy[T] * w, hiT = t.y0 + (t.box_iy[T] + 1) * w;
                     double Dc = (src_height_box(med, C.ls, C.a, loS, hiS) + tgt_height_box(med, C.lt, C.b, loT, hiT)) +
                                 C.Hc;
-                    bool far = std::abs(t.box_ix[S] - t.box_ix[T]) >= 2 || Dc >= 2.0 * w * (1.0 - 1e-9);
+                    bool far = (std::abs(t.box_ix[S] - t.box_ix[T]) >= 2 && ky_tab * (w - Dc) <= REACT_COND_EXP) ||
+                               Dc >= 2.0 * w * (1.0 - 1e-9);
                     if (far) vr[T].push_back({c, S});
                     else nearl[T].push_back(S);
                 }

@@ -27,4 +27,5 @@ from .geometry import (  # noqa: F401
     random_bodies,
     layered_small,
     layered_wide,
+    layered_wide_c3,
 )

@@ -299,3 +299,19 @@ def layered_wide(n_bodies: int = 5, nodes: int = 80, seed: int = 21) -> Workload
         if any(_crosses(p, med.interfaces) for p in polys):
             break
     return Workload("wide_c2_medium", med, polys, np.array([45.0]), p=20, leaf_size=8)
+
+
+def layered_wide_c3(n_bodies: int = 10, nodes: int = 48, seed: int = 53) -> Workload:
+    """Few small bodies spread over the region of the million-point four-layer workload
+    (interfaces y = 0, -6, -12; k = 6, 10, 8, 12; region [-40, 40] x [-18, 6]): its
+    wide-band levels (orders up to 75) and straddling cells at a size the oracle can
+    still evaluate densely."""
+    med = Medium(interfaces=[0.0, -6.0, -12.0], k=[6.0, 10.0, 8.0, 12.0], eta=[1.0, 2.0, 3.0, 4.0])
+    rng = np.random.default_rng(seed)
+    while True:
+        polys = random_bodies(rng, n_bodies, ((-40.0, 40.0), (-18.0, 6.0)), med.interfaces, nodes,
+                              rmin=0.2, rmax=0.6, iface_tol=1e-3)
+        if sum(_crosses(p, med.interfaces) for p in polys) >= 2:
+            break
+    return Workload("wide_c3_medium", med, polys, np.array([45.0]), p=20, leaf_size=8)
+
