@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the million-point four-layer workload block")
     ap.add_argument("--autotune", type=int, default=0,
                     help="1: choose the M2L work-item schedule by timing at set-up")
     ap.add_argument("--replay", action="store_true",
@@ -295,6 +296,75 @@ def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
                         f"latency under Poisson arrivals at 1.5x the FP64 one-at-a-time capacity "
                         f"({rate:.2f} requests/s); tol 1e-8 on the FP64 residual",
             "hbm_budget_bytes": budget, **out}
+
+
+def run_c3(lfmm, steps=5):
+    """The precision form's own workload, C3: four layers (interfaces y = 0, -6, -12; k = 6, 10,
+    8, 12; eta = 1..4), 1024 circles/ellipses x 1024 nodes over [-40, 40] x [-18, 6] (seed
+    12453), N = 1,048,576, p = 20.  Set-up time, the FP64 and precision-form matvec (L2 flushed,
+    CUDA events, median), the errors of both against the 64 stored oracle rows (x non-zero on a
+    seeded 4k-point subset) and of the precision form against FP64 on a dense random x, and the
+    per-stage times of each operator."""
+    import torch
+
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_c3_sampled_rows as gen
+    from workloads import config_c3
+
+    wl = config_c3()
+    med = wl.medium
+    M = lfmm.medium_create(med.interfaces, med.k, med.eta)
+    pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+    t0 = time.perf_counter()
+    G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size, profile=True)
+    setup_s = time.perf_counter() - t0
+    n = G.n
+    with open(os.path.join(ROOT, "tests", "golden", "c3_sampled_rows.json")) as f:
+        fx = json.load(f)
+    cols, xs, rows = gen.sample(n)
+    ref = np.array([complex(*v) for v in fx["y"]])
+    xsp = np.zeros(n, dtype=np.complex128)
+    xsp[cols] = xs
+    xsp = torch.from_numpy(xsp).cuda()
+    gen_t = torch.Generator(device="cpu").manual_seed(77)
+    x = torch.complex(torch.randn(n, generator=gen_t, dtype=torch.float64),
+                      torch.randn(n, generator=gen_t, dtype=torch.float64)).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "C3: 4 layers (y=0,-6,-12; k=6,10,8,12; eta=1..4), 1024 circles/ellipses x 1024 nodes, "
+                       "N=1048576, p=20", "N": n, "setup_seconds": setup_s,
+           "tree": {k: float(v) for k, v in zip(["D", "l0", "boxes", "components", "near_blocks", "near_entries",
+                                                  "reaction_tables"], lfmm.geometry_query(G, "tree_params",
+                                                                                          np.float64)[3:10])}}
+    ys = {}
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        y = torch.empty_like(x)
+        for _ in range(2):
+            lfmm.matvec(G, x, y, mixed=mixed)
+        torch.cuda.synchronize()
+        st0 = lfmm.stage_times(G)
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lfmm.matvec(G, x, y, mixed=mixed)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st1 = lfmm.stage_times(G)
+        ys[name] = y
+        yr = lfmm.matvec(G, xsp, mixed=mixed).cpu().numpy()[rows]
+        err = np.abs(yr - ref) / np.abs(ref)
+        ms = float(np.median(times))
+        out[name] = {"ms_per_matvec": ms, "Mpts_per_s": n / ms / 1e3,
+                     "oracle_rows_max_rel_err": float(err.max()), "oracle_rows_median_rel_err": float(np.median(err)),
+                     "stages_ms": {k: (st1[k]["ms"] - st0[k]["ms"]) / max(st1[k]["count"] - st0[k]["count"], 1)
+                                   for k in st1}}
+    out["mixed"]["op_rel_diff_vs_fp64"] = float(torch.linalg.norm(ys["mixed"] - ys["fp64"]) /
+                                                torch.linalg.norm(ys["fp64"]))
+    G.destroy()
+    return out
 
 
 def run_batch(lfmm, index=10, steps=5):
@@ -596,6 +666,9 @@ def run_ours(args):
     if not args.no_solve:
         combined = run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n)
 
+    c3 = None
+    if rank == 0 and not args.no_c3 and args.workload == "c2":
+        c3 = run_c3(lfmm)
     batch = None
     if rank == 0 and not args.no_batch and args.workload == "c2":
         batch = run_batch(lfmm)
@@ -626,6 +699,7 @@ def run_ours(args):
             "solve": solve,
             "mixed": mixed,
             "combined_field": combined,
+            "c3": c3,
             "batch": batch,
             "serve": serve,
             "setup_seconds": setup_s,

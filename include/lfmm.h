@@ -30,8 +30,11 @@
  *    copied; outputs are caller allocated.  Handles are owned by the library
  *    until the matching _destroy.  A geometry keeps a reference to its medium:
  *    destroying a medium that still has geometries is refused.
- *  - Thread safety: calls on different geometries may run concurrently;
- *    calls on one geometry must be serialised by the caller.
+ *  - Thread safety: calls on different geometries may run concurrently.  Calls
+ *    on one geometry take the geometry's lock, so calls from several threads
+ *    enqueue their work one after another; device work they enqueue on
+ *    different streams is not ordered by the library, so a caller using one
+ *    geometry from several streams orders those streams itself.
  */
 #ifndef LFMM_H
 #define LFMM_H
@@ -66,10 +69,14 @@ enum {
     LFMM_MIXED = 2          /* lfmm_matvec: apply the precision form of the operator --
                                the far field (P2M, M2M, M2L free space and reaction, L2L,
                                L2P) in FP32 on scaled expansions on the levels whose order
-                               is at most 1.5 p; the coarser wide-band levels, the stored near
-                               field and every sum into y stay FP64.  Its relative
+                               is at most 1.5 p, and the regular near field (stored blocks
+                               that hold only free-space entries) in complex64 with FP32
+                               products.  FP64 stays for the coarser wide-band levels, the
+                               self terms I^s, the near blocks that hold reaction
+                               (Sommerfeld) entries and every sum into y.  Its relative
                                difference from the FP64 operator is a few 1e-7 (no
                                counterpart in the paper, which works in FP64 throughout).
+                               The complex64 near field is built on the first such call.
                                With 16 or more columns its M2L runs on the tensor cores
                                (3xTF32, tcgen05) */,
     LFMM_SIMT_M2L = 8,      /* with LFMM_MIXED: keep the FP32 M2L on the SIMT kernel for
@@ -203,6 +210,22 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
                         int32_t flags, void *stream);
 
 /*
+ * y = P^{-1} x, the overlapping domain-decomposition preconditioner of Sec. 4.2
+ * alone (the operator lfmm_gmres_solve applies on the right when prm->precond
+ * is set).  For every leaf box B of every layer's tree, P_B is the local matrix
+ * of eq. localmatix on the points of B and of its same-layer neighbour leaves
+ * (the free-space Nystrom entries with the self terms I^s on the diagonal); only
+ * the rows of P_B^{-1} that belong to B's own points are kept (restricted
+ * additive Schwarz), so y_B = (P_B^{-1} x_J)|_B.  Built on first use (one LU
+ * per leaf).  x and y: [n x nrhs] complex128 in host memory, or device memory
+ * with flags = LFMM_DEVICE_PTRS; they must not overlap.  Errors:
+ * LFMM_ERR_INVALID_ARG (NULL, nrhs < 1, x == y, other flags, misaligned device
+ * vectors); LFMM_ERR_CUDA or LFMM_ERR_OUT_OF_MEMORY from the set-up.
+ */
+lfmm_status lfmm_precond_apply(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
+                               int32_t flags, void *stream);
+
+/*
  * y = K x like lfmm_matvec (one right-hand side, DEVICE pointers on `stream`),
  * but allocating nothing.  The paper has no counterpart: this exists for
  * callers that cannot allocate device memory when they need a matvec --
@@ -218,6 +241,14 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
  *   - All calls share the array and it keeps the last call's contents; calls
  *     that overlap on the GPU (other streams or threads) race and must be
  *     serialised by the caller.
+ *   - While the call runs, the geometry's work-buffer fields point into the
+ *     array.  It holds the geometry's lock meanwhile, so another thread's call
+ *     on the same geometry (lfmm_matvec, lfmm_gmres_solve, ...) waits; work
+ *     such calls enqueued earlier on other streams must have finished (the
+ *     caller orders the streams).
+ *   - Errors: LFMM_ERR_INVALID_ARG for NULL, overlapping or not 8-byte aligned
+ *     vectors and for geometries whose work buffers do not fit (y is then left
+ *     untouched); LFMM_ERR_CUDA for a failed launch.
  *   - Geometries whose work buffers (sorted x and y, multipole and local
  *     coefficients, M2L partial sums) exceed the array are rejected with LFMM_ERR_INVALID_ARG
  *     before any device work (C2-sized problems, N = 65536, need about 16 MiB).
@@ -247,8 +278,17 @@ lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void *b, void 
  *   targets : 2m doubles (host)
  *   u       : [m x nrhs] complex output (host or device memory)
  *   flags   : LFMM_C64 for single-precision density and u, else 0
- * The field is summed directly over all elements (no FMM).  A target on an
- * interface returns LFMM_ERR_NODE_ON_INTERFACE.  Synchronises the stream.
+ * The field is evaluated through the same expansions as lfmm_matvec: the call
+ * builds a field geometry -- the elements followed by the m targets, which carry
+ * weight 0 and are never sources -- with the geometry's order p, leaf size and
+ * operator, and takes the targets' rows of one FMM product with [Phi; 0]
+ * (far field by P2M, M2M, M2L, L2L, L2P; near field by the stored free-space and
+ * Sommerfeld entries, built only for leaves that hold targets).  Cost: one
+ * geometry set-up over n + m points plus one product, instead of m n Sommerfeld
+ * integrals; every sum has a fixed order, so repeated calls give the same bits.
+ * Targets must lie off the boundary (a target at an element centre meets the
+ * kernel's singularity).  A target on an interface returns
+ * LFMM_ERR_NODE_ON_INTERFACE.  Synchronises the stream.
  */
 lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void *density, int64_t m,
                             const double *targets, void *u, int32_t flags, void *stream);

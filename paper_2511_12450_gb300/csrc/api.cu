@@ -20,6 +20,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -37,13 +39,6 @@ void set_error(const std::string& msg) { t_last_error = msg; }
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw CudaError{std::string(what) + ": " + cudaGetErrorString(e)};
 }
-
-struct ArgError {
-    std::string msg;
-};
-struct InterfaceError {
-    std::string msg;
-};
 
 // 8-point Gauss-Legendre rule by Newton iteration on P_8 (no stored tables)
 static void gauss_legendre8(double* x, double* w) {
@@ -92,7 +87,7 @@ QuadRule make_quad_rule(const MediumDev& m) {
     // neither the wide-band nor the C2 parity (1.2e-10, a few 1e-9) and cost 1.6x
     // the set-up time
     q.tab_panel_mult = 1;
-    q.tab_T = m.kmax + 0.75;
+    q.tab_T = table_detour_end(m);
     gauss_legendre8(q.gl_x, q.gl_w);
     return q;
 }
@@ -157,6 +152,8 @@ static lfmm_status guarded(F&& f) {
     if (st < 0) (void)cudaGetLastError();
     return st;
 }
+
+lfmm_status guarded_call(const std::function<lfmm_status()>& f) { return guarded(f); }
 
 static void require(bool c, const char* msg) {
     if (!c) throw ArgError{msg};
@@ -259,13 +256,17 @@ lfmm_status lfmm_medium_destroy(lfmm_medium m) {
     });
 }
 
-lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points, const double* weights,
-                                const double* normals, const lfmm_params* prm, lfmm_geometry* out) {
+// Builds a geometry; throws on any failure after releasing what it built.  Points with
+// input index >= n_src (n_src < n only for the field geometries of lfmm_eval_field) are
+// field points: weight 0, never a source, and only the leaves that hold them get near-field
+// blocks.
+static lfmm_geometry_s* build_geometry(lfmm_medium med, int64_t n, const double* points, const double* weights,
+                                       const double* normals, const lfmm_params* prm, int64_t n_src) {
     lfmm_geometry_s* g = nullptr;
-    lfmm_status st = guarded([&]() -> lfmm_status {
+    try {
         auto t0 = std::chrono::steady_clock::now();
-        require(med != nullptr && out != nullptr, "medium/out is NULL");
         require(n >= 1 && n < (int64_t)1 << 31, "n must be in [1, 2^31)");
+        require(n_src >= 1 && n_src <= n, "field geometry: bad element count");
         require(points != nullptr && weights != nullptr, "points/weights is NULL");
         int p = prm ? prm->p : 20;
         int leaf = prm ? prm->leaf_size : 64;
@@ -274,7 +275,7 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         const bool cf = prm && (prm->flags & LFMM_COMBINED_FIELD);
         require(!cf || normals != nullptr, "the combined-field operator needs the normals");
         if (cf)
-            for (int64_t i = 0; i < n; ++i) {
+            for (int64_t i = 0; i < n_src; ++i) {
                 const double nn = std::hypot(normals[2 * i], normals[2 * i + 1]);
                 require(std::isfinite(nn) && std::fabs(nn - 1.0) <= 1e-8, "normals must be unit vectors");
             }
@@ -286,7 +287,8 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
             py[i] = points[2 * i + 1];
             pw[i] = weights[i];
             require(std::isfinite(px[i]) && std::isfinite(py[i]), "points must be finite");
-            require(std::isfinite(pw[i]) && pw[i] > 0.0, "weights must be positive");
+            // element weights are positive; the field points of a field geometry carry weight 0
+            require(std::isfinite(pw[i]) && (i < n_src ? pw[i] > 0.0 : pw[i] == 0.0), "weights must be positive");
             int l = 0;
             while (l < m.nl - 1 && py[i] < m.yint[l]) ++l;
             layer[i] = l;
@@ -297,6 +299,7 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
             }
         }
         g = new lfmm_geometry_s();
+        g->n_src = n_src;
         g->med = med;
         g->m = m;
         g->n = n;
@@ -333,12 +336,15 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         if (cf) {
             std::vector<double> hnx(n), hny(n);
             for (int64_t s = 0; s < n; ++s) {
-                hnx[s] = normals[2 * t.perm[s]];
-                hny[s] = normals[2 * t.perm[s] + 1];
+                // field points carry no normal (weight 0, never a source)
+                hnx[s] = t.perm[s] < n_src ? normals[2 * t.perm[s]] : 1.0;
+                hny[s] = t.perm[s] < n_src ? normals[2 * t.perm[s] + 1] : 0.0;
             }
             g->combined = true;
             g->d_nx = dupload(g, hnx);
             g->d_ny = dupload(g, hny);
+            g->hnx = std::move(hnx);
+            g->hny = std::move(hny);
         }
         g->d_layer = dupload(g, t.layer_sorted);
         g->d_perm = dupload(g, t.perm);
@@ -368,16 +374,26 @@ lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points
         fmm_build(g);
         if (prm && (prm->flags & LFMM_AUTOTUNE)) fmm_autotune(g);
         g->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return g;
+    } catch (...) {
+        if (g) {
+            free_geometry(g);
+            delete g;
+        }
+        throw;
+    }
+}
+
+lfmm_status lfmm_geometry_build(lfmm_medium med, int64_t n, const double* points, const double* weights,
+                                const double* normals, const lfmm_params* prm, lfmm_geometry* out) {
+    if (out) *out = nullptr;
+    return guarded([&]() -> lfmm_status {
+        require(med != nullptr && out != nullptr, "medium/out is NULL");
+        lfmm_geometry_s* g = build_geometry(med, n, points, weights, normals, prm, n);
         med->geometries += 1;
         *out = g;
         return LFMM_OK;
     });
-    if (st != LFMM_OK && g) {
-        free_geometry(g);
-        delete g;
-    }
-    if (st != LFMM_OK && out) *out = nullptr;
-    return st;
 }
 
 lfmm_status lfmm_geometry_destroy(lfmm_geometry g) {
@@ -396,6 +412,7 @@ static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, int32_t flags, void* stream) {
     return guarded([&]() -> lfmm_status {
         require(g != nullptr && x != nullptr && y != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
         require(nrhs >= 1, "nrhs must be >= 1");
         require(x != y, "x and y must not overlap");
         const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
@@ -434,10 +451,45 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
     });
 }
 
+lfmm_status lfmm_precond_apply(lfmm_geometry g, int32_t nrhs, const void* x, void* y, int32_t flags,
+                               void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(g != nullptr && x != nullptr && y != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
+        require(nrhs >= 1, "nrhs must be >= 1");
+        require(x != y, "x and y must not overlap");
+        require((flags & ~LFMM_DEVICE_PTRS) == 0, "lfmm_precond_apply takes LFMM_DEVICE_PTRS or 0 as flags");
+        const bool dev = (flags & LFMM_DEVICE_PTRS) != 0;
+        require(!dev || ((uintptr_t)x % 8 == 0 && (uintptr_t)y % 8 == 0), "device vectors must be 8-byte aligned");
+        cudaStream_t s = as_stream(stream);
+        if (!g->pc_ready) precond_build(g);
+        ensure_scratch(g, nrhs);
+        const size_t elems = (size_t)g->n * nrhs;
+        const void* xin = x;
+        void* yout = y;
+        if (!dev) {
+            ensure_hostbuf(g, elems);
+            cuda_check(cudaMemcpyAsync(g->d_hostbuf_x, x, sizeof(cd) * elems, cudaMemcpyHostToDevice, s), "x h2d");
+            xin = g->d_hostbuf_x;
+            yout = g->d_hostbuf_y;
+        }
+        gather_sorted(g, (const cd*)xin, g->d_xs, nrhs, s);
+        for (int c = 0; c < nrhs; ++c)
+            precond_apply_sorted(g, g->d_xs + (size_t)c * g->n, g->d_ys + (size_t)c * g->n, s);
+        scatter_sorted(g, g->d_ys, (cd*)yout, nrhs, s);
+        if (!dev) {
+            cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, sizeof(cd) * elems, cudaMemcpyDeviceToHost, s), "y d2h");
+            cuda_check(cudaStreamSynchronize(s), "precond sync");
+        }
+        return LFMM_OK;
+    });
+}
+
 lfmm_status lfmm_gmres_solve(lfmm_geometry g, int32_t nrhs, const void* b, void* x, const lfmm_gmres_params* prm,
                              lfmm_gmres_info* info, void* stream) {
     return guarded([&]() -> lfmm_status {
         require(g != nullptr && b != nullptr && x != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
         require(nrhs >= 1, "nrhs must be >= 1");
         double tol = prm ? prm->tol : 1e-8;
         int maxit = prm ? prm->max_iter : 1000;
@@ -476,6 +528,7 @@ lfmm_status lfmm_rhs_plane_wave(lfmm_geometry g, int32_t nrhs, const double* ang
                                 void* stream) {
     return guarded([&]() -> lfmm_status {
         require(g != nullptr && angle_rad != nullptr && b != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
         require(nrhs >= 1, "nrhs must be >= 1");
         for (int c = 0; c < nrhs; ++c)
             require(std::isfinite(angle_rad[c]) && angle_rad[c] > 0.0 && angle_rad[c] < M_PI,
@@ -503,47 +556,78 @@ lfmm_status lfmm_eval_field(lfmm_geometry g, int32_t nrhs, const void* density, 
                             void* u, int32_t flags, void* stream) {
     return guarded([&]() -> lfmm_status {
         require(g != nullptr && density != nullptr && targets != nullptr && u != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
         require(nrhs >= 1 && m >= 1, "nrhs and m must be >= 1");
+        require(g->n + m < (int64_t)1 << 31, "too many field points");
         const MediumDev& md = g->m;
+        std::vector<double> inv_eta(m);
         for (int64_t i = 0; i < m; ++i) {
             require(std::isfinite(targets[2 * i]) && std::isfinite(targets[2 * i + 1]), "targets must be finite");
+            int l = 0;
             for (int j = 0; j + 1 < md.nl; ++j) {
                 double sc = std::max(1.0, std::fabs(md.yint[j]));
                 if (std::fabs(targets[2 * i + 1] - md.yint[j]) <= 1e-12 * sc)
                     throw InterfaceError{"a target lies on an interface"};
+                if (targets[2 * i + 1] < md.yint[j]) l = j + 1;
             }
+            inv_eta[i] = 1.0 / md.eta[l];
         }
         const bool c64 = (flags & LFMM_C64) != 0;
         cudaStream_t s = as_stream(stream);
-        ensure_scratch(g, nrhs);
-        const size_t elems = (size_t)g->n * nrhs;
-        // density and u may be host or device memory (cudaMemcpyDefault); the
-        // single-precision forms are widened and rounded on the device
-        cuda_check(cudaMemcpyAsync(g->d_ys, density, (c64 ? sizeof(float2) : sizeof(cd)) * elems, cudaMemcpyDefault,
-                                   s), "density copy");
-        if (c64) gather_sorted_c64(g, (const float2*)g->d_ys, g->d_xs, nrhs, s);
-        else gather_sorted(g, g->d_ys, g->d_xs, nrhs, s);
-        double* d_t = nullptr;
-        cd* d_u = nullptr;
-        float2* d_u32 = nullptr;
-        cuda_check(cudaMallocAsync((void**)&d_t, sizeof(double) * 2 * m, s), "malloc targets");
-        cuda_check(cudaMallocAsync((void**)&d_u, sizeof(cd) * m * nrhs, s), "malloc u");
-        if (c64) cuda_check(cudaMallocAsync((void**)&d_u32, sizeof(float2) * m * nrhs, s), "malloc u");
-        struct F {
-            double* a;
-            cd* b;
-            float2* c;
-            cudaStream_t s;
-            ~F() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); if (c) cudaFreeAsync(c, s); }
-        } fr{d_t, d_u, d_u32, s};
-        cuda_check(cudaMemcpyAsync(d_t, targets, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s), "targets");
-        eval_field_direct(g, nrhs, g->d_xs, m, d_t, d_u, s);
-        if (c64) {
-            round_to_c64(d_u, d_u32, (int64_t)m * nrhs, s);
-            cuda_check(cudaMemcpyAsync(u, d_u32, sizeof(float2) * m * nrhs, cudaMemcpyDefault, s), "u copy");
-        } else {
-            cuda_check(cudaMemcpyAsync(u, d_u, sizeof(cd) * m * nrhs, cudaMemcpyDefault, s), "u copy");
+        // the field geometry: the elements in their input order, then the field points
+        // (weight 0, never a source); same order p, leaf size and operator
+        const int64_t n = g->n, nm = g->n + m;
+        std::vector<double> pts(2 * nm), wts(nm, 0.0), nrm;
+        if (g->combined) nrm.assign(2 * nm, 0.0);
+        for (int64_t q = 0; q < n; ++q) {
+            const int64_t i = g->tree.perm[q];
+            pts[2 * i] = g->hx[q];
+            pts[2 * i + 1] = g->hy[q];
+            wts[i] = g->hw[q];
+            if (g->combined) { nrm[2 * i] = g->hnx[q]; nrm[2 * i + 1] = g->hny[q]; }
         }
+        for (int64_t j = 0; j < m; ++j) {
+            pts[2 * (n + j)] = targets[2 * j];
+            pts[2 * (n + j) + 1] = targets[2 * j + 1];
+            if (g->combined) nrm[2 * (n + j)] = 1.0;
+        }
+        const lfmm_params prm{g->p, g->leaf_size, g->combined ? LFMM_COMBINED_FIELD : 0, 0};
+        struct FieldGeometry {
+            lfmm_geometry_s* F = nullptr;
+            cudaStream_t s;
+            ~FieldGeometry() {
+                if (!F) return;
+                cudaStreamSynchronize(s);
+                free_geometry(F);
+                delete F;
+            }
+        } fg{nullptr, s};
+        fg.F = build_geometry(g->med, nm, pts.data(), wts.data(), g->combined ? nrm.data() : nullptr, &prm, n);
+        lfmm_geometry_s* F = fg.F;
+        ensure_scratch(F, nrhs);
+        const size_t esz = c64 ? sizeof(float2) : sizeof(cd);
+        void* d_phi = nullptr;
+        cd* d_xy = nullptr;
+        double* d_ie = nullptr;
+        void* d_u = nullptr;
+        cuda_check(cudaMallocAsync(&d_phi, esz * n * nrhs, s), "malloc density");
+        cuda_check(cudaMallocAsync((void**)&d_xy, sizeof(cd) * nm * nrhs, s), "malloc field vector");
+        cuda_check(cudaMallocAsync((void**)&d_ie, sizeof(double) * m, s), "malloc 1/eta");
+        cuda_check(cudaMallocAsync(&d_u, esz * m * nrhs, s), "malloc u");
+        struct Fr {
+            void *a, *b, *c, *d;
+            cudaStream_t s;
+            ~Fr() { cudaFreeAsync(a, s); cudaFreeAsync(b, s); cudaFreeAsync(c, s); cudaFreeAsync(d, s); }
+        } fr{d_phi, d_xy, d_ie, d_u, s};
+        // density and u may be host or device memory (cudaMemcpyDefault)
+        cuda_check(cudaMemcpyAsync(d_phi, density, esz * n * nrhs, cudaMemcpyDefault, s), "density copy");
+        cuda_check(cudaMemcpyAsync(d_ie, inv_eta.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s), "1/eta");
+        field_pack(d_phi, c64, n, m, nrhs, d_xy, s);
+        gather_sorted(F, d_xy, F->d_xs, nrhs, s);
+        apply_operator_sorted(F, F->d_xs, F->d_ys, nrhs, s);
+        scatter_sorted(F, F->d_ys, d_xy, nrhs, s);
+        field_unpack(d_xy, d_ie, n, m, nrhs, c64, d_u, s);
+        cuda_check(cudaMemcpyAsync(u, d_u, esz * m * nrhs, cudaMemcpyDefault, s), "u copy");
         cuda_check(cudaStreamSynchronize(s), "field sync");
         return LFMM_OK;
     });

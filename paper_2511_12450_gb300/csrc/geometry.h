@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <functional>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -132,10 +134,14 @@ struct lfmm_geometry_s {
     lfmm_medium_s* med = nullptr;
     MediumDev m;
     int64_t n = 0;
+    // points with input index >= n_src are field points (weight 0) of a field
+    // geometry built by lfmm_eval_field; n_src = n for a geometry of elements only
+    int64_t n_src = 0;
     int p = 20, leaf_size = 64;
     lfmm::TreeHost tree;
     lfmm::QuadRule quad;
     std::vector<double> hx, hy, hw;   // sorted-order host copies
+    std::vector<double> hnx, hny;     // sorted-order normals (combined field only)
     int nleaf = 0, leaf0 = 0;         // leaves are boxes [leaf0, leaf0 + nleaf)
 
     // sorted-order point data
@@ -183,6 +189,24 @@ struct lfmm_geometry_s {
     cd *d_nb_val = nullptr;           // blocks stored column-major (source index major)
     int64_t nb_nnz = 0;
     int n_blocks = 0;
+    // a target leaf's blocks lie one after another: one nT x nJ column-major matrix per leaf
+    int64_t *d_nl_off = nullptr;      // per leaf: offset of its first block
+    int *d_nl_jptr = nullptr;         // per leaf: column range
+    int *d_nl_j = nullptr;            // per column: sorted source position
+    std::vector<int> nb_ptr_host, nb_src_host;
+    std::vector<int64_t> nb_off_host;
+    std::vector<unsigned char> nb_react_host;   // 1: the block holds reaction entries
+    // precision form of the near field (built on its first use): blocks without reaction
+    // entries in complex64 (self terms moved to an FP64 diagonal), the others in FP64
+    bool near32_ready = false;
+    float2 *d_nv32 = nullptr;
+    int64_t *d_nl_off32 = nullptr;
+    int *d_nl_jptr32 = nullptr, *d_nl_j32 = nullptr;
+    cd *d_nv64r = nullptr;
+    int64_t *d_nl_off64r = nullptr;
+    int *d_nl_jptr64r = nullptr, *d_nl_j64r = nullptr;
+    cd *d_ndiag = nullptr;
+    int64_t near32_nnz = 0, near64r_nnz = 0;
     // translation tables
     int *d_p_level = nullptr;
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
@@ -231,6 +255,10 @@ struct lfmm_geometry_s {
     bool pc_ready = false;
     double setup_seconds = 0.0;
     std::vector<void*> allocs;        // everything cudaMalloc'ed for this geometry
+    // held by every call that applies the operator or the preconditioner to vectors
+    // (matvec, the allocation-free matvec, precondition, solve, right-hand side, field):
+    // calls on one geometry run one after another even if a caller does not serialise them
+    std::mutex call_mu;
 };
 
 namespace lfmm {
@@ -243,6 +271,15 @@ struct CudaError {
 struct TimeoutError {   // a bounded device wait gave up (LFMM_ERR_TIMEOUT)
     std::string msg;
 };
+struct ArgError {       // an invalid argument (LFMM_ERR_INVALID_ARG)
+    std::string msg;
+};
+struct InterfaceError { // a point on an interface (LFMM_ERR_NODE_ON_INTERFACE)
+    std::string msg;
+};
+// Runs f and maps every exception to the entry points' status codes; a failed call
+// also clears the thread's last CUDA error (api.cu).
+lfmm_status guarded_call(const std::function<lfmm_status()>& f);
 void cuda_check(cudaError_t e, const char* what);
 // Device memory of a geometry.  Allocations are stream-ordered on the calling
 // thread's default stream so that building or releasing one geometry does not
@@ -286,7 +323,7 @@ T* dupload(lfmm_geometry_s* g, const std::vector<T>& v) {
 
 // near field (near.cu)
 void near_build(lfmm_geometry_s* g);
-void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s);
+void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false);
 // FMM far field (fmm.cu)
 void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false,
@@ -325,8 +362,11 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
                  cudaStream_t s, lfmm_gmres_info* info, int precision = 0, int restart = 0);
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s);
 void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_host, cd* b_sorted, cudaStream_t s);
-void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t m, const double* d_targets,
-                       cd* u, cudaStream_t s);
+// scattered field through a field geometry (api.cu builds it): x = [Phi; 0] per column,
+// u = (field-point rows of K x) / eta of each field point's layer
+void field_pack(const void* phi, bool c64, int64_t n, int64_t m, int nrhs, cd* x, cudaStream_t s);
+void field_unpack(const cd* y, const double* inv_eta, int64_t n, int64_t m, int nrhs, bool c64, void* u,
+                  cudaStream_t s);
 
 QuadRule make_quad_rule(const MediumDev& m);
 

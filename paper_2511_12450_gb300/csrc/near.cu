@@ -52,7 +52,9 @@ __global__ void k_near_free(MediumDev m, const int* __restrict__ blk_tgt, const 
         cd out = mk(0.0, 0.0);
         if (fr) {
             int pi = tb + i, pj = sb + j;
-            if (pi == pj) {
+            if (pw[pj] == 0.0) {
+                // a field point (weight 0) is never a source; its own diagonal is 0
+            } else if (pi == pj) {
                 out = self_entry(k, pw[pi], cf);
             } else {
                 out = pw[pj] * free_kernel(k, px[pj] - px[pi], py[pj] - py[pi], cf, cf ? nx[pj] : 0.0,
@@ -90,6 +92,7 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
         const int c = tk.comp;
         const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
         const int pi = tb + i, pj = sb + j;
+        if (pw[pj] == 0.0) continue;   // a field point (weight 0) is never a source (uniform per warp)
         const double X = px[pj] - px[pi];
         const double hs = (a == 0) ? (py[pj] - m.yint[ls]) : (m.yint[ls - 1] - py[pj]);
         const double ht = (b == 0) ? (m.yint[lt - 1] - py[pi]) : (py[pi] - m.yint[lt]);
@@ -110,39 +113,125 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
     }
 }
 
-// y_T += sum_S B_{TS} x_S for all target leaves (one CTA per leaf)
-__global__ void __launch_bounds__(128) k_near_apply(const int* __restrict__ nb_ptr, const int* __restrict__ nb_src,
-                                                    const int64_t* __restrict__ nb_off, const cd* __restrict__ val,
-                                                    const int* __restrict__ box_begin, const int* __restrict__ box_end,
-                                                    int leaf0, const cd* __restrict__ x, cd* __restrict__ y,
-                                                    int64_t n, int nrhs) {
-    __shared__ cd part[128];
-    const int T = leaf0 + blockIdx.x;
-    const int tb = box_begin[T], nT = box_end[T] - tb;
+// y_T += (near row of leaf T) x, one warp per target leaf.
+//
+// The blocks of one target leaf T are stored one after another, each column-major
+// with leading dimension nT = |T|, so together they form one column-major nT x nJ
+// matrix whose column c multiplies x at the sorted position J[c].  A warp takes the
+// rows in chunks of r = min(32, nT) rows: G = 32 / r groups of r lanes each walk
+// every G-th column of the chunk (lanes beyond G r idle), and the groups' sums meet
+// by warp shuffles in a fixed order.  Consecutive lanes of a group read consecutive
+// entries of a column.
+//
+// FP64 form: one matrix, the stored FP64 blocks (free space, reaction, self terms).
+// Precision form (MIX): the blocks without reaction entries as complex64 with their
+// self terms taken out (products and sums in FP32), the blocks that hold reaction
+// entries as FP64 copies, and the self terms as an FP64 diagonal;
+// the three parts are added in FP64.
+struct NearRowPart {
+    const int64_t* off;   // per leaf: first value of its matrix
+    const int* jptr;      // per leaf: column range [jptr[T], jptr[T + 1])
+    const int* j;         // sorted source position of each column
+};
+
+__device__ __forceinline__ void near_fma(cd& acc, const cd& v, const cd& x) { cfma(acc, v, x); }
+__device__ __forceinline__ void near_fma(float2& acc, const float2& v, const cd& x) {
+    const float xr = (float)x.x, xi = (float)x.y;
+    acc.x = fmaf(v.x, xr, acc.x);
+    acc.x = fmaf(-v.y, xi, acc.x);
+    acc.y = fmaf(v.x, xi, acc.y);
+    acc.y = fmaf(v.y, xr, acc.y);
+}
+
+template <typename V, typename A>
+__device__ __forceinline__ void near_row_sum(const V* __restrict__ val, const NearRowPart& P, int leaf, int nT, int i,
+                                             int g, int G, const cd* __restrict__ x, A& acc) {
+    const int c0 = P.jptr[leaf], c1 = P.jptr[leaf + 1];
+    const V* v = val + P.off[leaf] + i;
+    A a1{}, a2{}, a3{};
+    int c = c0 + g;
+    // four columns in flight per lane
+    for (; c + 3 * G < c1; c += 4 * G) {
+        const V v0 = v[(int64_t)(c - c0) * nT], v1 = v[(int64_t)(c + G - c0) * nT];
+        const V v2 = v[(int64_t)(c + 2 * G - c0) * nT], v3 = v[(int64_t)(c + 3 * G - c0) * nT];
+        const cd x0 = x[P.j[c]], x1 = x[P.j[c + G]], x2 = x[P.j[c + 2 * G]], x3 = x[P.j[c + 3 * G]];
+        near_fma(acc, v0, x0);
+        near_fma(a1, v1, x1);
+        near_fma(a2, v2, x2);
+        near_fma(a3, v3, x3);
+    }
+    for (; c < c1; c += G) near_fma(acc, v[(int64_t)(c - c0) * nT], x[P.j[c]]);
+    acc.x += a1.x; acc.y += a1.y;
+    a2.x += a3.x; a2.y += a3.y;
+    acc.x += a2.x; acc.y += a2.y;
+}
+
+template <bool MIX>
+__global__ void __launch_bounds__(128) k_near_leaf(int nleaf, int leaf0, const int* __restrict__ box_begin,
+                                                   const int* __restrict__ box_end, NearRowPart P64,
+                                                   const cd* __restrict__ val64, NearRowPart P32,
+                                                   const float2* __restrict__ val32, const cd* __restrict__ diag,
+                                                   const cd* __restrict__ x, cd* __restrict__ y, int64_t n,
+                                                   int nrhs) {
+    const int leaf = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (leaf >= nleaf) return;   // whole warps only: the shuffles below see full warps
+    const int tb = box_begin[leaf0 + leaf], nT = box_end[leaf0 + leaf] - tb;
     for (int col = 0; col < nrhs; ++col) {
         const cd* xc = x + (int64_t)col * n;
-        for (int i0 = 0; i0 < nT; i0 += blockDim.x) {
-            const int nTi = min(nT - i0, (int)blockDim.x);
-            const int Gi = (nTi >= (int)blockDim.x) ? 1 : (int)blockDim.x / nTi;
-            const int i = i0 + (threadIdx.x % nTi);
-            const int g = threadIdx.x / nTi;
+        for (int i0 = 0; i0 < nT; i0 += 32) {
+            const int r = min(32, nT - i0), G = 32 / r;
+            const int i = i0 + lane % r, g = lane / r;
             cd acc = mk(0.0, 0.0);
-            if (g < Gi) {
-                for (int k = nb_ptr[blockIdx.x]; k < nb_ptr[blockIdx.x + 1]; ++k) {
-                    const int S = nb_src[k];
-                    const int sb = box_begin[S], nS = box_end[S] - sb;
-                    const cd* v = val + nb_off[k];
-                    for (int j = g; j < nS; j += Gi) cfma(acc, v[(int64_t)j * nT + i], xc[sb + j]);
+            if (g < G) {
+                near_row_sum(val64, P64, leaf, nT, i, g, G, xc, acc);
+                if (MIX) {
+                    float2 a32 = make_float2(0.f, 0.f);
+                    near_row_sum(val32, P32, leaf, nT, i, g, G, xc, a32);
+                    acc.x += (double)a32.x;
+                    acc.y += (double)a32.y;
                 }
             }
-            part[threadIdx.x] = acc;
-            __syncthreads();
-            if (threadIdx.x < nTi) {
-                cd s = mk(0.0, 0.0);
-                for (int gg = 0; gg < Gi; ++gg) s += part[gg * nTi + threadIdx.x];
-                y[(int64_t)col * n + tb + i0 + threadIdx.x] += s;
+            for (int gg = 1; gg < G; ++gg) {
+                const int src = (lane + gg * r) & 31;
+                const double ox = __shfl_sync(0xffffffffu, acc.x, src);
+                const double oy = __shfl_sync(0xffffffffu, acc.y, src);
+                if (lane < r) { acc.x += ox; acc.y += oy; }
             }
-            __syncthreads();
+            if (lane < r) {
+                const int64_t q = (int64_t)col * n + tb + i;
+                if (MIX) cfma(acc, diag[tb + i], xc[tb + i]);
+                y[q] += acc;
+            }
+        }
+    }
+}
+
+// one block copied into the precision form's stores
+struct NearCopy {
+    int64_t src;    // offset in the FP64 blocks
+    int64_t dst;    // offset in the FP32 or FP64 store
+    int nT, nS;
+    int self;       // 1: block (T, T) going to FP32: its diagonal moves to the FP64 diagonal
+    int to32;       // 1: FP32 store, 0: FP64 store
+    int tb;         // first sorted position of T
+};
+__global__ void k_near_repack(const NearCopy* __restrict__ cp, const cd* __restrict__ val, float2* __restrict__ v32,
+                              cd* __restrict__ v64, cd* __restrict__ diag) {
+    const NearCopy c = cp[blockIdx.x];
+    const int ne = c.nT * c.nS;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const cd v = val[c.src + e];
+        if (!c.to32) {
+            v64[c.dst + e] = v;
+            continue;
+        }
+        const int i = e % c.nT, j = e / c.nT;
+        if (c.self && i == j) {
+            diag[c.tb + i] = v;
+            v32[c.dst + e] = make_float2(0.f, 0.f);
+        } else {
+            v32[c.dst + e] = make_float2((float)v.x, (float)v.y);
         }
     }
 }
@@ -154,12 +243,20 @@ void near_build(lfmm_geometry_s* g) {
     g->nleaf = t.level_start[D + 1] - g->leaf0;
     // blocks per target leaf: union of free-space and reaction near lists
     std::vector<int> blk_tgt, blk_src, nb_ptr(g->nleaf + 1, 0);
-    std::vector<unsigned char> blk_free;
+    std::vector<unsigned char> blk_free, blk_react;
     std::vector<int64_t> blk_off;
     std::vector<NearTask> tasks;
     int64_t off = 0, work = 0;
     for (int li = 0; li < g->nleaf; ++li) {
         const int T = g->leaf0 + li;
+        if (g->n_src < g->n) {   // field geometry: only the rows of field points are needed
+            bool has_field = false;
+            for (int q = t.box_begin[T]; q < t.box_end[T] && !has_field; ++q) has_field = t.perm[q] >= g->n_src;
+            if (!has_field) {
+                nb_ptr[li + 1] = (int)blk_tgt.size();
+                continue;
+            }
+        }
         std::vector<int> srcs;
         for (int k = t.ufree_ptr[T]; k < t.ufree_ptr[T + 1]; ++k) srcs.push_back(t.ufree_idx[k]);
         for (int k = t.ureact_ptr[T]; k < t.ureact_ptr[T + 1]; ++k) srcs.push_back(t.ureact_idx[k]);
@@ -175,11 +272,14 @@ void near_build(lfmm_geometry_s* g) {
             blk_free.push_back(fr ? 1 : 0);
             blk_off.push_back(off);
             const int nS = t.box_end[S] - t.box_begin[S];
+            bool re = false;
             for (int k = t.ureact_ptr[T]; k < t.ureact_ptr[T + 1]; ++k) {
                 if (t.ureact_idx[k] != S) continue;
                 tasks.push_back(NearTask{bi, t.ureact_comp[k], work});
                 work += (int64_t)nT * nS;
+                re = true;
             }
+            blk_react.push_back(re ? 1 : 0);
             off += (int64_t)nT * nS;
         }
         nb_ptr[li + 1] = (int)blk_tgt.size();
@@ -192,6 +292,24 @@ void near_build(lfmm_geometry_s* g) {
     g->d_nb_ptr = dupload(g, nb_ptr);
     unsigned char* d_bf = dupload(g, blk_free);
     g->d_nb_val = dalloc<cd>(g, (size_t)off);
+    // each leaf's blocks as one matrix: column -> sorted source position
+    {
+        std::vector<int> jptr(g->nleaf + 1, 0), jl;
+        std::vector<int64_t> loff(g->nleaf, 0);
+        for (int li = 0; li < g->nleaf; ++li) {
+            loff[li] = nb_ptr[li] < nb_ptr[li + 1] ? blk_off[nb_ptr[li]] : 0;
+            for (int k = nb_ptr[li]; k < nb_ptr[li + 1]; ++k)
+                for (int p = t.box_begin[blk_src[k]]; p < t.box_end[blk_src[k]]; ++p) jl.push_back(p);
+            jptr[li + 1] = (int)jl.size();
+        }
+        g->d_nl_jptr = dupload(g, jptr);
+        g->d_nl_j = dupload(g, jl);
+        g->d_nl_off = dupload(g, loff);
+    }
+    g->nb_ptr_host = nb_ptr;
+    g->nb_src_host = blk_src;
+    g->nb_off_host = blk_off;
+    g->nb_react_host = blk_react;
     std::vector<double> compH(t.comps.size());
     for (size_t c = 0; c < t.comps.size(); ++c) compH[c] = t.comps[c].Hc;
     double* d_compH = dupload(g, compH);
@@ -215,12 +333,75 @@ void near_build(lfmm_geometry_s* g) {
     cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "near_build");
 }
 
-void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s) {
+// The precision form's near field (built on its first use): blocks without reaction
+// entries in complex64 with the self terms moved to an FP64 diagonal, blocks with
+// reaction entries (Sommerfeld quadrature near interfaces) kept in FP64.
+static void near_mixed_build(lfmm_geometry_s* g) {
+    const TreeHost& t = g->tree;
+    const int nleaf = g->nleaf;
+    std::vector<NearCopy> cps;
+    std::vector<int> jp32(nleaf + 1, 0), jp64(nleaf + 1, 0), j32, j64;
+    std::vector<int64_t> o32(nleaf, 0), o64(nleaf, 0);
+    int64_t n32 = 0, n64 = 0;
+    for (int li = 0; li < nleaf; ++li) {
+        const int T = g->leaf0 + li;
+        const int tb = t.box_begin[T], nT = t.box_end[T] - tb;
+        o32[li] = n32;
+        o64[li] = n64;
+        for (int k = g->nb_ptr_host[li]; k < g->nb_ptr_host[li + 1]; ++k) {
+            const int S = g->nb_src_host[k];
+            const int nS = t.box_end[S] - t.box_begin[S];
+            const bool to32 = g->nb_react_host[k] == 0;
+            NearCopy c{g->nb_off_host[k], to32 ? n32 : n64, nT, nS, (to32 && S == T) ? 1 : 0, to32 ? 1 : 0, tb};
+            cps.push_back(c);
+            std::vector<int>& jl = to32 ? j32 : j64;
+            for (int p = t.box_begin[S]; p < t.box_end[S]; ++p) jl.push_back(p);
+            (to32 ? n32 : n64) += (int64_t)nT * nS;
+        }
+        jp32[li + 1] = (int)j32.size();
+        jp64[li + 1] = (int)j64.size();
+    }
+    g->d_nl_jptr32 = dupload(g, jp32);
+    g->d_nl_j32 = dupload(g, j32);
+    g->d_nl_off32 = dupload(g, o32);
+    g->d_nl_jptr64r = dupload(g, jp64);
+    g->d_nl_j64r = dupload(g, j64);
+    g->d_nl_off64r = dupload(g, o64);
+    g->d_nv32 = dalloc<float2>(g, (size_t)n32);
+    g->d_nv64r = dalloc<cd>(g, (size_t)n64);
+    g->d_ndiag = dalloc<cd>(g, (size_t)g->n);
+    g->near32_nnz = n32;
+    g->near64r_nnz = n64;
+    cuda_check(cudaMemsetAsync(g->d_ndiag, 0, sizeof(cd) * g->n, cudaStreamPerThread), "memset diag");
+    if (!cps.empty()) {
+        NearCopy* d_cps = dupload(g, cps);
+        k_near_repack<<<(int)cps.size(), 128, 0, cudaStreamPerThread>>>(d_cps, g->d_nb_val, g->d_nv32, g->d_nv64r,
+                                                                        g->d_ndiag);
+        cuda_check(cudaGetLastError(), "k_near_repack");
+    }
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "near_mixed_build");
+    g->near32_ready = true;
+}
+
+void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed) {
     if (g->nleaf == 0) return;
+    if (mixed && !g->near32_ready) near_mixed_build(g);
     prof_begin(g, ST_NEAR, s);
-    k_near_apply<<<g->nleaf, 128, 0, s>>>(g->d_nb_ptr, g->d_nb_src, g->d_nb_off, g->d_nb_val, g->d_box_begin,
-                                          g->d_box_end, g->leaf0, x_sorted, y_sorted, g->n, nrhs);
-    cuda_check(cudaGetLastError(), "k_near_apply");
+    const int warps_per_cta = 4;
+    const int grid = (g->nleaf + warps_per_cta - 1) / warps_per_cta;
+    if (mixed) {
+        const NearRowPart p64{g->d_nl_off64r, g->d_nl_jptr64r, g->d_nl_j64r};
+        const NearRowPart p32{g->d_nl_off32, g->d_nl_jptr32, g->d_nl_j32};
+        k_near_leaf<true><<<grid, 32 * warps_per_cta, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end, p64,
+                                                              g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
+                                                              y_sorted, g->n, nrhs);
+    } else {
+        const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
+        k_near_leaf<false><<<grid, 32 * warps_per_cta, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end, p64,
+                                                               g->d_nb_val, p64, nullptr, nullptr, x_sorted, y_sorted,
+                                                               g->n, nrhs);
+    }
+    cuda_check(cudaGetLastError(), "k_near_leaf");
     ++g->n_launches;
     prof_end(g, ST_NEAR, s);
 }

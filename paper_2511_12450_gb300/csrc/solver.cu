@@ -82,7 +82,7 @@ void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted,
     // field (bound by the FP64 pipe); both add into y, the leaf evaluations after it
     cuda_check(cudaEventRecord(g->ev_fork, s), "fork");
     cuda_check(cudaStreamWaitEvent(g->side, g->ev_fork, 0), "fork");
-    near_apply(g, x_sorted, y_sorted, nrhs, g->side);
+    near_apply(g, x_sorted, y_sorted, nrhs, g->side, mixed);
     cuda_check(cudaEventRecord(g->ev_join, g->side), "join");
     fmm_apply(g, x_sorted, y_sorted, nrhs, s, mixed, g->ev_join);
     cuda_check(cudaStreamWaitEvent(s, g->ev_join, 0), "join");   // also when there is no far field
@@ -720,68 +720,50 @@ void rhs_plane_wave_sorted(lfmm_geometry_s* g, int nrhs, const double* angles_ho
 }
 
 // ------------------------------------------------------------------ scattered field (eq. integralrep)
-// one warp per (target, source) pair; u[target] += |Gamma_e| Phi_e G(c_e, r) / eta, or in
-// the combined-field form |Gamma_e| Phi_e [n_e . grad_{c_e} - i k] G(c_e, r) / eta
-__global__ void k_field(MediumDev m, QuadRule q, const double* __restrict__ px, const double* __restrict__ py,
-                        const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
-                        const int* __restrict__ layer, const int* __restrict__ comp,
-                        const double* __restrict__ compH, int ncomp, const cd* __restrict__ phi, int64_t n,
-                        int nrhs, const double* __restrict__ tgt, int64_t mt, cd* __restrict__ u) {
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (int64_t wk = warp; wk < mt * n; wk += nw) {
-        const int64_t it = wk / n, e = wk - it * n;
-        const double xt = tgt[2 * it], yt = tgt[2 * it + 1];
-        int lt = 0;
-        while (lt < m.nl - 1 && yt < m.yint[lt]) ++lt;
-        const int ls = layer[e];
-        cd G = mk(0.0, 0.0);
-        for (int c = 0; c < ncomp; ++c) {
-            const int cls = comp[4 * c], a = comp[4 * c + 1], clt = comp[4 * c + 2], b = comp[4 * c + 3];
-            if (cls != ls || clt != lt) continue;
-            const double hs = (a == 0) ? (py[e] - m.yint[ls]) : (m.yint[ls - 1] - py[e]);
-            const double ht = (b == 0) ? (m.yint[lt - 1] - yt) : (yt - m.yint[lt]);
-            if (nx) {
-                cd gk[3];
-                react_kernel_grad_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht, gk);
-                G += react_cf_combine(gk, a, m.k[ls], nx[e], ny[e]);
+// The field is one operator product on a field geometry (elements followed by the m
+// field points, which carry weight 0): x = [Phi; 0] per column, and the field-point
+// rows of K x are sum_e |Gamma_e| G(c_e, r) Phi_e (or the combined-field kernel).
+// x[c (n + m) + i] = Phi[c n + i] (i < n), 0 for the field points; Phi in FP64 or FP32.
+__global__ void k_field_pack(const void* __restrict__ phi, int c64, int64_t n, int64_t m, int nrhs,
+                             cd* __restrict__ x) {
+    const int64_t nm = n + m, tot = nm * nrhs;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = q / nm, i = q - c * nm;
+        cd v = mk(0.0, 0.0);
+        if (i < n) {
+            if (c64) {
+                const float2 f = ((const float2*)phi)[c * n + i];
+                v = mk((double)f.x, (double)f.y);
             } else {
-                G += react_kernel_warp(m, q, ls, a, lt, b, compH[c], px[e] - xt, hs, ht);
+                v = ((const cd*)phi)[c * n + i];
             }
         }
-        if (lane == 0) {
-            if (ls == lt)
-                G += free_kernel(m.k[ls], px[e] - xt, py[e] - yt, nx != nullptr, nx ? nx[e] : 0.0, nx ? ny[e] : 0.0);
-            double sc = pw[e] / m.eta[lt];
-            for (int col = 0; col < nrhs; ++col) {
-                cd v = (sc * G) * phi[(int64_t)col * n + e];
-                atomicAdd(&u[(int64_t)col * mt + it].x, v.x);
-                atomicAdd(&u[(int64_t)col * mt + it].y, v.y);
-            }
-        }
+        x[q] = v;
+    }
+}
+// u[c m + j] = y[c (n + m) + n + j] / eta_{l(r_j)}, in FP64 or rounded to FP32
+__global__ void k_field_unpack(const cd* __restrict__ y, const double* __restrict__ inv_eta, int64_t n, int64_t m,
+                               int nrhs, int c64, void* __restrict__ u) {
+    const int64_t tot = m * nrhs;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = q / m, j = q - c * m;
+        const cd v = y[c * (n + m) + n + j] * inv_eta[j];
+        if (c64) ((float2*)u)[q] = make_float2((float)v.x, (float)v.y);
+        else ((cd*)u)[q] = v;
     }
 }
 
-void eval_field_direct(lfmm_geometry_s* g, int nrhs, const cd* phi_sorted, int64_t mt, const double* d_targets,
-                       cd* u, cudaStream_t s) {
-    std::vector<double> compH(g->tree.comps.size());
-    for (size_t c = 0; c < compH.size(); ++c) compH[c] = g->tree.comps[c].Hc;
-    double* d_compH = nullptr;
-    cuda_check(cudaMallocAsync((void**)&d_compH, sizeof(double) * std::max<size_t>(1, compH.size()), s), "malloc compH");
-    if (!compH.empty())
-        cuda_check(cudaMemcpyAsync(d_compH, compH.data(), sizeof(double) * compH.size(), cudaMemcpyHostToDevice, s),
-                   "compH");
-    cuda_check(cudaMemsetAsync(u, 0, sizeof(cd) * mt * nrhs, s), "memset u");
-    int64_t work = mt * g->n;
-    int64_t blocks = std::min<int64_t>((work * 32 + 255) / 256, 152 * 32);
-    k_field<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g->m, g->quad, g->d_x, g->d_y, g->d_w, g->d_nx,
-                                                             g->d_ny, g->d_layer,
-                                                             g->d_comp, d_compH, (int)compH.size(), phi_sorted, g->n,
-                                                             nrhs, d_targets, mt, u);
-    cuda_check(cudaGetLastError(), "k_field");
-    cuda_check(cudaStreamSynchronize(s), "field");
-    cudaFreeAsync(d_compH, s);
+void field_pack(const void* phi, bool c64, int64_t n, int64_t m, int nrhs, cd* x, cudaStream_t s) {
+    const int64_t tot = (n + m) * nrhs;
+    k_field_pack<<<(int)std::min<int64_t>(nblk(tot), 152 * 16), 256, 0, s>>>(phi, c64 ? 1 : 0, n, m, nrhs, x);
+    cuda_check(cudaGetLastError(), "k_field_pack");
+}
+void field_unpack(const cd* y, const double* inv_eta, int64_t n, int64_t m, int nrhs, bool c64, void* u,
+                  cudaStream_t s) {
+    const int64_t tot = m * nrhs;
+    k_field_unpack<<<(int)std::min<int64_t>(nblk(tot), 152 * 16), 256, 0, s>>>(y, inv_eta, n, m, nrhs, c64 ? 1 : 0,
+                                                                                u);
+    cuda_check(cudaGetLastError(), "k_field_unpack");
 }
 
 }  // namespace lfmm

@@ -19,7 +19,13 @@
 //    it has to start at zero: the sorted output is cleared by the call itself and
 //    every coefficient is written before it is read.  Calls that overlap on the GPU
 //    (other streams, other threads) race on the array and must be serialised;
-//  * geometries whose work buffers do not fit are rejected before any device work.
+//  * geometries whose work buffers do not fit are rejected before any device work;
+//  * for the length of the call the geometry's work-buffer fields point into the
+//    array, under the geometry's call lock, which every other entry point that
+//    applies the operator also takes: a concurrent lfmm_matvec, lfmm_gmres_solve,
+//    lfmm_eval_field or server worker on the same geometry waits on the host instead
+//    of enqueueing work on the array.  Work already enqueued on another stream is
+//    not waited for: the caller orders the streams it uses with one geometry.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -54,36 +60,52 @@ static void* scratch_address() {
 
 static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The geometry's work-buffer fields, pointed at the static array for the length of one
+// call and restored when the call ends (also when it throws).
+struct ScratchSwap {
+    lfmm_geometry_s* g;
+    cd *xs, *ys, *M, *L, *Mp, *Lp, *part;
+    int nrhs_cap, coef_cols, part_cols;
+    bool prof;
+    explicit ScratchSwap(lfmm_geometry_s* geo)
+        : g(geo), xs(geo->d_xs), ys(geo->d_ys), M(geo->d_M), L(geo->d_L), Mp(geo->d_Mp), Lp(geo->d_Lp),
+          part(geo->d_m2l_part), nrhs_cap(geo->nrhs_cap), coef_cols(geo->coef_cols),
+          part_cols(geo->m2l_part_cols), prof(geo->prof.on) {}
+    ~ScratchSwap() {
+        g->d_xs = xs; g->d_ys = ys; g->d_M = M; g->d_L = L; g->d_Mp = Mp; g->d_Lp = Lp;
+        g->d_m2l_part = part;
+        g->nrhs_cap = nrhs_cap;
+        g->coef_cols = coef_cols;
+        g->m2l_part_cols = part_cols;
+        g->prof.on = prof;
+    }
+};
+
 }  // namespace lfmm
 
 using namespace lfmm;
 
 extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* y, void* stream) {
-    set_error("");
-    if (!g || !x || !y) { set_error("NULL argument"); return LFMM_ERR_INVALID_ARG; }
-    if (x == y) { set_error("x and y must not overlap"); return LFMM_ERR_INVALID_ARG; }
-    // work buffers: sorted x and y, multipoles/locals (cell centres and reaction centres), M2L partial
-    // sums, one column
-    const size_t n = (size_t)g->n;
-    const size_t b_xs = align256(sizeof(cd) * n), b_ys = b_xs;
-    const size_t b_m = align256(sizeof(cd) * (size_t)(g->ncoef > 0 ? g->ncoef : 1));
-    const size_t b_mp = align256(sizeof(cd) * (size_t)(g->nslotcoef > 0 ? g->nslotcoef : 1));
-    const size_t b_part = align256(sizeof(cd) * (size_t)(g->n_m2l_parts > 0 ? g->n_m2l_parts : 1) * 3 * XT_W);
-    const size_t need = b_xs + b_ys + 2 * b_m + 2 * b_mp + b_part;
-    if (need > LFMM_STATIC_SCRATCH_BYTES) {
-        set_error("geometry needs " + std::to_string(need) + " bytes of work memory; lfmm_matvec_static holds " +
-                  std::to_string((size_t)LFMM_STATIC_SCRATCH_BYTES) + " (use lfmm_matvec)");
-        return LFMM_ERR_INVALID_ARG;
-    }
-    // save the geometry's own (lazily allocated) buffers and point it at the array
-    cd *sxs = g->d_xs, *sys = g->d_ys, *sM = g->d_M, *sL = g->d_L, *sMp = g->d_Mp, *sLp = g->d_Lp;
-    cd* spart = g->d_m2l_part;
-    int s_nrhs = g->nrhs_cap, s_cols = g->coef_cols, s_pcols = g->m2l_part_cols;
-    bool s_prof = g->prof.on;
-    g->prof.on = false;   // the stage timers synchronise the stream; this entry point never does
-    lfmm_status st = LFMM_OK;
-    try {
+    return guarded_call([&]() -> lfmm_status {
+        if (!g || !x || !y) throw ArgError{"NULL argument"};
+        if (x == y) throw ArgError{"x and y must not overlap"};
+        if ((uintptr_t)x % 8 != 0 || (uintptr_t)y % 8 != 0) throw ArgError{"device vectors must be 8-byte aligned"};
+        // work buffers: sorted x and y, multipoles/locals (cell centres and reaction centres), M2L
+        // partial sums, one column
+        const size_t n = (size_t)g->n;
+        const size_t b_xs = align256(sizeof(cd) * n), b_ys = b_xs;
+        const size_t b_m = align256(sizeof(cd) * (size_t)(g->ncoef > 0 ? g->ncoef : 1));
+        const size_t b_mp = align256(sizeof(cd) * (size_t)(g->nslotcoef > 0 ? g->nslotcoef : 1));
+        const size_t b_part = align256(sizeof(cd) * (size_t)(g->n_m2l_parts > 0 ? g->n_m2l_parts : 1) * 3 * XT_W);
+        const size_t need = b_xs + b_ys + 2 * b_m + 2 * b_mp + b_part;
+        if (need > LFMM_STATIC_SCRATCH_BYTES)
+            throw ArgError{"geometry needs " + std::to_string(need) + " bytes of work memory; lfmm_matvec_static holds " +
+                           std::to_string((size_t)LFMM_STATIC_SCRATCH_BYTES) + " (use lfmm_matvec)"};
+        // other calls on this geometry wait while its buffer fields point at the array
+        std::lock_guard<std::mutex> call_lock(g->call_mu);
         unsigned char* base = (unsigned char*)scratch_address();
+        ScratchSwap keep(g);
+        g->prof.on = false;   // the stage timers synchronise the stream; this entry point never does
         size_t o = 0;
         g->d_xs = (cd*)(base + o); o += b_xs;
         g->d_ys = (cd*)(base + o); o += b_ys;
@@ -99,18 +121,6 @@ extern "C" lfmm_status lfmm_matvec_static(lfmm_geometry g, const void* x, void* 
         gather_sorted(g, (const cd*)x, g->d_xs, 1, s);
         apply_operator_sorted(g, g->d_xs, g->d_ys, 1, s);
         scatter_sorted(g, g->d_ys, (cd*)y, 1, s);
-    } catch (const CudaError& e) {
-        set_error(e.msg);
-        st = LFMM_ERR_CUDA;
-    } catch (...) {
-        set_error("unknown error");
-        st = LFMM_ERR_CUDA;
-    }
-    g->d_xs = sxs; g->d_ys = sys; g->d_M = sM; g->d_L = sL; g->d_Mp = sMp; g->d_Lp = sLp;
-    g->d_m2l_part = spart;
-    g->nrhs_cap = s_nrhs;
-    g->coef_cols = s_cols;
-    g->m2l_part_cols = s_pcols;
-    g->prof.on = s_prof;
-    return st;
+        return LFMM_OK;
+    });
 }

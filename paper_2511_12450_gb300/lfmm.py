@@ -40,6 +40,7 @@ EXPORTED = [
     "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
     "lfmm_rhs_plane_wave", "lfmm_matvec", "lfmm_gmres_solve", "lfmm_eval_field",
     "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error", "lfmm_matvec_static",
+    "lfmm_precond_apply",
     "lfmm_server_create", "lfmm_server_submit", "lfmm_server_wait", "lfmm_server_stats", "lfmm_server_destroy",
 ]
 
@@ -109,6 +110,7 @@ def library():
         lib.lfmm_rhs_plane_wave.argtypes = [vp, i32, dp, vp, i32, vp]
         lib.lfmm_matvec.argtypes = [vp, i32, vp, vp, i32, vp]
         lib.lfmm_matvec_static.argtypes = [vp, vp, vp, vp]
+        lib.lfmm_precond_apply.argtypes = [vp, i32, vp, vp, i32, vp]
         lib.lfmm_gmres_solve.argtypes = [vp, i32, vp, vp, ctypes.POINTER(GmresParams), ctypes.POINTER(GmresInfo), vp]
         lib.lfmm_eval_field.argtypes = [vp, i32, vp, i64, dp, vp, i32, vp]
         lib.lfmm_polygon_elements.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]
@@ -269,14 +271,29 @@ def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False, simt_m2l: b
     return y
 
 
+def precond_apply(g: Geometry, x, y=None, stream=None):
+    """y = P^{-1} x, the overlapping domain-decomposition preconditioner (Sec. 4.2) alone."""
+    xp, nrhs, flags, keep = _vec_args(x, g.n, allow_c64=False)
+    if y is None:
+        y = _empty_like(x, g.n, nrhs)
+    yp, _, flags_y, keep_y = _vec_args(y, g.n, allow_c64=False)
+    if flags != flags_y:
+        raise ValueError("x and y must both be host arrays or both device tensors")
+    st = _stream_of(stream) if flags & LFMM_DEVICE_PTRS else ctypes.c_void_p(0)
+    _check(library().lfmm_precond_apply(g.handle, nrhs, xp, yp, flags, st))
+    return y
+
+
 def matvec_static(g: Geometry, x, y, stream=None):
     """y = K x with the library's fixed device work array (device tensors, one column, no allocation)."""
     if not (_is_torch_cuda(x) and _is_torch_cuda(y)):
         raise TypeError("matvec_static takes CUDA tensors")
+    # contiguous complex128 only: the library reads and writes 16 n bytes through these pointers
+    xp, nx, fx, keep = _vec_args(x, g.n, allow_c64=False)
+    yp, ny, fy, keep_y = _vec_args(y, g.n, allow_c64=False)
     if x.numel() != g.n or y.numel() != g.n:
         raise ValueError("one column of n entries expected")
-    _check(library().lfmm_matvec_static(g.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                        _stream_of(stream)))
+    _check(library().lfmm_matvec_static(g.handle, xp, yp, _stream_of(stream)))
     return y
 
 

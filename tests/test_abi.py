@@ -136,3 +136,25 @@ def test_failed_geometry_build_returns_a_null_handle(lib):
     assert st == lib.LFMM_ERR_NODE_ON_INTERFACE
     assert not h.value
     assert "interface" in lib.library().lfmm_last_error().decode()
+
+
+def test_static_matvec_and_precond_reject_host_or_wrong_vectors_in_the_binding(lib):
+    # the binding refuses what the device entry points would read out of bounds, before
+    # any call into the library (no geometry or GPU needed)
+    g = lib.Geometry(None, None, 8)
+    x = np.zeros(8, dtype=np.complex128)
+    with pytest.raises(TypeError):
+        lib.matvec_static(g, x, np.zeros(8, dtype=np.complex128))   # host arrays
+    with pytest.raises(TypeError):
+        lib.precond_apply(g, x.astype(np.complex64))                # single precision
+
+
+def test_null_arguments_rejected_by_every_vector_entry_point(lib):
+    import ctypes
+
+    so = lib.library()
+    buf = (ctypes.c_double * 4)()
+    assert so.lfmm_matvec_static(None, buf, buf, None) == lib.LFMM_ERR_INVALID_ARG
+    assert "NULL" in so.lfmm_last_error().decode()
+    assert so.lfmm_precond_apply(None, 1, buf, buf, 0, None) == lib.LFMM_ERR_INVALID_ARG
+    assert so.lfmm_matvec(None, 1, buf, buf, 0, None) == lib.LFMM_ERR_INVALID_ARG

@@ -1,0 +1,78 @@
+"""The precision form's own workload at full size on the GPU: C3, four layers (interfaces
+y = 0, -6, -12; k = 6, 10, 8, 12; eta = 1..4), 1024 circles/ellipses x 1024 nodes over
+[-40, 40] x [-18, 6] (seed 12453), N = 1,048,576, p = 20, leaf 64 -- the launch configuration
+of the benchmark's C3 block.
+
+Expected values: the 64 stored oracle rows of tests/golden/c3_sampled_rows.json (y = K x for
+x non-zero on a seeded 4,096-point subset; 8 of the rows have their own column in the subset,
+so the self terms are covered).  The FP64 operator is held to the FMM truncation level at
+p = 20 measured on these rows (worst 9.8e-8, median 1e-11); the precision form to its FP32
+level, and against the FP64 operator on a dense random x.
+"""
+
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROW_TOL_FP64 = 3e-7
+ROW_TOL_MIXED = 5e-6
+OP_TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def c3(gpu_lib):
+    from workloads import config_c3
+
+    lf = gpu_lib
+    wl = config_c3()
+    med = wl.medium
+    pts, w, nrm = lf.polygon_elements(wl.bodies)
+    M = lf.medium_create(med.interfaces, med.k, med.eta)
+    G = lf.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size)
+    yield dict(lf=lf, G=G, M=M)
+    G.destroy()
+
+
+def test_c3_sampled_rows_fp64_and_precision_form(c3):
+    import torch
+
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    import make_c3_sampled_rows as gen
+
+    lf, G = c3["lf"], c3["G"]
+    with open(os.path.join(HERE, "golden", "c3_sampled_rows.json")) as f:
+        d = json.load(f)
+    assert d["n"] == G.n
+    cols, xs, rows = gen.sample(G.n)
+    x = np.zeros(G.n, dtype=np.complex128)
+    x[cols] = xs
+    xt = torch.from_numpy(x).cuda()
+    ref = np.array([complex(*v) for v in d["y"]])
+    for mixed, tol in ((False, ROW_TOL_FP64), (True, ROW_TOL_MIXED)):
+        y = lf.matvec(G, xt, mixed=mixed).cpu().numpy()[rows]
+        err = np.abs(y - ref) / np.abs(ref)
+        print(f"C3 {'precision form' if mixed else 'FP64'}: 64 oracle rows, max rel err {err.max():.3e}, "
+              f"median {np.median(err):.3e}")
+        assert err.max() <= tol
+
+
+def test_c3_precision_form_against_fp64(c3):
+    import torch
+
+    lf, G = c3["lf"], c3["G"]
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.complex(torch.randn(G.n, generator=gen, dtype=torch.float64),
+                      torch.randn(G.n, generator=gen, dtype=torch.float64)).cuda()
+    y64 = lf.matvec(G, x)
+    y32 = lf.matvec(G, x, mixed=True)
+    d = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
+    print(f"C3 precision form vs FP64 (dense random x): {d:.3e}")
+    assert d <= OP_TOL_MIXED
+    # repeated products give the same bits (fixed summation order in every kernel)
+    assert torch.equal(lf.matvec(G, x), y64)

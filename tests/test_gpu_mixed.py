@@ -143,3 +143,35 @@ def test_kernel_shared_memory_limits_only_grow_across_geometries(c2):
     assert max(relerr(y_small[:, c], y_big64[:, c]) for c in range(16)) <= 1e-2
     assert np.array_equal(lf.matvec(G, X, mixed=True), y_big)
     assert np.array_equal(lf.matvec(G, X), y_big64)
+
+
+def test_precision_form_near_field_split(gpu_lib):
+    # Every pair near (leaf size above N).  In three layers the single block holds
+    # reaction (Sommerfeld) entries, so the precision form keeps it in FP64 and equals
+    # the FP64 operator bit for bit.  In one layer the block holds only free-space
+    # entries: its off-diagonal entries go to complex64 (FP32 products), the self terms
+    # I^s stay FP64, and the difference from the FP64 operator is FP32 rounding.
+    from workloads import Medium, layered_small
+
+    lf = gpu_lib
+    wl = layered_small(n_bodies=3, nodes=150, seed=7)
+    pts, w, _, _ = onys.elements(wl.bodies)
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal(pts.shape[0]) + 1j * rng.standard_normal(pts.shape[0])
+    med = wl.medium
+    G3 = lf.geometry_build(lf.medium_create(med.interfaces, med.k, med.eta), pts, w, p=20, leaf_size=1024)
+    assert np.array_equal(lf.matvec(G3, x, mixed=True), lf.matvec(G3, x))
+    one = Medium(interfaces=[], k=[4.0], eta=[1.0])
+    K1 = onys.dense_matrix(one, pts, w)
+    G1 = lf.geometry_build(lf.medium_create(one.interfaces, one.k, one.eta), pts, w, p=20, leaf_size=1024)
+    y64, y32 = lf.matvec(G1, x), lf.matvec(G1, x, mixed=True)
+    d, d_or = relerr(y32, y64), relerr(y32, K1 @ x)
+    print(f"one layer, all near: precision form vs FP64 {d:.3e}, vs oracle {d_or:.3e}")
+    assert 1e-12 < d <= 3e-7 and d_or <= 3e-7
+    # the self terms are applied in FP64: on a vector with one non-zero entry the
+    # diagonal entry of the product carries no FP32 rounding
+    e = np.zeros(pts.shape[0], dtype=np.complex128)
+    e[17] = 1.0
+    d17 = lf.matvec(G1, e)[17]
+    assert lf.matvec(G1, e, mixed=True)[17] == d17
+    assert abs(d17 - K1[17, 17]) <= 1e-12 * abs(K1[17, 17])
