@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblfmm.so")
-SOURCES = ["api.cu", "near.cu", "fmm.cu", "solver.cu", "precond.cu", "tree.cpp", "static_scratch.cu", "mixed.cu", "serve.cpp"]
+SOURCES = ["api.cu", "near.cu", "fmm.cu", "solver.cu", "precond.cu", "tree.cpp", "tree_gpu.cu", "static_scratch.cu", "mixed.cu", "serve.cpp"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without contraction of a*b+c into FMA (GCC's default on aarch64, not on x86): the

@@ -41,10 +41,16 @@ struct TreeHost {
     double cy(int b) const { return y0 + (box_iy[b] + 0.5) * width(box_level[b]); }
 };
 
-// Builds the quadtree and all interaction lists (tree.cpp).  Throws std::runtime_error
+// Builds the quadtree and all interaction lists on the host (tree.cpp: the reference
+// statement of the tree definition, run by the CPU tests).  Throws std::runtime_error
 // on invalid input.
 void build_tree(TreeHost& t, const std::vector<double>& px, const std::vector<double>& py,
                 const std::vector<int>& layer, const MediumDev& med, int p, int leaf_size);
+// The same tree and lists built on the GPU from device arrays of the input points and
+// their layers (tree_gpu.cu), equal to build_tree's bit for bit; the library builds every
+// geometry's tree this way.
+void build_tree_gpu(TreeHost& t, const double* d_px, const double* d_py, const int* d_layer, int64_t n,
+                    const MediumDev& med, int p, int leaf_size);
 
 // End of the real-axis stretch of the moment tables' contour, just past the largest
 // branch point (the M2L table rule and the tree's admissibility test share it).
