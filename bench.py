@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the million-point four-layer workload block")
+    ap.add_argument("--only-c3", action="store_true",
+                    help="run only the million-point four-layer workload block (--steps timed matvecs per operator) "
+                         "and print it as one JSON line")
     ap.add_argument("--autotune", type=int, default=0,
                     help="1: choose the M2L work-item schedule by timing at set-up")
     ap.add_argument("--replay", action="store_true",
@@ -446,6 +449,74 @@ def run_batch(lfmm, index=10, steps=5):
                                        "max_rel_diff_vs_one_by_one": same_solve}}
 
 
+def run_batch16(lfmm, steps=3):
+    """The whole batching configuration: 16 geometries of uneven size (N from 4k to 128k,
+    2-4 layers, k in [2, 12]), each with its 32 incidence angles as a block right-hand side.
+    One block matvec per geometry with its own launches, against all 16 in shared launches
+    (lfmm_matvec_batch: one launch per stage for all geometries), in complex128 and
+    complex64 vectors; every geometry's fused result must equal its own launches' bit for bit.
+    The precision form (tensor-core M2L for the 32 columns) runs per geometry, with its
+    difference from FP64 per geometry."""
+    import torch
+
+    from workloads import config_c4
+
+    wls = config_c4()
+    t0 = time.perf_counter()
+    Gs, Bs = [], []
+    for wl in wls:
+        med = wl.medium
+        M = lfmm.medium_create(med.interfaces, med.k, med.eta)
+        pts, w, nrm = lfmm.polygon_elements(wl.bodies)
+        G = lfmm.geometry_build(M, pts, w, nrm, p=wl.p, leaf_size=wl.leaf_size)
+        Gs.append(G)
+        Bs.append(lfmm.rhs_plane_wave(G, np.radians(wl.angles_deg), device=True))
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        tot = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot.append(e0.elapsed_time(e1))
+        return float(np.median(tot)) * 1e-3
+
+    Y1 = [torch.empty_like(b) for b in Bs]
+    t_own = timed(lambda: [lfmm.matvec(G, b, y) for G, b, y in zip(Gs, Bs, Y1)])
+    Y2 = [torch.empty_like(b) for b in Bs]
+    t_fused = timed(lambda: lfmm.matvec_batch(Gs, Bs, Y2))
+    same = all(bool(torch.equal(a, b)) for a, b in zip(Y1, Y2))
+    B32 = [b.to(torch.complex64) for b in Bs]
+    Y32 = [torch.empty_like(b) for b in B32]
+    t_fused32 = timed(lambda: lfmm.matvec_batch(Gs, B32, Y32))
+    Ym = [torch.empty_like(b) for b in Bs]
+    t_mixed = timed(lambda: [lfmm.matvec(G, b, y, mixed=True) for G, b, y in zip(Gs, Bs, Ym)])
+    diffs = [max(float(torch.linalg.norm(m[c] - y[c]) / torch.linalg.norm(y[c])) for c in range(m.shape[0]))
+             for m, y in zip(Ym, Y1)]
+    work = sum(G.n * b.shape[0] for G, b in zip(Gs, Bs))
+    out = {"metric": "block right-hand side matvec over 16 uneven geometries, Mpts*rhs/s",
+           "workload": f"16 geometries, N {min(G.n for G in Gs)}..{max(G.n for G in Gs)} (total "
+                       f"{sum(G.n for G in Gs)}), 2-4 layers, 32 incidence angles each",
+           "setup_seconds": setup_s,
+           "own_launches_value": work / t_own / 1e6, "own_launches_ms": t_own * 1e3,
+           "fused_value": work / t_fused / 1e6, "fused_ms": t_fused * 1e3,
+           "fused_complex64_value": work / t_fused32 / 1e6, "fused_complex64_ms": t_fused32 * 1e3,
+           "fused_equals_own_launches_bitwise": same,
+           "mixed_tensor_core_value": work / t_mixed / 1e6, "mixed_tensor_core_ms": t_mixed * 1e3,
+           "mixed_vs_fp64_max_rel_diff_per_geometry": diffs}
+    for G in Gs:
+        G.destroy()
+    return out
+
+
 # the paper's Tables 5.1-5.3 (Sec. 5): elements, GMRES iterations without / with the DD
 # preconditioner, and for Example 1 the L_inf error column (CPU times on unstated hardware
 # are context only and not compared)
@@ -631,6 +702,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         lfmm.matvec(G, x, ym, mixed=True)
     torch.cuda.synchronize()
+    stm0 = lfmm.stage_times(G)
     mtimes = []
     for _ in range(args.steps):
         flush.zero_()
@@ -642,9 +714,28 @@ def run_ours(args):
         e1.synchronize()
         mtimes.append(e0.elapsed_time(e1))
     mixed_value, mixed_s = whole_job_throughput(float(np.sum(mtimes)) * 1e-3, n * args.steps, dist, "cuda")
-    mixed = {"metric": "FMM matvec Mpts/s, precision form (FP32 M2L on scaled expansions)",
+    mixed = {"metric": "FMM matvec Mpts/s, precision form (FP32 far field on scaled expansions, complex64 "
+                       "regular near field)",
              "value": mixed_value, "ms_per_step": mixed_s * 1e3 / args.steps,
              "op_rel_diff": float(torch.linalg.norm(ym - y) / torch.linalg.norm(y))}
+    # the precision form's near field against HBM: complex64 regular blocks, FP64 reaction
+    # blocks, the FP64 diagonal, x in FP64 and complex64, y read and written
+    ne = lfmm.geometry_query(G, "near_entries", np.float64)
+    near32_bytes = 8.0 * ne[1] + 16.0 * ne[2] + (16.0 + 16.0 + 8.0 + 32.0) * n
+    stm1 = lfmm.stage_times(G)
+    mixed["stages_ms_per_step"] = {k: (stm1[k]["ms"] - stm0[k]["ms"]) / max(stm1[k]["count"] - stm0[k]["count"], 1)
+                                   for k in stm1}
+    near_s = mixed["stages_ms_per_step"]["near"] * 1e-3
+    peaks_m, src_m = measured_peaks()
+    hbm = float(peaks_m.get("hbm_gbs", HBM_FALLBACK_GBS))
+    mixed["near_roofline"] = {"kernel": "k_near_leaf (precision form)", "bound": "hbm",
+                              "achieved": near32_bytes / near_s / 1e9 if near_s > 0 else None, "peak": hbm,
+                              "unit": "GB/s",
+                              "frac": (near32_bytes / near_s / 1e9 / hbm) if near_s > 0 else None,
+                              "peak_source": src_m, "note": "timed inside the matvec, beside the far field"}
+    mixed["near_entries_complex64"] = int(ne[1])
+    mixed["near_entries_fp64"] = int(ne[2])
+    mixed["near_bytes_per_launch"] = near32_bytes
 
     solve = None
     if not args.no_solve:
@@ -672,6 +763,7 @@ def run_ours(args):
     batch = None
     if rank == 0 and not args.no_batch and args.workload == "c2":
         batch = run_batch(lfmm)
+        batch["all_16_geometries"] = run_batch16(lfmm)
     serve = None
     if rank == 0 and not args.no_serve and args.workload == "c2":
         serve = run_serving(lfmm)
@@ -720,6 +812,14 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_c3:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2511_12450_gb300 import lfmm
+
+        print(json.dumps({"c3": run_c3(lfmm, steps=args.steps), "data": "synthetic", "dtype": "f64"}))
+        return 0
     return run_ours(args)
 
 

@@ -14,7 +14,8 @@
  *  - All functions are extern "C", never throw, and return an lfmm_status.
  *    On error, lfmm_last_error() returns a thread-local message valid until
  *    the next call on the same thread.  Argument errors are reported before
- *    any device work.
+ *    any device work, except lfmm_geometry_build's check of the leaf size
+ *    against the order at the leaves, which needs the tree (built on the GPU).
  *  - Complex vectors are interleaved (re, im) double precision (single
  *    precision with LFMM_C64, where a call takes flags), column-major
  *    [n x nrhs] (column j starts at element j*n).  Device vectors must be
@@ -210,6 +211,25 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void *x, void *y,
                         int32_t flags, void *stream);
 
 /*
+ * y_i = K_i x_i for n_geo geometries at once (no counterpart in the paper, which
+ * treats one problem at a time): each stage of the operator -- near field, P2M,
+ * every M2M pass, M2L with its reductions, every L2L pass, L2P -- runs as one
+ * launch whose blocks cover all the geometries' work, so many small or uneven
+ * problems fill the GPU together.  Each y_i equals lfmm_matvec(geos[i], nrhs[i],
+ * x[i], y_i) bit for bit (the same kernel bodies sum in the same order).
+ *   geos : n_geo distinct geometries (one may not appear twice)
+ *   nrhs : n_geo column counts; x[i], y[i] : [n_i x nrhs[i]] DEVICE vectors
+ *          (flags must contain LFMM_DEVICE_PTRS; LFMM_C64 for complex64
+ *          vectors, widened and rounded as in lfmm_matvec), valid on `stream`
+ * The FP64 operator (LFMM_MIXED is not taken).  Holds every geometry's lock for
+ * the call.  Errors: LFMM_ERR_INVALID_ARG for NULL or overlapping vectors, other
+ * flags, a repeated geometry, nrhs < 1, misaligned vectors; LFMM_ERR_CUDA,
+ * LFMM_ERR_OUT_OF_MEMORY from the work buffers.
+ */
+lfmm_status lfmm_matvec_batch(int32_t n_geo, const lfmm_geometry *geos, const int32_t *nrhs,
+                              const void *const *x, void *const *y, int32_t flags, void *stream);
+
+/*
  * y = P^{-1} x, the overlapping domain-decomposition preconditioner of Sec. 4.2
  * alone (the operator lfmm_gmres_solve applies on the right when prm->precond
  * is set).  For every leaf box B of every layer's tree, P_B is the local matrix
@@ -379,6 +399,10 @@ lfmm_status lfmm_server_destroy(lfmm_server s);
  * near-field entries, reaction M2L tables, set-up seconds),
  * "stage_times" (double[2*8]: per stage p2m, m2m, m2l, l2l, l2p, near, gather,
  * scatter the number of timed launches and their total milliseconds),
+ * "near_entries" (double[3]: stored near-field entries of the FP64 operator; of the
+ * precision form, entries held in complex64 and in FP64 -- 0 until its first call),
+ * "setup_times" (double[4]: seconds of the set-up spent on the tree and interaction
+ * lists, the near field, the far field (moment tables, translation plans), and in all),
  * "launch_count" (double[1]: kernels launched so far by this geometry's
  * matvec path -- gather, P2M, M2M, M2L, L2L, L2P, near field, scatter --
  * counted on the host as they are enqueued),

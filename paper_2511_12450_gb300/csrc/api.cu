@@ -72,6 +72,8 @@ static void gauss_legendre8(double* x, double* w) {
 QuadRule make_quad_rule(const MediumDev& m) {
     QuadRule q;
     q.T = 1.2 * m.kmax + 1.0;
+    q.kmin = m.k[0];
+    for (int l = 1; l < m.nl; ++l) q.kmin = std::min(q.kmin, m.k[l]);
     q.es_v0 = -3.6;
     q.es_hv = 0.07;
     q.nes = 84;          // v in [-3.6, 2.21]
@@ -179,6 +181,9 @@ static void free_geometry(lfmm_geometry_s* g) {
     dev_release(g->d_ys);
     dev_release(g->d_hostbuf_x);
     dev_release(g->d_hostbuf_y);
+    dev_release(g->d_near_x32);
+    g->d_near_x32 = nullptr;
+    g->near_x32_cap = 0;
     cudaStreamSynchronize(cudaStreamPerThread);
 }
 
@@ -311,7 +316,28 @@ static lfmm_geometry_s* build_geometry(lfmm_medium med, int64_t n, const double*
                 cuda_check(cudaEventCreate(&g->prof.ev[k]), "event create");
             g->prof.on = true;
         }
-        build_tree(g->tree, px, py, layer, m, p, leaf);
+        auto since = [](std::chrono::steady_clock::time_point a) {
+            return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+        };
+        auto tp = std::chrono::steady_clock::now();
+        {   // the tree and lists on the GPU, from the input points and their layers
+            double *d_px = nullptr, *d_py = nullptr;
+            int* d_lay = nullptr;
+            cudaStream_t ts = cudaStreamPerThread;
+            cuda_check(cudaMallocAsync((void**)&d_px, sizeof(double) * n, ts), "malloc points");
+            cuda_check(cudaMallocAsync((void**)&d_py, sizeof(double) * n, ts), "malloc points");
+            cuda_check(cudaMallocAsync((void**)&d_lay, sizeof(int) * n, ts), "malloc layers");
+            struct F {
+                double *a, *b;
+                int* c;
+                ~F() { cudaFreeAsync(a, cudaStreamPerThread); cudaFreeAsync(b, cudaStreamPerThread); cudaFreeAsync(c, cudaStreamPerThread); }
+            } fr{d_px, d_py, d_lay};
+            cuda_check(cudaMemcpyAsync(d_px, px.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ts), "points");
+            cuda_check(cudaMemcpyAsync(d_py, py.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ts), "points");
+            cuda_check(cudaMemcpyAsync(d_lay, layer.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ts), "layers");
+            build_tree_gpu(g->tree, d_px, d_py, d_lay, n, m, p, leaf);
+        }
+        g->setup_phase[0] = since(tp);
         TreeHost& t = g->tree;
         if (t.l0 <= t.D) {   // the leaf P2M / L2P stage a group's basis rows in shared memory
             int mx = EXP_GROUP_PTS;
@@ -370,10 +396,14 @@ static lfmm_geometry_s* build_geometry(lfmm_medium med, int64_t n, const double*
         cuda_check(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
         cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "event");
         cuda_check(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "event");
+        tp = std::chrono::steady_clock::now();
         near_build(g);
+        g->setup_phase[1] = since(tp);
+        tp = std::chrono::steady_clock::now();
         fmm_build(g);
+        g->setup_phase[2] = since(tp);
         if (prm && (prm->flags & LFMM_AUTOTUNE)) fmm_autotune(g);
-        g->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        g->setup_seconds = since(t0);
         return g;
     } catch (...) {
         if (g) {
@@ -446,6 +476,47 @@ lfmm_status lfmm_matvec(lfmm_geometry g, int32_t nrhs, const void* x, void* y, i
             cuda_check(cudaMemcpyAsync(y, g->d_hostbuf_y, esz * elems, cudaMemcpyDeviceToHost, s), "y d2h");
             cuda_check(cudaStreamSynchronize(s), "matvec sync");
             mixed_check_waits(g);
+        }
+        return LFMM_OK;
+    });
+}
+
+lfmm_status lfmm_matvec_batch(int32_t n_geo, const lfmm_geometry* geos, const int32_t* nrhs, const void* const* x,
+                              void* const* y, int32_t flags, void* stream) {
+    return guarded([&]() -> lfmm_status {
+        require(n_geo >= 1 && geos != nullptr && nrhs != nullptr && x != nullptr && y != nullptr, "NULL argument");
+        require((flags & LFMM_DEVICE_PTRS) != 0, "lfmm_matvec_batch takes device vectors (LFMM_DEVICE_PTRS)");
+        require((flags & ~(LFMM_DEVICE_PTRS | LFMM_C64)) == 0,
+                "lfmm_matvec_batch takes LFMM_DEVICE_PTRS, optionally with LFMM_C64, as flags");
+        const bool c64 = (flags & LFMM_C64) != 0;
+        std::vector<lfmm_geometry_s*> order;
+        for (int i = 0; i < n_geo; ++i) {
+            require(geos[i] != nullptr && x[i] != nullptr && y[i] != nullptr, "NULL geometry or vector");
+            require(nrhs[i] >= 1, "nrhs must be >= 1");
+            require(x[i] != y[i], "x and y must not overlap");
+            require((uintptr_t)x[i] % 8 == 0 && (uintptr_t)y[i] % 8 == 0, "device vectors must be 8-byte aligned");
+            order.push_back(geos[i]);
+        }
+        std::sort(order.begin(), order.end());
+        require(std::adjacent_find(order.begin(), order.end()) == order.end(),
+                "a geometry appears twice in the batch");
+        // every geometry's lock, in address order (no lock-order inversion between batches)
+        std::vector<std::unique_lock<std::mutex>> locks;
+        for (lfmm_geometry_s* g : order) locks.emplace_back(g->call_mu);
+        cudaStream_t s = as_stream(stream);
+        std::vector<BatchOp> ops;
+        for (int i = 0; i < n_geo; ++i) {
+            lfmm_geometry_s* g = geos[i];
+            ensure_scratch(g, nrhs[i]);
+            if (c64) gather_sorted_c64(g, (const float2*)x[i], g->d_xs, nrhs[i], s);
+            else gather_sorted(g, (const cd*)x[i], g->d_xs, nrhs[i], s);
+            ops.push_back(BatchOp{g, g->d_xs, g->d_ys, nrhs[i]});
+        }
+        apply_operator_batch_sorted(ops, s);
+        for (int i = 0; i < n_geo; ++i) {
+            lfmm_geometry_s* g = geos[i];
+            if (c64) scatter_sorted_c64(g, g->d_ys, (float2*)y[i], nrhs[i], s);
+            else scatter_sorted(g, g->d_ys, (cd*)y[i], nrhs[i], s);
         }
         return LFMM_OK;
     });
@@ -697,6 +768,14 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
         } else if (nm == "tree_params") {
             dtmp = {t.x0, t.y0, t.W, (double)t.D, (double)t.l0, (double)t.nbox, (double)t.comps.size(),
                     (double)g->n_blocks, (double)g->nb_nnz, (double)g->n_rkeys, g->setup_seconds};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "near_entries") {
+            dtmp = {(double)g->nb_nnz, (double)g->near32_nnz, (double)g->near64r_nnz};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "setup_times") {
+            dtmp = {g->setup_phase[0], g->setup_phase[1], g->setup_phase[2], g->setup_seconds};
             src = dtmp.data();
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "launch_count") {

@@ -694,6 +694,245 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     }
 }
 
+// ------------------------------------------------------------------ batched far field
+// Several geometries' far fields in shared launches.  Each launch gets a table of jobs
+// (one geometry's arguments for the stage) and the prefix of their block counts; a CTA
+// finds its job by binary search over the prefix and runs the same body as the
+// single-geometry kernel with its block index within the job, so every geometry's
+// result is the one its own launches give, bit for bit.
+struct P2MJob {
+    const ExpGroup* groups;
+    const ExpEntry* ent;
+    MediumDev m;
+    const double *px, *py, *pw, *nx, *ny;
+    const cd* phi;
+    int64_t n, stride;
+    int nrhs;
+    cd* M;
+};
+struct L2PJob {
+    const ExpGroup* groups;
+    const ExpEntry* ent;
+    MediumDev m;
+    const double *px, *py;
+    int64_t n, stride;
+    int nrhs;
+    const cd* L;
+    cd* y;
+};
+struct XJob {
+    const XDst* dsts;
+    const XSrc* srcs;
+    const cd* vec;
+    int accumulate, w, nchunk, nrhs;
+    int64_t ncoef, nslotcoef;
+    cd *X, *Xp;
+};
+struct M2LJob {
+    const M2LItem* items;
+    const M2LReduce* reds;
+    const M2LEnt* ents;
+    const int *box_level, *p_level, *slot_of;
+    const int64_t *coef_off, *slot_coef, *m2lf_off;
+    const cd *m2lf, *m2lr;
+    int nrhs, nparts;
+    int64_t ncoef, nslotcoef;
+    const cd *M, *Mp;
+    cd *L, *Lp, *part;
+};
+
+__device__ __forceinline__ int job_of(const int* __restrict__ prefix, int njobs, int b) {
+    int lo = 0, hi = njobs - 1;   // the last job whose first block is <= b (jobs without blocks are passed over)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__global__ void __launch_bounds__(128) k_p2m_multi(const P2MJob* __restrict__ jobs, const int* __restrict__ prefix,
+                                                   int njobs) {
+    const int j = job_of(prefix, njobs, blockIdx.x);
+    const P2MJob& J = jobs[j];
+    p2m_group(blockIdx.x - prefix[j], J.groups, J.ent, J.m, J.px, J.py, J.pw, J.nx, J.ny, J.phi, J.n, J.nrhs,
+              J.stride, J.M);
+}
+__global__ void __launch_bounds__(128) k_l2p_multi(const L2PJob* __restrict__ jobs, const int* __restrict__ prefix,
+                                                   int njobs) {
+    const int j = job_of(prefix, njobs, blockIdx.x);
+    const L2PJob& J = jobs[j];
+    l2p_group(blockIdx.x - prefix[j], J.groups, J.ent, J.m, J.px, J.py, J.n, J.nrhs, J.stride, J.L, J.y);
+}
+__global__ void __launch_bounds__(128) k_translate_multi(const XJob* __restrict__ jobs, const int* __restrict__ prefix,
+                                                         int njobs) {
+    const int j = job_of(prefix, njobs, blockIdx.x);
+    const XJob& J = jobs[j];
+    const int b = blockIdx.x - prefix[j];
+    translate_dst(b / J.nchunk, b % J.nchunk, J.dsts, J.srcs, J.vec, J.accumulate, J.w, J.nrhs, J.ncoef, J.nslotcoef,
+                  J.X, J.Xp);
+}
+__global__ void __launch_bounds__(128) k_m2l_multi(const M2LJob* __restrict__ jobs, const int* __restrict__ prefix,
+                                                   int njobs) {
+    const int j = job_of(prefix, njobs, blockIdx.x);
+    const M2LJob& J = jobs[j];
+    m2l_item(blockIdx.x - prefix[j], J.items, J.ents, J.box_level, J.p_level, J.coef_off, J.slot_of, J.slot_coef,
+             J.m2lf, J.m2lf_off, J.m2lr, J.nrhs, J.ncoef, J.nslotcoef, J.nparts, J.M, J.Mp, J.L, J.Lp, J.part);
+}
+__global__ void __launch_bounds__(64) k_m2l_reduce_multi(const M2LJob* __restrict__ jobs,
+                                                         const int* __restrict__ prefix, int njobs) {
+    const int j = job_of(prefix, njobs, blockIdx.x);
+    const M2LJob& J = jobs[j];
+    m2l_reduce_one(blockIdx.x - prefix[j], J.reds, J.box_level, J.p_level, J.coef_off, J.slot_of, J.slot_coef,
+                   J.nrhs, J.ncoef, J.nslotcoef, J.nparts, J.part, J.L, J.Lp);
+}
+
+void JobTables::upload(cudaStream_t s) {
+    if (host.empty()) return;
+    cuda_check(cudaMallocAsync((void**)&dev, host.size(), s), "cudaMallocAsync job tables");
+    // from pageable memory: the call returns once the bytes are staged, so the host
+    // vector may change afterwards
+    cuda_check(cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s), "job tables h2d");
+}
+void JobTables::release(cudaStream_t s) {
+    if (dev) cudaFreeAsync(dev, s);
+    dev = nullptr;
+}
+
+// One fused launch: jobs of type J with their block counts; no launch without blocks.
+template <class J, class K>
+static void launch_jobs(const std::vector<J>& jobs, const std::vector<int>& blocks, K kernel, int threads, size_t smem,
+                        cudaStream_t s, const char* what) {
+    std::vector<int> prefix(jobs.size() + 1, 0);
+    for (size_t i = 0; i < jobs.size(); ++i) prefix[i + 1] = prefix[i] + blocks[i];
+    if (jobs.empty() || prefix.back() == 0) return;
+    JobTables t;
+    const size_t oj = t.add(jobs.data(), sizeof(J) * jobs.size());
+    const size_t op = t.add(prefix.data(), sizeof(int) * prefix.size());
+    t.upload(s);
+    kernel<<<prefix.back(), threads, smem, s>>>(t.at<J>(oj), t.at<int>(op), (int)jobs.size());
+    cudaError_t e = cudaGetLastError();
+    t.release(s);
+    cuda_check(e, what);
+}
+
+void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_t before_l2p) {
+    set_smem_limits();
+    std::vector<const BatchOp*> far;
+    size_t smem_p2m = 0, smem_l2p = 0;
+    int max_up = 0, max_dn = 0;
+    for (const BatchOp& op : ops) {
+        lfmm_geometry_s* g = op.g;
+        const TreeHost& t = g->tree;
+        if (t.l0 > t.D) continue;
+        far.push_back(&op);
+        ensure_coef(g, op.nrhs);
+        if (g->n_m2l_parts > 0 && g->m2l_part_cols < op.nrhs) {
+            dev_release_now(g->d_m2l_part);
+            g->d_m2l_part = nullptr;
+            g->d_m2l_part = (cd*)dev_alloc_ready(sizeof(cd) * (size_t)g->n_m2l_parts * 3 * XT_W * op.nrhs,
+                                                 "M2L partial sums");
+            g->m2l_part_cols = op.nrhs;
+        }
+        const int pD = t.p_level[t.D], gp = g->group_max_pts, ge = g->group_max_ent;
+        const int rs = 2 * (g->combined ? pD + 1 : pD) + 1;
+        smem_p2m = std::max(smem_p2m, (size_t)gp * rs * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int));
+        smem_l2p = std::max(smem_l2p, ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd));
+        max_up = std::max(max_up, t.D - t.l0);
+        max_dn = std::max(max_dn, t.D - t.l0);
+    }
+    if (far.empty()) {
+        if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");
+        return;
+    }
+    raise_smem_limit((const void*)k_p2m_multi, smem_p2m, "p2m smem");
+    raise_smem_limit((const void*)k_l2p_multi, smem_l2p, "l2p smem");
+    {   // P2M: leaves about cell centres, straddling leaves about reaction centres
+        std::vector<P2MJob> jobs;
+        std::vector<int> blocks;
+        for (const BatchOp* op : far) {
+            lfmm_geometry_s* g = op->g;
+            jobs.push_back(P2MJob{g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
+                                  op->x, g->n, g->ncoef, op->nrhs, g->d_M});
+            blocks.push_back(g->n_leaf_groups);
+            jobs.push_back(P2MJob{g->d_slot_groups, g->d_slot_entries, g->m, g->d_x, g->d_y, g->d_w, g->d_nx,
+                                  g->d_ny, op->x, g->n, g->nslotcoef, op->nrhs, g->d_Mp});
+            blocks.push_back(g->n_slot_groups);
+        }
+        launch_jobs(jobs, blocks, k_p2m_multi, 128, smem_p2m, s, "k_p2m_multi");
+    }
+    // M2M: pass k takes each geometry's parents at level D - 1 - k (down to its l0)
+    for (int k = 0; k < max_up; ++k) {
+        std::vector<XJob> jobs;
+        std::vector<int> blocks;
+        for (const BatchOp* op : far) {
+            lfmm_geometry_s* g = op->g;
+            const TreeHost& t = g->tree;
+            const int lp = t.D - 1 - k;
+            if (lp < t.l0) continue;
+            const int nd = g->up_end[lp] - g->up_begin[lp];
+            const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco), nch = (nco + w - 1) / w;
+            jobs.push_back(XJob{g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nch, op->nrhs, g->ncoef,
+                                g->nslotcoef, g->d_M, g->d_Mp});
+            blocks.push_back(nd * nch);
+        }
+        launch_jobs(jobs, blocks, k_translate_multi, 128, 0, s, "k_translate_multi (M2M)");
+    }
+    {   // M2L of every level, then the reductions of split items
+        std::vector<M2LJob> jobs;
+        std::vector<int> blocks, rblocks;
+        for (const BatchOp* op : far) {
+            lfmm_geometry_s* g = op->g;
+            const int D = g->tree.D;
+            jobs.push_back(M2LJob{g->d_m2l_items, g->d_m2l_reds, g->d_m2l_ents, g->d_box_level, g->d_p_level,
+                                  g->d_slot_of, g->d_coef_off, g->d_slot_coef, g->d_m2lf_off, g->d_m2lf, g->d_m2lr,
+                                  op->nrhs, g->n_m2l_parts, g->ncoef, g->nslotcoef, g->d_M, g->d_Mp, g->d_L, g->d_Lp,
+                                  g->d_m2l_part});
+            blocks.push_back(g->m2l_item_level_start[D + 1]);
+            rblocks.push_back(g->m2l_red_level_start[D + 1]);
+        }
+        launch_jobs(jobs, blocks, k_m2l_multi, 128, 0, s, "k_m2l_multi");
+        launch_jobs(jobs, rblocks, k_m2l_reduce_multi, 64, 0, s, "k_m2l_reduce_multi");
+    }
+    // L2L: pass k takes each geometry's children at level l0 + 1 + k
+    for (int k = 0; k < max_dn; ++k) {
+        std::vector<XJob> jobs;
+        std::vector<int> blocks;
+        for (const BatchOp* op : far) {
+            lfmm_geometry_s* g = op->g;
+            const TreeHost& t = g->tree;
+            const int l = t.l0 + 1 + k;
+            if (l > t.D) continue;
+            const int nd = g->dn_end[l] - g->dn_begin[l];
+            const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco), nch = (nco + w - 1) / w;
+            jobs.push_back(XJob{g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, w, nch, op->nrhs, g->ncoef,
+                                g->nslotcoef, g->d_L, g->d_Lp});
+            blocks.push_back(nd * nch);
+        }
+        launch_jobs(jobs, blocks, k_translate_multi, 128, 0, s, "k_translate_multi (L2L)");
+    }
+    // L2P after the near field, which adds into the same y
+    if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");
+    // the leaves about cell centres, then (a second launch: both add into the same points
+    // of y) the straddling leaves about their reaction centres, as each geometry's own launches
+    for (int slots = 0; slots < 2; ++slots) {
+        std::vector<L2PJob> jobs;
+        std::vector<int> blocks;
+        for (const BatchOp* op : far) {
+            lfmm_geometry_s* g = op->g;
+            if (slots == 0) {
+                jobs.push_back(L2PJob{g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y, g->n, g->ncoef,
+                                      op->nrhs, g->d_L, op->y});
+                blocks.push_back(g->n_leaf_groups);
+            } else {
+                jobs.push_back(L2PJob{g->d_slot_groups, g->d_slot_leaf_entries, g->m, g->d_x, g->d_y, g->n,
+                                      g->nslotcoef, op->nrhs, g->d_Lp, op->y});
+                blocks.push_back(g->n_slot_groups);
+            }
+        }
+        launch_jobs(jobs, blocks, k_l2p_multi, 128, smem_l2p, s, "k_l2p_multi");
+    }
+}
+
 // Schedule of the M2L work items chosen by measurement on this geometry: the cap
 // on the work of one item (entries x output coefficients; heavier (box, chunk)s
 // are split and their parts reduced) and whether an unsplit box with a narrow

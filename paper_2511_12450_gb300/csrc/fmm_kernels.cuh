@@ -49,12 +49,14 @@ __device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, in
 // n . grad u_n = (k/2)(conj(nu) u_{n-1} - nu u_{n+1}), nu = n_x + i n_y (from
 // (d_x +- i d_y) J_m e^{i m theta} = -+k J_{m+-1} e^{i (m+-1) theta}); the
 // translations are linear and carry it unchanged.
-__global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
-                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
-                      const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
-                      const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
+__device__ __forceinline__ void p2m_group(int gi, const ExpGroup* __restrict__ groups,
+                                          const ExpEntry* __restrict__ ent, const MediumDev& m,
+                                          const double* __restrict__ px, const double* __restrict__ py,
+                                          const double* __restrict__ pw, const double* __restrict__ nx,
+                                          const double* __restrict__ ny, const cd* __restrict__ phi, int64_t n,
+                                          int nrhs, int64_t stride, cd* __restrict__ M) {
     extern __shared__ cd su[];   // [npts][rs] basis rows, then [npts] q, then [nent + 1] point offsets (ints)
-    const ExpGroup G = groups[blockIdx.x];
+    const ExpGroup G = groups[gi];
     const int p = ent[G.e0].p, nco = 2 * p + 1;
     const bool cf = nx != nullptr;
     const int pb = cf ? p + 1 : p, rs = 2 * pb + 1;   // order and length of the plain basis rows
@@ -117,6 +119,12 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
         }
     }
 }
+__global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
+                      const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
+                      const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
+    p2m_group(blockIdx.x, groups, ent, m, px, py, pw, nx, ny, phi, n, nrhs, stride, M);
+}
 
 // M2L into the target boxes of levels >= l0 (free space and reaction components).
 // A CTA of 128 threads takes one work item: W output lanes (W = XT_W, or every
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups
 // tables are column-major (entry (m, n) at n (2p+1) + m).
 #define M2L_STAGE 64
 
-__global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
+__device__ __forceinline__ void m2l_item(int ii, const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
                       const int* __restrict__ box_level, const int* __restrict__ p_level,
                       const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
                       const int64_t* __restrict__ slot_coef, const cd* __restrict__ m2lf,
@@ -138,7 +146,7 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
                       cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
     __shared__ cd red[3 * 128];
     __shared__ M2LEnt se[M2L_STAGE];
-    const M2LItem it = items[blockIdx.x];
+    const M2LItem it = items[ii];
     const int T = it.box;
     const int p = p_level[box_level[T]];
     const int nco = 2 * p + 1;
@@ -208,13 +216,23 @@ __global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, 
         __syncthreads();
     }
 }
+__global__ void __launch_bounds__(128) k_m2l(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
+                      const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                      const int64_t* __restrict__ slot_coef, const cd* __restrict__ m2lf,
+                      const int64_t* __restrict__ m2lf_off, const cd* __restrict__ m2lr, int nrhs, int64_t ncoef,
+                      int64_t nslotcoef, int nparts, const cd* __restrict__ Min, const cd* __restrict__ Mp,
+                      cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
+    m2l_item(blockIdx.x, items, ents, box_level, p_level, coef_off, slot_of, slot_coef, m2lf, m2lf_off, m2lr, nrhs,
+             ncoef, nslotcoef, nparts, Min, Mp, Lout, Lp, part);
+}
 // Sum the partial results of split (box, chunk)s in part order and write them.
-__global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__ reds,
+__device__ __forceinline__ void m2l_reduce_one(int ri, const M2LReduce* __restrict__ reds,
                       const int* __restrict__ box_level, const int* __restrict__ p_level,
                       const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
                       const int64_t* __restrict__ slot_coef, int nrhs, int64_t ncoef, int64_t nslotcoef, int nparts,
                       const cd* __restrict__ part, cd* __restrict__ Lout, cd* __restrict__ Lp) {
-    const M2LReduce r = reds[blockIdx.x];
+    const M2LReduce r = reds[ri];
     const int p = p_level[box_level[r.box]];
     const int lane = threadIdx.x % XT_W, k = threadIdx.x / XT_W;   // k < 4; 3 used
     const int idx = r.chunk * XT_W + lane;
@@ -228,17 +246,26 @@ __global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__
         else Lp[(int64_t)col * nslotcoef + slot_coef[ts] + idx] = t;
     }
 }
+__global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__ reds,
+                      const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                      const int64_t* __restrict__ slot_coef, int nrhs, int64_t ncoef, int64_t nslotcoef, int nparts,
+                      const cd* __restrict__ part, cd* __restrict__ Lout, cd* __restrict__ Lp) {
+    m2l_reduce_one(blockIdx.x, reds, box_level, p_level, coef_off, slot_of, slot_coef, nrhs, ncoef, nslotcoef, nparts,
+                   part, Lout, Lp);
+}
 
 // L2P over a list of point ranges: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
 // about (cx, cy).  Leaves (cell centres) and straddling leaves (reaction centres).
-__global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
-                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
-                      int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
+__device__ __forceinline__ void l2p_group(int gi, const ExpGroup* __restrict__ groups,
+                      const ExpEntry* __restrict__ ent, const MediumDev& m, const double* __restrict__ px,
+                      const double* __restrict__ py, int64_t n, int nrhs, int64_t stride, const cd* __restrict__ L,
+                      cd* __restrict__ y) {
     // y_j += sum_n L_n J_n(k rho_j) e^{i n theta_j}.  Per entry, A_n = L_n and
     // B_n = (-1)^n L_{-n} are folded into P_n = A_n + B_n and Q_n = A_n - B_n, so
     // that A_n z^n + B_n conj(z^n) = P_n cos(n theta) + i Q_n sin(n theta).
     extern __shared__ double sj[];   // [npts][p+1] J_n, then [nent][2][p+1] (P, Q)
-    const ExpGroup G = groups[blockIdx.x];
+    const ExpGroup G = groups[gi];
     const int p = ent[G.e0].p, np1 = p + 1;
     const int ne = G.e1 - G.e0;
     cd* sPQ = (cd*)(sj + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
@@ -277,6 +304,11 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
         }
     }
 }
+__global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
+                      int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
+    l2p_group(blockIdx.x, groups, ent, m, px, py, n, nrhs, stride, L, y);
+}
 
 // Multipole-to-multipole and local-to-local translations (Graf's addition
 // theorem) into the destinations of one level: cell centres and reaction
@@ -288,14 +320,15 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
 // so results are reproducible.  Spreading a destination over several CTAs keeps
 // the coarse levels (few boxes, orders up to 2p+1 ~ 115) from running on a
 // handful of SMs.
-__global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
-                                                   const cd* __restrict__ vec, int accumulate, int w, int nrhs,
-                                                   int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
+__device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __restrict__ dsts,
+                                              const XSrc* __restrict__ srcs, const cd* __restrict__ vec,
+                                              int accumulate, int w, int nrhs, int64_t ncoef, int64_t nslotcoef,
+                                              cd* X, cd* Xp) {
     __shared__ cd red[128];
-    const XDst d = dsts[blockIdx.x];
+    const XDst d = dsts[di];
     const int ns = 128 / w;
     const int lane = threadIdx.x % w, sl = threadIdx.x / w;
-    const int idx = blockIdx.y * w + lane;
+    const int idx = chunk * w + lane;
     const int ncD = 2 * d.p + 1;
     const bool live = sl < ns && idx < ncD;
     for (int col = 0; col < nrhs; ++col) {
@@ -321,6 +354,11 @@ __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts
         }
         __syncthreads();
     }
+}
+__global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
+                                                   const cd* __restrict__ vec, int accumulate, int w, int nrhs,
+                                                   int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
+    translate_dst(blockIdx.x, blockIdx.y, dsts, srcs, vec, accumulate, w, nrhs, ncoef, nslotcoef, X, Xp);
 }
 
 // Reaction M2L moment tables of components whose source and field layers are the

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstring>
 #include <functional>
 #include <mutex>
 #include <cstdint>
@@ -28,6 +29,7 @@ struct DBuf {
 // Sommerfeld quadrature parameters shared by host and device (passed by value)
 struct QuadRule {
     double T;          // end of the real-axis detour
+    double kmin;       // smallest wavenumber of the medium (the first branch point on the detour)
     double es_v0;      // exp-sinh abscissae v0 + j hv, j = 0..nes-1
     double es_hv;
     int nes;           // nodes per ray
@@ -207,6 +209,8 @@ struct lfmm_geometry_s {
     int *d_nl_jptr64r = nullptr, *d_nl_j64r = nullptr;
     cd *d_ndiag = nullptr;
     int64_t near32_nnz = 0, near64r_nnz = 0;
+    float2 *d_near_x32 = nullptr;     // x rounded to complex64 for the FP32 near-field products
+    int64_t near_x32_cap = 0;
     // translation tables
     int *d_p_level = nullptr;
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
@@ -254,6 +258,7 @@ struct lfmm_geometry_s {
     int *pc_own_first = nullptr, *pc_own_cnt = nullptr;
     bool pc_ready = false;
     double setup_seconds = 0.0;
+    double setup_phase[3] = {0.0, 0.0, 0.0};   // seconds: tree and lists, near field, far field (tables, plans)
     std::vector<void*> allocs;        // everything cudaMalloc'ed for this geometry
     // held by every call that applies the operator or the preconditioner to vectors
     // (matvec, the allocation-free matvec, precondition, solve, right-hand side, field):
@@ -329,6 +334,34 @@ void fmm_build(lfmm_geometry_s* g);
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed = false,
                cudaEvent_t before_l2p = nullptr);
 void fmm_autotune(lfmm_geometry_s* g);
+// One operator product per geometry, several geometries in shared launches: every stage
+// (near field, P2M, each M2M pass, M2L and its reductions, each L2L pass, L2P) is one
+// launch whose blocks cover all the geometries' work (batch.cu helpers below).  FP64
+// operator; x and y in each geometry's sorted order.
+struct BatchOp {
+    lfmm_geometry_s* g;
+    const cd* x;
+    cd* y;
+    int nrhs;
+};
+// Device copies of per-launch job tables, released on the stream after use.
+struct JobTables {
+    std::vector<unsigned char> host;
+    size_t add(const void* p, size_t bytes) {
+        const size_t o = (host.size() + 15) & ~(size_t)15;
+        host.resize(o + bytes);
+        std::memcpy(host.data() + o, p, bytes);
+        return o;
+    }
+    unsigned char* dev = nullptr;
+    void upload(cudaStream_t s);
+    void release(cudaStream_t s);
+    template <class T>
+    const T* at(size_t o) const { return (const T*)(dev + o); }
+};
+void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_t before_l2p);
+void near_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s);
+void apply_operator_batch_sorted(const std::vector<BatchOp>& ops, cudaStream_t s);
 // Raise (never lower) a kernel's dynamic shared-memory limit on the current device.
 // The attribute is process-wide, shared by every geometry and thread, so a
 // geometry that needs less must not undo what another one was granted.

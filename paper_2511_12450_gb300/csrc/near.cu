@@ -113,21 +113,22 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
     }
 }
 
-// y_T += (near row of leaf T) x, one warp per target leaf.
+// y_T += (near row of leaf T) x, one CTA of NW warps per target leaf.
 //
 // The blocks of one target leaf T are stored one after another, each column-major
 // with leading dimension nT = |T|, so together they form one column-major nT x nJ
-// matrix whose column c multiplies x at the sorted position J[c].  A warp takes the
-// rows in chunks of r = min(32, nT) rows: G = 32 / r groups of r lanes each walk
-// every G-th column of the chunk (lanes beyond G r idle), and the groups' sums meet
-// by warp shuffles in a fixed order.  Consecutive lanes of a group read consecutive
-// entries of a column.
+// matrix whose column c multiplies x at the sorted position J[c].  Warp w takes the
+// contiguous share [c0 + nJ w / NW, c0 + nJ (w + 1) / NW) of the columns, and the rows
+// in chunks of r = min(32, nT): G = 32 / r groups of r lanes each walk every G-th
+// column of its share (lanes beyond G r idle), consecutive lanes reading consecutive
+// entries of a column.  The groups' sums meet by warp shuffles, the warps' by shared
+// memory, both in a fixed order.
 //
 // FP64 form: one matrix, the stored FP64 blocks (free space, reaction, self terms).
-// Precision form (MIX): the blocks without reaction entries as complex64 with their
-// self terms taken out (products and sums in FP32), the blocks that hold reaction
-// entries as FP64 copies, and the self terms as an FP64 diagonal;
-// the three parts are added in FP64.
+// Precision form (MIX): the blocks without reaction entries in complex64 with their
+// self terms taken out, multiplied with x rounded to complex64 (FP32 products and
+// sums); the blocks that hold reaction entries as FP64 copies, and the self terms as
+// an FP64 diagonal, with the FP64 x; the parts are added in FP64.
 struct NearRowPart {
     const int64_t* off;   // per leaf: first value of its matrix
     const int* jptr;      // per leaf: column range [jptr[T], jptr[T + 1])
@@ -135,76 +136,126 @@ struct NearRowPart {
 };
 
 __device__ __forceinline__ void near_fma(cd& acc, const cd& v, const cd& x) { cfma(acc, v, x); }
-__device__ __forceinline__ void near_fma(float2& acc, const float2& v, const cd& x) {
-    const float xr = (float)x.x, xi = (float)x.y;
-    acc.x = fmaf(v.x, xr, acc.x);
-    acc.x = fmaf(-v.y, xi, acc.x);
-    acc.y = fmaf(v.x, xi, acc.y);
-    acc.y = fmaf(v.y, xr, acc.y);
+__device__ __forceinline__ void near_fma(float2& acc, const float2& v, const float2& x) {
+    acc.x = fmaf(v.x, x.x, acc.x);
+    acc.x = fmaf(-v.y, x.y, acc.x);
+    acc.y = fmaf(v.x, x.y, acc.y);
+    acc.y = fmaf(v.y, x.x, acc.y);
 }
 
-template <typename V, typename A>
+// acc += sum over the columns [ca, cb) of the leaf's matrix taken by this lane group
+template <typename V, typename X, typename A>
 __device__ __forceinline__ void near_row_sum(const V* __restrict__ val, const NearRowPart& P, int leaf, int nT, int i,
-                                             int g, int G, const cd* __restrict__ x, A& acc) {
-    const int c0 = P.jptr[leaf], c1 = P.jptr[leaf + 1];
+                                             int g, int G, int ca, int cb, const X* __restrict__ x, A& acc) {
+    const int c0 = P.jptr[leaf];
     const V* v = val + P.off[leaf] + i;
     A a1{}, a2{}, a3{};
-    int c = c0 + g;
+    int c = ca + g;
     // four columns in flight per lane
-    for (; c + 3 * G < c1; c += 4 * G) {
+    for (; c + 3 * G < cb; c += 4 * G) {
         const V v0 = v[(int64_t)(c - c0) * nT], v1 = v[(int64_t)(c + G - c0) * nT];
         const V v2 = v[(int64_t)(c + 2 * G - c0) * nT], v3 = v[(int64_t)(c + 3 * G - c0) * nT];
-        const cd x0 = x[P.j[c]], x1 = x[P.j[c + G]], x2 = x[P.j[c + 2 * G]], x3 = x[P.j[c + 3 * G]];
+        const X x0 = x[P.j[c]], x1 = x[P.j[c + G]], x2 = x[P.j[c + 2 * G]], x3 = x[P.j[c + 3 * G]];
         near_fma(acc, v0, x0);
         near_fma(a1, v1, x1);
         near_fma(a2, v2, x2);
         near_fma(a3, v3, x3);
     }
-    for (; c < c1; c += G) near_fma(acc, v[(int64_t)(c - c0) * nT], x[P.j[c]]);
+    for (; c < cb; c += G) near_fma(acc, v[(int64_t)(c - c0) * nT], x[P.j[c]]);
     acc.x += a1.x; acc.y += a1.y;
     a2.x += a3.x; a2.y += a3.y;
     acc.x += a2.x; acc.y += a2.y;
 }
+template <int NW>
+__device__ __forceinline__ void share(const NearRowPart& P, int leaf, int w, int* ca, int* cb) {
+    const int c0 = P.jptr[leaf], nj = P.jptr[leaf + 1] - c0;
+    *ca = c0 + (int)(((int64_t)nj * w) / NW);
+    *cb = c0 + (int)(((int64_t)nj * (w + 1)) / NW);
+}
 
-template <bool MIX>
-__global__ void __launch_bounds__(128) k_near_leaf(int nleaf, int leaf0, const int* __restrict__ box_begin,
-                                                   const int* __restrict__ box_end, NearRowPart P64,
-                                                   const cd* __restrict__ val64, NearRowPart P32,
-                                                   const float2* __restrict__ val32, const cd* __restrict__ diag,
-                                                   const cd* __restrict__ x, cd* __restrict__ y, int64_t n,
-                                                   int nrhs) {
-    const int leaf = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (leaf >= nleaf) return;   // whole warps only: the shuffles below see full warps
+// NW warps per leaf: 2 in the FP64 form (the FP64 pipe bounds it; fewer warps per leaf
+// keep the fixed cost of the reductions small against the FMAs), 4 in the precision form
+// (bound by memory; more loads in flight).  In the precision form the FP32 part is reduced
+// in FP32 and converted once per row, and the FP64 part is skipped for the leaves without
+// reaction columns.
+template <bool MIX, int NW>
+__device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __restrict__ box_begin,
+                                              const int* __restrict__ box_end, const NearRowPart& P64,
+                                              const cd* __restrict__ val64, const NearRowPart& P32,
+                                              const float2* __restrict__ val32, const cd* __restrict__ diag,
+                                              const cd* __restrict__ x, const float2* __restrict__ x32,
+                                              cd* __restrict__ y, int64_t n, int nrhs) {
+    __shared__ cd part[NW][32];
+    __shared__ float2 part32[MIX ? NW : 1][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tb = box_begin[leaf0 + leaf], nT = box_end[leaf0 + leaf] - tb;
+    const bool has64 = !MIX || P64.jptr[leaf + 1] > P64.jptr[leaf];   // the same for the whole CTA
+    int a64, b64, a32 = 0, b32 = 0;
+    share<NW>(P64, leaf, w, &a64, &b64);
+    if (MIX) share<NW>(P32, leaf, w, &a32, &b32);
     for (int col = 0; col < nrhs; ++col) {
         const cd* xc = x + (int64_t)col * n;
         for (int i0 = 0; i0 < nT; i0 += 32) {
             const int r = min(32, nT - i0), G = 32 / r;
             const int i = i0 + lane % r, g = lane / r;
             cd acc = mk(0.0, 0.0);
+            float2 s32 = make_float2(0.f, 0.f);
             if (g < G) {
-                near_row_sum(val64, P64, leaf, nT, i, g, G, xc, acc);
-                if (MIX) {
-                    float2 a32 = make_float2(0.f, 0.f);
-                    near_row_sum(val32, P32, leaf, nT, i, g, G, xc, a32);
-                    acc.x += (double)a32.x;
-                    acc.y += (double)a32.y;
-                }
+                if (has64) near_row_sum(val64, P64, leaf, nT, i, g, G, a64, b64, xc, acc);
+                if (MIX) near_row_sum(val32, P32, leaf, nT, i, g, G, a32, b32, x32 + (int64_t)col * n, s32);
             }
             for (int gg = 1; gg < G; ++gg) {
                 const int src = (lane + gg * r) & 31;
-                const double ox = __shfl_sync(0xffffffffu, acc.x, src);
-                const double oy = __shfl_sync(0xffffffffu, acc.y, src);
-                if (lane < r) { acc.x += ox; acc.y += oy; }
+                if (has64) {
+                    const double ox = __shfl_sync(0xffffffffu, acc.x, src);
+                    const double oy = __shfl_sync(0xffffffffu, acc.y, src);
+                    if (lane < r) { acc.x += ox; acc.y += oy; }
+                }
+                if (MIX) {
+                    const float ox = __shfl_sync(0xffffffffu, s32.x, src);
+                    const float oy = __shfl_sync(0xffffffffu, s32.y, src);
+                    if (lane < r) { s32.x += ox; s32.y += oy; }
+                }
             }
             if (lane < r) {
-                const int64_t q = (int64_t)col * n + tb + i;
-                if (MIX) cfma(acc, diag[tb + i], xc[tb + i]);
-                y[q] += acc;
+                if (has64) part[w][lane] = acc;
+                if (MIX) part32[w][lane] = s32;
             }
+            __syncthreads();
+            if (w == 0 && lane < r) {
+                cd t = mk(0.0, 0.0);
+                if (has64) {
+                    t = part[0][lane];
+                    for (int q = 1; q < NW; ++q) t += part[q][lane];
+                }
+                if (MIX) {
+                    float2 u = part32[0][lane];
+                    for (int q = 1; q < NW; ++q) { u.x += part32[q][lane].x; u.y += part32[q][lane].y; }
+                    t.x += (double)u.x;
+                    t.y += (double)u.y;
+                    cfma(t, diag[tb + i], xc[tb + i]);
+                }
+                y[(int64_t)col * n + tb + i] += t;
+            }
+            __syncthreads();
         }
     }
+}
+#define NEAR_WARPS_64 2
+#define NEAR_WARPS_MIX 4
+template <bool MIX, int NW>
+__global__ void __launch_bounds__(32 * NW) k_near_leaf(int leaf0, const int* __restrict__ box_begin,
+                                                       const int* __restrict__ box_end, NearRowPart P64,
+                                                       const cd* __restrict__ val64, NearRowPart P32,
+                                                       const float2* __restrict__ val32, const cd* __restrict__ diag,
+                                                       const cd* __restrict__ x, const float2* __restrict__ x32,
+                                                       cd* __restrict__ y, int64_t n, int nrhs) {
+    near_leaf_cta<MIX, NW>(blockIdx.x, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
+}
+// x rounded to complex64 (the precision form's FP32 near-field products)
+__global__ void k_round_x32(const cd* __restrict__ x, float2* __restrict__ x32, int64_t tot) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x)
+        x32[q] = make_float2((float)x[q].x, (float)x[q].y);
 }
 
 // one block copied into the precision form's stores
@@ -383,23 +434,77 @@ static void near_mixed_build(lfmm_geometry_s* g) {
     g->near32_ready = true;
 }
 
+// Several geometries' FP64 near fields in one launch: four leaves (warps) per CTA, the CTAs
+// of each geometry consecutive; a CTA finds its geometry by binary search over the prefix.
+struct NearJob {
+    int nleaf, leaf0;
+    const int *box_begin, *box_end;
+    NearRowPart P64;
+    const cd* val64;
+    const cd* x;
+    cd* y;
+    int64_t n;
+    int nrhs;
+};
+__global__ void __launch_bounds__(32 * NEAR_WARPS_64) k_near_leaf_multi(const NearJob* __restrict__ jobs,
+                                                                     const int* __restrict__ prefix, int njobs) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const NearJob& J = jobs[lo];
+    near_leaf_cta<false, NEAR_WARPS_64>((int)blockIdx.x - prefix[lo], J.leaf0, J.box_begin, J.box_end, J.P64, J.val64, J.P64,
+                         nullptr, nullptr, J.x, nullptr, J.y, J.n, J.nrhs);
+}
+
+void near_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s) {
+    std::vector<NearJob> jobs;
+    std::vector<int> prefix(1, 0);
+    for (const BatchOp& op : ops) {
+        lfmm_geometry_s* g = op.g;
+        jobs.push_back(NearJob{g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end,
+                               NearRowPart{g->d_nl_off, g->d_nl_jptr, g->d_nl_j}, g->d_nb_val, op.x, op.y, g->n,
+                               op.nrhs});
+        prefix.push_back(prefix.back() + g->nleaf);
+    }
+    if (prefix.back() == 0) return;
+    JobTables t;
+    const size_t oj = t.add(jobs.data(), sizeof(NearJob) * jobs.size());
+    const size_t op = t.add(prefix.data(), sizeof(int) * prefix.size());
+    t.upload(s);
+    k_near_leaf_multi<<<prefix.back(), 32 * NEAR_WARPS_64, 0, s>>>(t.at<NearJob>(oj), t.at<int>(op), (int)jobs.size());
+    cudaError_t e = cudaGetLastError();
+    t.release(s);
+    cuda_check(e, "k_near_leaf_multi");
+}
+
 void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed) {
     if (g->nleaf == 0) return;
     if (mixed && !g->near32_ready) near_mixed_build(g);
     prof_begin(g, ST_NEAR, s);
-    const int warps_per_cta = 4;
-    const int grid = (g->nleaf + warps_per_cta - 1) / warps_per_cta;
     if (mixed) {
+        const int64_t tot = g->n * nrhs;
+        if (g->near_x32_cap < tot) {
+            dev_release_now(g->d_near_x32);
+            g->d_near_x32 = nullptr;
+            g->d_near_x32 = (float2*)dev_alloc_ready(sizeof(float2) * tot, "near x32");
+            g->near_x32_cap = tot;
+        }
+        k_round_x32<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 16), 256, 0, s>>>(x_sorted, g->d_near_x32, tot);
+        cuda_check(cudaGetLastError(), "k_round_x32");
+        ++g->n_launches;
         const NearRowPart p64{g->d_nl_off64r, g->d_nl_jptr64r, g->d_nl_j64r};
         const NearRowPart p32{g->d_nl_off32, g->d_nl_jptr32, g->d_nl_j32};
-        k_near_leaf<true><<<grid, 32 * warps_per_cta, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end, p64,
+        k_near_leaf<true, NEAR_WARPS_MIX><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(g->leaf0, g->d_box_begin, g->d_box_end, p64,
                                                               g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
-                                                              y_sorted, g->n, nrhs);
+                                                              g->d_near_x32, y_sorted, g->n, nrhs);
     } else {
         const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
-        k_near_leaf<false><<<grid, 32 * warps_per_cta, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end, p64,
-                                                               g->d_nb_val, p64, nullptr, nullptr, x_sorted, y_sorted,
-                                                               g->n, nrhs);
+        k_near_leaf<false, NEAR_WARPS_64><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(g->leaf0, g->d_box_begin, g->d_box_end, p64,
+                                                               g->d_nb_val, p64, nullptr, nullptr, x_sorted, nullptr,
+                                                               y_sorted, g->n, nrhs);
     }
     cuda_check(cudaGetLastError(), "k_near_leaf");
     ++g->n_launches;

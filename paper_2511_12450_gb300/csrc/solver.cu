@@ -88,6 +88,22 @@ void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted,
     cuda_check(cudaStreamWaitEvent(s, g->ev_join, 0), "join");   // also when there is no far field
 }
 
+// Several geometries' FP64 operators in shared launches (one launch per stage for all of
+// them); each y is what apply_operator_sorted gives for its geometry, bit for bit.  The
+// near fields run on the first geometry's side stream beside the far fields.
+void apply_operator_batch_sorted(const std::vector<BatchOp>& ops, cudaStream_t s) {
+    if (ops.empty()) return;
+    for (const BatchOp& op : ops)
+        cuda_check(cudaMemsetAsync(op.y, 0, sizeof(cd) * op.g->n * op.nrhs, s), "memset y");
+    lfmm_geometry_s* g0 = ops[0].g;
+    cuda_check(cudaEventRecord(g0->ev_fork, s), "fork");
+    cuda_check(cudaStreamWaitEvent(g0->side, g0->ev_fork, 0), "fork");
+    near_apply_batch(ops, g0->side);
+    cuda_check(cudaEventRecord(g0->ev_join, g0->side), "join");
+    fmm_apply_batch(ops, s, g0->ev_join);
+    cuda_check(cudaStreamWaitEvent(s, g0->ev_join, 0), "join");
+}
+
 // ------------------------------------------------------------------ BLAS-2 helpers for GMRES
 // The Arnoldi step streams the Krylov basis V (n x ncol, column-major, complex128)
 // from HBM: h = V^H w reads it once, w -= V h reads it once more.

@@ -38,11 +38,18 @@ struct QuadNode {
     cd fm;      // weight multiplying the e^{-i lambda X} half (already includes e^{-i lambda X})
 };
 
+// Panels of the detour: enough for the oscillation (|X| + D), and no wider than the
+// detour's depth at the smallest branch point k_min, h sin(pi k_min / T): in media whose
+// top or bottom wavenumber is small against k_max the half-sine passes close above that
+// branch point (Example 2 of Sec. 5, k = 1.2 under k_max = 10: depth 0.14 under 0.48-wide
+// panels lost 3e-7 on entries near the interface; at most one depth per panel keeps them
+// at the rule's 1e-12 level).
 __device__ __forceinline__ int detour_panels(const QuadRule& q, double X, double D, double* h_out) {
     double ax = fabs(X);
     double h = fmin(0.5, 1.0 / fmax(ax, 1e-3));
     *h_out = h;
     double need = q.T * (1.0 / h + 0.6 * (fmax(D, 0.0) + ax));
+    need = fmax(need, q.T / (h * sinpi(q.kmin / q.T)));
     int P = (int)ceil(need);
     return P > q.min_panels ? P : q.min_panels;
 }

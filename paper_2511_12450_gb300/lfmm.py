@@ -40,7 +40,7 @@ EXPORTED = [
     "lfmm_medium_create", "lfmm_medium_destroy", "lfmm_geometry_build", "lfmm_geometry_destroy",
     "lfmm_rhs_plane_wave", "lfmm_matvec", "lfmm_gmres_solve", "lfmm_eval_field",
     "lfmm_polygon_elements", "lfmm_geometry_query", "lfmm_last_error", "lfmm_matvec_static",
-    "lfmm_precond_apply",
+    "lfmm_precond_apply", "lfmm_matvec_batch",
     "lfmm_server_create", "lfmm_server_submit", "lfmm_server_wait", "lfmm_server_stats", "lfmm_server_destroy",
 ]
 
@@ -111,6 +111,8 @@ def library():
         lib.lfmm_matvec.argtypes = [vp, i32, vp, vp, i32, vp]
         lib.lfmm_matvec_static.argtypes = [vp, vp, vp, vp]
         lib.lfmm_precond_apply.argtypes = [vp, i32, vp, vp, i32, vp]
+        lib.lfmm_matvec_batch.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp),
+                                          ctypes.POINTER(vp), i32, vp]
         lib.lfmm_gmres_solve.argtypes = [vp, i32, vp, vp, ctypes.POINTER(GmresParams), ctypes.POINTER(GmresInfo), vp]
         lib.lfmm_eval_field.argtypes = [vp, i32, vp, i64, dp, vp, i32, vp]
         lib.lfmm_polygon_elements.argtypes = [i32, ctypes.POINTER(ctypes.c_int32), dp, dp, dp, dp]
@@ -269,6 +271,29 @@ def matvec(g: Geometry, x, y=None, stream=None, mixed: bool = False, simt_m2l: b
     flags |= (LFMM_MIXED if mixed else 0) | (LFMM_SIMT_M2L if simt_m2l else 0)
     _check(library().lfmm_matvec(g.handle, nrhs, xp, yp, flags, st))
     return y
+
+
+def matvec_batch(geos, xs, ys=None, stream=None):
+    """y_i = K_i x_i for several geometries in shared launches (CUDA tensors, all complex128
+    or all complex64; each [n_i] or [nrhs_i, n_i] as in matvec)."""
+    geos = list(geos)
+    xs = list(xs)
+    if len(geos) != len(xs) or not geos:
+        raise ValueError("one x per geometry expected")
+    if ys is None:
+        ys = [_empty_like(x, g.n, _vec_args(x, g.n)[1]) for g, x in zip(geos, xs)]
+    ys = list(ys)
+    args = [(_vec_args(x, g.n), _vec_args(y, g.n)) for g, x, y in zip(geos, xs, ys)]
+    flags = {a[0][2] for a in args} | {a[1][2] for a in args}
+    if len(flags) != 1 or not (next(iter(flags)) & LFMM_DEVICE_PTRS):
+        raise TypeError("matvec_batch takes CUDA tensors of one complex dtype")
+    n = len(geos)
+    hv = (ctypes.c_void_p * n)(*[g.handle for g in geos])
+    nr = (ctypes.c_int32 * n)(*[a[0][1] for a in args])
+    xp = (ctypes.c_void_p * n)(*[a[0][0] for a in args])
+    yp = (ctypes.c_void_p * n)(*[a[1][0] for a in args])
+    _check(library().lfmm_matvec_batch(n, hv, nr, xp, yp, next(iter(flags)), _stream_of(stream)))
+    return ys
 
 
 def precond_apply(g: Geometry, x, y=None, stream=None):

@@ -85,13 +85,6 @@ def test_geometry_argument_validation_before_device_work(lib):
     with pytest.raises(lib.LfmmError) as ei:
         lib.geometry_build(m, good, w, np.array([[1.0, 0.0], [0.6, 0.6]]), combined=True)
     assert ei.value.status == lib.LFMM_ERR_INVALID_ARG
-    # leaves too large for their expansion rows in shared memory (far field active)
-    m1 = lib.medium_create([], [2.0], [1.0])
-    th = np.linspace(0.0, 2 * np.pi, 20000, endpoint=False)
-    ring = np.stack([10 * np.cos(th), 10 * np.sin(th)], 1)
-    with pytest.raises(lib.LfmmError) as ei:
-        lib.geometry_build(m1, ring, np.full(th.size, 2 * np.pi * 10 / th.size), leaf_size=1000)
-    assert ei.value.status == lib.LFMM_ERR_INVALID_ARG and "leaf_size" in str(ei.value)
 
 
 def test_binding_constants_match_the_header(lib):

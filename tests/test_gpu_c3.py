@@ -6,8 +6,8 @@ of the benchmark's C3 block.
 Expected values: the 64 stored oracle rows of tests/golden/c3_sampled_rows.json (y = K x for
 x non-zero on a seeded 4,096-point subset; 8 of the rows have their own column in the subset,
 so the self terms are covered).  The FP64 operator is held to the FMM truncation level at
-p = 20 measured on these rows (worst 9.8e-8, median 1e-11); the precision form to its FP32
-level, and against the FP64 operator on a dense random x.
+p = 20 measured on these rows (worst 9.8e-8, median 7.8e-12); the precision form to its FP32
+level (measured: worst row 1.2e-6, median 1.9e-7; 2.6e-7 from FP64 on a dense random x).
 """
 
 import json
@@ -21,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROW_TOL_FP64 = 3e-7
-ROW_TOL_MIXED = 5e-6
-OP_TOL_MIXED = 1e-5
+ROW_TOL_MIXED = 4e-6
+OP_TOL_MIXED = 1e-6
 
 
 @pytest.fixture(scope="module")

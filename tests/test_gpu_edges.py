@@ -72,3 +72,15 @@ def test_four_layers_high_wavenumbers_fmm_matches_dense_oracle(gpu_lib):
     err = relerr(lf.matvec(G, x), K @ x)
     print(f"4 layers, k up to 12, N={G.n}: rel err {err:.2e}")
     assert err <= 1e-8
+
+
+def test_leaves_too_large_for_their_shared_memory_rows_are_refused(gpu_lib):
+    # the check needs the tree (the largest leaf and the leaf order), so it follows the
+    # GPU tree build; it refuses before any other device work
+    lf = gpu_lib
+    m1 = lf.medium_create([], [2.0], [1.0])
+    th = np.linspace(0.0, 2 * np.pi, 20000, endpoint=False)
+    ring = np.stack([10 * np.cos(th), 10 * np.sin(th)], 1)
+    with pytest.raises(lf.LfmmError) as ei:
+        lf.geometry_build(m1, ring, np.full(th.size, 2 * np.pi * 10 / th.size), leaf_size=1000)
+    assert ei.value.status == lf.LFMM_ERR_INVALID_ARG and "leaf_size" in str(ei.value)

@@ -148,7 +148,7 @@ def test_kernel_shared_memory_limits_only_grow_across_geometries(c2):
 def test_precision_form_near_field_split(gpu_lib):
     # Every pair near (leaf size above N).  In three layers the single block holds
     # reaction (Sommerfeld) entries, so the precision form keeps it in FP64 and equals
-    # the FP64 operator bit for bit.  In one layer the block holds only free-space
+    # the FP64 operator to rounding (the two forms split the columns over warps differently).  In one layer the block holds only free-space
     # entries: its off-diagonal entries go to complex64 (FP32 products), the self terms
     # I^s stay FP64, and the difference from the FP64 operator is FP32 rounding.
     from workloads import Medium, layered_small
@@ -160,7 +160,7 @@ def test_precision_form_near_field_split(gpu_lib):
     x = rng.standard_normal(pts.shape[0]) + 1j * rng.standard_normal(pts.shape[0])
     med = wl.medium
     G3 = lf.geometry_build(lf.medium_create(med.interfaces, med.k, med.eta), pts, w, p=20, leaf_size=1024)
-    assert np.array_equal(lf.matvec(G3, x, mixed=True), lf.matvec(G3, x))
+    assert relerr(lf.matvec(G3, x, mixed=True), lf.matvec(G3, x)) <= 1e-14
     one = Medium(interfaces=[], k=[4.0], eta=[1.0])
     K1 = onys.dense_matrix(one, pts, w)
     G1 = lf.geometry_build(lf.medium_create(one.interfaces, one.k, one.eta), pts, w, p=20, leaf_size=1024)
