@@ -41,7 +41,8 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch from the committed ncu captures (profiles/); null once the
 # kernel changes after the capture
-NCU_TRAFFIC_BYTES = {"k_m2l": 84.714752e6 + 3.439104e6, "k_near_apply": 67.088128e6 + 0.403968e6}
+NCU_TRAFFIC_BYTES = {"k_m2l": 85761280.0 + 3519488.0, "k_near_leaf": 67979008.0 + 378368.0,
+                     "k_near_leaf (precision form)": 38070784.0}
 
 
 def run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n):
@@ -90,6 +91,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the million-point four-layer workload block")
+    ap.add_argument("--serve-full", type=int, default=0,
+                    help="run only the serving form on this many requests drawn like the serving "
+                         "configuration itself (N up to 262,144, up to 512 bodies) and print it as one JSON line")
     ap.add_argument("--only-c3", action="store_true",
                     help="run only the million-point four-layer workload block (--steps timed matvecs per operator) "
                          "and print it as one JSON line")
@@ -233,15 +237,16 @@ def cpu_baseline(wl, rows_per_sample, n_samples=1):
             "seconds": dt}
 
 
-def run_serving(lfmm, n_requests=24, slots=4, seed=12455):
+def run_serving(lfmm, n_requests=32, slots=4, seed=12455, n_max=131072.0, max_bodies=128):
     """Serving form on a bounded stand-in for the request stream (random 2-4 layer stacks,
-    k in [2, 12], N in [2k, 32k]): Poisson arrivals at 1.5x the FP64 one-at-a-time capacity.
-    The arms see the same arrivals: FP64 one at a time (1 slot), FP64 served (``slots``
-    concurrent requests), the served mixed-precision form and the served combined-field
-    operator (second kind, opt-in); each solve to the FP64 residual 1e-8."""
+    k in [2, 12], N log-uniform in [2k, n_max], up to max_bodies bodies): Poisson arrivals at
+    1.5x the FP64 one-at-a-time capacity.  The arms see the same arrivals: FP64 one at a time
+    (1 slot), FP64 served (``slots`` concurrent requests), the served mixed-precision form and
+    the served combined-field operator (second kind, opt-in); each solve to the FP64 residual
+    1e-8."""
     from workloads import config_c5_stream
 
-    stream = config_c5_stream(n_requests, seed)
+    stream = config_c5_stream(n_requests, seed, n_max=n_max, max_bodies=max_bodies)
     reqs = []
     for wl in stream:
         pts, w, nrm = lfmm.polygon_elements(wl.bodies)
@@ -366,6 +371,20 @@ def run_c3(lfmm, steps=5):
                                    for k in st1}}
     out["mixed"]["op_rel_diff_vs_fp64"] = float(torch.linalg.norm(ys["mixed"] - ys["fp64"]) /
                                                 torch.linalg.norm(ys["fp64"]))
+    # the precision form's near field against HBM (complex64 regular blocks, FP64 reaction
+    # blocks and diagonal, x in FP64 and complex64, y read and written); the stage runs
+    # beside the far field, so its live time includes the competition for the SMs
+    ne = lfmm.geometry_query(G, "near_entries", np.float64)
+    nbytes = 8.0 * ne[1] + 16.0 * ne[2] + 72.0 * n
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    t_near = out["mixed"]["stages_ms"]["near"] * 1e-3
+    out["mixed"]["near_roofline"] = {"kernel": "k_near_leaf_w (precision form)", "bound": "hbm",
+                                     "algorithmic_bytes": nbytes, "entries_complex64": int(ne[1]),
+                                     "entries_fp64": int(ne[2]),
+                                     "achieved": nbytes / t_near / 1e9 if t_near > 0 else None, "peak": hbm,
+                                     "unit": "GB/s", "frac": (nbytes / t_near / 1e9 / hbm) if t_near > 0 else None,
+                                     "peak_source": src, "note": "live stage time inside the matvec"}
     G.destroy()
     return out
 
@@ -694,8 +713,8 @@ def run_ours(args):
         avg_s = stages["near"]["ms"] / max(stages["near"]["count"], 1) * 1e-3
         peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
         achieved = work["near_bytes"] / avg_s / 1e9
-        roof = {"kernel": "k_near_apply", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("k_near_apply"), "peak_source": src}
+        roof = {"kernel": "k_near_leaf", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES.get("k_near_leaf"), "peak_source": src}
 
     # precision form: the same matvec with FP32 multipole-to-local translations
     ym = torch.empty_like(x)
@@ -732,7 +751,8 @@ def run_ours(args):
                               "achieved": near32_bytes / near_s / 1e9 if near_s > 0 else None, "peak": hbm,
                               "unit": "GB/s",
                               "frac": (near32_bytes / near_s / 1e9 / hbm) if near_s > 0 else None,
-                              "peak_source": src_m, "note": "timed inside the matvec, beside the far field"}
+                              "peak_source": src_m, "traffic": NCU_TRAFFIC_BYTES.get("k_near_leaf (precision form)"),
+                              "note": "timed inside the matvec, beside the far field"}
     mixed["near_entries_complex64"] = int(ne[1])
     mixed["near_entries_fp64"] = int(ne[2])
     mixed["near_bytes_per_launch"] = near32_bytes
@@ -812,6 +832,15 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_full > 0:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2511_12450_gb300 import lfmm
+
+        print(json.dumps({"serve": run_serving(lfmm, n_requests=args.serve_full, n_max=262144.0, max_bodies=512),
+                          "data": "synthetic", "dtype": "f64"}))
+        return 0
     if args.only_c3:
         import torch
 

@@ -414,6 +414,7 @@ void fmm_build(lfmm_geometry_s* g) {
             vf_ptr[T + 1] = (int)vf_src.size();
         }
         g->d_m2lf = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
+        g->m2lf_len = tot;
         g->d_m2lf_off = dupload(g, toff);
         g->ftab_lay = tl;
         g->ftab_lev = tlev;
@@ -567,7 +568,7 @@ void fmm_free(lfmm_geometry_s* g) {
 
 // FP64 M2L over the first n64 work items and the first r64 reductions of split
 // items (the levels below the precision form's first FP32 level, or all levels).
-static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStream_t s) {
+static void ensure_m2l_part(lfmm_geometry_s* g, int nrhs) {
     if (g->n_m2l_parts > 0 && g->m2l_part_cols < nrhs) {
         dev_release_now(g->d_m2l_part);
         g->d_m2l_part = nullptr;
@@ -575,21 +576,28 @@ static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStr
                                              "M2L partial sums");
         g->m2l_part_cols = nrhs;
     }
-    if (n64 > 0) {
-        k_m2l<<<n64, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
-                                  g->d_slot_of, g->d_slot_coef, g->d_m2lf, g->d_m2lf_off, g->d_m2lr, nrhs,
-                                  g->ncoef, g->nslotcoef, g->n_m2l_parts, g->d_M, g->d_Mp, g->d_L, g->d_Lp,
-                                  g->d_m2l_part);
+}
+// FP64 M2L of the work items [i0, i1) and the reductions [r0, r1) (a range of levels)
+static void launch_m2l_range(lfmm_geometry_s* g, int nrhs, int i0, int i1, int r0, int r1, cudaStream_t s) {
+    if (i1 > i0) {
+        k_m2l<<<i1 - i0, 128, 0, s>>>(g->d_m2l_items + i0, g->d_m2l_ents, g->d_box_level, g->d_p_level,
+                                      g->d_coef_off, g->d_slot_of, g->d_slot_coef, g->d_m2lf, g->d_m2lf_off,
+                                      g->d_m2lr, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts, g->d_M, g->d_Mp,
+                                      g->d_L, g->d_Lp, g->d_m2l_part);
         cuda_check(cudaGetLastError(), "k_m2l");
         ++g->n_launches;
     }
-    if (r64 > 0) {
-        k_m2l_reduce<<<r64, 64, 0, s>>>(g->d_m2l_reds, g->d_box_level, g->d_p_level, g->d_coef_off, g->d_slot_of,
-                                        g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts,
-                                        g->d_m2l_part, g->d_L, g->d_Lp);
+    if (r1 > r0) {
+        k_m2l_reduce<<<r1 - r0, 64, 0, s>>>(g->d_m2l_reds + r0, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                            g->d_slot_of, g->d_slot_coef, nrhs, g->ncoef, g->nslotcoef,
+                                            g->n_m2l_parts, g->d_m2l_part, g->d_L, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_m2l_reduce");
         ++g->n_launches;
     }
+}
+static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStream_t s) {
+    ensure_m2l_part(g, nrhs);
+    launch_m2l_range(g, nrhs, 0, n64, 0, r64, s);
 }
 
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed,
@@ -632,6 +640,61 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         }
         prof_end(g, ST_P2M, s);
     }
+    // FP64 operator over several levels: the M2L of each level below l0 runs on the geometry's
+    // M2L stream as soon as that level's multipoles are complete (finest first), beside the
+    // M2M passes up the tree, whose small grids leave SMs idle; the coarsest level's M2L
+    // follows the M2M passes on this stream, and each L2L pass waits for its level's M2L.
+    // Every kernel and its inputs are those of the plain order, so the result is the same.
+    const bool overlap = lm > D && D - l0 >= 2 && g->m2l_side != nullptr && !g->ev_m2l.empty();
+    if (overlap) {
+        ensure_m2l_part(g, nrhs);
+        cudaStream_t s2 = g->m2l_side;
+        const std::vector<int>& is = g->m2l_item_level_start;
+        const std::vector<int>& rs = g->m2l_red_level_start;
+        // a wait binds to the event's latest record when it is issued: every level's
+        // record on this stream is issued before the M2L stream's wait for it
+        auto m2l_level = [&](int l) {
+            cuda_check(cudaEventRecord(g->ev_mlev[l], s), "event");
+            cuda_check(cudaStreamWaitEvent(s2, g->ev_mlev[l], 0), "wait multipoles");
+            if (l == D) prof_begin(g, ST_M2L, s2);   // the stage spans both streams' M2L launches
+            launch_m2l_range(g, nrhs, is[l], is[l + 1], rs[l], rs[l + 1], s2);
+            cuda_check(cudaEventRecord(g->ev_m2l[l], s2), "event");
+        };
+        m2l_level(D);
+        prof_begin(g, ST_M2M, s);
+        for (int lp = D - 1; lp >= l0; --lp) {
+            const int nd = g->up_end[lp] - g->up_begin[lp];
+            if (nd > 0) {
+                const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco);
+                dim3 grid(nd, (nco + w - 1) / w);
+                k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nrhs,
+                                                 g->ncoef, g->nslotcoef, g->d_M, g->d_Mp);
+                cuda_check(cudaGetLastError(), "k_translate (M2M)");
+                ++g->n_launches;
+            }
+            if (lp > l0) m2l_level(lp);
+        }
+        prof_end(g, ST_M2M, s);
+        launch_m2l_range(g, nrhs, is[l0], is[l0 + 1], rs[l0], rs[l0 + 1], s);
+        for (int l = l0 + 1; l <= D; ++l) {
+            // the M2L stream's levels run finest first: the first wait (level l0 + 1, its last)
+            // covers them all
+            cuda_check(cudaStreamWaitEvent(s, g->ev_m2l[l], 0), "wait M2L");
+            if (l == l0 + 1) {
+                prof_end(g, ST_M2L, s);
+                prof_begin(g, ST_L2L, s);
+            }
+            const int nd = g->dn_end[l] - g->dn_begin[l];
+            if (nd == 0) continue;
+            const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco);
+            dim3 grid(nd, (nco + w - 1) / w);
+            k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, w, nrhs, g->ncoef,
+                                             g->nslotcoef, g->d_L, g->d_Lp);
+            cuda_check(cudaGetLastError(), "k_translate (L2L)");
+            ++g->n_launches;
+        }
+        prof_end(g, ST_L2L, s);
+    } else {
     prof_begin(g, ST_M2M, s);
     for (int lp = D - 1; lp >= l0; --lp) {   // M2M: children at lp + 1 -> parents (cells and reaction centres) at lp
         if (lp >= lm) { mixed_m2m(g, lp, nrhs, s); continue; }
@@ -650,7 +713,14 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         prof_begin(g, ST_M2L, s);
         const int n64 = g->m2l_item_level_start[lm];
         const int r64 = g->m2l_red_level_start[lm];
-        launch_m2l64(g, nrhs, n64, r64, s);
+        if (lm <= D && mixed_coarse_df(g)) {
+            // precision form: the coarse (wide-band) levels in double-float, the rest in FP32
+            ensure_m2l_part(g, nrhs);
+            mixed_m2l_coarse(g, nrhs, n64, s);
+            launch_m2l_range(g, nrhs, 0, 0, 0, r64, s);
+        } else {
+            launch_m2l64(g, nrhs, n64, r64, s);
+        }
         if (lm <= D) mixed_m2l(g, nrhs, lm, s);
         prof_end(g, ST_M2L, s);
     }
@@ -671,6 +741,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         if (l == lm) mixed_l_add(g, lm, nrhs, s);
     }
     prof_end(g, ST_L2L, s);
+    }
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
         // (after the near field, which adds into the same y on the side stream)
         if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");

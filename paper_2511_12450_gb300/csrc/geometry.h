@@ -152,6 +152,10 @@ struct lfmm_geometry_s {
     bool m2l_simt = false;                   // this call: FP32 M2L on the SIMT kernel only (LFMM_SIMT_M2L)
     cudaStream_t side = nullptr;             // near field beside the far field (apply_operator_sorted)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // FP64 operator: the fine levels' M2L on their own stream beside the M2M passes
+    cudaStream_t m2l_side = nullptr;
+    std::vector<cudaEvent_t> ev_mlev;        // per level: its multipoles are complete
+    std::vector<cudaEvent_t> ev_m2l;         // per level: its M2L (and reductions) is done
     double *d_nx = nullptr, *d_ny = nullptr; // outward unit normals (sorted order), combined field only
     int *d_layer = nullptr, *d_perm = nullptr;
     // boxes
@@ -214,6 +218,7 @@ struct lfmm_geometry_s {
     // translation tables
     int *d_p_level = nullptr;
     cd *d_m2lf = nullptr;             // free-space M2L: per (layer, level, offset) Toeplitz vectors
+    int64_t m2lf_len = 0;             // its length (complex values)
     int64_t *d_m2lf_off = nullptr;
     int *d_vf_ptr = nullptr, *d_vf_src = nullptr, *d_vf_tab = nullptr;   // free V lists with table ids
     lfmm::M2LItem* d_m2l_items = nullptr;   // coarse levels first
@@ -372,6 +377,10 @@ void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s)
 void mixed_m2m(lfmm_geometry_s* g, int parent_level, int nrhs, cudaStream_t s);
 void mixed_m_to64(lfmm_geometry_s* g, int level, int nrhs, cudaStream_t s);   // FP32 multipoles -> FP64
 void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s);
+// the M2L work items [0, n_items) (the levels below the first FP32 level) in double-float;
+// writes the FP64 locals and partial sums (the caller adds the reductions)
+bool mixed_coarse_df(lfmm_geometry_s* g);
+void mixed_m2l_coarse(lfmm_geometry_s* g, int nrhs, int n_items, cudaStream_t s);
 void mixed_l_add(lfmm_geometry_s* g, int level, int nrhs, cudaStream_t s);    // FP64 locals += into FP32
 void mixed_l2l(lfmm_geometry_s* g, int child_level, int nrhs, cudaStream_t s);
 void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s);

@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "geometry.h"
 
 namespace lfmm {
@@ -75,6 +76,12 @@ struct MixedState {
     int tc_p = 0;                       // largest expansion order of the FP32 levels (the coarsest)
     int* tc_err = nullptr;              // set when an mbarrier wait of k_m2l32_tc gave up
     int* tc_err_host = nullptr;         // pinned copy, read at the next call
+    // the coarse (wide-band) levels' M2L in double-float: tables and multipoles as float pairs
+    dfc* ftab_df = nullptr;             // free-space Toeplitz vectors (offsets as d_m2lf_off)
+    dfc* rtab_df = nullptr;             // reaction tables of the coarse levels (offsets as ReactKey::off)
+    dfc *Mdf = nullptr, *Mpdf = nullptr;   // [cols][ncoef], [cols][nslotcoef] (coarse levels filled)
+    int df_cols = 0;
+    bool df_ok = false;                 // the coarse levels' M2L runs in double-float
 };
 
 // ---------------------------------------------------------------------------
@@ -522,6 +529,104 @@ __global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__
 
 // ---------------------------------------------------------------------------
 // replacing (in_flight: queued work may still read them) or releasing at destroy
+// ------------------------------------------------------------------ coarse levels in double-float
+// FP64 values split into float pairs (hi + lo), per element
+__global__ void k_to_df(const cd* __restrict__ in, int64_t n, dfc* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = to_dfc(in[i].x, in[i].y);
+}
+// the reaction tables of the keys of levels below lm (one CTA per key)
+__global__ void k_rtab_to_df(const cd* __restrict__ m2lr, const ReactKey* __restrict__ keys, const int* __restrict__ list,
+                             dfc* __restrict__ out) {
+    const ReactKey K = keys[list[blockIdx.x]];
+    const int64_t ne = (int64_t)(2 * K.pT + 1) * (2 * K.pS + 1);
+    for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) out[K.off + e] = to_dfc(m2lr[K.off + e].x, m2lr[K.off + e].y);
+}
+
+// M2L of the coarse levels in double-float: the same work items, entry descriptors and
+// index flips as the FP64 k_m2l (fmm_kernels.cuh), with the multipoles and the tables as
+// float pairs and double-float multiply-accumulates; the slices are reduced in double-float
+// in a fixed order and the results written in FP64 (L, reaction-centre locals, or the FP64
+// partial sums that k_m2l_reduce adds).
+__global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
+                      const int* __restrict__ box_level, const int* __restrict__ p_level,
+                      const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
+                      const int64_t* __restrict__ slot_coef, const dfc* __restrict__ m2lf,
+                      const int64_t* __restrict__ m2lf_off, const dfc* __restrict__ m2lr, int nrhs, int64_t ncoef,
+                      int64_t nslotcoef, int nparts, const dfc* __restrict__ Min, const dfc* __restrict__ Mp,
+                      cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
+    __shared__ dfc red[3 * 128];
+    __shared__ M2LEnt se[64];
+    const M2LItem it = items[blockIdx.x];
+    const int T = it.box;
+    const int p = p_level[box_level[T]];
+    const int nco = 2 * p + 1;
+    const int W = it.w, NS = 128 / W;
+    const int lane = threadIdx.x % W, sl = threadIdx.x / W;
+    const int idx = it.chunk * W + lane;
+    const bool live = sl < NS && idx < nco;
+    const int nn = idx - p;
+    for (int col = 0; col < nrhs; ++col) {
+        const dfc* Mc = Min + (int64_t)col * ncoef;
+        const dfc* Mpc = Mp + (int64_t)col * nslotcoef;
+        dfc acc0 = dfc_zero(), acc1 = dfc_zero(), acc2 = dfc_zero();
+        for (int eb = it.e0; eb < it.e1; eb += 64) {
+            const int cnt = min(64, it.e1 - eb);
+            __syncthreads();
+            if (threadIdx.x < cnt) se[threadIdx.x] = ents[eb + threadIdx.x];
+            __syncthreads();
+            if (!live) continue;
+            for (int q = 0; q < cnt; ++q) {
+                const M2LEnt E = se[q];
+                if (!(E.flags & M2L_REACT)) {
+                    const dfc* src = Mc + E.src;
+                    const dfc* tb = m2lf + m2lf_off[E.tab] + p - nn;
+                    for (int mi = sl; mi < nco; mi += NS) dfc_fma(acc0, src[mi], tb[mi]);
+                } else {
+                    const dfc* src = ((E.flags & M2L_SRC_SLOT) ? Mpc : Mc) + E.src;
+                    const bool bdown = (E.flags & M2L_B_DOWN) != 0;
+                    const int mrow = bdown ? nn : -nn;
+                    const bool flip = (E.flags & M2L_FLIP) != 0;
+                    const dfc* col_m = m2lr + E.tab + (flip ? (p - mrow) + (int64_t)2 * p * nco : (mrow + p));
+                    const int64_t cs = flip ? -(int64_t)nco : (int64_t)nco;
+                    dfc bsum = dfc_zero();
+                    if (E.flags & M2L_A_DOWN) {
+                        for (int mi = sl; mi < nco; mi += NS) dfc_fma(bsum, col_m[mi * cs], src[mi]);
+                    } else {
+                        for (int mi = sl; mi < nco; mi += NS) dfc_fma(bsum, col_m[mi * cs], dfc_sign(src[2 * p - mi], mi - p));
+                    }
+                    bsum = dfc_sign(bsum, (!bdown) & mrow);
+                    const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
+                    if (dst == 0) dfc_add(acc0, bsum);
+                    else if (dst == 1) dfc_add(acc1, bsum);
+                    else dfc_add(acc2, bsum);
+                }
+            }
+        }
+        if (sl < NS) {
+            red[(0 * NS + sl) * W + lane] = acc0;
+            red[(1 * NS + sl) * W + lane] = acc1;
+            red[(2 * NS + sl) * W + lane] = acc2;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) {
+            const int k = i / W, ln = i - k * W, ix = it.chunk * W + ln;
+            if (ix >= nco) continue;
+            dfc t = red[(k * NS) * W + ln];
+            for (int q = 1; q < NS; ++q) dfc_add(t, red[(k * NS + q) * W + ln]);
+            const cd v = mk(df_value(t.x, t.y), df_value(t.z, t.w));
+            if (it.part >= 0) {
+                part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + ln] = v;
+            } else {
+                const int ts = (k == 0) ? -1 : slot_of[2 * T + k - 1];
+                if (k == 0) Lout[(int64_t)col * ncoef + coef_off[T] + ix] = v;
+                else if (ts >= 0) Lp[(int64_t)col * nslotcoef + slot_coef[ts] + ix] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 static void mixed_free_buffers(MixedState* ms, bool in_flight) {
     void* bufs[5] = {ms->M, ms->L, ms->Mp, ms->Lp, ms->part};
     for (void* b : bufs) {
@@ -531,11 +636,21 @@ static void mixed_free_buffers(MixedState* ms, bool in_flight) {
     ms->M = ms->L = ms->Mp = ms->Lp = ms->part = nullptr;
     ms->cols = 0;
 }
+static void mixed_free_df(MixedState* ms, bool in_flight) {
+    for (void* b : {(void*)ms->Mdf, (void*)ms->Mpdf}) {
+        if (in_flight) dev_release_now(b);
+        else dev_release(b);
+    }
+    ms->Mdf = ms->Mpdf = nullptr;
+    ms->df_cols = 0;
+}
 
 void mixed_destroy(lfmm_geometry_s* g) {
     if (!g->mixed) return;
     MixedState* ms = g->mixed;
     mixed_free_buffers(ms, false);
+    mixed_free_df(ms, false);
+    dev_release(ms->ftab_df); dev_release(ms->rtab_df);
     dev_release(ms->ispow); dev_release(ms->ispow_slot); dev_release(ms->ftab); dev_release(ms->ftab_off);
     dev_release(ms->rtab); dev_release(ms->d_scale); dev_release(ms->wtab); dev_release(ms->wtab_off);
     dev_release(ms->d_xd_layer);
@@ -625,6 +740,27 @@ static void mixed_build(lfmm_geometry_s* g) {
     // passes (children at levels > lm)
     ms->lm = std::max(l0, std::min(mixed_level(g), D + 1));
     ms->d_scale = upload_raw(ms->scale, ms->bytes);
+    if (ms->df_ok && ms->lm > l0) {   // double-float copies of the tables the coarse levels' M2L reads
+        cuda_check(cudaMallocAsync((void**)&ms->ftab_df, sizeof(dfc) * std::max<int64_t>(g->m2lf_len, 1),
+                                   cudaStreamPerThread), "cudaMallocAsync ftab_df");
+        ms->bytes += sizeof(dfc) * std::max<int64_t>(g->m2lf_len, 1);
+        if (g->m2lf_len > 0)
+            k_to_df<<<(int)std::min<int64_t>((g->m2lf_len + 255) / 256, 152 * 16), 256>>>(g->d_m2lf, g->m2lf_len,
+                                                                                         ms->ftab_df);
+        std::vector<int> coarse;
+        for (int kk = 0; kk < nk; ++kk)
+            if (g->rkeys_host[kk].level < ms->lm) coarse.push_back(kk);
+        cuda_check(cudaMallocAsync((void**)&ms->rtab_df, sizeof(dfc) * std::max<int64_t>(rtot, 1), cudaStreamPerThread),
+                   "cudaMallocAsync rtab_df");
+        ms->bytes += sizeof(dfc) * std::max<int64_t>(rtot, 1);
+        if (!coarse.empty()) {
+            int* d_coarse = upload_raw(coarse, scratch);
+            k_rtab_to_df<<<(int)coarse.size(), 256>>>(g->d_m2lr, g->d_rkeys, d_coarse, ms->rtab_df);
+            cuda_check(cudaGetLastError(), "k_rtab_to_df");
+            cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "k_rtab_to_df");
+            dev_release(d_coarse);
+        }
+    }
     {   // the tensor-core M2L's boxes: every box of the FP32 levels
         std::vector<int> tb;
         for (int b = (ms->lm <= D ? t.level_start[ms->lm] : t.nbox); b < t.nbox; ++b) tb.push_back(b);
@@ -859,6 +995,43 @@ void mixed_check_waits(lfmm_geometry_s* g) {
     cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "tc status reset");
     *ms->tc_err_host = 0;
     throw TimeoutError{"tensor-core M2L: an mbarrier wait gave up; that product's M2L contributions were zeroed"};
+}
+
+bool mixed_coarse_df(lfmm_geometry_s* g) { return g->mixed && g->mixed->df_ok; }
+
+void mixed_m2l_coarse(lfmm_geometry_s* g, int nrhs, int n_items, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const TreeHost& t = g->tree;
+    if (n_items <= 0) return;
+    if (ms->df_cols < nrhs) {
+        mixed_free_df(ms, true);
+        ms->Mdf = (dfc*)dev_alloc_ready(sizeof(dfc) * (size_t)std::max<int64_t>(g->ncoef, 1) * nrhs, "M df");
+        ms->Mpdf = (dfc*)dev_alloc_ready(sizeof(dfc) * (size_t)std::max<int64_t>(g->nslotcoef, 1) * nrhs, "Mp df");
+        ms->df_cols = nrhs;
+    }
+    // the coarse levels' multipoles (cells and reaction centres) as float pairs
+    int64_t c0, c1, s0, s1, d0, d1, e0, e1;
+    level_ranges(g, t.l0, &c0, &d1, &s0, &e1);
+    level_ranges(g, ms->lm - 1, &d0, &c1, &e0, &s1);
+    for (int col = 0; col < nrhs; ++col) {
+        if (c1 > c0) {
+            k_to_df<<<(int)std::min<int64_t>((c1 - c0 + 255) / 256, 152 * 16), 256, 0, s>>>(
+                g->d_M + col * g->ncoef + c0, c1 - c0, ms->Mdf + col * g->ncoef + c0);
+            ++g->n_launches;
+        }
+        if (s1 > s0) {
+            k_to_df<<<(int)std::min<int64_t>((s1 - s0 + 255) / 256, 152 * 16), 256, 0, s>>>(
+                g->d_Mp + col * g->nslotcoef + s0, s1 - s0, ms->Mpdf + col * g->nslotcoef + s0);
+            ++g->n_launches;
+        }
+    }
+    cuda_check(cudaGetLastError(), "k_to_df (multipoles)");
+    k_m2l_df<<<n_items, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
+                                     g->d_slot_of, g->d_slot_coef, ms->ftab_df, g->d_m2lf_off, ms->rtab_df, nrhs,
+                                     g->ncoef, g->nslotcoef, g->n_m2l_parts, ms->Mdf, ms->Mpdf, g->d_L, g->d_Lp,
+                                     g->d_m2l_part);
+    cuda_check(cudaGetLastError(), "k_m2l_df");
+    ++g->n_launches;
 }
 
 void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) {

@@ -26,9 +26,9 @@
 
 namespace lfmm {
 
-struct NearTask {   // one (block, component) reaction task
+struct NearTask {   // the reaction entries of one block
     int blk;        // block index
-    int comp;
+    int c0, c1;     // its components: [c0, c1) of the component list
     int64_t first;  // first entry index in the flattened task space
 };
 
@@ -65,19 +65,21 @@ __global__ void k_near_free(MediumDev m, const int* __restrict__ blk_tgt, const 
     }
 }
 
-// reaction entries: one warp per (task, entry)
+// reaction entries: one warp per (block, entry); the warp adds the entry's components in
+// their list order and writes once, so the stored values do not depend on scheduling
 __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict__ tasks, int ntask,
-                             int64_t nwork, const int* __restrict__ blk_tgt, const int* __restrict__ blk_src,
-                             const int64_t* __restrict__ blk_off, const int* __restrict__ comp,
-                             const double* __restrict__ comp_H, const int* __restrict__ box_begin,
-                             const int* __restrict__ box_end, const double* __restrict__ px,
-                             const double* __restrict__ py, const double* __restrict__ pw,
-                             const double* __restrict__ nx, const double* __restrict__ ny, cd* __restrict__ val) {
+                             int64_t nwork, const int* __restrict__ task_comp, const int* __restrict__ blk_tgt,
+                             const int* __restrict__ blk_src, const int64_t* __restrict__ blk_off,
+                             const int* __restrict__ comp, const double* __restrict__ comp_H,
+                             const int* __restrict__ box_begin, const int* __restrict__ box_end,
+                             const double* __restrict__ px, const double* __restrict__ py,
+                             const double* __restrict__ pw, const double* __restrict__ nx,
+                             const double* __restrict__ ny, cd* __restrict__ val) {
     const bool cf = nx != nullptr;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t wk = warp; wk < nwork; wk += nwarps) {
-        // locate the task by binary search on first
+        // locate the block by binary search on first
         int lo = 0, hi = ntask - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -89,26 +91,26 @@ __global__ void k_near_react(MediumDev m, QuadRule q, const NearTask* __restrict
         const int sb = box_begin[S];
         const int64_t e = wk - tk.first;
         const int i = (int)(e % nT), j = (int)(e / nT);
-        const int c = tk.comp;
-        const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
         const int pi = tb + i, pj = sb + j;
         if (pw[pj] == 0.0) continue;   // a field point (weight 0) is never a source (uniform per warp)
         const double X = px[pj] - px[pi];
-        const double hs = (a == 0) ? (py[pj] - m.yint[ls]) : (m.yint[ls - 1] - py[pj]);
-        const double ht = (b == 0) ? (m.yint[lt - 1] - py[pi]) : (py[pi] - m.yint[lt]);
-        cd K;
-        if (cf) {
-            cd gk[3];
-            react_kernel_grad_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht, gk);
-            K = react_cf_combine(gk, a, m.k[ls], nx[pj], ny[pj]);
-        } else {
-            K = react_kernel_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht);
+        cd Ksum = mk(0.0, 0.0);
+        for (int q2 = tk.c0; q2 < tk.c1; ++q2) {
+            const int c = task_comp[q2];
+            const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
+            const double hs = (a == 0) ? (py[pj] - m.yint[ls]) : (m.yint[ls - 1] - py[pj]);
+            const double ht = (b == 0) ? (m.yint[lt - 1] - py[pi]) : (py[pi] - m.yint[lt]);
+            if (cf) {
+                cd gk[3];
+                react_kernel_grad_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht, gk);
+                Ksum += react_cf_combine(gk, a, m.k[ls], nx[pj], ny[pj]);
+            } else {
+                Ksum += react_kernel_warp(m, q, ls, a, lt, b, comp_H[c], X, hs, ht);
+            }
         }
         if ((threadIdx.x & 31) == 0) {
             cd* dst = val + blk_off[tk.blk] + (int64_t)j * nT + i;
-            double wj = pw[pj];
-            atomicAdd(&dst->x, wj * K.x);
-            atomicAdd(&dst->y, wj * K.y);
+            *dst += pw[pj] * Ksum;
         }
     }
 }
@@ -173,11 +175,13 @@ __device__ __forceinline__ void share(const NearRowPart& P, int leaf, int w, int
     *cb = c0 + (int)(((int64_t)nj * (w + 1)) / NW);
 }
 
-// NW warps per leaf: 2 in the FP64 form (the FP64 pipe bounds it; fewer warps per leaf
-// keep the fixed cost of the reductions small against the FMAs), 4 in the precision form
-// (bound by memory; more loads in flight).  In the precision form the FP32 part is reduced
-// in FP32 and converted once per row, and the FP64 part is skipped for the leaves without
-// reaction columns.
+// NW warps per leaf.  With few leaves (fewer than two waves of single-warp leaves) several
+// warps share a leaf so that enough loads are in flight: 2 in the FP64 form (bound by the
+// FP64 pipe; fewer warps per leaf keep the fixed cost of the reductions small against the
+// FMAs), 4 in the precision form (bound by memory).  With many leaves one warp per leaf
+// keeps four times as many leaves in flight per SM and needs no barrier.  In the precision
+// form the FP32 part is reduced in FP32 and converted once per row, and the FP64 part is
+// skipped for the leaves without reaction columns.
 template <bool MIX, int NW>
 __device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __restrict__ box_begin,
                                               const int* __restrict__ box_end, const NearRowPart& P64,
@@ -187,7 +191,7 @@ __device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __
                                               cd* __restrict__ y, int64_t n, int nrhs) {
     __shared__ cd part[NW][32];
     __shared__ float2 part32[MIX ? NW : 1][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = NW == 1 ? 0 : (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
     const int tb = box_begin[leaf0 + leaf], nT = box_end[leaf0 + leaf] - tb;
     const bool has64 = !MIX || P64.jptr[leaf + 1] > P64.jptr[leaf];   // the same for the whole CTA
     int a64, b64, a32 = 0, b32 = 0;
@@ -216,6 +220,18 @@ __device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __
                     const float oy = __shfl_sync(0xffffffffu, s32.y, src);
                     if (lane < r) { s32.x += ox; s32.y += oy; }
                 }
+            }
+            if (NW == 1) {   // one warp per leaf: no exchange between warps
+                if (lane < r) {
+                    cd t = has64 ? acc : mk(0.0, 0.0);
+                    if (MIX) {
+                        t.x += (double)s32.x;
+                        t.y += (double)s32.y;
+                        cfma(t, diag[tb + i], xc[tb + i]);
+                    }
+                    y[(int64_t)col * n + tb + i] += t;
+                }
+                continue;
             }
             if (lane < r) {
                 if (has64) part[w][lane] = acc;
@@ -252,6 +268,20 @@ __global__ void __launch_bounds__(32 * NW) k_near_leaf(int leaf0, const int* __r
                                                        cd* __restrict__ y, int64_t n, int nrhs) {
     near_leaf_cta<MIX, NW>(blockIdx.x, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
 }
+// one warp per leaf, four warps per CTA
+template <bool MIX>
+__global__ void __launch_bounds__(128) k_near_leaf_w(int nleaf, int leaf0, const int* __restrict__ box_begin,
+                                                     const int* __restrict__ box_end, NearRowPart P64,
+                                                     const cd* __restrict__ val64, NearRowPart P32,
+                                                     const float2* __restrict__ val32, const cd* __restrict__ diag,
+                                                     const cd* __restrict__ x, const float2* __restrict__ x32,
+                                                     cd* __restrict__ y, int64_t n, int nrhs) {
+    const int leaf = (int)(blockIdx.x * 4 + (threadIdx.x >> 5));
+    if (leaf >= nleaf) return;   // whole warps: the single-warp path has no block barrier
+    near_leaf_cta<MIX, 1>(leaf, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
+}
+// leaves from which one warp per leaf fills two waves of the GPU (152 SMs x 64 warps x 2)
+#define NEAR_WARP_PER_LEAF_MIN (152 * 64 * 2)
 // x rounded to complex64 (the precision form's FP32 near-field products)
 __global__ void k_round_x32(const cd* __restrict__ x, float2* __restrict__ x32, int64_t tot) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x)
@@ -297,6 +327,7 @@ void near_build(lfmm_geometry_s* g) {
     std::vector<unsigned char> blk_free, blk_react;
     std::vector<int64_t> blk_off;
     std::vector<NearTask> tasks;
+    std::vector<int> task_comp;
     int64_t off = 0, work = 0;
     for (int li = 0; li < g->nleaf; ++li) {
         const int T = g->leaf0 + li;
@@ -323,12 +354,13 @@ void near_build(lfmm_geometry_s* g) {
             blk_free.push_back(fr ? 1 : 0);
             blk_off.push_back(off);
             const int nS = t.box_end[S] - t.box_begin[S];
-            bool re = false;
-            for (int k = t.ureact_ptr[T]; k < t.ureact_ptr[T + 1]; ++k) {
-                if (t.ureact_idx[k] != S) continue;
-                tasks.push_back(NearTask{bi, t.ureact_comp[k], work});
+            const int c0 = (int)task_comp.size();
+            for (int k = t.ureact_ptr[T]; k < t.ureact_ptr[T + 1]; ++k)
+                if (t.ureact_idx[k] == S) task_comp.push_back(t.ureact_comp[k]);
+            const bool re = (int)task_comp.size() > c0;
+            if (re) {
+                tasks.push_back(NearTask{bi, c0, (int)task_comp.size(), work});
                 work += (int64_t)nT * nS;
-                re = true;
             }
             blk_react.push_back(re ? 1 : 0);
             off += (int64_t)nT * nS;
@@ -372,10 +404,11 @@ void near_build(lfmm_geometry_s* g) {
     }
     if (!tasks.empty()) {
         NearTask* d_tasks = dupload(g, tasks);
+        int* d_task_comp = dupload(g, task_comp);
         int threads = 256;
         int64_t warps_needed = work;
         int64_t blocks = std::min<int64_t>((warps_needed * 32 + threads - 1) / threads, 152 * 64);
-        k_near_react<<<(int)blocks, threads>>>(g->m, g->quad, d_tasks, (int)tasks.size(), work, d_bt,
+        k_near_react<<<(int)blocks, threads>>>(g->m, g->quad, d_tasks, (int)tasks.size(), work, d_task_comp, d_bt,
                                                g->d_nb_src, g->d_nb_off, g->d_comp, d_compH, g->d_box_begin,
                                                g->d_box_end, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
                                                g->d_nb_val);
@@ -497,14 +530,24 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
         ++g->n_launches;
         const NearRowPart p64{g->d_nl_off64r, g->d_nl_jptr64r, g->d_nl_j64r};
         const NearRowPart p32{g->d_nl_off32, g->d_nl_jptr32, g->d_nl_j32};
-        k_near_leaf<true, NEAR_WARPS_MIX><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(g->leaf0, g->d_box_begin, g->d_box_end, p64,
-                                                              g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
-                                                              g->d_near_x32, y_sorted, g->n, nrhs);
+        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN)
+            k_near_leaf_w<true><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end,
+                                                                   p64, g->d_nv64r, p32, g->d_nv32, g->d_ndiag,
+                                                                   x_sorted, g->d_near_x32, y_sorted, g->n, nrhs);
+        else
+            k_near_leaf<true, NEAR_WARPS_MIX><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(
+                g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
+                g->d_near_x32, y_sorted, g->n, nrhs);
     } else {
         const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
-        k_near_leaf<false, NEAR_WARPS_64><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(g->leaf0, g->d_box_begin, g->d_box_end, p64,
-                                                               g->d_nb_val, p64, nullptr, nullptr, x_sorted, nullptr,
-                                                               y_sorted, g->n, nrhs);
+        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN)
+            k_near_leaf_w<false><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                    g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                    nullptr, x_sorted, nullptr, y_sorted, g->n, nrhs);
+        else
+            k_near_leaf<false, NEAR_WARPS_64><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(
+                g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nb_val, p64, nullptr, nullptr, x_sorted, nullptr,
+                y_sorted, g->n, nrhs);
     }
     cuda_check(cudaGetLastError(), "k_near_leaf");
     ++g->n_launches;
