@@ -191,6 +191,21 @@ def whole_job_throughput(local_seconds, units_per_rank, dist=None, device="cpu")
     return world * units_per_rank / slowest / 1e6, slowest
 
 
+def setup_report(lf, G, seconds):
+    """Set-up time of a geometry with its phases, and the reaction moment tables' FP64 rate: their
+    complex multiply-adds (8 flop each; entries x quadrature nodes x 2 terms) over the far-field
+    phase, which the tables dominate (an upper bound on their own time)."""
+    ph = lf.geometry_query(G, "setup_times", np.float64)
+    cm = lf.geometry_query(G, "table_work", np.float64)
+    flops = 8.0 * float(cm[0] + cm[1])
+    far_s = float(ph[2])
+    tf = flops / far_s / 1e12 if far_s > 0 else None
+    return {"seconds": seconds, "tree_and_lists_s": float(ph[0]), "near_field_s": float(ph[1]),
+            "far_field_s": far_s, "table_gflop": flops / 1e9,
+            "table_cmacs_cross_same": [float(cm[0]), float(cm[1])],
+            "table_fp64_tflops": tf, "table_fp64_frac": (tf / FP64_PEAK_TFLOPS) if tf else None}
+
+
 def algorithmic_work(lf, G, n):
     """Per-launch algorithmic FLOPs of M2L and bytes of the near field (one RHS column)."""
     lev = lf.geometry_query(G, "box_level")
@@ -341,6 +356,7 @@ def run_c3(lfmm, steps=5):
     stream = torch.cuda.current_stream()
     out = {"workload": "C3: 4 layers (y=0,-6,-12; k=6,10,8,12; eta=1..4), 1024 circles/ellipses x 1024 nodes, "
                        "N=1048576, p=20", "N": n, "setup_seconds": setup_s,
+           "setup": setup_report(lfmm, G, setup_s),
            "tree": {k: float(v) for k, v in zip(["D", "l0", "boxes", "components", "near_blocks", "near_entries",
                                                   "reaction_tables"], lfmm.geometry_query(G, "tree_params",
                                                                                           np.float64)[3:10])}}
@@ -371,6 +387,10 @@ def run_c3(lfmm, steps=5):
                                    for k in st1}}
     out["mixed"]["op_rel_diff_vs_fp64"] = float(torch.linalg.norm(ys["mixed"] - ys["fp64"]) /
                                                 torch.linalg.norm(ys["fp64"]))
+    pf = lfmm.geometry_query(G, "precision_form", np.float64)
+    out["mixed"]["fp32_from_level"] = int(pf[0])
+    out["mixed"]["coarse_m2l"] = "double-float" if pf[1] == 1 else "FP64"
+    out["mixed"]["coarse_log10_ranges"] = [float(v) for v in pf[2:]]
     # the precision form's near field against HBM (complex64 regular blocks, FP64 reaction
     # blocks and diagonal, x in FP64 and complex64, y read and written); the stage runs
     # beside the far field, so its live time includes the competition for the SMs
@@ -737,6 +757,9 @@ def run_ours(args):
                        "regular near field)",
              "value": mixed_value, "ms_per_step": mixed_s * 1e3 / args.steps,
              "op_rel_diff": float(torch.linalg.norm(ym - y) / torch.linalg.norm(y))}
+    pf = lfmm.geometry_query(G, "precision_form", np.float64)
+    mixed["fp32_from_level"] = int(pf[0])
+    mixed["coarse_m2l"] = "double-float" if pf[1] == 1 else "FP64"
     # the precision form's near field against HBM: complex64 regular blocks, FP64 reaction
     # blocks, the FP64 diagonal, x in FP64 and complex64, y read and written
     ne = lfmm.geometry_query(G, "near_entries", np.float64)
@@ -815,6 +838,7 @@ def run_ours(args):
             "batch": batch,
             "serve": serve,
             "setup_seconds": setup_s,
+            "setup": setup_report(lfmm, G, setup_s),
             "m2l_schedule": lfmm.tuning(G),
         }
         print(json.dumps(line))

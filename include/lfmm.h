@@ -403,6 +403,12 @@ lfmm_status lfmm_server_destroy(lfmm_server s);
  * precision form, entries held in complex64 and in FP64 -- 0 until its first call),
  * "setup_times" (double[4]: seconds of the set-up spent on the tree and interaction
  * lists, the near field, the far field (moment tables, translation plans), and in all),
+ * "table_work" (double[2]: complex multiply-adds of the set-up's reaction moment tables,
+ * cross-layer and same-layer components: entries x quadrature nodes x 2),
+ * "precision_form" (double[5]: first level of the precision form's FP32 far field;
+ * 1 if its coarser levels' M2L runs in double-float, 0 if in FP64, -1 before its first call;
+ * log10 of the largest free-space and reaction table component of those levels and of their
+ * largest scaled multipole basis value -- double-float needs their sums to stay at most 26),
  * "launch_count" (double[1]: kernels launched so far by this geometry's
  * matvec path -- gather, P2M, M2M, M2L, L2L, L2P, near field, scatter --
  * counted on the host as they are enqueued),

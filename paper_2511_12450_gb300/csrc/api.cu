@@ -170,15 +170,6 @@ static void free_geometry(lfmm_geometry_s* g) {
     if (g->ev_fork) cudaEventDestroy(g->ev_fork);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
     g->ev_fork = g->ev_join = nullptr;
-    if (g->m2l_side) {
-        cudaStreamSynchronize(g->m2l_side);
-        cudaStreamDestroy(g->m2l_side);
-        g->m2l_side = nullptr;
-    }
-    for (cudaEvent_t e : g->ev_mlev) if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : g->ev_m2l) if (e) cudaEventDestroy(e);
-    g->ev_mlev.clear();
-    g->ev_m2l.clear();
     if (g->prof.on)
         for (int k = 0; k < 2 * ST_COUNT; ++k) cudaEventDestroy(g->prof.ev[k]);
     g->prof.on = false;
@@ -403,13 +394,6 @@ static lfmm_geometry_s* build_geometry(lfmm_medium med, int64_t n, const double*
         }
         g->d_comp = dupload(g, comp);
         cuda_check(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking), "side stream");
-        cuda_check(cudaStreamCreateWithFlags(&g->m2l_side, cudaStreamNonBlocking), "M2L stream");
-        g->ev_mlev.assign(t.D + 1, nullptr);
-        g->ev_m2l.assign(t.D + 1, nullptr);
-        for (int l = 0; l <= t.D; ++l) {
-            cuda_check(cudaEventCreateWithFlags(&g->ev_mlev[l], cudaEventDisableTiming), "event");
-            cuda_check(cudaEventCreateWithFlags(&g->ev_m2l[l], cudaEventDisableTiming), "event");
-        }
         cuda_check(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming), "event");
         cuda_check(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming), "event");
         tp = std::chrono::steady_clock::now();
@@ -792,6 +776,17 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "setup_times") {
             dtmp = {g->setup_phase[0], g->setup_phase[1], g->setup_phase[2], g->setup_seconds};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "table_work") {
+            dtmp = {g->table_cmacs[0], g->table_cmacs[1]};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "precision_form") {
+            int lm = 0, df = 0;
+            double rg[3];
+            mixed_info(g, &lm, &df, rg);
+            dtmp = {(double)lm, (double)df, rg[0], rg[1], rg[2]};
             src = dtmp.data();
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "launch_count") {

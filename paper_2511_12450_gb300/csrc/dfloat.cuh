@@ -18,8 +18,9 @@ namespace lfmm {
 typedef float4 dfc;
 
 __device__ __forceinline__ void df_acc(float& ah, float& al, float bh, float bl, float ch, float cl) {
-    // (ah, al) += (bh, bl) (ch, cl)
-    const float p = bh * ch;
+    // (ah, al) += (bh, bl) (ch, cl); the product is rounded on its own (__fmul_rn is never
+    // contracted into the following addition), as the two-sum below requires
+    const float p = __fmul_rn(bh, ch);
     float pe = fmaf(bh, ch, -p);
     pe = fmaf(bh, cl, pe);
     pe = fmaf(bl, ch, pe);

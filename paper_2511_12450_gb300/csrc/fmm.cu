@@ -488,24 +488,37 @@ void fmm_build(lfmm_geometry_s* g) {
         g->rkeys_host = keys;
         g->d_m2lr = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
         if (!keys.empty()) {
-            // same-layer components: Toeplitz tables from 4p+1 moments; others tile by tile
-            std::vector<TableWork> work;
+            // same-layer components: Toeplitz tables from 4p+1 moments; others in runs of entries
+            std::vector<TableChunk> work;
             std::vector<int> same;
             int pmax_same = 0;
+            size_t smem = 0;
             for (int kk = 0; kk < (int)keys.size(); ++kk) {
                 const Component& C = t.comps[keys[kk].comp];
                 int p = keys[kk].pS;
+                double hq = 0.0;
+                const int P0 = table_panels(g->quad, keys[kk].X, keys[kk].D, &hq) * g->quad.tab_panel_mult;
                 if (C.ls == C.lt && keys[kk].pS == keys[kk].pT) {
                     same.push_back(kk);
                     pmax_same = std::max(pmax_same, p);
+                    // 4p + 1 moments, two terms per node
+                    g->table_cmacs[1] += 2.0 * (4 * p + 1) * ((P0 + 2 * p) * 8.0 + 2 * g->quad.tab_nes);
                     continue;
                 }
-                for (int m0 = -p; m0 <= p; m0 += 32)
-                    for (int n0 = -p; n0 <= p; n0 += 32) work.push_back(TableWork{kk, m0, n0});
+                // (2pT + 1) (2pS + 1) entries, two terms per node
+                const int ncT = 2 * keys[kk].pT + 1, ne = ncT * (2 * keys[kk].pS + 1);
+                g->table_cmacs[0] += 2.0 * ne * ((P0 + keys[kk].pS + keys[kk].pT) * 8.0 + 2 * g->quad.tab_nes);
+                // runs of nearly equal length, at most 256 TAB_KPER entries each
+                const int nch = (ne + 256 * TAB_KPER - 1) / (256 * TAB_KPER);
+                for (int ci = 0; ci < nch; ++ci) {
+                    const int e0 = (int)((int64_t)ne * ci / nch), e1 = (int)((int64_t)ne * (ci + 1) / nch);
+                    work.push_back(TableChunk{kk, e0, e1});
+                    smem = std::max(smem, table_chunk_smem(ncT, (e1 - 1) / ncT - e0 / ncT + 1));
+                }
             }
             if (!work.empty()) {
-                TableWork* d_work = dupload(g, work);
-                size_t smem = (size_t)(16 * 32 * 4 + 4 * 256) * sizeof(cd);   // k_react_tables layout
+                TableChunk* d_work = dupload(g, work);
+                raise_smem_limit((const void*)k_react_tables, smem, "reaction tables smem");
                 k_react_tables<<<(int)work.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_work, g->d_comp,
                                                                 g->d_m2lr);
                 cuda_check(cudaGetLastError(), "k_react_tables");
@@ -640,61 +653,6 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         }
         prof_end(g, ST_P2M, s);
     }
-    // FP64 operator over several levels: the M2L of each level below l0 runs on the geometry's
-    // M2L stream as soon as that level's multipoles are complete (finest first), beside the
-    // M2M passes up the tree, whose small grids leave SMs idle; the coarsest level's M2L
-    // follows the M2M passes on this stream, and each L2L pass waits for its level's M2L.
-    // Every kernel and its inputs are those of the plain order, so the result is the same.
-    const bool overlap = lm > D && D - l0 >= 2 && g->m2l_side != nullptr && !g->ev_m2l.empty();
-    if (overlap) {
-        ensure_m2l_part(g, nrhs);
-        cudaStream_t s2 = g->m2l_side;
-        const std::vector<int>& is = g->m2l_item_level_start;
-        const std::vector<int>& rs = g->m2l_red_level_start;
-        // a wait binds to the event's latest record when it is issued: every level's
-        // record on this stream is issued before the M2L stream's wait for it
-        auto m2l_level = [&](int l) {
-            cuda_check(cudaEventRecord(g->ev_mlev[l], s), "event");
-            cuda_check(cudaStreamWaitEvent(s2, g->ev_mlev[l], 0), "wait multipoles");
-            if (l == D) prof_begin(g, ST_M2L, s2);   // the stage spans both streams' M2L launches
-            launch_m2l_range(g, nrhs, is[l], is[l + 1], rs[l], rs[l + 1], s2);
-            cuda_check(cudaEventRecord(g->ev_m2l[l], s2), "event");
-        };
-        m2l_level(D);
-        prof_begin(g, ST_M2M, s);
-        for (int lp = D - 1; lp >= l0; --lp) {
-            const int nd = g->up_end[lp] - g->up_begin[lp];
-            if (nd > 0) {
-                const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco);
-                dim3 grid(nd, (nco + w - 1) / w);
-                k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nrhs,
-                                                 g->ncoef, g->nslotcoef, g->d_M, g->d_Mp);
-                cuda_check(cudaGetLastError(), "k_translate (M2M)");
-                ++g->n_launches;
-            }
-            if (lp > l0) m2l_level(lp);
-        }
-        prof_end(g, ST_M2M, s);
-        launch_m2l_range(g, nrhs, is[l0], is[l0 + 1], rs[l0], rs[l0 + 1], s);
-        for (int l = l0 + 1; l <= D; ++l) {
-            // the M2L stream's levels run finest first: the first wait (level l0 + 1, its last)
-            // covers them all
-            cuda_check(cudaStreamWaitEvent(s, g->ev_m2l[l], 0), "wait M2L");
-            if (l == l0 + 1) {
-                prof_end(g, ST_M2L, s);
-                prof_begin(g, ST_L2L, s);
-            }
-            const int nd = g->dn_end[l] - g->dn_begin[l];
-            if (nd == 0) continue;
-            const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco);
-            dim3 grid(nd, (nco + w - 1) / w);
-            k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, w, nrhs, g->ncoef,
-                                             g->nslotcoef, g->d_L, g->d_Lp);
-            cuda_check(cudaGetLastError(), "k_translate (L2L)");
-            ++g->n_launches;
-        }
-        prof_end(g, ST_L2L, s);
-    } else {
     prof_begin(g, ST_M2M, s);
     for (int lp = D - 1; lp >= l0; --lp) {   // M2M: children at lp + 1 -> parents (cells and reaction centres) at lp
         if (lp >= lm) { mixed_m2m(g, lp, nrhs, s); continue; }
@@ -741,7 +699,6 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         if (l == lm) mixed_l_add(g, lm, nrhs, s);
     }
     prof_end(g, ST_L2L, s);
-    }
     {   // L2P: leaves from cell centres, straddling leaves from their reaction centres
         // (after the near field, which adds into the same y on the side stream)
         if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");

@@ -440,97 +440,125 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
     }
 }
 
-// Reaction M2L moment tables (eq. generalintegral): one CTA per (key, 32x32 tile).
-struct TableWork {
+// Reaction M2L moment tables (eq. generalintegral) of the cross-layer components:
+//     I_mn = sum_q [ F+_q v_q^-m u_q^n + F-_q v_q^m u_q^-n ]
+// over the table rule's nodes q (u = w(k_a), v = w(k_b), F+- the weights with the spectral
+// density and the height factors).  One CTA per run of consecutive entries of one table
+// (column-major, (m, n) at (n + pS) ncT + (m + pT)); each thread keeps up to TAB_KPER of them
+// in registers.  Per chunk of TAB_CH nodes the CTA stores the powers v^k (k = -pT..pT, one
+// table serves both v^-m and v^m) and, for its columns, F+ u^n and F- u^-n (the weights folded
+// in), so each entry costs two complex multiply-adds per node and nothing else: the FP64 pipe,
+// which bounds the kernel, does only the sum itself, apart from the powers and node values
+// (a few per cent).
+#define TAB_KPER 16
+#define TAB_CH 8
+#define TAB_NB 128
+struct TableChunk {
     int key;
-    int m0, n0;   // first row / column of the tile (indices from -p)
+    int e0, e1;   // entry range [e0, e1) of the key's table, e1 - e0 <= 256 TAB_KPER
 };
+// dynamic shared memory of one chunk: TAB_CH x (ncT + 2 ncols) powers + 4 TAB_NB node values
+__host__ __device__ inline size_t table_chunk_smem(int ncT, int ncols) {
+    return (size_t)(TAB_CH * (ncT + 2 * ncols) + 4 * TAB_NB) * sizeof(cd);
+}
 
 __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q, const ReactKey* __restrict__ keys,
-                                                      const TableWork* __restrict__ work,
+                                                      const TableChunk* __restrict__ work,
                                                       const int* __restrict__ comp, cd* __restrict__ out) {
     extern __shared__ cd st[];
-    const TableWork wk = work[blockIdx.x];
+    const TableChunk wk = work[blockIdx.x];
     const ReactKey K = keys[wk.key];
     const int c = K.comp;
     const int ls = comp[4 * c], a = comp[4 * c + 1], lt = comp[4 * c + 2], b = comp[4 * c + 3];
     const int pS = K.pS, pT = K.pT;
     const int ncT = 2 * pT + 1;
     const double ka = med.k[ls], kb = med.k[lt];
-    // nodes in batches of NB = 256 (all threads evaluate the spectral density, one
-    // node each), then in chunks of CH for the power tables and the tile update
-    const int CH = 16, NB = 256;
-    cd* Up = st;                       // [CH][32]  u^n  for the tile's n
-    cd* Um = Up + CH * 32;             // [CH][32]  u^-n
-    cd* Vp = Um + CH * 32;             // [CH][32]  v^-m for the tile's m
-    cd* Vm = Vp + CH * 32;             // [CH][32]  v^m
-    cd* Fp = Vm + CH * 32;             // [NB]
-    cd* Fm = Fp + NB;                  // [NB]
-    cd* uu = Fm + NB;                  // [NB] u
-    cd* vv = uu + NB;                  // [NB] v
-    // table rule: its own contour (table_contour_node), panels growing with the
-    // orders, finer rays
+    const int nlo = wk.e0 / ncT, nhi = (wk.e1 - 1) / ncT;   // column indices (from -pS) of the run
+    const int ncols = nhi - nlo + 1;
+    cd* Wv = st;                          // [TAB_CH][ncT]    v^(k - pT)
+    cd* Up = Wv + TAB_CH * ncT;           // [TAB_CH][ncols]  F+ u^n,  n = nlo + j - pS
+    cd* Um = Up + TAB_CH * ncols;         // [TAB_CH][ncols]  F- u^-n
+    cd* Fp = Um + TAB_CH * ncols;         // [TAB_NB]
+    cd* Fm = Fp + TAB_NB;                 // [TAB_NB]
+    cd* uu = Fm + TAB_NB;                 // [TAB_NB] u
+    cd* vv = uu + TAB_NB;                 // [TAB_NB] v
+    // this thread's entries: e = e0 + threadIdx.x + 256 k; row mi and column j within the run
+    const int kper = (wk.e1 - wk.e0 + 255) / 256;
+    int rowc[TAB_KPER], colc[TAB_KPER];
+#pragma unroll
+    for (int k = 0; k < TAB_KPER; ++k) {
+        const int e = min(wk.e0 + (int)threadIdx.x + 256 * k, wk.e1 - 1);
+        rowc[k] = e % ncT;
+        colc[k] = e / ncT - nlo;
+    }
     double h;
     const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + (pS + pT);
     const int ntot = P * 8 + 2 * q.tab_nes;
-    const int tm = threadIdx.x >> 3;          // 0..31 row within tile
-    const int tn = (threadIdx.x & 7) * 4;     // 0..28 first column within tile
-    cd acc[4] = {mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
-    for (int jb = 0; jb < ntot; jb += NB) {
-        const int cntB = min(NB, ntot - jb);
+    cd acc[TAB_KPER];
+#pragma unroll
+    for (int k = 0; k < TAB_KPER; ++k) acc[k] = mk(0, 0);
+    const int wruns = (ncT + 31) / 32, uruns = (ncols + 31) / 32;
+    for (int jb = 0; jb < ntot; jb += TAB_NB) {
+        const int cntB = min(TAB_NB, ntot - jb);
         __syncthreads();
         if (threadIdx.x < cntB) {
             QuadNode nd = table_contour_node(q, jb + threadIdx.x, P, h, K.X, K.D);
             cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
-            cd E = eikh(kya, K.hS) * eikh(kyb, K.hT);
-            cd SE = S * E;
+            cd SE = S * (eikh(kya, K.hS) * eikh(kyb, K.hT));
             Fp[threadIdx.x] = SE * nd.fp;
             Fm[threadIdx.x] = SE * nd.fm;
             uu[threadIdx.x] = w_of(kya, nd.lam, ka);
             vv[threadIdx.x] = w_of(kyb, nd.lam, kb);
         }
-        for (int j0 = 0; j0 < cntB; j0 += CH) {
-            const int cnt = min(CH, cntB - j0);
+        for (int j0 = 0; j0 < cntB; j0 += TAB_CH) {
+            const int cnt = min(TAB_CH, cntB - j0);
             __syncthreads();
-            // power tables of the tile: for each node four runs of 32 consecutive powers
-            // (u^n and u^-n over the tile's columns, v^-m and v^m over its rows), one
-            // thread per run: a starting power by binary exponentiation, then 31 products
-            for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
-                const int r = e >> 2, which = e & 3;
-                const cd u = uu[j0 + r], v = vv[j0 + r];
-                cd base, step;
-                int e0;
+            // powers in runs of 32, one thread per run: the run's first power by binary
+            // exponentiation, then 31 products (the weights folded into the u runs)
+            const int nrun = cnt * (wruns + 2 * uruns);
+            for (int t = threadIdx.x; t < nrun; t += blockDim.x) {
+                const int r = t / (wruns + 2 * uruns), w = t - r * (wruns + 2 * uruns);
+                cd base, fac;
+                int e0, len;
                 cd* dst;
-                if (which == 0) { base = u; step = u; e0 = wk.n0; dst = Up; }               // u^n
-                else if (which == 1) { base = u; step = cinv(u); e0 = -wk.n0; dst = Um; }   // u^-n
-                else if (which == 2) { base = v; step = cinv(v); e0 = -wk.m0; dst = Vp; }   // v^-m
-                else { base = v; step = v; e0 = wk.m0; dst = Vm; }                         // v^m
-                // start = base^e0 (e0 may be negative)
+                bool inv = false;
+                if (w < wruns) {                       // v^(k - pT), k = 32 w ..
+                    base = vv[j0 + r]; fac = mk(1.0, 0.0);
+                    e0 = 32 * w - pT; len = min(32, ncT - 32 * w); dst = Wv + r * ncT + 32 * w;
+                } else {
+                    const int w2 = w - wruns, sgn = w2 & 1, run = w2 >> 1;
+                    base = uu[j0 + r];
+                    const int n0 = nlo + 32 * run - pS;
+                    len = min(32, ncols - 32 * run);
+                    if (sgn == 0) { fac = Fp[j0 + r]; e0 = n0; dst = Up + r * ncols + 32 * run; }
+                    else { fac = Fm[j0 + r]; e0 = -n0; dst = Um + r * ncols + 32 * run; inv = true; }
+                }
+                const cd step = inv ? cinv(base) : base;
                 cd bb = (e0 >= 0) ? base : cinv(base);
-                int k2 = e0 >= 0 ? e0 : -e0;
-                cd cur = mk(1.0, 0.0);
-                while (k2 > 0) { if (k2 & 1) cur = cur * bb; bb = bb * bb; k2 >>= 1; }
-                for (int s2 = 0; s2 < 32; ++s2) { dst[r * 32 + s2] = cur; cur = cur * step; }
+                cd cur = fac;
+                for (int k2 = e0 >= 0 ? e0 : -e0; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
+                for (int s2 = 0; s2 < len; ++s2) { dst[s2] = cur; cur = cur * step; }
             }
             __syncthreads();
             for (int r = 0; r < cnt; ++r) {
-                cd a1 = Fp[j0 + r] * Vp[r * 32 + tm];
-                cd a2 = Fm[j0 + r] * Vm[r * 32 + tm];
+                const cd* W = Wv + r * ncT;
+                const cd* P1 = Up + r * ncols;
+                const cd* P2 = Um + r * ncols;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    cfma(acc[t], a1, Up[r * 32 + tn + t]);
-                    cfma(acc[t], a2, Um[r * 32 + tn + t]);
+                for (int k = 0; k < TAB_KPER; ++k) {
+                    if (k < kper) {
+                        cfma(acc[k], W[2 * pT - rowc[k]], P1[colc[k]]);   // F+ v^-m u^n
+                        cfma(acc[k], W[rowc[k]], P2[colc[k]]);            // F- v^m u^-n
+                    }
                 }
             }
         }
     }
-    const int mm = wk.m0 + tm;
-    if (mm <= pT) {
-        for (int t = 0; t < 4; ++t) {
-            int nn = wk.n0 + tn + t;
-            if (nn <= pS) out[K.off + (int64_t)(nn + pS) * ncT + (mm + pT)] = acc[t];
-        }
+#pragma unroll
+    for (int k = 0; k < TAB_KPER; ++k) {
+        const int e = wk.e0 + (int)threadIdx.x + 256 * k;
+        if (k < kper && e < wk.e1) out[K.off + e] = acc[k];
     }
 }
 

@@ -152,10 +152,6 @@ struct lfmm_geometry_s {
     bool m2l_simt = false;                   // this call: FP32 M2L on the SIMT kernel only (LFMM_SIMT_M2L)
     cudaStream_t side = nullptr;             // near field beside the far field (apply_operator_sorted)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // FP64 operator: the fine levels' M2L on their own stream beside the M2M passes
-    cudaStream_t m2l_side = nullptr;
-    std::vector<cudaEvent_t> ev_mlev;        // per level: its multipoles are complete
-    std::vector<cudaEvent_t> ev_m2l;         // per level: its M2L (and reductions) is done
     double *d_nx = nullptr, *d_ny = nullptr; // outward unit normals (sorted order), combined field only
     int *d_layer = nullptr, *d_perm = nullptr;
     // boxes
@@ -264,6 +260,7 @@ struct lfmm_geometry_s {
     bool pc_ready = false;
     double setup_seconds = 0.0;
     double setup_phase[3] = {0.0, 0.0, 0.0};   // seconds: tree and lists, near field, far field (tables, plans)
+    double table_cmacs[2] = {0.0, 0.0};        // complex multiply-adds of the moment tables: cross-layer, same-layer
     std::vector<void*> allocs;        // everything cudaMalloc'ed for this geometry
     // held by every call that applies the operator or the preconditioner to vectors
     // (matvec, the allocation-free matvec, precondition, solve, right-hand side, field):
@@ -380,6 +377,11 @@ void mixed_m2l(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s);
 // the M2L work items [0, n_items) (the levels below the first FP32 level) in double-float;
 // writes the FP64 locals and partial sums (the caller adds the reductions)
 bool mixed_coarse_df(lfmm_geometry_s* g);
+// first FP32 level of the precision form, whether its coarser levels' M2L runs in
+// double-float (1), in FP64 (0), or is not set up yet (-1: no precision-form call so far), and
+// the log10 magnitudes that decided it (largest free-space and reaction table component, largest
+// scaled multipole basis value)
+void mixed_info(lfmm_geometry_s* g, int* lm, int* df, double* range);
 void mixed_m2l_coarse(lfmm_geometry_s* g, int nrhs, int n_items, cudaStream_t s);
 void mixed_l_add(lfmm_geometry_s* g, int level, int nrhs, cudaStream_t s);    // FP64 locals += into FP32
 void mixed_l2l(lfmm_geometry_s* g, int child_level, int nrhs, cudaStream_t s);

@@ -24,7 +24,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -76,12 +78,16 @@ struct MixedState {
     int tc_p = 0;                       // largest expansion order of the FP32 levels (the coarsest)
     int* tc_err = nullptr;              // set when an mbarrier wait of k_m2l32_tc gave up
     int* tc_err_host = nullptr;         // pinned copy, read at the next call
-    // the coarse (wide-band) levels' M2L in double-float: tables and multipoles as float pairs
-    dfc* ftab_df = nullptr;             // free-space Toeplitz vectors (offsets as d_m2lf_off)
-    dfc* rtab_df = nullptr;             // reaction tables of the coarse levels (offsets as ReactKey::off)
-    dfc *Mdf = nullptr, *Mpdf = nullptr;   // [cols][ncoef], [cols][nslotcoef] (coarse levels filled)
+    // the coarse (wide-band) levels' M2L in double-float (levels l0 .. lm - 1)
+    dfc* ftab_df = nullptr;             // [2][m2lf_len]: scaled and unscaled Toeplitz vectors (offsets d_m2lf_off)
+    dfc* rtab_df = nullptr;             // scaled reaction tables of those levels (offsets as ReactKey::off)
+    float* rtab_rsc = nullptr;          // their row factors 2^e_m (at ReactKey::off + row)
+    dfc *Mdf = nullptr, *Mudf = nullptr, *Mpdf = nullptr;   // [cols][ncd] scaled / unscaled, [cols][nsd]
+    int* df_emax = nullptr;             // [cols] exponent bound of each column's coarse multipoles
+    int64_t df_c0 = 0, df_ncd = 0, df_s0 = 0, df_nsd = 0;  // coefficient ranges of those levels
     int df_cols = 0;
     bool df_ok = false;                 // the coarse levels' M2L runs in double-float
+    double df_range[3] = {0, 0, 0};     // log10: largest free-space, reaction table component; scaled basis
 };
 
 // ---------------------------------------------------------------------------
@@ -115,9 +121,10 @@ static double log10_env_j(double x, int n) {
 // |J_p(x)| / s^p (x = k w / sqrt(2), the farthest point of the box), and the
 // largest scaled translation entry.  s is a power of two in (0, 1]; the chosen
 // one minimises the largest of the three log-magnitudes.
-static double choose_scale(double k, double w, int p) {
+// big_m_out (optional) receives log10 of the largest scaled basis value at the chosen s.
+static double choose_scale(double k, double w, int p, double* big_m_out = nullptr) {
     const double x = k * w / std::sqrt(2.0);
-    double best_s = 1.0, best_v = 1e300;
+    double best_s = 1.0, best_v = 1e300, best_m = 0.0;
     for (int j = 0; j <= 80; ++j) {
         const double s = std::ldexp(1.0, -j), ls = std::log10(s);
         double big_m = -1e300;
@@ -125,8 +132,9 @@ static double choose_scale(double k, double w, int p) {
         const double small_m = log10_env_j(x, p) - p * ls;
         const double big_t = log10_max_scaled_y(2.0 * k * w, 2 * p, s);
         const double v = std::max(std::max(big_m, big_t), -small_m);
-        if (v < best_v) { best_v = v; best_s = s; }
+        if (v < best_v) { best_v = v; best_s = s; best_m = big_m; }
     }
+    if (big_m_out) *big_m_out = best_m;
     return best_s;
 }
 
@@ -530,32 +538,141 @@ __global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__
 // ---------------------------------------------------------------------------
 // replacing (in_flight: queued work may still read them) or releasing at destroy
 // ------------------------------------------------------------------ coarse levels in double-float
-// FP64 values split into float pairs (hi + lo), per element
-__global__ void k_to_df(const cd* __restrict__ in, int64_t n, dfc* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = to_dfc(in[i].x, in[i].y);
+// The coarse (wide-band) levels' M2L runs in double-float, with the same scales s as the FP32
+// levels (the unscaled tables reach |H_2p(2 k w)| ~ 1e40 and more at orders near 75 in the
+// low-k layers, past the FP32 exponent range).  The free-space sum
+//     L_n = sum_m T_{m-n} M_m
+// is split by the signs of n and m.  Where they differ (or m = 0), |m - n| = |m| + |n| and the
+// scaled dense entry s^(|n| + |m|) T_{m-n} equals the scaled Toeplitz entry
+// V~_{m-n} = s^|m-n| T_{m-n}: that half runs on (V~, M~) in scaled units.  Where they agree,
+// |m - n| <= p and the unscaled T_{m-n} and M_m stay in range: that half runs unscaled.  So
+// both halves keep the Toeplitz vectors (4p + 1 entries per table) and each lane of a slice
+// takes one half per step: a slice's step q covers the opposite-sign half for q <= p and the
+// same-sign half after.  The reaction part uses the dense scaled tables
+// s_T^|m| s_S^|n| I_mn on scaled multipoles, as the FP32 levels do.  The results are summed
+// and unscaled in FP64: L_n = s^-|n| (scaled sum) + (unscaled sum).
+
+// scaled and unscaled double-float Toeplitz vectors of the listed free-space tables; amax
+// collects the largest |component| stored (as float bits; non-finite values store +inf)
+__device__ __forceinline__ void note_max(unsigned* amax, double a, double b) {
+    double m = fmax(fabs(a), fabs(b));
+    if (!(m <= 3.0e38)) m = 3.0e38 * 2.0;
+    atomicMax(amax, __float_as_uint((float)m));
 }
-// the reaction tables of the keys of levels below lm (one CTA per key)
-__global__ void k_rtab_to_df(const cd* __restrict__ m2lr, const ReactKey* __restrict__ keys, const int* __restrict__ list,
-                             dfc* __restrict__ out) {
-    const ReactKey K = keys[list[blockIdx.x]];
-    const int64_t ne = (int64_t)(2 * K.pT + 1) * (2 * K.pS + 1);
-    for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) out[K.off + e] = to_dfc(m2lr[K.off + e].x, m2lr[K.off + e].y);
+__global__ void k_ftab_df(const cd* __restrict__ m2lf, const int64_t* __restrict__ m2lf_off,
+                          const int* __restrict__ list, const int* __restrict__ tab_p, const double* __restrict__ tab_s,
+                          dfc* __restrict__ outs, dfc* __restrict__ outu, unsigned* __restrict__ amax) {
+    const int id = list[blockIdx.x];
+    const int p = tab_p[id];
+    const double s = tab_s[id];
+    const int64_t off = m2lf_off[id];
+    for (int e = threadIdx.x; e <= 4 * p; e += blockDim.x) {
+        const int j = abs(e - 2 * p);
+        const cd v = m2lf[off + e];
+        const double f = pow(s, (double)j);
+        outs[off + e] = to_dfc(f * v.x, f * v.y);
+        note_max(amax, f * v.x, f * v.y);
+        if (j <= p) {
+            outu[off + e] = to_dfc(v.x, v.y);
+            note_max(amax, v.x, v.y);
+        } else {
+            outu[off + e] = dfc_zero();
+        }
+    }
+}
+// scaled double-float reaction tables of the listed keys (one CTA per key).  Each row m is
+// further divided by 2^e_m, e_m the binary exponent of its largest scaled entry, so that every
+// stored entry is below 1 in magnitude and a product with a scaled multipole stays inside the
+// FP32 exponent range whatever the table's own growth; rsc[K.off + row] keeps 2^e_m, by which
+// the M2L multiplies the row's sum (exactly: a power of two).
+__global__ void k_rtab_df(const cd* __restrict__ m2lr, const ReactKey* __restrict__ keys, const int* __restrict__ list,
+                          const double* __restrict__ key_ss, const double* __restrict__ key_st, dfc* __restrict__ out,
+                          float* __restrict__ rsc, unsigned* __restrict__ amax) {
+    const int kk = list[blockIdx.x];
+    const ReactKey K = keys[kk];
+    const int ncT = 2 * K.pT + 1, ncS = 2 * K.pS + 1;
+    const double ss = key_ss[kk], st = key_st[kk];
+    for (int mi = threadIdx.x; mi < ncT; mi += blockDim.x) {   // (m_out, n_in) at n_in ncT + m_out
+        const double fm = pow(st, (double)abs(mi - K.pT));
+        double mx = 0.0;
+        for (int ni = 0; ni < ncS; ++ni) {
+            const double f = fm * pow(ss, (double)abs(ni - K.pS));
+            const cd v = m2lr[K.off + (int64_t)ni * ncT + mi];
+            mx = fmax(mx, fmax(fabs(f * v.x), fabs(f * v.y)));
+        }
+        int e = 0;
+        if (mx > 0.0 && mx <= 1e300) frexp(mx, &e);
+        if (!(mx <= 1e300) || e > 120 || e < -120) {   // not representable: reported, never used
+            note_max(amax, 1e300, 0.0);
+            e = 0;
+        }
+        const double r = ldexp(1.0, -e);
+        for (int ni = 0; ni < ncS; ++ni) {
+            const double f = r * fm * pow(ss, (double)abs(ni - K.pS));
+            const cd v = m2lr[K.off + (int64_t)ni * ncT + mi];
+            out[K.off + (int64_t)ni * ncT + mi] = to_dfc(f * v.x, f * v.y);
+        }
+        rsc[K.off + mi] = ldexpf(1.0f, e);
+        note_max(amax, mx, 0.0);
+    }
+}
+// Per column, the binary exponent bound of the coarse levels' scaled multipoles (cells and
+// reaction centres): emax[col] >= ilogb of every |component| of M ispow.  The double-float
+// M2L divides that column by 2^(emax + 1), so its multipoles are below 1 in magnitude and its
+// sums are bounded by the tables alone, whatever the scale of x.
+__global__ void k_m_absmax(const cd* __restrict__ in, int64_t ld_in, const double* __restrict__ isp, int64_t c0,
+                           int64_t n, int nrhs, int* __restrict__ emax) {
+    int e = INT_MIN, col = -1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const int64_t i = t - (int64_t)c * n;
+        const cd v = in[(int64_t)c * ld_in + c0 + i];
+        const double a = fmax(fabs(v.x), fabs(v.y)) * isp[c0 + i];
+        if (c != col) {
+            if (col >= 0 && e != INT_MIN) atomicMax(&emax[col], e);
+            col = c;
+            e = INT_MIN;
+        }
+        if (a > 0.0) e = max(e, min(ilogb(a), 2000));
+    }
+    if (col >= 0 && e != INT_MIN) atomicMax(&emax[col], e);
+}
+// the coarse levels' multipoles of every column as double-float, scaled (M ispow) and divided
+// by 2^(emax + 1), and where outu is given also unscaled (M only divided by the same power of
+// two); in: [cols][ld_in] from offset c0, out: [cols][n]
+__global__ void k_m_to_df(const cd* __restrict__ in, int64_t ld_in, const double* __restrict__ isp, int64_t c0,
+                          int64_t n, int nrhs, const int* __restrict__ emax, dfc* __restrict__ outs,
+                          dfc* __restrict__ outu) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t / n, i = t - col * n;
+        const cd v = in[col * ld_in + c0 + i];
+        const int e = emax[col];
+        const double r = (e < -2000) ? 1.0 : ldexp(1.0, -(e + 1));   // < -2000: an all-zero column
+        const double f = isp[c0 + i] * r;
+        outs[t] = to_dfc(f * v.x, f * v.y);
+        if (outu) outu[t] = to_dfc(r * v.x, r * v.y);
+    }
 }
 
-// M2L of the coarse levels in double-float: the same work items, entry descriptors and
-// index flips as the FP64 k_m2l (fmm_kernels.cuh), with the multipoles and the tables as
-// float pairs and double-float multiply-accumulates; the slices are reduced in double-float
-// in a fixed order and the results written in FP64 (L, reaction-centre locals, or the FP64
-// partial sums that k_m2l_reduce adds).
+// M2L of the coarse levels in double-float: the work items, entry descriptors, index flips
+// and partial-sum slots of the FP64 k_m2l (fmm_kernels.cuh).  Multipoles: Ms (scaled) and Mu
+// (unscaled) of the boxes from coefficient c0, Mps (scaled) of the reaction centres from s0.
+// Each thread turns its sums to unscaled FP64 before the slices are added in a fixed order;
+// the outputs (L, reaction-centre locals, or partial sums for k_m2l_reduce) are FP64.
 __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ items, const M2LEnt* __restrict__ ents,
                       const int* __restrict__ box_level, const int* __restrict__ p_level,
                       const int64_t* __restrict__ coef_off, const int* __restrict__ slot_of,
-                      const int64_t* __restrict__ slot_coef, const dfc* __restrict__ m2lf,
-                      const int64_t* __restrict__ m2lf_off, const dfc* __restrict__ m2lr, int nrhs, int64_t ncoef,
-                      int64_t nslotcoef, int nparts, const dfc* __restrict__ Min, const dfc* __restrict__ Mp,
-                      cd* __restrict__ Lout, cd* __restrict__ Lp, cd* __restrict__ part) {
-    __shared__ dfc red[3 * 128];
+                      const int64_t* __restrict__ slot_coef, const dfc* __restrict__ fts,
+                      const dfc* __restrict__ ftu, const int64_t* __restrict__ m2lf_off,
+                      const dfc* __restrict__ rts, const float* __restrict__ rsc, const double* __restrict__ ispow,
+                      int nrhs, int64_t ncoef,
+                      int64_t nslotcoef, int nparts, const dfc* __restrict__ Ms, const dfc* __restrict__ Mu,
+                      int64_t c0, int64_t ncd, const dfc* __restrict__ Mps, int64_t s0, int64_t nsd,
+                      const int* __restrict__ emax, cd* __restrict__ Lout, cd* __restrict__ Lp,
+                      cd* __restrict__ part) {
+    __shared__ cd red[3 * 128];
     __shared__ M2LEnt se[64];
     const M2LItem it = items[blockIdx.x];
     const int T = it.box;
@@ -566,10 +683,14 @@ __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ item
     const int idx = it.chunk * W + lane;
     const bool live = sl < NS && idx < nco;
     const int nn = idx - p;
+    const int sg = nn >= 0 ? 1 : -1;
+    const double isp = live ? ispow[coef_off[T] + idx] : 0.0;   // s^-|n| of the target box
     for (int col = 0; col < nrhs; ++col) {
-        const dfc* Mc = Min + (int64_t)col * ncoef;
-        const dfc* Mpc = Mp + (int64_t)col * nslotcoef;
-        dfc acc0 = dfc_zero(), acc1 = dfc_zero(), acc2 = dfc_zero();
+        const dfc* Msc = Ms + (int64_t)col * ncd - c0 + p;    // [E.src + m] is M~_m of the source box
+        const dfc* Muc = Mu + (int64_t)col * ncd - c0 + p;
+        const dfc* Mpc = Mps + (int64_t)col * nsd - s0;
+        const dfc* Mbc = Ms + (int64_t)col * ncd - c0;
+        dfc acc0 = dfc_zero(), acc1 = dfc_zero(), acc2 = dfc_zero(), accu = dfc_zero();
         for (int eb = it.e0; eb < it.e1; eb += 64) {
             const int cnt = min(64, it.e1 - eb);
             __syncthreads();
@@ -579,15 +700,25 @@ __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ item
             for (int q = 0; q < cnt; ++q) {
                 const M2LEnt E = se[q];
                 if (!(E.flags & M2L_REACT)) {
-                    const dfc* src = Mc + E.src;
-                    const dfc* tb = m2lf + m2lf_off[E.tab] + p - nn;
-                    for (int mi = sl; mi < nco; mi += NS) dfc_fma(acc0, src[mi], tb[mi]);
+                    const int64_t tb = m2lf_off[E.tab] + 2 * p - nn;   // [tb + m] is entry m - n
+                    const dfc* ms_ = Msc + E.src;
+                    const dfc* mu_ = Muc + E.src;
+                    for (int k = sl; k < nco; k += NS) {
+                        if (k <= p) {
+                            const int m = -sg * k;
+                            dfc_fma(acc0, ms_[m], fts[tb + m]);
+                        } else {
+                            const int m = sg * (k - p);
+                            dfc_fma(accu, mu_[m], ftu[tb + m]);
+                        }
+                    }
                 } else {
-                    const dfc* src = ((E.flags & M2L_SRC_SLOT) ? Mpc : Mc) + E.src;
+                    const dfc* src = (E.flags & M2L_SRC_SLOT) ? Mpc + E.src : Mbc + E.src;
                     const bool bdown = (E.flags & M2L_B_DOWN) != 0;
                     const int mrow = bdown ? nn : -nn;
                     const bool flip = (E.flags & M2L_FLIP) != 0;
-                    const dfc* col_m = m2lr + E.tab + (flip ? (p - mrow) + (int64_t)2 * p * nco : (mrow + p));
+                    const int row = flip ? p - mrow : p + mrow;
+                    const dfc* col_m = rts + E.tab + row + (flip ? (int64_t)2 * p * nco : 0);
                     const int64_t cs = flip ? -(int64_t)nco : (int64_t)nco;
                     dfc bsum = dfc_zero();
                     if (E.flags & M2L_A_DOWN) {
@@ -595,7 +726,8 @@ __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ item
                     } else {
                         for (int mi = sl; mi < nco; mi += NS) dfc_fma(bsum, col_m[mi * cs], dfc_sign(src[2 * p - mi], mi - p));
                     }
-                    bsum = dfc_sign(bsum, (!bdown) & mrow);
+                    const float rf = rsc[E.tab + row];
+                    bsum = dfc_sign(make_float4(bsum.x * rf, bsum.y * rf, bsum.z * rf, bsum.w * rf), (!bdown) & mrow);
                     const int dst = (E.flags >> M2L_DST_SHIFT) & 3;
                     if (dst == 0) dfc_add(acc0, bsum);
                     else if (dst == 1) dfc_add(acc1, bsum);
@@ -604,17 +736,20 @@ __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ item
             }
         }
         if (sl < NS) {
-            red[(0 * NS + sl) * W + lane] = acc0;
-            red[(1 * NS + sl) * W + lane] = acc1;
-            red[(2 * NS + sl) * W + lane] = acc2;
+            const int ecol = emax[col];
+            const double unit = (ecol < -2000) ? 1.0 : ldexp(1.0, ecol + 1);   // the column's normalisation
+            const double f = isp * unit;
+            red[(0 * NS + sl) * W + lane] = mk(fma(f, df_value(acc0.x, acc0.y), unit * df_value(accu.x, accu.y)),
+                                               fma(f, df_value(acc0.z, acc0.w), unit * df_value(accu.z, accu.w)));
+            red[(1 * NS + sl) * W + lane] = mk(f * df_value(acc1.x, acc1.y), f * df_value(acc1.z, acc1.w));
+            red[(2 * NS + sl) * W + lane] = mk(f * df_value(acc2.x, acc2.y), f * df_value(acc2.z, acc2.w));
         }
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * W; i += blockDim.x) {
             const int k = i / W, ln = i - k * W, ix = it.chunk * W + ln;
             if (ix >= nco) continue;
-            dfc t = red[(k * NS) * W + ln];
-            for (int q = 1; q < NS; ++q) dfc_add(t, red[(k * NS + q) * W + ln]);
-            const cd v = mk(df_value(t.x, t.y), df_value(t.z, t.w));
+            cd v = red[(k * NS) * W + ln];
+            for (int q = 1; q < NS; ++q) v += red[(k * NS + q) * W + ln];
             if (it.part >= 0) {
                 part[(((int64_t)col * nparts + it.part) * 3 + k) * XT_W + ln] = v;
             } else {
@@ -637,11 +772,12 @@ static void mixed_free_buffers(MixedState* ms, bool in_flight) {
     ms->cols = 0;
 }
 static void mixed_free_df(MixedState* ms, bool in_flight) {
-    for (void* b : {(void*)ms->Mdf, (void*)ms->Mpdf}) {
+    for (void* b : {(void*)ms->Mdf, (void*)ms->Mudf, (void*)ms->Mpdf, (void*)ms->df_emax}) {
         if (in_flight) dev_release_now(b);
         else dev_release(b);
     }
-    ms->Mdf = ms->Mpdf = nullptr;
+    ms->Mdf = ms->Mudf = ms->Mpdf = nullptr;
+    ms->df_emax = nullptr;
     ms->df_cols = 0;
 }
 
@@ -650,7 +786,7 @@ void mixed_destroy(lfmm_geometry_s* g) {
     MixedState* ms = g->mixed;
     mixed_free_buffers(ms, false);
     mixed_free_df(ms, false);
-    dev_release(ms->ftab_df); dev_release(ms->rtab_df);
+    dev_release(ms->ftab_df); dev_release(ms->rtab_df); dev_release(ms->rtab_rsc);
     dev_release(ms->ispow); dev_release(ms->ispow_slot); dev_release(ms->ftab); dev_release(ms->ftab_off);
     dev_release(ms->rtab); dev_release(ms->d_scale); dev_release(ms->wtab); dev_release(ms->wtab_off);
     dev_release(ms->d_xd_layer);
@@ -670,6 +806,21 @@ static T* upload_raw(const std::vector<T>& v, size_t& bytes) {
         cuda_check(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, cudaStreamPerThread),
                    "upload");
     return p;
+}
+
+// coefficient ranges of one level: boxes, then reaction centres (both follow box order)
+static void level_ranges(lfmm_geometry_s* g, int l, int64_t* c0, int64_t* c1, int64_t* s0, int64_t* s1) {
+    const TreeHost& t = g->tree;
+    *c0 = g->box_coef_off_host[t.level_start[l]];
+    *c1 = (l < t.D) ? g->box_coef_off_host[t.level_start[l + 1]] : g->ncoef;
+    *s0 = g->nslotcoef;
+    *s1 = g->nslotcoef;
+    for (size_t q = 0; q < g->slot_box_host.size(); ++q) {
+        const int lv = t.box_level[g->slot_box_host[q]];
+        if (lv >= l && *s0 == g->nslotcoef) *s0 = g->slot_coef_host[q];
+        if (lv > l) { *s1 = g->slot_coef_host[q]; break; }
+    }
+    if (*s1 < *s0) *s1 = *s0;
 }
 
 // Scales and FP32 tables of the precision form (once per geometry, on first use).
@@ -740,25 +891,74 @@ static void mixed_build(lfmm_geometry_s* g) {
     // passes (children at levels > lm)
     ms->lm = std::max(l0, std::min(mixed_level(g), D + 1));
     ms->d_scale = upload_raw(ms->scale, ms->bytes);
-    if (ms->df_ok && ms->lm > l0) {   // double-float copies of the tables the coarse levels' M2L reads
-        cuda_check(cudaMallocAsync((void**)&ms->ftab_df, sizeof(dfc) * std::max<int64_t>(g->m2lf_len, 1),
-                                   cudaStreamPerThread), "cudaMallocAsync ftab_df");
-        ms->bytes += sizeof(dfc) * std::max<int64_t>(g->m2lf_len, 1);
-        if (g->m2lf_len > 0)
-            k_to_df<<<(int)std::min<int64_t>((g->m2lf_len + 255) / 256, 152 * 16), 256>>>(g->d_m2lf, g->m2lf_len,
-                                                                                         ms->ftab_df);
-        std::vector<int> coarse;
+    if (ms->lm > l0) {
+        // Double-float tables of the coarse levels' M2L.  They are used when every stored
+        // component stays below 1e13 and the scaled multipole basis below 1e13 (log10 sum at
+        // most 26): products then stay below 1e26 times the sources' total |weight x|,
+        // far inside the FP32 exponent range.  Otherwise those levels keep the FP64 M2L.
+        double big_m = 0.0;
+        for (int lay = 0; lay < nl; ++lay)
+            for (int l = l0; l < ms->lm; ++l) {
+                double bm = 0.0;
+                choose_scale(g->m.k[lay], t.width(l), t.p_level[l], &bm);
+                big_m = std::max(big_m, bm);
+            }
+        std::vector<int> ftl, rkl;
+        for (int id = 0; id < ntab; ++id)
+            if (g->ftab_lev[id] < ms->lm) ftl.push_back(id);
         for (int kk = 0; kk < nk; ++kk)
-            if (g->rkeys_host[kk].level < ms->lm) coarse.push_back(kk);
+            if (g->rkeys_host[kk].level < ms->lm) rkl.push_back(kk);
+        const int64_t flen = std::max<int64_t>(g->m2lf_len, 1);
+        cuda_check(cudaMallocAsync((void**)&ms->ftab_df, sizeof(dfc) * 2 * flen, cudaStreamPerThread),
+                   "cudaMallocAsync ftab_df");
         cuda_check(cudaMallocAsync((void**)&ms->rtab_df, sizeof(dfc) * std::max<int64_t>(rtot, 1), cudaStreamPerThread),
                    "cudaMallocAsync rtab_df");
-        ms->bytes += sizeof(dfc) * std::max<int64_t>(rtot, 1);
-        if (!coarse.empty()) {
-            int* d_coarse = upload_raw(coarse, scratch);
-            k_rtab_to_df<<<(int)coarse.size(), 256>>>(g->d_m2lr, g->d_rkeys, d_coarse, ms->rtab_df);
-            cuda_check(cudaGetLastError(), "k_rtab_to_df");
-            cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "k_rtab_to_df");
-            dev_release(d_coarse);
+        cuda_check(cudaMallocAsync((void**)&ms->rtab_rsc, sizeof(float) * std::max<int64_t>(rtot, 1),
+                                   cudaStreamPerThread), "cudaMallocAsync rtab_rsc");
+        unsigned* d_amax = nullptr;   // [2]: free-space, reaction
+        cuda_check(cudaMallocAsync((void**)&d_amax, 2 * sizeof(unsigned), cudaStreamPerThread), "cudaMallocAsync amax");
+        cuda_check(cudaMemsetAsync(d_amax, 0, 2 * sizeof(unsigned), cudaStreamPerThread), "amax reset");
+        if (!ftl.empty()) {
+            int* d_l = upload_raw(ftl, scratch);
+            k_ftab_df<<<(int)ftl.size(), 256, 0, cudaStreamPerThread>>>(g->d_m2lf, g->d_m2lf_off, d_l, d_tp, d_ts,
+                                                                        ms->ftab_df, ms->ftab_df + flen, d_amax);
+            cuda_check(cudaGetLastError(), "k_ftab_df");
+            dev_release(d_l);
+        }
+        if (!rkl.empty()) {
+            int* d_l = upload_raw(rkl, scratch);
+            k_rtab_df<<<(int)rkl.size(), 256, 0, cudaStreamPerThread>>>(g->d_m2lr, g->d_rkeys, d_l, d_kss, d_kst,
+                                                                        ms->rtab_df, ms->rtab_rsc, d_amax + 1);
+            cuda_check(cudaGetLastError(), "k_rtab_df");
+            dev_release(d_l);
+        }
+        unsigned amax_bits[2] = {0, 0};
+        cuda_check(cudaMemcpyAsync(amax_bits, d_amax, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                   cudaStreamPerThread), "amax read");
+        cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "double-float tables");
+        dev_release(d_amax);
+        float amax[2];
+        std::memcpy(amax, amax_bits, sizeof(amax));
+        for (int i = 0; i < 2; ++i)
+            ms->df_range[i] = std::isfinite(amax[i]) ? std::log10(std::max(amax[i], 1e-30f)) : 1e300;
+        ms->df_range[2] = big_m;
+        // The multipoles enter normalised below 1 (per column) and the reaction rows are stored
+        // below 1 with their own factors, so every product is bounded by the free-space tables;
+        // those must stay far inside the FP32 range (and the reaction rows' factors within it).
+        ms->df_ok = ms->df_range[1] <= 1e299 && ms->df_range[0] <= 20.0;
+        if (ms->df_ok) {
+            ms->bytes += sizeof(dfc) * (2 * flen + std::max<int64_t>(rtot, 1)) + sizeof(float) * std::max<int64_t>(rtot, 1);
+            int64_t d0, d1, e0, e1;
+            level_ranges(g, l0, &ms->df_c0, &d1, &ms->df_s0, &e1);
+            level_ranges(g, ms->lm - 1, &d0, &d1, &e0, &e1);
+            ms->df_ncd = d1 - ms->df_c0;
+            ms->df_nsd = e1 - ms->df_s0;
+        } else {
+            dev_release(ms->ftab_df);
+            dev_release(ms->rtab_df);
+            dev_release(ms->rtab_rsc);
+            ms->ftab_df = ms->rtab_df = nullptr;
+            ms->rtab_rsc = nullptr;
         }
     }
     {   // the tensor-core M2L's boxes: every box of the FP32 levels
@@ -887,20 +1087,6 @@ void mixed_l2l(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
     pass32(g, g->dn_begin[l], g->dn_end[l], g->tree.p_level[l], 1, nrhs, g->mixed->L, g->mixed->Lp, s);
 }
 
-// coefficient ranges of one level: boxes, then reaction centres (both follow box order)
-static void level_ranges(lfmm_geometry_s* g, int l, int64_t* c0, int64_t* c1, int64_t* s0, int64_t* s1) {
-    const TreeHost& t = g->tree;
-    *c0 = g->box_coef_off_host[t.level_start[l]];
-    *c1 = (l < t.D) ? g->box_coef_off_host[t.level_start[l + 1]] : g->ncoef;
-    *s0 = g->nslotcoef;
-    *s1 = g->nslotcoef;
-    for (size_t q = 0; q < g->slot_box_host.size(); ++q) {
-        const int lv = t.box_level[g->slot_box_host[q]];
-        if (lv >= l && *s0 == g->nslotcoef) *s0 = g->slot_coef_host[q];
-        if (lv > l) { *s1 = g->slot_coef_host[q]; break; }
-    }
-    if (*s1 < *s0) *s1 = *s0;
-}
 
 void mixed_m_to64(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
     MixedState* ms = g->mixed;
@@ -998,37 +1184,59 @@ void mixed_check_waits(lfmm_geometry_s* g) {
 }
 
 bool mixed_coarse_df(lfmm_geometry_s* g) { return g->mixed && g->mixed->df_ok; }
+void mixed_info(lfmm_geometry_s* g, int* lm, int* df, double* range) {
+    *lm = g->mixed ? g->mixed->lm : std::max(g->tree.l0, std::min(mixed_level(g), g->tree.D + 1));
+    *df = g->mixed ? (g->mixed->df_ok ? 1 : 0) : -1;
+    for (int i = 0; i < 3; ++i) range[i] = g->mixed ? g->mixed->df_range[i] : 0.0;
+}
 
 void mixed_m2l_coarse(lfmm_geometry_s* g, int nrhs, int n_items, cudaStream_t s) {
     MixedState* ms = g->mixed;
-    const TreeHost& t = g->tree;
     if (n_items <= 0) return;
     if (ms->df_cols < nrhs) {
         mixed_free_df(ms, true);
-        ms->Mdf = (dfc*)dev_alloc_ready(sizeof(dfc) * (size_t)std::max<int64_t>(g->ncoef, 1) * nrhs, "M df");
-        ms->Mpdf = (dfc*)dev_alloc_ready(sizeof(dfc) * (size_t)std::max<int64_t>(g->nslotcoef, 1) * nrhs, "Mp df");
+        const size_t nc = (size_t)std::max<int64_t>(ms->df_ncd, 1) * nrhs;
+        ms->Mdf = (dfc*)dev_alloc_ready(sizeof(dfc) * nc, "M double-float");
+        ms->Mudf = (dfc*)dev_alloc_ready(sizeof(dfc) * nc, "M double-float");
+        ms->Mpdf = (dfc*)dev_alloc_ready(sizeof(dfc) * (size_t)std::max<int64_t>(ms->df_nsd, 1) * nrhs,
+                                         "reaction-centre M double-float");
+        ms->df_emax = (int*)dev_alloc_ready(sizeof(int) * nrhs, "column exponents");
         ms->df_cols = nrhs;
     }
-    // the coarse levels' multipoles (cells and reaction centres) as float pairs
-    int64_t c0, c1, s0, s1, d0, d1, e0, e1;
-    level_ranges(g, t.l0, &c0, &d1, &s0, &e1);
-    level_ranges(g, ms->lm - 1, &d0, &c1, &e0, &s1);
-    for (int col = 0; col < nrhs; ++col) {
-        if (c1 > c0) {
-            k_to_df<<<(int)std::min<int64_t>((c1 - c0 + 255) / 256, 152 * 16), 256, 0, s>>>(
-                g->d_M + col * g->ncoef + c0, c1 - c0, ms->Mdf + col * g->ncoef + c0);
-            ++g->n_launches;
-        }
-        if (s1 > s0) {
-            k_to_df<<<(int)std::min<int64_t>((s1 - s0 + 255) / 256, 152 * 16), 256, 0, s>>>(
-                g->d_Mp + col * g->nslotcoef + s0, s1 - s0, ms->Mpdf + col * g->nslotcoef + s0);
-            ++g->n_launches;
-        }
+    // every column's exponent bound over its coarse multipoles (cells and reaction centres)
+    cuda_check(cudaMemsetAsync(ms->df_emax, 0x80, sizeof(int) * nrhs, s), "exponent reset");   // 0x80808080: none
+    if (ms->df_ncd > 0) {
+        const int64_t n = ms->df_ncd * nrhs;
+        k_m_absmax<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+            g->d_M, g->ncoef, ms->ispow, ms->df_c0, ms->df_ncd, nrhs, ms->df_emax);
+        ++g->n_launches;
     }
-    cuda_check(cudaGetLastError(), "k_to_df (multipoles)");
+    if (ms->df_nsd > 0) {
+        const int64_t n = ms->df_nsd * nrhs;
+        k_m_absmax<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+            g->d_Mp, g->nslotcoef, ms->ispow_slot, ms->df_s0, ms->df_nsd, nrhs, ms->df_emax);
+        ++g->n_launches;
+    }
+    // the coarse levels' multipoles (cells: scaled and unscaled; reaction centres: scaled)
+    if (ms->df_ncd > 0) {
+        const int64_t n = ms->df_ncd * nrhs;
+        k_m_to_df<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            g->d_M, g->ncoef, ms->ispow, ms->df_c0, ms->df_ncd, nrhs, ms->df_emax, ms->Mdf, ms->Mudf);
+        ++g->n_launches;
+    }
+    if (ms->df_nsd > 0) {
+        const int64_t n = ms->df_nsd * nrhs;
+        k_m_to_df<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            g->d_Mp, g->nslotcoef, ms->ispow_slot, ms->df_s0, ms->df_nsd, nrhs, ms->df_emax, ms->Mpdf, nullptr);
+        ++g->n_launches;
+    }
+    cuda_check(cudaGetLastError(), "k_m_to_df");
     k_m2l_df<<<n_items, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
-                                     g->d_slot_of, g->d_slot_coef, ms->ftab_df, g->d_m2lf_off, ms->rtab_df, nrhs,
-                                     g->ncoef, g->nslotcoef, g->n_m2l_parts, ms->Mdf, ms->Mpdf, g->d_L, g->d_Lp,
+                                     g->d_slot_of, g->d_slot_coef, ms->ftab_df,
+                                     ms->ftab_df + std::max<int64_t>(g->m2lf_len, 1), g->d_m2lf_off, ms->rtab_df,
+                                     ms->rtab_rsc, ms->ispow, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts, ms->Mdf, ms->Mudf,
+                                     ms->df_c0, ms->df_ncd, ms->Mpdf, ms->df_s0, ms->df_nsd, ms->df_emax, g->d_L,
+                                     g->d_Lp,
                                      g->d_m2l_part);
     cuda_check(cudaGetLastError(), "k_m2l_df");
     ++g->n_launches;

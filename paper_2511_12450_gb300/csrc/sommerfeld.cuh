@@ -102,7 +102,7 @@ __device__ __forceinline__ QuadNode contour_node(const QuadRule& q, int j, int P
 // (it keeps its full depth there), then the two rays from T' - i h.  The region
 // between this path and the real axis right of T' holds no singularity, so the
 // rays replace the rest of the real axis as before.  P panels on the detour.
-__device__ __forceinline__ int table_panels(const QuadRule& q, double X, double D, double* h_out) {
+__host__ __device__ __forceinline__ int table_panels(const QuadRule& q, double X, double D, double* h_out) {
     double ax = fabs(X);
     double h = fmin(0.5, 1.0 / fmax(ax, 1e-3));
     *h_out = h;

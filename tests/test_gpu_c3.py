@@ -8,6 +8,7 @@ x non-zero on a seeded 4,096-point subset; 8 of the rows have their own column i
 so the self terms are covered).  The FP64 operator is held to the FMM truncation level at
 p = 20 measured on these rows (worst 9.8e-8, median 7.8e-12); the precision form to its FP32
 level (measured: worst row 1.2e-6, median 1.9e-7; 2.6e-7 from FP64 on a dense random x).
+Its coarse wide-band levels run the M2L in double-float (pairs of FP32).
 """
 
 import json
@@ -72,7 +73,12 @@ def test_c3_precision_form_against_fp64(c3):
     y64 = lf.matvec(G, x)
     y32 = lf.matvec(G, x, mixed=True)
     d = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
-    print(f"C3 precision form vs FP64 (dense random x): {d:.3e}")
+    lm, df, rf, rr, bm = lf.geometry_query(G, "precision_form", np.float64)
+    print(f"C3 precision form vs FP64 (dense random x): {d:.3e}; FP32 from level {int(lm)}, "
+          f"coarser levels' M2L in {'double-float' if df == 1 else 'FP64'} (log10 ranges: free tables "
+          f"{rf:.1f}, reaction tables {rr:.1f}, scaled basis {bm:.1f})")
+    # the wide-band levels 4..6 (orders 74, 47, 31) take the double-float M2L
+    assert df == 1
     assert d <= OP_TOL_MIXED
     # repeated products give the same bits (fixed summation order in every kernel)
     assert torch.equal(lf.matvec(G, x), y64)
