@@ -252,13 +252,14 @@ def cpu_baseline(wl, rows_per_sample, n_samples=1):
             "seconds": dt}
 
 
-def run_serving(lfmm, n_requests=32, slots=4, seed=12455, n_max=131072.0, max_bodies=128):
+def run_serving(lfmm, n_requests=32, slots=8, seed=12455, n_max=131072.0, max_bodies=128, max_iter=2000):
     """Serving form on a bounded stand-in for the request stream (random 2-4 layer stacks,
     k in [2, 12], N log-uniform in [2k, n_max], up to max_bodies bodies): Poisson arrivals at
     1.5x the FP64 one-at-a-time capacity.  The arms see the same arrivals: FP64 one at a time
-    (1 slot), FP64 served (``slots`` concurrent requests), the served mixed-precision form and
-    the served combined-field operator (second kind, opt-in); each solve to the FP64 residual
-    1e-8."""
+    (1 slot), FP64 served (``slots`` requests in flight, their GMRES steps advanced together
+    with the FP64 products in shared launches), the served mixed-precision form and the served
+    combined-field operator (second kind, opt-in); each solve to the FP64 residual 1e-8 within
+    max_iter steps."""
     from workloads import config_c5_stream
 
     stream = config_c5_stream(n_requests, seed, n_max=n_max, max_bodies=max_bodies)
@@ -278,7 +279,7 @@ def run_serving(lfmm, n_requests=32, slots=4, seed=12455, n_max=131072.0, max_bo
             if dt > 0:
                 time.sleep(dt)
             tickets.append(srv.submit(med.interfaces, med.k, med.eta, pts, w, ang, tol=1e-8,
-                                      precision=precision, max_iter=1000, normals=nrm, combined=combined))
+                                      precision=precision, max_iter=max_iter, normals=nrm, combined=combined))
         lat, conv, res, its = [], 0, 0.0, 0
         for t in tickets:
             _x, info, tm = srv.wait(t)

@@ -53,8 +53,10 @@ typedef enum {
     LFMM_ERR_OUT_OF_MEMORY = -2,
     LFMM_ERR_CUDA = -3,
     LFMM_ERR_NODE_ON_INTERFACE = -4,  /* a point lies on (or within 1e-12*scale of) an interface */
-    LFMM_ERR_QUADRATURE = -5,         /* reserved: the library's quadrature rules are fixed
-                                         (no adaptive step that could fail to converge) */
+    LFMM_ERR_QUADRATURE = -5,         /* lfmm_geometry_build: a stored near-field value or a
+                                         translation table came out non-finite (checked at the
+                                         end of every build); the quadrature rules are fixed, so
+                                         this marks a medium or order beyond their range */
     LFMM_ERR_TIMEOUT = -6,            /* a bounded device wait gave up: the tensor-core
                                          M2L of LFMM_MIXED (16+ columns) waits on its own
                                          MMAs.  The affected products were computed with
@@ -403,6 +405,11 @@ lfmm_status lfmm_server_destroy(lfmm_server s);
  * precision form, entries held in complex64 and in FP64 -- 0 until its first call),
  * "setup_times" (double[4]: seconds of the set-up spent on the tree and interaction
  * lists, the near field, the far field (moment tables, translation plans), and in all),
+ * "nonfinite" (double[4]: non-finite entries of the stored near field, the free-space and
+ * reaction translation tables, and the preconditioner once built -- all 0 for a sound geometry),
+ * "reaction_tables" (double[8 * tables]: per reaction moment table its component, level,
+ * order, horizontal offset X, source and target heights, effective distance D and its
+ * non-finite entries),
  * "table_work" (double[2]: complex multiply-adds of the set-up's reaction moment tables,
  * cross-layer and same-layer components: entries x quadrature nodes x 2),
  * "precision_form" (double[5]: first level of the precision form's FP32 far field;

@@ -127,6 +127,9 @@ static lfmm_status guarded_body(F&& f) {
     } catch (const InterfaceError& e) {
         set_error(e.msg);
         return LFMM_ERR_NODE_ON_INTERFACE;
+    } catch (const QuadratureError& e) {
+        set_error(e.msg);
+        return LFMM_ERR_QUADRATURE;
     } catch (const TimeoutError& e) {
         set_error(e.msg);
         return LFMM_ERR_TIMEOUT;
@@ -402,6 +405,14 @@ static lfmm_geometry_s* build_geometry(lfmm_medium med, int64_t n, const double*
         tp = std::chrono::steady_clock::now();
         fmm_build(g);
         g->setup_phase[2] = since(tp);
+        {   // every stored kernel value and translation table must be finite
+            double bad[4];
+            count_nonfinite(g, bad);
+            if (bad[0] + bad[1] + bad[2] > 0)
+                throw QuadratureError{"non-finite values in the stored near field (" + std::to_string((long long)bad[0]) +
+                                      "), free-space tables (" + std::to_string((long long)bad[1]) +
+                                      ") or reaction tables (" + std::to_string((long long)bad[2]) + ")"};
+        }
         if (prm && (prm->flags & LFMM_AUTOTUNE)) fmm_autotune(g);
         g->setup_seconds = since(t0);
         return g;
@@ -776,6 +787,15 @@ lfmm_status lfmm_geometry_query(lfmm_geometry g, const char* name, void* host_ou
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "setup_times") {
             dtmp = {g->setup_phase[0], g->setup_phase[1], g->setup_phase[2], g->setup_seconds};
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "nonfinite") {
+            dtmp.assign(4, 0.0);
+            count_nonfinite(g, dtmp.data());
+            src = dtmp.data();
+            bytes = (int64_t)(dtmp.size() * sizeof(double));
+        } else if (nm == "reaction_tables") {
+            react_key_report(g, dtmp);
             src = dtmp.data();
             bytes = (int64_t)(dtmp.size() * sizeof(double));
         } else if (nm == "table_work") {

@@ -42,6 +42,49 @@ __host__ __device__ __forceinline__ cd cdiv(cd a, cd b) {
     }
 }
 __host__ __device__ __forceinline__ cd cinv(cd b) { return cdiv(mk(1.0, 0.0), b); }
+// A complex value with its own binary exponent, m 2^e (max(|m.x|, |m.y|) in [0.5, 1), or
+// m = 0): products of many factors without intermediate overflow or underflow.  The
+// rescaling is by powers of two, so a product rounds as the plain one does wherever that
+// stays in range.
+struct xcd {
+    cd m;
+    int e;
+};
+__host__ __device__ __forceinline__ xcd xnorm(cd m, int e) {
+    const double a = fmax(fabs(m.x), fabs(m.y));
+    xcd r;
+    if (!(a > 0.0) || !(a <= 1.7e308)) { r.m = m; r.e = e; return r; }   // zero or not finite: as is
+    int k = 0;
+    frexp(a, &k);
+    r.m.x = ldexp(m.x, -k);
+    r.m.y = ldexp(m.y, -k);
+    r.e = e + k;
+    return r;
+}
+__host__ __device__ __forceinline__ xcd xmul(xcd a, xcd b) {
+    cd m;
+    m.x = a.m.x * b.m.x - a.m.y * b.m.y;
+    m.y = a.m.x * b.m.y + a.m.y * b.m.x;
+    return xnorm(m, a.e + b.e);
+}
+// the plain value (0 below the smallest double, infinite above the largest)
+__host__ __device__ __forceinline__ cd xval(xcd a) {
+    cd r;
+    r.x = ldexp(a.m.x, a.e);
+    r.y = ldexp(a.m.y, a.e);
+    return r;
+}
+// f u^k (k of either sign) by binary exponentiation on scaled values
+__host__ __device__ __forceinline__ xcd xpow_times(cd f, cd u, int k) {
+    xcd bb;
+    bb = xnorm(k >= 0 ? u : cinv(u), 0);
+    xcd cur = xnorm(f, 0);
+    for (int k2 = k >= 0 ? k : -k; k2 > 0; k2 >>= 1) {
+        if (k2 & 1) cur = xmul(cur, bb);
+        if (k2 > 1) bb = xmul(bb, bb);
+    }
+    return cur;
+}
 // fused a += b * c
 __host__ __device__ __forceinline__ void cfma(cd& a, cd b, cd c) {
     a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));

@@ -487,6 +487,7 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_rkeys = dupload(g, keys);
         g->rkeys_host = keys;
         g->d_m2lr = dalloc<cd>(g, (size_t)std::max<int64_t>(tot, 1));
+        g->m2lr_len = tot;
         if (!keys.empty()) {
             // same-layer components: Toeplitz tables from 4p+1 moments; others in runs of entries
             std::vector<TableChunk> work;
@@ -526,7 +527,7 @@ void fmm_build(lfmm_geometry_s* g) {
             if (!same.empty()) {
                 int* d_same = dupload(g, same);
                 const int nd = 4 * pmax_same + 1;
-                const size_t smem = (size_t)(16 * nd + 3 * 256 + nd) * sizeof(cd);   // k_react_tables_same layout
+                const size_t smem = (size_t)(2 * TAB_SAME_CH * nd + 3 * 256 + nd) * sizeof(cd);   // k_react_tables_same layout
                 raise_smem_limit((const void*)k_react_tables_same, smem, "same-layer tables smem");
                 k_react_tables_same<<<(int)same.size(), 256, smem>>>(g->m, g->quad, g->d_rkeys, d_same, g->d_comp,
                                                                      g->d_m2lr);

@@ -364,7 +364,11 @@ __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts
 // Reaction M2L moment tables of components whose source and field layers are the
 // same (k_S = k_T, so u = v on every node): I_{mn} = h_{n-m} with
 // h_d = sum_q (Fp_q u_q^d + Fm_q u_q^-d), d = -2p..2p -- 4p+1 moments per key
-// instead of (2p+1)^2.  One CTA per key; the table is then written out dense.
+// instead of (2p+1)^2.  One CTA per key; the table is then written out dense.  The
+// weights are folded into the power rows, each run of 16 starting from F u^d0 formed
+// with a separate exponent (xpow_times): far along the rays u^d alone leaves the double
+// range (|u| ~ 2 lambda / k) where F u^d does not, and F = 0 there must not meet u^d = inf.
+#define TAB_SAME_CH 8
 __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRule q,
                                                            const ReactKey* __restrict__ keys,
                                                            const int* __restrict__ key_list,
@@ -377,16 +381,17 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
     const double ka = med.k[ls];
     // nodes in batches of NB = 256 (all threads evaluate the spectral density, one
     // node each), then in chunks of CH for the power rows and the moment sums
-    const int CH = 16, NB = 256;
-    cd* Pw = sh;                 // [CH][nd]  u^d, d = -2p..2p
-    cd* Fp = Pw + CH * nd;       // [NB]
+    const int CH = TAB_SAME_CH, NB = 256;
+    cd* Pp = sh;                 // [CH][nd]  Fp u^(d - 2p)
+    cd* Pm = Pp + CH * nd;       // [CH][nd]  Fm u^(2p - d)
+    cd* Fp = Pm + CH * nd;       // [NB]
     cd* Fm = Fp + NB;            // [NB]
     cd* uu = Fm + NB;            // [NB]
     cd* hs = uu + NB;            // [nd] moments
     double h;
     const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
     const int ntot = P * 8 + 2 * q.tab_nes;
-    const int nseg = (nd + 15) / 16;   // runs of 16 consecutive powers per node
+    const int nseg = (nd + 15) / 16;   // runs of 16 consecutive powers per node and side
     cd acc[2] = {mk(0, 0), mk(0, 0)};   // d = threadIdx.x and threadIdx.x + 256
     for (int jb = 0; jb < ntot; jb += NB) {
         const int cntB = min(NB, ntot - jb);
@@ -403,17 +408,16 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
         for (int j0 = 0; j0 < cntB; j0 += CH) {
             const int cnt = min(CH, cntB - j0);
             __syncthreads();
-            // powers u^-2p .. u^2p: one thread per run of 16, its first power by binary
-            // exponentiation, then 15 products
-            for (int e = threadIdx.x; e < cnt * nseg; e += blockDim.x) {
-                const int r = e / nseg, sg = e - r * nseg, d0 = sg * 16;
+            // one thread per run of 16: its first value F u^e0 on scaled values, then 15 products
+            for (int e = threadIdx.x; e < cnt * 2 * nseg; e += blockDim.x) {
+                const int r = e / (2 * nseg), w = e - r * 2 * nseg, side = w / nseg, d0 = (w - side * nseg) * 16;
                 const cd u = uu[j0 + r];
-                const int e0 = d0 - 2 * p;
-                cd bb = (e0 >= 0) ? u : cinv(u), cur = mk(1.0, 0.0);
-                for (int k2 = e0 >= 0 ? e0 : -e0; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
-                cd* row = Pw + r * nd;
+                const int e0 = side == 0 ? d0 - 2 * p : 2 * p - d0;
+                cd cur = xval(xpow_times(side == 0 ? Fp[j0 + r] : Fm[j0 + r], u, e0));
+                const cd step = side == 0 ? u : cinv(u);
+                cd* row = (side == 0 ? Pp : Pm) + r * nd;
                 const int d1 = min(nd, d0 + 16);
-                for (int d = d0; d < d1; ++d) { row[d] = cur; cur = cur * u; }
+                for (int d = d0; d < d1; ++d) { row[d] = cur; cur = cur * step; }
             }
             __syncthreads();
             for (int s2 = 0; s2 < 2; ++s2) {
@@ -421,8 +425,8 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
                 if (di >= nd) break;
                 cd ac = acc[s2];
                 for (int r = 0; r < cnt; ++r) {
-                    cfma(ac, Fp[j0 + r], Pw[r * nd + di]);             // u^d
-                    cfma(ac, Fm[j0 + r], Pw[r * nd + (nd - 1 - di)]);   // u^-d
+                    ac += Pp[r * nd + di];   // Fp u^d
+                    ac += Pm[r * nd + di];   // Fm u^-d
                 }
                 acc[s2] = ac;
             }
@@ -506,10 +510,14 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
             cd S = sigma_comp(med, nd.lam, ls, a, lt, b);
             cd kya = ky_of(ka, nd.lam), kyb = ky_of(kb, nd.lam);
             cd SE = S * (eikh(kya, K.hS) * eikh(kyb, K.hT));
-            Fp[threadIdx.x] = SE * nd.fp;
-            Fm[threadIdx.x] = SE * nd.fm;
-            uu[threadIdx.x] = w_of(kya, nd.lam, ka);
-            vv[threadIdx.x] = w_of(kyb, nd.lam, kb);
+            const cd fp = SE * nd.fp, fm = SE * nd.fm;
+            Fp[threadIdx.x] = fp;
+            Fm[threadIdx.x] = fm;
+            // a node whose weights vanish (far along a ray) adds nothing: powers of 1 keep
+            // its finite-valued rows from meeting an infinite power
+            const bool zero = fp.x == 0.0 && fp.y == 0.0 && fm.x == 0.0 && fm.y == 0.0;
+            uu[threadIdx.x] = zero ? mk(1.0, 0.0) : w_of(kya, nd.lam, ka);
+            vv[threadIdx.x] = zero ? mk(1.0, 0.0) : w_of(kyb, nd.lam, kb);
         }
         for (int j0 = 0; j0 < cntB; j0 += TAB_CH) {
             const int cnt = min(TAB_CH, cntB - j0);
@@ -535,9 +543,7 @@ __global__ void __launch_bounds__(256) k_react_tables(MediumDev med, QuadRule q,
                     else { fac = Fm[j0 + r]; e0 = -n0; dst = Um + r * ncols + 32 * run; inv = true; }
                 }
                 const cd step = inv ? cinv(base) : base;
-                cd bb = (e0 >= 0) ? base : cinv(base);
-                cd cur = fac;
-                for (int k2 = e0 >= 0 ? e0 : -e0; k2 > 0; k2 >>= 1) { if (k2 & 1) cur = cur * bb; bb = bb * bb; }
+                cd cur = xval(xpow_times(fac, base, e0));   // on scaled values: no overflow on the way
                 for (int s2 = 0; s2 < len; ++s2) { dst[s2] = cur; cur = cur * step; }
             }
             __syncthreads();

@@ -261,6 +261,7 @@ struct lfmm_geometry_s {
     double setup_seconds = 0.0;
     double setup_phase[3] = {0.0, 0.0, 0.0};   // seconds: tree and lists, near field, far field (tables, plans)
     double table_cmacs[2] = {0.0, 0.0};        // complex multiply-adds of the moment tables: cross-layer, same-layer
+    int64_t m2lr_len = 0, pc_w_len = 0;         // entries of the reaction tables and of the preconditioner's W
     std::vector<void*> allocs;        // everything cudaMalloc'ed for this geometry
     // held by every call that applies the operator or the preconditioner to vectors
     // (matvec, the allocation-free matvec, precondition, solve, right-hand side, field):
@@ -279,6 +280,9 @@ struct TimeoutError {   // a bounded device wait gave up (LFMM_ERR_TIMEOUT)
     std::string msg;
 };
 struct ArgError {       // an invalid argument (LFMM_ERR_INVALID_ARG)
+    std::string msg;
+};
+struct QuadratureError { // a stored kernel value or translation table is not finite (LFMM_ERR_QUADRATURE)
     std::string msg;
 };
 struct InterfaceError { // a point on an interface (LFMM_ERR_NODE_ON_INTERFACE)
@@ -402,6 +406,21 @@ void round_to_c64(const cd* in, float2* out, int64_t n, cudaStream_t s);
 void apply_operator_sorted(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s,
                            bool mixed = false);
 void precond_build(lfmm_geometry_s* g);
+// non-finite entries of the stored near field, free-space and reaction tables and preconditioner
+void count_nonfinite(lfmm_geometry_s* g, double out[4]);
+// per reaction table: component, level, order, X, hS, hT, D, non-finite entries
+void react_key_report(lfmm_geometry_s* g, std::vector<double>& out);
+// lockstep solves of the serving loop (solver.cu): create on the request's stream (builds
+// the preconditioner, gathers b from input order), then begin, rounds and finish on the
+// engine's stream; destroy releases everything
+struct BatchSolve;
+BatchSolve* batch_solve_create(lfmm_geometry_s* g, const cd* b_in, double tol, int maxit, bool pre, int precision,
+                               cudaStream_t s);
+void batch_solve_begin(BatchSolve* S, cudaStream_t s);
+void batch_solve_round(const std::vector<BatchSolve*>& all, cudaStream_t s);
+bool batch_solve_done(const BatchSolve* S);
+void batch_solve_finish(BatchSolve* S, cd* x_out, lfmm_gmres_info* info, cudaStream_t s);
+void batch_solve_destroy(BatchSolve* S, cudaStream_t s);
 int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, int maxit, bool pre,
                  cudaStream_t s, lfmm_gmres_info* info, int precision = 0, int restart = 0);
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s);

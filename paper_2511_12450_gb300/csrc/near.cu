@@ -497,6 +497,14 @@ void near_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s) {
     std::vector<int> prefix(1, 0);
     for (const BatchOp& op : ops) {
         lfmm_geometry_s* g = op.g;
+        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN) {   // as near_apply: its own warp-per-leaf launch (same sums)
+            const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
+            k_near_leaf_w<false><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                    g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                    nullptr, op.x, nullptr, op.y, g->n, op.nrhs);
+            cuda_check(cudaGetLastError(), "k_near_leaf_w");
+            continue;
+        }
         jobs.push_back(NearJob{g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end,
                                NearRowPart{g->d_nl_off, g->d_nl_jptr, g->d_nl_j}, g->d_nb_val, op.x, op.y, g->n,
                                op.nrhs});

@@ -189,6 +189,7 @@ void precond_build(lfmm_geometry_s* g) {
     int* d_lay = dupload(g, lay);
     int64_t* d_aoff = dupload(g, aoff);
     g->d_pc_W = dalloc<cd>(g, (size_t)wt);
+    g->pc_w_len = wt;
     cd* Ascr = nullptr;
     int* piv = nullptr;
     cuda_check(cudaMallocAsync((void**)&Ascr, sizeof(cd) * std::max<int64_t>(at, 1), cudaStreamPerThread),
@@ -206,6 +207,64 @@ void precond_build(lfmm_geometry_s* g) {
     g->pc_own_first = d_own_first;
     g->pc_own_cnt = d_own_cnt;
     g->pc_ready = true;
+}
+
+__global__ void k_count_nonfinite(const cd* __restrict__ v, int64_t n, unsigned long long* __restrict__ cnt) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (isfinite(v[i].x) && isfinite(v[i].y)) ? 0ull : 1ull;
+    if (c) atomicAdd(cnt, c);
+}
+
+void count_nonfinite(lfmm_geometry_s* g, double out[4]) {
+    unsigned long long* d = nullptr;
+    cuda_check(cudaMallocAsync((void**)&d, 4 * sizeof(unsigned long long), cudaStreamPerThread), "malloc count");
+    cuda_check(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), cudaStreamPerThread), "memset count");
+    const cd* bufs[4] = {g->d_nb_val, g->d_m2lf, g->d_m2lr, g->d_pc_W};
+    const int64_t lens[4] = {g->nb_nnz, g->m2lf_len, g->m2lr_len, g->pc_ready ? g->pc_w_len : 0};
+    for (int i = 0; i < 4; ++i)
+        if (bufs[i] && lens[i] > 0)
+            k_count_nonfinite<<<152 * 4, 256, 0, cudaStreamPerThread>>>(bufs[i], lens[i], d + i);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cuda_check(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, cudaStreamPerThread), "count d2h");
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "count sync");
+    dev_release(d);
+    for (int i = 0; i < 4; ++i) out[i] = (double)h[i];
+}
+
+// per reaction table: its non-finite entries (one CTA per key)
+__global__ void k_key_nonfinite(const cd* __restrict__ tab, const ReactKey* __restrict__ keys, double* __restrict__ out) {
+    const ReactKey K = keys[blockIdx.x];
+    const int64_t ne = (int64_t)(2 * K.pT + 1) * (2 * K.pS + 1);
+    int c = 0;
+    for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) c += (isfinite(tab[K.off + e].x) && isfinite(tab[K.off + e].y)) ? 0 : 1;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ int sc[8];
+    if ((threadIdx.x & 31) == 0) sc[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sc[i];
+        out[blockIdx.x] = (double)t;
+    }
+}
+
+void react_key_report(lfmm_geometry_s* g, std::vector<double>& out) {
+    const int nk = (int)g->rkeys_host.size();
+    out.assign((size_t)nk * 8, 0.0);
+    if (nk == 0) return;
+    double* d = nullptr;
+    cuda_check(cudaMallocAsync((void**)&d, sizeof(double) * nk, cudaStreamPerThread), "malloc key report");
+    k_key_nonfinite<<<nk, 256, 0, cudaStreamPerThread>>>(g->d_m2lr, g->d_rkeys, d);
+    std::vector<double> h(nk);
+    cuda_check(cudaMemcpyAsync(h.data(), d, sizeof(double) * nk, cudaMemcpyDeviceToHost, cudaStreamPerThread), "d2h");
+    cuda_check(cudaStreamSynchronize(cudaStreamPerThread), "key report");
+    dev_release(d);
+    for (int k = 0; k < nk; ++k) {
+        const ReactKey& K = g->rkeys_host[k];
+        const double v[8] = {(double)K.comp, (double)K.level, (double)K.pS, K.X, K.hS, K.hT, K.D, h[k]};
+        for (int i = 0; i < 8; ++i) out[(size_t)k * 8 + i] = v[i];
+    }
 }
 
 void precond_apply_sorted(lfmm_geometry_s* g, const cd* v_sorted, cd* z_sorted, cudaStream_t s) {

@@ -7,14 +7,17 @@
 // the precision, the operator: single layer or combined field) queue in arrival
 // order.  `slots` worker threads each drive one CUDA stream; a worker takes the
 // request at the head of the queue as soon as the estimated device footprints of
-// the requests on the GPU plus this one fit the HBM budget, and runs it end to
-// end on its stream: medium, geometry (tree,
-// tables, near field, preconditioner), right-hand side, GMRES, copy of the
-// solution to host memory, release.  Requests that arrive while others run are
-// admitted as slots and memory free up, and their kernels overlap on the device
-// with the others'.  Each request keeps its own geometry and Krylov basis, and
-// every kernel sums in a fixed order, so a result is the same alone and in the
-// mix.
+// the requests on the GPU plus this one fit the HBM budget, and builds it on its
+// stream: medium, geometry (tree, tables, near field, preconditioner), right-hand
+// side.  The solve itself joins the batch engine: one thread that advances every
+// admitted solve by one GMRES step per round (lockstep solves, solver.cu), their FP64
+// operator products in shared launches (one launch per stage for all of them) and one
+// host synchronisation per round; a request joins at the next round after its set-up
+// and leaves when it has converged or stopped.  The worker then copies the solution
+// to host memory and releases the request.  Requests that arrive while others run
+// are admitted as slots and memory free up; set-ups overlap the engine's rounds on
+// the device.  A solve in a batch takes the same steps with the same bits as alone
+// (solver.cu), so a result is the same alone and in the mix.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -30,6 +33,7 @@
 #include <vector>
 
 #include "../../include/lfmm.h"
+#include "geometry.h"
 
 namespace {
 
@@ -54,6 +58,12 @@ struct Request {
     std::string err;
     double t_submit = 0, t_admit = 0, t_done = 0, setup_s = 0;
     bool done = false;
+    // between set-up and finalisation
+    lfmm_medium med = nullptr;
+    lfmm_geometry geo = nullptr;
+    void* db = nullptr;                  // right-hand side (device, input order)
+    lfmm::BatchSolve* bs = nullptr;
+    bool solved = false;                 // the engine is done with it (or it failed)
 };
 
 }  // namespace
@@ -69,6 +79,11 @@ struct lfmm_server_s {
     bool stop = false;
     int device = 0;
     std::vector<std::thread> workers;
+    // the batch engine: solves handed over by the workers, and those it is running
+    std::thread engine;
+    std::condition_variable cv_engine, cv_solved;
+    std::vector<std::shared_ptr<Request>> pending;
+    int workers_left = 0;
 };
 
 namespace {
@@ -83,49 +98,78 @@ int64_t footprint_estimate(int64_t n, int p, int leaf, int max_iter) {
     return (int64_t)(per_point * (double)n + expansions) + ((int64_t)256 << 20);
 }
 
-void run_request(Request& r, cudaStream_t s) {
+// set-up of a request on its worker's stream: medium, geometry, right-hand side, and the
+// solve's state (preconditioner, sorted right-hand side); false on an error (recorded)
+bool setup_request(Request& r, cudaStream_t s) {
     const double t0 = now_s();
-    lfmm_medium med = nullptr;
-    lfmm_geometry geo = nullptr;
-    void *db = nullptr, *dx = nullptr;
     auto fail = [&](lfmm_status st) {
         r.status = st;
         r.err = lfmm_last_error();
+        return false;
     };
-    do {
-        lfmm_status st = lfmm_medium_create(r.n_layers, r.yint.data(), r.k.data(), r.eta.data(), &med);
-        if (st < 0) { fail(st); break; }
-        lfmm_params prm{r.p, r.leaf, r.flags, 0};
-        st = lfmm_geometry_build(med, r.n, r.pts.data(), r.w.data(), r.nrm.empty() ? nullptr : r.nrm.data(), &prm,
-                                 &geo);
-        if (st < 0) { fail(st); break; }
-        r.setup_s = now_s() - t0;
-        if (cudaMallocAsync(&db, 16 * (size_t)r.n, s) != cudaSuccess ||
-            cudaMallocAsync(&dx, 16 * (size_t)r.n, s) != cudaSuccess) {
-            (void)cudaGetLastError();   // not this worker's next request's error
-            r.status = LFMM_ERR_OUT_OF_MEMORY;
-            r.err = "cudaMallocAsync failed for the request's vectors";
-            break;
-        }
-        st = lfmm_rhs_plane_wave(geo, 1, &r.angle, db, LFMM_DEVICE_PTRS, s);
-        if (st < 0) { fail(st); break; }
-        lfmm_gmres_params gp{r.tol, r.max_iter, 0, r.precond, r.precision};
-        st = lfmm_gmres_solve(geo, 1, db, dx, &gp, &r.info, s);
-        if (st < 0) { fail(st); break; }
-        r.status = st;
-        r.x.resize(2 * (size_t)r.n);
-        if (cudaMemcpyAsync(r.x.data(), dx, 16 * (size_t)r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
+    lfmm_status st = lfmm_medium_create(r.n_layers, r.yint.data(), r.k.data(), r.eta.data(), &r.med);
+    if (st < 0) return fail(st);
+    lfmm_params prm{r.p, r.leaf, r.flags, 0};
+    st = lfmm_geometry_build(r.med, r.n, r.pts.data(), r.w.data(), r.nrm.empty() ? nullptr : r.nrm.data(), &prm,
+                             &r.geo);
+    if (st < 0) return fail(st);
+    if (cudaMallocAsync(&r.db, 16 * (size_t)r.n, s) != cudaSuccess) {
+        (void)cudaGetLastError();   // not this worker's next request's error
+        r.db = nullptr;
+        r.status = LFMM_ERR_OUT_OF_MEMORY;
+        r.err = "cudaMallocAsync failed for the request's right-hand side";
+        return false;
+    }
+    st = lfmm_rhs_plane_wave(r.geo, 1, &r.angle, r.db, LFMM_DEVICE_PTRS, s);
+    if (st < 0) return fail(st);
+    st = lfmm::guarded_call([&]() -> lfmm_status {
+        r.bs = lfmm::batch_solve_create(r.geo, (const cd*)r.db, r.tol, r.max_iter, r.precond != 0, r.precision,
+                                        s);
+        return LFMM_OK;
+    });
+    if (st < 0) return fail(st);
+    r.setup_s = now_s() - t0;
+    return true;
+}
+
+// the solution to host memory and the release of everything the request holds
+void finish_request(Request& r, cudaStream_t s) {
+    if (r.bs && r.status >= 0) {
+        void* dx = nullptr;
+        if (cudaMallocAsync(&dx, 16 * (size_t)r.n, s) != cudaSuccess) {
             (void)cudaGetLastError();
-            r.status = LFMM_ERR_CUDA;
-            r.err = "copy of the solution failed";
+            r.status = LFMM_ERR_OUT_OF_MEMORY;
+            r.err = "cudaMallocAsync failed for the request's solution";
+        } else {
+            const lfmm_status st = lfmm::guarded_call([&]() -> lfmm_status {
+                lfmm::batch_solve_finish(r.bs, (cd*)dx, &r.info, s);
+                return LFMM_OK;
+            });
+            if (st < 0) {
+                r.status = st;
+                r.err = lfmm_last_error();
+            } else {
+                r.status = r.info.converged ? LFMM_OK : LFMM_NOT_CONVERGED;
+                r.x.resize(2 * (size_t)r.n);
+                if (cudaMemcpyAsync(r.x.data(), dx, 16 * (size_t)r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    r.status = LFMM_ERR_CUDA;
+                    r.err = "copy of the solution failed";
+                }
+            }
+            cudaFreeAsync(dx, s);
         }
-    } while (false);
-    if (db) cudaFreeAsync(db, s);
-    if (dx) cudaFreeAsync(dx, s);
+    }
+    if (r.bs) lfmm::guarded_call([&]() -> lfmm_status { lfmm::batch_solve_destroy(r.bs, s); return LFMM_OK; });
+    r.bs = nullptr;
+    if (r.db) cudaFreeAsync(r.db, s);
+    r.db = nullptr;
     cudaStreamSynchronize(s);
-    if (geo) lfmm_geometry_destroy(geo);
-    if (med) lfmm_medium_destroy(med);
+    if (r.geo) lfmm_geometry_destroy(r.geo);
+    if (r.med) lfmm_medium_destroy(r.med);
+    r.geo = nullptr;
+    r.med = nullptr;
 }
 
 void worker_main(lfmm_server_s* S) {
@@ -151,7 +195,14 @@ void worker_main(lfmm_server_s* S) {
             r->t_admit = now_s();
         }
         try {
-            run_request(*r, s);
+            if (setup_request(*r, s)) {
+                // hand the solve to the engine and wait for it
+                std::unique_lock<std::mutex> lk(S->mu);
+                S->pending.push_back(r);
+                S->cv_engine.notify_all();
+                S->cv_solved.wait(lk, [&] { return r->solved; });
+            }
+            finish_request(*r, s);
         } catch (const std::bad_alloc&) {   // the host copy of the solution
             r->status = LFMM_ERR_OUT_OF_MEMORY;
             r->err = "host allocation failed";
@@ -167,6 +218,70 @@ void worker_main(lfmm_server_s* S) {
         S->cv_work.notify_all();
     }
     if (s) cudaStreamDestroy(s);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->workers_left -= 1;
+    }
+    S->cv_engine.notify_all();
+}
+
+// The batch engine: every round takes the solves handed over since the last one, then
+// advances all running solves by one GMRES step together.
+void engine_main(lfmm_server_s* S) {
+    cudaSetDevice(S->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    std::vector<std::shared_ptr<Request>> active;
+    bool released = false;
+    auto release = [&](const std::shared_ptr<Request>& r) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->solved = true;
+        released = true;
+    };
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> fresh;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_engine.wait(lk, [&] { return !S->pending.empty() || !active.empty() || S->workers_left == 0; });
+            if (S->pending.empty() && active.empty()) break;   // every worker has stopped
+            fresh.swap(S->pending);
+        }
+        for (auto& r : fresh) {
+            const lfmm_status st = lfmm::guarded_call([&]() -> lfmm_status {
+                lfmm::batch_solve_begin(r->bs, s);
+                return LFMM_OK;
+            });
+            if (st < 0) {
+                r->status = st;
+                r->err = lfmm_last_error();
+                release(r);
+            } else {
+                active.push_back(r);
+            }
+        }
+        std::vector<lfmm::BatchSolve*> round;
+        for (auto& r : active) round.push_back(r->bs);
+        const lfmm_status st = lfmm::guarded_call([&]() -> lfmm_status {
+            lfmm::batch_solve_round(round, s);
+            return LFMM_OK;
+        });
+        std::vector<std::shared_ptr<Request>> keep;
+        for (auto& r : active) {
+            if (st < 0) {   // the round failed: every solve in it reports the error
+                r->status = st;
+                r->err = lfmm_last_error();
+                release(r);
+            } else if (lfmm::batch_solve_done(r->bs)) {
+                release(r);
+            } else {
+                keep.push_back(r);
+            }
+        }
+        if (released) S->cv_solved.notify_all();
+        released = false;
+        active.swap(keep);
+    }
+    if (s) cudaStreamDestroy(s);
 }
 
 }  // namespace
@@ -178,7 +293,9 @@ extern "C" lfmm_status lfmm_server_create(const lfmm_server_params* prm, lfmm_se
     lfmm_server_s* S = new lfmm_server_s();
     S->budget = prm->hbm_budget;
     if (cudaGetDevice(&S->device) != cudaSuccess) { delete S; return LFMM_ERR_CUDA; }
+    S->workers_left = prm->slots;
     for (int i = 0; i < prm->slots; ++i) S->workers.emplace_back(worker_main, S);
+    S->engine = std::thread(engine_main, S);
     *out = S;
     return LFMM_OK;
 }
@@ -273,6 +390,8 @@ extern "C" lfmm_status lfmm_server_destroy(lfmm_server S) {
     }
     S->cv_work.notify_all();
     for (auto& t : S->workers) t.join();
+    S->cv_engine.notify_all();
+    if (S->engine.joinable()) S->engine.join();
     delete S;
     return LFMM_OK;
 }

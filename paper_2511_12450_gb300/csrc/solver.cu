@@ -658,6 +658,299 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
     return all;
 }
 
+// ------------------------------------------------------------------ lockstep solves (serving)
+// The serving loop's batched form: several solves, each of its own geometry with one
+// right-hand side, advanced together, one Krylov step of each per round.  The FP64
+// products of a round share launches (apply_operator_batch_sorted: one launch per stage
+// for all of them); precision-form products stay per geometry.  A solve's passes, Arnoldi
+// steps (CGS2), Givens rotations, stopping tests and refinement are those of gmres_sorted
+// with restart 0 and one column (gmres_one), with the same kernels in the same order, and
+// a shared launch gives each geometry the bits of its own launches, so a solve's result
+// equals the same solve alone, bit for bit.  A round runs on one stream with one host
+// synchronisation for all of its solves.
+struct BatchSolve {
+    typedef std::complex<double> C;
+    lfmm_geometry_s* g = nullptr;
+    int64_t n = 0;
+    double tol = 1e-8;
+    int maxit = 1000, precision = 0;
+    bool pre = true;
+    cd *b = nullptr, *x = nullptr;   // sorted order, owned
+    // the driver (gmres_sorted)
+    bool done = false;
+    int ok = 0, outer = 0, total = 0, f64 = 0, it = 0;
+    double bn = 0, rn = 0, eps = 0, below = 0, res_est = 0;
+    cd *r = nullptr, *d = nullptr, *y2 = nullptr;
+    // the current pass (gmres_one)
+    bool in_pass = false;
+    const cd* prhs = nullptr;
+    cd* pout = nullptr;
+    double beta = 0, res = 1, tol_in = 0, below_in = 0;
+    int cap = 0, msteps = 0;
+    bool mixed_step = false;
+    cd *V = nullptr, *w = nullptr, *z = nullptr, *hd = nullptr;
+    Blas* bl = nullptr;      // Arnoldi results (columns up to maxit + 1)
+    Blas* bo = nullptr;      // norms of the driver
+    cd* hpin = nullptr;      // pinned copy of bl->dres
+    std::vector<std::vector<C>> H;
+    std::vector<C> cs, sn, gg;
+    OpGraph opm;             // the precision-form operator z -> w
+    std::chrono::steady_clock::time_point t0;
+};
+
+BatchSolve* batch_solve_create(lfmm_geometry_s* g, const cd* b_in, double tol, int maxit, bool pre, int precision,
+                               cudaStream_t s) {
+    BatchSolve* S = new BatchSolve();
+    S->g = g;
+    S->n = g->n;
+    S->tol = tol;
+    S->maxit = maxit;
+    S->pre = pre;
+    S->precision = precision;
+    if (pre && !g->pc_ready) precond_build(g);
+    const int64_t n = g->n;
+    cuda_check(cudaMallocAsync((void**)&S->b, sizeof(cd) * n, s), "malloc b");
+    cuda_check(cudaMallocAsync((void**)&S->x, sizeof(cd) * n, s), "malloc x");
+    gather_sorted(g, b_in, S->b, 1, s);
+    cuda_check(cudaStreamSynchronize(s), "batch solve create");
+    return S;
+}
+
+static void bs_pass_start(BatchSolve& S, const cd* rhs, cd* out, double tol_in, double below_in, int cap,
+                          cudaStream_t s) {
+    const int64_t n = S.n;
+    if (!S.V) {   // the largest pass: maxit steps
+        cuda_check(cudaMallocAsync((void**)&S.V, sizeof(cd) * n * (size_t)(S.maxit + 1), s), "malloc V");
+        cuda_check(cudaMallocAsync((void**)&S.w, sizeof(cd) * n, s), "malloc w");
+        cuda_check(cudaMallocAsync((void**)&S.z, sizeof(cd) * n, s), "malloc z");
+        cuda_check(cudaMallocAsync((void**)&S.hd, sizeof(cd) * (S.maxit + 2), s), "malloc h");
+        S.bl = new Blas(S.g, s, S.maxit + 1);
+        cuda_check(cudaMallocHost((void**)&S.hpin, sizeof(cd) * (2 * S.bl->cap + 1)), "pinned h");
+    }
+    S.prhs = rhs;
+    S.pout = out;
+    S.tol_in = tol_in;
+    S.below_in = below_in;
+    S.cap = cap;
+    S.msteps = 0;
+    S.beta = S.bl->norm(rhs, n);
+    cuda_check(cudaMemsetAsync(out, 0, sizeof(cd) * n, s), "memset x");
+    S.H.clear(); S.cs.clear(); S.sn.clear();
+    S.gg.assign(1, BatchSolve::C(S.beta, 0.0));
+    S.res = 1.0;
+    S.in_pass = S.beta != 0.0;
+    if (!S.in_pass) S.res = 0.0;
+    else k_scale<<<nblk(n), 256, 0, s>>>(rhs, 1.0 / S.beta, S.V, n);
+}
+
+// ||(A_mixed - A) v|| / ||A v||, as gmres_sorted measures it
+static double bs_op_diff(BatchSolve& S, const cd* v, cudaStream_t s) {
+    apply_operator_sorted(S.g, v, S.y2, 1, s, true);
+    apply_operator_sorted(S.g, v, S.d, 1, s);
+    const double an = S.bo->norm(S.d, S.n);
+    k_sub_from<<<nblk(S.n), 256, 0, s>>>(S.y2, S.d, S.n);
+    const double dn = S.bo->norm(S.d, S.n);
+    return an > 0.0 ? dn / an : 0.0;
+}
+
+// the next pass of the refinement loop of gmres_sorted (precision 1), or the end
+static void bs_next_or_finish(BatchSolve& S, cudaStream_t s) {
+    const double tol1 = 0.3 * S.tol;
+    if (S.bn > 0.0 && S.rn > S.tol * S.bn && S.total < S.maxit && S.outer < 5) {
+        const double tol_in = (S.outer == 0) ? tol1 : std::min(0.5, 0.5 * S.tol * S.bn / S.rn);
+        const double below_in = (S.outer == 0) ? S.below : S.below * S.bn / S.rn;
+        bs_pass_start(S, S.r, S.d, tol_in, below_in, S.maxit - S.total, s);
+        if (S.in_pass) return;
+        // a zero residual: the pass is empty (as gmres_one with beta = 0)
+    }
+    if (!S.in_pass) {
+        S.it = S.total;
+        S.ok = (S.bn == 0.0 || S.rn <= S.tol * S.bn) ? 1 : 0;
+        S.res_est = S.bn > 0.0 ? S.rn / S.bn : 0.0;
+        S.done = true;
+    }
+}
+
+void batch_solve_begin(BatchSolve* Sp, cudaStream_t s) {
+    BatchSolve& S = *Sp;
+    S.t0 = std::chrono::steady_clock::now();
+    const int64_t n = S.n;
+    cuda_check(cudaMallocAsync((void**)&S.r, sizeof(cd) * n, s), "malloc r");
+    cuda_check(cudaMallocAsync((void**)&S.d, sizeof(cd) * n, s), "malloc d");
+    cuda_check(cudaMallocAsync((void**)&S.y2, sizeof(cd) * n, s), "malloc y2");
+    S.bo = new Blas(S.g, s, 2);
+    S.bn = S.bo->norm(S.b, n);
+    if (S.precision == 0) {
+        bs_pass_start(S, S.b, S.x, S.tol, 0.0, S.maxit, s);
+        if (!S.in_pass) {   // b = 0
+            S.it = 0; S.res_est = 0.0; S.ok = 1;
+            apply_operator_sorted(S.g, S.x, S.r, 1, s);
+            k_sub_from<<<nblk(n), 256, 0, s>>>(S.b, S.r, n);
+            S.rn = S.bo->norm(S.r, n);
+            S.f64 = 1;
+            S.done = true;
+        }
+        return;
+    }
+    S.eps = (S.bn > 0.0) ? std::max(bs_op_diff(S, S.b, s), 1e-300) : 1e-300;
+    S.f64 += 1;
+    S.below = 0.1 * (0.3 * S.tol) / S.eps;
+    cuda_check(cudaMemsetAsync(S.x, 0, sizeof(cd) * n, s), "memset x");
+    cuda_check(cudaMemcpyAsync(S.r, S.b, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s), "r = b");
+    S.rn = S.bn;
+    bs_next_or_finish(S, s);
+}
+
+// end of a pass: the iterate from the Krylov basis (gmres_one's end), then the driver
+static void bs_pass_end(BatchSolve& S, cudaStream_t s) {
+    typedef BatchSolve::C C;
+    const int64_t n = S.n;
+    const int m = (int)S.H.size();
+    std::vector<C> y(m);
+    for (int i = m - 1; i >= 0; --i) {
+        C sacc = S.gg[i];
+        for (int k2 = i + 1; k2 < m; ++k2) sacc -= S.H[k2][i] * y[k2];
+        y[i] = sacc / S.H[i][i];
+    }
+    std::vector<cd> yh(m);
+    for (int i = 0; i < m; ++i) yh[i] = mk(y[i].real(), y[i].imag());
+    cuda_check(cudaMemcpyAsync(S.hd, yh.data(), sizeof(cd) * m, cudaMemcpyHostToDevice, s), "y h2d");
+    if (S.pre) {
+        k_combine<<<nblk(n), 256, 0, s>>>(S.V, m, n, S.hd, S.z, n);
+        precond_apply_sorted(S.g, S.z, S.pout, s);
+    } else {
+        k_combine<<<nblk(n), 256, 0, s>>>(S.V, m, n, S.hd, S.pout, n);
+    }
+    cuda_check(cudaStreamSynchronize(s), "pass end");   // yh is a local host buffer
+    S.in_pass = false;
+    const int its = m;
+    if (S.precision == 0) {
+        S.it = its;
+        S.res_est = S.res;
+        S.ok = S.res <= S.tol ? 1 : 0;
+        apply_operator_sorted(S.g, S.x, S.r, 1, s);
+        k_sub_from<<<nblk(n), 256, 0, s>>>(S.b, S.r, n);
+        S.rn = S.bo->norm(S.r, n);
+        S.f64 = 1;
+        S.done = true;
+        return;
+    }
+    S.total += its;
+    S.f64 += its - S.msteps;
+    k_add<<<nblk(n), 256, 0, s>>>(S.x, S.d, n);
+    apply_operator_sorted(S.g, S.x, S.r, 1, s);
+    k_sub_from<<<nblk(n), 256, 0, s>>>(S.b, S.r, n);
+    ++S.f64;
+    ++S.outer;
+    const double rn_new = S.bo->norm(S.r, n);
+    const bool stalled = rn_new > 0.5 * S.rn;
+    S.rn = rn_new;
+    if (stalled) {
+        S.it = S.total;
+        S.ok = (S.bn == 0.0 || S.rn <= S.tol * S.bn) ? 1 : 0;
+        S.res_est = S.bn > 0.0 ? S.rn / S.bn : 0.0;
+        S.done = true;
+        return;
+    }
+    bs_next_or_finish(S, s);
+}
+
+void batch_solve_round(const std::vector<BatchSolve*>& all, cudaStream_t s) {
+    typedef BatchSolve::C C;
+    std::vector<BatchSolve*> act;
+    for (BatchSolve* S : all)
+        if (!S->done && S->in_pass) act.push_back(S);
+    if (act.empty()) return;
+    // preconditioned directions
+    for (BatchSolve* S : act) {
+        const int j = (int)S->H.size();
+        const cd* vj = S->V + (int64_t)j * S->n;
+        S->mixed_step = S->res <= S->below_in;
+        if (S->mixed_step) ++S->msteps;
+        if (S->pre) precond_apply_sorted(S->g, vj, S->z, s);
+        else cuda_check(cudaMemcpyAsync(S->z, vj, sizeof(cd) * S->n, cudaMemcpyDeviceToDevice, s), "z = v_j");
+    }
+    // products: the FP64 ones in shared launches, the precision form's per geometry
+    std::vector<BatchOp> ops;
+    for (BatchSolve* S : act)
+        if (!S->mixed_step) ops.push_back(BatchOp{S->g, S->z, S->w, 1});
+    apply_operator_batch_sorted(ops, s);
+    for (BatchSolve* S : act)
+        if (S->mixed_step) S->opm.apply(S->g, S->z, S->w, true, s);
+    // Arnoldi steps; one synchronisation for all
+    for (BatchSolve* S : act) {
+        const int j = (int)S->H.size();
+        const int64_t n = S->n;
+        Blas& bl = *S->bl;
+        for (int pass = 0; pass < 2; ++pass) {
+            cd* hp = bl.dres + pass * bl.cap;
+            bl.vh(S->V, j + 1, n, S->w, n, hp);
+            k_update<<<nblk(n), 256, 0, s>>>(S->V, j + 1, n, hp, S->w, n);
+        }
+        bl.vh(S->w, 1, n, S->w, n, bl.dres + 2 * bl.cap);
+        k_scale_by_norm<<<nblk(n), 256, 0, s>>>(S->w, bl.dres + 2 * bl.cap, S->V + (int64_t)(j + 1) * n, n);
+        cuda_check(cudaMemcpyAsync(S->hpin, bl.dres, sizeof(cd) * (2 * bl.cap + 1), cudaMemcpyDeviceToHost, s),
+                   "arnoldi d2h");
+    }
+    cuda_check(cudaStreamSynchronize(s), "round sync");
+    for (BatchSolve* S : act) {
+        const int j = (int)S->H.size();
+        const int capb = S->bl->cap;
+        const cd* hh = S->hpin;
+        std::vector<C> h(j + 2, C(0, 0));
+        for (int c = 0; c <= j; ++c) h[c] = C(hh[c].x, hh[c].y) + C(hh[capb + c].x, hh[capb + c].y);
+        const double hn = std::sqrt(std::max(hh[2 * capb].x, 0.0));
+        h[j + 1] = C(hn, 0.0);
+        for (int i = 0; i < j; ++i) {
+            C t = S->cs[i] * h[i] + S->sn[i] * h[i + 1];
+            h[i + 1] = -std::conj(S->sn[i]) * h[i] + std::conj(S->cs[i]) * h[i + 1];
+            h[i] = t;
+        }
+        C a = h[j], c = h[j + 1];
+        double rr = std::hypot(std::abs(a), std::abs(c));
+        C cj, sj;
+        if (rr == 0) { cj = 1; sj = 0; }
+        else if (std::abs(a) == 0) { cj = 0; sj = std::conj(c) / std::abs(c); }
+        else { cj = std::abs(a) / rr; sj = (a / std::abs(a)) * std::conj(c) / rr; }
+        h[j] = cj * a + sj * c;
+        h[j + 1] = 0;
+        S->cs.push_back(cj); S->sn.push_back(sj);
+        S->gg.push_back(-std::conj(sj) * S->gg[j]);
+        S->gg[j] = cj * S->gg[j];
+        S->H.push_back(h);
+        S->res = std::abs(S->gg[j + 1]) / S->beta;
+        if (S->res <= S->tol_in || hn == 0.0 || (int)S->H.size() >= S->cap) bs_pass_end(*S, s);
+    }
+}
+
+bool batch_solve_done(const BatchSolve* S) { return S->done; }
+
+void batch_solve_finish(BatchSolve* S, cd* x_out, lfmm_gmres_info* info, cudaStream_t s) {
+    scatter_sorted(S->g, S->x, x_out, 1, s);
+    if (info) {
+        info->iterations = S->it;
+        info->converged = S->ok;
+        info->rel_residual = S->res_est;
+        info->true_rel_residual = S->bn > 0 ? S->rn / S->bn : 0.0;
+        info->solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+        info->refinements = S->outer;
+        info->fp64_matvecs = S->f64;
+        info->op_rel_diff = (S->precision == 1 && S->eps >= 1e-299) ? S->eps : 0.0;
+    }
+    cuda_check(cudaStreamSynchronize(s), "batch solve finish");
+}
+
+void batch_solve_destroy(BatchSolve* S, cudaStream_t s) {
+    if (!S) return;
+    for (cd* p : {S->b, S->x, S->r, S->d, S->y2, S->V, S->w, S->z, S->hd})
+        if (p) cudaFreeAsync(p, s);
+    delete S->bl;
+    delete S->bo;
+    cudaStreamSynchronize(s);
+    if (S->hpin) cudaFreeHost(S->hpin);
+    delete S;
+}
+
 // ------------------------------------------------------------------ right-hand side (Sec. 2.2)
 // Background field of a plane wave, by the generalized reflection/transmission
 // recursions of the paper (A_l, B_l after eq. TLhelmholtztotallayer2) written
