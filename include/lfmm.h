@@ -136,7 +136,10 @@ typedef struct {
                            Krylov basis to (m + 1) n complex values per column.  Columns are
                            then solved one after another */
     int32_t precond;    /* 1 = overlapping DD preconditioner (Sec. 4.2, default), 0 = none */
-    int32_t precision;  /* 0 = FP64 operator (default).  1 = relaxed mixed precision:
+    int32_t precision;  /* 0 = FP64 operator (default); if the residual recomputed after
+                           full GMRES misses tol (rounding drift of a long run), refinement
+                           passes on b - K x follow while steps remain.  1 = relaxed mixed
+                           precision:
                            the relative difference eps of the LFMM_MIXED and FP64
                            operators is measured on b; GMRES multiplies by the FP64
                            operator until its residual falls below 0.03 tol / eps and by
@@ -151,8 +154,9 @@ typedef struct {
     double rel_residual;       /* final GMRES residual estimate (max over columns) */
     double true_rel_residual;  /* ||b - K x|| / ||b|| recomputed with lfmm_matvec (max over columns) */
     double solve_seconds;      /* wall time of the solve */
-    int32_t refinements;       /* GMRES passes of the last column: restart cycles and
-                                  refinement steps included (0 for full FP64 GMRES) */
+    int32_t refinements;       /* GMRES passes of the last column after the first: restart
+                                  cycles and refinement steps (full FP64 GMRES: 0, unless the
+                                  recomputed residual missed tol and refinement passes ran) */
     int32_t fp64_matvecs;      /* FP64 operator applications, Krylov steps and residuals
                                   (last column) */
     double op_rel_diff;        /* precision 1: ||(A_mixed - A) b|| / ||A b|| (max over columns),

@@ -581,6 +581,28 @@ int gmres_sorted(lfmm_geometry_s* g, const cd* b, cd* x, int nrhs, double tol, i
             k_sub_from<<<nblk(n), 256, 0, s>>>(bc, r, n);
             rn = bl.norm(r, n);
             f64 = 1;
+            // the estimate reached tol but the recomputed residual did not (rounding drift over a
+            // long Krylov run): refinement passes A d = r, x += d, while steps remain and each
+            // pass at least halves ||r||
+            while (bn > 0.0 && rn > tol * bn && it < maxit && outer < 4) {
+                int its = 0;
+                double rr = 0.0;
+                gmres_one(g, r, d, std::min(0.5, 0.5 * tol * bn / rn), maxit - it, pre, s, &its, &rr);
+                it += its;
+                k_add<<<nblk(n), 256, 0, s>>>(xc, d, n);
+                apply_operator_sorted(g, xc, r, 1, s);
+                k_sub_from<<<nblk(n), 256, 0, s>>>(bc, r, n);
+                ++f64;
+                ++outer;
+                const double rn_new = bl.norm(r, n);
+                const bool stalled = rn_new > 0.5 * rn;
+                rn = rn_new;
+                if (stalled) break;
+            }
+            if (outer > 0) {
+                ok = rn <= tol * bn ? 1 : 0;
+                res = bn > 0.0 ? rn / bn : 0.0;
+            }
         } else if (precision == 0) {
             // GMRES(m): each cycle solves A d = r from a fresh Krylov space of at most m vectors
             cuda_check(cudaMemsetAsync(xc, 0, sizeof(cd) * n, s), "memset x");
@@ -696,6 +718,8 @@ struct BatchSolve {
     std::vector<C> cs, sn, gg;
     OpGraph opm;             // the precision-form operator z -> w
     std::chrono::steady_clock::time_point t0;
+    cudaStream_t st = nullptr;   // the solve's own stream: everything but the shared products
+    cudaEvent_t ev = nullptr;    // its direction z is ready
 };
 
 BatchSolve* batch_solve_create(lfmm_geometry_s* g, const cd* b_in, double tol, int maxit, bool pre, int precision,
@@ -771,9 +795,14 @@ static void bs_next_or_finish(BatchSolve& S, cudaStream_t s) {
     }
 }
 
-void batch_solve_begin(BatchSolve* Sp, cudaStream_t s) {
+void batch_solve_begin(BatchSolve* Sp, cudaStream_t engine) {
     BatchSolve& S = *Sp;
     S.t0 = std::chrono::steady_clock::now();
+    cuda_check(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking), "solve stream");
+    cuda_check(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming), "solve event");
+    cuda_check(cudaEventRecord(S.ev, engine), "event");      // after the set-up seen by the engine
+    cuda_check(cudaStreamWaitEvent(S.st, S.ev, 0), "wait");
+    cudaStream_t s = S.st;
     const int64_t n = S.n;
     cuda_check(cudaMallocAsync((void**)&S.r, sizeof(cd) * n, s), "malloc r");
     cuda_check(cudaMallocAsync((void**)&S.d, sizeof(cd) * n, s), "malloc d");
@@ -825,13 +854,32 @@ static void bs_pass_end(BatchSolve& S, cudaStream_t s) {
     S.in_pass = false;
     const int its = m;
     if (S.precision == 0) {
-        S.it = its;
-        S.res_est = S.res;
-        S.ok = S.res <= S.tol ? 1 : 0;
+        if (S.outer == 0) {   // the first pass solved for x itself
+            S.it = its;
+            S.res_est = S.res;
+            S.ok = S.res <= S.tol ? 1 : 0;
+            S.f64 = 1;
+        } else {              // a refinement pass: x += d
+            S.it += its;
+            k_add<<<nblk(n), 256, 0, s>>>(S.x, S.d, n);
+            ++S.f64;
+        }
         apply_operator_sorted(S.g, S.x, S.r, 1, s);
         k_sub_from<<<nblk(n), 256, 0, s>>>(S.b, S.r, n);
-        S.rn = S.bo->norm(S.r, n);
-        S.f64 = 1;
+        const double rn_new = S.bo->norm(S.r, n);
+        const bool stalled = S.outer > 0 && rn_new > 0.5 * S.rn;
+        S.rn = rn_new;
+        if (S.outer > 0) {
+            S.ok = S.rn <= S.tol * S.bn ? 1 : 0;
+            S.res_est = S.bn > 0.0 ? S.rn / S.bn : 0.0;
+        }
+        // as gmres_sorted: refinement while the recomputed residual misses tol
+        if (!stalled && S.bn > 0.0 && S.rn > S.tol * S.bn && S.it < S.maxit && S.outer < 4) {
+            ++S.outer;
+            bs_pass_start(S, S.r, S.d, std::min(0.5, 0.5 * S.tol * S.bn / S.rn), 0.0, S.maxit - S.it, s);
+            if (S.in_pass) return;
+            --S.outer;
+        }
         S.done = true;
         return;
     }
@@ -861,23 +909,34 @@ void batch_solve_round(const std::vector<BatchSolve*>& all, cudaStream_t s) {
     for (BatchSolve* S : all)
         if (!S->done && S->in_pass) act.push_back(S);
     if (act.empty()) return;
-    // preconditioned directions
+    // preconditioned directions, each on its solve's stream; precision-form products there too
+    std::vector<BatchOp> ops;
     for (BatchSolve* S : act) {
         const int j = (int)S->H.size();
         const cd* vj = S->V + (int64_t)j * S->n;
         S->mixed_step = S->res <= S->below_in;
         if (S->mixed_step) ++S->msteps;
-        if (S->pre) precond_apply_sorted(S->g, vj, S->z, s);
-        else cuda_check(cudaMemcpyAsync(S->z, vj, sizeof(cd) * S->n, cudaMemcpyDeviceToDevice, s), "z = v_j");
+        if (S->pre) precond_apply_sorted(S->g, vj, S->z, S->st);
+        else cuda_check(cudaMemcpyAsync(S->z, vj, sizeof(cd) * S->n, cudaMemcpyDeviceToDevice, S->st), "z = v_j");
+        if (S->mixed_step) {
+            S->opm.apply(S->g, S->z, S->w, true, S->st);
+        } else {
+            cuda_check(cudaEventRecord(S->ev, S->st), "event");
+            cuda_check(cudaStreamWaitEvent(s, S->ev, 0), "wait for z");
+            ops.push_back(BatchOp{S->g, S->z, S->w, 1});
+        }
     }
-    // products: the FP64 ones in shared launches, the precision form's per geometry
-    std::vector<BatchOp> ops;
-    for (BatchSolve* S : act)
-        if (!S->mixed_step) ops.push_back(BatchOp{S->g, S->z, S->w, 1});
-    apply_operator_batch_sorted(ops, s);
-    for (BatchSolve* S : act)
-        if (S->mixed_step) S->opm.apply(S->g, S->z, S->w, true, s);
-    // Arnoldi steps; one synchronisation for all
+    // the FP64 products in shared launches on the engine's stream
+    if (!ops.empty()) {
+        apply_operator_batch_sorted(ops, s);
+        cudaEvent_t done = nullptr;
+        cuda_check(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "event");
+        cuda_check(cudaEventRecord(done, s), "event");
+        for (BatchSolve* S : act)
+            if (!S->mixed_step) cuda_check(cudaStreamWaitEvent(S->st, done, 0), "wait for the products");
+        cudaEventDestroy(done);   // released once the waits above have been satisfied
+    }
+    // Arnoldi steps on each solve's stream, then one wait for all of them
     for (BatchSolve* S : act) {
         const int j = (int)S->H.size();
         const int64_t n = S->n;
@@ -885,14 +944,14 @@ void batch_solve_round(const std::vector<BatchSolve*>& all, cudaStream_t s) {
         for (int pass = 0; pass < 2; ++pass) {
             cd* hp = bl.dres + pass * bl.cap;
             bl.vh(S->V, j + 1, n, S->w, n, hp);
-            k_update<<<nblk(n), 256, 0, s>>>(S->V, j + 1, n, hp, S->w, n);
+            k_update<<<nblk(n), 256, 0, S->st>>>(S->V, j + 1, n, hp, S->w, n);
         }
         bl.vh(S->w, 1, n, S->w, n, bl.dres + 2 * bl.cap);
-        k_scale_by_norm<<<nblk(n), 256, 0, s>>>(S->w, bl.dres + 2 * bl.cap, S->V + (int64_t)(j + 1) * n, n);
-        cuda_check(cudaMemcpyAsync(S->hpin, bl.dres, sizeof(cd) * (2 * bl.cap + 1), cudaMemcpyDeviceToHost, s),
+        k_scale_by_norm<<<nblk(n), 256, 0, S->st>>>(S->w, bl.dres + 2 * bl.cap, S->V + (int64_t)(j + 1) * n, n);
+        cuda_check(cudaMemcpyAsync(S->hpin, bl.dres, sizeof(cd) * (2 * bl.cap + 1), cudaMemcpyDeviceToHost, S->st),
                    "arnoldi d2h");
     }
-    cuda_check(cudaStreamSynchronize(s), "round sync");
+    for (BatchSolve* S : act) cuda_check(cudaStreamSynchronize(S->st), "round sync");
     for (BatchSolve* S : act) {
         const int j = (int)S->H.size();
         const int capb = S->bl->cap;
@@ -919,13 +978,14 @@ void batch_solve_round(const std::vector<BatchSolve*>& all, cudaStream_t s) {
         S->gg[j] = cj * S->gg[j];
         S->H.push_back(h);
         S->res = std::abs(S->gg[j + 1]) / S->beta;
-        if (S->res <= S->tol_in || hn == 0.0 || (int)S->H.size() >= S->cap) bs_pass_end(*S, s);
+        if (S->res <= S->tol_in || hn == 0.0 || (int)S->H.size() >= S->cap) bs_pass_end(*S, S->st);
     }
 }
 
 bool batch_solve_done(const BatchSolve* S) { return S->done; }
 
 void batch_solve_finish(BatchSolve* S, cd* x_out, lfmm_gmres_info* info, cudaStream_t s) {
+    if (S->st) cuda_check(cudaStreamSynchronize(S->st), "solve stream");
     scatter_sorted(S->g, S->x, x_out, 1, s);
     if (info) {
         info->iterations = S->it;
@@ -942,12 +1002,16 @@ void batch_solve_finish(BatchSolve* S, cd* x_out, lfmm_gmres_info* info, cudaStr
 
 void batch_solve_destroy(BatchSolve* S, cudaStream_t s) {
     if (!S) return;
+    if (S->st) cudaStreamSynchronize(S->st);
     for (cd* p : {S->b, S->x, S->r, S->d, S->y2, S->V, S->w, S->z, S->hd})
         if (p) cudaFreeAsync(p, s);
-    delete S->bl;
+    delete S->bl;   // frees on the solve's stream
     delete S->bo;
+    if (S->st) cudaStreamSynchronize(S->st);
     cudaStreamSynchronize(s);
     if (S->hpin) cudaFreeHost(S->hpin);
+    if (S->ev) cudaEventDestroy(S->ev);
+    if (S->st) cudaStreamDestroy(S->st);
     delete S;
 }
 
