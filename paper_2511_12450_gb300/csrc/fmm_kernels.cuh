@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts
 // same (k_S = k_T, so u = v on every node): I_{mn} = h_{n-m} with
 // h_d = sum_q (Fp_q u_q^d + Fm_q u_q^-d), d = -2p..2p -- 4p+1 moments per key
 // instead of (2p+1)^2.  One CTA per key; the table is then written out dense.  The
-// weights are folded into the power rows, each run of 16 starting from F u^d0 formed
+// weights are folded into the power rows, each run of 32 starting from F u^d0 formed
 // with a separate exponent (xpow_times): far along the rays u^d alone leaves the double
 // range (|u| ~ 2 lambda / k) where F u^d does not, and F = 0 there must not meet u^d = inf.
 #define TAB_SAME_CH 8
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
     double h;
     const int P = table_panels(q, K.X, K.D, &h) * q.tab_panel_mult + 2 * p;
     const int ntot = P * 8 + 2 * q.tab_nes;
-    const int nseg = (nd + 15) / 16;   // runs of 16 consecutive powers per node and side
+    const int nseg = (nd + 31) / 32;   // runs of 32 consecutive powers per node and side
     cd acc[2] = {mk(0, 0), mk(0, 0)};   // d = threadIdx.x and threadIdx.x + 256
     for (int jb = 0; jb < ntot; jb += NB) {
         const int cntB = min(NB, ntot - jb);
@@ -408,15 +408,15 @@ __global__ void __launch_bounds__(256) k_react_tables_same(MediumDev med, QuadRu
         for (int j0 = 0; j0 < cntB; j0 += CH) {
             const int cnt = min(CH, cntB - j0);
             __syncthreads();
-            // one thread per run of 16: its first value F u^e0 on scaled values, then 15 products
+            // one thread per run of 32: its first value F u^e0 on scaled values, then 31 products
             for (int e = threadIdx.x; e < cnt * 2 * nseg; e += blockDim.x) {
-                const int r = e / (2 * nseg), w = e - r * 2 * nseg, side = w / nseg, d0 = (w - side * nseg) * 16;
+                const int r = e / (2 * nseg), w = e - r * 2 * nseg, side = w / nseg, d0 = (w - side * nseg) * 32;
                 const cd u = uu[j0 + r];
                 const int e0 = side == 0 ? d0 - 2 * p : 2 * p - d0;
                 cd cur = xval(xpow_times(side == 0 ? Fp[j0 + r] : Fm[j0 + r], u, e0));
                 const cd step = side == 0 ? u : cinv(u);
                 cd* row = (side == 0 ? Pp : Pm) + r * nd;
-                const int d1 = min(nd, d0 + 16);
+                const int d1 = min(nd, d0 + 32);
                 for (int d = d0; d < d1; ++d) { row[d] = cur; cur = cur * step; }
             }
             __syncthreads();
