@@ -661,7 +661,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         const int nd = g->up_end[lp] - g->up_begin[lp];
         if (nd == 0) continue;
         const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco);
-        dim3 grid(nd, (nco + w - 1) / w);
+        dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
         k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nrhs, g->ncoef,
                                          g->nslotcoef, g->d_M, g->d_Mp);
         cuda_check(cudaGetLastError(), "k_translate (M2M)");
@@ -692,7 +692,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         // into the FP32 locals, which the FP32 M2L has written
         const int acc = (l == lm) ? 0 : 1;
         const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco);
-        dim3 grid(nd, (nco + w - 1) / w);
+        dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
         k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, acc, w, nrhs, g->ncoef,
                                          g->nslotcoef, g->d_L, g->d_Lp);
         cuda_check(cudaGetLastError(), "k_translate (L2L)");
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(128) k_translate_multi(const XJob* __restrict_
     const int j = job_of(prefix, njobs, blockIdx.x);
     const XJob& J = jobs[j];
     const int b = blockIdx.x - prefix[j];
-    translate_dst(b / J.nchunk, b % J.nchunk, J.dsts, J.srcs, J.vec, J.accumulate, J.w, J.nrhs, J.ncoef, J.nslotcoef,
+    translate_dst(b / J.nchunk, b % J.nchunk, J.dsts, J.srcs, J.vec, J.accumulate, J.w, 0, J.nrhs, J.ncoef, J.nslotcoef,
                   J.X, J.Xp);
 }
 __global__ void __launch_bounds__(128) k_m2l_multi(const M2LJob* __restrict__ jobs, const int* __restrict__ prefix,

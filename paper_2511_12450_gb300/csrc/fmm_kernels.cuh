@@ -322,8 +322,8 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
 // handful of SMs.
 __device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __restrict__ dsts,
                                               const XSrc* __restrict__ srcs, const cd* __restrict__ vec,
-                                              int accumulate, int w, int nrhs, int64_t ncoef, int64_t nslotcoef,
-                                              cd* X, cd* Xp) {
+                                              int accumulate, int w, int col0, int col1, int64_t ncoef,
+                                              int64_t nslotcoef, cd* X, cd* Xp) {
     __shared__ cd red[128];
     const XDst d = dsts[di];
     const int ns = 128 / w;
@@ -331,7 +331,7 @@ __device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __r
     const int idx = chunk * w + lane;
     const int ncD = 2 * d.p + 1;
     const bool live = sl < ns && idx < ncD;
-    for (int col = 0; col < nrhs; ++col) {
+    for (int col = col0; col < col1; ++col) {
         cd a = mk(0, 0);
         if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
@@ -358,7 +358,10 @@ __device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __r
 __global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
                                                    const cd* __restrict__ vec, int accumulate, int w, int nrhs,
                                                    int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
-    translate_dst(blockIdx.x, blockIdx.y, dsts, srcs, vec, accumulate, w, nrhs, ncoef, nslotcoef, X, Xp);
+    // blockIdx.z: a group of columns (the columns of a block right-hand side split over CTAs)
+    const int cpb = (nrhs + gridDim.z - 1) / gridDim.z;
+    const int col0 = blockIdx.z * cpb, col1 = min(nrhs, col0 + cpb);
+    translate_dst(blockIdx.x, blockIdx.y, dsts, srcs, vec, accumulate, w, col0, col1, ncoef, nslotcoef, X, Xp);
 }
 
 // Reaction M2L moment tables of components whose source and field layers are the

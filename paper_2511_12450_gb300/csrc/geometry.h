@@ -84,6 +84,9 @@ struct M2LItem {
     int part;         // -1: write L directly; else partial-sum slot (always XT_W lanes)
     int w;            // output lanes per row: XT_W (chunks of XT_W coefficients) or 2p+1 (all of them)
 };
+// CTAs a block right-hand side's columns are split over in the translation and double-float
+// M2L kernels (groups of four columns); one column keeps one CTA
+inline int col_groups(int nrhs) { return nrhs <= 2 ? 1 : (nrhs + 3) / 4; }
 // Lanes per output row for nco coefficients on a 128-thread CTA: chunks of XT_W
 // lanes (8 slices of the sum), or one lane per coefficient with 128 / nco slices,
 // whichever keeps more threads on an output (41 of 48 vs 123 of 128 at p = 20).

@@ -476,7 +476,9 @@ __global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ ds
     const int idx = blockIdx.y * w + lane;
     const int ncD = 2 * d.p + 1;
     const bool live = sl < ns && idx < ncD;
-    for (int col = 0; col < nrhs; ++col) {
+    const int cpb = (nrhs + gridDim.z - 1) / gridDim.z;   // blockIdx.z: a group of columns
+    const int col0 = blockIdx.z * cpb, col1 = min(nrhs, col0 + cpb);
+    for (int col = col0; col < col1; ++col) {
         cf a = mkf(0, 0);
         if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
@@ -526,6 +528,28 @@ __global__ void k_xtab32(const XDst* __restrict__ dsts, const XSrc* __restrict__
 }
 
 // L~ (FP32) += L (FP64) / ispow over a coefficient range
+// the same over a coefficient range [c0, c0 + n) of every column (leading dimension ld): one
+// launch for all columns
+__global__ void k_from32_cols(const cf* __restrict__ in, const double* __restrict__ ispow, int64_t c0, int64_t n,
+                              int nrhs, int64_t ld, cd* __restrict__ out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t / n, i = c0 + (t - col * n);
+        const double f = 1.0 / ispow[i];   // multipoles: M = M~ s^|m|
+        const cf v = in[col * ld + i];
+        out[col * ld + i] = mk(f * (double)v.x, f * (double)v.y);
+    }
+}
+__global__ void k_add_to32_cols(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t c0, int64_t n,
+                                int nrhs, int64_t ld, cf* __restrict__ out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t / n, i = c0 + (t - col * n);
+        const double f = 1.0 / ispow[i];
+        const cd v = in[col * ld + i];
+        out[col * ld + i] = addf(out[col * ld + i], mkf((float)(f * v.x), (float)(f * v.y)));
+    }
+}
 __global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t n,
                            cf* __restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -685,7 +709,9 @@ __global__ void __launch_bounds__(128) k_m2l_df(const M2LItem* __restrict__ item
     const int nn = idx - p;
     const int sg = nn >= 0 ? 1 : -1;
     const double isp = live ? ispow[coef_off[T] + idx] : 0.0;   // s^-|n| of the target box
-    for (int col = 0; col < nrhs; ++col) {
+    const int cpb = (nrhs + gridDim.y - 1) / gridDim.y;   // blockIdx.y: a group of columns
+    const int col0 = blockIdx.y * cpb, col1 = min(nrhs, col0 + cpb);
+    for (int col = col0; col < col1; ++col) {
         const dfc* Msc = Ms + (int64_t)col * ncd - c0 + p;    // [E.src + m] is M~_m of the source box
         const dfc* Muc = Mu + (int64_t)col * ncd - c0 + p;
         const dfc* Mpc = Mps + (int64_t)col * nsd - s0;
@@ -1072,7 +1098,7 @@ static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate
     // FP32 translations are not bound by an arithmetic pipe: 16-lane chunks (more CTAs)
     // measured faster here than rows as wide as the coefficient count
     const int nco = 2 * p_dst + 1, w = XT_W;
-    dim3 grid(nd, (nco + w - 1) / w);
+    dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
     k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, w,
                                        nrhs, g->ncoef, g->nslotcoef, X, Xp);
     cuda_check(cudaGetLastError(), "k_translate32");
@@ -1092,40 +1118,38 @@ void mixed_m_to64(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
     MixedState* ms = g->mixed;
     int64_t c0, c1, s0, s1;
     level_ranges(g, l, &c0, &c1, &s0, &s1);
-    for (int col = 0; col < nrhs; ++col) {
-        if (c1 > c0) {
-            k_from32<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(ms->M + col * g->ncoef + c0, ms->ispow + c0,
-                                                                       c1 - c0, 1, g->d_M + col * g->ncoef + c0, 1);
-            ++g->n_launches;
-        }
-        if (s1 > s0) {
-            k_from32<<<(unsigned)((s1 - s0 + 255) / 256), 256, 0, s>>>(ms->Mp + col * g->nslotcoef + s0,
-                                                                       ms->ispow_slot + s0, s1 - s0, 1,
-                                                                       g->d_Mp + col * g->nslotcoef + s0, 1);
-            ++g->n_launches;
-        }
+    if (c1 > c0) {
+        const int64_t n = (c1 - c0) * nrhs;
+        k_from32_cols<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            ms->M, ms->ispow, c0, c1 - c0, nrhs, g->ncoef, g->d_M);
+        ++g->n_launches;
     }
-    cuda_check(cudaGetLastError(), "k_from32 (multipoles)");
+    if (s1 > s0) {
+        const int64_t n = (s1 - s0) * nrhs;
+        k_from32_cols<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            ms->Mp, ms->ispow_slot, s0, s1 - s0, nrhs, g->nslotcoef, g->d_Mp);
+        ++g->n_launches;
+    }
+    cuda_check(cudaGetLastError(), "k_from32_cols");
 }
 
 void mixed_l_add(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
     MixedState* ms = g->mixed;
     int64_t c0, c1, s0, s1;
     level_ranges(g, l, &c0, &c1, &s0, &s1);
-    for (int col = 0; col < nrhs; ++col) {
-        if (c1 > c0) {
-            k_add_to32<<<(unsigned)((c1 - c0 + 255) / 256), 256, 0, s>>>(g->d_L + col * g->ncoef + c0, ms->ispow + c0,
-                                                                         c1 - c0, ms->L + col * g->ncoef + c0);
-            ++g->n_launches;
-        }
-        if (s1 > s0) {
-            k_add_to32<<<(unsigned)((s1 - s0 + 255) / 256), 256, 0, s>>>(g->d_Lp + col * g->nslotcoef + s0,
-                                                                         ms->ispow_slot + s0, s1 - s0,
-                                                                         ms->Lp + col * g->nslotcoef + s0);
-            ++g->n_launches;
-        }
+    if (c1 > c0) {
+        const int64_t n = (c1 - c0) * nrhs;
+        k_add_to32_cols<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            g->d_L, ms->ispow, c0, c1 - c0, nrhs, g->ncoef, ms->L);
+        ++g->n_launches;
     }
-    cuda_check(cudaGetLastError(), "k_add_to32");
+    if (s1 > s0) {
+        const int64_t n = (s1 - s0) * nrhs;
+        k_add_to32_cols<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            g->d_Lp, ms->ispow_slot, s0, s1 - s0, nrhs, g->nslotcoef, ms->Lp);
+        ++g->n_launches;
+    }
+    cuda_check(cudaGetLastError(), "k_add_to32_cols");
 }
 
 void mixed_l2p(lfmm_geometry_s* g, cd* y_sorted, int nrhs, cudaStream_t s) {
@@ -1231,7 +1255,7 @@ void mixed_m2l_coarse(lfmm_geometry_s* g, int nrhs, int n_items, cudaStream_t s)
         ++g->n_launches;
     }
     cuda_check(cudaGetLastError(), "k_m_to_df");
-    k_m2l_df<<<n_items, 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
+    k_m2l_df<<<dim3(n_items, col_groups(nrhs)), 128, 0, s>>>(g->d_m2l_items, g->d_m2l_ents, g->d_box_level, g->d_p_level, g->d_coef_off,
                                      g->d_slot_of, g->d_slot_coef, ms->ftab_df,
                                      ms->ftab_df + std::max<int64_t>(g->m2lf_len, 1), g->d_m2lf_off, ms->rtab_df,
                                      ms->rtab_rsc, ms->ispow, nrhs, g->ncoef, g->nslotcoef, g->n_m2l_parts, ms->Mdf, ms->Mudf,
