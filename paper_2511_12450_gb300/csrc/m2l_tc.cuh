@@ -9,7 +9,9 @@
 // and arrival flips and the mirror symmetry folded in) and X_S the (2p+1) x ncols
 // block of the source's scaled multipoles.  Complex products in real form,
 //   [Re Y; Im Y] = [[Ar, -Ai], [Ai, Ar]] [Re X; Im X],
-// so one MMA has M = 128 >= 2(2p+1) rows, K = 2(2p+1) padded to a multiple of 8,
+// so one MMA has M = 128 >= 2(2p+1) rows, K = 2 kh padded to a multiple of 8 (the real
+// part's columns from K = 0, the imaginary part's from kh = 2p+1 rounded up to 4, so that
+// staging writes 16-byte row segments),
 // and N = the columns padded to a multiple of 16 (at most TC_MAXN per launch).
 // Every operand is split into a TF32 head and an FP32 tail, and the three
 // products head.head + head.tail + tail.head (3xTF32) keep the FP32 accuracy of
@@ -133,30 +135,42 @@ __global__ void __launch_bounds__(128) k_m2l32_tc(
     bool ok = true;
     for (int e = e0; e < e1 && ok; ++e) {
         const M2LEnt E = ents[e];
-        for (int q = tid; q < nco * nco; q += 128) {
-            const int i = q % nco, j = q / nco;
-            const cf a = tc_entry_value(E, i, j, p, nco, ftab, ftab_off, rtab);
-            float rh, rl, ih, il;
-            tc_split(a.x, rh, rl);
-            tc_split(a.y, ih, il);
-            sAh[tc_canon(i, j, kp)] = rh;           sAl[tc_canon(i, j, kp)] = rl;
-            sAh[tc_canon(i, j + nco, kp)] = -ih;    sAl[tc_canon(i, j + nco, kp)] = -il;
-            sAh[tc_canon(i + nco, j, kp)] = ih;     sAl[tc_canon(i + nco, j, kp)] = il;
-            sAh[tc_canon(i + nco, j + nco, kp)] = rh; sAl[tc_canon(i + nco, j + nco, kp)] = rl;
+        // four consecutive K positions per store (one 16-byte row segment of a core matrix):
+        // the real part's columns start at K = 0, the imaginary part's at K = kh (a multiple of
+        // four), the positions between nco and kh are written as zeros
+        const int kh = (nco + 3) & ~3, nq = kh >> 2;
+        for (int q = tid; q < nco * nq; q += 128) {
+            const int i = q % nco, j0 = (q / nco) * 4;
+            float4 arh, arl, aih, ail;
+            float* f[4] = {&arh.x, &arl.x, &aih.x, &ail.x};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const cf a = (j0 + t < nco) ? tc_entry_value(E, i, j0 + t, p, nco, ftab, ftab_off, rtab) : mkf(0.f, 0.f);
+                tc_split(a.x, f[0][t], f[1][t]);
+                tc_split(a.y, f[2][t], f[3][t]);
+            }
+            const float4 naih = make_float4(-aih.x, -aih.y, -aih.z, -aih.w);
+            const float4 nail = make_float4(-ail.x, -ail.y, -ail.z, -ail.w);
+            *(float4*)&sAh[tc_canon(i, j0, kp)] = arh;            *(float4*)&sAl[tc_canon(i, j0, kp)] = arl;
+            *(float4*)&sAh[tc_canon(i, kh + j0, kp)] = naih;      *(float4*)&sAl[tc_canon(i, kh + j0, kp)] = nail;
+            *(float4*)&sAh[tc_canon(i + nco, j0, kp)] = aih;      *(float4*)&sAl[tc_canon(i + nco, j0, kp)] = ail;
+            *(float4*)&sAh[tc_canon(i + nco, kh + j0, kp)] = arh; *(float4*)&sAl[tc_canon(i + nco, kh + j0, kp)] = arl;
         }
         const bool from_slot = (E.flags & M2L_REACT) && (E.flags & M2L_SRC_SLOT);
         const cf* src = (from_slot ? Mp : Min) + E.src;
         const int64_t stride = from_slot ? nslotcoef : ncoef;
-        for (int q = tid; q < ncols * nco; q += 128) {
-            const int j = q % nco, c = q / nco;
-            const cf v = src[(int64_t)(col0 + c) * stride + j];
-            float h, l;
-            tc_split(v.x, h, l);
-            sBh[tc_canon(c, j, kp)] = h;
-            sBl[tc_canon(c, j, kp)] = l;
-            tc_split(v.y, h, l);
-            sBh[tc_canon(c, j + nco, kp)] = h;
-            sBl[tc_canon(c, j + nco, kp)] = l;
+        for (int q = tid; q < ncols * nq; q += 128) {
+            const int jq = q % nq, c = q / nq, j0 = jq * 4;
+            float4 xrh, xrl, xih, xil;
+            float* f[4] = {&xrh.x, &xrl.x, &xih.x, &xil.x};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const cf v = (j0 + t < nco) ? src[(int64_t)(col0 + c) * stride + j0 + t] : mkf(0.f, 0.f);
+                tc_split(v.x, f[0][t], f[1][t]);
+                tc_split(v.y, f[2][t], f[3][t]);
+            }
+            *(float4*)&sBh[tc_canon(c, j0, kp)] = xrh;       *(float4*)&sBl[tc_canon(c, j0, kp)] = xrl;
+            *(float4*)&sBh[tc_canon(c, kh + j0, kp)] = xih;  *(float4*)&sBl[tc_canon(c, kh + j0, kp)] = xil;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");

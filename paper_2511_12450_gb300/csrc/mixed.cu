@@ -1178,7 +1178,8 @@ static bool m2l_tc(lfmm_geometry_s* g, int nrhs, int min_level, cudaStream_t s) 
     if (nrhs < TC_MIN_COLS || g->m2l_simt || ms->n_tc_boxes == 0 || 2 * nco > 128 || min_level != ms->lm)
         return false;
     mixed_check_waits(g);
-    const int kp = (2 * nco + 7) / 8 * 8;
+    // K: real part at 0, imaginary part at kh = nco rounded up to 4 (16-byte stores), padded to 8
+    const int kp = (2 * ((nco + 3) / 4 * 4) + 7) / 8 * 8;
     for (int c0 = 0; c0 < nrhs; c0 += TC_MAXN) {
         const int nc = std::min(TC_MAXN, nrhs - c0);
         const int np = nc <= 16 ? 16 : 32;
