@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--serve-full", type=int, default=0,
                     help="run only the serving form on this many requests drawn like the serving "
                          "configuration itself (N up to 262,144, up to 512 bodies) and print it as one JSON line")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="only the block right-hand side of one batching geometry (32 angles) and print it")
     ap.add_argument("--only-c3", action="store_true",
                     help="run only the million-point four-layer workload block (--steps timed matvecs per operator) "
                          "and print it as one JSON line")
@@ -865,6 +867,14 @@ def main():
 
         print(json.dumps({"serve": run_serving(lfmm, n_requests=args.serve_full, n_max=262144.0, max_bodies=512),
                           "data": "synthetic", "dtype": "f64"}))
+        return 0
+    if args.only_batch:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2511_12450_gb300 import lfmm
+
+        print(json.dumps({"batch": run_batch(lfmm, steps=args.steps), "data": "synthetic", "dtype": "f64"}))
         return 0
     if args.only_c3:
         import torch

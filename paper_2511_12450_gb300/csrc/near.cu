@@ -145,28 +145,48 @@ __device__ __forceinline__ void near_fma(float2& acc, const float2& v, const flo
     acc.y = fmaf(v.y, x.x, acc.y);
 }
 
-// acc += sum over the columns [ca, cb) of the leaf's matrix taken by this lane group
-template <typename V, typename X, typename A>
+// acc[q] += sum over the columns [ca, cb) of the leaf's matrix taken by this lane group, for
+// the right-hand sides q < ncb (x + q n): each stored entry is read once for all of them, and
+// every right-hand side's sum runs in the order of the single-column sum (four partial sums)
+template <int CB, typename V, typename X, typename A>
 __device__ __forceinline__ void near_row_sum(const V* __restrict__ val, const NearRowPart& P, int leaf, int nT, int i,
-                                             int g, int G, int ca, int cb, const X* __restrict__ x, A& acc) {
+                                             int g, int G, int ca, int cb, const X* __restrict__ x, int64_t n,
+                                             int ncb, A (&acc)[CB]) {
     const int c0 = P.jptr[leaf];
     const V* v = val + P.off[leaf] + i;
-    A a1{}, a2{}, a3{};
+    A a1[CB], a2[CB], a3[CB];
+#pragma unroll
+    for (int q = 0; q < CB; ++q) { a1[q] = A{}; a2[q] = A{}; a3[q] = A{}; }
     int c = ca + g;
     // four columns in flight per lane
     for (; c + 3 * G < cb; c += 4 * G) {
         const V v0 = v[(int64_t)(c - c0) * nT], v1 = v[(int64_t)(c + G - c0) * nT];
         const V v2 = v[(int64_t)(c + 2 * G - c0) * nT], v3 = v[(int64_t)(c + 3 * G - c0) * nT];
-        const X x0 = x[P.j[c]], x1 = x[P.j[c + G]], x2 = x[P.j[c + 2 * G]], x3 = x[P.j[c + 3 * G]];
-        near_fma(acc, v0, x0);
-        near_fma(a1, v1, x1);
-        near_fma(a2, v2, x2);
-        near_fma(a3, v3, x3);
+        const int j0 = P.j[c], j1 = P.j[c + G], j2 = P.j[c + 2 * G], j3 = P.j[c + 3 * G];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+            if (q < ncb) {
+                const X* xq = x + q * n;
+                near_fma(acc[q], v0, xq[j0]);
+                near_fma(a1[q], v1, xq[j1]);
+                near_fma(a2[q], v2, xq[j2]);
+                near_fma(a3[q], v3, xq[j3]);
+            }
+        }
     }
-    for (; c < cb; c += G) near_fma(acc, v[(int64_t)(c - c0) * nT], x[P.j[c]]);
-    acc.x += a1.x; acc.y += a1.y;
-    a2.x += a3.x; a2.y += a3.y;
-    acc.x += a2.x; acc.y += a2.y;
+    for (; c < cb; c += G) {
+        const V vc = v[(int64_t)(c - c0) * nT];
+        const int jc = P.j[c];
+#pragma unroll
+        for (int q = 0; q < CB; ++q)
+            if (q < ncb) near_fma(acc[q], vc, x[q * n + jc]);
+    }
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+        acc[q].x += a1[q].x; acc[q].y += a1[q].y;
+        a2[q].x += a3[q].x; a2[q].y += a3[q].y;
+        acc[q].x += a2[q].x; acc[q].y += a2[q].y;
+    }
 }
 template <int NW>
 __device__ __forceinline__ void share(const NearRowPart& P, int leaf, int w, int* ca, int* cb) {
@@ -182,7 +202,7 @@ __device__ __forceinline__ void share(const NearRowPart& P, int leaf, int w, int
 // keeps four times as many leaves in flight per SM and needs no barrier.  In the precision
 // form the FP32 part is reduced in FP32 and converted once per row, and the FP64 part is
 // skipped for the leaves without reaction columns.
-template <bool MIX, int NW>
+template <bool MIX, int NW, int CB>
 __device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __restrict__ box_begin,
                                               const int* __restrict__ box_end, const NearRowPart& P64,
                                               const cd* __restrict__ val64, const NearRowPart& P32,
@@ -197,79 +217,89 @@ __device__ __forceinline__ void near_leaf_cta(int leaf, int leaf0, const int* __
     int a64, b64, a32 = 0, b32 = 0;
     share<NW>(P64, leaf, w, &a64, &b64);
     if (MIX) share<NW>(P32, leaf, w, &a32, &b32);
-    for (int col = 0; col < nrhs; ++col) {
-        const cd* xc = x + (int64_t)col * n;
+    for (int col0 = 0; col0 < nrhs; col0 += CB) {   // CB right-hand sides per pass over the entries
+        const int ncb = min(CB, nrhs - col0);
         for (int i0 = 0; i0 < nT; i0 += 32) {
             const int r = min(32, nT - i0), G = 32 / r;
             const int i = i0 + lane % r, g = lane / r;
-            cd acc = mk(0.0, 0.0);
-            float2 s32 = make_float2(0.f, 0.f);
+            cd acc[CB];
+            float2 s32[CB];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) { acc[q] = mk(0.0, 0.0); s32[q] = make_float2(0.f, 0.f); }
             if (g < G) {
-                if (has64) near_row_sum(val64, P64, leaf, nT, i, g, G, a64, b64, xc, acc);
-                if (MIX) near_row_sum(val32, P32, leaf, nT, i, g, G, a32, b32, x32 + (int64_t)col * n, s32);
+                if (has64) near_row_sum<CB>(val64, P64, leaf, nT, i, g, G, a64, b64, x + (int64_t)col0 * n, n, ncb, acc);
+                if (MIX)
+                    near_row_sum<CB>(val32, P32, leaf, nT, i, g, G, a32, b32, x32 + (int64_t)col0 * n, n, ncb, s32);
             }
-            for (int gg = 1; gg < G; ++gg) {
-                const int src = (lane + gg * r) & 31;
-                if (has64) {
-                    const double ox = __shfl_sync(0xffffffffu, acc.x, src);
-                    const double oy = __shfl_sync(0xffffffffu, acc.y, src);
-                    if (lane < r) { acc.x += ox; acc.y += oy; }
-                }
-                if (MIX) {
-                    const float ox = __shfl_sync(0xffffffffu, s32.x, src);
-                    const float oy = __shfl_sync(0xffffffffu, s32.y, src);
-                    if (lane < r) { s32.x += ox; s32.y += oy; }
-                }
-            }
-            if (NW == 1) {   // one warp per leaf: no exchange between warps
-                if (lane < r) {
-                    cd t = has64 ? acc : mk(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < CB; ++q) {
+                if (q >= ncb) break;
+                const int col = col0 + q;
+                const cd* xc = x + (int64_t)col * n;
+                for (int gg = 1; gg < G; ++gg) {
+                    const int src = (lane + gg * r) & 31;
+                    if (has64) {
+                        const double ox = __shfl_sync(0xffffffffu, acc[q].x, src);
+                        const double oy = __shfl_sync(0xffffffffu, acc[q].y, src);
+                        if (lane < r) { acc[q].x += ox; acc[q].y += oy; }
+                    }
                     if (MIX) {
-                        t.x += (double)s32.x;
-                        t.y += (double)s32.y;
+                        const float ox = __shfl_sync(0xffffffffu, s32[q].x, src);
+                        const float oy = __shfl_sync(0xffffffffu, s32[q].y, src);
+                        if (lane < r) { s32[q].x += ox; s32[q].y += oy; }
+                    }
+                }
+                if (NW == 1) {   // one warp per leaf: no exchange between warps
+                    if (lane < r) {
+                        cd t = has64 ? acc[q] : mk(0.0, 0.0);
+                        if (MIX) {
+                            t.x += (double)s32[q].x;
+                            t.y += (double)s32[q].y;
+                            cfma(t, diag[tb + i], xc[tb + i]);
+                        }
+                        y[(int64_t)col * n + tb + i] += t;
+                    }
+                    continue;
+                }
+                if (lane < r) {
+                    if (has64) part[w][lane] = acc[q];
+                    if (MIX) part32[w][lane] = s32[q];
+                }
+                __syncthreads();
+                if (w == 0 && lane < r) {
+                    cd t = mk(0.0, 0.0);
+                    if (has64) {
+                        t = part[0][lane];
+                        for (int k = 1; k < NW; ++k) t += part[k][lane];
+                    }
+                    if (MIX) {
+                        float2 u = part32[0][lane];
+                        for (int k = 1; k < NW; ++k) { u.x += part32[k][lane].x; u.y += part32[k][lane].y; }
+                        t.x += (double)u.x;
+                        t.y += (double)u.y;
                         cfma(t, diag[tb + i], xc[tb + i]);
                     }
                     y[(int64_t)col * n + tb + i] += t;
                 }
-                continue;
+                __syncthreads();
             }
-            if (lane < r) {
-                if (has64) part[w][lane] = acc;
-                if (MIX) part32[w][lane] = s32;
-            }
-            __syncthreads();
-            if (w == 0 && lane < r) {
-                cd t = mk(0.0, 0.0);
-                if (has64) {
-                    t = part[0][lane];
-                    for (int q = 1; q < NW; ++q) t += part[q][lane];
-                }
-                if (MIX) {
-                    float2 u = part32[0][lane];
-                    for (int q = 1; q < NW; ++q) { u.x += part32[q][lane].x; u.y += part32[q][lane].y; }
-                    t.x += (double)u.x;
-                    t.y += (double)u.y;
-                    cfma(t, diag[tb + i], xc[tb + i]);
-                }
-                y[(int64_t)col * n + tb + i] += t;
-            }
-            __syncthreads();
         }
     }
 }
 #define NEAR_WARPS_64 2
 #define NEAR_WARPS_MIX 4
-template <bool MIX, int NW>
+// CB: right-hand sides per pass over the stored entries (1, or 4 for a block right-hand side)
+template <bool MIX, int NW, int CB>
 __global__ void __launch_bounds__(32 * NW) k_near_leaf(int leaf0, const int* __restrict__ box_begin,
                                                        const int* __restrict__ box_end, NearRowPart P64,
                                                        const cd* __restrict__ val64, NearRowPart P32,
                                                        const float2* __restrict__ val32, const cd* __restrict__ diag,
                                                        const cd* __restrict__ x, const float2* __restrict__ x32,
                                                        cd* __restrict__ y, int64_t n, int nrhs) {
-    near_leaf_cta<MIX, NW>(blockIdx.x, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
+    near_leaf_cta<MIX, NW, CB>(blockIdx.x, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
 }
 // one warp per leaf, four warps per CTA
-template <bool MIX>
+template <bool MIX, int CB>
 __global__ void __launch_bounds__(128) k_near_leaf_w(int nleaf, int leaf0, const int* __restrict__ box_begin,
                                                      const int* __restrict__ box_end, NearRowPart P64,
                                                      const cd* __restrict__ val64, NearRowPart P32,
@@ -278,7 +308,7 @@ __global__ void __launch_bounds__(128) k_near_leaf_w(int nleaf, int leaf0, const
                                                      cd* __restrict__ y, int64_t n, int nrhs) {
     const int leaf = (int)(blockIdx.x * 4 + (threadIdx.x >> 5));
     if (leaf >= nleaf) return;   // whole warps: the single-warp path has no block barrier
-    near_leaf_cta<MIX, 1>(leaf, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
+    near_leaf_cta<MIX, 1, CB>(leaf, leaf0, box_begin, box_end, P64, val64, P32, val32, diag, x, x32, y, n, nrhs);
 }
 // leaves from which one warp per leaf fills two waves of the GPU (152 SMs x 64 warps x 2)
 #define NEAR_WARP_PER_LEAF_MIN (152 * 64 * 2)
@@ -479,6 +509,7 @@ struct NearJob {
     int64_t n;
     int nrhs;
 };
+template <int CB>
 __global__ void __launch_bounds__(32 * NEAR_WARPS_64) k_near_leaf_multi(const NearJob* __restrict__ jobs,
                                                                      const int* __restrict__ prefix, int njobs) {
     int lo = 0, hi = njobs - 1;
@@ -488,7 +519,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS_64) k_near_leaf_multi(const Ne
         else hi = mid - 1;
     }
     const NearJob& J = jobs[lo];
-    near_leaf_cta<false, NEAR_WARPS_64>((int)blockIdx.x - prefix[lo], J.leaf0, J.box_begin, J.box_end, J.P64, J.val64, J.P64,
+    near_leaf_cta<false, NEAR_WARPS_64, CB>((int)blockIdx.x - prefix[lo], J.leaf0, J.box_begin, J.box_end, J.P64, J.val64, J.P64,
                          nullptr, nullptr, J.x, nullptr, J.y, J.n, J.nrhs);
 }
 
@@ -499,9 +530,14 @@ void near_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s) {
         lfmm_geometry_s* g = op.g;
         if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN) {   // as near_apply: its own warp-per-leaf launch (same sums)
             const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
-            k_near_leaf_w<false><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
-                                                                    g->d_box_end, p64, g->d_nb_val, p64, nullptr,
-                                                                    nullptr, op.x, nullptr, op.y, g->n, op.nrhs);
+            if (op.nrhs > 1)
+                k_near_leaf_w<false, 4><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                       g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                       nullptr, op.x, nullptr, op.y, g->n, op.nrhs);
+            else
+                k_near_leaf_w<false, 1><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                       g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                       nullptr, op.x, nullptr, op.y, g->n, op.nrhs);
             cuda_check(cudaGetLastError(), "k_near_leaf_w");
             continue;
         }
@@ -515,7 +551,14 @@ void near_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s) {
     const size_t oj = t.add(jobs.data(), sizeof(NearJob) * jobs.size());
     const size_t op = t.add(prefix.data(), sizeof(int) * prefix.size());
     t.upload(s);
-    k_near_leaf_multi<<<prefix.back(), 32 * NEAR_WARPS_64, 0, s>>>(t.at<NearJob>(oj), t.at<int>(op), (int)jobs.size());
+    int maxr = 1;
+    for (const NearJob& J : jobs) maxr = std::max(maxr, J.nrhs);
+    if (maxr > 1)
+        k_near_leaf_multi<4><<<prefix.back(), 32 * NEAR_WARPS_64, 0, s>>>(t.at<NearJob>(oj), t.at<int>(op),
+                                                                          (int)jobs.size());
+    else
+        k_near_leaf_multi<1><<<prefix.back(), 32 * NEAR_WARPS_64, 0, s>>>(t.at<NearJob>(oj), t.at<int>(op),
+                                                                          (int)jobs.size());
     cudaError_t e = cudaGetLastError();
     t.release(s);
     cuda_check(e, "k_near_leaf_multi");
@@ -538,24 +581,48 @@ void near_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, 
         ++g->n_launches;
         const NearRowPart p64{g->d_nl_off64r, g->d_nl_jptr64r, g->d_nl_j64r};
         const NearRowPart p32{g->d_nl_off32, g->d_nl_jptr32, g->d_nl_j32};
-        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN)
-            k_near_leaf_w<true><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin, g->d_box_end,
-                                                                   p64, g->d_nv64r, p32, g->d_nv32, g->d_ndiag,
-                                                                   x_sorted, g->d_near_x32, y_sorted, g->n, nrhs);
-        else
-            k_near_leaf<true, NEAR_WARPS_MIX><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(
+        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN) {
+            if (nrhs > 1)
+                k_near_leaf_w<true, 4><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                       g->d_box_end, p64, g->d_nv64r, p32, g->d_nv32,
+                                                                       g->d_ndiag, x_sorted, g->d_near_x32, y_sorted,
+                                                                       g->n, nrhs);
+            else
+                k_near_leaf_w<true, 1><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                       g->d_box_end, p64, g->d_nv64r, p32, g->d_nv32,
+                                                                       g->d_ndiag, x_sorted, g->d_near_x32, y_sorted,
+                                                                       g->n, nrhs);
+        } else if (nrhs > 1) {
+            k_near_leaf<true, NEAR_WARPS_MIX, 4><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(
                 g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
                 g->d_near_x32, y_sorted, g->n, nrhs);
+        } else {
+            k_near_leaf<true, NEAR_WARPS_MIX, 1><<<g->nleaf, 32 * NEAR_WARPS_MIX, 0, s>>>(
+                g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nv64r, p32, g->d_nv32, g->d_ndiag, x_sorted,
+                g->d_near_x32, y_sorted, g->n, nrhs);
+        }
     } else {
         const NearRowPart p64{g->d_nl_off, g->d_nl_jptr, g->d_nl_j};
-        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN)
-            k_near_leaf_w<false><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
-                                                                    g->d_box_end, p64, g->d_nb_val, p64, nullptr,
-                                                                    nullptr, x_sorted, nullptr, y_sorted, g->n, nrhs);
-        else
-            k_near_leaf<false, NEAR_WARPS_64><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(
+        if (g->nleaf >= NEAR_WARP_PER_LEAF_MIN) {
+            if (nrhs > 1)
+                k_near_leaf_w<false, 4><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                        g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                        nullptr, x_sorted, nullptr, y_sorted, g->n,
+                                                                        nrhs);
+            else
+                k_near_leaf_w<false, 1><<<(g->nleaf + 3) / 4, 128, 0, s>>>(g->nleaf, g->leaf0, g->d_box_begin,
+                                                                        g->d_box_end, p64, g->d_nb_val, p64, nullptr,
+                                                                        nullptr, x_sorted, nullptr, y_sorted, g->n,
+                                                                        nrhs);
+        } else if (nrhs > 1) {
+            k_near_leaf<false, NEAR_WARPS_64, 4><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(
                 g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nb_val, p64, nullptr, nullptr, x_sorted, nullptr,
                 y_sorted, g->n, nrhs);
+        } else {
+            k_near_leaf<false, NEAR_WARPS_64, 1><<<g->nleaf, 32 * NEAR_WARPS_64, 0, s>>>(
+                g->leaf0, g->d_box_begin, g->d_box_end, p64, g->d_nb_val, p64, nullptr, nullptr, x_sorted, nullptr,
+                y_sorted, g->n, nrhs);
+        }
     }
     cuda_check(cudaGetLastError(), "k_near_leaf");
     ++g->n_launches;
