@@ -168,25 +168,6 @@ __global__ void k_react32_tables(const cd* __restrict__ m2lr, const ReactKey* __
         out[K.off + e] = mkf((float)(f * v.x), (float)(f * v.y));
     }
 }
-// out (FP32) = in (FP64) * ispow, column by column
-__global__ void k_to32(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t n, int nrhs,
-                       cf* __restrict__ out) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * nrhs) return;
-    const double f = ispow[t % n];
-    const cd v = in[t];
-    out[t] = mkf((float)(f * v.x), (float)(f * v.y));
-}
-// out (FP64) = in (FP32) * ispow (locals: L = L~ s^-|n|), or in / ispow with
-// multipole = 1 (M = M~ s^|n|)
-__global__ void k_from32(const cf* __restrict__ in, const double* __restrict__ ispow, int64_t n, int nrhs,
-                         cd* __restrict__ out, int multipole = 0) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * nrhs) return;
-    const double f = multipole ? 1.0 / ispow[t % n] : ispow[t % n];
-    const cf v = in[t];
-    out[t] = mk(f * (double)v.x, f * (double)v.y);
-}
 
 // ---------------------------------------------------------------------------
 // M2L in FP32 on the scaled expansions: the same work items, entry descriptors,
@@ -527,9 +508,9 @@ __global__ void k_xtab32(const XDst* __restrict__ dsts, const XSrc* __restrict__
     }
 }
 
-// L~ (FP32) += L (FP64) / ispow over a coefficient range
-// the same over a coefficient range [c0, c0 + n) of every column (leading dimension ld): one
-// launch for all columns
+// Level hand-over between the FP32 and FP64 levels, over a coefficient range [c0, c0 + n) of
+// every column (leading dimension ld), one launch for all columns: multipoles M = M~ s^|m| into
+// FP64 (k_from32_cols), locals L~ += L s^|n| into FP32 (k_add_to32_cols; ispow = s^-|n|)
 __global__ void k_from32_cols(const cf* __restrict__ in, const double* __restrict__ ispow, int64_t c0, int64_t n,
                               int nrhs, int64_t ld, cd* __restrict__ out) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * nrhs;
@@ -549,14 +530,6 @@ __global__ void k_add_to32_cols(const cd* __restrict__ in, const double* __restr
         const cd v = in[col * ld + i];
         out[col * ld + i] = addf(out[col * ld + i], mkf((float)(f * v.x), (float)(f * v.y)));
     }
-}
-__global__ void k_add_to32(const cd* __restrict__ in, const double* __restrict__ ispow, int64_t n,
-                           cf* __restrict__ out) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const double f = 1.0 / ispow[t];
-    const cd v = in[t];
-    out[t] = addf(out[t], mkf((float)(f * v.x), (float)(f * v.y)));
 }
 
 // ---------------------------------------------------------------------------
