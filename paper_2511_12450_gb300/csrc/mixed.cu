@@ -447,6 +447,9 @@ __global__ void __launch_bounds__(128) k_l2p32(const ExpGroup* __restrict__ grou
 
 // M2M / L2L in FP32 on scaled expansions: out_n (= or +=) sum_j sum_m src_j[m] W_j[m][n],
 // W_j dense (column-major, (n, m) at m ncD + n) with the scale factors folded in.
+// GROUPS: the columns split over blockIdx.z in groups of four (col_groups); otherwise every
+// CTA walks all columns (the single-column form keeps its registers)
+template <bool GROUPS>
 __global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
                         const int64_t* __restrict__ wtab_off, const cf* __restrict__ wtab, int accumulate, int w,
                         int nrhs, int64_t ncoef, int64_t nslotcoef, cf* X, cf* Xp) {
@@ -457,8 +460,7 @@ __global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ ds
     const int idx = blockIdx.y * w + lane;
     const int ncD = 2 * d.p + 1;
     const bool live = sl < ns && idx < ncD;
-    const int cpb = (nrhs + gridDim.z - 1) / gridDim.z;   // blockIdx.z: a group of columns
-    const int col0 = blockIdx.z * cpb, col1 = min(nrhs, col0 + cpb);
+    const int col0 = GROUPS ? blockIdx.z * 4 : 0, col1 = GROUPS ? min(nrhs, col0 + 4) : nrhs;
     for (int col = col0; col < col1; ++col) {
         cf a = mkf(0, 0);
         if (live) {
@@ -1071,9 +1073,14 @@ static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate
     // FP32 translations are not bound by an arithmetic pipe: 16-lane chunks (more CTAs)
     // measured faster here than rows as wide as the coefficient count
     const int nco = 2 * p_dst + 1, w = XT_W;
-    dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
-    k_translate32<<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab, accumulate, w,
-                                       nrhs, g->ncoef, g->nslotcoef, X, Xp);
+    const int ng = col_groups(nrhs);
+    dim3 grid(nd, (nco + w - 1) / w, ng);
+    if (ng > 1)
+        k_translate32<true><<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab,
+                                                 accumulate, w, nrhs, g->ncoef, g->nslotcoef, X, Xp);
+    else
+        k_translate32<false><<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab,
+                                                  accumulate, w, nrhs, g->ncoef, g->nslotcoef, X, Xp);
     cuda_check(cudaGetLastError(), "k_translate32");
     ++g->n_launches;
 }
