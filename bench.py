@@ -41,8 +41,8 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch from the committed ncu captures (profiles/); null once the
 # kernel changes after the capture
-NCU_TRAFFIC_BYTES = {"k_m2l": 85761280.0 + 3519488.0, "k_near_leaf": 67979008.0 + 378368.0,
-                     "k_near_leaf (precision form)": 38070784.0}
+NCU_TRAFFIC_BYTES = {"k_m2l": 85761280.0 + 3519488.0, "k_near_leaf": 67980800.0 + 316160.0,
+                     "k_near_leaf (precision form)": 38071040.0}
 
 
 def run_combined(lfmm, wl, M, pts, w, nrm, x, flush, stream, args, dist, n):
