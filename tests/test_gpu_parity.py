@@ -336,6 +336,23 @@ def test_fmm_multiple_rhs_columns_match_single(small3):
         assert relerr(Y[:, c], y1) <= 1e-14
 
 
+def test_block_columns_equal_single_column_products(wide):
+    # seven columns: the translations, the double-float M2L and the near field split a block's
+    # columns in groups of four (one ragged group of three); each column must come out with the
+    # bits of its own single-column product, in the FP64 form and in the precision form (whose
+    # coarse wide-band levels run the double-float M2L here)
+    lf, pts, w = wide["lf"], wide["pts"], wide["w"]
+    G = lf.geometry_build(wide["M"], pts, w, p=20, leaf_size=8)
+    rng = np.random.default_rng(11)
+    X = np.asfortranarray(rng.standard_normal((G.n, 7)) + 1j * rng.standard_normal((G.n, 7)))
+    for mixed in (False, True):
+        Y = lf.matvec(G, X, mixed=mixed)
+        for c in range(7):
+            assert np.array_equal(Y[:, c], lf.matvec(G, np.ascontiguousarray(X[:, c]), mixed=mixed)), (mixed, c)
+    lm, df = lf.geometry_query(G, "precision_form", np.float64)[:2]
+    assert df == 1 and lm > lf.geometry_query(G, "tree_params", np.float64)[4]
+
+
 # FMM truncation error of the 65,536-point workload against the stored oracle rows
 # (largest row error over the 12 rows, relative to that row's |y|), per order p: measured
 # 1.5e-7, 2.5e-9, 4.5e-11, 3.2e-11 (medians 3.8e-8, 1.1e-10, 7.7e-12, 1.3e-12); the bounds
