@@ -139,22 +139,38 @@ __global__ void __launch_bounds__(128) k_m2l32_tc(
         // the real part's columns start at K = 0, the imaginary part's at K = kh (a multiple of
         // four), the positions between nco and kh are written as zeros
         const int kh = (nco + 3) & ~3, nq = kh >> 2;
-        for (int q = tid; q < nco * nq; q += 128) {
-            const int i = q % nco, j0 = (q / nco) * 4;
-            float4 arh, arl, aih, ail;
-            float* f[4] = {&arh.x, &arl.x, &aih.x, &ail.x};
+        // two units per round: all eight table values are loaded before any is split or
+        // stored, so their loads are in flight together
+        for (int q0 = tid; q0 < nco * nq; q0 += 256) {
+            cf raw[2][4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const cf a = (j0 + t < nco) ? tc_entry_value(E, i, j0 + t, p, nco, ftab, ftab_off, rtab) : mkf(0.f, 0.f);
-                tc_split(a.x, f[0][t], f[1][t]);
-                tc_split(a.y, f[2][t], f[3][t]);
+            for (int u = 0; u < 2; ++u) {
+                const int q = q0 + 128 * u;
+                const int i = q % nco, j0 = (q / nco) * 4;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    raw[u][t] = (q < nco * nq && j0 + t < nco) ? tc_entry_value(E, i, j0 + t, p, nco, ftab, ftab_off, rtab)
+                                                             : mkf(0.f, 0.f);
             }
-            const float4 naih = make_float4(-aih.x, -aih.y, -aih.z, -aih.w);
-            const float4 nail = make_float4(-ail.x, -ail.y, -ail.z, -ail.w);
-            *(float4*)&sAh[tc_canon(i, j0, kp)] = arh;            *(float4*)&sAl[tc_canon(i, j0, kp)] = arl;
-            *(float4*)&sAh[tc_canon(i, kh + j0, kp)] = naih;      *(float4*)&sAl[tc_canon(i, kh + j0, kp)] = nail;
-            *(float4*)&sAh[tc_canon(i + nco, j0, kp)] = aih;      *(float4*)&sAl[tc_canon(i + nco, j0, kp)] = ail;
-            *(float4*)&sAh[tc_canon(i + nco, kh + j0, kp)] = arh; *(float4*)&sAl[tc_canon(i + nco, kh + j0, kp)] = arl;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int q = q0 + 128 * u;
+                if (q >= nco * nq) break;
+                const int i = q % nco, j0 = (q / nco) * 4;
+                float4 arh, arl, aih, ail;
+                float* f[4] = {&arh.x, &arl.x, &aih.x, &ail.x};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    tc_split(raw[u][t].x, f[0][t], f[1][t]);
+                    tc_split(raw[u][t].y, f[2][t], f[3][t]);
+                }
+                const float4 naih = make_float4(-aih.x, -aih.y, -aih.z, -aih.w);
+                const float4 nail = make_float4(-ail.x, -ail.y, -ail.z, -ail.w);
+                *(float4*)&sAh[tc_canon(i, j0, kp)] = arh;            *(float4*)&sAl[tc_canon(i, j0, kp)] = arl;
+                *(float4*)&sAh[tc_canon(i, kh + j0, kp)] = naih;      *(float4*)&sAl[tc_canon(i, kh + j0, kp)] = nail;
+                *(float4*)&sAh[tc_canon(i + nco, j0, kp)] = aih;      *(float4*)&sAl[tc_canon(i + nco, j0, kp)] = ail;
+                *(float4*)&sAh[tc_canon(i + nco, kh + j0, kp)] = arh; *(float4*)&sAl[tc_canon(i + nco, kh + j0, kp)] = arl;
+            }
         }
         const bool from_slot = (E.flags & M2L_REACT) && (E.flags & M2L_SRC_SLOT);
         const cf* src = (from_slot ? Mp : Min) + E.src;
