@@ -33,6 +33,7 @@
 #pragma once
 
 #define TC_MAXN 32          // columns per launch (N of the MMA)
+#define TC_UNITS 4          // staging units (4 table values each) loaded together
 #define TC_WAIT_LIMIT (1 << 24)
 
 __device__ __forceinline__ uint32_t tc_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -139,12 +140,12 @@ __global__ void __launch_bounds__(128) k_m2l32_tc(
         // the real part's columns start at K = 0, the imaginary part's at K = kh (a multiple of
         // four), the positions between nco and kh are written as zeros
         const int kh = (nco + 3) & ~3, nq = kh >> 2;
-        // two units per round: all eight table values are loaded before any is split or
+        // TC_UNITS units per round: all their table values are loaded before any is split or
         // stored, so their loads are in flight together
-        for (int q0 = tid; q0 < nco * nq; q0 += 256) {
-            cf raw[2][4];
+        for (int q0 = tid; q0 < nco * nq; q0 += 128 * TC_UNITS) {
+            cf raw[TC_UNITS][4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < TC_UNITS; ++u) {
                 const int q = q0 + 128 * u;
                 const int i = q % nco, j0 = (q / nco) * 4;
 #pragma unroll
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(128) k_m2l32_tc(
                                                              : mkf(0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < TC_UNITS; ++u) {
                 const int q = q0 + 128 * u;
                 if (q >= nco * nq) break;
                 const int i = q % nco, j0 = (q / nco) * 4;
@@ -175,18 +176,32 @@ __global__ void __launch_bounds__(128) k_m2l32_tc(
         const bool from_slot = (E.flags & M2L_REACT) && (E.flags & M2L_SRC_SLOT);
         const cf* src = (from_slot ? Mp : Min) + E.src;
         const int64_t stride = from_slot ? nslotcoef : ncoef;
-        for (int q = tid; q < ncols * nq; q += 128) {
-            const int jq = q % nq, c = q / nq, j0 = jq * 4;
-            float4 xrh, xrl, xih, xil;
-            float* f[4] = {&xrh.x, &xrl.x, &xih.x, &xil.x};
+        for (int q0 = tid; q0 < ncols * nq; q0 += 128 * TC_UNITS) {
+            cf raw[TC_UNITS][4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const cf v = (j0 + t < nco) ? src[(int64_t)(col0 + c) * stride + j0 + t] : mkf(0.f, 0.f);
-                tc_split(v.x, f[0][t], f[1][t]);
-                tc_split(v.y, f[2][t], f[3][t]);
+            for (int u = 0; u < TC_UNITS; ++u) {
+                const int q = q0 + 128 * u;
+                const int jq = q % nq, c = q / nq, j0 = jq * 4;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    raw[u][t] = (q < ncols * nq && j0 + t < nco) ? src[(int64_t)(col0 + c) * stride + j0 + t]
+                                                                 : mkf(0.f, 0.f);
             }
-            *(float4*)&sBh[tc_canon(c, j0, kp)] = xrh;       *(float4*)&sBl[tc_canon(c, j0, kp)] = xrl;
-            *(float4*)&sBh[tc_canon(c, kh + j0, kp)] = xih;  *(float4*)&sBl[tc_canon(c, kh + j0, kp)] = xil;
+#pragma unroll
+            for (int u = 0; u < TC_UNITS; ++u) {
+                const int q = q0 + 128 * u;
+                if (q >= ncols * nq) break;
+                const int jq = q % nq, c = q / nq, j0 = jq * 4;
+                float4 xrh, xrl, xih, xil;
+                float* f[4] = {&xrh.x, &xrl.x, &xih.x, &xil.x};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    tc_split(raw[u][t].x, f[0][t], f[1][t]);
+                    tc_split(raw[u][t].y, f[2][t], f[3][t]);
+                }
+                *(float4*)&sBh[tc_canon(c, j0, kp)] = xrh;       *(float4*)&sBl[tc_canon(c, j0, kp)] = xrl;
+                *(float4*)&sBh[tc_canon(c, kh + j0, kp)] = xih;  *(float4*)&sBl[tc_canon(c, kh + j0, kp)] = xil;
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
