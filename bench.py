@@ -412,7 +412,7 @@ def run_c3(lfmm, steps=5):
     return out
 
 
-def run_batch(lfmm, index=10, steps=5):
+def run_batch(lfmm, index=10, steps=5, solve=True):
     """Block right-hand side: one geometry of the batching configuration (C4 geometry
     `index`, 2-4 layers, k in [2, 12]) with its 32 incidence angles as one 32-column matvec,
     against 32 single-column matvecs; L2 flushed before every timed call."""
@@ -464,6 +464,15 @@ def run_batch(lfmm, index=10, steps=5):
     t_mixed_tc = timed(lambda: lfmm.matvec(G, B, Ym, mixed=True))
     t_mixed_simt = timed(lambda: lfmm.matvec(G, B, Ys, mixed=True, simt_m2l=True))
     rel = lambda a, b: max(float(torch.linalg.norm(a[c] - b[c]) / torch.linalg.norm(b[c])) for c in range(nr))
+    out = {"metric": "block right-hand side matvec, Mpts*rhs/s", "workload": f"C4 geometry {index}: {len(med.k)} layers, "
+           f"N={n}, {nr} incidence angles", "block_value": n * nr / t_block / 1e6,
+           "single_column_value": n * nr / t_single / 1e6, "block_ms": t_block * 1e3,
+           "single_columns_ms": t_single * 1e3, "max_rel_diff_block_vs_single": same,
+           "mixed_block_tensor_core_value": n * nr / t_mixed_tc / 1e6, "mixed_block_tensor_core_ms": t_mixed_tc * 1e3,
+           "mixed_block_simt_value": n * nr / t_mixed_simt / 1e6, "mixed_block_simt_ms": t_mixed_simt * 1e3,
+           "mixed_tensor_core_vs_fp64_max_rel_diff": rel(Ym, Y), "mixed_tensor_core_vs_simt_max_rel_diff": rel(Ym, Ys)}
+    if not solve:
+        return out
     # several angles solved together (one Krylov space per column, block matvecs) against
     # the same angles one by one; 8 of the 32 keep the section short
     na = 8
@@ -478,17 +487,11 @@ def run_batch(lfmm, index=10, steps=5):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     same_solve = max(float(torch.linalg.norm(X8[c] - xs1[c]) / torch.linalg.norm(xs1[c])) for c in range(na))
-    return {"metric": "block right-hand side matvec, Mpts*rhs/s", "workload": f"C4 geometry {index}: {len(med.k)} layers, "
-            f"N={n}, {nr} incidence angles", "block_value": n * nr / t_block / 1e6,
-            "single_column_value": n * nr / t_single / 1e6, "block_ms": t_block * 1e3,
-            "single_columns_ms": t_single * 1e3, "max_rel_diff_block_vs_single": same,
-            "mixed_block_tensor_core_value": n * nr / t_mixed_tc / 1e6, "mixed_block_tensor_core_ms": t_mixed_tc * 1e3,
-            "mixed_block_simt_value": n * nr / t_mixed_simt / 1e6, "mixed_block_simt_ms": t_mixed_simt * 1e3,
-            "mixed_tensor_core_vs_fp64_max_rel_diff": rel(Ym, Y), "mixed_tensor_core_vs_simt_max_rel_diff": rel(Ym, Ys),
-            "angles_solved_together": {"angles": na, "seconds": t_simul, "one_by_one_seconds": t_seq,
-                                       "converged": bool(info8["converged"]),
-                                       "true_rel_residual": info8["true_rel_residual"],
-                                       "max_rel_diff_vs_one_by_one": same_solve}}
+    out["angles_solved_together"] = {"angles": na, "seconds": t_simul, "one_by_one_seconds": t_seq,
+                                     "converged": bool(info8["converged"]),
+                                     "true_rel_residual": info8["true_rel_residual"],
+                                     "max_rel_diff_vs_one_by_one": same_solve}
+    return out
 
 
 def run_batch16(lfmm, steps=3):
@@ -874,7 +877,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2511_12450_gb300 import lfmm
 
-        print(json.dumps({"batch": run_batch(lfmm, steps=args.steps), "data": "synthetic", "dtype": "f64"}))
+        print(json.dumps({"batch": run_batch(lfmm, steps=args.steps, solve=not args.no_solve), "data": "synthetic",
+                          "dtype": "f64"}))
         return 0
     if args.only_c3:
         import torch
