@@ -276,9 +276,9 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_leaf_entries = dupload(g, leaf_e);
         g->d_slot_entries = dupload(g, slot_e);
         g->d_slot_leaf_entries = dupload(g, slot_leaf_e);
-        // Upward (M2M) and downward (L2L) passes.  Each level's pass is a list of
-        // destination vectors (cell centres and reaction centres alike), each with
-        // its sources and one translation vector per source:
+        // Upward (M2M) and downward (L2L) passes.  Cells translate as families (a
+        // parent and its children, k_translate); each reaction centre of a straddling
+        // cell is a destination with its sources and one translation vector per source:
         //   dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
         // M2M uses V_k = J_k(k|d|) e^{-i k theta_d} (d = source centre - destination
         // centre); L2L uses J_k(k|u|) e^{+i k theta_u} (u = destination - source)
@@ -295,34 +295,48 @@ void fmm_build(lfmm_geometry_s* g) {
             xvec.insert(xvec.end(), v.begin(), v.end());
             return o;
         };
-        // cell-to-cell vectors, shared per (layer, child level, quadrant of the child)
-        std::vector<int64_t> up_tab(nl * nlev * 4, -1), dn_tab(nl * nlev * 4, -1);
+        // cell-to-cell base vectors, one per (layer, child level): the quadrant-3 child
+        // (+w/2, +w/2); the other quadrants' vectors differ from it by the phases of
+        // quarter turns, which the quadrant form applies (quad_up / quad_dn)
+        std::vector<int64_t> up_tab(nl * nlev, -1), dn_tab(nl * nlev, -1);
         for (int lay = 0; lay < nl; ++lay)
             for (int l = l0 + 1; l <= D; ++l) {
                 int hw = t.p_level[l - 1] + t.p_level[l];
                 double w = t.width(l);
-                for (int quad = 0; quad < 4; ++quad) {
-                    double dx = (quad & 1) ? 0.5 * w : -0.5 * w;
-                    double dy = (quad & 2) ? 0.5 * w : -0.5 * w;
-                    up_tab[(lay * nlev + l) * 4 + quad] = put_vec(g->m.k[lay], dx, dy, hw, -1, false);
-                    dn_tab[(lay * nlev + l) * 4 + quad] = put_vec(g->m.k[lay], dx, dy, hw, +1, true);
-                }
+                up_tab[lay * nlev + l] = put_vec(g->m.k[lay], 0.5 * w, 0.5 * w, hw, -1, false);
+                dn_tab[lay * nlev + l] = put_vec(g->m.k[lay], 0.5 * w, 0.5 * w, hw, +1, true);
             }
+        g->qvec_host.assign((size_t)nl * nlev * 2, -1);
+        for (int i = 0; i < nl * nlev; ++i) {
+            g->qvec_host[2 * i] = up_tab[i];
+            g->qvec_host[2 * i + 1] = dn_tab[i];
+        }
         auto quad_of = [&](int c) { return (t.box_ix[c] & 1) | ((t.box_iy[c] & 1) << 1); };
         auto slot_y = [&](int b, int sl) { return sl >= 0 ? slot_cy[sl] : t.cy(b); };
+        // families: every parent cell at l - 1 with its children at l
+        std::vector<QuadX> qx;
+        g->q_begin.assign(nlev + 1, 0); g->q_end.assign(nlev + 1, 0);
+        for (int l = l0 + 1; l <= D; ++l) {
+            g->q_begin[l] = (int)qx.size();
+            for (int P = t.level_start[l - 1]; P < t.level_start[l]; ++P) {
+                const int lay = t.box_layer[P];
+                QuadX f{off[P], {-1, -1, -1, -1}, up_tab[lay * nlev + l], dn_tab[lay * nlev + l], lay, 0};
+                for (int c = t.child_begin[P]; c < t.child_end[P]; ++c) {
+                    f.ch[quad_of(c)] = off[c];
+                    for (int side = 0; side < 2; ++side)
+                        if (slot_of[2 * P + side] >= 0 && slot_of[2 * c + side] < 0) f.dn_skip |= 1 << quad_of(c);
+                }
+                qx.push_back(f);
+            }
+            g->q_end[l] = (int)qx.size();
+        }
         g->up_begin.assign(nlev + 1, 0); g->up_end.assign(nlev + 1, 0);
         g->dn_begin.assign(nlev + 1, 0); g->dn_end.assign(nlev + 1, 0);
+        // the remaining destinations: reaction centres of straddling cells, each with its
+        // own sources and vectors
         for (int lp = D - 1; lp >= l0; --lp) {   // M2M into parents at level lp
             const int pP = t.p_level[lp], pC = t.p_level[lp + 1], hw = pP + pC;
             g->up_begin[lp] = (int)xd.size();
-            for (int b = t.level_start[lp]; b < t.level_start[lp + 1]; ++b) {
-                XDst d{off[b], pP, 0, (int)xs.size(), 0};
-                for (int c = t.child_begin[b]; c < t.child_end[b]; ++c)
-                    xs.push_back(XSrc{off[c], up_tab[(t.box_layer[b] * nlev + lp + 1) * 4 + quad_of(c)], pC, 0});
-                d.src_end = (int)xs.size();
-                xd.push_back(d);
-                xd_layer.push_back(t.box_layer[b]);
-            }
             for (int side = 0; side < 2; ++side)
                 for (int b = t.level_start[lp]; b < t.level_start[lp + 1]; ++b) {
                     const int sp = slot_of[2 * b + side];
@@ -343,19 +357,26 @@ void fmm_build(lfmm_geometry_s* g) {
         for (int l = l0 + 1; l <= D; ++l) {   // L2L into children at level l
             const int pP = t.p_level[l - 1], pC = t.p_level[l], hw = pP + pC;
             g->dn_begin[l] = (int)xd.size();
-            for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
-                const int P = t.box_parent[b];
-                XDst d{off[b], pC, 0, (int)xs.size(), 0};
-                xs.push_back(XSrc{off[P], dn_tab[(t.box_layer[b] * nlev + l) * 4 + quad_of(b)], pP, 0});
-                for (int side = 0; side < 2; ++side) {   // reaction locals of a straddling parent
-                    const int sp = slot_of[2 * P + side];
-                    if (sp < 0 || slot_of[2 * b + side] >= 0) continue;
-                    const int64_t v = put_vec(g->m.k[t.box_layer[b]], t.cx(b) - t.cx(P), t.cy(b) - slot_cy[sp], hw, +1, true);
-                    xs.push_back(XSrc{slot_coef[sp], v, pP, 1});
+            // cells under a straddling parent that do not straddle that interface: the
+            // parent's cell local and its reaction-centre locals
+            for (int q = g->q_begin[l]; q < g->q_end[l]; ++q) {
+                const int P = t.level_start[l - 1] + (q - g->q_begin[l]);   // one family per parent, in order
+                if (!qx[q].dn_skip) continue;
+                for (int c = t.child_begin[P]; c < t.child_end[P]; ++c) {
+                    if (!((qx[q].dn_skip >> quad_of(c)) & 1)) continue;
+                    XDst d{off[c], pC, 0, (int)xs.size(), 0};
+                    xs.push_back(XSrc{off[P], put_vec(g->m.k[t.box_layer[c]], t.cx(c) - t.cx(P), t.cy(c) - t.cy(P), hw, +1, true),
+                                      pP, 0});
+                    for (int side = 0; side < 2; ++side) {
+                        const int sp = slot_of[2 * P + side];
+                        if (sp < 0 || slot_of[2 * c + side] >= 0) continue;
+                        const int64_t v = put_vec(g->m.k[t.box_layer[c]], t.cx(c) - t.cx(P), t.cy(c) - slot_cy[sp], hw, +1, true);
+                        xs.push_back(XSrc{slot_coef[sp], v, pP, 1});
+                    }
+                    d.src_end = (int)xs.size();
+                    xd.push_back(d);
+                    xd_layer.push_back(t.box_layer[c]);
                 }
-                d.src_end = (int)xs.size();
-                xd.push_back(d);
-                xd_layer.push_back(t.box_layer[b]);
             }
             for (int side = 0; side < 2; ++side)
                 for (int b = t.level_start[l]; b < t.level_start[l + 1]; ++b) {
@@ -374,6 +395,8 @@ void fmm_build(lfmm_geometry_s* g) {
                 }
             g->dn_end[l] = (int)xd.size();
         }
+        g->d_qx = dupload(g, qx);
+        g->qx_host = qx;
         g->d_xdst = dupload(g, xd);
         g->d_xsrc = dupload(g, xs);
         g->d_xvec = dupload(g, xvec);
@@ -614,6 +637,42 @@ static void launch_m2l64(lfmm_geometry_s* g, int nrhs, int n64, int r64, cudaStr
     launch_m2l_range(g, nrhs, 0, n64, 0, r64, s);
 }
 
+// one level's M2M (into parents at level - 1: down = 0) or L2L (into children at level:
+// down = 1) pass over a block of nrhs columns
+static XPass make_pass(lfmm_geometry_s* g, int level, int down, int accumulate, int nrhs) {
+    const TreeHost& t = g->tree;
+    XPass P;
+    P.dsts = g->d_xdst + (down ? g->dn_begin[level] : g->up_begin[level - 1]);
+    P.srcs = g->d_xsrc;
+    P.vec = g->d_xvec;
+    P.qx = g->d_qx + g->q_begin[level];
+    P.nq = g->q_end[level] - g->q_begin[level];
+    P.nd = down ? g->dn_end[level] - g->dn_begin[level] : g->up_end[level - 1] - g->up_begin[level - 1];
+    P.pS = down ? t.p_level[level - 1] : t.p_level[level];
+    P.pD = down ? t.p_level[level] : t.p_level[level - 1];
+    const int nco = 2 * P.pD + 1;
+    P.w = lane_width(nco);
+    P.nch = (nco + P.w - 1) / P.w;
+    xpass_fam_split(P.nq, P.pD, &P.fch, &P.fr);
+    P.down = down;
+    P.accumulate = accumulate;
+    P.ncoef = g->ncoef;
+    P.nslotcoef = g->nslotcoef;
+    P.X = down ? g->d_L : g->d_M;
+    P.Xp = down ? g->d_Lp : g->d_Mp;
+    (void)nrhs;
+    return P;
+}
+static void launch_pass(lfmm_geometry_s* g, const XPass& P, int nrhs, cudaStream_t s, const char* what) {
+    const int items = xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch;
+    if (items == 0) return;
+    const size_t smem = xpass_smem(P.down, P.pS);
+    raise_smem_limit((const void*)k_translate, smem, "translate smem");
+    k_translate<<<dim3(items, 1, col_groups(nrhs)), 128, smem, s>>>(P, nrhs);
+    cuda_check(cudaGetLastError(), what);
+    ++g->n_launches;
+}
+
 void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, cudaStream_t s, bool mixed,
                cudaEvent_t before_l2p) {
     set_smem_limits();
@@ -658,14 +717,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     for (int lp = D - 1; lp >= l0; --lp) {   // M2M: children at lp + 1 -> parents (cells and reaction centres) at lp
         if (lp >= lm) { mixed_m2m(g, lp, nrhs, s); continue; }
         if (lp == lm - 1) mixed_m_to64(g, lm, nrhs, s);   // the FP64 levels start from the FP32 ones' multipoles
-        const int nd = g->up_end[lp] - g->up_begin[lp];
-        if (nd == 0) continue;
-        const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco);
-        dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
-        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nrhs, g->ncoef,
-                                         g->nslotcoef, g->d_M, g->d_Mp);
-        cuda_check(cudaGetLastError(), "k_translate (M2M)");
-        ++g->n_launches;
+        launch_pass(g, make_pass(g, lp + 1, 0, 0, nrhs), nrhs, s, "k_translate (M2M)");
     }
     prof_end(g, ST_M2M, s);
     {   // M2L, all levels (precision form: the levels >= lm in FP32)
@@ -686,17 +738,10 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     prof_begin(g, ST_L2L, s);
     for (int l = l0 + 1; l <= D; ++l) {   // L2L: parents at l - 1 -> children (cells and reaction centres) at l
         if (l > lm) { mixed_l2l(g, l, nrhs, s); continue; }
-        const int nd = g->dn_end[l] - g->dn_begin[l];
-        if (nd == 0) continue;
         // at the first FP32 level the FP64 translation writes (not adds) and is then added
         // into the FP32 locals, which the FP32 M2L has written
         const int acc = (l == lm) ? 0 : 1;
-        const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco);
-        dim3 grid(nd, (nco + w - 1) / w, col_groups(nrhs));
-        k_translate<<<grid, 128, 0, s>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, acc, w, nrhs, g->ncoef,
-                                         g->nslotcoef, g->d_L, g->d_Lp);
-        cuda_check(cudaGetLastError(), "k_translate (L2L)");
-        ++g->n_launches;
+        launch_pass(g, make_pass(g, l, 1, acc, nrhs), nrhs, s, "k_translate (L2L)");
         if (l == lm) mixed_l_add(g, lm, nrhs, s);
     }
     prof_end(g, ST_L2L, s);
@@ -750,12 +795,8 @@ struct L2PJob {
     cd* y;
 };
 struct XJob {
-    const XDst* dsts;
-    const XSrc* srcs;
-    const cd* vec;
-    int accumulate, w, nchunk, nrhs;
-    int64_t ncoef, nslotcoef;
-    cd *X, *Xp;
+    XPass P;
+    int nrhs;
 };
 struct M2LJob {
     const M2LItem* items;
@@ -794,11 +835,10 @@ __global__ void __launch_bounds__(128) k_l2p_multi(const L2PJob* __restrict__ jo
 }
 __global__ void __launch_bounds__(128) k_translate_multi(const XJob* __restrict__ jobs, const int* __restrict__ prefix,
                                                          int njobs) {
+    extern __shared__ cd xsm[];
     const int j = job_of(prefix, njobs, blockIdx.x);
-    const XJob& J = jobs[j];
-    const int b = blockIdx.x - prefix[j];
-    translate_dst(b / J.nchunk, b % J.nchunk, J.dsts, J.srcs, J.vec, J.accumulate, J.w, 0, J.nrhs, J.ncoef, J.nslotcoef,
-                  J.X, J.Xp);
+    const XPass P = jobs[j].P;
+    translate_item(blockIdx.x - prefix[j], P, 0, jobs[j].nrhs, xsm);
 }
 __global__ void __launch_bounds__(128) k_m2l_multi(const M2LJob* __restrict__ jobs, const int* __restrict__ prefix,
                                                    int njobs) {
@@ -893,18 +933,19 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
     for (int k = 0; k < max_up; ++k) {
         std::vector<XJob> jobs;
         std::vector<int> blocks;
+        size_t smem = 0;
         for (const BatchOp* op : far) {
             lfmm_geometry_s* g = op->g;
             const TreeHost& t = g->tree;
             const int lp = t.D - 1 - k;
             if (lp < t.l0) continue;
-            const int nd = g->up_end[lp] - g->up_begin[lp];
-            const int nco = 2 * t.p_level[lp] + 1, w = lane_width(nco), nch = (nco + w - 1) / w;
-            jobs.push_back(XJob{g->d_xdst + g->up_begin[lp], g->d_xsrc, g->d_xvec, 0, w, nch, op->nrhs, g->ncoef,
-                                g->nslotcoef, g->d_M, g->d_Mp});
-            blocks.push_back(nd * nch);
+            const XPass P = make_pass(g, lp + 1, 0, 0, op->nrhs);
+            jobs.push_back(XJob{P, op->nrhs});
+            blocks.push_back(xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch);
+            smem = std::max(smem, xpass_smem(0, P.pS));
         }
-        launch_jobs(jobs, blocks, k_translate_multi, 128, 0, s, "k_translate_multi (M2M)");
+        raise_smem_limit((const void*)k_translate_multi, smem, "translate smem");
+        launch_jobs(jobs, blocks, k_translate_multi, 128, smem, s, "k_translate_multi (M2M)");
     }
     {   // M2L of every level, then the reductions of split items
         std::vector<M2LJob> jobs;
@@ -931,13 +972,11 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
             const TreeHost& t = g->tree;
             const int l = t.l0 + 1 + k;
             if (l > t.D) continue;
-            const int nd = g->dn_end[l] - g->dn_begin[l];
-            const int nco = 2 * t.p_level[l] + 1, w = lane_width(nco), nch = (nco + w - 1) / w;
-            jobs.push_back(XJob{g->d_xdst + g->dn_begin[l], g->d_xsrc, g->d_xvec, 1, w, nch, op->nrhs, g->ncoef,
-                                g->nslotcoef, g->d_L, g->d_Lp});
-            blocks.push_back(nd * nch);
+            const XPass P = make_pass(g, l, 1, 1, op->nrhs);
+            jobs.push_back(XJob{P, op->nrhs});
+            blocks.push_back(xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch);
         }
-        launch_jobs(jobs, blocks, k_translate_multi, 128, 0, s, "k_translate_multi (L2L)");
+        launch_jobs(jobs, blocks, k_translate_multi, 128, xpass_smem(1, 0), s, "k_translate_multi (L2L)");
     }
     // L2P after the near field, which adds into the same y
     if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");

@@ -15,6 +15,8 @@
 // beta_m = sum_n I_{nm} alpha_n (eq. metoleimage) with the moments I_{nm} of
 // eq. generalintegral tabulated per box-pair geometry.
 #pragma once
+#include <algorithm>
+
 #include "devmath.cuh"
 #include "sommerfeld.cuh"
 
@@ -310,23 +312,46 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
     l2p_group(blockIdx.x, groups, ent, m, px, py, n, nrhs, stride, L, y);
 }
 
-// Multipole-to-multipole and local-to-local translations (Graf's addition
-// theorem) into the destinations of one level: cell centres and reaction
-// centres of straddling cells alike, each with its own list of sources:
-//   dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
-// A CTA of 128 threads owns w consecutive output indices of one destination
-// (one per lane of a w-lane row; w = XT_W or all 2p+1 of them, see lane_width)
-// and 128 / w slices of the sum over m; the slices are reduced in a fixed order,
-// so results are reproducible.  Spreading a destination over several CTAs keeps
-// the coarse levels (few boxes, orders up to 2p+1 ~ 115) from running on a
-// handful of SMs.
-__device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __restrict__ dsts,
-                                              const XSrc* __restrict__ srcs, const cd* __restrict__ vec,
-                                              int accumulate, int w, int col0, int col1, int64_t ncoef,
-                                              int64_t nslotcoef, cd* X, cd* Xp) {
-    __shared__ cd red[128];
-    const XDst d = dsts[di];
-    const int ns = 128 / w;
+// Multipole-to-multipole and local-to-local translations (Graf's addition theorem),
+// one launch per level and pass over two kinds of work:
+//  - families (QuadX): a parent cell and its children about cell centres.  The
+//    children's offsets d_q = (+-w/2, +-w/2) share one length, and their angles are
+//    quarter turns apart, so child q's vector is the quadrant-3 (base) vector times a
+//    phase: V^q_k = B_k om_q^k, om_q a power of -i (M2M; L2L uses the conjugates).  With
+//    s = (n - m) mod 4 (M2M) or (m - n) mod 4 (L2L),
+//      M2M:  M^P_n = sum_s sum_{m: s} B_{n-m} S^s_m,   S^s_m = sum_q om_q^s M^q_m,
+//      L2L:  L^q_n = sum_s conj(om_q)^s T^s_n,        T^s_n = sum_{m: s} C_{m-n} L^P_m,
+//    where S and the sum over s are 4-point transforms (additions, negations and
+//    exchanges of real and imaginary parts).  A family thus costs one Toeplitz
+//    product instead of one per child.  The work is by warps: lane (n, s) of a round
+//    (32 consecutive pairs, 8 outputs x 4 residues) sums the terms of residue s of
+//    output n, and the 4 lanes of an output combine by shuffles in a fixed order;
+//  - reaction centres of straddling cells, and the cells that take a straddling
+//    parent's reaction-centre local (XDst), one CTA each, a sum over their own sources,  dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].  A CTA of
+//    128 threads owns w consecutive output indices (one per lane of a w-lane row; w =
+//    XT_W or all 2p+1 of them, see lane_width) and 128 / w slices of the sum over m,
+//    reduced in a fixed order.
+// Every sum runs in a fixed order, so results are reproducible.
+struct XPass {
+    const XDst* dsts;
+    const XSrc* srcs;
+    const cd* vec;
+    const QuadX* qx;
+    int nq, nd, nch, w;   // families, reaction-centre destinations, chunks of w outputs per destination
+    int fch, fr;          // warps per family, rounds of 32 (n, s) pairs per warp
+    int pS, pD;           // the families' source and destination orders
+    int down, accumulate; // L2L; add into the destinations (M2M always writes)
+    int64_t ncoef, nslotcoef;
+    cd *X, *Xp;
+};
+// dynamic shared memory of a pass: a destination CTA's 128 partial sums, or (M2M) the
+// 4 transformed source vectors of each warp's family
+inline size_t xpass_smem(int down, int pS) {
+    return sizeof(cd) * (size_t)std::max(128, down ? 0 : 16 * (2 * pS + 1));
+}
+__device__ __forceinline__ void translate_dst(int di, int chunk, const XPass& P, int col0, int col1, cd* red) {
+    const XDst d = P.dsts[di];
+    const int w = P.w, ns = 128 / w;
     const int lane = threadIdx.x % w, sl = threadIdx.x / w;
     const int idx = chunk * w + lane;
     const int ncD = 2 * d.p + 1;
@@ -335,10 +360,10 @@ __device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __r
         cd a = mk(0, 0);
         if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
-                const XSrc sr = srcs[j];
-                const cd* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
+                const XSrc sr = P.srcs[j];
+                const cd* src = (sr.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + sr.off;
                 // V[n - m + hw] with n = idx - pD, m = mi - pS, hw = pS + pD
-                const cd* Vb = vec + sr.vec_off + idx + 2 * sr.p;
+                const cd* Vb = P.vec + sr.vec_off + idx + 2 * sr.p;
                 const int ncS = 2 * sr.p + 1;
                 for (int mi = sl; mi < ncS; mi += ns) cfma(a, src[mi], Vb[-mi]);
             }
@@ -348,20 +373,155 @@ __device__ __forceinline__ void translate_dst(int di, int chunk, const XDst* __r
         if (sl == 0 && idx < ncD) {
             cd t = red[lane];
             for (int q = 1; q < ns; ++q) t += red[q * w + lane];
-            cd* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
-            if (accumulate) *dst += t;
+            cd* dst = (d.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + d.off + idx;
+            if (P.accumulate) *dst += t;
             else *dst = t;
         }
         __syncthreads();
     }
 }
-__global__ void __launch_bounds__(128) k_translate(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
-                                                   const cd* __restrict__ vec, int accumulate, int w, int nrhs,
-                                                   int64_t ncoef, int64_t nslotcoef, cd* X, cd* Xp) {
+
+__device__ __forceinline__ cd mul_i(cd v) { return mk(-v.y, v.x); }   // i v
+__device__ __forceinline__ cd shfl_xor_cd(cd v, int m) {
+    return mk(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+// sum over the 4 lanes of an output, the same value and order in each
+__device__ __forceinline__ cd quad_lane_sum(cd a) {
+    a += shfl_xor_cd(a, 1);
+    return a + shfl_xor_cd(a, 2);
+}
+
+// M2M of one family, warp part `chunk`: the parent's multipole from its children's.
+// S: this warp's 4 (2 pS + 1) shared values.  Each lane runs two rounds at once
+// (outputs ni and ni + 8, the same residue class of m).
+__device__ __forceinline__ void fam_up(int fam, int chunk, const XPass& P, int col0, int col1, cd* S) {
+    const QuadX f = P.qx[fam];
+    const int lane = threadIdx.x & 31, s = lane & 3;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const cd z = mk(0, 0);
+    for (int col = col0; col < col1; ++col) {
+        const cd* Xc = P.X + (int64_t)col * P.ncoef;
+        __syncwarp();
+        for (int mi = lane; mi < ncS; mi += 32) {
+            // om_q = 1, -i, -1, i for the quadrants 3, 2, 0, 1
+            const cd m0 = f.ch[0] >= 0 ? Xc[f.ch[0] + mi] : z, m1 = f.ch[1] >= 0 ? Xc[f.ch[1] + mi] : z;
+            const cd m2 = f.ch[2] >= 0 ? Xc[f.ch[2] + mi] : z, m3 = f.ch[3] >= 0 ? Xc[f.ch[3] + mi] : z;
+            const cd u = m3 + m0, v = m2 + m1, x = m3 - m0, iy = mul_i(m2 - m1);
+            S[mi] = u + v;
+            S[ncS + mi] = x - iy;
+            S[2 * ncS + mi] = u - v;
+            S[3 * ncS + mi] = x + iy;
+        }
+        __syncwarp();
+        const cd* Ss = S + s * ncS;
+        for (int k = 0; k < P.fr; k += 2) {
+            const int ni = (((chunk * P.fr + k) << 5) + lane) >> 2;   // output index; ni + 8 in round k + 1
+            const bool two = k + 1 < P.fr;
+            cd a = z, a2 = z;
+            if (ni < ncD) {
+                // (n - m) = (ni - pD) - (mi - pS) = s (mod 4); B[n - m + hw] = Vb[-mi]
+                const cd* Vb = P.vec + f.vup + ni + 2 * P.pS;
+                const int mi0 = (ni - P.pD + P.pS - s) & 3;
+                if (two) {
+                    // past the last output the second sum reads the last one's terms (not stored),
+                    // so every lane runs the same loop
+                    const cd* Vb2 = Vb + min(8, ncD - 1 - ni);
+                    for (int mi = mi0; mi < ncS; mi += 4) {
+                        const cd sv = Ss[mi];
+                        cfma(a, sv, Vb[-mi]);
+                        cfma(a2, sv, Vb2[-mi]);
+                    }
+                } else {
+                    for (int mi = mi0; mi < ncS; mi += 4) cfma(a, Ss[mi], Vb[-mi]);
+                }
+            }
+            a = quad_lane_sum(a);
+            if (s == 0 && ni < ncD) P.X[(int64_t)col * P.ncoef + f.par + ni] = a;
+            if (two) {
+                a2 = quad_lane_sum(a2);
+                if (s == 0 && ni + 8 < ncD) P.X[(int64_t)col * P.ncoef + f.par + ni + 8] = a2;
+            }
+        }
+    }
+}
+
+// lane s's child after the L2L transform (quadrant 3, 0, 2, 1 for s = 0, 1, 2, 3): from
+// the residue sums T_s of one output, conj(om_q) = 1, i, -1, -i for the quadrants
+// 3, 2, 0, 1:  e = T0 + T2, g = T1 + T3, h = T0 - T2, k = T1 - T3, then
+// q3 = e + g, q0 = e - g, q2 = h + i k, q1 = h - i k
+__device__ __forceinline__ cd quad_lane_transform(cd a, int s) {
+    const cd o2 = shfl_xor_cd(a, 2);
+    const cd b = (s < 2) ? a + o2 : o2 - a;
+    const cd o1 = shfl_xor_cd(b, 1);
+    return (s == 0) ? b + o1 : (s == 1) ? o1 - b : (s == 2) ? b + mul_i(o1) : o1 - mul_i(b);
+}
+
+// L2L of one family, warp part `chunk`: the children's locals from the parent's (the
+// children in dn_skip are destinations of their own)
+__device__ __forceinline__ void fam_dn(int fam, int chunk, const XPass& P, int col0, int col1) {
+    const QuadX f = P.qx[fam];
+    const int lane = threadIdx.x & 31, s = lane & 3;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const int q = (0x1203 >> (4 * s)) & 15;   // the child lane s holds after the transform
+    const int64_t chq = ((f.dn_skip >> q) & 1) ? -1 : P.qx[fam].ch[q];
+    const cd z = mk(0, 0);
+    for (int col = col0; col < col1; ++col) {
+        const cd* src = P.X + (int64_t)col * P.ncoef + f.par;
+        cd* Xc = P.X + (int64_t)col * P.ncoef + chq;
+        for (int k = 0; k < P.fr; k += 2) {
+            const int ni = (((chunk * P.fr + k) << 5) + lane) >> 2;
+            const bool two = k + 1 < P.fr;
+            cd a = z, a2 = z;
+            if (ni < ncD) {
+                // (m - n) = (mi - pS) - (ni - pD) = s (mod 4); C_{m-n} = Vb[-mi]
+                const cd* Vb = P.vec + f.vdn + ni + 2 * P.pS;
+                const int mi0 = (ni - P.pD + P.pS + s) & 3;
+                if (two) {
+                    const cd* Vb2 = Vb + min(8, ncD - 1 - ni);   // as fam_up
+                    for (int mi = mi0; mi < ncS; mi += 4) {
+                        const cd sv = src[mi];
+                        cfma(a, sv, Vb[-mi]);
+                        cfma(a2, sv, Vb2[-mi]);
+                    }
+                } else {
+                    for (int mi = mi0; mi < ncS; mi += 4) cfma(a, src[mi], Vb[-mi]);
+                }
+            }
+            const cd out = quad_lane_transform(a, s);
+            if (ni < ncD && chq >= 0) {
+                if (P.accumulate) Xc[ni] += out;
+                else Xc[ni] = out;
+            }
+            if (two) {
+                const cd out2 = quad_lane_transform(a2, s);
+                if (ni + 8 < ncD && chq >= 0) {
+                    if (P.accumulate) Xc[ni + 8] += out2;
+                    else Xc[ni + 8] = out2;
+                }
+            }
+        }
+    }
+}
+
+// CTA b of a pass: family warps first (4 per CTA), then reaction-centre destinations
+__device__ __forceinline__ void translate_item(int b, const XPass& P, int col0, int col1, cd* sm) {
+    const int fb = xpass_fam_ctas(P.nq, P.fch);
+    if (b < fb) {
+        const int gw = b * 4 + (threadIdx.x >> 5);
+        if (gw >= P.nq * P.fch) return;   // whole warps; the family work has no CTA barrier
+        if (P.down) fam_dn(gw / P.fch, gw % P.fch, P, col0, col1);
+        else fam_up(gw / P.fch, gw % P.fch, P, col0, col1, sm + (threadIdx.x >> 5) * 4 * (2 * P.pS + 1));
+    } else {
+        b -= fb;
+        translate_dst(b / P.nch, b % P.nch, P, col0, col1, sm);
+    }
+}
+__global__ void __launch_bounds__(128) k_translate(const XPass P, int nrhs) {
+    extern __shared__ cd xsm[];
     // blockIdx.z: a group of columns (the columns of a block right-hand side split over CTAs)
     const int cpb = (nrhs + gridDim.z - 1) / gridDim.z;
     const int col0 = blockIdx.z * cpb, col1 = min(nrhs, col0 + cpb);
-    translate_dst(blockIdx.x, blockIdx.y, dsts, srcs, vec, accumulate, w, col0, col1, ncoef, nslotcoef, X, Xp);
+    translate_item(blockIdx.x, P, col0, col1, xsm);
 }
 
 // Reaction M2L moment tables of components whose source and field layers are the

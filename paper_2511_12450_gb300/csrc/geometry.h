@@ -8,6 +8,7 @@
 #include <mutex>
 #include <cstdint>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "lfmm_internal.h"
@@ -75,6 +76,17 @@ struct XSrc {
     int p;                // source order
     int in_slots;
 };
+// A parent cell and its children about cell centres: the quadrant form of M2M and
+// L2L (k_translate).  Children are stored by quadrant (ix & 1) | ((iy & 1) << 1); the
+// quadrant-3 child (+w/2, +w/2) carries the base vectors.  A child that also takes a
+// straddling parent's reaction-centre local is an L2L destination of its own (dn_skip).
+struct QuadX {
+    int64_t par;          // parent's coefficient offset
+    int64_t ch[4];        // children's coefficient offsets by quadrant (-1: no child)
+    int64_t vup, vdn;     // base vectors of the family's layer and level (M2M; L2L reversed)
+    int lay;              // the family's layer
+    int dn_skip;          // bit q: the L2L of child q is a destination of its own
+};
 // M2L work: XT_W output coefficients of one target box over a range of its
 // list entries; part >= 0 sends the partial sums to the reduction buffer.
 #define XT_W 16
@@ -97,6 +109,18 @@ inline int lane_width(int nco) {
     const double uf = (double)(nco * (128 / nco)) / 128.0;
     return (uf > u16 + 0.02) ? nco : XT_W;
 }
+// CTAs (4 warps) of a pass's families
+__host__ __device__ inline int xpass_fam_ctas(int nq, int fch) { return (nq * fch + 3) / 4; }
+// warps per family and rounds per warp: whole families per warp when there are enough
+// of them to fill the GPU (16 warps per SM), else each family split over more warps
+inline void xpass_fam_split(int nq, int pD, int* fch, int* fr) {
+    const int rounds = (4 * (2 * pD + 1) + 31) / 32;
+    const int want = nq > 0 ? (152 * 16 + nq - 1) / nq : 1;
+    const int ch = std::max(1, std::min(rounds, want));
+    *fr = (rounds + ch - 1) / ch;
+    *fch = (rounds + *fr - 1) / *fr;
+}
+
 // one list entry of a target box
 // M2L_FLIP: the table is that of the mirrored pair (offset -X), read with both
 // indices reversed
@@ -181,6 +205,11 @@ struct lfmm_geometry_s {
     // M2M (up) and L2L (down) passes: per level, a range of destinations
     // (cells and reaction centres) with their sources and translation vectors
     std::vector<int> up_begin, up_end, dn_begin, dn_end;
+    // parent/child cell families per child level (q_begin[l]..q_end[l]: parents at l - 1)
+    std::vector<int> q_begin, q_end;
+    lfmm::QuadX* d_qx = nullptr;
+    std::vector<lfmm::QuadX> qx_host;
+    std::vector<int64_t> qvec_host;   // base vector per ((layer nlev + child level) 2 + down), -1: none
     lfmm::XDst* d_xdst = nullptr;
     lfmm::XSrc* d_xsrc = nullptr;
     cd* d_xvec = nullptr;

@@ -69,6 +69,13 @@ struct MixedState {
     cf* wtab = nullptr;                 // dense scaled M2M / L2L tables of the FP32 passes
     int64_t* wtab_off = nullptr;        // per XSrc (-1 outside the FP32 passes)
     int* d_xd_layer = nullptr;          // layer per XDst
+    // cell families: base table per ((child level 2 + down) nl + layer), and the records
+    // k_xtab32 builds them from
+    int64_t* qoff = nullptr;
+    XDst* q_bd = nullptr;
+    XSrc* q_bs = nullptr;
+    int* q_blay = nullptr;
+    int64_t* q_bwoff = nullptr;
     size_t smem_p2m = 0, smem_l2p = 0;
     size_t bytes = 0;
     // block right-hand-side M2L on the tensor cores (m2l_tc.cuh)
@@ -445,29 +452,41 @@ __global__ void __launch_bounds__(128) k_l2p32(const ExpGroup* __restrict__ grou
     }
 }
 
-// M2M / L2L in FP32 on scaled expansions: out_n (= or +=) sum_j sum_m src_j[m] W_j[m][n],
-// W_j dense (column-major, (n, m) at m ncD + n) with the scale factors folded in.
-// GROUPS: the columns split over blockIdx.z in groups of four (col_groups); otherwise every
-// CTA walks all columns (the single-column form keeps its registers)
-template <bool GROUPS>
-__global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ dsts, const XSrc* __restrict__ srcs,
-                        const int64_t* __restrict__ wtab_off, const cf* __restrict__ wtab, int accumulate, int w,
-                        int nrhs, int64_t ncoef, int64_t nslotcoef, cf* X, cf* Xp) {
-    __shared__ cf red[128];
-    const XDst d = dsts[blockIdx.x];
-    const int ns = 128 / w;
+// M2M / L2L in FP32 on scaled expansions, one launch per level and pass over the same
+// two kinds of work item as the FP64 pass (k_translate): cell families in the quadrant
+// form, with the base table W_B of the family's layer, and reaction-centre destinations,
+//   out_n (= or +=) sum_j sum_m src_j[m] W_j[m][n].
+// The tables are dense (column-major, (n, m) at m ncD + n) with the scale factors folded
+// in.  The factors depend on |m| and |n| only, so the quadrant phases factor out of the
+// scaled tables as they do of the vectors.
+struct XPass32 {
+    const XDst* dsts;
+    const XSrc* srcs;
+    const int64_t* wtab_off;   // per XSrc
+    const cf* wtab;
+    const QuadX* qx;
+    const int64_t* qoff;       // base table of each layer (this level and pass)
+    int nq, nd, nch, w, fch, fr, pS, pD, down, accumulate;
+    int64_t ncoef, nslotcoef;
+    cf *X, *Xp;
+};
+__device__ __forceinline__ cf subf(cf a, cf b) { return mkf(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cf mul_if(cf v) { return mkf(-v.y, v.x); }   // i v
+
+__device__ __forceinline__ void translate32_dst(int di, int chunk, const XPass32& P, int col0, int col1, cf* red) {
+    const XDst d = P.dsts[di];
+    const int w = P.w, ns = 128 / w;
     const int lane = threadIdx.x % w, sl = threadIdx.x / w;
-    const int idx = blockIdx.y * w + lane;
+    const int idx = chunk * w + lane;
     const int ncD = 2 * d.p + 1;
     const bool live = sl < ns && idx < ncD;
-    const int col0 = GROUPS ? blockIdx.z * 4 : 0, col1 = GROUPS ? min(nrhs, col0 + 4) : nrhs;
     for (int col = col0; col < col1; ++col) {
         cf a = mkf(0, 0);
         if (live) {
             for (int j = d.src_begin; j < d.src_end; ++j) {
-                const XSrc sr = srcs[j];
-                const cf* src = (sr.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + sr.off;
-                const cf* W = wtab + wtab_off[j] + idx;
+                const XSrc sr = P.srcs[j];
+                const cf* src = (sr.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + sr.off;
+                const cf* W = P.wtab + P.wtab_off[j] + idx;
                 const int ncS = 2 * sr.p + 1;
                 for (int mi = sl; mi < ncS; mi += ns) cfmaf(a, src[mi], W[mi * ncD]);
             }
@@ -477,11 +496,132 @@ __global__ void __launch_bounds__(128) k_translate32(const XDst* __restrict__ ds
         if (sl == 0 && idx < ncD) {
             cf t = red[lane];
             for (int q = 1; q < ns; ++q) t = addf(t, red[q * w + lane]);
-            cf* dst = (d.in_slots ? Xp + (int64_t)col * nslotcoef : X + (int64_t)col * ncoef) + d.off + idx;
-            if (accumulate) *dst = addf(*dst, t);
+            cf* dst = (d.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + d.off + idx;
+            if (P.accumulate) *dst = addf(*dst, t);
             else *dst = t;
         }
         __syncthreads();
+    }
+}
+
+__device__ __forceinline__ cf shfl_xor_cf(cf v, int m) {
+    return mkf(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// the FP32 family passes: the warp design of fam_up / fam_dn (two rounds per lane at
+// once) with the base table W_B (W_B[m][n] at m ncD + n) in place of the base vector
+__device__ __forceinline__ void fam_up32(int fam, int chunk, const XPass32& P, int col0, int col1, cf* S) {
+    const QuadX f = P.qx[fam];
+    const int lane = threadIdx.x & 31, s = lane & 3;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const cf* W = P.wtab + P.qoff[f.lay];
+    const cf z = mkf(0, 0);
+    for (int col = col0; col < col1; ++col) {
+        const cf* Xc = P.X + (int64_t)col * P.ncoef;
+        __syncwarp();
+        for (int mi = lane; mi < ncS; mi += 32) {
+            // om_q = 1, -i, -1, i for the quadrants 3, 2, 0, 1
+            const cf m0 = f.ch[0] >= 0 ? Xc[f.ch[0] + mi] : z, m1 = f.ch[1] >= 0 ? Xc[f.ch[1] + mi] : z;
+            const cf m2 = f.ch[2] >= 0 ? Xc[f.ch[2] + mi] : z, m3 = f.ch[3] >= 0 ? Xc[f.ch[3] + mi] : z;
+            const cf u = addf(m3, m0), v = addf(m2, m1), x = subf(m3, m0), iy = mul_if(subf(m2, m1));
+            S[mi] = addf(u, v);
+            S[ncS + mi] = subf(x, iy);
+            S[2 * ncS + mi] = subf(u, v);
+            S[3 * ncS + mi] = addf(x, iy);
+        }
+        __syncwarp();
+        const cf* Ss = S + s * ncS;
+        for (int k = 0; k < P.fr; k += 2) {
+            const int ni = (((chunk * P.fr + k) << 5) + lane) >> 2;
+            const bool two = k + 1 < P.fr;
+            cf a = z, a2 = z;
+            if (ni < ncD) {
+                const int mi0 = (ni - P.pD + P.pS - s) & 3;
+                if (two) {
+                    const int ni2 = min(ni + 8, ncD - 1);   // past the last output: not stored (as fam_up)
+                    for (int mi = mi0; mi < ncS; mi += 4) {
+                        const cf sv = Ss[mi];
+                        cfmaf(a, sv, W[mi * ncD + ni]);
+                        cfmaf(a2, sv, W[mi * ncD + ni2]);
+                    }
+                } else {
+                    for (int mi = mi0; mi < ncS; mi += 4) cfmaf(a, Ss[mi], W[mi * ncD + ni]);
+                }
+            }
+            a = addf(a, shfl_xor_cf(a, 1));
+            a = addf(a, shfl_xor_cf(a, 2));
+            if (s == 0 && ni < ncD) P.X[(int64_t)col * P.ncoef + f.par + ni] = a;
+            if (two) {
+                a2 = addf(a2, shfl_xor_cf(a2, 1));
+                a2 = addf(a2, shfl_xor_cf(a2, 2));
+                if (s == 0 && ni + 8 < ncD) P.X[(int64_t)col * P.ncoef + f.par + ni + 8] = a2;
+            }
+        }
+    }
+}
+
+// the lane transform of fam_dn (quad_lane_transform) in FP32
+__device__ __forceinline__ cf quad_lane_transform32(cf a, int s) {
+    const cf o2 = shfl_xor_cf(a, 2);
+    const cf b = (s < 2) ? addf(a, o2) : subf(o2, a);
+    const cf o1 = shfl_xor_cf(b, 1);
+    return (s == 0) ? addf(b, o1) : (s == 1) ? subf(o1, b) : (s == 2) ? addf(b, mul_if(o1)) : subf(o1, mul_if(b));
+}
+
+__device__ __forceinline__ void fam_dn32(int fam, int chunk, const XPass32& P, int col0, int col1) {
+    const QuadX f = P.qx[fam];
+    const int lane = threadIdx.x & 31, s = lane & 3;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const int q = (0x1203 >> (4 * s)) & 15;   // the child lane s holds after the transform
+    const int64_t chq = ((f.dn_skip >> q) & 1) ? -1 : P.qx[fam].ch[q];
+    const cf* W = P.wtab + P.qoff[f.lay];
+    const cf z = mkf(0, 0);
+    for (int col = col0; col < col1; ++col) {
+        const cf* src = P.X + (int64_t)col * P.ncoef + f.par;
+        cf* Xc = P.X + (int64_t)col * P.ncoef + chq;
+        for (int k = 0; k < P.fr; k += 2) {
+            const int ni = (((chunk * P.fr + k) << 5) + lane) >> 2;
+            const bool two = k + 1 < P.fr;
+            cf a = z, a2 = z;
+            if (ni < ncD) {
+                const int mi0 = (ni - P.pD + P.pS + s) & 3;
+                if (two) {
+                    const int ni2 = min(ni + 8, ncD - 1);
+                    for (int mi = mi0; mi < ncS; mi += 4) {
+                        const cf sv = src[mi];
+                        cfmaf(a, sv, W[mi * ncD + ni]);
+                        cfmaf(a2, sv, W[mi * ncD + ni2]);
+                    }
+                } else {
+                    for (int mi = mi0; mi < ncS; mi += 4) cfmaf(a, src[mi], W[mi * ncD + ni]);
+                }
+            }
+            const cf out = quad_lane_transform32(a, s);
+            if (ni < ncD && chq >= 0) Xc[ni] = P.accumulate ? addf(Xc[ni], out) : out;
+            if (two) {
+                const cf out2 = quad_lane_transform32(a2, s);
+                if (ni + 8 < ncD && chq >= 0) Xc[ni + 8] = P.accumulate ? addf(Xc[ni + 8], out2) : out2;
+            }
+        }
+    }
+}
+
+// GROUPS: the columns split over blockIdx.z in groups of four (col_groups); otherwise every
+// CTA walks all columns (the single-column form keeps its registers)
+template <bool GROUPS>
+__global__ void __launch_bounds__(128) k_translate32(const XPass32 P, int nrhs) {
+    extern __shared__ cf xsm32[];
+    const int col0 = GROUPS ? blockIdx.z * 4 : 0, col1 = GROUPS ? min(nrhs, col0 + 4) : nrhs;
+    int b = blockIdx.x;
+    const int fb = xpass_fam_ctas(P.nq, P.fch);
+    if (b < fb) {
+        const int gw = b * 4 + (threadIdx.x >> 5);
+        if (gw >= P.nq * P.fch) return;   // whole warps; the family work has no CTA barrier
+        if (P.down) fam_dn32(gw / P.fch, gw % P.fch, P, col0, col1);
+        else fam_up32(gw / P.fch, gw % P.fch, P, col0, col1, xsm32 + (threadIdx.x >> 5) * 4 * (2 * P.pS + 1));
+    } else {
+        b -= fb;
+        translate32_dst(b / P.nch, b % P.nch, P, col0, col1, xsm32);
     }
 }
 
@@ -791,6 +931,8 @@ void mixed_destroy(lfmm_geometry_s* g) {
     dev_release(ms->ispow); dev_release(ms->ispow_slot); dev_release(ms->ftab); dev_release(ms->ftab_off);
     dev_release(ms->rtab); dev_release(ms->d_scale); dev_release(ms->wtab); dev_release(ms->wtab_off);
     dev_release(ms->d_xd_layer);
+    dev_release(ms->qoff); dev_release(ms->q_bd); dev_release(ms->q_bs); dev_release(ms->q_blay);
+    dev_release(ms->q_bwoff);
     dev_release(ms->tc_boxes); dev_release(ms->tc_ent_ptr); dev_release(ms->tc_err);
     if (ms->tc_err_host) cudaFreeHost(ms->tc_err_host);
     delete ms;
@@ -988,6 +1130,29 @@ static void mixed_build(lfmm_geometry_s* g) {
     };
     for (int lp = D - 1; lp >= ms->lm; --lp) plan(g->up_begin[lp], g->up_end[lp]);
     for (int l = ms->lm + 1; l <= D; ++l) plan(g->dn_begin[l], g->dn_end[l]);
+    // cell families of the FP32 passes (child levels lm + 1 .. D): a base table per
+    // (level, pass, layer), record i = ((l - lm - 1) 2 + down) nl + layer
+    std::vector<XDst> bd;
+    std::vector<XSrc> bs;
+    std::vector<int> blay;
+    std::vector<int64_t> bwoff, qoff((size_t)(nlev + 1) * 2 * nl, -1);
+    for (int l = ms->lm + 1; l <= D; ++l)
+        for (int down = 0; down < 2; ++down)
+            for (int lay = 0; lay < nl; ++lay) {
+                const int pS = down ? t.p_level[l - 1] : t.p_level[l], pD = down ? t.p_level[l] : t.p_level[l - 1];
+                const int i = (int)bd.size();
+                bd.push_back(XDst{0, pD, 0, i, i + 1});
+                bs.push_back(XSrc{0, g->qvec_host[(size_t)(lay * nlev + l) * 2 + down], pS, 0});
+                blay.push_back(lay);
+                bwoff.push_back(wtot);
+                qoff[(size_t)(l * 2 + down) * nl + lay] = wtot;
+                wtot += (int64_t)(2 * pD + 1) * (2 * pS + 1);
+            }
+    ms->qoff = upload_raw(qoff, ms->bytes);
+    ms->q_bd = upload_raw(bd, ms->bytes);
+    ms->q_bs = upload_raw(bs, ms->bytes);
+    ms->q_blay = upload_raw(blay, ms->bytes);
+    ms->q_bwoff = upload_raw(bwoff, ms->bytes);
     ms->wtab_off = upload_raw(woff, ms->bytes);
     cuda_check(cudaMallocAsync((void**)&ms->wtab, sizeof(cf) * std::max<int64_t>(wtot, 1), cudaStreamPerThread),
                "cudaMallocAsync pass tables 32");
@@ -1003,7 +1168,13 @@ static void mixed_build(lfmm_geometry_s* g) {
         if (nd > 0)
             k_xtab32<<<nd, 256>>>(g->d_xdst + g->dn_begin[l], g->d_xsrc, ms->d_xd_layer + g->dn_begin[l], g->d_xvec,
                                   ms->d_scale, nlev, l - 1, l, 1, ms->wtab_off, ms->wtab);
+        for (int down = 0; down < 2; ++down) {
+            const int b0 = ((l - ms->lm - 1) * 2 + down) * nl;
+            k_xtab32<<<nl, 256>>>(ms->q_bd + b0, ms->q_bs, ms->q_blay + b0, g->d_xvec, ms->d_scale, nlev,
+                                  down ? l - 1 : l, down ? l : l - 1, down, ms->q_bwoff, ms->wtab);
+        }
     }
+    cuda_check(cudaGetLastError(), "k_xtab32");
     // shared memory of the FP32 P2M / L2P (all entries at the leaf order)
     const int pD = t.p_level[D], gp = g->group_max_pts, ge = g->group_max_ent;
     const int rs_p2m = g->combined ? 2 * pD + 3 : pD + 1;   // basis row length (k_p2m32)
@@ -1066,32 +1237,53 @@ void mixed_p2m(lfmm_geometry_s* g, const cd* x_sorted, int nrhs, cudaStream_t s)
     }
 }
 
-static void pass32(lfmm_geometry_s* g, int b0, int b1, int p_dst, int accumulate, int nrhs, cf* X, cf* Xp,
-                   cudaStream_t s) {
-    const int nd = b1 - b0;
-    if (nd == 0) return;
+// one FP32 level pass: M2M into the parents at level - 1 (down = 0) or L2L into the
+// children at level (down = 1)
+static void pass32(lfmm_geometry_s* g, int level, int down, int nrhs, cudaStream_t s) {
+    MixedState* ms = g->mixed;
+    const TreeHost& t = g->tree;
+    XPass32 P;
+    P.dsts = g->d_xdst + (down ? g->dn_begin[level] : g->up_begin[level - 1]);
+    P.srcs = g->d_xsrc;
+    P.wtab_off = ms->wtab_off;
+    P.wtab = ms->wtab;
+    P.qx = g->d_qx + g->q_begin[level];
+    P.qoff = ms->qoff + (size_t)(level * 2 + down) * g->m.nl;
+    P.nq = g->q_end[level] - g->q_begin[level];
+    P.nd = down ? g->dn_end[level] - g->dn_begin[level] : g->up_end[level - 1] - g->up_begin[level - 1];
+    P.pS = down ? t.p_level[level - 1] : t.p_level[level];
+    P.pD = down ? t.p_level[level] : t.p_level[level - 1];
     // FP32 translations are not bound by an arithmetic pipe: 16-lane chunks (more CTAs)
     // measured faster here than rows as wide as the coefficient count
-    const int nco = 2 * p_dst + 1, w = XT_W;
+    const int nco = 2 * P.pD + 1;
+    P.w = XT_W;
+    P.nch = (nco + P.w - 1) / P.w;
+    xpass_fam_split(P.nq, P.pD, &P.fch, &P.fr);
+    P.down = down;
+    P.accumulate = down;   // M2M writes, L2L adds to the FP32 M2L's locals
+    P.ncoef = g->ncoef;
+    P.nslotcoef = g->nslotcoef;
+    P.X = down ? ms->L : ms->M;
+    P.Xp = down ? ms->Lp : ms->Mp;
+    const int items = xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch;
+    if (items == 0) return;
+    const size_t smem = sizeof(cf) * (size_t)std::max(128, down ? 0 : 16 * (2 * P.pS + 1));
     const int ng = col_groups(nrhs);
-    dim3 grid(nd, (nco + w - 1) / w, ng);
-    if (ng > 1)
-        k_translate32<true><<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab,
-                                                 accumulate, w, nrhs, g->ncoef, g->nslotcoef, X, Xp);
-    else
-        k_translate32<false><<<grid, 128, 0, s>>>(g->d_xdst + b0, g->d_xsrc, g->mixed->wtab_off, g->mixed->wtab,
-                                                  accumulate, w, nrhs, g->ncoef, g->nslotcoef, X, Xp);
+    dim3 grid(items, 1, ng);
+    if (ng > 1) {
+        raise_smem_limit((const void*)k_translate32<true>, smem, "translate32 smem");
+        k_translate32<true><<<grid, 128, smem, s>>>(P, nrhs);
+    } else {
+        raise_smem_limit((const void*)k_translate32<false>, smem, "translate32 smem");
+        k_translate32<false><<<grid, 128, smem, s>>>(P, nrhs);
+    }
     cuda_check(cudaGetLastError(), "k_translate32");
     ++g->n_launches;
 }
 
-void mixed_m2m(lfmm_geometry_s* g, int lp, int nrhs, cudaStream_t s) {
-    pass32(g, g->up_begin[lp], g->up_end[lp], g->tree.p_level[lp], 0, nrhs, g->mixed->M, g->mixed->Mp, s);
-}
+void mixed_m2m(lfmm_geometry_s* g, int lp, int nrhs, cudaStream_t s) { pass32(g, lp + 1, 0, nrhs, s); }
 
-void mixed_l2l(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
-    pass32(g, g->dn_begin[l], g->dn_end[l], g->tree.p_level[l], 1, nrhs, g->mixed->L, g->mixed->Lp, s);
-}
+void mixed_l2l(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) { pass32(g, l, 1, nrhs, s); }
 
 
 void mixed_m_to64(lfmm_geometry_s* g, int l, int nrhs, cudaStream_t s) {
