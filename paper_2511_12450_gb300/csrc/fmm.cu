@@ -666,7 +666,7 @@ static XPass make_pass(lfmm_geometry_s* g, int level, int down, int accumulate, 
 static void launch_pass(lfmm_geometry_s* g, const XPass& P, int nrhs, cudaStream_t s, const char* what) {
     const int items = xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch;
     if (items == 0) return;
-    const size_t smem = xpass_smem(P.down, P.pS);
+    const size_t smem = xpass_smem(P.down, P.pS, P.pD, P.w);
     raise_smem_limit((const void*)k_translate, smem, "translate smem");
     k_translate<<<dim3(items, 1, col_groups(nrhs)), 128, smem, s>>>(P, nrhs);
     cuda_check(cudaGetLastError(), what);
@@ -942,7 +942,7 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
             const XPass P = make_pass(g, lp + 1, 0, 0, op->nrhs);
             jobs.push_back(XJob{P, op->nrhs});
             blocks.push_back(xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch);
-            smem = std::max(smem, xpass_smem(0, P.pS));
+            smem = std::max(smem, xpass_smem(0, P.pS, P.pD, P.w));
         }
         raise_smem_limit((const void*)k_translate_multi, smem, "translate smem");
         launch_jobs(jobs, blocks, k_translate_multi, 128, smem, s, "k_translate_multi (M2M)");
@@ -967,6 +967,7 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
     for (int k = 0; k < max_dn; ++k) {
         std::vector<XJob> jobs;
         std::vector<int> blocks;
+        size_t smem = 0;
         for (const BatchOp* op : far) {
             lfmm_geometry_s* g = op->g;
             const TreeHost& t = g->tree;
@@ -975,8 +976,10 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
             const XPass P = make_pass(g, l, 1, 1, op->nrhs);
             jobs.push_back(XJob{P, op->nrhs});
             blocks.push_back(xpass_fam_ctas(P.nq, P.fch) + P.nd * P.nch);
+            smem = std::max(smem, xpass_smem(1, P.pS, P.pD, P.w));
         }
-        launch_jobs(jobs, blocks, k_translate_multi, 128, xpass_smem(1, 0), s, "k_translate_multi (L2L)");
+        raise_smem_limit((const void*)k_translate_multi, smem, "translate smem");
+        launch_jobs(jobs, blocks, k_translate_multi, 128, smem, s, "k_translate_multi (L2L)");
     }
     // L2P after the near field, which adds into the same y
     if (before_l2p) cuda_check(cudaStreamWaitEvent(s, before_l2p, 0), "wait for the near field");

@@ -344,29 +344,41 @@ struct XPass {
     int64_t ncoef, nslotcoef;
     cd *X, *Xp;
 };
-// dynamic shared memory of a pass: a destination CTA's 128 partial sums, or (M2M) the
-// 4 transformed source vectors of each warp's family
-inline size_t xpass_smem(int down, int pS) {
-    return sizeof(cd) * (size_t)std::max(128, down ? 0 : 16 * (2 * pS + 1));
+// dynamic shared memory of a pass (complex values): per family warp (4 per CTA) its base
+// vector and (M2M) the 4 transformed source vectors or (L2L) the parent's local; per
+// reaction-centre CTA the 128 partial sums, one source and the window of its vector
+inline size_t xpass_smem(int down, int pS, int pD, int w) {
+    const int ncS = 2 * pS + 1, nv = 2 * (pS + pD) + 1;
+    const int fam = 4 * ((down ? ncS : 4 * ncS) + nv);
+    const int dst = 128 + ncS + w + 2 * pS;
+    return sizeof(cd) * (size_t)std::max(fam, dst);
 }
-__device__ __forceinline__ void translate_dst(int di, int chunk, const XPass& P, int col0, int col1, cd* red) {
+
+__device__ __forceinline__ void translate_dst(int di, int chunk, const XPass& P, int col0, int col1, cd* sm) {
     const XDst d = P.dsts[di];
     const int w = P.w, ns = 128 / w;
     const int lane = threadIdx.x % w, sl = threadIdx.x / w;
     const int idx = chunk * w + lane;
-    const int ncD = 2 * d.p + 1;
+    const int ncD = 2 * d.p + 1, ncS = 2 * P.pS + 1;   // every source of a pass has the order pS
     const bool live = sl < ns && idx < ncD;
+    cd* red = sm;
+    cd* xs = sm + 128;          // the source
+    cd* vs = xs + ncS;          // V[chunk w .. chunk w + w - 1 + 2 pS] (n - m + hw over this chunk)
+    const int nv = w + 2 * P.pS;
     for (int col = col0; col < col1; ++col) {
         cd a = mk(0, 0);
-        if (live) {
-            for (int j = d.src_begin; j < d.src_end; ++j) {
-                const XSrc sr = P.srcs[j];
-                const cd* src = (sr.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + sr.off;
-                // V[n - m + hw] with n = idx - pD, m = mi - pS, hw = pS + pD
-                const cd* Vb = P.vec + sr.vec_off + idx + 2 * sr.p;
-                const int ncS = 2 * sr.p + 1;
-                for (int mi = sl; mi < ncS; mi += ns) cfma(a, src[mi], Vb[-mi]);
-            }
+        for (int j = d.src_begin; j < d.src_end; ++j) {
+            const XSrc sr = P.srcs[j];
+            const cd* src = (sr.in_slots ? P.Xp + (int64_t)col * P.nslotcoef : P.X + (int64_t)col * P.ncoef) + sr.off;
+            const cd* V = P.vec + sr.vec_off + chunk * w;
+            const int nvv = min(nv, 2 * (P.pS + d.p) + 1 - chunk * w);   // the vector's end
+            __syncthreads();
+            for (int i = threadIdx.x; i < ncS; i += blockDim.x) xs[i] = src[i];
+            for (int i = threadIdx.x; i < nvv; i += blockDim.x) vs[i] = V[i];
+            __syncthreads();
+            // V[n - m + hw] with n = idx - pD, m = mi - pS, hw = pS + pD: vs[lane + 2 pS - mi]
+            if (live)
+                for (int mi = sl; mi < ncS; mi += ns) cfma(a, xs[mi], vs[lane + 2 * P.pS - mi]);
         }
         if (sl < ns) red[sl * w + lane] = a;
         __syncthreads();
@@ -397,8 +409,10 @@ __device__ __forceinline__ cd quad_lane_sum(cd a) {
 __device__ __forceinline__ void fam_up(int fam, int chunk, const XPass& P, int col0, int col1, cd* S) {
     const QuadX f = P.qx[fam];
     const int lane = threadIdx.x & 31, s = lane & 3;
-    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1, nv = 2 * (P.pS + P.pD) + 1;
     const cd z = mk(0, 0);
+    cd* Bs = S + 4 * ncS;   // the base vector
+    for (int i = lane; i < nv; i += 32) Bs[i] = P.vec[f.vup + i];
     for (int col = col0; col < col1; ++col) {
         const cd* Xc = P.X + (int64_t)col * P.ncoef;
         __syncwarp();
@@ -420,7 +434,7 @@ __device__ __forceinline__ void fam_up(int fam, int chunk, const XPass& P, int c
             cd a = z, a2 = z;
             if (ni < ncD) {
                 // (n - m) = (ni - pD) - (mi - pS) = s (mod 4); B[n - m + hw] = Vb[-mi]
-                const cd* Vb = P.vec + f.vup + ni + 2 * P.pS;
+                const cd* Vb = Bs + ni + 2 * P.pS;
                 const int mi0 = (ni - P.pD + P.pS - s) & 3;
                 if (two) {
                     // past the last output the second sum reads the last one's terms (not stored),
@@ -458,15 +472,22 @@ __device__ __forceinline__ cd quad_lane_transform(cd a, int s) {
 
 // L2L of one family, warp part `chunk`: the children's locals from the parent's (the
 // children in dn_skip are destinations of their own)
-__device__ __forceinline__ void fam_dn(int fam, int chunk, const XPass& P, int col0, int col1) {
+// Sm: this warp's shared values, the parent's local then the base vector
+__device__ __forceinline__ void fam_dn(int fam, int chunk, const XPass& P, int col0, int col1, cd* Sm) {
     const QuadX f = P.qx[fam];
     const int lane = threadIdx.x & 31, s = lane & 3;
-    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1;
+    const int ncS = 2 * P.pS + 1, ncD = 2 * P.pD + 1, nv = 2 * (P.pS + P.pD) + 1;
     const int q = (0x1203 >> (4 * s)) & 15;   // the child lane s holds after the transform
     const int64_t chq = ((f.dn_skip >> q) & 1) ? -1 : P.qx[fam].ch[q];
     const cd z = mk(0, 0);
+    cd* src = Sm;
+    cd* Cs = Sm + ncS;
+    for (int i = lane; i < nv; i += 32) Cs[i] = P.vec[f.vdn + i];
     for (int col = col0; col < col1; ++col) {
-        const cd* src = P.X + (int64_t)col * P.ncoef + f.par;
+        const cd* Lp = P.X + (int64_t)col * P.ncoef + f.par;
+        __syncwarp();
+        for (int i = lane; i < ncS; i += 32) src[i] = Lp[i];
+        __syncwarp();
         cd* Xc = P.X + (int64_t)col * P.ncoef + chq;
         for (int k = 0; k < P.fr; k += 2) {
             const int ni = (((chunk * P.fr + k) << 5) + lane) >> 2;
@@ -474,7 +495,7 @@ __device__ __forceinline__ void fam_dn(int fam, int chunk, const XPass& P, int c
             cd a = z, a2 = z;
             if (ni < ncD) {
                 // (m - n) = (mi - pS) - (ni - pD) = s (mod 4); C_{m-n} = Vb[-mi]
-                const cd* Vb = P.vec + f.vdn + ni + 2 * P.pS;
+                const cd* Vb = Cs + ni + 2 * P.pS;
                 const int mi0 = (ni - P.pD + P.pS + s) & 3;
                 if (two) {
                     const cd* Vb2 = Vb + min(8, ncD - 1 - ni);   // as fam_up
@@ -509,8 +530,10 @@ __device__ __forceinline__ void translate_item(int b, const XPass& P, int col0, 
     if (b < fb) {
         const int gw = b * 4 + (threadIdx.x >> 5);
         if (gw >= P.nq * P.fch) return;   // whole warps; the family work has no CTA barrier
-        if (P.down) fam_dn(gw / P.fch, gw % P.fch, P, col0, col1);
-        else fam_up(gw / P.fch, gw % P.fch, P, col0, col1, sm + (threadIdx.x >> 5) * 4 * (2 * P.pS + 1));
+        const int ncS = 2 * P.pS + 1, nv = 2 * (P.pS + P.pD) + 1;
+        cd* wsm = sm + (threadIdx.x >> 5) * ((P.down ? ncS : 4 * ncS) + nv);
+        if (P.down) fam_dn(gw / P.fch, gw % P.fch, P, col0, col1, wsm);
+        else fam_up(gw / P.fch, gw % P.fch, P, col0, col1, wsm);
     } else {
         b -= fb;
         translate_dst(b / P.nch, b % P.nch, P, col0, col1, sm);
