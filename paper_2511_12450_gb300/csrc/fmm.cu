@@ -297,7 +297,7 @@ void fmm_build(lfmm_geometry_s* g) {
         };
         // cell-to-cell base vectors, one per (layer, child level): the quadrant-3 child
         // (+w/2, +w/2); the other quadrants' vectors differ from it by the phases of
-        // quarter turns, which the quadrant form applies (quad_up / quad_dn)
+        // quarter turns, which the quadrant form applies (fam_up / fam_dn)
         std::vector<int64_t> up_tab(nl * nlev, -1), dn_tab(nl * nlev, -1);
         for (int lay = 0; lay < nl; ++lay)
             for (int l = l0 + 1; l <= D; ++l) {
