@@ -252,12 +252,18 @@ void fmm_build(lfmm_geometry_s* g) {
         // P2M entries: leaves about cell centres, straddling boxes about reaction centres
         std::vector<ExpEntry> leaf_e, slot_e, slot_leaf_e;
         for (int b = t.level_start[D]; b < t.level_start[D + 1]; ++b)
-            leaf_e.push_back(ExpEntry{t.box_begin[b], t.box_end[b], t.box_layer[b], t.p_level[D], t.cx(b), t.cy(b), off[b]});
+            leaf_e.push_back(ExpEntry{t.box_begin[b], t.box_end[b], t.box_layer[b], t.p_level[D], t.cx(b), t.cy(b), off[b],
+                                      t.box_begin[b]});
+        int64_t brows = g->n;   // basis rows: the points, then each straddling leaf's points again
         for (int q = 0; q < g->n_slots; ++q) {
             int b = slot_box[q];
             ExpEntry e{t.box_begin[b], t.box_end[b], t.box_layer[b], t.p_level[t.box_level[b]], t.cx(b), slot_cy[q],
-                       slot_coef[q]};
-            if (t.box_level[b] == D) { slot_e.push_back(e); slot_leaf_e.push_back(e); }
+                       slot_coef[q], brows};
+            if (t.box_level[b] == D) {
+                slot_e.push_back(e);
+                slot_leaf_e.push_back(e);
+                brows += t.box_end[b] - t.box_begin[b];
+            }
         }
         g->n_leaf_entries = (int)leaf_e.size();
         g->n_slot_entries = (int)slot_e.size();
@@ -276,6 +282,21 @@ void fmm_build(lfmm_geometry_s* g) {
         g->d_leaf_entries = dupload(g, leaf_e);
         g->d_slot_entries = dupload(g, slot_e);
         g->d_slot_leaf_entries = dupload(g, slot_leaf_e);
+        // the P2M / L2P basis of every (entry, point), once: J_n(k rho) e^{i n theta} up to the
+        // leaf order (one more for the combined field's dipole basis)
+        g->basis_ord = t.p_level[D] + (g->combined ? 1 : 0);
+        g->d_basis = dalloc<cd>(g, (size_t)brows * (g->basis_ord + 1));
+        {
+            const size_t smem = (size_t)g->group_max_pts * (g->basis_ord + 1) * sizeof(double);
+            raise_smem_limit((const void*)k_basis, smem, "basis smem");
+            if (g->n_leaf_groups > 0)
+                k_basis<<<g->n_leaf_groups, 128, smem>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
+                                                         g->basis_ord, g->d_basis);
+            if (g->n_slot_groups > 0)
+                k_basis<<<g->n_slot_groups, 128, smem>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x, g->d_y,
+                                                         g->basis_ord, g->d_basis);
+            cuda_check(cudaGetLastError(), "k_basis");
+        }
         // Upward (M2M) and downward (L2L) passes.  Cells translate as families (a
         // parent and its children, k_translate); each reaction centre of a straddling
         // cell is a destination with its sources and one translation vector per source:
@@ -687,7 +708,7 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
     const int gp = g->group_max_pts, ge = g->group_max_ent;
     const int rs_p2m = 2 * (g->combined ? pD + 1 : pD) + 1;   // basis row length (k_p2m)
     const size_t smem_p2m = (size_t)gp * rs_p2m * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int);
-    const size_t smem_l2p = ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd);
+    const size_t smem_l2p = (size_t)ge * 2 * (pD + 1) * sizeof(cd);
     raise_smem_limit((const void*)k_p2m, smem_p2m, "p2m smem");
     raise_smem_limit((const void*)k_l2p, smem_l2p, "l2p smem");
     // precision form: the levels >= lm run in FP32 on scaled expansions (lm > D: none)
@@ -698,15 +719,15 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         if (lm <= D) {
             mixed_p2m(g, x_sorted, nrhs, s);
         } else {
-            k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
-                                                          g->d_w, g->d_nx, g->d_ny, x_sorted, g->n, nrhs, g->ncoef,
-                                                          g->d_M);
+            k_p2m<<<g->n_leaf_groups, 128, smem_p2m, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_w, g->d_nx,
+                                                          g->d_ny, g->d_basis, g->basis_ord + 1, x_sorted, g->n, nrhs,
+                                                          g->ncoef, g->d_M);
             cuda_check(cudaGetLastError(), "k_p2m");
             ++g->n_launches;
             if (g->n_slot_groups > 0) {
-                k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_x,
-                                                              g->d_y, g->d_w, g->d_nx, g->d_ny, x_sorted, g->n, nrhs,
-                                                              g->nslotcoef, g->d_Mp);
+                k_p2m<<<g->n_slot_groups, 128, smem_p2m, s>>>(g->d_slot_groups, g->d_slot_entries, g->m, g->d_w,
+                                                              g->d_nx, g->d_ny, g->d_basis, g->basis_ord + 1, x_sorted,
+                                                              g->n, nrhs, g->nslotcoef, g->d_Mp);
                 cuda_check(cudaGetLastError(), "k_p2m slots");
                 ++g->n_launches;
             }
@@ -752,13 +773,13 @@ void fmm_apply(lfmm_geometry_s* g, const cd* x_sorted, cd* y_sorted, int nrhs, c
         if (lm <= D) {
             mixed_l2p(g, y_sorted, nrhs, s);
         } else {
-            k_l2p<<<g->n_leaf_groups, 128, smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y,
-                                                          g->n, nrhs, g->ncoef, g->d_L, y_sorted);
+            k_l2p<<<g->n_leaf_groups, 128, smem_l2p, s>>>(g->d_leaf_groups, g->d_leaf_entries, g->d_basis,
+                                                          g->basis_ord + 1, g->n, nrhs, g->ncoef, g->d_L, y_sorted);
             cuda_check(cudaGetLastError(), "k_l2p");
             ++g->n_launches;
             if (g->n_slot_groups > 0) {
-                k_l2p<<<g->n_slot_groups, 128, smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->m,
-                                                              g->d_x, g->d_y, g->n, nrhs, g->nslotcoef, g->d_Lp,
+                k_l2p<<<g->n_slot_groups, 128, smem_l2p, s>>>(g->d_slot_groups, g->d_slot_leaf_entries, g->d_basis,
+                                                              g->basis_ord + 1, g->n, nrhs, g->nslotcoef, g->d_Lp,
                                                               y_sorted);
                 cuda_check(cudaGetLastError(), "k_l2p slots");
                 ++g->n_launches;
@@ -778,7 +799,9 @@ struct P2MJob {
     const ExpGroup* groups;
     const ExpEntry* ent;
     MediumDev m;
-    const double *px, *py, *pw, *nx, *ny;
+    const double *pw, *nx, *ny;
+    const cd* basis;
+    int bstride;
     const cd* phi;
     int64_t n, stride;
     int nrhs;
@@ -787,8 +810,8 @@ struct P2MJob {
 struct L2PJob {
     const ExpGroup* groups;
     const ExpEntry* ent;
-    MediumDev m;
-    const double *px, *py;
+    const cd* basis;
+    int bstride;
     int64_t n, stride;
     int nrhs;
     const cd* L;
@@ -824,14 +847,14 @@ __global__ void __launch_bounds__(128) k_p2m_multi(const P2MJob* __restrict__ jo
                                                    int njobs) {
     const int j = job_of(prefix, njobs, blockIdx.x);
     const P2MJob& J = jobs[j];
-    p2m_group(blockIdx.x - prefix[j], J.groups, J.ent, J.m, J.px, J.py, J.pw, J.nx, J.ny, J.phi, J.n, J.nrhs,
+    p2m_group(blockIdx.x - prefix[j], J.groups, J.ent, J.m, J.pw, J.nx, J.ny, J.basis, J.bstride, J.phi, J.n, J.nrhs,
               J.stride, J.M);
 }
 __global__ void __launch_bounds__(128) k_l2p_multi(const L2PJob* __restrict__ jobs, const int* __restrict__ prefix,
                                                    int njobs) {
     const int j = job_of(prefix, njobs, blockIdx.x);
     const L2PJob& J = jobs[j];
-    l2p_group(blockIdx.x - prefix[j], J.groups, J.ent, J.m, J.px, J.py, J.n, J.nrhs, J.stride, J.L, J.y);
+    l2p_group(blockIdx.x - prefix[j], J.groups, J.ent, J.basis, J.bstride, J.n, J.nrhs, J.stride, J.L, J.y);
 }
 __global__ void __launch_bounds__(128) k_translate_multi(const XJob* __restrict__ jobs, const int* __restrict__ prefix,
                                                          int njobs) {
@@ -905,7 +928,7 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
         const int pD = t.p_level[t.D], gp = g->group_max_pts, ge = g->group_max_ent;
         const int rs = 2 * (g->combined ? pD + 1 : pD) + 1;
         smem_p2m = std::max(smem_p2m, (size_t)gp * rs * sizeof(cd) + (size_t)gp * sizeof(cd) + (size_t)(gp + 1) * sizeof(int));
-        smem_l2p = std::max(smem_l2p, ((size_t)gp * (pD + 1) + 1) * sizeof(double) + (size_t)ge * 2 * (pD + 1) * sizeof(cd));
+        smem_l2p = std::max(smem_l2p, (size_t)ge * 2 * (pD + 1) * sizeof(cd));
         max_up = std::max(max_up, t.D - t.l0);
         max_dn = std::max(max_dn, t.D - t.l0);
     }
@@ -920,11 +943,11 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
         std::vector<int> blocks;
         for (const BatchOp* op : far) {
             lfmm_geometry_s* g = op->g;
-            jobs.push_back(P2MJob{g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y, g->d_w, g->d_nx, g->d_ny,
-                                  op->x, g->n, g->ncoef, op->nrhs, g->d_M});
+            jobs.push_back(P2MJob{g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_w, g->d_nx, g->d_ny, g->d_basis,
+                                  g->basis_ord + 1, op->x, g->n, g->ncoef, op->nrhs, g->d_M});
             blocks.push_back(g->n_leaf_groups);
-            jobs.push_back(P2MJob{g->d_slot_groups, g->d_slot_entries, g->m, g->d_x, g->d_y, g->d_w, g->d_nx,
-                                  g->d_ny, op->x, g->n, g->nslotcoef, op->nrhs, g->d_Mp});
+            jobs.push_back(P2MJob{g->d_slot_groups, g->d_slot_entries, g->m, g->d_w, g->d_nx, g->d_ny, g->d_basis,
+                                  g->basis_ord + 1, op->x, g->n, g->nslotcoef, op->nrhs, g->d_Mp});
             blocks.push_back(g->n_slot_groups);
         }
         launch_jobs(jobs, blocks, k_p2m_multi, 128, smem_p2m, s, "k_p2m_multi");
@@ -991,11 +1014,11 @@ void fmm_apply_batch(const std::vector<BatchOp>& ops, cudaStream_t s, cudaEvent_
         for (const BatchOp* op : far) {
             lfmm_geometry_s* g = op->g;
             if (slots == 0) {
-                jobs.push_back(L2PJob{g->d_leaf_groups, g->d_leaf_entries, g->m, g->d_x, g->d_y, g->n, g->ncoef,
-                                      op->nrhs, g->d_L, op->y});
+                jobs.push_back(L2PJob{g->d_leaf_groups, g->d_leaf_entries, g->d_basis, g->basis_ord + 1, g->n,
+                                      g->ncoef, op->nrhs, g->d_L, op->y});
                 blocks.push_back(g->n_leaf_groups);
             } else {
-                jobs.push_back(L2PJob{g->d_slot_groups, g->d_slot_leaf_entries, g->m, g->d_x, g->d_y, g->n,
+                jobs.push_back(L2PJob{g->d_slot_groups, g->d_slot_leaf_entries, g->d_basis, g->basis_ord + 1, g->n,
                                       g->nslotcoef, op->nrhs, g->d_Lp, op->y});
                 blocks.push_back(g->n_slot_groups);
             }

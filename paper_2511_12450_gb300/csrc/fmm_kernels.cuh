@@ -53,9 +53,9 @@ __device__ __forceinline__ void group_point(const ExpEntry* __restrict__ ent, in
 // translations are linear and carry it unchanged.
 __device__ __forceinline__ void p2m_group(int gi, const ExpGroup* __restrict__ groups,
                                           const ExpEntry* __restrict__ ent, const MediumDev& m,
-                                          const double* __restrict__ px, const double* __restrict__ py,
                                           const double* __restrict__ pw, const double* __restrict__ nx,
-                                          const double* __restrict__ ny, const cd* __restrict__ phi, int64_t n,
+                                          const double* __restrict__ ny, const cd* __restrict__ basis,
+                                          int bstride, const cd* __restrict__ phi, int64_t n,
                                           int nrhs, int64_t stride, cd* __restrict__ M) {
     extern __shared__ cd su[];   // [npts][rs] basis rows, then [npts] q, then [nent + 1] point offsets (ints)
     const ExpGroup G = groups[gi];
@@ -74,22 +74,15 @@ __device__ __forceinline__ void p2m_group(int gi, const ExpGroup* __restrict__ g
         int er, j;
         group_point(ent, G.e0, G.e1, t, &er, &j);
         const ExpEntry& E = ent[G.e0 + er];
-        const double dx = px[j] - E.cx, dy = py[j] - E.cy;
-        const double rho = hypot(dx, dy);
         cd* u = su + (size_t)t * rs;
-        double* Jd = (double*)u;   // J_0..J_pb in the first pb+1 doubles of the row
-        bessel_j_seq_small(m.k[E.lay] * rho, pb, Jd);
-        double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
-        const cd z = (rho > 0.0) ? mk(dx * irho, -dy * irho) : mk(1.0, 0.0);
-        // u_n, n = 0..pb, into cd slots pb..2pb (doubles 2pb.., above the J's),
-        // z^n upward from z^0 = 1
-        cd zn = mk(1.0, 0.0);
+        // u_n = J_n(k rho) e^{-i n theta} = conj of the stored basis, n = 0..pb, into slots pb..2pb
+        const cd* b = basis + (E.brow + (j - E.beg)) * (int64_t)bstride;
         for (int k2 = 0; k2 <= pb; ++k2) {
-            if (k2 > 0) zn = zn * z;
-            u[pb + k2] = Jd[k2] * zn;
+            const cd v = b[k2];
+            u[pb + k2] = mk(v.x, -v.y);
         }
-        // u_{-n} = (-1)^n conj(u_n) into slots pb-1..0 (the J's are no longer needed);
-        // the signs by integer bit flips (no FP64 instruction)
+        // u_{-n} = (-1)^n conj(u_n) into slots pb-1..0; the signs by integer bit flips
+        // (no FP64 instruction)
         for (int k2 = 1; k2 <= pb; ++k2) {
             const cd v = u[pb + k2];
             u[pb - k2] = mk(dsign(v.x, k2), dsign(v.y, k2 + 1));
@@ -122,10 +115,39 @@ __device__ __forceinline__ void p2m_group(int gi, const ExpGroup* __restrict__ g
     }
 }
 __global__ void __launch_bounds__(128) k_p2m(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
-                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py,
-                      const double* __restrict__ pw, const double* __restrict__ nx, const double* __restrict__ ny,
+                      MediumDev m, const double* __restrict__ pw, const double* __restrict__ nx,
+                      const double* __restrict__ ny, const cd* __restrict__ basis, int bstride,
                       const cd* __restrict__ phi, int64_t n, int nrhs, int64_t stride, cd* __restrict__ M) {
-    p2m_group(blockIdx.x, groups, ent, m, px, py, pw, nx, ny, phi, n, nrhs, stride, M);
+    p2m_group(blockIdx.x, groups, ent, m, pw, nx, ny, basis, bstride, phi, n, nrhs, stride, M);
+}
+
+// The expansion basis of every (entry, point), computed once per geometry:
+// b_n = J_n(k rho) e^{i n theta}, n = 0..ord, with (rho, theta) the point's polar
+// coordinates about the entry's centre (the cell centre, or a straddling leaf's reaction
+// centre).  L2P uses b_n, P2M its conjugate.  e^{i n theta} by powers upward from 1.
+__global__ void __launch_bounds__(128) k_basis(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
+                                               MediumDev m, const double* __restrict__ px,
+                                               const double* __restrict__ py, int ord, cd* __restrict__ basis) {
+    extern __shared__ double sjb[];   // [npts][ord + 1] J_n
+    const ExpGroup G = groups[blockIdx.x];
+    for (int t = threadIdx.x; t < G.npts; t += blockDim.x) {
+        int er, j;
+        group_point(ent, G.e0, G.e1, t, &er, &j);
+        const ExpEntry& E = ent[G.e0 + er];
+        const double dx = px[j] - E.cx, dy = py[j] - E.cy;
+        const double rho = hypot(dx, dy);
+        double* J = sjb + (size_t)t * (ord + 1);
+        bessel_j_seq_small(m.k[E.lay] * rho, ord, J);
+        const double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
+        const cd z = (rho > 0.0) ? mk(dx * irho, dy * irho) : mk(1.0, 0.0);
+        cd* b = basis + (E.brow + (j - E.beg)) * (int64_t)(ord + 1);
+        b[0] = mk(J[0], 0.0);
+        cd zz = mk(1.0, 0.0);
+        for (int k2 = 1; k2 <= ord; ++k2) {
+            zz = zz * z;
+            b[k2] = mk(J[k2] * zz.x, J[k2] * zz.y);
+        }
+    }
 }
 
 // M2L into the target boxes of levels >= l0 (free space and reaction components).
@@ -260,17 +282,16 @@ __global__ void __launch_bounds__(64) k_m2l_reduce(const M2LReduce* __restrict__
 // L2P over a list of point ranges: y_i += sum_n L_n J_n(k rho_i) e^{i n theta_i}
 // about (cx, cy).  Leaves (cell centres) and straddling leaves (reaction centres).
 __device__ __forceinline__ void l2p_group(int gi, const ExpGroup* __restrict__ groups,
-                      const ExpEntry* __restrict__ ent, const MediumDev& m, const double* __restrict__ px,
-                      const double* __restrict__ py, int64_t n, int nrhs, int64_t stride, const cd* __restrict__ L,
-                      cd* __restrict__ y) {
+                      const ExpEntry* __restrict__ ent, const cd* __restrict__ basis, int bstride, int64_t n,
+                      int nrhs, int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
     // y_j += sum_n L_n J_n(k rho_j) e^{i n theta_j}.  Per entry, A_n = L_n and
     // B_n = (-1)^n L_{-n} are folded into P_n = A_n + B_n and Q_n = A_n - B_n, so
-    // that A_n z^n + B_n conj(z^n) = P_n cos(n theta) + i Q_n sin(n theta).
-    extern __shared__ double sj[];   // [npts][p+1] J_n, then [nent][2][p+1] (P, Q)
+    // that A_n z^n + B_n conj(z^n) = P_n cos(n theta) + i Q_n sin(n theta); the point's
+    // J_n cos(n theta) and J_n sin(n theta) are its stored basis row.
+    extern __shared__ cd sPQ[];   // [nent][2][p+1] (P, Q)
     const ExpGroup G = groups[gi];
     const int p = ent[G.e0].p, np1 = p + 1;
     const int ne = G.e1 - G.e0;
-    cd* sPQ = (cd*)(sj + (((size_t)G.npts * np1 + 1) & ~(size_t)1));
     for (int col = 0; col < nrhs; ++col) {
         __syncthreads();
         for (int i = threadIdx.x; i < ne * np1; i += blockDim.x) {
@@ -286,30 +307,23 @@ __device__ __forceinline__ void l2p_group(int gi, const ExpGroup* __restrict__ g
             int er, j;
             group_point(ent, G.e0, G.e1, t, &er, &j);
             const ExpEntry& E = ent[G.e0 + er];
-            const double dx = px[j] - E.cx, dy = py[j] - E.cy;
-            const double rho = hypot(dx, dy);
-            double* J = sj + (size_t)t * np1;
-            if (col == 0) bessel_j_seq_small(m.k[E.lay] * rho, p, J);
-            const double irho = (rho > 0.0) ? 1.0 / rho : 0.0;
-            const cd z = (rho > 0.0) ? mk(dx * irho, dy * irho) : mk(1.0, 0.0);
+            const cd* b = basis + (E.brow + (j - E.beg)) * (int64_t)bstride;
             const cd* P = sPQ + (er * 2) * np1;
             const cd* Q = P + np1;
-            cd acc = P[0] * J[0];
-            cd zz = mk(1.0, 0.0);
+            cd acc = P[0] * b[0].x;
             for (int k2 = 1; k2 <= p; ++k2) {
-                zz = zz * z;
-                const double cj = J[k2] * zz.x, sjn = J[k2] * zz.y;
-                acc.x = fma(P[k2].x, cj, fma(-Q[k2].y, sjn, acc.x));
-                acc.y = fma(P[k2].y, cj, fma(Q[k2].x, sjn, acc.y));
+                const cd v = b[k2];
+                acc.x = fma(P[k2].x, v.x, fma(-Q[k2].y, v.y, acc.x));
+                acc.y = fma(P[k2].y, v.x, fma(Q[k2].x, v.y, acc.y));
             }
             y[(int64_t)col * n + j] += acc;
         }
     }
 }
 __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups, const ExpEntry* __restrict__ ent,
-                      MediumDev m, const double* __restrict__ px, const double* __restrict__ py, int64_t n, int nrhs,
-                      int64_t stride, const cd* __restrict__ L, cd* __restrict__ y) {
-    l2p_group(blockIdx.x, groups, ent, m, px, py, n, nrhs, stride, L, y);
+                      const cd* __restrict__ basis, int bstride, int64_t n, int nrhs, int64_t stride,
+                      const cd* __restrict__ L, cd* __restrict__ y) {
+    l2p_group(blockIdx.x, groups, ent, basis, bstride, n, nrhs, stride, L, y);
 }
 
 // Multipole-to-multipole and local-to-local translations (Graf's addition theorem),

@@ -54,6 +54,7 @@ struct ExpEntry {
     int beg, end, lay, p;
     double cx, cy;
     int64_t off;   // coefficient offset in the output/input array
+    int64_t brow;  // row of the entry's first point in the stored expansion basis
 };
 // consecutive entries processed by one CTA (at most EXP_GROUP_PTS points and
 // EXP_GROUP_ENTRIES entries, or a single larger entry)
@@ -201,6 +202,10 @@ struct lfmm_geometry_s {
     int n_leaf_entries = 0, n_slot_entries = 0, n_slot_leaf_entries = 0;
     lfmm::ExpEntry *d_leaf_entries = nullptr, *d_slot_entries = nullptr, *d_slot_leaf_entries = nullptr;
     lfmm::ExpGroup *d_leaf_groups = nullptr, *d_slot_groups = nullptr;   // P2M / L2P work groups
+    // J_n(k rho) e^{i n theta}, n = 0..basis_ord, one row per (entry, point): leaf entries at
+    // rows 0..n-1 (the point's index), straddling leaves' reaction-centre entries after them
+    cd* d_basis = nullptr;
+    int basis_ord = 0;
     int n_leaf_groups = 0, n_slot_groups = 0, group_max_pts = 1, group_max_ent = 1;
     // M2M (up) and L2L (down) passes: per level, a range of destinations
     // (cells and reaction centres) with their sources and translation vectors

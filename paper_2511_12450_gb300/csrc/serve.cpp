@@ -90,10 +90,12 @@ namespace {
 
 // Device bytes one request holds while it runs: the Krylov basis (max_iter + 1
 // vectors), the stored near field and preconditioner (~62 and ~50 complex entries
-// per point at leaf size 64), multipoles/locals and work vectors, and the
-// reaction tables and set-up scratch (a fixed allowance).
+// per point at leaf size 64), the leaf expansion basis (p + 2 complex values per
+// point), multipoles/locals and work vectors, and the reaction tables and set-up
+// scratch (a fixed allowance).
 int64_t footprint_estimate(int64_t n, int p, int leaf, int max_iter) {
-    const double per_point = 16.0 * (max_iter + 1) + 16.0 * (1.0 + leaf / 64.0) * 120.0 + 16.0 * 24.0;
+    const double per_point = 16.0 * (max_iter + 1) + 16.0 * (1.0 + leaf / 64.0) * 120.0 + 16.0 * 24.0 +
+                             16.0 * (p + 2.0);
     const double expansions = 16.0 * (2.0 * p + 1.0) * (double)n / 4.0;
     return (int64_t)(per_point * (double)n + expansions) + ((int64_t)256 << 20);
 }
