@@ -339,12 +339,15 @@ __global__ void __launch_bounds__(128) k_l2p(const ExpGroup* __restrict__ groups
 //    exchanges of real and imaginary parts).  A family thus costs one Toeplitz
 //    product instead of one per child.  The work is by warps: lane (n, s) of a round
 //    (32 consecutive pairs, 8 outputs x 4 residues) sums the terms of residue s of
-//    output n, and the 4 lanes of an output combine by shuffles in a fixed order;
+//    output n, and the 4 lanes of an output combine by shuffles in a fixed order.
+//    Each warp first stages its base vector and sources in shared memory;
 //  - reaction centres of straddling cells, and the cells that take a straddling
-//    parent's reaction-centre local (XDst), one CTA each, a sum over their own sources,  dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].  A CTA of
-//    128 threads owns w consecutive output indices (one per lane of a w-lane row; w =
-//    XT_W or all 2p+1 of them, see lane_width) and 128 / w slices of the sum over m,
-//    reduced in a fixed order.
+//    parent's reaction-centre local (XDst), one CTA each, a sum over their own sources,
+//      dst_n (= or +=) sum_j sum_m src_j[m] V_j[n - m + pS_j + pD].
+//    A CTA of 128 threads owns w consecutive output indices (one per lane of a w-lane
+//    row; w = XT_W or all 2p+1 of them, see lane_width) and 128 / w slices of the sum
+//    over m, reduced in a fixed order; each source and its vector window are staged in
+//    shared memory.
 // Every sum runs in a fixed order, so results are reproducible.
 struct XPass {
     const XDst* dsts;
